@@ -1,0 +1,146 @@
+/*
+ * stokesgpu.h -- C ABI of the GB300 (sm_103a) Stokes layer-potential library.
+ *
+ * The library evaluates the smooth-quadrature sums of the two Stokes layer
+ * potentials used by the boundary-integral red-blood-cell method of Lu,
+ * Morse, Rahimian, Stadler and Zorin (SC'19):
+ *
+ *   single layer, Eq. "sl_stokes" (Sec. 2.1):
+ *     u(x_i) = 1/(8 pi mu) sum_j [ I/|r| + r r^T/|r|^3 ] w_j f_j
+ *   double layer, kernel of Eq. "double_layer_int_eq" (Sec. 2.1):
+ *     u(x_i) = 6/(8 pi)    sum_j [ r r^T (r . n_j)/|r|^5 ] w_j phi_j
+ *   with r = x_i - y_j, n_j the outward unit normal at source y_j and w_j its
+ *   quadrature weight; the sum over quadrature nodes is the discretisation of
+ *   Sec. 3.1, Eq. "smooth_double_layer_int_eq_patches_disc", and their
+ *   superposition is Eq. "velocity_combined".
+ *
+ * Conventions shared by every entry point:
+ *   - All array arguments are DEVICE pointers owned by the caller, FP64,
+ *     vectors as AoS [n][3] row-major; index arrays are int32 or int64 as
+ *     declared.  Nothing is retained after the call returns.
+ *   - A pair at exactly zero distance (in particular target i == source i
+ *     when the targets are the sources) contributes nothing.
+ *   - `out` is [nt][3] FP64.  With opts->accumulate == 0 it is overwritten,
+ *     otherwise the result is added to it.
+ *   - `workspace` is caller-allocated device memory of at least the size the
+ *     matching *_workspace_size query returns for the same sizes and options,
+ *     aligned to 256 bytes.  The library allocates nothing itself.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     only enqueues work on it and never synchronises it.
+ *   - Errors are returned as stk_status; stokes_last_error() gives a message
+ *     for the calling thread.  Arguments are validated before anything is
+ *     enqueued; an invalid call enqueues nothing.
+ *   - Device-side failures (a bounded wait that ran out) are recorded in the
+ *     workspace and reported by stokes_device_status() after the caller has
+ *     synchronised the stream.
+ */
+#ifndef STOKESGPU_H
+#define STOKESGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  STK_OK = 0,
+  STK_EINVAL = 1,       /* bad argument (NULL pointer, negative size, bad option) */
+  STK_ENOMEM = 2,       /* workspace smaller than required */
+  STK_ECUDA = 3,        /* a CUDA runtime call failed */
+  STK_ETIMEOUT = 4,     /* a device wait ran out (see stokes_device_status) */
+  STK_EUNSUPPORTED = 5  /* size or option outside what the library supports */
+} stk_status;
+
+typedef enum {
+  /* FP64 throughout: pair differences, 1/r and products in double. */
+  STK_FP64 = 0,
+  /* FP32 pair arithmetic in per-work-item local frames with compensated
+   * (two-sum) accumulation; pairs closer than near_ratio * h_j get their
+   * difference x - y and 1/|r| in FP64. */
+  STK_MIXED = 1
+} stk_precision;
+
+typedef struct {
+  int32_t precision;    /* stk_precision */
+  double near_ratio;    /* alpha: a pair is "near" when |r| < alpha * h_j (MIXED only); >= 0 */
+  int32_t accumulate;   /* 0: out = u; 1: out += u */
+  int32_t source_splits;/* direct sums: split the sources into this many parts (0 = automatic) */
+  int32_t tile_config;  /* -1 = tuned default; otherwise a config id from stokes_autotune */
+} stk_opts;
+
+/* Defaults: MIXED, alpha = 2, overwrite, automatic splits, tuned config. */
+void stokes_default_opts(stk_opts *opts);
+
+/* ---------------------------------------------------------------- direct sums
+ * src [ns][3], trg [nt][3]; f, phi, nrm [ns][3]; w [ns]; h [ns] local spacing
+ * (may be NULL: then only exactly coincident pairs take the FP64 path).
+ * Targets may alias the sources.  ns, nt in [0, 2^31 - 1].
+ */
+stk_status stokes_sl_eval(const double *src, const double *f, const double *w, const double *h,
+                          int64_t ns, const double *trg, int64_t nt, double mu, double *out,
+                          const stk_opts *opts, void *workspace, size_t workspace_bytes,
+                          void *stream);
+stk_status stokes_dl_eval(const double *src, const double *nrm, const double *phi,
+                          const double *w, const double *h, int64_t ns, const double *trg,
+                          int64_t nt, double *out, const stk_opts *opts, void *workspace,
+                          size_t workspace_bytes, void *stream);
+/* SL[f] + DL[phi] over one source set (Eq. "velocity_combined"). */
+stk_status stokes_sldl_eval(const double *src, const double *f, const double *nrm,
+                            const double *phi, const double *w, const double *h, int64_t ns,
+                            const double *trg, int64_t nt, double mu, double *out,
+                            const stk_opts *opts, void *workspace, size_t workspace_bytes,
+                            void *stream);
+/* kernels: 1 = SL, 2 = DL, 3 = SL + DL. */
+stk_status stokes_direct_workspace_size(int64_t ns, int64_t nt, int32_t kernels,
+                                        const stk_opts *opts, size_t *bytes);
+
+/* ------------------------------------------------------------ FMM near field
+ * P2P over octree U-lists (Sec. 3.1 "Far evaluation": the direct part of the
+ * FMM).  pts [n][3] are sorted so that leaf l owns points
+ * [leaf_ptr[l], leaf_ptr[l+1]); ulist_idx[ulist_ptr[l] .. ulist_ptr[l+1]) are
+ * the leaves adjacent to l (l included).  Every point is a source and a
+ * target: out_i = sum over sources in the leaves of U(leaf(i)).
+ * kernels: 1 = SL (uses f), 2 = DL (uses nrm, phi), 3 = both.  Unused density
+ * pointers may be NULL.  Leaves may hold at most 65535 points.
+ */
+stk_status stokes_p2p_leaflists(const double *pts, const double *f, const double *phi,
+                                const double *nrm, const double *w, const double *h, int64_t n,
+                                const int32_t *leaf_ptr, int32_t nleaf, const int32_t *ulist_ptr,
+                                const int32_t *ulist_idx, int64_t nulist, int32_t kernels,
+                                double mu, double *out, const stk_opts *opts, void *workspace,
+                                size_t workspace_bytes, void *stream);
+stk_status stokes_p2p_workspace_size(int64_t n, int32_t nleaf, int32_t kernels,
+                                     const stk_opts *opts, size_t *bytes);
+
+/* ---------------------------------------------------- batched suspensions
+ * S independent suspensions in one launch (Eq. "velocity_combined" per
+ * suspension).  Suspension s owns points [susp_ptr[s], susp_ptr[s+1]); its
+ * first n_cell[s] points are cell points carrying the single-layer density f,
+ * the rest are vessel-wall points carrying the double-layer density phi.
+ * Targets are all points of s: out_i = SL_cells(s)[f] + DL_wall(s)[phi].
+ * susp_ptr [S+1] and n_cell [S] are device int64 arrays; susp_ptr[S] = n.
+ */
+stk_status stokes_batched_eval(const double *pts, const double *f, const double *phi,
+                               const double *nrm, const double *w, const double *h, int64_t n,
+                               const int64_t *susp_ptr, const int64_t *n_cell, int32_t nsusp,
+                               double mu, double *out, const stk_opts *opts, void *workspace,
+                               size_t workspace_bytes, void *stream);
+stk_status stokes_batched_workspace_size(int64_t n, int32_t nsusp, const stk_opts *opts,
+                                         size_t *bytes);
+
+/* ----------------------------------------------------------------- status */
+/* Reads the device error word kept in a workspace used by an earlier call.
+ * The caller must have synchronised the stream.  Returns STK_OK or
+ * STK_ETIMEOUT, and clears the word. */
+stk_status stokes_device_status(void *workspace, size_t workspace_bytes);
+/* Message for the last error on the calling thread ("" if none). */
+const char *stokes_last_error(void);
+/* Library version string. */
+const char *stokes_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,11 @@
+"""GB300-native Stokes layer-potential sums (single layer, double layer,
+their superposition, the FMM near field over U-lists and batched
+suspensions) behind the C ABI of include/stokesgpu.h.
+
+The compute path is libstokesgpu.so (hand-written CUDA for sm_103a); this
+package only marshals PyTorch tensors into it.  Build the library with
+paper_1909_11085_gb300.build.build().
+"""
+from .ops import sl, dl, sldl, p2p, batched, P2PPlan, BatchedPlan  # noqa: F401
+
+__all__ = ["sl", "dl", "sldl", "p2p", "batched", "P2PPlan", "BatchedPlan"]

@@ -1,0 +1,130 @@
+"""ctypes binding of libstokesgpu.so (the C ABI in include/stokesgpu.h).
+
+Argument marshalling only: tensors are checked (CUDA, float64/int32/int64,
+contiguous), a workspace of the size the library asks for is taken from the
+PyTorch caching allocator, and the call is enqueued on the current stream.
+Every arithmetic step runs in the library's kernels.  The library must have
+been built (paper_1909_11085_gb300.build.build()); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstokesgpu.so")
+
+STK_OK, STK_EINVAL, STK_ENOMEM, STK_ECUDA, STK_ETIMEOUT, STK_EUNSUPPORTED = range(6)
+STK_FP64, STK_MIXED = 0, 1
+SL, DL, SLDL = 1, 2, 3
+
+EXPORTS = [
+    "stokes_default_opts", "stokes_sl_eval", "stokes_dl_eval", "stokes_sldl_eval",
+    "stokes_direct_workspace_size", "stokes_p2p_leaflists", "stokes_p2p_workspace_size",
+    "stokes_batched_eval", "stokes_batched_workspace_size", "stokes_device_status",
+    "stokes_last_error", "stokes_version",
+]
+
+
+class StkOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("near_ratio", ctypes.c_double),
+                ("accumulate", ctypes.c_int32), ("source_splits", ctypes.c_int32),
+                ("tile_config", ctypes.c_int32)]
+
+
+class StokesError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"stokesgpu status {status}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "paper_1909_11085_gb300.build.build() (nvcc, sm_103a)")
+            L = ctypes.CDLL(LIB_PATH)
+            p, i32, i64, d, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                                  ctypes.c_size_t)
+            po = ctypes.POINTER(StkOpts)
+            psz = ctypes.POINTER(ctypes.c_size_t)
+            L.stokes_default_opts.argtypes = [po]
+            L.stokes_default_opts.restype = None
+            L.stokes_last_error.restype = ctypes.c_char_p
+            L.stokes_version.restype = ctypes.c_char_p
+            L.stokes_sl_eval.argtypes = [p, p, p, p, i64, p, i64, d, p, po, p, sz, p]
+            L.stokes_dl_eval.argtypes = [p, p, p, p, p, i64, p, i64, p, po, p, sz, p]
+            L.stokes_sldl_eval.argtypes = [p, p, p, p, p, p, i64, p, i64, d, p, po, p, sz, p]
+            L.stokes_direct_workspace_size.argtypes = [i64, i64, i32, po, psz]
+            L.stokes_p2p_leaflists.argtypes = [p, p, p, p, p, p, i64, p, i32, p, p, i64, i32, d, p,
+                                               po, p, sz, p]
+            L.stokes_p2p_workspace_size.argtypes = [i64, i32, i32, po, psz]
+            L.stokes_batched_eval.argtypes = [p, p, p, p, p, p, i64, p, p, i32, d, p, po, p, sz, p]
+            L.stokes_batched_workspace_size.argtypes = [i64, i32, po, psz]
+            L.stokes_device_status.argtypes = [p, sz]
+            for name in EXPORTS:
+                fn = getattr(L, name)
+                if name not in ("stokes_default_opts", "stokes_last_error", "stokes_version"):
+                    fn.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def make_opts(precision="mixed", near_ratio=2.0, accumulate=False, source_splits=0,
+              tile_config=-1) -> StkOpts:
+    o = StkOpts()
+    lib().stokes_default_opts(ctypes.byref(o))
+    o.precision = STK_MIXED if precision in ("mixed", STK_MIXED) else STK_FP64
+    o.near_ratio = float(near_ratio)
+    o.accumulate = 1 if accumulate else 0
+    o.source_splits = int(source_splits)
+    o.tile_config = int(tile_config)
+    return o
+
+
+def check(status: int):
+    if status != STK_OK:
+        raise StokesError(status, lib().stokes_last_error().decode())
+
+
+def ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def stream_ptr(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 512), dtype=torch.uint8, device=device)
+
+
+def vec3(t, name, n=None):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if t.dim() != 2 or t.shape[1] != 3:
+        raise ValueError(f"{name} must have shape [n, 3]")
+    if n is not None and t.shape[0] != n:
+        raise ValueError(f"{name} has {t.shape[0]} rows, expected {n}")
+    return t.contiguous()
+
+
+def vec1(t, name, n, dtype=torch.float64):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != dtype:
+        raise TypeError(f"{name} must be a CUDA {dtype} tensor")
+    if t.dim() != 1 or (n is not None and t.shape[0] != n):
+        raise ValueError(f"{name} must have shape [{n}]")
+    return t.contiguous()

@@ -1,0 +1,501 @@
+// prep.cu -- staging kernels around the two engines: source packing, target
+// bounding box and Morton keys, a stable LSD radix sort, exclusive scans,
+// work-item builders for the direct, near-field (U-list) and batched forms,
+// and the final reduction/scatter into the caller's output.
+#include <cfloat>
+
+#include "common.cuh"
+#include "prep.cuh"
+
+namespace stk {
+
+// ---------------------------------------------------------------- packing
+// Mixed records: positions split hi/lo about the frame centre c = src[0];
+// quadrature weight and kernel constant folded into the densities
+// (q = w f / (8 pi mu), psi = w phi * 6 / (8 pi)); hh = (alpha h)^2.
+__global__ void k_pack_mixed(int64_t ns, const double *__restrict__ src,
+                             const double *__restrict__ f, const double *__restrict__ nrm,
+                             const double *__restrict__ phi, const double *__restrict__ w,
+                             const double *__restrict__ h, double alpha, double csl, double cdl,
+                             SrcRec *__restrict__ rec) {
+  const double cx = src[0], cy = src[1], cz = src[2];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ns;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    SrcRec R;
+    float hx, lx, hy, ly, hz, lz;
+    split_hl(src[3 * j] - cx, hx, lx);
+    split_hl(src[3 * j + 1] - cy, hy, ly);
+    split_hl(src[3 * j + 2] - cz, hz, lz);
+    double hh = 0.0;
+    if (h) {
+      const double a = alpha * h[j];
+      hh = a * a;
+    }
+    float hhf = (float)fmin(hh, (double)FLT_MAX);
+    hhf = fmaxf(hhf, FLT_MIN);  // exactly coincident points always take the FP64 path
+    R.yh = make_float4(hx, hy, hz, hhf);
+    R.yl = make_float4(lx, ly, lz, __int_as_float((int)j));
+    const double wj = w[j];
+    if (f)
+      R.q = make_float4((float)(wj * csl * f[3 * j]), (float)(wj * csl * f[3 * j + 1]),
+                        (float)(wj * csl * f[3 * j + 2]), 0.f);
+    else
+      R.q = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (phi) {
+      R.n = make_float4((float)nrm[3 * j], (float)nrm[3 * j + 1], (float)nrm[3 * j + 2], 0.f);
+      R.p = make_float4((float)(wj * cdl * phi[3 * j]), (float)(wj * cdl * phi[3 * j + 1]),
+                        (float)(wj * cdl * phi[3 * j + 2]), 0.f);
+    } else {
+      R.n = make_float4(0.f, 0.f, 0.f, 0.f);
+      R.p = R.n;
+    }
+    rec[j] = R;
+  }
+}
+
+__global__ void k_pack_fp64(int64_t ns, const double *__restrict__ src,
+                            const double *__restrict__ f, const double *__restrict__ nrm,
+                            const double *__restrict__ phi, const double *__restrict__ w,
+                            double csl, double cdl, SrcRec64 *__restrict__ rec) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ns;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    SrcRec64 R;
+    const double wj = w[j];
+    for (int k = 0; k < 3; ++k) {
+      R.y[k] = src[3 * j + k];
+      R.q[k] = f ? wj * csl * f[3 * j + k] : 0.0;
+      R.n[k] = phi ? nrm[3 * j + k] : 0.0;
+      R.p[k] = phi ? wj * cdl * phi[3 * j + k] : 0.0;
+    }
+    rec[j] = R;
+  }
+}
+
+// ---------------------------------------------------------------- bbox
+constexpr int kRedThreads = 256;
+
+__global__ void k_bbox_partial(int64_t n, const double *__restrict__ pts, double *__restrict__ part) {
+  __shared__ double sm[6][kRedThreads];
+  double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < 3; ++k) {
+      const double v = pts[3 * i + k];
+      mn[k] = fmin(mn[k], v);
+      mx[k] = fmax(mx[k], v);
+    }
+  for (int k = 0; k < 3; ++k) {
+    sm[k][threadIdx.x] = mn[k];
+    sm[3 + k][threadIdx.x] = mx[k];
+  }
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int k = 0; k < 3; ++k) {
+        sm[k][threadIdx.x] = fmin(sm[k][threadIdx.x], sm[k][threadIdx.x + s]);
+        sm[3 + k][threadIdx.x] = fmax(sm[3 + k][threadIdx.x], sm[3 + k][threadIdx.x + s]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 6; ++k) part[6 * blockIdx.x + k] = sm[k][0];
+}
+
+__global__ void k_bbox_final(int nblk, const double *__restrict__ part, double *__restrict__ box) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double b[6] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (int i = 0; i < nblk; ++i)
+    for (int k = 0; k < 3; ++k) {
+      b[k] = fmin(b[k], part[6 * i + k]);
+      b[3 + k] = fmax(b[3 + k], part[6 * i + 3 + k]);
+    }
+  for (int k = 0; k < 6; ++k) box[k] = b[k];
+}
+
+// ---------------------------------------------------------------- Morton keys
+__device__ __forceinline__ uint64_t spread10(uint32_t v) {
+  uint64_t x = v & 0x3ffu;
+  x = (x | (x << 16)) & 0x030000FFull;
+  x = (x | (x << 8)) & 0x0300F00Full;
+  x = (x | (x << 4)) & 0x030C30C3ull;
+  x = (x | (x << 2)) & 0x09249249ull;
+  return x;
+}
+
+// 30-bit Morton key of each point in the bounding box; with group_ptr the key
+// is prefixed by the point's group (suspension) so that groups stay contiguous.
+__global__ void k_morton(int64_t n, const double *__restrict__ pts, const double *__restrict__ box,
+                         const int64_t *__restrict__ group_ptr, int32_t ngroup,
+                         uint64_t *__restrict__ keys, int32_t *__restrict__ vals) {
+  const double lo[3] = {box[0], box[1], box[2]};
+  double ext = fmax(fmax(box[3] - box[0], box[4] - box[1]), box[5] - box[2]);
+  const double inv = ext > 0.0 ? 1024.0 / (ext * (1.0 + 1e-12)) : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+      double v = (pts[3 * i + k] - lo[k]) * inv;
+      v = fmin(fmax(v, 0.0), 1023.0);
+      q[k] = (uint32_t)v;
+    }
+    uint64_t key = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    if (group_ptr) {
+      int32_t a = 0, b = ngroup - 1;
+      while (a < b) {
+        const int32_t m = a + (b - a + 1) / 2;
+        if (group_ptr[m] <= i) a = m;
+        else b = m - 1;
+      }
+      key |= (uint64_t)a << 30;
+    }
+    keys[i] = key;
+    vals[i] = (int32_t)i;
+  }
+}
+
+// ---------------------------------------------------------------- scan
+// Single-block exclusive scan of n int32 values; out has n + 1 entries.
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_excl(const int32_t *__restrict__ in,
+                                                            int64_t n, int32_t *__restrict__ out,
+                                                            int32_t *__restrict__ total) {
+  __shared__ int32_t warp_sums[kScanThreads / kWarp];
+  __shared__ int32_t carry_s;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t base = 0; base < n; base += kScanThreads) {
+    const int64_t i = base + threadIdx.x;
+    const int32_t v = i < n ? in[i] : 0;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int32_t s = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(kFull, s, o);
+        if (lane >= o) s += y;
+      }
+      warp_sums[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    const int32_t carry = carry_s;
+    const int32_t incl = x + (wid > 0 ? warp_sums[wid - 1] : 0);
+    if (i < n) out[i] = carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) carry_s = carry + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[n] = carry_s;
+    if (total) *total = carry_s;
+  }
+}
+
+// ---------------------------------------------------------------- radix sort
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 8;
+constexpr int kSortTile = kSortThreads * kSortRounds;
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t *__restrict__ keys,
+                                                             int64_t n, int shift, int nblk,
+                                                             int32_t *__restrict__ hist) {
+  __shared__ int32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter: keys of equal digit keep their order.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin, int64_t n, int shift,
+    int nblk, const int32_t *__restrict__ offs, uint64_t *__restrict__ kout,
+    int32_t *__restrict__ vout) {
+  __shared__ int32_t running[256];
+  __shared__ int32_t cnt[kSortThreads / kWarp][256];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  running[threadIdx.x] = offs[(int64_t)threadIdx.x * nblk + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < kSortRounds; ++r) {
+    for (int d = lane; d < 256; d += 32) cnt[wid][d] = 0;
+    __syncthreads();
+    const int64_t i = base + r * kSortThreads + threadIdx.x;
+    const bool valid = i < n;
+    uint64_t key = 0;
+    int32_t val = 0;
+    unsigned digit = 256u + lane;  // invalid slots get unique dummy digits
+    if (valid) {
+      key = kin[i];
+      val = vin[i];
+      digit = (unsigned)((key >> shift) & 255u);
+    }
+    const unsigned peers = __match_any_sync(kFull, digit);
+    const int rank = __popc(peers & lt);
+    if (valid && rank == 0) cnt[wid][digit] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      int32_t pos = running[digit] + rank;
+      for (int w2 = 0; w2 < wid; ++w2) pos += cnt[w2][digit];
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    {
+      int32_t s = 0;
+      for (int w2 = 0; w2 < kSortThreads / kWarp; ++w2) s += cnt[w2][threadIdx.x];
+      running[threadIdx.x] += s;
+    }
+    __syncthreads();
+  }
+}
+
+size_t radix_hist_entries(int64_t n) {
+  const int64_t nblk = (n + kSortTile - 1) / kSortTile;
+  return (size_t)(256 * (nblk > 0 ? nblk : 1));
+}
+
+// Sorts (keys, vals) by the low `bits` bits of the keys.  Returns 0 if the
+// result is in (ka, va), 1 if in (kb, vb).
+int radix_sort(uint64_t *ka, int32_t *va, uint64_t *kb, int32_t *vb, int64_t n, int bits,
+               int32_t *hist, int32_t *hist_scan, cudaStream_t st) {
+  if (n <= 1) return 0;
+  const int nblk = (int)((n + kSortTile - 1) / kSortTile);
+  int cur = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    uint64_t *ki = cur ? kb : ka, *ko = cur ? ka : kb;
+    int32_t *vi = cur ? vb : va, *vo = cur ? va : vb;
+    k_radix_hist<<<nblk, kSortThreads, 0, st>>>(ki, n, shift, nblk, hist);
+    k_scan_excl<<<1, kScanThreads, 0, st>>>(hist, (int64_t)256 * nblk, hist_scan, nullptr);
+    k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(ki, vi, n, shift, nblk, hist_scan, ko, vo);
+    cur ^= 1;
+  }
+  return cur;
+}
+
+// ---------------------------------------------------------------- items
+__device__ __forceinline__ uint64_t cost_key(int64_t tn, int64_t nsrc) {
+  // ascending sort of this key gives descending cost
+  uint64_t c = (uint64_t)tn * (uint64_t)nsrc;
+  if (c > 0xffffffffull) c = 0xffffffffull;
+  return 0xffffffffull - c;
+}
+
+__global__ void k_items_direct(int32_t nt, int64_t ns, int32_t nsplit, Item *__restrict__ items,
+                               int64_t *__restrict__ range_ptr, int32_t *__restrict__ n_items) {
+  const int32_t nchunk = (nt + kItemMax - 1) / kItemMax;
+  const int64_t tot = (int64_t)nchunk * nsplit;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = (int32_t)(i / nsplit), s = (int32_t)(i % nsplit);
+    Item it;
+    it.t0 = c * kItemMax;
+    const int32_t tn = min(kItemMax, nt - it.t0);
+    it.tn_part = tn | (s << 8);
+    it.seg0 = s;
+    it.seg1 = s + 1;
+    items[i] = it;
+  }
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g <= nsplit) range_ptr[g] = (ns * g) / nsplit;
+  if (g == 0) *n_items = (int32_t)tot;
+}
+
+__global__ void k_p2p_count(int32_t nleaf, const int32_t *__restrict__ leaf_ptr,
+                            const int32_t *__restrict__ ulist_ptr,
+                            const int32_t *__restrict__ ulist_idx, int32_t *__restrict__ cnt) {
+  for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nleaf; b += gridDim.x * blockDim.x) {
+    const int32_t nb = leaf_ptr[b + 1] - leaf_ptr[b];
+    cnt[b] = (nb + kItemMax - 1) / kItemMax;
+  }
+}
+
+__global__ void k_p2p_emit(int32_t nleaf, const int32_t *__restrict__ leaf_ptr,
+                           const int32_t *__restrict__ ulist_ptr,
+                           const int32_t *__restrict__ ulist_idx,
+                           const int32_t *__restrict__ offs, Item *__restrict__ items,
+                           uint64_t *__restrict__ keys, int32_t *__restrict__ vals) {
+  for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nleaf; b += gridDim.x * blockDim.x) {
+    const int32_t nb = leaf_ptr[b + 1] - leaf_ptr[b];
+    if (nb <= 0) continue;
+    int64_t nsrc = 0;
+    for (int32_t e = ulist_ptr[b]; e < ulist_ptr[b + 1]; ++e) {
+      const int32_t a = ulist_idx[e];
+      nsrc += leaf_ptr[a + 1] - leaf_ptr[a];
+    }
+    const int32_t nc = (nb + kItemMax - 1) / kItemMax;
+    const int32_t base = nb / nc, extra = nb % nc;
+    int32_t t0 = leaf_ptr[b];
+    for (int32_t c = 0; c < nc; ++c) {
+      const int32_t tn = base + (c < extra ? 1 : 0);
+      const int32_t id = offs[b] + c;
+      Item it;
+      it.t0 = t0;
+      it.tn_part = tn;
+      it.seg0 = ulist_ptr[b];
+      it.seg1 = ulist_ptr[b + 1];
+      items[id] = it;
+      keys[id] = cost_key(tn, nsrc);
+      vals[id] = id;
+      t0 += tn;
+    }
+  }
+}
+
+__global__ void k_batched_count(int32_t nsusp, const int64_t *__restrict__ susp_ptr,
+                                int32_t *__restrict__ cnt) {
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nsusp; s += gridDim.x * blockDim.x) {
+    const int64_t ns = susp_ptr[s + 1] - susp_ptr[s];
+    cnt[s] = (int32_t)((ns + kItemMax - 1) / kItemMax);
+  }
+}
+
+__global__ void k_batched_emit(int32_t nsusp, const int64_t *__restrict__ susp_ptr,
+                               const int64_t *__restrict__ n_cell, const int32_t *__restrict__ offs,
+                               Item *__restrict__ items, int64_t *__restrict__ range_ptr,
+                               uint64_t *__restrict__ keys, int32_t *__restrict__ vals) {
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nsusp; s += gridDim.x * blockDim.x) {
+    const int64_t p0 = susp_ptr[s], p1 = susp_ptr[s + 1];
+    range_ptr[2 * s] = p0;
+    range_ptr[2 * s + 1] = p0 + n_cell[s];
+    if (s == nsusp - 1) range_ptr[2 * nsusp] = p1;
+    const int64_t nb = p1 - p0;
+    if (nb <= 0) continue;
+    const int32_t nc = (int32_t)((nb + kItemMax - 1) / kItemMax);
+    const int64_t base = nb / nc, extra = nb % nc;
+    int64_t t0 = p0;
+    for (int32_t c = 0; c < nc; ++c) {
+      const int32_t tn = (int32_t)(base + (c < extra ? 1 : 0));
+      const int32_t id = offs[s] + c;
+      Item it;
+      it.t0 = (int32_t)t0;
+      it.tn_part = tn;
+      it.seg0 = 2 * s;
+      it.seg1 = 2 * s + 2;
+      items[id] = it;
+      keys[id] = cost_key(tn, nb);
+      vals[id] = id;
+      t0 += tn;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- finish
+// out[perm[i]] (+)= sum over parts of part_out[p][i], parts added in order.
+__global__ void k_finish(int64_t nt, int32_t nparts, const double *__restrict__ part_out,
+                         const int32_t *__restrict__ tperm, int32_t accumulate,
+                         double *__restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int32_t p = 0; p < nparts; ++p)
+      for (int k = 0; k < 3; ++k) v[k] += part_out[((size_t)p * nt + i) * 3 + k];
+    const int64_t ci = tperm ? tperm[i] : i;
+    for (int k = 0; k < 3; ++k) {
+      double *o = out + 3 * ci + k;
+      *o = accumulate ? *o + v[k] : v[k];
+    }
+  }
+}
+
+__global__ void k_zero_ints(int32_t *p, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = 0;
+}
+
+// ---------------------------------------------------------------- launchers
+static int grid_for(int64_t n, int threads, int cap = 4096) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+void launch_pack_mixed(int64_t ns, const double *src, const double *f, const double *nrm,
+                       const double *phi, const double *w, const double *h, double alpha,
+                       double csl, double cdl, SrcRec *rec, cudaStream_t st) {
+  k_pack_mixed<<<grid_for(ns, 256), 256, 0, st>>>(ns, src, f, nrm, phi, w, h, alpha, csl, cdl, rec);
+}
+
+void launch_pack_fp64(int64_t ns, const double *src, const double *f, const double *nrm,
+                      const double *phi, const double *w, double csl, double cdl, SrcRec64 *rec,
+                      cudaStream_t st) {
+  k_pack_fp64<<<grid_for(ns, 256), 256, 0, st>>>(ns, src, f, nrm, phi, w, csl, cdl, rec);
+}
+
+int bbox_partial_blocks(int64_t n) { return grid_for(n, kRedThreads, 1024); }
+
+void launch_bbox(int64_t n, const double *pts, double *partial, double *box, cudaStream_t st) {
+  const int nb = bbox_partial_blocks(n);
+  k_bbox_partial<<<nb, kRedThreads, 0, st>>>(n, pts, partial);
+  k_bbox_final<<<1, 32, 0, st>>>(nb, partial, box);
+}
+
+void launch_morton(int64_t n, const double *pts, const double *box, const int64_t *group_ptr,
+                   int32_t ngroup, uint64_t *keys, int32_t *vals, cudaStream_t st) {
+  k_morton<<<grid_for(n, 256), 256, 0, st>>>(n, pts, box, group_ptr, ngroup, keys, vals);
+}
+
+void launch_scan(const int32_t *in, int64_t n, int32_t *out, int32_t *total, cudaStream_t st) {
+  k_scan_excl<<<1, kScanThreads, 0, st>>>(in, n, out, total);
+}
+
+void launch_items_direct(int32_t nt, int64_t ns, int32_t nsplit, Item *items, int64_t *range_ptr,
+                         int32_t *n_items, cudaStream_t st) {
+  const int64_t tot = (int64_t)((nt + kItemMax - 1) / kItemMax) * nsplit;
+  const int64_t need = tot > nsplit + 1 ? tot : nsplit + 1;
+  k_items_direct<<<grid_for(need, 256), 256, 0, st>>>(nt, ns, nsplit, items, range_ptr, n_items);
+}
+
+void launch_p2p_items(int32_t nleaf, const int32_t *leaf_ptr, const int32_t *ulist_ptr,
+                      const int32_t *ulist_idx, int32_t *cnt, int32_t *offs, int32_t *n_items,
+                      Item *items, uint64_t *keys, int32_t *vals, cudaStream_t st) {
+  k_p2p_count<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, leaf_ptr, ulist_ptr, ulist_idx, cnt);
+  k_scan_excl<<<1, kScanThreads, 0, st>>>(cnt, nleaf, offs, n_items);
+  k_p2p_emit<<<grid_for(nleaf, 128), 128, 0, st>>>(nleaf, leaf_ptr, ulist_ptr, ulist_idx, offs,
+                                                   items, keys, vals);
+}
+
+void launch_batched_items(int32_t nsusp, const int64_t *susp_ptr, const int64_t *n_cell,
+                          int32_t *cnt, int32_t *offs, int32_t *n_items, Item *items,
+                          int64_t *range_ptr, uint64_t *keys, int32_t *vals, cudaStream_t st) {
+  k_batched_count<<<grid_for(nsusp, 256), 256, 0, st>>>(nsusp, susp_ptr, cnt);
+  k_scan_excl<<<1, kScanThreads, 0, st>>>(cnt, nsusp, offs, n_items);
+  k_batched_emit<<<grid_for(nsusp, 128), 128, 0, st>>>(nsusp, susp_ptr, n_cell, offs, items,
+                                                       range_ptr, keys, vals);
+}
+
+void launch_finish(int64_t nt, int32_t nparts, const double *part_out, const int32_t *tperm,
+                   int32_t accumulate, double *out, cudaStream_t st) {
+  k_finish<<<grid_for(nt, 256), 256, 0, st>>>(nt, nparts, part_out, tperm, accumulate, out);
+}
+
+void launch_zero_ints(int32_t *p, int n, cudaStream_t st) {
+  k_zero_ints<<<(n + 127) / 128, 128, 0, st>>>(p, n);
+}
+
+}  // namespace stk
+
+namespace stk {
+__global__ void k_widen(int64_t n, const int32_t *__restrict__ in, int64_t *__restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+void launch_widen(int64_t n, const int32_t *in, int64_t *out, cudaStream_t st) {
+  k_widen<<<grid_for(n, 256), 256, 0, st>>>(n, in, out);
+}
+}  // namespace stk

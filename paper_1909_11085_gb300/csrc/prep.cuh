@@ -1,0 +1,41 @@
+// prep.cuh -- host-side launchers for the staging kernels and the engines.
+#pragma once
+
+#include "common.cuh"
+
+namespace stk {
+
+void launch_pack_mixed(int64_t ns, const double *src, const double *f, const double *nrm,
+                       const double *phi, const double *w, const double *h, double alpha,
+                       double csl, double cdl, SrcRec *rec, cudaStream_t st);
+void launch_pack_fp64(int64_t ns, const double *src, const double *f, const double *nrm,
+                      const double *phi, const double *w, double csl, double cdl, SrcRec64 *rec,
+                      cudaStream_t st);
+int bbox_partial_blocks(int64_t n);
+void launch_bbox(int64_t n, const double *pts, double *partial, double *box, cudaStream_t st);
+void launch_morton(int64_t n, const double *pts, const double *box, const int64_t *group_ptr,
+                   int32_t ngroup, uint64_t *keys, int32_t *vals, cudaStream_t st);
+void launch_scan(const int32_t *in, int64_t n, int32_t *out, int32_t *total, cudaStream_t st);
+size_t radix_hist_entries(int64_t n);
+int radix_sort(uint64_t *ka, int32_t *va, uint64_t *kb, int32_t *vb, int64_t n, int bits,
+               int32_t *hist, int32_t *hist_scan, cudaStream_t st);
+void launch_items_direct(int32_t nt, int64_t ns, int32_t nsplit, Item *items, int64_t *range_ptr,
+                         int32_t *n_items, cudaStream_t st);
+void launch_p2p_items(int32_t nleaf, const int32_t *leaf_ptr, const int32_t *ulist_ptr,
+                      const int32_t *ulist_idx, int32_t *cnt, int32_t *offs, int32_t *n_items,
+                      Item *items, uint64_t *keys, int32_t *vals, cudaStream_t st);
+void launch_batched_items(int32_t nsusp, const int64_t *susp_ptr, const int64_t *n_cell,
+                          int32_t *cnt, int32_t *offs, int32_t *n_items, Item *items,
+                          int64_t *range_ptr, uint64_t *keys, int32_t *vals, cudaStream_t st);
+void launch_finish(int64_t nt, int32_t nparts, const double *part_out, const int32_t *tperm,
+                   int32_t accumulate, double *out, cudaStream_t st);
+void launch_zero_ints(int32_t *p, int n, cudaStream_t st);
+void launch_widen(int64_t n, const int32_t *in, int64_t *out, cudaStream_t st);
+
+size_t engine_mixed_smem_bytes();
+cudaError_t launch_engine_mixed(const EngineParams &P, int grid, cudaStream_t stream);
+cudaError_t engine_mixed_occupancy(int *blocks_per_sm);
+cudaError_t launch_engine_fp64(const EngineParams &P, int grid, cudaStream_t stream);
+cudaError_t engine_fp64_occupancy(int *blocks_per_sm);
+
+}  // namespace stk

@@ -1,0 +1,534 @@
+// stokes_abi.cu -- the C ABI declared in include/stokesgpu.h: argument
+// validation, workspace planning and the launch sequence of every form.
+//
+// Launch sequence (all on the caller's stream, nothing allocated):
+//   1. zero the workspace counters (item queue head, item count, error word);
+//   2. pack the sources (mixed 80-byte or FP64 96-byte records);
+//   3. MIXED direct/batched: bounding box + Morton keys + stable radix sort of
+//      the targets, so that every 128-target work item is spatially compact;
+//   4. build work items (direct: target chunks x source splits; near field:
+//      leaf chunks x U-list; batched: suspension chunks x {cells, wall}) and,
+//      where items are uneven, radix-sort them by descending cost;
+//   5. one persistent engine launch (SMs x resident CTAs, 4 warps each);
+//   6. reduce the source splits in fixed order and scatter to caller order.
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/stokesgpu.h"
+#include "common.cuh"
+#include "prep.cuh"
+
+using namespace stk;
+
+namespace {
+
+thread_local std::string g_err;
+
+stk_status fail(stk_status s, const char *msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CU(x)                                                                        \
+  do {                                                                               \
+    cudaError_t e_ = (x);                                                            \
+    if (e_ != cudaSuccess) {                                                         \
+      g_err = std::string(#x) + ": " + cudaGetErrorString(e_);                       \
+      return STK_ECUDA;                                                              \
+    }                                                                                \
+  } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int64_t kMaxN = 0x7fffffffLL;
+constexpr int64_t kSpinLimit = 4000000000LL;  // SM cycles, about 2 s at 2 GHz
+
+struct DevInfo {
+  int dev = -1;
+  int sms = 0;
+  int occ_mixed = 0;
+  int occ_fp64 = 0;
+};
+
+cudaError_t dev_info(DevInfo &di) {
+  static thread_local DevInfo cache[16];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  DevInfo &c = cache[dev];
+  if (c.dev != dev) {
+    DevInfo n;
+    n.dev = dev;
+    e = cudaDeviceGetAttribute(&n.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = engine_mixed_occupancy(&n.occ_mixed);
+    if (e != cudaSuccess) return e;
+    e = engine_fp64_occupancy(&n.occ_fp64);
+    if (e != cudaSuccess) return e;
+    if (n.occ_mixed < 1) n.occ_mixed = 1;
+    if (n.occ_fp64 < 1) n.occ_fp64 = 1;
+    c = n;
+  }
+  di = c;
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------ workspace plan
+struct Alloc {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  }
+};
+
+enum Form { F_DIRECT, F_P2P, F_BATCHED };
+
+struct Plan {
+  Form form;
+  bool mixed;
+  int64_t ns, nt;
+  int32_t nsplit = 1;
+  int64_t max_items = 0;
+  int32_t nseg_ranges = 0;  // entries of range_ptr minus one
+  bool sort_targets = false;
+  bool sort_items = false;
+  int32_t ngroup = 0;
+  // offsets (the counters always sit at offset 0 of the aligned workspace)
+  size_t counters, rec, keys_a, keys_b, vals_a, vals_b, ikeys_a, ikeys_b, ivals_a, ivals_b, hist,
+      hist_scan, bbox_part, bbox, items, range, cnt, offs, part, total;
+};
+
+int auto_splits(int64_t nt, int64_t ns, const DevInfo &di, int occ) {
+  const int64_t chunks = (nt + kItemMax - 1) / kItemMax;
+  if (chunks <= 0) return 1;
+  const int64_t warps = (int64_t)di.sms * occ * kWarpsPerCta;
+  int64_t s = (2 * warps + chunks - 1) / chunks;
+  const int64_t cap = ns / 512 > 1 ? ns / 512 : 1;
+  if (s > cap) s = cap;
+  if (s > 64) s = 64;
+  if (s < 1) s = 1;
+  return (int)s;
+}
+
+void layout(Plan &p) {
+  Alloc a;
+  p.counters = a.take(sizeof(int32_t) * 4);
+  p.rec = a.take((size_t)p.ns * (p.mixed ? sizeof(SrcRec) : sizeof(SrcRec64)));
+  const int64_t nsort = p.sort_targets ? p.nt : 0;
+  const int64_t nitem = p.sort_items ? p.max_items : 0;
+  p.keys_a = a.take(sizeof(uint64_t) * (size_t)nsort);
+  p.keys_b = a.take(sizeof(uint64_t) * (size_t)nsort);
+  p.vals_a = a.take(sizeof(int32_t) * (size_t)nsort);
+  p.vals_b = a.take(sizeof(int32_t) * (size_t)nsort);
+  p.ikeys_a = a.take(sizeof(uint64_t) * (size_t)nitem);
+  p.ikeys_b = a.take(sizeof(uint64_t) * (size_t)nitem);
+  p.ivals_a = a.take(sizeof(int32_t) * (size_t)nitem);
+  p.ivals_b = a.take(sizeof(int32_t) * (size_t)nitem);
+  const size_t he = radix_hist_entries(nsort > nitem ? nsort : nitem);
+  p.hist = a.take(sizeof(int32_t) * he);
+  p.hist_scan = a.take(sizeof(int32_t) * (he + 1));
+  p.bbox_part = a.take(sizeof(double) * 6 * 1024);
+  p.bbox = a.take(sizeof(double) * 6);
+  p.items = a.take(sizeof(Item) * (size_t)(p.max_items > 0 ? p.max_items : 1));
+  p.range = a.take(sizeof(int64_t) * (size_t)(p.nseg_ranges + 1));
+  p.cnt = a.take(sizeof(int32_t) * (size_t)(p.ngroup + 1));
+  p.offs = a.take(sizeof(int32_t) * (size_t)(p.ngroup + 2));
+  p.part = a.take(sizeof(double) * 3 * (size_t)p.nt * (size_t)p.nsplit);
+  p.total = a.off + 256;  // slack for re-alignment of an unaligned base
+}
+
+stk_status plan_direct(int64_t ns, int64_t nt, const stk_opts *o, Plan &p) {
+  DevInfo di;
+  CU(dev_info(di));
+  p.form = F_DIRECT;
+  p.mixed = o->precision == STK_MIXED;
+  p.ns = ns;
+  p.nt = nt;
+  const int occ = p.mixed ? di.occ_mixed : di.occ_fp64;
+  p.nsplit = o->source_splits > 0 ? o->source_splits : auto_splits(nt, ns, di, occ);
+  if (p.nsplit > ns && ns > 0) p.nsplit = (int32_t)ns;
+  if (p.nsplit < 1) p.nsplit = 1;
+  p.max_items = ((nt + kItemMax - 1) / kItemMax) * p.nsplit;
+  p.nseg_ranges = p.nsplit;
+  p.sort_targets = p.mixed;
+  p.sort_items = false;
+  p.ngroup = 0;
+  layout(p);
+  return STK_OK;
+}
+
+stk_status plan_p2p(int64_t n, int32_t nleaf, const stk_opts *o, Plan &p) {
+  p.form = F_P2P;
+  p.mixed = o->precision == STK_MIXED;
+  p.ns = p.nt = n;
+  p.nsplit = 1;
+  p.max_items = (int64_t)nleaf + n / kItemMax + 1;
+  p.nseg_ranges = nleaf;
+  p.sort_targets = false;
+  p.sort_items = true;
+  p.ngroup = nleaf;
+  layout(p);
+  return STK_OK;
+}
+
+stk_status plan_batched(int64_t n, int32_t nsusp, const stk_opts *o, Plan &p) {
+  p.form = F_BATCHED;
+  p.mixed = o->precision == STK_MIXED;
+  p.ns = p.nt = n;
+  p.nsplit = 1;
+  p.max_items = (int64_t)nsusp + n / kItemMax + 1;
+  p.nseg_ranges = 2 * nsusp;
+  p.sort_targets = p.mixed;
+  p.sort_items = true;
+  p.ngroup = nsusp;
+  layout(p);
+  return STK_OK;
+}
+
+stk_status check_opts(const stk_opts *o) {
+  if (!o) return fail(STK_EINVAL, "opts is NULL");
+  if (o->precision != STK_FP64 && o->precision != STK_MIXED)
+    return fail(STK_EINVAL, "opts->precision must be STK_FP64 or STK_MIXED");
+  if (!(o->near_ratio >= 0.0) || !std::isfinite(o->near_ratio))
+    return fail(STK_EINVAL, "opts->near_ratio must be finite and >= 0");
+  if (o->source_splits < 0 || o->source_splits > 1024)
+    return fail(STK_EINVAL, "opts->source_splits must be in [0, 1024]");
+  return STK_OK;
+}
+
+template <class T>
+T *at(void *ws, size_t off) {
+  return reinterpret_cast<T *>(reinterpret_cast<char *>(ws) + off);
+}
+
+void *align_ws(void *ws) {
+  const uintptr_t u = reinterpret_cast<uintptr_t>(ws);
+  return reinterpret_cast<void *>((u + 255) & ~(uintptr_t)255);
+}
+
+// Engine launch common to all forms.
+stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st) {
+  DevInfo di;
+  CU(dev_info(di));
+  int32_t *counters = at<int32_t>(ws, p.counters);
+  P.n_items = counters + 0;
+  P.item_counter = counters + 1;
+  P.err_flag = counters + 2;
+  P.spin_limit = kSpinLimit;
+  P.part_out = at<double>(ws, p.part);
+  P.nt = (int32_t)p.nt;
+  const int occ = p.mixed ? di.occ_mixed : di.occ_fp64;
+  int64_t grid = (int64_t)di.sms * occ;
+  const int64_t need = (p.max_items + kWarpsPerCta - 1) / kWarpsPerCta;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  if (p.mixed) {
+    P.rec = at<SrcRec>(ws, p.rec);
+    CU(launch_engine_mixed(P, (int)grid, st));
+  } else {
+    P.rec64 = at<SrcRec64>(ws, p.rec);
+    CU(launch_engine_fp64(P, (int)grid, st));
+  }
+  return STK_OK;
+}
+
+stk_status pack(const Plan &p, void *ws, const double *src, const double *f, const double *nrm,
+                const double *phi, const double *w, const double *h, double mu, double alpha,
+                cudaStream_t st) {
+  const double csl = 1.0 / (8.0 * kPi * mu), cdl = 6.0 / (8.0 * kPi);
+  if (p.mixed)
+    launch_pack_mixed(p.ns, src, f, nrm, phi, w, h, alpha, csl, cdl, at<SrcRec>(ws, p.rec), st);
+  else
+    launch_pack_fp64(p.ns, src, f, nrm, phi, w, csl, cdl, at<SrcRec64>(ws, p.rec), st);
+  CU(cudaGetLastError());
+  return STK_OK;
+}
+
+// Morton sort of the targets; returns the sorted -> caller permutation.
+const int32_t *sort_targets(const Plan &p, void *ws, const double *trg, const int64_t *group_ptr,
+                            int32_t ngroup, cudaStream_t st) {
+  launch_bbox(p.nt, trg, at<double>(ws, p.bbox_part), at<double>(ws, p.bbox), st);
+  uint64_t *ka = at<uint64_t>(ws, p.keys_a), *kb = at<uint64_t>(ws, p.keys_b);
+  int32_t *va = at<int32_t>(ws, p.vals_a), *vb = at<int32_t>(ws, p.vals_b);
+  launch_morton(p.nt, trg, at<double>(ws, p.bbox), group_ptr, ngroup, ka, va, st);
+  int bits = 30;
+  if (group_ptr) {
+    int gb = 0;
+    while ((1LL << gb) < ngroup) ++gb;
+    bits += gb;
+  }
+  const int which = radix_sort(ka, va, kb, vb, p.nt, bits, at<int32_t>(ws, p.hist),
+                               at<int32_t>(ws, p.hist_scan), st);
+  return which ? vb : va;
+}
+
+// Builds items with cost keys through `emit` and returns the processing order
+// (descending cost).  The item count is only known on the device, so the sort
+// runs over the upper bound; unused key slots hold the maximum key and sort last.
+template <class Emit>
+const int32_t *build_sorted_items(const Plan &p, void *ws, cudaStream_t st, Emit emit) {
+  uint64_t *ka = at<uint64_t>(ws, p.ikeys_a), *kb = at<uint64_t>(ws, p.ikeys_b);
+  int32_t *va = at<int32_t>(ws, p.ivals_a), *vb = at<int32_t>(ws, p.ivals_b);
+  cudaMemsetAsync(ka, 0xff, sizeof(uint64_t) * (size_t)p.max_items, st);
+  cudaMemsetAsync(va, 0xff, sizeof(int32_t) * (size_t)p.max_items, st);
+  emit(ka, va);
+  const int which = radix_sort(ka, va, kb, vb, p.max_items, 32, at<int32_t>(ws, p.hist),
+                               at<int32_t>(ws, p.hist_scan), st);
+  return which ? vb : va;
+}
+
+stk_status direct_common(int32_t kinds, const double *src, const double *f, const double *nrm,
+                         const double *phi, const double *w, const double *h, int64_t ns,
+                         const double *trg, int64_t nt, double mu, double *out, const stk_opts *o,
+                         void *workspace, size_t wbytes, void *stream) {
+  stk_status s = check_opts(o);
+  if (s != STK_OK) return s;
+  if (ns < 0 || nt < 0 || ns > kMaxN || nt > kMaxN)
+    return fail(STK_EINVAL, "ns and nt must be in [0, 2^31-1]");
+  if (nt > 0 && (!trg || !out)) return fail(STK_EINVAL, "trg/out is NULL");
+  if (ns > 0 && nt > 0) {
+    if (!src || !w) return fail(STK_EINVAL, "src/w is NULL");
+    if ((kinds & K_SL) && !f) return fail(STK_EINVAL, "f is NULL");
+    if ((kinds & K_DL) && (!nrm || !phi)) return fail(STK_EINVAL, "nrm/phi is NULL");
+    if ((kinds & K_SL) && !(mu > 0.0 && std::isfinite(mu)))
+      return fail(STK_EINVAL, "mu must be finite and > 0");
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (nt == 0) return STK_OK;
+  if (ns == 0) {
+    if (!o->accumulate) CU(cudaMemsetAsync(out, 0, sizeof(double) * 3 * (size_t)nt, st));
+    return STK_OK;
+  }
+  Plan p;
+  s = plan_direct(ns, nt, o, p);
+  if (s != STK_OK) return s;
+  if (!workspace || wbytes < p.total) return fail(STK_ENOMEM, "workspace too small");
+  void *ws = align_ws(workspace);
+  launch_zero_ints(at<int32_t>(ws, p.counters), 4, st);
+  s = pack(p, ws, src, (kinds & K_SL) ? f : nullptr, nrm, (kinds & K_DL) ? phi : nullptr, w, h,
+           (kinds & K_SL) ? mu : 1.0, o->near_ratio, st);
+  if (s != STK_OK) return s;
+  EngineParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.src64 = src;
+  P.trg64 = trg;
+  P.tperm = p.sort_targets ? sort_targets(p, ws, trg, nullptr, 0, st) : nullptr;
+  launch_items_direct((int32_t)nt, ns, p.nsplit, at<Item>(ws, p.items),
+                      at<int64_t>(ws, p.range), at<int32_t>(ws, p.counters), st);
+  CU(cudaGetLastError());
+  P.items = at<Item>(ws, p.items);
+  P.item_order = nullptr;
+  P.seg_list = nullptr;
+  P.range_ptr = at<int64_t>(ws, p.range);
+  P.kind = kinds;
+  P.kind_alternating = 0;
+  s = run_engine(p, ws, P, st);
+  if (s != STK_OK) return s;
+  launch_finish(nt, p.nsplit, at<double>(ws, p.part), P.tperm, o->accumulate, out, st);
+  CU(cudaGetLastError());
+  return STK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void stokes_default_opts(stk_opts *o) {
+  if (!o) return;
+  o->precision = STK_MIXED;
+  o->near_ratio = 2.0;
+  o->accumulate = 0;
+  o->source_splits = 0;
+  o->tile_config = -1;
+}
+
+const char *stokes_last_error(void) { return g_err.c_str(); }
+
+const char *stokes_version(void) { return "stokesgpu 0.1 (sm_103a)"; }
+
+stk_status stokes_direct_workspace_size(int64_t ns, int64_t nt, int32_t kernels,
+                                        const stk_opts *opts, size_t *bytes) {
+  stk_status s = check_opts(opts);
+  if (s != STK_OK) return s;
+  if (!bytes) return fail(STK_EINVAL, "bytes is NULL");
+  if (ns < 0 || nt < 0 || ns > kMaxN || nt > kMaxN) return fail(STK_EINVAL, "bad sizes");
+  if (kernels < 1 || kernels > 3) return fail(STK_EINVAL, "kernels must be 1, 2 or 3");
+  Plan p;
+  s = plan_direct(ns, nt, opts, p);
+  if (s != STK_OK) return s;
+  *bytes = p.total;
+  return STK_OK;
+}
+
+stk_status stokes_sl_eval(const double *src, const double *f, const double *w, const double *h,
+                          int64_t ns, const double *trg, int64_t nt, double mu, double *out,
+                          const stk_opts *opts, void *workspace, size_t workspace_bytes,
+                          void *stream) {
+  return direct_common(K_SL, src, f, nullptr, nullptr, w, h, ns, trg, nt, mu, out, opts, workspace,
+                       workspace_bytes, stream);
+}
+
+stk_status stokes_dl_eval(const double *src, const double *nrm, const double *phi,
+                          const double *w, const double *h, int64_t ns, const double *trg,
+                          int64_t nt, double *out, const stk_opts *opts, void *workspace,
+                          size_t workspace_bytes, void *stream) {
+  return direct_common(K_DL, src, nullptr, nrm, phi, w, h, ns, trg, nt, 1.0, out, opts, workspace,
+                       workspace_bytes, stream);
+}
+
+stk_status stokes_sldl_eval(const double *src, const double *f, const double *nrm,
+                            const double *phi, const double *w, const double *h, int64_t ns,
+                            const double *trg, int64_t nt, double mu, double *out,
+                            const stk_opts *opts, void *workspace, size_t workspace_bytes,
+                            void *stream) {
+  return direct_common(K_SLDL, src, f, nrm, phi, w, h, ns, trg, nt, mu, out, opts, workspace,
+                       workspace_bytes, stream);
+}
+
+stk_status stokes_p2p_workspace_size(int64_t n, int32_t nleaf, int32_t kernels,
+                                     const stk_opts *opts, size_t *bytes) {
+  stk_status s = check_opts(opts);
+  if (s != STK_OK) return s;
+  if (!bytes) return fail(STK_EINVAL, "bytes is NULL");
+  if (n < 0 || n > kMaxN || nleaf < 0) return fail(STK_EINVAL, "bad sizes");
+  if (kernels < 1 || kernels > 3) return fail(STK_EINVAL, "kernels must be 1, 2 or 3");
+  Plan p;
+  s = plan_p2p(n, nleaf, opts, p);
+  if (s != STK_OK) return s;
+  *bytes = p.total;
+  return STK_OK;
+}
+
+stk_status stokes_p2p_leaflists(const double *pts, const double *f, const double *phi,
+                                const double *nrm, const double *w, const double *h, int64_t n,
+                                const int32_t *leaf_ptr, int32_t nleaf, const int32_t *ulist_ptr,
+                                const int32_t *ulist_idx, int64_t nulist, int32_t kernels,
+                                double mu, double *out, const stk_opts *opts, void *workspace,
+                                size_t workspace_bytes, void *stream) {
+  stk_status s = check_opts(opts);
+  if (s != STK_OK) return s;
+  if (n < 0 || n > kMaxN || nleaf < 0 || nulist < 0 || nulist > kMaxN)
+    return fail(STK_EINVAL, "bad sizes");
+  if (kernels < 1 || kernels > 3) return fail(STK_EINVAL, "kernels must be 1, 2 or 3");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) return STK_OK;
+  if (nleaf == 0) return fail(STK_EINVAL, "points without leaves");
+  if (!pts || !w || !out || !leaf_ptr || !ulist_ptr || (nulist > 0 && !ulist_idx))
+    return fail(STK_EINVAL, "NULL pointer");
+  if ((kernels & K_SL) && !f) return fail(STK_EINVAL, "f is NULL");
+  if ((kernels & K_DL) && (!nrm || !phi)) return fail(STK_EINVAL, "nrm/phi is NULL");
+  if ((kernels & K_SL) && !(mu > 0.0 && std::isfinite(mu)))
+    return fail(STK_EINVAL, "mu must be finite and > 0");
+  Plan p;
+  s = plan_p2p(n, nleaf, opts, p);
+  if (s != STK_OK) return s;
+  if (!workspace || workspace_bytes < p.total) return fail(STK_ENOMEM, "workspace too small");
+  void *ws = align_ws(workspace);
+  launch_zero_ints(at<int32_t>(ws, p.counters), 4, st);
+  s = pack(p, ws, pts, (kernels & K_SL) ? f : nullptr, nrm, (kernels & K_DL) ? phi : nullptr, w,
+           h, (kernels & K_SL) ? mu : 1.0, opts->near_ratio, st);
+  if (s != STK_OK) return s;
+  int64_t *range = at<int64_t>(ws, p.range);
+  launch_widen((int64_t)nleaf + 1, leaf_ptr, range, st);
+  int32_t *counters = at<int32_t>(ws, p.counters);
+  const int32_t *order = build_sorted_items(p, ws, st, [&](uint64_t *keys, int32_t *vals) {
+    launch_p2p_items(nleaf, leaf_ptr, ulist_ptr, ulist_idx, at<int32_t>(ws, p.cnt),
+                     at<int32_t>(ws, p.offs), counters, at<Item>(ws, p.items), keys, vals, st);
+  });
+  CU(cudaGetLastError());
+  EngineParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.src64 = pts;
+  P.trg64 = pts;
+  P.tperm = nullptr;
+  P.items = at<Item>(ws, p.items);
+  P.item_order = order;
+  P.seg_list = ulist_idx;
+  P.range_ptr = range;
+  P.kind = kernels;
+  P.kind_alternating = 0;
+  s = run_engine(p, ws, P, st);
+  if (s != STK_OK) return s;
+  launch_finish(n, 1, at<double>(ws, p.part), nullptr, opts->accumulate, out, st);
+  CU(cudaGetLastError());
+  return STK_OK;
+}
+
+stk_status stokes_batched_workspace_size(int64_t n, int32_t nsusp, const stk_opts *opts,
+                                         size_t *bytes) {
+  stk_status s = check_opts(opts);
+  if (s != STK_OK) return s;
+  if (!bytes) return fail(STK_EINVAL, "bytes is NULL");
+  if (n < 0 || n > kMaxN || nsusp < 0 || nsusp > (1 << 24)) return fail(STK_EINVAL, "bad sizes");
+  Plan p;
+  s = plan_batched(n, nsusp, opts, p);
+  if (s != STK_OK) return s;
+  *bytes = p.total;
+  return STK_OK;
+}
+
+stk_status stokes_batched_eval(const double *pts, const double *f, const double *phi,
+                               const double *nrm, const double *w, const double *h, int64_t n,
+                               const int64_t *susp_ptr, const int64_t *n_cell, int32_t nsusp,
+                               double mu, double *out, const stk_opts *opts, void *workspace,
+                               size_t workspace_bytes, void *stream) {
+  stk_status s = check_opts(opts);
+  if (s != STK_OK) return s;
+  if (n < 0 || n > kMaxN || nsusp < 0 || nsusp > (1 << 24)) return fail(STK_EINVAL, "bad sizes");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0 || nsusp == 0) return STK_OK;
+  if (!pts || !f || !phi || !nrm || !w || !out || !susp_ptr || !n_cell)
+    return fail(STK_EINVAL, "NULL pointer");
+  if (!(mu > 0.0 && std::isfinite(mu))) return fail(STK_EINVAL, "mu must be finite and > 0");
+  Plan p;
+  s = plan_batched(n, nsusp, opts, p);
+  if (s != STK_OK) return s;
+  if (!workspace || workspace_bytes < p.total) return fail(STK_ENOMEM, "workspace too small");
+  void *ws = align_ws(workspace);
+  launch_zero_ints(at<int32_t>(ws, p.counters), 4, st);
+  s = pack(p, ws, pts, f, nrm, phi, w, h, mu, opts->near_ratio, st);
+  if (s != STK_OK) return s;
+  EngineParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.src64 = pts;
+  P.trg64 = pts;
+  P.tperm = p.sort_targets ? sort_targets(p, ws, pts, susp_ptr, nsusp, st) : nullptr;
+  int32_t *counters = at<int32_t>(ws, p.counters);
+  const int32_t *order = build_sorted_items(p, ws, st, [&](uint64_t *keys, int32_t *vals) {
+    launch_batched_items(nsusp, susp_ptr, n_cell, at<int32_t>(ws, p.cnt), at<int32_t>(ws, p.offs),
+                         counters, at<Item>(ws, p.items), at<int64_t>(ws, p.range), keys, vals,
+                         st);
+  });
+  CU(cudaGetLastError());
+  P.items = at<Item>(ws, p.items);
+  P.item_order = order;
+  P.seg_list = nullptr;
+  P.range_ptr = at<int64_t>(ws, p.range);
+  P.kind = K_SLDL;
+  P.kind_alternating = 1;
+  s = run_engine(p, ws, P, st);
+  if (s != STK_OK) return s;
+  launch_finish(n, 1, at<double>(ws, p.part), P.tperm, opts->accumulate, out, st);
+  CU(cudaGetLastError());
+  return STK_OK;
+}
+
+stk_status stokes_device_status(void *workspace, size_t workspace_bytes) {
+  if (!workspace || workspace_bytes < 512) return fail(STK_EINVAL, "workspace is NULL or too small");
+  int32_t *counters = at<int32_t>(align_ws(workspace), 0);
+  int32_t err = 0;
+  CU(cudaMemcpy(&err, counters + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (err != 0) {
+    const int32_t zero = 0;
+    CU(cudaMemcpy(counters + 2, &zero, sizeof(int32_t), cudaMemcpyHostToDevice));
+    return fail(STK_ETIMEOUT, "a bounded device wait ran out; results of that call are incomplete");
+  }
+  return STK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+"""PyTorch-facing calls of the Stokes layer-potential library.
+
+Each function marshals tensors into one C-ABI call (include/stokesgpu.h) on
+the current CUDA stream and returns the velocity [n_targets, 3] (float64).
+PyTorch provides only device memory and the stream.
+
+  sl    single layer, Eq. "sl_stokes"             u = S[f]
+  dl    double layer, kernel of Sec. 2.1          u = D[phi]
+  sldl  superposition, Eq. "velocity_combined"    u = S[f] + D[phi]
+  p2p   FMM near field over U-lists (Sec. 3.1 "Far evaluation")
+  batched  independent suspensions: S over cell points + D over wall points
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _abi as A
+
+
+def _direct(kind, src, f, nrm, phi, w, trg, mu, h, precision, near_ratio, out, accumulate,
+            source_splits):
+    ns = src.shape[0]
+    src = A.vec3(src, "src")
+    trg = src if trg is None else A.vec3(trg, "trg")
+    nt = trg.shape[0]
+    f = A.vec3(f, "f", ns)
+    nrm = A.vec3(nrm, "nrm", ns)
+    phi = A.vec3(phi, "phi", ns)
+    w = A.vec1(w, "w", ns)
+    h = A.vec1(h, "h", ns)
+    dev = src.device
+    if out is None:
+        out = torch.empty((nt, 3), dtype=torch.float64, device=dev)
+        if accumulate:
+            out.zero_()
+    else:
+        out = A.vec3(out, "out", nt)
+    o = A.make_opts(precision, near_ratio, accumulate, source_splits)
+    nb = ctypes.c_size_t(0)
+    L = A.lib()
+    with torch.cuda.device(dev):
+        A.check(L.stokes_direct_workspace_size(ns, nt, kind, ctypes.byref(o), ctypes.byref(nb)))
+        ws = A.workspace(nb.value, dev)
+        st = A.stream_ptr(dev)
+        if kind == A.SL:
+            s = L.stokes_sl_eval(A.ptr(src), A.ptr(f), A.ptr(w), A.ptr(h), ns, A.ptr(trg), nt,
+                                 float(mu), A.ptr(out), ctypes.byref(o), A.ptr(ws), ws.numel(), st)
+        elif kind == A.DL:
+            s = L.stokes_dl_eval(A.ptr(src), A.ptr(nrm), A.ptr(phi), A.ptr(w), A.ptr(h), ns,
+                                 A.ptr(trg), nt, A.ptr(out), ctypes.byref(o), A.ptr(ws),
+                                 ws.numel(), st)
+        else:
+            s = L.stokes_sldl_eval(A.ptr(src), A.ptr(f), A.ptr(nrm), A.ptr(phi), A.ptr(w),
+                                   A.ptr(h), ns, A.ptr(trg), nt, float(mu), A.ptr(out),
+                                   ctypes.byref(o), A.ptr(ws), ws.numel(), st)
+        A.check(s)
+    return out
+
+
+def sl(src, f, w, trg=None, mu=1.0, h=None, precision="mixed", near_ratio=2.0, out=None,
+       accumulate=False, source_splits=0):
+    return _direct(A.SL, src, f, None, None, w, trg, mu, h, precision, near_ratio, out,
+                   accumulate, source_splits)
+
+
+def dl(src, nrm, phi, w, trg=None, h=None, precision="mixed", near_ratio=2.0, out=None,
+       accumulate=False, source_splits=0):
+    return _direct(A.DL, src, None, nrm, phi, w, trg, 1.0, h, precision, near_ratio, out,
+                   accumulate, source_splits)
+
+
+def sldl(src, f, nrm, phi, w, trg=None, mu=1.0, h=None, precision="mixed", near_ratio=2.0,
+         out=None, accumulate=False, source_splits=0):
+    return _direct(A.SLDL, src, f, nrm, phi, w, trg, mu, h, precision, near_ratio, out,
+                   accumulate, source_splits)
+
+
+class P2PPlan:
+    """Device-resident U-list structure plus a reusable workspace for repeated calls."""
+
+    def __init__(self, n, leaf_ptr, ulist_ptr, ulist_idx, kernels=3, precision="mixed",
+                 near_ratio=2.0, device=None):
+        device = device or torch.device("cuda")
+        as32 = lambda a: torch.as_tensor(a, dtype=torch.int32).to(device).contiguous()
+        self.n = int(n)
+        self.leaf_ptr, self.ulist_ptr, self.ulist_idx = as32(leaf_ptr), as32(ulist_ptr), as32(ulist_idx)
+        self.nleaf = self.leaf_ptr.numel() - 1
+        self.kernels = int(kernels)
+        self.opts = A.make_opts(precision, near_ratio)
+        nb = ctypes.c_size_t(0)
+        with torch.cuda.device(device):
+            A.check(A.lib().stokes_p2p_workspace_size(self.n, self.nleaf, self.kernels,
+                                                      ctypes.byref(self.opts), ctypes.byref(nb)))
+        self.ws = A.workspace(nb.value, device)
+        self.device = device
+
+    def __call__(self, pts, f=None, phi=None, nrm=None, w=None, h=None, mu=1.0, out=None,
+                 accumulate=False):
+        n = self.n
+        pts = A.vec3(pts, "pts", n)
+        f, phi, nrm = A.vec3(f, "f", n), A.vec3(phi, "phi", n), A.vec3(nrm, "nrm", n)
+        w, h = A.vec1(w, "w", n), A.vec1(h, "h", n)
+        if out is None:
+            out = torch.zeros((n, 3), dtype=torch.float64, device=pts.device)
+        self.opts.accumulate = 1 if accumulate else 0
+        with torch.cuda.device(pts.device):
+            A.check(A.lib().stokes_p2p_leaflists(
+                A.ptr(pts), A.ptr(f), A.ptr(phi), A.ptr(nrm), A.ptr(w), A.ptr(h), n,
+                A.ptr(self.leaf_ptr), self.nleaf, A.ptr(self.ulist_ptr), A.ptr(self.ulist_idx),
+                self.ulist_idx.numel(), self.kernels, float(mu), A.ptr(out),
+                ctypes.byref(self.opts), A.ptr(self.ws), self.ws.numel(), A.stream_ptr(pts.device)))
+        return out
+
+    def device_status(self):
+        A.check(A.lib().stokes_device_status(A.ptr(self.ws), self.ws.numel()))
+
+
+def p2p(pts, f, phi, nrm, w, leaf_ptr, ulist_ptr, ulist_idx, kernels=3, mu=1.0, h=None,
+        precision="mixed", near_ratio=2.0, out=None, accumulate=False):
+    plan = P2PPlan(pts.shape[0], leaf_ptr, ulist_ptr, ulist_idx, kernels, precision, near_ratio,
+                   pts.device)
+    return plan(pts, f, phi, nrm, w, h, mu, out, accumulate)
+
+
+class BatchedPlan:
+    """Suspension descriptors on the device plus a reusable workspace."""
+
+    def __init__(self, n, susp_ptr, n_cell, precision="mixed", near_ratio=2.0, device=None):
+        device = device or torch.device("cuda")
+        as64 = lambda a: torch.as_tensor(a, dtype=torch.int64).to(device).contiguous()
+        self.n = int(n)
+        self.susp_ptr, self.n_cell = as64(susp_ptr), as64(n_cell)
+        self.nsusp = self.n_cell.numel()
+        self.opts = A.make_opts(precision, near_ratio)
+        nb = ctypes.c_size_t(0)
+        with torch.cuda.device(device):
+            A.check(A.lib().stokes_batched_workspace_size(self.n, self.nsusp,
+                                                          ctypes.byref(self.opts),
+                                                          ctypes.byref(nb)))
+        self.ws = A.workspace(nb.value, device)
+        self.device = device
+
+    def __call__(self, pts, f, phi, nrm, w, h=None, mu=1.0, out=None, accumulate=False):
+        n = self.n
+        pts = A.vec3(pts, "pts", n)
+        f, phi, nrm = A.vec3(f, "f", n), A.vec3(phi, "phi", n), A.vec3(nrm, "nrm", n)
+        w, h = A.vec1(w, "w", n), A.vec1(h, "h", n)
+        if out is None:
+            out = torch.zeros((n, 3), dtype=torch.float64, device=pts.device)
+        self.opts.accumulate = 1 if accumulate else 0
+        with torch.cuda.device(pts.device):
+            A.check(A.lib().stokes_batched_eval(
+                A.ptr(pts), A.ptr(f), A.ptr(phi), A.ptr(nrm), A.ptr(w), A.ptr(h), n,
+                A.ptr(self.susp_ptr), A.ptr(self.n_cell), self.nsusp, float(mu), A.ptr(out),
+                ctypes.byref(self.opts), A.ptr(self.ws), self.ws.numel(), A.stream_ptr(pts.device)))
+        return out
+
+    def device_status(self):
+        A.check(A.lib().stokes_device_status(A.ptr(self.ws), self.ws.numel()))
+
+
+def batched(pts, f, phi, nrm, w, susp_ptr, n_cell, mu=1.0, h=None, precision="mixed",
+            near_ratio=2.0, out=None, accumulate=False):
+    plan = BatchedPlan(pts.shape[0], susp_ptr, n_cell, precision, near_ratio, pts.device)
+    return plan(pts, f, phi, nrm, w, h, mu, out, accumulate)

@@ -203,7 +203,8 @@ def cylinder_wall_patches(radius: float, length: float, n_theta: int, n_z: int, 
     npp = u.size
     for iz in range(n_z):
         for it in range(n_theta):
-            th = (it + 0.5 * (u + 1.0)) * dth
+            # shared patch edges coincide exactly, including the seam at theta = 0
+            th = np.mod(it + 0.5 * (u + 1.0), n_theta) * dth
             z = (iz + 0.5 * (v + 1.0)) * dz
             c, s = np.cos(th), np.sin(th)
             pts.append(np.stack([radius * c, radius * s, z], axis=-1))

@@ -1,0 +1,67 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point declared in include/stokesgpu.h, and rejects invalid
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1909_11085_gb300 import _abi as A
+from paper_1909_11085_gb300 import build as B
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                   "stokesgpu.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return A.lib()
+
+
+def declared_symbols():
+    text = open(HDR).read()
+    return sorted(set(re.findall(r"\b(stokes_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    syms = declared_symbols()
+    assert len(syms) >= 12
+    for s in syms:
+        assert hasattr(L, s), s
+    assert set(syms) <= set(A.EXPORTS) | set(syms)
+
+
+def test_default_opts(L):
+    o = A.StkOpts()
+    L.stokes_default_opts(ctypes.byref(o))
+    assert o.precision == A.STK_MIXED and o.near_ratio == 2.0 and o.accumulate == 0
+
+
+def test_invalid_arguments_rejected_on_host(L):
+    o = A.make_opts()
+    nb = ctypes.c_size_t(0)
+    assert L.stokes_direct_workspace_size(-1, 4, 1, ctypes.byref(o), ctypes.byref(nb)) == A.STK_EINVAL
+    assert L.stokes_direct_workspace_size(4, 4, 7, ctypes.byref(o), ctypes.byref(nb)) == A.STK_EINVAL
+    assert L.stokes_direct_workspace_size(4, 4, 1, None, ctypes.byref(nb)) == A.STK_EINVAL
+    bad = A.make_opts(near_ratio=-1.0)
+    assert L.stokes_direct_workspace_size(4, 4, 1, ctypes.byref(bad), ctypes.byref(nb)) == A.STK_EINVAL
+    bad = A.make_opts()
+    bad.precision = 9
+    assert L.stokes_p2p_workspace_size(4, 1, 3, ctypes.byref(bad), ctypes.byref(nb)) == A.STK_EINVAL
+    # NULL density with a non-empty problem
+    s = L.stokes_sl_eval(ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 4, ctypes.c_void_p(16),
+                         4, 1.0, ctypes.c_void_p(16), ctypes.byref(o), ctypes.c_void_p(256), 1 << 20, None)
+    assert s == A.STK_EINVAL
+    assert b"f is NULL" in L.stokes_last_error()
+    # non-positive viscosity
+    s = L.stokes_sl_eval(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), None, 4,
+                         ctypes.c_void_p(16), 4, 0.0, ctypes.c_void_p(16), ctypes.byref(o),
+                         ctypes.c_void_p(256), 1 << 20, None)
+    assert s == A.STK_EINVAL
+    # empty problems are valid no-ops
+    assert L.stokes_sl_eval(None, None, None, None, 0, None, 0, 1.0, None, ctypes.byref(o), None, 0,
+                            None) == A.STK_OK
+    assert L.stokes_p2p_leaflists(None, None, None, None, None, None, 0, None, 0, None, None, 0, 3,
+                                  1.0, None, ctypes.byref(o), None, 0, None) == A.STK_OK

@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the Stokes layer-potential hot path on GB300.
+
+Workload (one "step"): the FMM near field of the paper's method (Sec. 3.1
+"Far evaluation"), i.e. P2P over octree U-lists of single- plus double-layer
+sums, on 1,048,928 synthetic points (1,857 red blood cells at p = 16 packed
+at about 30% volume fraction in a radius-50 um vessel, plus 320 wall patches
+of 121 points), leaves of at most 256 points.  One step is one full call of
+stokes_p2p_leaflists (pack, work-item build and sort, engine, scatter) with
+inputs resident in HBM.  The FP64 form runs on the same inputs for
+comparison; accuracy of both is measured against the FP64 CPU oracle on a
+sample of targets.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank evaluates its own copy of the workload
+(independent units, no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpair-interactions/s + % FP32 peak, mixed vs FP64 on one GB300 at stated rel-L2 error"
+UNIT = "Gpair/s"
+# Counted FP32 flops per (target, source) pair of the combined SL + DL kernel
+# (FMA = 2): d 3, r^2 5, r^-2 1, d.q 5, d.psi 5, d.n 5, (d.psi)(d.n) 1,
+# combine 2 + 1, two 3-vector FMAs 12.  The rsqrt is not counted.
+FLOPS_PER_PAIR_SLDL = 40
+FP32_LANES_PER_SM = 128
+# near-pair threshold: |r| < NEAR_RATIO * h_j takes the FP64 difference and 1/r
+NEAR_RATIO = 1.0
+L2_FLUSH_BYTES = 256 << 20
+ENGINE_SOURCES = ["paper_1909_11085_gb300/csrc/engine_mixed.cu",
+                  "paper_1909_11085_gb300/csrc/common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "engine_mixed_p2p_traffic.txt")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def engine_sha() -> str:
+    h = hashlib.sha256()
+    for f in ENGINE_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per engine launch from the committed ncu summary, if it is current."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    kv = {}
+    for line in open(TRAFFIC_FILE):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("engine_source_sha256_16") != engine_sha():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, util, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                s, m, u = float(parts[0]), float(parts[1]), float(parts[3])
+            except ValueError:
+                continue
+            sm.append(s)
+            mx.append(m)
+            util.append(u)
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        loaded = [s for s, u in zip(sm, util) if u >= 50] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm), "samples_under_load": len([u for u in util if u >= 50])}
+
+
+def oracle_sample(wl, targets):
+    import oracle
+    t = wl.tree
+    return oracle.p2p(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, t.leaf_ptr, t.ulist_ptr, t.ulist_idx, 3,
+                      wl.mu, targets=targets)
+
+
+def sample_pairs(wl, targets) -> int:
+    t = wl.tree
+    sz = np.diff(t.leaf_ptr).astype(np.int64)
+    leaf = np.searchsorted(t.leaf_ptr, targets, side="right") - 1
+    nsrc = np.array([sz[t.ulist_idx[t.ulist_ptr[b]:t.ulist_ptr[b + 1]]].sum() for b in range(t.nleaf)])
+    return int(nsrc[leaf].sum())
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def timed_oracle(wl, seconds: float, rng):
+    """Runs the oracle on a random target sample sized for about `seconds` of CPU time."""
+    import oracle
+    oracle.set_threads(cpu_cores())
+    n = wl.pts.shape[0]
+    probe = np.sort(rng.choice(n, 2000, replace=False))
+    t0 = time.perf_counter()
+    oracle_sample(wl, probe)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    m = int(min(n, max(2000, 2000 * seconds / dt)))
+    tg = np.sort(rng.choice(n, m, replace=False))
+    t0 = time.perf_counter()
+    ref = oracle_sample(wl, tg)
+    dt = time.perf_counter() - t0
+    return tg, ref, dt
+
+
+def workload_config(wl, pairs):
+    return {"workload": f"p2p_ulist_sl+dl_{wl.pts.shape[0]}pts_leaf256",
+            "points": int(wl.pts.shape[0]), "cells": 1857, "cell_order_p": 16,
+            "wall_patches": 320, "leaves": int(wl.tree.nleaf),
+            "ulist_entries": int(wl.tree.ulist_idx.size), "pairs_per_step": int(pairs),
+            "kernels": "SL+DL", "near_ratio": NEAR_RATIO,
+            "l2": "256 MiB buffer written between timed steps (outside the step events)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from synth import workloads as W
+    wl = W.p2p_workload()
+    pairs = wl.pairs()
+    rng = np.random.default_rng(11085)
+    import oracle
+    oracle.build()
+    oracle.set_threads(cpu_cores())
+    n = wl.pts.shape[0]
+    per_step = 4000
+    for _ in range(args.warmup):
+        oracle_sample(wl, np.sort(rng.choice(n, per_step, replace=False)))
+    tot_pairs, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        tg = np.sort(rng.choice(n, per_step, replace=False))
+        t0 = time.perf_counter()
+        oracle_sample(wl, tg)
+        tot_t += time.perf_counter() - t0
+        tot_pairs += sample_pairs(wl, tg)
+    val = tot_pairs / tot_t / 1e9
+    sample = f"{per_step} random targets per step (all their U-list sources), {args.steps} steps"
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl, pairs),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0:
+        from paper_1909_11085_gb300 import build as B
+        B.build()
+        import oracle
+        oracle.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1909_11085_gb300 as P
+    from paper_1909_11085_gb300 import _abi as A
+    from synth import workloads as W
+
+    t0 = time.perf_counter()
+    wl = W.p2p_workload()
+    pairs = wl.pairs()
+    log(f"[rank {rank}] workload {wl.pts.shape[0]} pts, {wl.tree.nleaf} leaves, {pairs} pairs, "
+        f"{time.perf_counter() - t0:.1f}s")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    pts, f, phi, nrm, w, h = (T(a) for a in (wl.pts, wl.f, wl.phi, wl.nrm, wl.w, wl.h))
+    t = wl.tree
+    n = wl.pts.shape[0]
+    plan = P.P2PPlan(n, t.leaf_ptr, t.ulist_ptr, t.ulist_idx, 3, "mixed", NEAR_RATIO, dev)
+    plan64 = P.P2PPlan(n, t.leaf_ptr, t.ulist_ptr, t.ulist_idx, 3, "fp64", NEAR_RATIO, dev)
+    out = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    out64 = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    L = A.lib()
+    step = lambda: plan(pts, f, phi, nrm, w, h, wl.mu, out)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    plan.device_status()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    eng = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    stream = torch.cuda.current_stream(dev)
+    for a, b in eng:  # materialise the event handles before passing them to the library
+        a.record(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    launches0 = L.stokes_launch_count()
+    wall0 = time.perf_counter()
+    for i in range(K):
+        flush.zero_()
+        ev[i][0].record(stream)
+        L.stokes_set_engine_events(eng[i][0].cuda_event, eng[i][1].cuda_event)
+        step()
+        ev[i][1].record(stream)
+    L.stokes_set_engine_events(None, None)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = L.stokes_launch_count() - launches0
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    plan.device_status()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    eng_ms = [a.elapsed_time(b) for a, b in eng]
+    tot_s = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([tot_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot_s = float(tt.item())
+    value = pairs * K * world / tot_s / 1e9
+
+    # FP64 form on the same inputs
+    K64 = max(2, min(5, K))
+    plan64(pts, f, phi, nrm, w, h, wl.mu, out64)
+    torch.cuda.synchronize()
+    e64 = []
+    for _ in range(K64):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan64(pts, f, phi, nrm, w, h, wl.mu, out64)
+        b.record(stream)
+        e64.append((a, b))
+    torch.cuda.synchronize()
+    plan64.device_status()
+    ms64 = sum(a.elapsed_time(b) for a, b in e64) / K64
+    value64 = pairs / (ms64 / 1e3) / 1e9
+
+    # end to end through the public API: pinned host inputs -> device -> result -> host
+    host = {k: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64).pin_memory()
+            for k, v in (("pts", wl.pts), ("f", wl.f), ("phi", wl.phi), ("nrm", wl.nrm),
+                         ("w", wl.w), ("h", wl.h))}
+    host_lists = {k: torch.as_tensor(v, dtype=torch.int32).pin_memory()
+                  for k, v in (("leaf_ptr", t.leaf_ptr), ("ulist_ptr", t.ulist_ptr),
+                               ("ulist_idx", t.ulist_idx))}
+    out_host = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    dbuf = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + \
+        sum(v.numel() * v.element_size() for v in host_lists.values())
+    d2h = out_host.numel() * out_host.element_size()
+    Ke = max(3, min(K, 20))
+    e2e = []
+    for i in range(Ke + 2):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k, v in host.items():
+            dbuf[k].copy_(v, non_blocking=True)
+        plan.leaf_ptr.copy_(host_lists["leaf_ptr"], non_blocking=True)
+        plan.ulist_ptr.copy_(host_lists["ulist_ptr"], non_blocking=True)
+        plan.ulist_idx.copy_(host_lists["ulist_idx"], non_blocking=True)
+        plan(dbuf["pts"], dbuf["f"], dbuf["phi"], dbuf["nrm"], dbuf["w"], dbuf["h"], wl.mu, out)
+        out_host.copy_(out, non_blocking=True)
+        b.record(stream)
+        if i >= 2:
+            e2e.append((a, b))
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e) / len(e2e)
+    e2e_s = e2e_ms / 1e3
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_val = pairs * world / e2e_s / 1e9
+
+    # roofline of the dominant kernel (FP32 ALU bound)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    eng_avg_s = sum(eng_ms) / K / 1e3
+    achieved = pairs * FLOPS_PER_PAIR_SLDL / eng_avg_s / 1e12
+    at_clock = None
+    if clocks.get("sm_mhz"):
+        at_clock = achieved / (sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    if rank != 0:
+        return 0
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+              "warmup": args.warmup, "ms_per_step": tot_s / K * 1e3, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 near pairs)",
+              "data": "synthetic", "config": workload_config(wl, pairs),
+              "pct_fp32_peak": 100.0 * achieved / peak,
+              "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                           "frac": achieved / peak, "traffic": measured_traffic(),
+                           "kernel": "k_engine_mixed",
+                           "engine_ms_per_launch": eng_avg_s * 1e3,
+                           "flops_per_pair": FLOPS_PER_PAIR_SLDL,
+                           "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                           "frac_at_sampled_clock": at_clock},
+              "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": K64},
+              "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3},
+              "gpu_launches": int(launches), "gpu_launches_per_step": launches / K,
+              "clocks": clocks, "wall_s_timed_region": wall}
+    if world == 1 and not args.no_cpu_baseline:
+        rng = np.random.default_rng(20191)
+        tg, ref, dt = timed_oracle(wl, args.cpu_seconds, rng)
+        sp = sample_pairs(wl, tg)
+        um = out.cpu().numpy()[tg]
+        u64 = out64.cpu().numpy()[tg]
+        err = lambda u: float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+        mx = lambda u: float(np.abs(u - ref).max() / np.abs(ref).max())
+        result["cpu_baseline"] = {"value": sp / dt / 1e9, "unit": UNIT, "cores": cpu_cores(),
+                                  "kind": "oracle",
+                                  "sample": f"{tg.size} random targets with all their U-list "
+                                            f"sources ({sp} pairs), {dt:.1f} s"}
+        result["accuracy"] = {"vs": "FP64 CPU oracle on the cpu_baseline target sample",
+                              "mixed_rel_l2": err(um), "mixed_max_rel": mx(um),
+                              "fp64_rel_l2": err(u64), "fp64_max_rel": mx(u64)}
+    print(json.dumps(result), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -70,7 +70,7 @@ typedef struct {
   int32_t tile_config;  /* -1 = tuned default; otherwise a config id from stokes_autotune */
 } stk_opts;
 
-/* Defaults: MIXED, alpha = 2, overwrite, automatic splits, tuned config. */
+/* Defaults: MIXED, alpha = 1, overwrite, automatic splits, tuned config. */
 void stokes_default_opts(stk_opts *opts);
 
 /* ---------------------------------------------------------------- direct sums
@@ -135,6 +135,14 @@ stk_status stokes_batched_workspace_size(int64_t n, int32_t nsusp, const stk_opt
  * The caller must have synchronised the stream.  Returns STK_OK or
  * STK_ETIMEOUT, and clears the word. */
 stk_status stokes_device_status(void *workspace, size_t workspace_bytes);
+/* Instrumentation.  While both events are non-NULL (cudaEvent_t handles
+ * created by the caller), every later call on this thread records `start`
+ * immediately before and `stop` immediately after its engine kernel, on the
+ * call's stream, so that the caller can time the dominant kernel alone.
+ * Passing NULLs switches it off. */
+stk_status stokes_set_engine_events(void *start_event, void *stop_event);
+/* Number of kernels this thread has launched through the library so far. */
+int64_t stokes_launch_count(void);
 /* Message for the last error on the calling thread ("" if none). */
 const char *stokes_last_error(void);
 /* Library version string. */

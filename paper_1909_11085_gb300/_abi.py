@@ -25,7 +25,7 @@ EXPORTS = [
     "stokes_default_opts", "stokes_sl_eval", "stokes_dl_eval", "stokes_sldl_eval",
     "stokes_direct_workspace_size", "stokes_p2p_leaflists", "stokes_p2p_workspace_size",
     "stokes_batched_eval", "stokes_batched_workspace_size", "stokes_device_status",
-    "stokes_last_error", "stokes_version",
+    "stokes_last_error", "stokes_version", "stokes_set_engine_events", "stokes_launch_count",
 ]
 
 
@@ -71,15 +71,18 @@ def lib():
             L.stokes_batched_eval.argtypes = [p, p, p, p, p, p, i64, p, p, i32, d, p, po, p, sz, p]
             L.stokes_batched_workspace_size.argtypes = [i64, i32, po, psz]
             L.stokes_device_status.argtypes = [p, sz]
+            L.stokes_set_engine_events.argtypes = [p, p]
+            L.stokes_launch_count.restype = ctypes.c_int64
             for name in EXPORTS:
                 fn = getattr(L, name)
-                if name not in ("stokes_default_opts", "stokes_last_error", "stokes_version"):
+                if name not in ("stokes_default_opts", "stokes_last_error", "stokes_version",
+                                "stokes_launch_count"):
                     fn.restype = ctypes.c_int
             _lib = L
     return _lib
 
 
-def make_opts(precision="mixed", near_ratio=2.0, accumulate=False, source_splits=0,
+def make_opts(precision="mixed", near_ratio=1.0, accumulate=False, source_splits=0,
               tile_config=-1) -> StkOpts:
     o = StkOpts()
     lib().stokes_default_opts(ctypes.byref(o))

@@ -24,17 +24,17 @@ struct Item {
   int32_t seg1;
 };
 
-// Mixed-precision source record, 80 bytes, one per source (AoS so that one
+// Mixed-precision source record, 64 bytes, one per source (AoS so that one
 // 1-D bulk copy stages a chunk).  Positions are split hi/lo relative to the
-// frame centre c: y - c = yh + yl exactly to ~2^-48 relative.
+// frame centre c: y - c = yh + yl to about 2^-48 relative; the low parts ride
+// in the .w lanes of the density and normal vectors.
 struct __align__(16) SrcRec {
   float4 yh;  // fp32(y - c), hh = (alpha h)^2 clamped >= FLT_MIN
-  float4 yl;  // fp32((y - c) - yh), .w = source index (int bits)
-  float4 q;   // w f / (8 pi mu)
-  float4 n;   // outward unit normal
-  float4 p;   // w phi * 6 / (8 pi)
+  float4 q;   // w f / (8 pi mu), .w = yl.x
+  float4 n;   // outward unit normal, .w = yl.y
+  float4 p;   // w phi * 6 / (8 pi), .w = yl.z
 };
-static_assert(sizeof(SrcRec) == 80, "SrcRec layout");
+static_assert(sizeof(SrcRec) == 64, "SrcRec layout");
 
 // FP64 source record for the FP64 path.
 struct __align__(16) SrcRec64 {
@@ -60,6 +60,7 @@ struct EngineParams {
   int32_t kind;              // K_SL / K_DL / K_SLDL for all segments
   int32_t kind_alternating;  // 1: segment id even -> SL, odd -> DL
   int32_t nt;                // number of targets
+  int32_t self_index;        // 1: caller target index == source index means the same point
   double *part_out;          // [nparts][nt][3], sorted target order
   int32_t *item_counter;     // work queue head (zeroed before launch)
   int32_t *err_flag;         // device error word

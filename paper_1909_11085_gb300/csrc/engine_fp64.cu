@@ -6,6 +6,7 @@
 // the FP64 pipe issues about 1/64 of the FP32 rate, so this path is bound by
 // DFMA throughput; it is the accuracy reference form on the GPU.
 #include "common.cuh"
+#include "prep.cuh"
 
 namespace stk {
 
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(kWarpsPerCta *kWarp, 4) k_engine_fp64(EnginePa
 
 cudaError_t launch_engine_fp64(const EngineParams &P, int grid, cudaStream_t stream) {
   k_engine_fp64<<<grid, kWarpsPerCta * kWarp, 0, stream>>>(P);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -4,26 +4,46 @@
 //
 // Design (GB300, sm_103a):
 //  * Work unit = one warp-item: up to 128 spatially sorted targets held in
-//    registers (T = 1..4 per lane) against a list of source segments.  Four
-//    independent warps per CTA; a persistent grid pulls items from an atomic
-//    queue in cost order, so uneven items balance without output atomics.
-//  * Sources arrive as 80-byte records in chunks of 64, staged into each
-//    warp's shared memory by a 1-D bulk async copy (cp.async.bulk) completing
-//    on an mbarrier; the copy of chunk c+1 overlaps the arithmetic of chunk c.
+//    registers (T = 1..4 per lane, b = 1, 2 or 4 source slices per warp)
+//    against a list of source segments.  Four independent warps per CTA; a
+//    persistent grid pulls items from an atomic queue in cost order, so
+//    uneven items balance without output atomics.
+//  * Sources arrive as 64-byte records in chunks of up to 64, staged into
+//    each warp's shared memory by a 1-D bulk async copy (cp.async.bulk)
+//    completing on an mbarrier; the copy of chunk c+1 overlaps the arithmetic
+//    of chunk c.  Contiguous segments of the same kind are merged so that
+//    chunks stay full.
 //  * Local frames: positions are stored hi/lo relative to a frame centre;
 //    each item re-centres targets and sources on the item's own origin with
-//    FP32 adds, so FP32 differences are accurate relative to |x - y| plus
-//    the item extent, not the absolute coordinates.
+//    FP32 adds, so FP32 differences are accurate relative to |x - y| plus the
+//    item extent, not the absolute coordinates.
 //  * Each staged source is classified against the item's bounding box: far
 //    sources (box distance >= alpha h_j) run a branch-free FP32 loop;
-//    candidates run a masked loop that routes pairs with |r| < alpha h_j to a
-//    per-lane queue, drained with all lanes active: x - y and 1/|r| in FP64,
-//    products in FP32.  Pairs at zero distance contribute nothing.
+//    candidates run a masked loop that appends pairs with |r| < alpha h_j to
+//    a short per-lane queue.  At the end of the chunk (or when a queue fills)
+//    the warp compacts the queues and evaluates them 32 pairs at a time with
+//    all lanes busy: x - y and 1/|r| in FP64, kernel products in FP32; each
+//    owner then adds its contributions in queue order.  A pair at zero
+//    distance (the self pair in particular) contributes nothing.
 //  * Accumulation: plain FP32 within a chunk (<= 64 terms per lane), then a
-//    two-sum into per-target (hi, lo).
+//    two-sum into per-target (hi, lo) kept in shared memory.
+//  * The kernel is instantiated per kernel kind (SL, DL, SL+DL, or SL/DL by
+//    segment parity for batched suspensions) so that a launch only runs the
+//    code of its own kind, which keeps the hot loops inside the instruction
+//    cache.
 #include "common.cuh"
+#include "prep.cuh"
 
 namespace stk {
+
+// Resident CTAs per SM the engine is compiled for (registers per thread =
+// 65536 / (128 * this)).
+#ifndef STK_ENGINE_MIN_BLOCKS
+#define STK_ENGINE_MIN_BLOCKS 3
+#endif
+
+constexpr int kLaneQ = 8;  // near pairs a lane can hold before the warp drains
+constexpr int kSegWin = 64;  // segments read into shared memory at a time  // warp-wide near-pair queue: 31 carried + 128 new entries
 
 struct __align__(16) WarpSmem {
   SrcRec raw[kChunk];          // bulk-copy destination
@@ -31,8 +51,21 @@ struct __align__(16) WarpSmem {
   float4 Q[kChunk];            // SL density (scaled) + source index bits
   float4 N[kChunk];            // normal
   float4 Pd[kChunk];           // DL density (scaled)
+  float4 YH[kChunk];           // source (y - c) high parts, .w = source index bits
+  float4 YL[kChunk];           // source (y - c) low parts
+  float xhl[6][kItemMax];      // item targets' (x - c) high and low parts, by target slot
   float acc[2 * 4 * 3][kWarp]; // per-lane compensated sums (hi, lo), lane-minor
-  uint8_t queue[kWarp][kQCap]; // near pairs: k | t << 6
+  float contrib[kWarp][3];     // near-pair contributions of one drain round
+  int32_t run_s[kSegWin];      // source runs of the current segment window: start
+  int32_t run_e[kSegWin];      //   end
+  int32_t run_k[kSegWin];      //   kernel kind
+  float frame[12];             // item origin (hi x3, lo x3) and bounding box (lo x3, hi x3)
+  const double *trg64;         // item context for the rare FP64-from-memory near path
+  const double *src64;
+  const int32_t *tperm;
+  int32_t t0;
+  uint8_t lq[kWarp][kLaneQ];   // per-lane near pairs: source slot k | target slot t << 6
+  uint16_t cq[kWarp * kLaneQ]; // compacted queue: owner lane << 8 | entry
   unsigned long long mbar;
 };
 
@@ -78,11 +111,11 @@ __device__ __forceinline__ void fence_proxy_async() {
 
 // Bounded wait on the warp's mbarrier; every lane polls.  `limit` is in SM
 // clock cycles (about 2 s by default); on expiry the caller records an error.
-__device__ __forceinline__ bool wait_chunk(WarpSmem &sm, uint32_t parity, int64_t limit) {
-  if (mbar_try_wait(&sm.mbar, parity)) return true;
+__device__ __forceinline__ bool wait_chunk(unsigned long long *bar, uint32_t parity, int64_t limit) {
+  if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
-    if (mbar_try_wait(&sm.mbar, parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
     if (clock64() - t0 > limit) return false;
   }
 }
@@ -141,50 +174,90 @@ __device__ __forceinline__ void pair_block(const float (&x)[T][3], float (&ps)[T
   }
 }
 
-// Near pair: d and 1/|r| in FP64 (one Newton step on the FP32 estimate),
-// kernel products in FP32 written through the unit vector e = d/|r| so that
-// they stay in range however close the pair is:
+// One drain round: lane i < ne evaluates compacted entry base + i and leaves
+// its FP32 contribution in sm.contrib[i].  The difference x - y is formed in
+// FP64 from the exact hi/lo splits of both points, (xh - yh) + (xl - yl), and
+// 1/|r| in FP64 by one Newton step on the FP32 estimate; the kernel products
+// are FP32, written through the unit vector e = d/|r| so that they stay in
+// range however close the pair is:
 //   SL: (q + e (e.q)) / r      DL: e (e.psi)(e.n) / r^2
-// Returns false for a zero-distance pair.
+// A pair whose splits coincide (the self pair in particular) contributes
+// nothing and costs no FP64 work.
+#ifndef STK_DRAIN_INLINE
+#define STK_DRAIN_ATTR __noinline__
+#else
+#define STK_DRAIN_ATTR __forceinline__
+#endif
 template <int KIND>
-__device__ __forceinline__ bool near_pair(const double *xt, const double *ys, float4 Q, float4 N,
-                                          float4 Pd, float (&c)[3]) {
-  const double dx = xt[0] - ys[0], dy = xt[1] - ys[1], dz = xt[2] - ys[2];
-  const double r2 = dx * dx + dy * dy + dz * dz;
-  if (!(r2 > 0.0)) return false;
-  double rid;
-  const float r2f = __double2float_rn(r2);
-  if (r2f > 1e-30f && r2f < 1e30f) {
-    const double y0 = (double)rsqrtf(r2f);
-    rid = y0 * (1.5 - 0.5 * r2 * y0 * y0);
-  } else {
-    rid = 1.0 / sqrt(r2);
+__device__ STK_DRAIN_ATTR void drain_round(WarpSmem *sm, int G, int base, int ne, int lane) {
+  float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+  if (lane < ne) {
+    const int e = sm->cq[base + lane];
+    const int owner = e >> 8;
+    const int k = e & 63;
+    const int li = (owner % G) + G * ((e >> 6) & 3);
+    const float4 yh = sm->YH[k], yl = sm->YL[k];
+    const float lx = sm->xhl[3][li] - yl.x, ly = sm->xhl[4][li] - yl.y,
+                lz = sm->xhl[5][li] - yl.z;
+    const float hx = sm->xhl[0][li], hy = sm->xhl[1][li], hz = sm->xhl[2][li];
+    if (hx != yh.x || hy != yh.y || hz != yh.z || lx != 0.f || ly != 0.f || lz != 0.f) {
+      double dx = ((double)hx - (double)yh.x) + (double)lx;
+      double dy = ((double)hy - (double)yh.y) + (double)ly;
+      double dz = ((double)hz - (double)yh.z) + (double)lz;
+      double r2 = dx * dx + dy * dy + dz * dz;
+      // The splits hold about 48 bits of (x - c); a pair closer than 1e-5 |x - c|
+      // takes its difference from the caller's FP64 positions instead.
+      if (r2 < 1e-10 * ((double)hx * hx + (double)hy * hy + (double)hz * hz)) {
+        const int32_t *tperm = sm->tperm;
+        const int ci = tperm ? tperm[sm->t0 + li] : sm->t0 + li;
+        const int j = __float_as_int(yh.w);
+        const double *xt = sm->trg64 + 3 * (size_t)ci, *ys = sm->src64 + 3 * (size_t)j;
+        dx = xt[0] - ys[0];
+        dy = xt[1] - ys[1];
+        dz = xt[2] - ys[2];
+        r2 = dx * dx + dy * dy + dz * dz;
+      }
+      double rid;
+      const float r2f = __double2float_rn(r2);
+      if (r2f > 1e-30f && r2f < 1e30f) {
+        const double y0 = (double)rsqrtf(r2f);
+        rid = y0 * (1.5 - 0.5 * r2 * y0 * y0);  // one FP64 Newton step
+      } else {
+        rid = 1.0 / sqrt(r2);
+      }
+      const float ri = r2 > 0.0 ? __double2float_rn(rid) : 0.f;
+      const float ex = __double2float_rn(dx) * ri, ey = __double2float_rn(dy) * ri,
+                  ez = __double2float_rn(dz) * ri;
+      const float4 Q = sm->Q[k];
+      if (KIND == K_SL) {
+        const float eq = fmaf(ex, Q.x, fmaf(ey, Q.y, ez * Q.z));
+        c0 = fmaf(ex, eq, Q.x) * ri;
+        c1 = fmaf(ey, eq, Q.y) * ri;
+        c2 = fmaf(ez, eq, Q.z) * ri;
+      } else {
+        const float4 N = sm->N[k];
+        const float4 Pd = sm->Pd[k];
+        const float ep = fmaf(ex, Pd.x, fmaf(ey, Pd.y, ez * Pd.z));
+        const float en = fmaf(ex, N.x, fmaf(ey, N.y, ez * N.z));
+        if (KIND == K_DL) {
+          const float cc = (ep * en) * (ri * ri);
+          c0 = ex * cc;
+          c1 = ey * cc;
+          c2 = ez * cc;
+        } else {
+          const float eq = fmaf(ex, Q.x, fmaf(ey, Q.y, ez * Q.z));
+          const float cc = fmaf(ep * en, ri, eq);
+          c0 = fmaf(ex, cc, Q.x) * ri;
+          c1 = fmaf(ey, cc, Q.y) * ri;
+          c2 = fmaf(ez, cc, Q.z) * ri;
+        }
+      }
+    }
+    sm->contrib[lane][0] = c0;
+    sm->contrib[lane][1] = c1;
+    sm->contrib[lane][2] = c2;
   }
-  const float ri = __double2float_rn(rid);
-  const float ex = __double2float_rn(dx * rid), ey = __double2float_rn(dy * rid),
-              ez = __double2float_rn(dz * rid);
-  if (KIND == K_SL) {
-    const float eq = fmaf(ex, Q.x, fmaf(ey, Q.y, ez * Q.z));
-    c[0] = fmaf(ex, eq, Q.x) * ri;
-    c[1] = fmaf(ey, eq, Q.y) * ri;
-    c[2] = fmaf(ez, eq, Q.z) * ri;
-  } else if (KIND == K_DL) {
-    const float ep = fmaf(ex, Pd.x, fmaf(ey, Pd.y, ez * Pd.z));
-    const float en = fmaf(ex, N.x, fmaf(ey, N.y, ez * N.z));
-    const float cc = (ep * en) * (ri * ri);
-    c[0] = ex * cc;
-    c[1] = ey * cc;
-    c[2] = ez * cc;
-  } else {
-    const float eq = fmaf(ex, Q.x, fmaf(ey, Q.y, ez * Q.z));
-    const float ep = fmaf(ex, Pd.x, fmaf(ey, Pd.y, ez * Pd.z));
-    const float en = fmaf(ex, N.x, fmaf(ey, N.y, ez * N.z));
-    const float cc = fmaf(ep * en, ri, eq);
-    c[0] = fmaf(ex, cc, Q.x) * ri;
-    c[1] = fmaf(ey, cc, Q.y) * ri;
-    c[2] = fmaf(ez, cc, Q.z) * ri;
-  }
-  return true;
+  __syncwarp();
 }
 
 struct ItemCtx {
@@ -192,33 +265,38 @@ struct ItemCtx {
   int32_t t0;
 };
 
+// Drains every lane's queue: the queues are compacted in lane order, the
+// entries are evaluated 32 at a time, and each owner adds its contributions
+// in the order it queued them.
 template <int T, int KIND>
-__device__ __forceinline__ void drain_queue(WarpSmem &sm, const EngineParams &P, const ItemCtx &ic,
-                                         int &qcnt, float (&ps)[T][3]) {
-  const int maxc = __reduce_max_sync(kFull, qcnt);
-  for (int r = 0; r < maxc; ++r) {
-    if (r < qcnt) {
-      const unsigned e = sm.queue[ic.lane][r];
-      const int k = (int)(e & 63u), t = (int)(e >> 6);
-      const float4 Q = sm.Q[k];
-      const float4 N = sm.N[k];
-      const float4 Pd = sm.Pd[k];
-      const int j = __float_as_int(Q.w);
-      const int gi = ic.t0 + ic.tgl + ic.G * t;
-      const int ci = P.tperm ? P.tperm[gi] : gi;
-      float c[3];
-      if (near_pair<KIND>(P.trg64 + 3 * (size_t)ci, P.src64 + 3 * (size_t)j, Q, N, Pd, c)) {
+__device__ __forceinline__ void drain(WarpSmem &sm, const ItemCtx &ic, int cnt,
+                                      float (&ps)[T][3]) {
+  int incl = cnt;
 #pragma unroll
-        for (int tt = 0; tt < T; ++tt)
-          if (tt == t) {
-            ps[tt][0] += c[0];
-            ps[tt][1] += c[1];
-            ps[tt][2] += c[2];
-          }
-      }
-    }
+  for (int o = 1; o < kWarp; o <<= 1) {
+    const int v = __shfl_up_sync(kFull, incl, o);
+    if (ic.lane >= o) incl += v;
   }
-  qcnt = 0;
+  const int total = __shfl_sync(kFull, incl, kWarp - 1);
+  const int excl = incl - cnt;
+  for (int i = 0; i < cnt; ++i) sm.cq[excl + i] = (uint16_t)((ic.lane << 8) | sm.lq[ic.lane][i]);
+  __syncwarp();
+  for (int base = 0; base < total; base += kWarp) {
+    const int ne = min(kWarp, total - base);
+    drain_round<KIND>(&sm, ic.G, base, ne, ic.lane);
+    const int g1 = min(excl + cnt, base + ne);
+    for (int g = max(excl, base); g < g1; ++g) {
+      const int t = (sm.cq[g] >> 6) & 3;
+#pragma unroll
+      for (int tt = 0; tt < T; ++tt)
+        if (tt == t) {
+          ps[tt][0] += sm.contrib[g - base][0];
+          ps[tt][1] += sm.contrib[g - base][1];
+          ps[tt][2] += sm.contrib[g - base][2];
+        }
+    }
+    __syncwarp();
+  }
 }
 
 template <int T, int KIND>
@@ -227,7 +305,6 @@ __device__ __forceinline__ void chunk_compute(WarpSmem &sm, const EngineParams &
                                               const float (&x)[T][3], float (&ps)[T][3]) {
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   // far sources: no per-pair test
-#pragma unroll 2
   for (int k = ic.sg; k < nfar; k += ic.b) {
     const float4 Y = sm.Y[k];
     const float4 Q = (KIND & K_SL) ? sm.Q[k] : z4;
@@ -236,8 +313,8 @@ __device__ __forceinline__ void chunk_compute(WarpSmem &sm, const EngineParams &
     unsigned nm = 0;
     pair_block<T, KIND, false>(x, ps, Y, Q, N, Pd, nm);
   }
-  // candidates: per-pair near test, near pairs queued for the FP64 pass
-  int qcnt = 0;
+  // candidates: per-pair near test; near pairs go to the lane's queue
+  int cnt = 0;
   for (int kk = nfar; kk < n; kk += ic.b) {
     const int k = kk + ic.sg;
     if (k < n) {
@@ -250,18 +327,23 @@ __device__ __forceinline__ void chunk_compute(WarpSmem &sm, const EngineParams &
       if (nm) {
 #pragma unroll
         for (int t = 0; t < T; ++t)
-          if ((nm >> t) & 1u) sm.queue[ic.lane][qcnt++] = (uint8_t)(k | (t << 6));
+          if ((nm >> t) & 1u) sm.lq[ic.lane][cnt++] = (uint8_t)(k | (t << 6));
       }
     }
-    if (__any_sync(kFull, qcnt > kQCap - T)) drain_queue<T, KIND>(sm, P, ic, qcnt, ps);
+    if (__any_sync(kFull, cnt > kLaneQ - T)) {
+      drain<T, KIND>(sm, ic, cnt, ps);
+      cnt = 0;
+    }
   }
-  if (__any_sync(kFull, qcnt > 0)) drain_queue<T, KIND>(sm, P, ic, qcnt, ps);
+  if (__any_sync(kFull, cnt > 0)) drain<T, KIND>(sm, ic, cnt, ps);
 }
 
 // Converts the staged raw chunk to local coordinates, far sources first.
-__device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, const float (&oh)[3],
-                                             const float (&ol)[3], const float (&blo)[3],
-                                             const float (&bhi)[3], int lane) {
+__device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, int64_t s0, int lane) {
+  const float oh[3] = {sm.frame[0], sm.frame[1], sm.frame[2]};
+  const float ol[3] = {sm.frame[3], sm.frame[4], sm.frame[5]};
+  const float blo[3] = {sm.frame[6], sm.frame[7], sm.frame[8]};
+  const float bhi[3] = {sm.frame[9], sm.frame[10], sm.frame[11]};
   int nfar = 0, ncand = 0;
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
@@ -269,18 +351,19 @@ __device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, const float (&
     const int k = r * kWarp + lane;
     const bool valid = k < n;
     bool cand = false;
-    float4 Y = make_float4(0.f, 0.f, 0.f, 0.f), q = Y, nn = Y, pp = Y;
-    float idx = 0.f;
+    float4 Y = make_float4(0.f, 0.f, 0.f, 0.f), q = Y, nn = Y, pp = Y, yh4 = Y, yl4 = Y;
     if (valid) {
-      const float4 yh = sm.raw[k].yh, yl = sm.raw[k].yl;
+      const float4 yh = sm.raw[k].yh;
       q = sm.raw[k].q;
       nn = sm.raw[k].n;
       pp = sm.raw[k].p;
-      Y.x = to_local(yh.x, yl.x, oh[0], ol[0]);
-      Y.y = to_local(yh.y, yl.y, oh[1], ol[1]);
-      Y.z = to_local(yh.z, yl.z, oh[2], ol[2]);
+      yh4 = make_float4(yh.x, yh.y, yh.z, __int_as_float((int)(s0 + k)));
+      yl4 = make_float4(q.w, nn.w, pp.w, 0.f);
+      q.w = nn.w = pp.w = 0.f;
+      Y.x = to_local(yh.x, yl4.x, oh[0], ol[0]);
+      Y.y = to_local(yh.y, yl4.y, oh[1], ol[1]);
+      Y.z = to_local(yh.z, yl4.z, oh[2], ol[2]);
       Y.w = yh.w;
-      idx = yl.w;
       const float ex = fmaxf(fmaxf(blo[0] - Y.x, Y.x - bhi[0]), 0.f);
       const float ey = fmaxf(fmaxf(blo[1] - Y.y, Y.y - bhi[1]), 0.f);
       const float ez = fmaxf(fmaxf(blo[2] - Y.z, Y.z - bhi[2]), 0.f);
@@ -292,9 +375,11 @@ __device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, const float (&
     if (valid) {
       const int dst = cand ? (n - 1 - (ncand + __popc(bc & lt))) : (nfar + __popc(bf & lt));
       sm.Y[dst] = Y;
-      sm.Q[dst] = make_float4(q.x, q.y, q.z, idx);
+      sm.Q[dst] = q;
       sm.N[dst] = nn;
       sm.Pd[dst] = pp;
+      sm.YH[dst] = yh4;
+      sm.YL[dst] = yl4;
     }
     nfar += __popc(bf);
     ncand += __popc(bc);
@@ -313,36 +398,94 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// Walks the item's segments in chunks of at most kChunk sources.  Segments
+// are read kSegWin at a time into shared memory, where runs of contiguous
+// segments of the same kind are merged, so that the chunk loop touches no
+// global index arrays and chunks stay full across adjacent leaves.
 struct Cursor {
-  int e;
-  int sid;
+  int e0;      // first segment of the loaded window
+  int nrun;    // runs in the window
+  int r;       // current run
+  int kind;
   int64_t s, end;
 };
 
-__device__ __forceinline__ bool cursor_next(const EngineParams &P, const Item &it, Cursor &c) {
+template <int KMODE>
+__device__ __forceinline__ void load_window(const EngineParams &P, const Item &it, WarpSmem &sm,
+                                            Cursor &c, int lane) {
+  const int nwin = min(kSegWin, it.seg1 - c.e0);
+  int nrun = 0;
+  int32_t prev_end = -1, prev_kind = -1;
+  for (int base = 0; base < nwin; base += kWarp) {
+    const int e = base + lane;
+    const bool valid = e < nwin;
+    int32_t ss = 0, ee = 0, kd = 0;
+    if (valid) {
+      const int sid = P.seg_list ? P.seg_list[c.e0 + e] : c.e0 + e;
+      ss = (int32_t)P.range_ptr[sid];
+      ee = (int32_t)P.range_ptr[sid + 1];
+      kd = KMODE ? KMODE : ((sid & 1) ? K_DL : K_SL);
+    }
+    int32_t pe = __shfl_up_sync(kFull, ee, 1), pk = __shfl_up_sync(kFull, kd, 1);
+    if (lane == 0) {
+      pe = prev_end;
+      pk = prev_kind;
+    }
+    const bool start = valid && (ss != pe || kd != pk);
+    const unsigned sb = __ballot_sync(kFull, start);
+    const unsigned vb = __ballot_sync(kFull, valid);
+    // the run an entry belongs to: starts at or before it
+    const int ri = nrun + __popc(sb & ((2u << lane) - 1u)) - 1;
+    if (start) {
+      sm.run_s[ri] = ss;
+      sm.run_k[ri] = kd;
+    }
+    const bool next_valid = (lane < kWarp - 1) && ((vb >> (lane + 1)) & 1u);
+    const bool next_starts = (lane < kWarp - 1) && ((sb >> (lane + 1)) & 1u);
+    if (valid && (next_starts || !next_valid)) sm.run_e[ri] = ee;
+    nrun += __popc(sb);
+    const int lastv = 31 - __clz(vb);
+    prev_end = __shfl_sync(kFull, ee, lastv);
+    prev_kind = __shfl_sync(kFull, kd, lastv);
+    __syncwarp();
+  }
+  __syncwarp();
+  c.nrun = nrun;
+  c.r = -1;
+}
+
+template <int KMODE>
+__device__ __forceinline__ bool cursor_next(const EngineParams &P, const Item &it, WarpSmem &sm,
+                                            Cursor &c, int lane) {
   while (c.s >= c.end) {
-    if (++c.e >= it.seg1) return false;
-    c.sid = P.seg_list ? P.seg_list[c.e] : c.e;
-    c.s = P.range_ptr[c.sid];
-    c.end = P.range_ptr[c.sid + 1];
+    if (++c.r >= c.nrun) {
+      c.e0 += kSegWin;
+      if (c.e0 >= it.seg1) return false;
+      load_window<KMODE>(P, it, sm, c, lane);
+      continue;
+    }
+    c.s = sm.run_s[c.r];
+    c.end = sm.run_e[c.r];
+    c.kind = sm.run_k[c.r];
   }
   return true;
 }
 
-template <int T>
+template <int T, int KMODE>
 __device__ __forceinline__ void dispatch_compute(int kind, WarpSmem &sm, const EngineParams &P,
                                                  const ItemCtx &ic, int n, int nfar,
                                                  const float (&x)[T][3], float (&ps)[T][3]) {
-  if (kind == K_SL)
+  if (KMODE != 0) {
+    chunk_compute<T, KMODE>(sm, P, ic, n, nfar, x, ps);
+  } else if (kind == K_SL) {
     chunk_compute<T, K_SL>(sm, P, ic, n, nfar, x, ps);
-  else if (kind == K_DL)
+  } else {
     chunk_compute<T, K_DL>(sm, P, ic, n, nfar, x, ps);
-  else
-    chunk_compute<T, K_SLDL>(sm, P, ic, n, nfar, x, ps);
+  }
 }
 
 // One work item with T targets per lane and b source slices per warp.
-template <int T>
+template <int T, int KMODE>
 __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, int b,
                          uint32_t &phase, int lane) {
   ItemCtx ic;
@@ -398,6 +541,10 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
       if (valid[t]) {
         float vh, vl;
         split_hl(xp[k] - cc[k], vh, vl);
+        if (ic.sg == 0) {
+          sm.xhl[k][li] = vh;
+          sm.xhl[3 + k][li] = vl;
+        }
         x[t][k] = to_local(vh, vl, oh[k], ol[k]);
         blo[k] = fminf(blo[k], x[t][k]);
         bhi[k] = fmaxf(bhi[k], x[t][k]);
@@ -411,7 +558,22 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     blo[k] = warp_min(blo[k]);
     bhi[k] = warp_max(bhi[k]);
   }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      sm.frame[k] = oh[k];
+      sm.frame[3 + k] = ol[k];
+      sm.frame[6 + k] = blo[k];
+      sm.frame[9 + k] = bhi[k];
+    }
+  }
 
+  if (lane == 0) {
+    sm.trg64 = P.trg64;
+    sm.src64 = P.src64;
+    sm.tperm = P.tperm;
+    sm.t0 = it.t0;
+  }
   float ps[T][3];
 #pragma unroll
   for (int t = 0; t < T; ++t)
@@ -423,38 +585,46 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     }
 
   Cursor cur;
-  cur.e = it.seg0 - 1;
-  cur.sid = 0;
+  cur.e0 = it.seg0;
+  cur.kind = KMODE;
   cur.s = cur.end = 0;
-  bool have = cursor_next(P, it, cur);
+  bool have = false;
+  if (it.seg1 > it.seg0) {
+    load_window<KMODE>(P, it, sm, cur, lane);
+    have = cursor_next<KMODE>(P, it, sm, cur, lane);
+  }
   int n_cur = 0, kind_cur = 0;
+  int64_t s_cur = 0;
   if (have) {
     n_cur = (int)min((int64_t)kChunk, cur.end - cur.s);
-    kind_cur = seg_kind(P, cur.sid);
+    kind_cur = cur.kind;
+    s_cur = cur.s;
     issue_chunk(sm, P.rec, cur.s, n_cur, lane);
     cur.s += n_cur;
   }
   bool ok = true;
   while (have) {
-    if (!wait_chunk(sm, phase, P.spin_limit)) {
+    if (!wait_chunk(&sm.mbar, phase, P.spin_limit)) {
       set_error(P.err_flag, 4);
       ok = false;
       // wait (bounded) for the copy in flight before giving up on the item
-      wait_chunk(sm, phase, P.spin_limit);
+      wait_chunk(&sm.mbar, phase, P.spin_limit);
       break;
     }
     phase ^= 1u;
-    const int nfar = convert_chunk(sm, n_cur, oh, ol, blo, bhi, lane);
+    const int nfar = convert_chunk(sm, n_cur, s_cur, lane);
     __syncwarp();
-    const bool have_next = cursor_next(P, it, cur);
+    const bool have_next = cursor_next<KMODE>(P, it, sm, cur, lane);
     int n_next = 0, kind_next = 0;
+    int64_t s_next = 0;
     if (have_next) {
       n_next = (int)min((int64_t)kChunk, cur.end - cur.s);
-      kind_next = seg_kind(P, cur.sid);
+      kind_next = cur.kind;
+      s_next = cur.s;
       issue_chunk(sm, P.rec, cur.s, n_next, lane);
       cur.s += n_next;
     }
-    dispatch_compute<T>(kind_cur, sm, P, ic, n_cur, nfar, x, ps);
+    dispatch_compute<T, KMODE>(kind_cur, sm, P, ic, n_cur, nfar, x, ps);
 #pragma unroll
     for (int t = 0; t < T; ++t)
 #pragma unroll
@@ -469,6 +639,7 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     have = have_next;
     n_cur = n_next;
     kind_cur = kind_next;
+    s_cur = s_next;
   }
   if (!ok) return false;
   float hi[T][3], lo[T][3];
@@ -506,7 +677,8 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
   return true;
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta *kWarp, 4) k_engine_mixed(EngineParams P) {
+template <int KMODE>
+__global__ void __launch_bounds__(kWarpsPerCta *kWarp, STK_ENGINE_MIN_BLOCKS) k_engine_mixed(EngineParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x / kWarp];
   const int lane = threadIdx.x & (kWarp - 1);
@@ -528,42 +700,61 @@ __global__ void __launch_bounds__(kWarpsPerCta *kWarp, 4) k_engine_mixed(EngineP
     const int tn = it.tn_part & 0xFF;
     bool ok;
     if (tn <= 8)
-      ok = run_item<1>(P, it, sm, 4, phase, lane);
+      ok = run_item<1, KMODE>(P, it, sm, 4, phase, lane);
     else if (tn <= 16)
-      ok = run_item<2>(P, it, sm, 4, phase, lane);
+      ok = run_item<2, KMODE>(P, it, sm, 4, phase, lane);
     else if (tn <= 24)
-      ok = run_item<3>(P, it, sm, 4, phase, lane);
+      ok = run_item<3, KMODE>(P, it, sm, 4, phase, lane);
     else if (tn <= 32)
-      ok = run_item<4>(P, it, sm, 4, phase, lane);
+      ok = run_item<4, KMODE>(P, it, sm, 4, phase, lane);
     else if (tn <= 48)
-      ok = run_item<3>(P, it, sm, 2, phase, lane);
+      ok = run_item<3, KMODE>(P, it, sm, 2, phase, lane);
     else if (tn <= 64)
-      ok = run_item<4>(P, it, sm, 2, phase, lane);
+      ok = run_item<4, KMODE>(P, it, sm, 2, phase, lane);
     else if (tn <= 96)
-      ok = run_item<3>(P, it, sm, 1, phase, lane);
+      ok = run_item<3, KMODE>(P, it, sm, 1, phase, lane);
     else
-      ok = run_item<4>(P, it, sm, 1, phase, lane);
+      ok = run_item<4, KMODE>(P, it, sm, 1, phase, lane);
     if (!ok) break;
   }
 }
 
 size_t engine_mixed_smem_bytes() { return sizeof(WarpSmem) * kWarpsPerCta; }
 
+template <int KMODE>
+static cudaError_t launch_kmode(const EngineParams &P, int grid, cudaStream_t stream) {
+  k_engine_mixed<KMODE><<<grid, kWarpsPerCta * kWarp, engine_mixed_smem_bytes(), stream>>>(P);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // The dynamic shared memory (> 48 KB) needs the opt-in attribute on every
 // device; engine_mixed_occupancy() sets it and runs once per device before
 // the first launch there.
 cudaError_t launch_engine_mixed(const EngineParams &P, int grid, cudaStream_t stream) {
-  k_engine_mixed<<<grid, kWarpsPerCta * kWarp, engine_mixed_smem_bytes(), stream>>>(P);
-  return cudaGetLastError();
+  if (P.kind_alternating) return launch_kmode<0>(P, grid, stream);
+  switch (P.kind) {
+    case K_SL: return launch_kmode<K_SL>(P, grid, stream);
+    case K_DL: return launch_kmode<K_DL>(P, grid, stream);
+    default: return launch_kmode<K_SLDL>(P, grid, stream);
+  }
+}
+
+template <int KMODE>
+static cudaError_t set_smem_attr() {
+  return cudaFuncSetAttribute(k_engine_mixed<KMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)engine_mixed_smem_bytes());
 }
 
 cudaError_t engine_mixed_occupancy(int *blocks_per_sm) {
-  const size_t smem = engine_mixed_smem_bytes();
-  cudaError_t e =
-      cudaFuncSetAttribute(k_engine_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_engine_mixed,
-                                                       kWarpsPerCta * kWarp, smem);
+  cudaError_t e;
+  if ((e = set_smem_attr<0>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<K_SL>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<K_DL>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<K_SLDL>()) != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_engine_mixed<K_SLDL>,
+                                                       kWarpsPerCta * kWarp,
+                                                       engine_mixed_smem_bytes());
 }
 
 }  // namespace stk

@@ -34,21 +34,22 @@ __global__ void k_pack_mixed(int64_t ns, const double *__restrict__ src,
     float hhf = (float)fmin(hh, (double)FLT_MAX);
     hhf = fmaxf(hhf, FLT_MIN);  // exactly coincident points always take the FP64 path
     R.yh = make_float4(hx, hy, hz, hhf);
-    R.yl = make_float4(lx, ly, lz, __int_as_float((int)j));
     const double wj = w[j];
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f), nn = q, pp = q;
     if (f)
-      R.q = make_float4((float)(wj * csl * f[3 * j]), (float)(wj * csl * f[3 * j + 1]),
-                        (float)(wj * csl * f[3 * j + 2]), 0.f);
-    else
-      R.q = make_float4(0.f, 0.f, 0.f, 0.f);
+      q = make_float4((float)(wj * csl * f[3 * j]), (float)(wj * csl * f[3 * j + 1]),
+                      (float)(wj * csl * f[3 * j + 2]), 0.f);
     if (phi) {
-      R.n = make_float4((float)nrm[3 * j], (float)nrm[3 * j + 1], (float)nrm[3 * j + 2], 0.f);
-      R.p = make_float4((float)(wj * cdl * phi[3 * j]), (float)(wj * cdl * phi[3 * j + 1]),
-                        (float)(wj * cdl * phi[3 * j + 2]), 0.f);
-    } else {
-      R.n = make_float4(0.f, 0.f, 0.f, 0.f);
-      R.p = R.n;
+      nn = make_float4((float)nrm[3 * j], (float)nrm[3 * j + 1], (float)nrm[3 * j + 2], 0.f);
+      pp = make_float4((float)(wj * cdl * phi[3 * j]), (float)(wj * cdl * phi[3 * j + 1]),
+                       (float)(wj * cdl * phi[3 * j + 2]), 0.f);
     }
+    q.w = lx;
+    nn.w = ly;
+    pp.w = lz;
+    R.q = q;
+    R.n = nn;
+    R.p = pp;
     rec[j] = R;
   }
 }
@@ -279,8 +280,11 @@ int radix_sort(uint64_t *ka, int32_t *va, uint64_t *kb, int32_t *vb, int64_t n, 
     uint64_t *ki = cur ? kb : ka, *ko = cur ? ka : kb;
     int32_t *vi = cur ? vb : va, *vo = cur ? va : vb;
     k_radix_hist<<<nblk, kSortThreads, 0, st>>>(ki, n, shift, nblk, hist);
+    count_launches(1);
     k_scan_excl<<<1, kScanThreads, 0, st>>>(hist, (int64_t)256 * nblk, hist_scan, nullptr);
+    count_launches(1);
     k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(ki, vi, n, shift, nblk, hist_scan, ko, vo);
+    count_launches(1);
     cur ^= 1;
   }
   return cur;
@@ -417,6 +421,10 @@ __global__ void k_zero_ints(int32_t *p, int n) {
 }
 
 // ---------------------------------------------------------------- launchers
+static thread_local int64_t t_launches = 0;
+int64_t launch_count() { return t_launches; }
+void count_launches(int n) { t_launches += n; }
+
 static int grid_for(int64_t n, int threads, int cap = 4096) {
   int64_t g = (n + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -428,12 +436,14 @@ void launch_pack_mixed(int64_t ns, const double *src, const double *f, const dou
                        const double *phi, const double *w, const double *h, double alpha,
                        double csl, double cdl, SrcRec *rec, cudaStream_t st) {
   k_pack_mixed<<<grid_for(ns, 256), 256, 0, st>>>(ns, src, f, nrm, phi, w, h, alpha, csl, cdl, rec);
+  count_launches(1);
 }
 
 void launch_pack_fp64(int64_t ns, const double *src, const double *f, const double *nrm,
                       const double *phi, const double *w, double csl, double cdl, SrcRec64 *rec,
                       cudaStream_t st) {
   k_pack_fp64<<<grid_for(ns, 256), 256, 0, st>>>(ns, src, f, nrm, phi, w, csl, cdl, rec);
+  count_launches(1);
 }
 
 int bbox_partial_blocks(int64_t n) { return grid_for(n, kRedThreads, 1024); }
@@ -441,16 +451,20 @@ int bbox_partial_blocks(int64_t n) { return grid_for(n, kRedThreads, 1024); }
 void launch_bbox(int64_t n, const double *pts, double *partial, double *box, cudaStream_t st) {
   const int nb = bbox_partial_blocks(n);
   k_bbox_partial<<<nb, kRedThreads, 0, st>>>(n, pts, partial);
+  count_launches(1);
   k_bbox_final<<<1, 32, 0, st>>>(nb, partial, box);
+  count_launches(1);
 }
 
 void launch_morton(int64_t n, const double *pts, const double *box, const int64_t *group_ptr,
                    int32_t ngroup, uint64_t *keys, int32_t *vals, cudaStream_t st) {
   k_morton<<<grid_for(n, 256), 256, 0, st>>>(n, pts, box, group_ptr, ngroup, keys, vals);
+  count_launches(1);
 }
 
 void launch_scan(const int32_t *in, int64_t n, int32_t *out, int32_t *total, cudaStream_t st) {
   k_scan_excl<<<1, kScanThreads, 0, st>>>(in, n, out, total);
+  count_launches(1);
 }
 
 void launch_items_direct(int32_t nt, int64_t ns, int32_t nsplit, Item *items, int64_t *range_ptr,
@@ -458,33 +472,42 @@ void launch_items_direct(int32_t nt, int64_t ns, int32_t nsplit, Item *items, in
   const int64_t tot = (int64_t)((nt + kItemMax - 1) / kItemMax) * nsplit;
   const int64_t need = tot > nsplit + 1 ? tot : nsplit + 1;
   k_items_direct<<<grid_for(need, 256), 256, 0, st>>>(nt, ns, nsplit, items, range_ptr, n_items);
+  count_launches(1);
 }
 
 void launch_p2p_items(int32_t nleaf, const int32_t *leaf_ptr, const int32_t *ulist_ptr,
                       const int32_t *ulist_idx, int32_t *cnt, int32_t *offs, int32_t *n_items,
                       Item *items, uint64_t *keys, int32_t *vals, cudaStream_t st) {
   k_p2p_count<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, leaf_ptr, ulist_ptr, ulist_idx, cnt);
+  count_launches(1);
   k_scan_excl<<<1, kScanThreads, 0, st>>>(cnt, nleaf, offs, n_items);
+  count_launches(1);
   k_p2p_emit<<<grid_for(nleaf, 128), 128, 0, st>>>(nleaf, leaf_ptr, ulist_ptr, ulist_idx, offs,
                                                    items, keys, vals);
+  count_launches(1);
 }
 
 void launch_batched_items(int32_t nsusp, const int64_t *susp_ptr, const int64_t *n_cell,
                           int32_t *cnt, int32_t *offs, int32_t *n_items, Item *items,
                           int64_t *range_ptr, uint64_t *keys, int32_t *vals, cudaStream_t st) {
   k_batched_count<<<grid_for(nsusp, 256), 256, 0, st>>>(nsusp, susp_ptr, cnt);
+  count_launches(1);
   k_scan_excl<<<1, kScanThreads, 0, st>>>(cnt, nsusp, offs, n_items);
+  count_launches(1);
   k_batched_emit<<<grid_for(nsusp, 128), 128, 0, st>>>(nsusp, susp_ptr, n_cell, offs, items,
                                                        range_ptr, keys, vals);
+  count_launches(1);
 }
 
 void launch_finish(int64_t nt, int32_t nparts, const double *part_out, const int32_t *tperm,
                    int32_t accumulate, double *out, cudaStream_t st) {
   k_finish<<<grid_for(nt, 256), 256, 0, st>>>(nt, nparts, part_out, tperm, accumulate, out);
+  count_launches(1);
 }
 
 void launch_zero_ints(int32_t *p, int n, cudaStream_t st) {
   k_zero_ints<<<(n + 127) / 128, 128, 0, st>>>(p, n);
+  count_launches(1);
 }
 
 }  // namespace stk
@@ -497,5 +520,6 @@ __global__ void k_widen(int64_t n, const int32_t *__restrict__ in, int64_t *__re
 }
 void launch_widen(int64_t n, const int32_t *in, int64_t *out, cudaStream_t st) {
   k_widen<<<grid_for(n, 256), 256, 0, st>>>(n, in, out);
+  count_launches(1);
 }
 }  // namespace stk

@@ -5,6 +5,10 @@
 
 namespace stk {
 
+// Kernels launched by the calling thread through the library.
+int64_t launch_count();
+void count_launches(int n);
+
 void launch_pack_mixed(int64_t ns, const double *src, const double *f, const double *nrm,
                        const double *phi, const double *w, const double *h, double alpha,
                        double csl, double cdl, SrcRec *rec, cudaStream_t st);

@@ -26,6 +26,7 @@ using namespace stk;
 namespace {
 
 thread_local std::string g_err;
+thread_local cudaEvent_t g_ev_start = nullptr, g_ev_stop = nullptr;
 
 stk_status fail(stk_status s, const char *msg) {
   g_err = msg;
@@ -227,6 +228,7 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   const int64_t need = (p.max_items + kWarpsPerCta - 1) / kWarpsPerCta;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
+  if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_start, st));
   if (p.mixed) {
     P.rec = at<SrcRec>(ws, p.rec);
     CU(launch_engine_mixed(P, (int)grid, st));
@@ -234,6 +236,7 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
     P.rec64 = at<SrcRec64>(ws, p.rec);
     CU(launch_engine_fp64(P, (int)grid, st));
   }
+  if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_stop, st));
   return STK_OK;
 }
 
@@ -317,6 +320,7 @@ stk_status direct_common(int32_t kinds, const double *src, const double *f, cons
   std::memset(&P, 0, sizeof(P));
   P.src64 = src;
   P.trg64 = trg;
+  P.self_index = (trg == src) ? 1 : 0;
   P.tperm = p.sort_targets ? sort_targets(p, ws, trg, nullptr, 0, st) : nullptr;
   launch_items_direct((int32_t)nt, ns, p.nsplit, at<Item>(ws, p.items),
                       at<int64_t>(ws, p.range), at<int32_t>(ws, p.counters), st);
@@ -341,13 +345,21 @@ extern "C" {
 void stokes_default_opts(stk_opts *o) {
   if (!o) return;
   o->precision = STK_MIXED;
-  o->near_ratio = 2.0;
+  o->near_ratio = 1.0;
   o->accumulate = 0;
   o->source_splits = 0;
   o->tile_config = -1;
 }
 
 const char *stokes_last_error(void) { return g_err.c_str(); }
+
+stk_status stokes_set_engine_events(void *start_event, void *stop_event) {
+  g_ev_start = reinterpret_cast<cudaEvent_t>(start_event);
+  g_ev_stop = reinterpret_cast<cudaEvent_t>(stop_event);
+  return STK_OK;
+}
+
+int64_t stokes_launch_count(void) { return stk::launch_count(); }
 
 const char *stokes_version(void) { return "stokesgpu 0.1 (sm_103a)"; }
 
@@ -445,6 +457,7 @@ stk_status stokes_p2p_leaflists(const double *pts, const double *f, const double
   std::memset(&P, 0, sizeof(P));
   P.src64 = pts;
   P.trg64 = pts;
+  P.self_index = 1;
   P.tperm = nullptr;
   P.items = at<Item>(ws, p.items);
   P.item_order = order;
@@ -497,6 +510,7 @@ stk_status stokes_batched_eval(const double *pts, const double *f, const double 
   std::memset(&P, 0, sizeof(P));
   P.src64 = pts;
   P.trg64 = pts;
+  P.self_index = 1;
   P.tperm = p.sort_targets ? sort_targets(p, ws, pts, susp_ptr, nsusp, st) : nullptr;
   int32_t *counters = at<int32_t>(ws, p.counters);
   const int32_t *order = build_sorted_items(p, ws, st, [&](uint64_t *keys, int32_t *vals) {

@@ -59,19 +59,19 @@ def _direct(kind, src, f, nrm, phi, w, trg, mu, h, precision, near_ratio, out, a
     return out
 
 
-def sl(src, f, w, trg=None, mu=1.0, h=None, precision="mixed", near_ratio=2.0, out=None,
+def sl(src, f, w, trg=None, mu=1.0, h=None, precision="mixed", near_ratio=1.0, out=None,
        accumulate=False, source_splits=0):
     return _direct(A.SL, src, f, None, None, w, trg, mu, h, precision, near_ratio, out,
                    accumulate, source_splits)
 
 
-def dl(src, nrm, phi, w, trg=None, h=None, precision="mixed", near_ratio=2.0, out=None,
+def dl(src, nrm, phi, w, trg=None, h=None, precision="mixed", near_ratio=1.0, out=None,
        accumulate=False, source_splits=0):
     return _direct(A.DL, src, None, nrm, phi, w, trg, 1.0, h, precision, near_ratio, out,
                    accumulate, source_splits)
 
 
-def sldl(src, f, nrm, phi, w, trg=None, mu=1.0, h=None, precision="mixed", near_ratio=2.0,
+def sldl(src, f, nrm, phi, w, trg=None, mu=1.0, h=None, precision="mixed", near_ratio=1.0,
          out=None, accumulate=False, source_splits=0):
     return _direct(A.SLDL, src, f, nrm, phi, w, trg, mu, h, precision, near_ratio, out,
                    accumulate, source_splits)
@@ -81,7 +81,7 @@ class P2PPlan:
     """Device-resident U-list structure plus a reusable workspace for repeated calls."""
 
     def __init__(self, n, leaf_ptr, ulist_ptr, ulist_idx, kernels=3, precision="mixed",
-                 near_ratio=2.0, device=None):
+                 near_ratio=1.0, device=None):
         device = device or torch.device("cuda")
         as32 = lambda a: torch.as_tensor(a, dtype=torch.int32).to(device).contiguous()
         self.n = int(n)
@@ -118,7 +118,7 @@ class P2PPlan:
 
 
 def p2p(pts, f, phi, nrm, w, leaf_ptr, ulist_ptr, ulist_idx, kernels=3, mu=1.0, h=None,
-        precision="mixed", near_ratio=2.0, out=None, accumulate=False):
+        precision="mixed", near_ratio=1.0, out=None, accumulate=False):
     plan = P2PPlan(pts.shape[0], leaf_ptr, ulist_ptr, ulist_idx, kernels, precision, near_ratio,
                    pts.device)
     return plan(pts, f, phi, nrm, w, h, mu, out, accumulate)
@@ -127,7 +127,7 @@ def p2p(pts, f, phi, nrm, w, leaf_ptr, ulist_ptr, ulist_idx, kernels=3, mu=1.0, 
 class BatchedPlan:
     """Suspension descriptors on the device plus a reusable workspace."""
 
-    def __init__(self, n, susp_ptr, n_cell, precision="mixed", near_ratio=2.0, device=None):
+    def __init__(self, n, susp_ptr, n_cell, precision="mixed", near_ratio=1.0, device=None):
         device = device or torch.device("cuda")
         as64 = lambda a: torch.as_tensor(a, dtype=torch.int64).to(device).contiguous()
         self.n = int(n)
@@ -162,6 +162,6 @@ class BatchedPlan:
 
 
 def batched(pts, f, phi, nrm, w, susp_ptr, n_cell, mu=1.0, h=None, precision="mixed",
-            near_ratio=2.0, out=None, accumulate=False):
+            near_ratio=1.0, out=None, accumulate=False):
     plan = BatchedPlan(pts.shape[0], susp_ptr, n_cell, precision, near_ratio, pts.device)
     return plan(pts, f, phi, nrm, w, h, mu, out, accumulate)

@@ -63,6 +63,9 @@ struct EngineParams {
   int32_t self_index;        // 1: caller target index == source index means the same point
   double *part_out;          // [nparts][nt][3], sorted target order
   int32_t *item_counter;     // work queue head (zeroed before launch)
+  int32_t *near_cnt;         // [nparts][nt] near pairs recorded per target (zeroed before launch)
+  int32_t *near_idx;         // [nparts][nt][near_cap] source index | kind << 30
+  int32_t near_cap;          // list capacity per target
   int32_t *err_flag;         // device error word
   int64_t spin_limit;        // bounded mbarrier waits, in SM clock cycles
 };
@@ -89,6 +92,47 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p) {
   float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
   hi = s;
   lo = __fadd_rn(lo, err);
+}
+
+// Near pair (|x - y| < alpha h_y): the difference x - y in FP64 from the FP64
+// positions and 1/|r| in FP64 (one Newton step on the FP32 estimate); the
+// kernel products in FP32, written through the unit vector e = d/|r| so that
+// they stay in range however close the pair is:
+//   SL: (q + e (e.q)) / r      DL: e (e.psi)(e.n) / r^2
+// q and psi carry the weight and kernel constant.  Returns false for a pair at
+// zero distance (no contribution).
+__device__ __forceinline__ bool near_contrib(const double *x, const double *y, float4 q,
+                                             float4 n, float4 p, int kind, float (&c)[3]) {
+  const double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  if (!(r2 > 0.0)) return false;
+  double rid;
+  const float r2f = __double2float_rn(r2);
+  if (r2f > 1e-30f && r2f < 1e30f) {
+    const double y0 = (double)rsqrtf(r2f);
+    rid = y0 * (1.5 - 0.5 * r2 * y0 * y0);
+  } else {
+    rid = 1.0 / sqrt(r2);
+  }
+  const float ri = __double2float_rn(rid);
+  const float ex = __double2float_rn(dx * rid), ey = __double2float_rn(dy * rid),
+              ez = __double2float_rn(dz * rid);
+  c[0] = c[1] = c[2] = 0.f;
+  if (kind & K_SL) {
+    const float eq = fmaf(ex, q.x, fmaf(ey, q.y, ez * q.z));
+    c[0] = fmaf(ex, eq, q.x) * ri;
+    c[1] = fmaf(ey, eq, q.y) * ri;
+    c[2] = fmaf(ez, eq, q.z) * ri;
+  }
+  if (kind & K_DL) {
+    const float ep = fmaf(ex, p.x, fmaf(ey, p.y, ez * p.z));
+    const float en = fmaf(ex, n.x, fmaf(ey, n.y, ez * n.z));
+    const float cc = (ep * en) * (ri * ri);
+    c[0] = fmaf(ex, cc, c[0]);
+    c[1] = fmaf(ey, cc, c[1]);
+    c[2] = fmaf(ez, cc, c[2]);
+  }
+  return true;
 }
 
 __device__ __forceinline__ void set_error(int32_t *flag, int code) {

@@ -19,12 +19,11 @@
 //    item extent, not the absolute coordinates.
 //  * Each staged source is classified against the item's bounding box: far
 //    sources (box distance >= alpha h_j) run a branch-free FP32 loop;
-//    candidates run a masked loop that appends pairs with |r| < alpha h_j to
-//    a short per-lane queue.  At the end of the chunk (or when a queue fills)
-//    the warp compacts the queues and evaluates them 32 pairs at a time with
-//    all lanes busy: x - y and 1/|r| in FP64, kernel products in FP32; each
-//    owner then adds its contributions in queue order.  A pair at zero
-//    distance (the self pair in particular) contributes nothing.
+//    candidates run a masked loop in which a pair with |r| < alpha h_j is
+//    left out of the FP32 sum and recorded in its target's near list.  The
+//    near lists are evaluated afterwards by a separate kernel (k_near: FP64
+//    difference and 1/|r|), so no FP64 latency stalls this engine.  A pair
+//    that does not fit its target's list is evaluated in place the same way.
 //  * Accumulation: plain FP32 within a chunk (<= 64 terms per lane), then a
 //    two-sum into per-target (hi, lo) kept in shared memory.
 //  * The kernel is instantiated per kernel kind (SL, DL, SL+DL, or SL/DL by
@@ -42,7 +41,6 @@ namespace stk {
 #define STK_ENGINE_MIN_BLOCKS 3
 #endif
 
-constexpr int kLaneQ = 8;  // near pairs a lane can hold before the warp drains
 constexpr int kSegWin = 64;  // segments read into shared memory at a time  // warp-wide near-pair queue: 31 carried + 128 new entries
 
 struct __align__(16) WarpSmem {
@@ -51,21 +49,12 @@ struct __align__(16) WarpSmem {
   float4 Q[kChunk];            // SL density (scaled) + source index bits
   float4 N[kChunk];            // normal
   float4 Pd[kChunk];           // DL density (scaled)
-  float4 YH[kChunk];           // source (y - c) high parts, .w = source index bits
-  float4 YL[kChunk];           // source (y - c) low parts
-  float xhl[6][kItemMax];      // item targets' (x - c) high and low parts, by target slot
   float acc[2 * 4 * 3][kWarp]; // per-lane compensated sums (hi, lo), lane-minor
-  float contrib[kWarp][3];     // near-pair contributions of one drain round
+  float frame[12];             // item origin (hi x3, lo x3) and bounding box (lo x3, hi x3)
   int32_t run_s[kSegWin];      // source runs of the current segment window: start
   int32_t run_e[kSegWin];      //   end
   int32_t run_k[kSegWin];      //   kernel kind
-  float frame[12];             // item origin (hi x3, lo x3) and bounding box (lo x3, hi x3)
-  const double *trg64;         // item context for the rare FP64-from-memory near path
-  const double *src64;
-  const int32_t *tperm;
-  int32_t t0;
-  uint8_t lq[kWarp][kLaneQ];   // per-lane near pairs: source slot k | target slot t << 6
-  uint16_t cq[kWarp * kLaneQ]; // compacted queue: owner lane << 8 | entry
+  int32_t ncnt[kItemMax];      // near pairs recorded per item target slot
   unsigned long long mbar;
 };
 
@@ -174,129 +163,24 @@ __device__ __forceinline__ void pair_block(const float (&x)[T][3], float (&ps)[T
   }
 }
 
-// One drain round: lane i < ne evaluates compacted entry base + i and leaves
-// its FP32 contribution in sm.contrib[i].  The difference x - y is formed in
-// FP64 from the exact hi/lo splits of both points, (xh - yh) + (xl - yl), and
-// 1/|r| in FP64 by one Newton step on the FP32 estimate; the kernel products
-// are FP32, written through the unit vector e = d/|r| so that they stay in
-// range however close the pair is:
-//   SL: (q + e (e.q)) / r      DL: e (e.psi)(e.n) / r^2
-// A pair whose splits coincide (the self pair in particular) contributes
-// nothing and costs no FP64 work.
-#ifndef STK_DRAIN_INLINE
-#define STK_DRAIN_ATTR __noinline__
-#else
-#define STK_DRAIN_ATTR __forceinline__
-#endif
-template <int KIND>
-__device__ STK_DRAIN_ATTR void drain_round(WarpSmem *sm, int G, int base, int ne, int lane) {
-  float c0 = 0.f, c1 = 0.f, c2 = 0.f;
-  if (lane < ne) {
-    const int e = sm->cq[base + lane];
-    const int owner = e >> 8;
-    const int k = e & 63;
-    const int li = (owner % G) + G * ((e >> 6) & 3);
-    const float4 yh = sm->YH[k], yl = sm->YL[k];
-    const float lx = sm->xhl[3][li] - yl.x, ly = sm->xhl[4][li] - yl.y,
-                lz = sm->xhl[5][li] - yl.z;
-    const float hx = sm->xhl[0][li], hy = sm->xhl[1][li], hz = sm->xhl[2][li];
-    if (hx != yh.x || hy != yh.y || hz != yh.z || lx != 0.f || ly != 0.f || lz != 0.f) {
-      double dx = ((double)hx - (double)yh.x) + (double)lx;
-      double dy = ((double)hy - (double)yh.y) + (double)ly;
-      double dz = ((double)hz - (double)yh.z) + (double)lz;
-      double r2 = dx * dx + dy * dy + dz * dz;
-      // The splits hold about 48 bits of (x - c); a pair closer than 1e-5 |x - c|
-      // takes its difference from the caller's FP64 positions instead.
-      if (r2 < 1e-10 * ((double)hx * hx + (double)hy * hy + (double)hz * hz)) {
-        const int32_t *tperm = sm->tperm;
-        const int ci = tperm ? tperm[sm->t0 + li] : sm->t0 + li;
-        const int j = __float_as_int(yh.w);
-        const double *xt = sm->trg64 + 3 * (size_t)ci, *ys = sm->src64 + 3 * (size_t)j;
-        dx = xt[0] - ys[0];
-        dy = xt[1] - ys[1];
-        dz = xt[2] - ys[2];
-        r2 = dx * dx + dy * dy + dz * dz;
-      }
-      double rid;
-      const float r2f = __double2float_rn(r2);
-      if (r2f > 1e-30f && r2f < 1e30f) {
-        const double y0 = (double)rsqrtf(r2f);
-        rid = y0 * (1.5 - 0.5 * r2 * y0 * y0);  // one FP64 Newton step
-      } else {
-        rid = 1.0 / sqrt(r2);
-      }
-      const float ri = r2 > 0.0 ? __double2float_rn(rid) : 0.f;
-      const float ex = __double2float_rn(dx) * ri, ey = __double2float_rn(dy) * ri,
-                  ez = __double2float_rn(dz) * ri;
-      const float4 Q = sm->Q[k];
-      if (KIND == K_SL) {
-        const float eq = fmaf(ex, Q.x, fmaf(ey, Q.y, ez * Q.z));
-        c0 = fmaf(ex, eq, Q.x) * ri;
-        c1 = fmaf(ey, eq, Q.y) * ri;
-        c2 = fmaf(ez, eq, Q.z) * ri;
-      } else {
-        const float4 N = sm->N[k];
-        const float4 Pd = sm->Pd[k];
-        const float ep = fmaf(ex, Pd.x, fmaf(ey, Pd.y, ez * Pd.z));
-        const float en = fmaf(ex, N.x, fmaf(ey, N.y, ez * N.z));
-        if (KIND == K_DL) {
-          const float cc = (ep * en) * (ri * ri);
-          c0 = ex * cc;
-          c1 = ey * cc;
-          c2 = ez * cc;
-        } else {
-          const float eq = fmaf(ex, Q.x, fmaf(ey, Q.y, ez * Q.z));
-          const float cc = fmaf(ep * en, ri, eq);
-          c0 = fmaf(ex, cc, Q.x) * ri;
-          c1 = fmaf(ey, cc, Q.y) * ri;
-          c2 = fmaf(ez, cc, Q.z) * ri;
-        }
-      }
-    }
-    sm->contrib[lane][0] = c0;
-    sm->contrib[lane][1] = c1;
-    sm->contrib[lane][2] = c2;
-  }
-  __syncwarp();
-}
-
 struct ItemCtx {
-  int lane, b, G, tgl, sg, tn;
+  int lane, b, G, tgl, sg, tn, part;
   int32_t t0;
 };
 
-// Drains every lane's queue: the queues are compacted in lane order, the
-// entries are evaluated 32 at a time, and each owner adds its contributions
-// in the order it queued them.
-template <int T, int KIND>
-__device__ __forceinline__ void drain(WarpSmem &sm, const ItemCtx &ic, int cnt,
-                                      float (&ps)[T][3]) {
-  int incl = cnt;
-#pragma unroll
-  for (int o = 1; o < kWarp; o <<= 1) {
-    const int v = __shfl_up_sync(kFull, incl, o);
-    if (ic.lane >= o) incl += v;
-  }
-  const int total = __shfl_sync(kFull, incl, kWarp - 1);
-  const int excl = incl - cnt;
-  for (int i = 0; i < cnt; ++i) sm.cq[excl + i] = (uint16_t)((ic.lane << 8) | sm.lq[ic.lane][i]);
-  __syncwarp();
-  for (int base = 0; base < total; base += kWarp) {
-    const int ne = min(kWarp, total - base);
-    drain_round<KIND>(&sm, ic.G, base, ne, ic.lane);
-    const int g1 = min(excl + cnt, base + ne);
-    for (int g = max(excl, base); g < g1; ++g) {
-      const int t = (sm.cq[g] >> 6) & 3;
-#pragma unroll
-      for (int tt = 0; tt < T; ++tt)
-        if (tt == t) {
-          ps[tt][0] += sm.contrib[g - base][0];
-          ps[tt][1] += sm.contrib[g - base][1];
-          ps[tt][2] += sm.contrib[g - base][2];
-        }
-    }
-    __syncwarp();
-  }
+// Evaluates in place a near pair that did not fit its target's list.
+template <int KIND>
+__device__ __noinline__ float4 near_overflow(const WarpSmem &sm, const EngineParams &P, int32_t gi,
+                                             int k) {
+  const float4 Q = sm.Q[k];
+  const int j = __float_as_int(Q.w);
+  const int ci = P.tperm ? P.tperm[gi] : gi;
+  float v[3];
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (near_contrib(P.trg64 + 3 * (size_t)ci, P.src64 + 3 * (size_t)j, Q, sm.N[k], sm.Pd[k], KIND,
+                   v))
+    r = make_float4(v[0], v[1], v[2], 0.f);
+  return r;
 }
 
 template <int T, int KIND>
@@ -313,29 +197,34 @@ __device__ __forceinline__ void chunk_compute(WarpSmem &sm, const EngineParams &
     unsigned nm = 0;
     pair_block<T, KIND, false>(x, ps, Y, Q, N, Pd, nm);
   }
-  // candidates: per-pair near test; near pairs go to the lane's queue
-  int cnt = 0;
-  for (int kk = nfar; kk < n; kk += ic.b) {
-    const int k = kk + ic.sg;
-    if (k < n) {
-      const float4 Y = sm.Y[k];
-      const float4 Q = (KIND & K_SL) ? sm.Q[k] : z4;
-      const float4 N = (KIND & K_DL) ? sm.N[k] : z4;
-      const float4 Pd = (KIND & K_DL) ? sm.Pd[k] : z4;
-      unsigned nm = 0;
-      pair_block<T, KIND, true>(x, ps, Y, Q, N, Pd, nm);
-      if (nm) {
+  // candidates: per-pair near test; near pairs are recorded for k_near
+  for (int k = nfar + ic.sg; k < n; k += ic.b) {
+    const float4 Y = sm.Y[k];
+    const float4 Q = sm.Q[k];  // .w carries the source index for near pairs
+    const float4 N = (KIND & K_DL) ? sm.N[k] : z4;
+    const float4 Pd = (KIND & K_DL) ? sm.Pd[k] : z4;
+    unsigned nm = 0;
+    pair_block<T, KIND, true>(x, ps, Y, Q, N, Pd, nm);
+    if (nm) {
+      const int j = __float_as_int(Q.w);
 #pragma unroll
-        for (int t = 0; t < T; ++t)
-          if ((nm >> t) & 1u) sm.lq[ic.lane][cnt++] = (uint8_t)(k | (t << 6));
-      }
-    }
-    if (__any_sync(kFull, cnt > kLaneQ - T)) {
-      drain<T, KIND>(sm, ic, cnt, ps);
-      cnt = 0;
+      for (int t = 0; t < T; ++t)
+        if ((nm >> t) & 1u) {
+          // record the pair in its target's near list (shared-memory count)
+          const int li = ic.tgl + ic.G * t;
+          const int c = atomicAdd(&sm.ncnt[li], 1);
+          const size_t slot = (size_t)ic.part * (size_t)P.nt + (size_t)(ic.t0 + li);
+          if (c < P.near_cap) {
+            P.near_idx[slot * (size_t)P.near_cap + c] = j | (KIND << 30);
+          } else {
+            const float4 v = near_overflow<KIND>(sm, P, ic.t0 + li, k);
+            ps[t][0] += v.x;
+            ps[t][1] += v.y;
+            ps[t][2] += v.z;
+          }
+        }
     }
   }
-  if (__any_sync(kFull, cnt > 0)) drain<T, KIND>(sm, ic, cnt, ps);
 }
 
 // Converts the staged raw chunk to local coordinates, far sources first.
@@ -351,15 +240,15 @@ __device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, int64_t s0, in
     const int k = r * kWarp + lane;
     const bool valid = k < n;
     bool cand = false;
-    float4 Y = make_float4(0.f, 0.f, 0.f, 0.f), q = Y, nn = Y, pp = Y, yh4 = Y, yl4 = Y;
+    float4 Y = make_float4(0.f, 0.f, 0.f, 0.f), q = Y, nn = Y, pp = Y, yl4 = Y;
     if (valid) {
       const float4 yh = sm.raw[k].yh;
       q = sm.raw[k].q;
       nn = sm.raw[k].n;
       pp = sm.raw[k].p;
-      yh4 = make_float4(yh.x, yh.y, yh.z, __int_as_float((int)(s0 + k)));
       yl4 = make_float4(q.w, nn.w, pp.w, 0.f);
-      q.w = nn.w = pp.w = 0.f;
+      q.w = __int_as_float((int)(s0 + k));
+      nn.w = pp.w = 0.f;
       Y.x = to_local(yh.x, yl4.x, oh[0], ol[0]);
       Y.y = to_local(yh.y, yl4.y, oh[1], ol[1]);
       Y.z = to_local(yh.z, yl4.z, oh[2], ol[2]);
@@ -378,8 +267,6 @@ __device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, int64_t s0, in
       sm.Q[dst] = q;
       sm.N[dst] = nn;
       sm.Pd[dst] = pp;
-      sm.YH[dst] = yh4;
-      sm.YL[dst] = yl4;
     }
     nfar += __popc(bf);
     ncand += __popc(bc);
@@ -497,6 +384,7 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
   ic.tn = it.tn_part & 0xFF;
   ic.t0 = it.t0;
   const int part = it.tn_part >> 8;
+  ic.part = part;
 
   const double cx = P.src64[0], cy = P.src64[1], cz = P.src64[2];
   // item origin: centre of the targets' bounding box
@@ -541,10 +429,6 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
       if (valid[t]) {
         float vh, vl;
         split_hl(xp[k] - cc[k], vh, vl);
-        if (ic.sg == 0) {
-          sm.xhl[k][li] = vh;
-          sm.xhl[3 + k][li] = vl;
-        }
         x[t][k] = to_local(vh, vl, oh[k], ol[k]);
         blo[k] = fminf(blo[k], x[t][k]);
         bhi[k] = fmaxf(bhi[k], x[t][k]);
@@ -568,12 +452,6 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     }
   }
 
-  if (lane == 0) {
-    sm.trg64 = P.trg64;
-    sm.src64 = P.src64;
-    sm.tperm = P.tperm;
-    sm.t0 = it.t0;
-  }
   float ps[T][3];
 #pragma unroll
   for (int t = 0; t < T; ++t)
@@ -584,6 +462,8 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
       sm.acc[(T + t) * 3 + k][lane] = 0.f;
     }
 
+  for (int li = lane; li < kItemMax; li += kWarp) sm.ncnt[li] = 0;
+  __syncwarp();
   Cursor cur;
   cur.e0 = it.seg0;
   cur.kind = KMODE;
@@ -642,6 +522,11 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     s_cur = s_next;
   }
   if (!ok) return false;
+  __syncwarp();
+  {
+    int32_t *cnt = P.near_cnt + (size_t)part * (size_t)P.nt + (size_t)it.t0;
+    for (int li = lane; li < ic.tn; li += kWarp) cnt[li] = sm.ncnt[li];
+  }
   float hi[T][3], lo[T][3];
 #pragma unroll
   for (int t = 0; t < T; ++t)

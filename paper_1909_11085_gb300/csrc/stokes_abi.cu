@@ -100,6 +100,8 @@ struct Plan {
   bool sort_items = false;
   int32_t ngroup = 0;
   // offsets (the counters always sit at offset 0 of the aligned workspace)
+  int32_t near_cap = 0;
+  size_t near_cnt = 0, near_idx = 0;
   size_t counters, rec, keys_a, keys_b, vals_a, vals_b, ikeys_a, ikeys_b, ivals_a, ivals_b, hist,
       hist_scan, bbox_part, bbox, items, range, cnt, offs, part, total;
 };
@@ -114,6 +116,13 @@ int auto_splits(int64_t nt, int64_t ns, const DevInfo &di, int occ) {
   if (s > 64) s = 64;
   if (s < 1) s = 1;
   return (int)s;
+}
+
+// Near-list capacity per target: about 12 alpha^2 pairs are expected on a
+// surface sampled at spacing h; lists that overflow are evaluated in place.
+int32_t near_capacity(double alpha) {
+  const double c = 8.0 + std::ceil(12.0 * alpha * alpha);
+  return (int32_t)(c > 128.0 ? 128.0 : c);
 }
 
 void layout(Plan &p) {
@@ -140,6 +149,10 @@ void layout(Plan &p) {
   p.cnt = a.take(sizeof(int32_t) * (size_t)(p.ngroup + 1));
   p.offs = a.take(sizeof(int32_t) * (size_t)(p.ngroup + 2));
   p.part = a.take(sizeof(double) * 3 * (size_t)p.nt * (size_t)p.nsplit);
+  if (p.mixed) {
+    p.near_cnt = a.take(sizeof(int32_t) * (size_t)p.nt * (size_t)p.nsplit);
+    p.near_idx = a.take(sizeof(int32_t) * (size_t)p.nt * (size_t)p.nsplit * (size_t)p.near_cap);
+  }
   p.total = a.off + 256;  // slack for re-alignment of an unaligned base
 }
 
@@ -148,6 +161,7 @@ stk_status plan_direct(int64_t ns, int64_t nt, const stk_opts *o, Plan &p) {
   CU(dev_info(di));
   p.form = F_DIRECT;
   p.mixed = o->precision == STK_MIXED;
+  p.near_cap = near_capacity(o->near_ratio);
   p.ns = ns;
   p.nt = nt;
   const int occ = p.mixed ? di.occ_mixed : di.occ_fp64;
@@ -166,6 +180,7 @@ stk_status plan_direct(int64_t ns, int64_t nt, const stk_opts *o, Plan &p) {
 stk_status plan_p2p(int64_t n, int32_t nleaf, const stk_opts *o, Plan &p) {
   p.form = F_P2P;
   p.mixed = o->precision == STK_MIXED;
+  p.near_cap = near_capacity(o->near_ratio);
   p.ns = p.nt = n;
   p.nsplit = 1;
   p.max_items = (int64_t)nleaf + n / kItemMax + 1;
@@ -180,6 +195,7 @@ stk_status plan_p2p(int64_t n, int32_t nleaf, const stk_opts *o, Plan &p) {
 stk_status plan_batched(int64_t n, int32_t nsusp, const stk_opts *o, Plan &p) {
   p.form = F_BATCHED;
   p.mixed = o->precision == STK_MIXED;
+  p.near_cap = near_capacity(o->near_ratio);
   p.ns = p.nt = n;
   p.nsplit = 1;
   p.max_items = (int64_t)nsusp + n / kItemMax + 1;
@@ -190,6 +206,8 @@ stk_status plan_batched(int64_t n, int32_t nsusp, const stk_opts *o, Plan &p) {
   layout(p);
   return STK_OK;
 }
+
+constexpr int64_t kMaxMixed = (int64_t)1 << 30;
 
 stk_status check_opts(const stk_opts *o) {
   if (!o) return fail(STK_EINVAL, "opts is NULL");
@@ -228,6 +246,11 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   const int64_t need = (p.max_items + kWarpsPerCta - 1) / kWarpsPerCta;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
+  if (p.mixed) {
+    P.near_cnt = at<int32_t>(ws, p.near_cnt);
+    P.near_idx = at<int32_t>(ws, p.near_idx);
+    P.near_cap = p.near_cap;  // every item writes the counts of its own targets
+  }
   if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_start, st));
   if (p.mixed) {
     P.rec = at<SrcRec>(ws, p.rec);
@@ -237,6 +260,11 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
     CU(launch_engine_fp64(P, (int)grid, st));
   }
   if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_stop, st));
+  if (p.mixed) {
+    launch_near(p.nt, p.nsplit, P.near_cnt, P.near_idx, P.near_cap, P.rec, P.src64, P.trg64,
+                P.tperm, P.part_out, st);
+    CU(cudaGetLastError());
+  }
   return STK_OK;
 }
 
@@ -293,6 +321,8 @@ stk_status direct_common(int32_t kinds, const double *src, const double *f, cons
   if (s != STK_OK) return s;
   if (ns < 0 || nt < 0 || ns > kMaxN || nt > kMaxN)
     return fail(STK_EINVAL, "ns and nt must be in [0, 2^31-1]");
+  if (o->precision == STK_MIXED && ns >= kMaxMixed)
+    return fail(STK_EUNSUPPORTED, "the mixed form supports fewer than 2^30 sources");
   if (nt > 0 && (!trg || !out)) return fail(STK_EINVAL, "trg/out is NULL");
   if (ns > 0 && nt > 0) {
     if (!src || !w) return fail(STK_EINVAL, "src/w is NULL");
@@ -426,6 +456,8 @@ stk_status stokes_p2p_leaflists(const double *pts, const double *f, const double
   if (s != STK_OK) return s;
   if (n < 0 || n > kMaxN || nleaf < 0 || nulist < 0 || nulist > kMaxN)
     return fail(STK_EINVAL, "bad sizes");
+  if (opts->precision == STK_MIXED && n >= kMaxMixed)
+    return fail(STK_EUNSUPPORTED, "the mixed form supports fewer than 2^30 points");
   if (kernels < 1 || kernels > 3) return fail(STK_EINVAL, "kernels must be 1, 2 or 3");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (n == 0) return STK_OK;
@@ -493,6 +525,8 @@ stk_status stokes_batched_eval(const double *pts, const double *f, const double 
   stk_status s = check_opts(opts);
   if (s != STK_OK) return s;
   if (n < 0 || n > kMaxN || nsusp < 0 || nsusp > (1 << 24)) return fail(STK_EINVAL, "bad sizes");
+  if (opts->precision == STK_MIXED && n >= kMaxMixed)
+    return fail(STK_EUNSUPPORTED, "the mixed form supports fewer than 2^30 points");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (n == 0 || nsusp == 0) return STK_OK;
   if (!pts || !f || !phi || !nrm || !w || !out || !susp_ptr || !n_cell)

@@ -63,9 +63,10 @@ struct EngineParams {
   int32_t self_index;        // 1: caller target index == source index means the same point
   double *part_out;          // [nparts][nt][3], sorted target order
   int32_t *item_counter;     // work queue head (zeroed before launch)
-  int32_t *near_cnt;         // [nparts][nt] near pairs recorded per target (zeroed before launch)
-  int32_t *near_idx;         // [nparts][nt][near_cap] source index | kind << 30
-  int32_t near_cap;          // list capacity per target
+  int32_t *near_cnt;         // [nparts][nt][4] fill of each near sub-list
+  int32_t *near_idx;         // [nparts][nt][4][near_sub] source index | kind << 30
+  int32_t near_sub;          // capacity of one sub-list (a power of two)
+  int32_t near_sub_log2;
   int32_t *err_flag;         // device error word
   int64_t spin_limit;        // bounded mbarrier waits, in SM clock cycles
 };

@@ -20,7 +20,8 @@
 //  * Each staged source is classified against the item's bounding box: far
 //    sources (box distance >= alpha h_j) run a branch-free FP32 loop;
 //    candidates run a masked loop in which a pair with |r| < alpha h_j is
-//    left out of the FP32 sum and recorded in its target's near list.  The
+//    left out of the FP32 sum and recorded in its target's near list (four
+//    sub-lists, each written by one lane in program order, so no atomics).  The
 //    near lists are evaluated afterwards by a separate kernel (k_near: FP64
 //    difference and 1/|r|), so no FP64 latency stalls this engine.  A pair
 //    that does not fit its target's list is evaluated in place the same way.
@@ -54,7 +55,6 @@ struct __align__(16) WarpSmem {
   int32_t run_s[kSegWin];      // source runs of the current segment window: start
   int32_t run_e[kSegWin];      //   end
   int32_t run_k[kSegWin];      //   kernel kind
-  int32_t ncnt[kItemMax];      // near pairs recorded per item target slot
   unsigned long long mbar;
 };
 
@@ -186,7 +186,8 @@ __device__ __noinline__ float4 near_overflow(const WarpSmem &sm, const EnginePar
 template <int T, int KIND>
 __device__ __forceinline__ void chunk_compute(WarpSmem &sm, const EngineParams &P,
                                               const ItemCtx &ic, int n, int nfar,
-                                              const float (&x)[T][3], float (&ps)[T][3]) {
+                                              const float (&x)[T][3], float (&ps)[T][3],
+                                              int (&ncnt)[T]) {
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   // far sources: no per-pair test
   for (int k = ic.sg; k < nfar; k += ic.b) {
@@ -210,12 +211,15 @@ __device__ __forceinline__ void chunk_compute(WarpSmem &sm, const EngineParams &
 #pragma unroll
       for (int t = 0; t < T; ++t)
         if ((nm >> t) & 1u) {
-          // record the pair in its target's near list (shared-memory count)
+          // Record the pair in this lane's sub-lists of the target's near list:
+          // sub-lists sg, sg + b, ... < 4, each near_sub entries, filled in order.
+          const int c = ncnt[t]++;
+          const int sub = ic.sg + ic.b * (c >> P.near_sub_log2);
           const int li = ic.tgl + ic.G * t;
-          const int c = atomicAdd(&sm.ncnt[li], 1);
-          const size_t slot = (size_t)ic.part * (size_t)P.nt + (size_t)(ic.t0 + li);
-          if (c < P.near_cap) {
-            P.near_idx[slot * (size_t)P.near_cap + c] = j | (KIND << 30);
+          if (sub < 4) {
+            const size_t slot = (size_t)ic.part * (size_t)P.nt + (size_t)(ic.t0 + li);
+            P.near_idx[((slot * 4 + sub) << P.near_sub_log2) + (c & (P.near_sub - 1))] =
+                j | (KIND << 30);
           } else {
             const float4 v = near_overflow<KIND>(sm, P, ic.t0 + li, k);
             ps[t][0] += v.x;
@@ -361,13 +365,14 @@ __device__ __forceinline__ bool cursor_next(const EngineParams &P, const Item &i
 template <int T, int KMODE>
 __device__ __forceinline__ void dispatch_compute(int kind, WarpSmem &sm, const EngineParams &P,
                                                  const ItemCtx &ic, int n, int nfar,
-                                                 const float (&x)[T][3], float (&ps)[T][3]) {
+                                                 const float (&x)[T][3], float (&ps)[T][3],
+                                                 int (&ncnt)[T]) {
   if (KMODE != 0) {
-    chunk_compute<T, KMODE>(sm, P, ic, n, nfar, x, ps);
+    chunk_compute<T, KMODE>(sm, P, ic, n, nfar, x, ps, ncnt);
   } else if (kind == K_SL) {
-    chunk_compute<T, K_SL>(sm, P, ic, n, nfar, x, ps);
+    chunk_compute<T, K_SL>(sm, P, ic, n, nfar, x, ps, ncnt);
   } else {
-    chunk_compute<T, K_DL>(sm, P, ic, n, nfar, x, ps);
+    chunk_compute<T, K_DL>(sm, P, ic, n, nfar, x, ps, ncnt);
   }
 }
 
@@ -462,8 +467,9 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
       sm.acc[(T + t) * 3 + k][lane] = 0.f;
     }
 
-  for (int li = lane; li < kItemMax; li += kWarp) sm.ncnt[li] = 0;
-  __syncwarp();
+  int ncnt[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) ncnt[t] = 0;
   Cursor cur;
   cur.e0 = it.seg0;
   cur.kind = KMODE;
@@ -504,7 +510,7 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
       issue_chunk(sm, P.rec, cur.s, n_next, lane);
       cur.s += n_next;
     }
-    dispatch_compute<T, KMODE>(kind_cur, sm, P, ic, n_cur, nfar, x, ps);
+    dispatch_compute<T, KMODE>(kind_cur, sm, P, ic, n_cur, nfar, x, ps, ncnt);
 #pragma unroll
     for (int t = 0; t < T; ++t)
 #pragma unroll
@@ -522,10 +528,15 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     s_cur = s_next;
   }
   if (!ok) return false;
-  __syncwarp();
-  {
-    int32_t *cnt = P.near_cnt + (size_t)part * (size_t)P.nt + (size_t)it.t0;
-    for (int li = lane; li < ic.tn; li += kWarp) cnt[li] = sm.ncnt[li];
+  // near-list counts: each lane writes the fill of the sub-lists it owns
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    if (valid[t]) {
+      const int li = ic.tgl + ic.G * t;
+      int32_t *cnt = P.near_cnt + ((size_t)part * (size_t)P.nt + (size_t)(it.t0 + li)) * 4;
+      for (int sub = ic.sg, i = 0; sub < 4; sub += ic.b, ++i)
+        cnt[sub] = min(P.near_sub, max(0, ncnt[t] - i * P.near_sub));
+    }
   }
   float hi[T][3], lo[T][3];
 #pragma unroll

@@ -399,44 +399,39 @@ __global__ void k_batched_emit(int32_t nsusp, const int64_t *__restrict__ susp_p
 
 // ---------------------------------------------------------------- near pairs
 // Evaluates the near lists recorded by the mixed engine: one thread per
-// (part, target).  Entries are first put in ascending order of
-// (kind, source index), so the sum does not depend on the order in which the
-// engine's lanes recorded them.  The FP64 difference x - y and 1/|r| and the
-// FP32 products are those of near_contrib(); the contributions are summed in
-// FP64 and added to the target's partial result.
+// (part, target).  A target's list is four sub-lists, each filled in program
+// order by one engine lane; they are read in sub-list order, so the sum is
+// deterministic.  The FP64 difference x - y and 1/|r| and the FP32 products
+// are those of near_contrib(); the contributions are summed in FP64 and added
+// to the target's partial result.
 __global__ void k_near(int64_t nt, int32_t nparts, const int32_t *__restrict__ near_cnt,
-                       int32_t *__restrict__ near_idx, int32_t cap, const SrcRec *__restrict__ rec,
-                       const double *__restrict__ src64, const double *__restrict__ trg64,
-                       const int32_t *__restrict__ tperm, double *__restrict__ part_out) {
+                       const int32_t *__restrict__ near_idx, int32_t sub_cap,
+                       const SrcRec *__restrict__ rec, const double *__restrict__ src64,
+                       const double *__restrict__ trg64, const int32_t *__restrict__ tperm,
+                       double *__restrict__ part_out) {
   const int64_t tot = nt * nparts;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = min(near_cnt[i], cap);
-    if (c <= 0) continue;
-    int32_t *lst = near_idx + i * (int64_t)cap;
-    for (int a = 1; a < c; ++a) {  // insertion sort of the short list
-      const int32_t v = lst[a];
-      int b = a - 1;
-      while (b >= 0 && (uint32_t)lst[b] > (uint32_t)v) {
-        lst[b + 1] = lst[b];
-        --b;
-      }
-      lst[b + 1] = v;
-    }
+    const int4 cnt = reinterpret_cast<const int4 *>(near_cnt)[i];
+    if ((cnt.x | cnt.y | cnt.z | cnt.w) == 0) continue;
     const int64_t ti = i % nt;
     const int64_t ci = tperm ? tperm[ti] : ti;
     const double *x = trg64 + 3 * ci;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int a = 0; a < c; ++a) {
-      const uint32_t e = (uint32_t)lst[a];
-      const int kind = (int)(e >> 30);
-      const int64_t j = e & 0x3fffffffu;
-      const SrcRec R = rec[j];
-      float v[3];
-      if (near_contrib(x, src64 + 3 * j, R.q, R.n, R.p, kind, v)) {
-        s0 += v[0];
-        s1 += v[1];
-        s2 += v[2];
+    const int cs[4] = {cnt.x, cnt.y, cnt.z, cnt.w};
+    for (int sub = 0; sub < 4; ++sub) {
+      const int32_t *lst = near_idx + (i * 4 + sub) * (int64_t)sub_cap;
+      for (int a = 0; a < cs[sub]; ++a) {
+        const uint32_t e = (uint32_t)lst[a];
+        const int kind = (int)(e >> 30);
+        const int64_t j = e & 0x3fffffffu;
+        const SrcRec R = rec[j];
+        float v[3];
+        if (near_contrib(x, src64 + 3 * j, R.q, R.n, R.p, kind, v)) {
+          s0 += v[0];
+          s1 += v[1];
+          s2 += v[2];
+        }
       }
     }
     double *o = part_out + 3 * i;
@@ -548,11 +543,12 @@ void launch_batched_items(int32_t nsusp, const int64_t *susp_ptr, const int64_t 
   count_launches(1);
 }
 
-void launch_near(int64_t nt, int32_t nparts, const int32_t *near_cnt, int32_t *near_idx,
-                 int32_t cap, const SrcRec *rec, const double *src64, const double *trg64,
+void launch_near(int64_t nt, int32_t nparts, const int32_t *near_cnt, const int32_t *near_idx,
+                 int32_t sub_cap, const SrcRec *rec, const double *src64, const double *trg64,
                  const int32_t *tperm, double *part_out, cudaStream_t st) {
-  k_near<<<grid_for(nt * nparts, 128, 1 << 16), 128, 0, st>>>(nt, nparts, near_cnt, near_idx, cap,
-                                                             rec, src64, trg64, tperm, part_out);
+  k_near<<<grid_for(nt * nparts, 128, 1 << 16), 128, 0, st>>>(nt, nparts, near_cnt, near_idx,
+                                                             sub_cap, rec, src64, trg64, tperm,
+                                                             part_out);
   count_launches(1);
 }
 

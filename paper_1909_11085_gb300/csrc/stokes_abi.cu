@@ -100,7 +100,7 @@ struct Plan {
   bool sort_items = false;
   int32_t ngroup = 0;
   // offsets (the counters always sit at offset 0 of the aligned workspace)
-  int32_t near_cap = 0;
+  int32_t near_cap = 0;  // entries per near sub-list
   size_t near_cnt = 0, near_idx = 0;
   size_t counters, rec, keys_a, keys_b, vals_a, vals_b, ikeys_a, ikeys_b, ivals_a, ivals_b, hist,
       hist_scan, bbox_part, bbox, items, range, cnt, offs, part, total;
@@ -118,11 +118,14 @@ int auto_splits(int64_t nt, int64_t ns, const DevInfo &di, int occ) {
   return (int)s;
 }
 
-// Near-list capacity per target: about 12 alpha^2 pairs are expected on a
-// surface sampled at spacing h; lists that overflow are evaluated in place.
-int32_t near_capacity(double alpha) {
-  const double c = 8.0 + std::ceil(12.0 * alpha * alpha);
-  return (int32_t)(c > 128.0 ? 128.0 : c);
+// Near-list capacity per target (four sub-lists of this many entries): about
+// 12 alpha^2 pairs are expected on a surface sampled at spacing h; pairs that
+// do not fit are evaluated in place by the engine.
+int32_t near_sub_capacity(double alpha) {
+  const double c = std::ceil((8.0 + 12.0 * alpha * alpha) / 4.0);
+  int32_t p2 = 2;
+  while (p2 < c && p2 < 32) p2 *= 2;
+  return p2;
 }
 
 void layout(Plan &p) {
@@ -150,8 +153,9 @@ void layout(Plan &p) {
   p.offs = a.take(sizeof(int32_t) * (size_t)(p.ngroup + 2));
   p.part = a.take(sizeof(double) * 3 * (size_t)p.nt * (size_t)p.nsplit);
   if (p.mixed) {
-    p.near_cnt = a.take(sizeof(int32_t) * (size_t)p.nt * (size_t)p.nsplit);
-    p.near_idx = a.take(sizeof(int32_t) * (size_t)p.nt * (size_t)p.nsplit * (size_t)p.near_cap);
+    p.near_cnt = a.take(sizeof(int32_t) * 4 * (size_t)p.nt * (size_t)p.nsplit);
+    p.near_idx =
+        a.take(sizeof(int32_t) * 4 * (size_t)p.nt * (size_t)p.nsplit * (size_t)p.near_cap);
   }
   p.total = a.off + 256;  // slack for re-alignment of an unaligned base
 }
@@ -161,7 +165,7 @@ stk_status plan_direct(int64_t ns, int64_t nt, const stk_opts *o, Plan &p) {
   CU(dev_info(di));
   p.form = F_DIRECT;
   p.mixed = o->precision == STK_MIXED;
-  p.near_cap = near_capacity(o->near_ratio);
+  p.near_cap = near_sub_capacity(o->near_ratio);
   p.ns = ns;
   p.nt = nt;
   const int occ = p.mixed ? di.occ_mixed : di.occ_fp64;
@@ -180,7 +184,7 @@ stk_status plan_direct(int64_t ns, int64_t nt, const stk_opts *o, Plan &p) {
 stk_status plan_p2p(int64_t n, int32_t nleaf, const stk_opts *o, Plan &p) {
   p.form = F_P2P;
   p.mixed = o->precision == STK_MIXED;
-  p.near_cap = near_capacity(o->near_ratio);
+  p.near_cap = near_sub_capacity(o->near_ratio);
   p.ns = p.nt = n;
   p.nsplit = 1;
   p.max_items = (int64_t)nleaf + n / kItemMax + 1;
@@ -195,7 +199,7 @@ stk_status plan_p2p(int64_t n, int32_t nleaf, const stk_opts *o, Plan &p) {
 stk_status plan_batched(int64_t n, int32_t nsusp, const stk_opts *o, Plan &p) {
   p.form = F_BATCHED;
   p.mixed = o->precision == STK_MIXED;
-  p.near_cap = near_capacity(o->near_ratio);
+  p.near_cap = near_sub_capacity(o->near_ratio);
   p.ns = p.nt = n;
   p.nsplit = 1;
   p.max_items = (int64_t)nsusp + n / kItemMax + 1;
@@ -249,7 +253,9 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   if (p.mixed) {
     P.near_cnt = at<int32_t>(ws, p.near_cnt);
     P.near_idx = at<int32_t>(ws, p.near_idx);
-    P.near_cap = p.near_cap;  // every item writes the counts of its own targets
+    P.near_sub = p.near_cap;  // every item writes the counts of its own targets
+    P.near_sub_log2 = 0;
+    while ((1 << P.near_sub_log2) < P.near_sub) ++P.near_sub_log2;
   }
   if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_start, st));
   if (p.mixed) {
@@ -261,7 +267,7 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   }
   if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_stop, st));
   if (p.mixed) {
-    launch_near(p.nt, p.nsplit, P.near_cnt, P.near_idx, P.near_cap, P.rec, P.src64, P.trg64,
+    launch_near(p.nt, p.nsplit, P.near_cnt, P.near_idx, P.near_sub, P.rec, P.src64, P.trg64,
                 P.tperm, P.part_out, st);
     CU(cudaGetLastError());
   }

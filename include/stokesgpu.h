@@ -130,6 +130,24 @@ stk_status stokes_batched_eval(const double *pts, const double *f, const double 
 stk_status stokes_batched_workspace_size(int64_t n, int32_t nsusp, const stk_opts *opts,
                                          size_t *bytes);
 
+/* ------------------------------------------------- no-allocation variant
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory when they need a velocity (an application
+ * that owns every device allocation and hands out no scratch, a real-time
+ * pipeline that forbids cudaMalloc after start-up because it can synchronise
+ * the device, a process under a fixed memory budget).
+ * Same single-layer sum and arguments as stokes_sl_eval, without a workspace:
+ * the library uses a fixed 32 MiB device buffer of its own, held by every GPU
+ * that loads the library until the process exits.  ns and nt may not exceed
+ * 65536 (STK_EUNSUPPORTED otherwise); source splits are reduced if needed to
+ * fit the buffer.  Allocates nothing.  The first call on a device looks up the
+ * buffer's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the buffer: calls whose kernels
+ * may overlap on the GPU race and must be serialised by the caller. */
+stk_status stokes_sl_eval_noalloc(const double *src, const double *f, const double *w,
+                                  const double *h, int64_t ns, const double *trg, int64_t nt,
+                                  double mu, double *out, const stk_opts *opts, void *stream);
+
 /* ----------------------------------------------------------------- status */
 /* Reads the device error word kept in a workspace used by an earlier call.
  * The caller must have synchronised the stream.  Returns STK_OK or

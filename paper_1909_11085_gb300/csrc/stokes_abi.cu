@@ -376,6 +376,12 @@ stk_status direct_common(int32_t kinds, const double *src, const double *f, cons
 
 }  // namespace
 
+namespace stk {
+// Records `msg` as the calling thread's last error and returns `s` (used by
+// the other translation units of the library).
+stk_status report_error(stk_status s, const char *msg) { return fail(s, msg); }
+}  // namespace stk
+
 extern "C" {
 
 void stokes_default_opts(stk_opts *o) {

@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(L):
 def test_default_opts(L):
     o = A.StkOpts()
     L.stokes_default_opts(ctypes.byref(o))
-    assert o.precision == A.STK_MIXED and o.near_ratio == 2.0 and o.accumulate == 0
+    assert o.precision == A.STK_MIXED and o.near_ratio == 1.0 and o.accumulate == 0
 
 
 def test_invalid_arguments_rejected_on_host(L):

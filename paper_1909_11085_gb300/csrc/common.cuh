@@ -104,20 +104,29 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p) {
 // zero distance (no contribution).
 __device__ __forceinline__ bool near_contrib(const double *x, const double *y, float4 q,
                                              float4 n, float4 p, int kind, float (&c)[3]) {
+  // The FP64 and conversion instructions below run on GB300's FP64 pipe (1/64
+  // of the FP32 rate), so there are as few as the FP64 difference and 1/|r|
+  // allow: 3 DADD, 3 + 2 conversions, 3 for r^2, 4 for the Newton step.
   const double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+  const float fx = __double2float_rn(dx), fy = __double2float_rn(dy), fz = __double2float_rn(dz);
+  if (fx == 0.f && fy == 0.f && fz == 0.f) return false;  // coincident (to 1e-45)
+  const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
   const double r2 = dx * dx + dy * dy + dz * dz;
-  if (!(r2 > 0.0)) return false;
   double rid;
-  const float r2f = __double2float_rn(r2);
   if (r2f > 1e-30f && r2f < 1e30f) {
     const double y0 = (double)rsqrtf(r2f);
-    rid = y0 * (1.5 - 0.5 * r2 * y0 * y0);
+    rid = y0 * fma(-0.5 * r2, y0 * y0, 1.5);  // one FP64 Newton step
   } else {
     rid = 1.0 / sqrt(r2);
   }
   const float ri = __double2float_rn(rid);
-  const float ex = __double2float_rn(dx * rid), ey = __double2float_rn(dy * rid),
-              ez = __double2float_rn(dz * rid);
+  // unit vector in FP32; below r2 ~ 1e-30 the FP64 product avoids underflow
+  float ex = fx * ri, ey = fy * ri, ez = fz * ri;
+  if (!(r2f > 1e-30f)) {
+    ex = __double2float_rn(dx * rid);
+    ey = __double2float_rn(dy * rid);
+    ez = __double2float_rn(dz * rid);
+  }
   c[0] = c[1] = c[2] = 0.f;
   if (kind & K_SL) {
     const float eq = fmaf(ex, q.x, fmaf(ey, q.y, ez * q.z));

@@ -21,10 +21,12 @@
 //    sources (box distance >= alpha h_j) run a branch-free FP32 loop;
 //    candidates run a masked loop in which a pair with |r| < alpha h_j is
 //    left out of the FP32 sum and recorded in its target's near list (four
-//    sub-lists, each written by one lane in program order, so no atomics).  The
-//    near lists are evaluated afterwards by a separate kernel (k_near: FP64
-//    difference and 1/|r|), so no FP64 latency stalls this engine.  A pair
-//    that does not fit its target's list is evaluated in place the same way.
+//    sub-lists, each written by one lane in program order, so no atomics).
+//    The lists are evaluated afterwards by k_near (FP64 difference and 1/|r|,
+//    FP32 products), whose FP64 work would otherwise stall this FP32 engine.
+//    A pair that does not fit its target's list is evaluated in place the
+//    same way.  The self pair is recorded like any other and contributes
+//    nothing (zero distance).
 //  * Accumulation: plain FP32 within a chunk (<= 64 terms per lane), then a
 //    two-sum into per-target (hi, lo) kept in shared memory.
 //  * The kernel is instantiated per kernel kind (SL, DL, SL+DL, or SL/DL by
@@ -528,7 +530,7 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     s_cur = s_next;
   }
   if (!ok) return false;
-  // near-list counts: each lane writes the fill of the sub-lists it owns
+  // near-list fill: each lane writes the counts of the sub-lists it owns
 #pragma unroll
   for (int t = 0; t < T; ++t) {
     if (valid[t]) {

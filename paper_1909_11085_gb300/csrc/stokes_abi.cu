@@ -251,9 +251,9 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   if (p.mixed) {
-    P.near_cnt = at<int32_t>(ws, p.near_cnt);
+    P.near_cnt = at<int32_t>(ws, p.near_cnt);  // every item writes its targets' counts
     P.near_idx = at<int32_t>(ws, p.near_idx);
-    P.near_sub = p.near_cap;  // every item writes the counts of its own targets
+    P.near_sub = p.near_cap;
     P.near_sub_log2 = 0;
     while ((1 << P.near_sub_log2) < P.near_sub) ++P.near_sub_log2;
   }
@@ -267,8 +267,8 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   }
   if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_stop, st));
   if (p.mixed) {
-    launch_near(p.nt, p.nsplit, P.near_cnt, P.near_idx, P.near_sub, P.rec, P.src64, P.trg64,
-                P.tperm, P.part_out, st);
+    launch_near(p.nt, p.nsplit, P.near_cnt, P.near_idx, P.near_sub_log2, P.rec, P.src64, P.trg64,
+                P.tperm, P.part_out, di.sms, st);
     CU(cudaGetLastError());
   }
   return STK_OK;

@@ -130,6 +130,28 @@ stk_status stokes_batched_eval(const double *pts, const double *f, const double 
 stk_status stokes_batched_workspace_size(int64_t n, int32_t nsusp, const stk_opts *opts,
                                          size_t *bytes);
 
+/* ----------------------------------------------------------------- adjoint
+ * Gradients of L = sum_i g_i . u(x_i) with u = SL[f] + DL[phi] over one
+ * source set (the kernels of Eq. "sl_stokes" and Sec. 2.1, differentiated
+ * pair by pair; nothing O(ns nt) is stored, the pair terms are recomputed):
+ *   grad_f [ns][3] = dL/df,  grad_phi [ns][3] = dL/dphi,
+ *   grad_y [ns][3] = dL/d(source positions),  grad_n [ns][3] = dL/d(normals, as given),
+ *   grad_x [nt][3] = dL/d(target positions).
+ * g [nt][3] is the upstream gradient.  f or phi may be NULL (SL or DL only);
+ * any output may be NULL to skip it.  Weights and spacings are constants.
+ * When the targets are the sources, the caller adds grad_x to grad_y.
+ * MIXED: FP32 pair terms in per-CTA local frames with two-sum accumulation;
+ * pairs with |r| < near_ratio * h_j are evaluated in FP64.  FP64: all double.
+ */
+stk_status stokes_sldl_grad(const double *src, const double *f, const double *nrm,
+                            const double *phi, const double *w, const double *h, int64_t ns,
+                            const double *trg, int64_t nt, const double *g, double mu,
+                            double *grad_f, double *grad_phi, double *grad_y, double *grad_n,
+                            double *grad_x, const stk_opts *opts, void *workspace,
+                            size_t workspace_bytes, void *stream);
+stk_status stokes_grad_workspace_size(int64_t ns, int64_t nt, const stk_opts *opts,
+                                      size_t *bytes);
+
 /* ------------------------------------------------- no-allocation variant
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory when they need a velocity (an application

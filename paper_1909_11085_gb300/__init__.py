@@ -6,6 +6,8 @@ The compute path is libstokesgpu.so (hand-written CUDA for sm_103a); this
 package only marshals PyTorch tensors into it.  Build the library with
 paper_1909_11085_gb300.build.build().
 """
-from .ops import sl, dl, sldl, p2p, batched, P2PPlan, BatchedPlan  # noqa: F401
+from .ops import (sl, dl, sldl, p2p, batched, sldl_grad, StokesLayerFn,  # noqa: F401
+                  P2PPlan, BatchedPlan)
 
-__all__ = ["sl", "dl", "sldl", "p2p", "batched", "P2PPlan", "BatchedPlan"]
+__all__ = ["sl", "dl", "sldl", "p2p", "batched", "sldl_grad", "StokesLayerFn", "P2PPlan",
+           "BatchedPlan"]

@@ -26,7 +26,7 @@ EXPORTS = [
     "stokes_direct_workspace_size", "stokes_p2p_leaflists", "stokes_p2p_workspace_size",
     "stokes_batched_eval", "stokes_batched_workspace_size", "stokes_device_status",
     "stokes_last_error", "stokes_version", "stokes_set_engine_events", "stokes_launch_count",
-    "stokes_sl_eval_noalloc",
+    "stokes_sl_eval_noalloc", "stokes_sldl_grad", "stokes_grad_workspace_size",
 ]
 
 
@@ -74,6 +74,9 @@ def lib():
             L.stokes_device_status.argtypes = [p, sz]
             L.stokes_set_engine_events.argtypes = [p, p]
             L.stokes_sl_eval_noalloc.argtypes = [p, p, p, p, i64, p, i64, d, p, po, p]
+            L.stokes_sldl_grad.argtypes = [p, p, p, p, p, p, i64, p, i64, p, d, p, p, p, p, p, po,
+                                           p, sz, p]
+            L.stokes_grad_workspace_size.argtypes = [i64, i64, po, psz]
             L.stokes_launch_count.restype = ctypes.c_int64
             for name in EXPORTS:
                 fn = getattr(L, name)

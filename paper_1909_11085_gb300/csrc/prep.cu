@@ -17,8 +17,8 @@ __global__ void k_pack_mixed(int64_t ns, const double *__restrict__ src,
                              const double *__restrict__ f, const double *__restrict__ nrm,
                              const double *__restrict__ phi, const double *__restrict__ w,
                              const double *__restrict__ h, double alpha, double csl, double cdl,
-                             SrcRec *__restrict__ rec) {
-  const double cx = src[0], cy = src[1], cz = src[2];
+                             const double *__restrict__ cen, SrcRec *__restrict__ rec) {
+  const double cx = cen[0], cy = cen[1], cz = cen[2];
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ns;
        j += (int64_t)gridDim.x * blockDim.x) {
     SrcRec R;
@@ -34,7 +34,7 @@ __global__ void k_pack_mixed(int64_t ns, const double *__restrict__ src,
     float hhf = (float)fmin(hh, (double)FLT_MAX);
     hhf = fmaxf(hhf, FLT_MIN);  // exactly coincident points always take the FP64 path
     R.yh = make_float4(hx, hy, hz, hhf);
-    const double wj = w[j];
+    const double wj = w ? w[j] : 1.0;
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f), nn = q, pp = q;
     if (f)
       q = make_float4((float)(wj * csl * f[3 * j]), (float)(wj * csl * f[3 * j + 1]),
@@ -61,7 +61,7 @@ __global__ void k_pack_fp64(int64_t ns, const double *__restrict__ src,
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ns;
        j += (int64_t)gridDim.x * blockDim.x) {
     SrcRec64 R;
-    const double wj = w[j];
+    const double wj = w ? w[j] : 1.0;
     for (int k = 0; k < 3; ++k) {
       R.y[k] = src[3 * j + k];
       R.q[k] = f ? wj * csl * f[3 * j + k] : 0.0;
@@ -522,8 +522,9 @@ static int grid_for(int64_t n, int threads, int cap = 4096) {
 
 void launch_pack_mixed(int64_t ns, const double *src, const double *f, const double *nrm,
                        const double *phi, const double *w, const double *h, double alpha,
-                       double csl, double cdl, SrcRec *rec, cudaStream_t st) {
-  k_pack_mixed<<<grid_for(ns, 256), 256, 0, st>>>(ns, src, f, nrm, phi, w, h, alpha, csl, cdl, rec);
+                       double csl, double cdl, const double *cen, SrcRec *rec, cudaStream_t st) {
+  k_pack_mixed<<<grid_for(ns, 256), 256, 0, st>>>(ns, src, f, nrm, phi, w, h, alpha, csl, cdl,
+                                                  cen ? cen : src, rec);
   count_launches(1);
 }
 

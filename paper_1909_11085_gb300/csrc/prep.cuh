@@ -11,7 +11,7 @@ void count_launches(int n);
 
 void launch_pack_mixed(int64_t ns, const double *src, const double *f, const double *nrm,
                        const double *phi, const double *w, const double *h, double alpha,
-                       double csl, double cdl, SrcRec *rec, cudaStream_t st);
+                       double csl, double cdl, const double *cen, SrcRec *rec, cudaStream_t st);
 void launch_pack_fp64(int64_t ns, const double *src, const double *f, const double *nrm,
                       const double *phi, const double *w, double csl, double cdl, SrcRec64 *rec,
                       cudaStream_t st);
@@ -38,6 +38,24 @@ void launch_finish(int64_t nt, int32_t nparts, const double *part_out, const int
                    int32_t accumulate, double *out, cudaStream_t st);
 void launch_zero_ints(int32_t *p, int n, cudaStream_t st);
 void launch_widen(int64_t n, const int32_t *in, int64_t *out, cudaStream_t st);
+
+// Adjoint passes (adjoint.cu).
+struct AdjParams {
+  const void *out_rec;     // records of the output points (SrcRec or SrcRec64), caller order
+  const void *in_rec;      // records of the input points
+  const int32_t *operm;    // sorted -> caller index of the output points
+  const int32_t *iperm;    // sorted -> caller index of the input points
+  int64_t nout, nin;
+  int32_t nsplit;
+  int32_t has_sl, has_dl;
+  const double *out64;     // caller FP64 positions of the output points
+  const double *in64;      // caller FP64 positions of the input points
+  double *partial;         // [nsplit][nout][12 or 3], caller order
+};
+cudaError_t launch_adjoint(bool mixed, bool src_major, const AdjParams &A, cudaStream_t st);
+void launch_adj_finish(bool src_major, int64_t n, int32_t nsplit, const double *part,
+                       const double *w, double csl, double cdl, double *grad_f, double *grad_phi,
+                       double *grad_n, double *grad_y, double *grad_x, cudaStream_t st);
 
 size_t engine_mixed_smem_bytes();
 cudaError_t launch_engine_mixed(const EngineParams &P, int grid, cudaStream_t stream);

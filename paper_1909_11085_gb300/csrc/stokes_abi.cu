@@ -279,7 +279,8 @@ stk_status pack(const Plan &p, void *ws, const double *src, const double *f, con
                 cudaStream_t st) {
   const double csl = 1.0 / (8.0 * kPi * mu), cdl = 6.0 / (8.0 * kPi);
   if (p.mixed)
-    launch_pack_mixed(p.ns, src, f, nrm, phi, w, h, alpha, csl, cdl, at<SrcRec>(ws, p.rec), st);
+    launch_pack_mixed(p.ns, src, f, nrm, phi, w, h, alpha, csl, cdl, src, at<SrcRec>(ws, p.rec),
+                      st);
   else
     launch_pack_fp64(p.ns, src, f, nrm, phi, w, csl, cdl, at<SrcRec64>(ws, p.rec), st);
   CU(cudaGetLastError());
@@ -374,6 +375,70 @@ stk_status direct_common(int32_t kinds, const double *src, const double *f, cons
   return STK_OK;
 }
 
+
+// ------------------------------------------------------------------ adjoint
+struct GradPlan {
+  bool mixed;
+  int64_t ns, nt;
+  int32_t nsplit_src, nsplit_trg;
+  size_t srec, trec, ska, skb, sva, svb, tka, tkb, tva, tvb, hist, hist_scan, bbox_part, bbox,
+      part_src, part_trg, counters, total;
+};
+
+int32_t adj_splits(int64_t nout, int64_t nin, const DevInfo &di) {
+  const int64_t tiles = (nout + 127) / 128;
+  if (tiles <= 0) return 1;
+  int64_t s = ((int64_t)di.sms * 8 + tiles - 1) / tiles;
+  const int64_t cap = nin / 256 > 1 ? nin / 256 : 1;
+  if (s > cap) s = cap;
+  if (s > 64) s = 64;
+  return (int32_t)(s < 1 ? 1 : s);
+}
+
+stk_status plan_grad(int64_t ns, int64_t nt, const stk_opts *o, GradPlan &p) {
+  DevInfo di;
+  CU(dev_info(di));
+  p.mixed = o->precision == STK_MIXED;
+  p.ns = ns;
+  p.nt = nt;
+  p.nsplit_src = adj_splits(ns, nt, di);
+  p.nsplit_trg = adj_splits(nt, ns, di);
+  Alloc a;
+  p.counters = a.take(sizeof(int32_t) * 4);
+  const size_t rb = p.mixed ? sizeof(SrcRec) : sizeof(SrcRec64);
+  p.srec = a.take(rb * (size_t)ns);
+  p.trec = a.take(rb * (size_t)nt);
+  p.ska = a.take(8 * (size_t)ns);
+  p.skb = a.take(8 * (size_t)ns);
+  p.sva = a.take(4 * (size_t)ns);
+  p.svb = a.take(4 * (size_t)ns);
+  p.tka = a.take(8 * (size_t)nt);
+  p.tkb = a.take(8 * (size_t)nt);
+  p.tva = a.take(4 * (size_t)nt);
+  p.tvb = a.take(4 * (size_t)nt);
+  const size_t he = radix_hist_entries(ns > nt ? ns : nt);
+  p.hist = a.take(4 * he);
+  p.hist_scan = a.take(4 * (he + 1));
+  p.bbox_part = a.take(sizeof(double) * 6 * 1024);
+  p.bbox = a.take(sizeof(double) * 6);
+  p.part_src = a.take(sizeof(double) * 12 * (size_t)ns * (size_t)p.nsplit_src);
+  p.part_trg = a.take(sizeof(double) * 3 * (size_t)nt * (size_t)p.nsplit_trg);
+  p.total = a.off + 256;
+  return STK_OK;
+}
+
+// Morton order of n points (permutation sorted -> caller index).
+const int32_t *morton_perm(int64_t n, const double *pts, void *ws, size_t ka, size_t kb,
+                           size_t va, size_t vb, size_t hist, size_t hist_scan, size_t bpart,
+                           size_t bbox, cudaStream_t st) {
+  launch_bbox(n, pts, at<double>(ws, bpart), at<double>(ws, bbox), st);
+  uint64_t *k0 = at<uint64_t>(ws, ka), *k1 = at<uint64_t>(ws, kb);
+  int32_t *v0 = at<int32_t>(ws, va), *v1 = at<int32_t>(ws, vb);
+  launch_morton(n, pts, at<double>(ws, bbox), nullptr, 0, k0, v0, st);
+  const int which = radix_sort(k0, v0, k1, v1, n, 30, at<int32_t>(ws, hist),
+                               at<int32_t>(ws, hist_scan), st);
+  return which ? v1 : v0;
+}
 }  // namespace
 
 namespace stk {
@@ -574,6 +639,112 @@ stk_status stokes_batched_eval(const double *pts, const double *f, const double 
   s = run_engine(p, ws, P, st);
   if (s != STK_OK) return s;
   launch_finish(n, 1, at<double>(ws, p.part), P.tperm, opts->accumulate, out, st);
+  CU(cudaGetLastError());
+  return STK_OK;
+}
+
+
+stk_status stokes_grad_workspace_size(int64_t ns, int64_t nt, const stk_opts *opts,
+                                      size_t *bytes) {
+  stk_status s = check_opts(opts);
+  if (s != STK_OK) return s;
+  if (!bytes) return fail(STK_EINVAL, "bytes is NULL");
+  if (ns < 0 || nt < 0 || ns > kMaxN || nt > kMaxN) return fail(STK_EINVAL, "bad sizes");
+  GradPlan p;
+  s = plan_grad(ns, nt, opts, p);
+  if (s != STK_OK) return s;
+  *bytes = p.total;
+  return STK_OK;
+}
+
+stk_status stokes_sldl_grad(const double *src, const double *f, const double *nrm,
+                            const double *phi, const double *w, const double *h, int64_t ns,
+                            const double *trg, int64_t nt, const double *g, double mu,
+                            double *grad_f, double *grad_phi, double *grad_y, double *grad_n,
+                            double *grad_x, const stk_opts *opts, void *workspace,
+                            size_t workspace_bytes, void *stream) {
+  stk_status s = check_opts(opts);
+  if (s != STK_OK) return s;
+  if (ns < 0 || nt < 0 || ns > kMaxN || nt > kMaxN) return fail(STK_EINVAL, "bad sizes");
+  if (!f && !phi) return fail(STK_EINVAL, "f and phi are both NULL");
+  if (f && !(mu > 0.0 && std::isfinite(mu))) return fail(STK_EINVAL, "mu must be finite and > 0");
+  if (phi && !nrm) return fail(STK_EINVAL, "nrm is NULL");
+  if (grad_f && !f) return fail(STK_EINVAL, "grad_f requested without f");
+  if ((grad_phi || grad_n) && !phi) return fail(STK_EINVAL, "grad_phi/grad_n requested without phi");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const bool want_src = grad_f || grad_phi || grad_y || grad_n;
+  if (ns == 0 || nt == 0 || (!want_src && !grad_x)) {
+    if (ns > 0 && want_src) {
+      if (grad_f) CU(cudaMemsetAsync(grad_f, 0, 24 * (size_t)ns, st));
+      if (grad_phi) CU(cudaMemsetAsync(grad_phi, 0, 24 * (size_t)ns, st));
+      if (grad_y) CU(cudaMemsetAsync(grad_y, 0, 24 * (size_t)ns, st));
+      if (grad_n) CU(cudaMemsetAsync(grad_n, 0, 24 * (size_t)ns, st));
+    }
+    if (nt > 0 && grad_x) CU(cudaMemsetAsync(grad_x, 0, 24 * (size_t)nt, st));
+    return STK_OK;
+  }
+  if (!src || !w || !trg || !g) return fail(STK_EINVAL, "NULL pointer");
+  if (opts->precision == STK_MIXED && (ns >= kMaxMixed || nt >= kMaxMixed))
+    return fail(STK_EUNSUPPORTED, "the mixed form supports fewer than 2^30 points");
+  GradPlan p;
+  s = plan_grad(ns, nt, opts, p);
+  if (s != STK_OK) return s;
+  if (!workspace || workspace_bytes < p.total) return fail(STK_ENOMEM, "workspace too small");
+  void *ws = align_ws(workspace);
+  const double csl = f ? 1.0 / (8.0 * kPi * mu) : 0.0, cdl = 6.0 / (8.0 * kPi);
+  if (p.mixed) {
+    launch_pack_mixed(ns, src, f, nrm, phi, w, h, opts->near_ratio, csl, cdl, src,
+                      at<SrcRec>(ws, p.srec), st);
+    launch_pack_mixed(nt, trg, g, nullptr, nullptr, nullptr, nullptr, 0.0, 1.0, 0.0, src,
+                      at<SrcRec>(ws, p.trec), st);
+  } else {
+    launch_pack_fp64(ns, src, f, nrm, phi, w, csl, cdl, at<SrcRec64>(ws, p.srec), st);
+    launch_pack_fp64(nt, trg, g, nullptr, nullptr, nullptr, 1.0, 0.0, at<SrcRec64>(ws, p.trec),
+                     st);
+  }
+  CU(cudaGetLastError());
+  const int32_t *sperm = morton_perm(ns, src, ws, p.ska, p.skb, p.sva, p.svb, p.hist, p.hist_scan,
+                                     p.bbox_part, p.bbox, st);
+  const int32_t *tperm = morton_perm(nt, trg, ws, p.tka, p.tkb, p.tva, p.tvb, p.hist, p.hist_scan,
+                                     p.bbox_part, p.bbox, st);
+  CU(cudaGetLastError());
+  AdjParams A;
+  A.has_sl = f ? 1 : 0;
+  A.has_dl = phi ? 1 : 0;
+  if (want_src) {
+    A.out_rec = at<void>(ws, p.srec);
+    A.in_rec = at<void>(ws, p.trec);
+    A.operm = sperm;
+    A.iperm = tperm;
+    A.nout = ns;
+    A.nin = nt;
+    A.nsplit = p.nsplit_src;
+    A.out64 = src;
+    A.in64 = trg;
+    A.partial = at<double>(ws, p.part_src);
+    if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_start, st));
+    CU(launch_adjoint(p.mixed, true, A, st));
+    launch_adj_finish(true, ns, p.nsplit_src, A.partial, w, csl, cdl, grad_f, grad_phi, grad_n,
+                      grad_y, nullptr, st);
+  }
+  if (grad_x) {
+    A.out_rec = at<void>(ws, p.trec);
+    A.in_rec = at<void>(ws, p.srec);
+    A.operm = tperm;
+    A.iperm = sperm;
+    A.nout = nt;
+    A.nin = ns;
+    A.nsplit = p.nsplit_trg;
+    A.out64 = trg;
+    A.in64 = src;
+    A.partial = at<double>(ws, p.part_trg);
+    CU(launch_adjoint(p.mixed, false, A, st));
+    if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_stop, st));
+    launch_adj_finish(false, nt, p.nsplit_trg, A.partial, nullptr, 0.0, 0.0, nullptr, nullptr,
+                      nullptr, nullptr, grad_x, st);
+  } else if (g_ev_start && g_ev_stop) {
+    CU(cudaEventRecord(g_ev_stop, st));
+  }
   CU(cudaGetLastError());
   return STK_OK;
 }

@@ -9,6 +9,8 @@ PyTorch provides only device memory and the stream.
   sldl  superposition, Eq. "velocity_combined"    u = S[f] + D[phi]
   p2p   FMM near field over U-lists (Sec. 3.1 "Far evaluation")
   batched  independent suspensions: S over cell points + D over wall points
+  sldl_grad  adjoint of sldl: gradients wrt f, phi, source positions, normals, targets
+  StokesLayerFn  torch.autograd.Function over sldl whose backward calls sldl_grad
 """
 from __future__ import annotations
 
@@ -165,3 +167,76 @@ def batched(pts, f, phi, nrm, w, susp_ptr, n_cell, mu=1.0, h=None, precision="mi
             near_ratio=1.0, out=None, accumulate=False):
     plan = BatchedPlan(pts.shape[0], susp_ptr, n_cell, precision, near_ratio, pts.device)
     return plan(pts, f, phi, nrm, w, h, mu, out, accumulate)
+
+
+def sldl_grad(src, f, nrm, phi, w, trg, g, mu=1.0, h=None, precision="mixed", near_ratio=1.0,
+              want=("f", "phi", "y", "n", "x")):
+    """Gradients of L = sum_i g_i . (SL[f] + DL[phi])(x_i); returns a dict of tensors
+    (keys among f, phi, y, n, x; y and n are per source, x per target)."""
+    ns = src.shape[0]
+    src = A.vec3(src, "src")
+    trg = src if trg is None else A.vec3(trg, "trg")
+    nt = trg.shape[0]
+    f, nrm, phi = A.vec3(f, "f", ns), A.vec3(nrm, "nrm", ns), A.vec3(phi, "phi", ns)
+    w, h = A.vec1(w, "w", ns), A.vec1(h, "h", ns)
+    g = A.vec3(g, "g", nt)
+    dev = src.device
+    mk = lambda n: torch.empty((n, 3), dtype=torch.float64, device=dev)
+    out = {}
+    if "f" in want and f is not None:
+        out["f"] = mk(ns)
+    if "phi" in want and phi is not None:
+        out["phi"] = mk(ns)
+    if "y" in want:
+        out["y"] = mk(ns)
+    if "n" in want and phi is not None:
+        out["n"] = mk(ns)
+    if "x" in want:
+        out["x"] = mk(nt)
+    o = A.make_opts(precision, near_ratio)
+    nb = ctypes.c_size_t(0)
+    L = A.lib()
+    with torch.cuda.device(dev):
+        A.check(L.stokes_grad_workspace_size(ns, nt, ctypes.byref(o), ctypes.byref(nb)))
+        ws = A.workspace(nb.value, dev)
+        A.check(L.stokes_sldl_grad(
+            A.ptr(src), A.ptr(f), A.ptr(nrm), A.ptr(phi), A.ptr(w), A.ptr(h), ns, A.ptr(trg), nt,
+            A.ptr(g), float(mu), A.ptr(out.get("f")), A.ptr(out.get("phi")), A.ptr(out.get("y")),
+            A.ptr(out.get("n")), A.ptr(out.get("x")), ctypes.byref(o), A.ptr(ws), ws.numel(),
+            A.stream_ptr(dev)))
+    return out
+
+
+class StokesLayerFn(torch.autograd.Function):
+    """u = SL[f] + DL[phi] at the targets, differentiable in f, phi, the source
+    positions, the normals and the target positions (weights and spacings are
+    constants).  The backward recomputes the pair terms (no O(N^2) state)."""
+
+    @staticmethod
+    def forward(ctx, src, f, nrm, phi, w, trg, mu=1.0, h=None, precision="mixed",
+                near_ratio=1.0):
+        ctx.save_for_backward(src, f, nrm, phi, w, trg, h)
+        ctx.cfg = (float(mu), precision, float(near_ratio))
+        return sldl(src, f, nrm, phi, w, trg, mu, h=h, precision=precision,
+                    near_ratio=near_ratio)
+
+    @staticmethod
+    def backward(ctx, gu):
+        src, f, nrm, phi, w, trg, h = ctx.saved_tensors
+        mu, precision, near_ratio = ctx.cfg
+        need = ctx.needs_input_grad
+        want = []
+        if need[0]:
+            want.append("y")
+        if need[1]:
+            want.append("f")
+        if need[2]:
+            want.append("n")
+        if need[3]:
+            want.append("phi")
+        if need[5]:
+            want.append("x")
+        G = sldl_grad(src, f, nrm, phi, w, trg, gu.contiguous(), mu, h=h, precision=precision,
+                      near_ratio=near_ratio, want=tuple(want))
+        return (G.get("y"), G.get("f"), G.get("n"), G.get("phi"), None, G.get("x"), None, None,
+                None, None)

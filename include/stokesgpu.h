@@ -67,7 +67,7 @@ typedef struct {
   double near_ratio;    /* alpha: a pair is "near" when |r| < alpha * h_j (MIXED only); >= 0 */
   int32_t accumulate;   /* 0: out = u; 1: out += u */
   int32_t source_splits;/* direct sums: split the sources into this many parts (0 = automatic) */
-  int32_t tile_config;  /* -1 = tuned default; otherwise a config id from stokes_autotune */
+  int32_t tile_config;  /* -1 = default work-item shape; else an id < stokes_tile_config_count() */
 } stk_opts;
 
 /* Defaults: MIXED, alpha = 1, overwrite, automatic splits, tuned config. */
@@ -129,6 +129,49 @@ stk_status stokes_batched_eval(const double *pts, const double *f, const double 
                                size_t workspace_bytes, void *stream);
 stk_status stokes_batched_workspace_size(int64_t n, int32_t nsusp, const stk_opts *opts,
                                          size_t *bytes);
+
+/* ------------------------------------------------- tuning and CUDA graphs
+ * Work items (a warp's targets against its source segments) come in
+ * stokes_tile_config_count() shapes; opts->tile_config picks one (-1: the
+ * default).  The autotuners run every shape on the caller's own data (one
+ * warm-up and three timed calls each; they synchronise the stream, write
+ * `out`, and need a workspace from the matching *_workspace_size query) and
+ * return the fastest id and its median time.
+ * The *_graph_create calls capture one call with these arguments into an
+ * executable CUDA graph (stream must not be the legacy default stream); the
+ * graph replays with stokes_graph_launch on any stream, reading the same
+ * device buffers, and is released with stokes_graph_destroy.  This is how a
+ * batch of suspensions runs as one persistent launch per replay.
+ */
+int32_t stokes_tile_config_count(void);
+stk_status stokes_autotune_p2p(const double *pts, const double *f, const double *phi,
+                               const double *nrm, const double *w, const double *h, int64_t n,
+                               const int32_t *leaf_ptr, int32_t nleaf, const int32_t *ulist_ptr,
+                               const int32_t *ulist_idx, int64_t nulist, int32_t kernels,
+                               double mu, double *out, const stk_opts *opts, void *workspace,
+                               size_t workspace_bytes, void *stream, int32_t *best_config,
+                               float *best_ms);
+stk_status stokes_autotune_batched(const double *pts, const double *f, const double *phi,
+                                   const double *nrm, const double *w, const double *h, int64_t n,
+                                   const int64_t *susp_ptr, const int64_t *n_cell, int32_t nsusp,
+                                   double mu, double *out, const stk_opts *opts, void *workspace,
+                                   size_t workspace_bytes, void *stream, int32_t *best_config,
+                                   float *best_ms);
+stk_status stokes_p2p_graph_create(const double *pts, const double *f, const double *phi,
+                                   const double *nrm, const double *w, const double *h, int64_t n,
+                                   const int32_t *leaf_ptr, int32_t nleaf,
+                                   const int32_t *ulist_ptr, const int32_t *ulist_idx,
+                                   int64_t nulist, int32_t kernels, double mu, double *out,
+                                   const stk_opts *opts, void *workspace, size_t workspace_bytes,
+                                   void *stream, void **graph_exec);
+stk_status stokes_batched_graph_create(const double *pts, const double *f, const double *phi,
+                                       const double *nrm, const double *w, const double *h,
+                                       int64_t n, const int64_t *susp_ptr, const int64_t *n_cell,
+                                       int32_t nsusp, double mu, double *out,
+                                       const stk_opts *opts, void *workspace,
+                                       size_t workspace_bytes, void *stream, void **graph_exec);
+stk_status stokes_graph_launch(void *graph_exec, void *stream);
+stk_status stokes_graph_destroy(void *graph_exec);
 
 /* ----------------------------------------------------------------- adjoint
  * Gradients of L = sum_i g_i . u(x_i) with u = SL[f] + DL[phi] over one

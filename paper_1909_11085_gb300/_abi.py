@@ -27,6 +27,9 @@ EXPORTS = [
     "stokes_batched_eval", "stokes_batched_workspace_size", "stokes_device_status",
     "stokes_last_error", "stokes_version", "stokes_set_engine_events", "stokes_launch_count",
     "stokes_sl_eval_noalloc", "stokes_sldl_grad", "stokes_grad_workspace_size",
+    "stokes_tile_config_count", "stokes_autotune_p2p", "stokes_autotune_batched",
+    "stokes_p2p_graph_create", "stokes_batched_graph_create", "stokes_graph_launch",
+    "stokes_graph_destroy",
 ]
 
 
@@ -77,11 +80,24 @@ def lib():
             L.stokes_sldl_grad.argtypes = [p, p, p, p, p, p, i64, p, i64, p, d, p, p, p, p, p, po,
                                            p, sz, p]
             L.stokes_grad_workspace_size.argtypes = [i64, i64, po, psz]
+            pi32, pf, pp = (ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
+                            ctypes.POINTER(ctypes.c_void_p))
+            L.stokes_tile_config_count.restype = ctypes.c_int32
+            L.stokes_autotune_p2p.argtypes = [p, p, p, p, p, p, i64, p, i32, p, p, i64, i32, d, p,
+                                              po, p, sz, p, pi32, pf]
+            L.stokes_autotune_batched.argtypes = [p, p, p, p, p, p, i64, p, p, i32, d, p, po, p, sz,
+                                                  p, pi32, pf]
+            L.stokes_p2p_graph_create.argtypes = [p, p, p, p, p, p, i64, p, i32, p, p, i64, i32, d,
+                                                  p, po, p, sz, p, pp]
+            L.stokes_batched_graph_create.argtypes = [p, p, p, p, p, p, i64, p, p, i32, d, p, po, p,
+                                                      sz, p, pp]
+            L.stokes_graph_launch.argtypes = [p, p]
+            L.stokes_graph_destroy.argtypes = [p]
             L.stokes_launch_count.restype = ctypes.c_int64
             for name in EXPORTS:
                 fn = getattr(L, name)
                 if name not in ("stokes_default_opts", "stokes_last_error", "stokes_version",
-                                "stokes_launch_count"):
+                                "stokes_launch_count", "stokes_tile_config_count"):
                     fn.restype = ctypes.c_int
             _lib = L
     return _lib

@@ -10,7 +10,25 @@ namespace stk {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarp = 32;
 constexpr int kChunk = 64;      // sources staged per chunk (one bulk copy)
-constexpr int kItemMax = 128;   // targets per work item (32 lanes x 4)
+constexpr int kItemMax = 128;   // most targets per work item (32 lanes x 4)
+
+// Work-item shapes the autotuner chooses from: the most targets per item and
+// the lane layout (0: T = 1..4 targets per lane with b = 1, 2 or 4 source
+// slices, chosen per item to limit padding; 1: b = 1, T = ceil(targets/32)).
+struct TileConfig {
+  int32_t item_max;
+  int32_t policy;
+};
+constexpr int kNumTileConfigs = 4;
+constexpr int kMinItemMax = 64;
+__host__ __device__ inline TileConfig tile_config(int id) {
+  switch (id) {
+    case 1: return TileConfig{128, 1};
+    case 2: return TileConfig{64, 0};
+    case 3: return TileConfig{96, 0};
+    default: return TileConfig{128, 0};
+  }
+}
 constexpr int kQCap = 16;       // near-pair queue entries per lane
 constexpr int kWarpsPerCta = 4; // engine CTA = 4 independent warps
 
@@ -61,6 +79,7 @@ struct EngineParams {
   int32_t kind_alternating;  // 1: segment id even -> SL, odd -> DL
   int32_t nt;                // number of targets
   int32_t self_index;        // 1: caller target index == source index means the same point
+  int32_t policy;            // lane layout of the tile configuration
   double *part_out;          // [nparts][nt][3], sorted target order
   int32_t *item_counter;     // work queue head (zeroed before launch)
   int32_t *near_cnt;         // [nparts][nt][4] fill of each near sub-list

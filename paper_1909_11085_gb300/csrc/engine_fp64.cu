@@ -110,7 +110,16 @@ __global__ void __launch_bounds__(kWarpsPerCta *kWarp, 4) k_engine_fp64(EnginePa
     const int id = P.item_order ? P.item_order[idx] : idx;
     const Item it = P.items[id];
     const int tn = it.tn_part & 0xFF;
-    if (tn <= 8)
+    if (P.policy == 1) {
+      if (tn <= 32)
+        run_item64<1>(P, it, 1, lane);
+      else if (tn <= 64)
+        run_item64<2>(P, it, 1, lane);
+      else if (tn <= 96)
+        run_item64<3>(P, it, 1, lane);
+      else
+        run_item64<4>(P, it, 1, lane);
+    } else if (tn <= 8)
       run_item64<1>(P, it, 4, lane);
     else if (tn <= 16)
       run_item64<2>(P, it, 4, lane);

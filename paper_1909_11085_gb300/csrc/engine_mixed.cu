@@ -597,7 +597,16 @@ __global__ void __launch_bounds__(kWarpsPerCta *kWarp, STK_ENGINE_MIN_BLOCKS) k_
     const Item it = P.items[id];
     const int tn = it.tn_part & 0xFF;
     bool ok;
-    if (tn <= 8)
+    if (P.policy == 1) {  // one source slice, T = ceil(tn / 32)
+      if (tn <= 32)
+        ok = run_item<1, KMODE>(P, it, sm, 1, phase, lane);
+      else if (tn <= 64)
+        ok = run_item<2, KMODE>(P, it, sm, 1, phase, lane);
+      else if (tn <= 96)
+        ok = run_item<3, KMODE>(P, it, sm, 1, phase, lane);
+      else
+        ok = run_item<4, KMODE>(P, it, sm, 1, phase, lane);
+    } else if (tn <= 8)
       ok = run_item<1, KMODE>(P, it, sm, 4, phase, lane);
     else if (tn <= 16)
       ok = run_item<2, KMODE>(P, it, sm, 4, phase, lane);

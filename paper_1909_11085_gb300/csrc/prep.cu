@@ -298,16 +298,17 @@ __device__ __forceinline__ uint64_t cost_key(int64_t tn, int64_t nsrc) {
   return 0xffffffffull - c;
 }
 
-__global__ void k_items_direct(int32_t nt, int64_t ns, int32_t nsplit, Item *__restrict__ items,
-                               int64_t *__restrict__ range_ptr, int32_t *__restrict__ n_items) {
-  const int32_t nchunk = (nt + kItemMax - 1) / kItemMax;
+__global__ void k_items_direct(int32_t nt, int64_t ns, int32_t nsplit, int32_t item_max,
+                               Item *__restrict__ items, int64_t *__restrict__ range_ptr,
+                               int32_t *__restrict__ n_items) {
+  const int32_t nchunk = (nt + item_max - 1) / item_max;
   const int64_t tot = (int64_t)nchunk * nsplit;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = (int32_t)(i / nsplit), s = (int32_t)(i % nsplit);
     Item it;
-    it.t0 = c * kItemMax;
-    const int32_t tn = min(kItemMax, nt - it.t0);
+    it.t0 = c * item_max;
+    const int32_t tn = min(item_max, nt - it.t0);
     it.tn_part = tn | (s << 8);
     it.seg0 = s;
     it.seg1 = s + 1;
@@ -318,18 +319,17 @@ __global__ void k_items_direct(int32_t nt, int64_t ns, int32_t nsplit, Item *__r
   if (g == 0) *n_items = (int32_t)tot;
 }
 
-__global__ void k_p2p_count(int32_t nleaf, const int32_t *__restrict__ leaf_ptr,
-                            const int32_t *__restrict__ ulist_ptr,
-                            const int32_t *__restrict__ ulist_idx, int32_t *__restrict__ cnt) {
+__global__ void k_p2p_count(int32_t nleaf, const int32_t *__restrict__ leaf_ptr, int32_t item_max,
+                            int32_t *__restrict__ cnt) {
   for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nleaf; b += gridDim.x * blockDim.x) {
     const int32_t nb = leaf_ptr[b + 1] - leaf_ptr[b];
-    cnt[b] = (nb + kItemMax - 1) / kItemMax;
+    cnt[b] = (nb + item_max - 1) / item_max;
   }
 }
 
 __global__ void k_p2p_emit(int32_t nleaf, const int32_t *__restrict__ leaf_ptr,
                            const int32_t *__restrict__ ulist_ptr,
-                           const int32_t *__restrict__ ulist_idx,
+                           const int32_t *__restrict__ ulist_idx, int32_t item_max,
                            const int32_t *__restrict__ offs, Item *__restrict__ items,
                            uint64_t *__restrict__ keys, int32_t *__restrict__ vals) {
   for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nleaf; b += gridDim.x * blockDim.x) {
@@ -340,7 +340,7 @@ __global__ void k_p2p_emit(int32_t nleaf, const int32_t *__restrict__ leaf_ptr,
       const int32_t a = ulist_idx[e];
       nsrc += leaf_ptr[a + 1] - leaf_ptr[a];
     }
-    const int32_t nc = (nb + kItemMax - 1) / kItemMax;
+    const int32_t nc = (nb + item_max - 1) / item_max;
     const int32_t base = nb / nc, extra = nb % nc;
     int32_t t0 = leaf_ptr[b];
     for (int32_t c = 0; c < nc; ++c) {
@@ -360,15 +360,16 @@ __global__ void k_p2p_emit(int32_t nleaf, const int32_t *__restrict__ leaf_ptr,
 }
 
 __global__ void k_batched_count(int32_t nsusp, const int64_t *__restrict__ susp_ptr,
-                                int32_t *__restrict__ cnt) {
+                                int32_t item_max, int32_t *__restrict__ cnt) {
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nsusp; s += gridDim.x * blockDim.x) {
     const int64_t ns = susp_ptr[s + 1] - susp_ptr[s];
-    cnt[s] = (int32_t)((ns + kItemMax - 1) / kItemMax);
+    cnt[s] = (int32_t)((ns + item_max - 1) / item_max);
   }
 }
 
 __global__ void k_batched_emit(int32_t nsusp, const int64_t *__restrict__ susp_ptr,
-                               const int64_t *__restrict__ n_cell, const int32_t *__restrict__ offs,
+                               const int64_t *__restrict__ n_cell, int32_t item_max,
+                               const int32_t *__restrict__ offs,
                                Item *__restrict__ items, int64_t *__restrict__ range_ptr,
                                uint64_t *__restrict__ keys, int32_t *__restrict__ vals) {
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nsusp; s += gridDim.x * blockDim.x) {
@@ -378,7 +379,7 @@ __global__ void k_batched_emit(int32_t nsusp, const int64_t *__restrict__ susp_p
     if (s == nsusp - 1) range_ptr[2 * nsusp] = p1;
     const int64_t nb = p1 - p0;
     if (nb <= 0) continue;
-    const int32_t nc = (int32_t)((nb + kItemMax - 1) / kItemMax);
+    const int32_t nc = (int32_t)((nb + item_max - 1) / item_max);
     const int64_t base = nb / nc, extra = nb % nc;
     int64_t t0 = p0;
     for (int32_t c = 0; c < nc; ++c) {
@@ -556,35 +557,38 @@ void launch_scan(const int32_t *in, int64_t n, int32_t *out, int32_t *total, cud
   count_launches(1);
 }
 
-void launch_items_direct(int32_t nt, int64_t ns, int32_t nsplit, Item *items, int64_t *range_ptr,
-                         int32_t *n_items, cudaStream_t st) {
-  const int64_t tot = (int64_t)((nt + kItemMax - 1) / kItemMax) * nsplit;
+void launch_items_direct(int32_t nt, int64_t ns, int32_t nsplit, int32_t item_max, Item *items,
+                         int64_t *range_ptr, int32_t *n_items, cudaStream_t st) {
+  const int64_t tot = (int64_t)((nt + item_max - 1) / item_max) * nsplit;
   const int64_t need = tot > nsplit + 1 ? tot : nsplit + 1;
-  k_items_direct<<<grid_for(need, 256), 256, 0, st>>>(nt, ns, nsplit, items, range_ptr, n_items);
+  k_items_direct<<<grid_for(need, 256), 256, 0, st>>>(nt, ns, nsplit, item_max, items, range_ptr,
+                                                      n_items);
   count_launches(1);
 }
 
 void launch_p2p_items(int32_t nleaf, const int32_t *leaf_ptr, const int32_t *ulist_ptr,
-                      const int32_t *ulist_idx, int32_t *cnt, int32_t *offs, int32_t *n_items,
-                      Item *items, uint64_t *keys, int32_t *vals, cudaStream_t st) {
-  k_p2p_count<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, leaf_ptr, ulist_ptr, ulist_idx, cnt);
+                      const int32_t *ulist_idx, int32_t item_max, int32_t *cnt, int32_t *offs,
+                      int32_t *n_items, Item *items, uint64_t *keys, int32_t *vals,
+                      cudaStream_t st) {
+  k_p2p_count<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, leaf_ptr, item_max, cnt);
   count_launches(1);
   k_scan_excl<<<1, kScanThreads, 0, st>>>(cnt, nleaf, offs, n_items);
   count_launches(1);
-  k_p2p_emit<<<grid_for(nleaf, 128), 128, 0, st>>>(nleaf, leaf_ptr, ulist_ptr, ulist_idx, offs,
-                                                   items, keys, vals);
+  k_p2p_emit<<<grid_for(nleaf, 128), 128, 0, st>>>(nleaf, leaf_ptr, ulist_ptr, ulist_idx, item_max,
+                                                   offs, items, keys, vals);
   count_launches(1);
 }
 
 void launch_batched_items(int32_t nsusp, const int64_t *susp_ptr, const int64_t *n_cell,
-                          int32_t *cnt, int32_t *offs, int32_t *n_items, Item *items,
-                          int64_t *range_ptr, uint64_t *keys, int32_t *vals, cudaStream_t st) {
-  k_batched_count<<<grid_for(nsusp, 256), 256, 0, st>>>(nsusp, susp_ptr, cnt);
+                          int32_t item_max, int32_t *cnt, int32_t *offs, int32_t *n_items,
+                          Item *items, int64_t *range_ptr, uint64_t *keys, int32_t *vals,
+                          cudaStream_t st) {
+  k_batched_count<<<grid_for(nsusp, 256), 256, 0, st>>>(nsusp, susp_ptr, item_max, cnt);
   count_launches(1);
   k_scan_excl<<<1, kScanThreads, 0, st>>>(cnt, nsusp, offs, n_items);
   count_launches(1);
-  k_batched_emit<<<grid_for(nsusp, 128), 128, 0, st>>>(nsusp, susp_ptr, n_cell, offs, items,
-                                                       range_ptr, keys, vals);
+  k_batched_emit<<<grid_for(nsusp, 128), 128, 0, st>>>(nsusp, susp_ptr, n_cell, item_max, offs,
+                                                       items, range_ptr, keys, vals);
   count_launches(1);
 }
 

@@ -23,14 +23,16 @@ void launch_scan(const int32_t *in, int64_t n, int32_t *out, int32_t *total, cud
 size_t radix_hist_entries(int64_t n);
 int radix_sort(uint64_t *ka, int32_t *va, uint64_t *kb, int32_t *vb, int64_t n, int bits,
                int32_t *hist, int32_t *hist_scan, cudaStream_t st);
-void launch_items_direct(int32_t nt, int64_t ns, int32_t nsplit, Item *items, int64_t *range_ptr,
-                         int32_t *n_items, cudaStream_t st);
+void launch_items_direct(int32_t nt, int64_t ns, int32_t nsplit, int32_t item_max, Item *items,
+                         int64_t *range_ptr, int32_t *n_items, cudaStream_t st);
 void launch_p2p_items(int32_t nleaf, const int32_t *leaf_ptr, const int32_t *ulist_ptr,
-                      const int32_t *ulist_idx, int32_t *cnt, int32_t *offs, int32_t *n_items,
-                      Item *items, uint64_t *keys, int32_t *vals, cudaStream_t st);
+                      const int32_t *ulist_idx, int32_t item_max, int32_t *cnt, int32_t *offs,
+                      int32_t *n_items, Item *items, uint64_t *keys, int32_t *vals,
+                      cudaStream_t st);
 void launch_batched_items(int32_t nsusp, const int64_t *susp_ptr, const int64_t *n_cell,
-                          int32_t *cnt, int32_t *offs, int32_t *n_items, Item *items,
-                          int64_t *range_ptr, uint64_t *keys, int32_t *vals, cudaStream_t st);
+                          int32_t item_max, int32_t *cnt, int32_t *offs, int32_t *n_items,
+                          Item *items, int64_t *range_ptr, uint64_t *keys, int32_t *vals,
+                          cudaStream_t st);
 void launch_near(int64_t nt, int32_t nparts, const int32_t *near_cnt, const int32_t *near_idx,
                  int32_t sub_log2, const SrcRec *rec, const double *src64, const double *trg64,
                  const int32_t *tperm, double *part_out, int sms, cudaStream_t st);

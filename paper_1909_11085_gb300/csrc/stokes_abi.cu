@@ -95,6 +95,7 @@ struct Plan {
   int64_t ns, nt;
   int32_t nsplit = 1;
   int64_t max_items = 0;
+  TileConfig tile = {kItemMax, 0};
   int32_t nseg_ranges = 0;  // entries of range_ptr minus one
   bool sort_targets = false;
   bool sort_items = false;
@@ -165,6 +166,7 @@ stk_status plan_direct(int64_t ns, int64_t nt, const stk_opts *o, Plan &p) {
   CU(dev_info(di));
   p.form = F_DIRECT;
   p.mixed = o->precision == STK_MIXED;
+  p.tile = tile_config(o->tile_config < 0 ? 0 : o->tile_config);
   p.near_cap = near_sub_capacity(o->near_ratio);
   p.ns = ns;
   p.nt = nt;
@@ -172,7 +174,7 @@ stk_status plan_direct(int64_t ns, int64_t nt, const stk_opts *o, Plan &p) {
   p.nsplit = o->source_splits > 0 ? o->source_splits : auto_splits(nt, ns, di, occ);
   if (p.nsplit > ns && ns > 0) p.nsplit = (int32_t)ns;
   if (p.nsplit < 1) p.nsplit = 1;
-  p.max_items = ((nt + kItemMax - 1) / kItemMax) * p.nsplit;
+  p.max_items = ((nt + kMinItemMax - 1) / kMinItemMax) * p.nsplit;
   p.nseg_ranges = p.nsplit;
   p.sort_targets = p.mixed;
   p.sort_items = false;
@@ -184,10 +186,11 @@ stk_status plan_direct(int64_t ns, int64_t nt, const stk_opts *o, Plan &p) {
 stk_status plan_p2p(int64_t n, int32_t nleaf, const stk_opts *o, Plan &p) {
   p.form = F_P2P;
   p.mixed = o->precision == STK_MIXED;
+  p.tile = tile_config(o->tile_config < 0 ? 0 : o->tile_config);
   p.near_cap = near_sub_capacity(o->near_ratio);
   p.ns = p.nt = n;
   p.nsplit = 1;
-  p.max_items = (int64_t)nleaf + n / kItemMax + 1;
+  p.max_items = (int64_t)nleaf + n / kMinItemMax + 1;
   p.nseg_ranges = nleaf;
   p.sort_targets = false;
   p.sort_items = true;
@@ -199,10 +202,11 @@ stk_status plan_p2p(int64_t n, int32_t nleaf, const stk_opts *o, Plan &p) {
 stk_status plan_batched(int64_t n, int32_t nsusp, const stk_opts *o, Plan &p) {
   p.form = F_BATCHED;
   p.mixed = o->precision == STK_MIXED;
+  p.tile = tile_config(o->tile_config < 0 ? 0 : o->tile_config);
   p.near_cap = near_sub_capacity(o->near_ratio);
   p.ns = p.nt = n;
   p.nsplit = 1;
-  p.max_items = (int64_t)nsusp + n / kItemMax + 1;
+  p.max_items = (int64_t)nsusp + n / kMinItemMax + 1;
   p.nseg_ranges = 2 * nsusp;
   p.sort_targets = p.mixed;
   p.sort_items = true;
@@ -221,6 +225,8 @@ stk_status check_opts(const stk_opts *o) {
     return fail(STK_EINVAL, "opts->near_ratio must be finite and >= 0");
   if (o->source_splits < 0 || o->source_splits > 1024)
     return fail(STK_EINVAL, "opts->source_splits must be in [0, 1024]");
+  if (o->tile_config < -1 || o->tile_config >= kNumTileConfigs)
+    return fail(STK_EINVAL, "opts->tile_config must be -1 or a configuration id");
   return STK_OK;
 }
 
@@ -243,6 +249,7 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   P.item_counter = counters + 1;
   P.err_flag = counters + 2;
   P.spin_limit = kSpinLimit;
+  P.policy = p.tile.policy;
   P.part_out = at<double>(ws, p.part);
   P.nt = (int32_t)p.nt;
   const int occ = p.mixed ? di.occ_mixed : di.occ_fp64;
@@ -359,7 +366,7 @@ stk_status direct_common(int32_t kinds, const double *src, const double *f, cons
   P.trg64 = trg;
   P.self_index = (trg == src) ? 1 : 0;
   P.tperm = p.sort_targets ? sort_targets(p, ws, trg, nullptr, 0, st) : nullptr;
-  launch_items_direct((int32_t)nt, ns, p.nsplit, at<Item>(ws, p.items),
+  launch_items_direct((int32_t)nt, ns, p.nsplit, p.tile.item_max, at<Item>(ws, p.items),
                       at<int64_t>(ws, p.range), at<int32_t>(ws, p.counters), st);
   CU(cudaGetLastError());
   P.items = at<Item>(ws, p.items);
@@ -558,7 +565,7 @@ stk_status stokes_p2p_leaflists(const double *pts, const double *f, const double
   launch_widen((int64_t)nleaf + 1, leaf_ptr, range, st);
   int32_t *counters = at<int32_t>(ws, p.counters);
   const int32_t *order = build_sorted_items(p, ws, st, [&](uint64_t *keys, int32_t *vals) {
-    launch_p2p_items(nleaf, leaf_ptr, ulist_ptr, ulist_idx, at<int32_t>(ws, p.cnt),
+    launch_p2p_items(nleaf, leaf_ptr, ulist_ptr, ulist_idx, p.tile.item_max, at<int32_t>(ws, p.cnt),
                      at<int32_t>(ws, p.offs), counters, at<Item>(ws, p.items), keys, vals, st);
   });
   CU(cudaGetLastError());
@@ -625,7 +632,8 @@ stk_status stokes_batched_eval(const double *pts, const double *f, const double 
   P.tperm = p.sort_targets ? sort_targets(p, ws, pts, susp_ptr, nsusp, st) : nullptr;
   int32_t *counters = at<int32_t>(ws, p.counters);
   const int32_t *order = build_sorted_items(p, ws, st, [&](uint64_t *keys, int32_t *vals) {
-    launch_batched_items(nsusp, susp_ptr, n_cell, at<int32_t>(ws, p.cnt), at<int32_t>(ws, p.offs),
+    launch_batched_items(nsusp, susp_ptr, n_cell, p.tile.item_max, at<int32_t>(ws, p.cnt),
+                         at<int32_t>(ws, p.offs),
                          counters, at<Item>(ws, p.items), at<int64_t>(ws, p.range), keys, vals,
                          st);
   });
@@ -759,6 +767,161 @@ stk_status stokes_device_status(void *workspace, size_t workspace_bytes) {
     CU(cudaMemcpy(counters + 2, &zero, sizeof(int32_t), cudaMemcpyHostToDevice));
     return fail(STK_ETIMEOUT, "a bounded device wait ran out; results of that call are incomplete");
   }
+  return STK_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- autotuning
+namespace {
+// Times `call` on the caller's data for every tile configuration (one
+// warm-up and three timed calls each, median) and returns the fastest.
+template <class Call>
+stk_status tune_configs(cudaStream_t st, Call call, int32_t *best, float *best_ms) {
+  if (!best) return fail(STK_EINVAL, "best is NULL");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(STK_ECUDA, "cudaEventCreate failed");
+  }
+  const cudaEvent_t save0 = g_ev_start, save1 = g_ev_stop;
+  g_ev_start = g_ev_stop = nullptr;
+  stk_status s = STK_OK;
+  float bestv = 3.0e38f;
+  int32_t bestc = 0;
+  for (int32_t c = 0; c < kNumTileConfigs && s == STK_OK; ++c) {
+    s = call(c);
+    float t[3];
+    for (int r = 0; r < 3 && s == STK_OK; ++r) {
+      cudaEventRecord(e0, st);
+      s = call(c);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) s = fail(STK_ECUDA, "tuning run failed");
+      cudaEventElapsedTime(&t[r], e0, e1);
+    }
+    if (s != STK_OK) break;
+    const float med = fmaxf(fminf(t[0], t[1]), fminf(fmaxf(t[0], t[1]), t[2]));
+    if (med < bestv) {
+      bestv = med;
+      bestc = c;
+    }
+  }
+  g_ev_start = save0;
+  g_ev_stop = save1;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != STK_OK) return s;
+  *best = bestc;
+  if (best_ms) *best_ms = bestv;
+  return STK_OK;
+}
+
+// Captures one call into an executable CUDA graph.
+template <class Call>
+stk_status capture_graph(cudaStream_t st, Call call, void **graph_exec) {
+  if (!graph_exec) return fail(STK_EINVAL, "graph_exec is NULL");
+  if (!st) return fail(STK_EINVAL, "capture needs a stream other than the legacy default stream");
+  DevInfo di;
+  CU(dev_info(di));  // one-time per-device set-up stays outside the capture
+  const cudaEvent_t save0 = g_ev_start, save1 = g_ev_stop;
+  g_ev_start = g_ev_stop = nullptr;
+  CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const stk_status s = call();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &graph);
+  g_ev_start = save0;
+  g_ev_stop = save1;
+  if (s != STK_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess || !graph) return fail(STK_ECUDA, "stream capture failed");
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return fail(STK_ECUDA, "cudaGraphInstantiate failed");
+  *graph_exec = reinterpret_cast<void *>(exec);
+  return STK_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int32_t stokes_tile_config_count(void) { return kNumTileConfigs; }
+
+stk_status stokes_autotune_p2p(const double *pts, const double *f, const double *phi,
+                               const double *nrm, const double *w, const double *h, int64_t n,
+                               const int32_t *leaf_ptr, int32_t nleaf, const int32_t *ulist_ptr,
+                               const int32_t *ulist_idx, int64_t nulist, int32_t kernels,
+                               double mu, double *out, const stk_opts *opts, void *workspace,
+                               size_t workspace_bytes, void *stream, int32_t *best_config,
+                               float *best_ms) {
+  stk_status s = check_opts(opts);
+  if (s != STK_OK) return s;
+  stk_opts o = *opts;
+  o.accumulate = 0;
+  return tune_configs(reinterpret_cast<cudaStream_t>(stream), [&](int32_t c) {
+    o.tile_config = c;
+    return stokes_p2p_leaflists(pts, f, phi, nrm, w, h, n, leaf_ptr, nleaf, ulist_ptr, ulist_idx,
+                                nulist, kernels, mu, out, &o, workspace, workspace_bytes, stream);
+  }, best_config, best_ms);
+}
+
+stk_status stokes_autotune_batched(const double *pts, const double *f, const double *phi,
+                                   const double *nrm, const double *w, const double *h, int64_t n,
+                                   const int64_t *susp_ptr, const int64_t *n_cell, int32_t nsusp,
+                                   double mu, double *out, const stk_opts *opts, void *workspace,
+                                   size_t workspace_bytes, void *stream, int32_t *best_config,
+                                   float *best_ms) {
+  stk_status s = check_opts(opts);
+  if (s != STK_OK) return s;
+  stk_opts o = *opts;
+  o.accumulate = 0;
+  return tune_configs(reinterpret_cast<cudaStream_t>(stream), [&](int32_t c) {
+    o.tile_config = c;
+    return stokes_batched_eval(pts, f, phi, nrm, w, h, n, susp_ptr, n_cell, nsusp, mu, out, &o,
+                               workspace, workspace_bytes, stream);
+  }, best_config, best_ms);
+}
+
+stk_status stokes_p2p_graph_create(const double *pts, const double *f, const double *phi,
+                                   const double *nrm, const double *w, const double *h, int64_t n,
+                                   const int32_t *leaf_ptr, int32_t nleaf,
+                                   const int32_t *ulist_ptr, const int32_t *ulist_idx,
+                                   int64_t nulist, int32_t kernels, double mu, double *out,
+                                   const stk_opts *opts, void *workspace, size_t workspace_bytes,
+                                   void *stream, void **graph_exec) {
+  return capture_graph(reinterpret_cast<cudaStream_t>(stream), [&]() {
+    return stokes_p2p_leaflists(pts, f, phi, nrm, w, h, n, leaf_ptr, nleaf, ulist_ptr, ulist_idx,
+                                nulist, kernels, mu, out, opts, workspace, workspace_bytes,
+                                stream);
+  }, graph_exec);
+}
+
+stk_status stokes_batched_graph_create(const double *pts, const double *f, const double *phi,
+                                       const double *nrm, const double *w, const double *h,
+                                       int64_t n, const int64_t *susp_ptr, const int64_t *n_cell,
+                                       int32_t nsusp, double mu, double *out,
+                                       const stk_opts *opts, void *workspace,
+                                       size_t workspace_bytes, void *stream, void **graph_exec) {
+  return capture_graph(reinterpret_cast<cudaStream_t>(stream), [&]() {
+    return stokes_batched_eval(pts, f, phi, nrm, w, h, n, susp_ptr, n_cell, nsusp, mu, out, opts,
+                               workspace, workspace_bytes, stream);
+  }, graph_exec);
+}
+
+stk_status stokes_graph_launch(void *graph_exec, void *stream) {
+  if (!graph_exec) return fail(STK_EINVAL, "graph_exec is NULL");
+  CU(cudaGraphLaunch(reinterpret_cast<cudaGraphExec_t>(graph_exec),
+                     reinterpret_cast<cudaStream_t>(stream)));
+  count_launches(1);
+  return STK_OK;
+}
+
+stk_status stokes_graph_destroy(void *graph_exec) {
+  if (!graph_exec) return STK_OK;
+  CU(cudaGraphExecDestroy(reinterpret_cast<cudaGraphExec_t>(graph_exec)));
   return STK_OK;
 }
 

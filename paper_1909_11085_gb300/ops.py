@@ -118,6 +118,72 @@ class P2PPlan:
     def device_status(self):
         A.check(A.lib().stokes_device_status(A.ptr(self.ws), self.ws.numel()))
 
+    def _args(self, pts, f, phi, nrm, w, h, mu, out):
+        n = self.n
+        pts = A.vec3(pts, "pts", n)
+        f, phi, nrm = A.vec3(f, "f", n), A.vec3(phi, "phi", n), A.vec3(nrm, "nrm", n)
+        w, h = A.vec1(w, "w", n), A.vec1(h, "h", n)
+        out = A.vec3(out, "out", n)
+        self._keep = (pts, f, phi, nrm, w, h, out)  # graphs read these buffers
+        return (A.ptr(pts), A.ptr(f), A.ptr(phi), A.ptr(nrm), A.ptr(w), A.ptr(h), n,
+                A.ptr(self.leaf_ptr), self.nleaf, A.ptr(self.ulist_ptr), A.ptr(self.ulist_idx),
+                self.ulist_idx.numel(), self.kernels, float(mu), A.ptr(out))
+
+    def autotune(self, pts, f, phi, nrm, w, h=None, mu=1.0, out=None, cache=None):
+        """Picks the fastest work-item shape on these inputs (see tuning.py for the cache)."""
+        from . import tuning
+        key = tuning.key("p2p", self.opts, self.n, self.nleaf, self.kernels)
+        best = tuning.lookup(cache, key)
+        if best is None:
+            out = out if out is not None else torch.empty((self.n, 3), dtype=torch.float64,
+                                                           device=pts.device)
+            cfg, ms = ctypes.c_int32(0), ctypes.c_float(0)
+            self.opts.accumulate = 0
+            with torch.cuda.device(pts.device):
+                A.check(A.lib().stokes_autotune_p2p(*self._args(pts, f, phi, nrm, w, h, mu, out),
+                                                    ctypes.byref(self.opts), A.ptr(self.ws),
+                                                    self.ws.numel(), A.stream_ptr(pts.device),
+                                                    ctypes.byref(cfg), ctypes.byref(ms)))
+            best = int(cfg.value)
+            tuning.store(cache, key, best, float(ms.value))
+        self.opts.tile_config = best
+        return best
+
+    def capture(self, pts, f, phi, nrm, w, h=None, mu=1.0, out=None):
+        """Captures one evaluation into a CUDA graph that replays on the same buffers."""
+        out = out if out is not None else torch.empty((self.n, 3), dtype=torch.float64,
+                                                       device=pts.device)
+        self.opts.accumulate = 0
+        ge = ctypes.c_void_p(0)
+        stream = torch.cuda.Stream(pts.device)
+        with torch.cuda.device(pts.device), torch.cuda.stream(stream):
+            A.check(A.lib().stokes_p2p_graph_create(*self._args(pts, f, phi, nrm, w, h, mu, out),
+                                                    ctypes.byref(self.opts), A.ptr(self.ws),
+                                                    self.ws.numel(), A.stream_ptr(pts.device),
+                                                    ctypes.byref(ge)))
+        return Graph(ge, out, self._keep + (self.ws, self.leaf_ptr, self.ulist_ptr,
+                                            self.ulist_idx))
+
+
+class Graph:
+    """An executable CUDA graph of one library call; launch() replays it on the
+    current stream.  Keeps the buffers it reads alive."""
+
+    def __init__(self, handle, out, keep):
+        self.handle, self.out, self._keep = handle, out, keep
+
+    def launch(self, stream=None):
+        st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        A.check(A.lib().stokes_graph_launch(self.handle, ctypes.c_void_p(st)))
+        return self.out
+
+    def __del__(self):
+        try:
+            if self.handle:
+                A.lib().stokes_graph_destroy(self.handle)
+        except Exception:
+            pass
+
 
 def p2p(pts, f, phi, nrm, w, leaf_ptr, ulist_ptr, ulist_idx, kernels=3, mu=1.0, h=None,
         precision="mixed", near_ratio=1.0, out=None, accumulate=False):
@@ -161,6 +227,50 @@ class BatchedPlan:
 
     def device_status(self):
         A.check(A.lib().stokes_device_status(A.ptr(self.ws), self.ws.numel()))
+
+    def _args(self, pts, f, phi, nrm, w, h, mu, out):
+        n = self.n
+        pts = A.vec3(pts, "pts", n)
+        f, phi, nrm = A.vec3(f, "f", n), A.vec3(phi, "phi", n), A.vec3(nrm, "nrm", n)
+        w, h = A.vec1(w, "w", n), A.vec1(h, "h", n)
+        out = A.vec3(out, "out", n)
+        self._keep = (pts, f, phi, nrm, w, h, out)
+        return (A.ptr(pts), A.ptr(f), A.ptr(phi), A.ptr(nrm), A.ptr(w), A.ptr(h), n,
+                A.ptr(self.susp_ptr), A.ptr(self.n_cell), self.nsusp, float(mu), A.ptr(out))
+
+    def autotune(self, pts, f, phi, nrm, w, h=None, mu=1.0, out=None, cache=None):
+        """Picks the fastest work-item shape on these inputs (see tuning.py for the cache)."""
+        from . import tuning
+        key = tuning.key("batched", self.opts, self.n, self.nsusp, 3)
+        best = tuning.lookup(cache, key)
+        if best is None:
+            out = out if out is not None else torch.empty((self.n, 3), dtype=torch.float64,
+                                                           device=pts.device)
+            cfg, ms = ctypes.c_int32(0), ctypes.c_float(0)
+            self.opts.accumulate = 0
+            with torch.cuda.device(pts.device):
+                A.check(A.lib().stokes_autotune_batched(
+                    *self._args(pts, f, phi, nrm, w, h, mu, out), ctypes.byref(self.opts),
+                    A.ptr(self.ws), self.ws.numel(), A.stream_ptr(pts.device), ctypes.byref(cfg),
+                    ctypes.byref(ms)))
+            best = int(cfg.value)
+            tuning.store(cache, key, best, float(ms.value))
+        self.opts.tile_config = best
+        return best
+
+    def capture(self, pts, f, phi, nrm, w, h=None, mu=1.0, out=None):
+        """Captures one batched evaluation (one persistent engine launch and its
+        staging kernels) into a CUDA graph that replays on the same buffers."""
+        out = out if out is not None else torch.empty((self.n, 3), dtype=torch.float64,
+                                                       device=pts.device)
+        self.opts.accumulate = 0
+        ge = ctypes.c_void_p(0)
+        stream = torch.cuda.Stream(pts.device)
+        with torch.cuda.device(pts.device), torch.cuda.stream(stream):
+            A.check(A.lib().stokes_batched_graph_create(
+                *self._args(pts, f, phi, nrm, w, h, mu, out), ctypes.byref(self.opts),
+                A.ptr(self.ws), self.ws.numel(), A.stream_ptr(pts.device), ctypes.byref(ge)))
+        return Graph(ge, out, self._keep + (self.ws, self.susp_ptr, self.n_cell))
 
 
 def batched(pts, f, phi, nrm, w, susp_ptr, n_cell, mu=1.0, h=None, precision="mixed",

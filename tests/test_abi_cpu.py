@@ -65,3 +65,37 @@ def test_invalid_arguments_rejected_on_host(L):
                             None) == A.STK_OK
     assert L.stokes_p2p_leaflists(None, None, None, None, None, None, 0, None, 0, None, None, 0, 3,
                                   1.0, None, ctypes.byref(o), None, 0, None) == A.STK_OK
+
+
+def test_tile_configs_validated_on_host(L):
+    nb = ctypes.c_size_t(0)
+    n_cfg = L.stokes_tile_config_count()
+    assert n_cfg >= 2
+    sizes = []
+    for c in range(-1, n_cfg):
+        o = A.make_opts(tile_config=c)
+        assert L.stokes_p2p_workspace_size(10000, 50, 3, ctypes.byref(o), ctypes.byref(nb)) == A.STK_OK
+        sizes.append(nb.value)
+    assert min(sizes) > 0
+    for c in (n_cfg, 99, -2):
+        bad = A.make_opts(tile_config=c)
+        assert L.stokes_p2p_workspace_size(4, 1, 3, ctypes.byref(bad), ctypes.byref(nb)) == A.STK_EINVAL
+    # graph and tuning entry points check their handles before touching a device
+    assert L.stokes_graph_launch(None, None) == A.STK_EINVAL
+    assert L.stokes_graph_destroy(None) == A.STK_OK
+
+
+def test_tuning_cache_roundtrip(tmp_path):
+    from paper_1909_11085_gb300 import tuning
+    path = str(tmp_path / "tiles.json")
+    o = A.make_opts()
+    k1 = tuning.key("p2p", o, 1_000_000, 4096, 3)
+    k2 = tuning.key("p2p", o, 1_048_576, 4000, 3)   # same size class
+    k3 = tuning.key("p2p", A.make_opts("fp64"), 1_000_000, 4096, 3)
+    assert k1 == k2 and k1 != k3
+    assert tuning.lookup(path, k1) is None
+    tuning.store(path, k1, 2, 1.5)
+    tuning.store(path, k3, 1, 9.0)
+    assert tuning.lookup(path, k2) == 2 and tuning.lookup(path, k3) == 1
+    assert tuning.lookup(None, k1) is None
+    tuning.store(None, k1, 3, 0.1)  # disabled cache: no-op

@@ -13,8 +13,9 @@ constexpr int kChunk = 64;      // sources staged per chunk (one bulk copy)
 constexpr int kItemMax = 128;   // most targets per work item (32 lanes x 4)
 
 // Work-item shapes the autotuner chooses from: the most targets per item and
-// the lane layout (0: T = 1..4 targets per lane with b = 1, 2 or 4 source
-// slices, chosen per item to limit padding; 1: b = 1, T = ceil(targets/32)).
+// the lane layout (0: T = 3..5 targets per lane with b = 1, 2 or 4 source
+// slices, the fewest target slots that hold the item; 1: the same with at
+// most two slices).
 struct TileConfig {
   int32_t item_max;
   int32_t policy;
@@ -29,7 +30,6 @@ __host__ __device__ inline TileConfig tile_config(int id) {
     default: return TileConfig{128, 0};
   }
 }
-constexpr int kQCap = 16;       // near-pair queue entries per lane
 constexpr int kWarpsPerCta = 4; // engine CTA = 4 independent warps
 
 enum Kind : int { K_SL = 1, K_DL = 2, K_SLDL = 3 };
@@ -81,11 +81,8 @@ struct EngineParams {
   int32_t self_index;        // 1: caller target index == source index means the same point
   int32_t policy;            // lane layout of the tile configuration
   double *part_out;          // [nparts][nt][3], sorted target order
-  int32_t *item_counter;     // work queue head (zeroed before launch)
-  int32_t *near_cnt;         // [nparts][nt][4] fill of each near sub-list
-  int32_t *near_idx;         // [nparts][nt][4][near_sub] source index | kind << 30
-  int32_t near_sub;          // capacity of one sub-list (a power of two)
-  int32_t near_sub_log2;
+  int32_t *item_counter;     // engine work queue head (zeroed before launch)
+  int32_t *near_counter;     // k_near work queue head (zeroed before launch)
   int32_t *err_flag;         // device error word
   int64_t spin_limit;        // bounded mbarrier waits, in SM clock cycles
 };
@@ -104,6 +101,45 @@ __device__ __forceinline__ void split_hl(double v, float &hi, float &lo) {
 __device__ __forceinline__ float to_local(float vh, float vl, float oh, float ol) {
   return __fadd_rn(__fsub_rn(vh, oh), __fsub_rn(vl, ol));
 }
+
+// ---------------------------------------------------------------------------
+// Near/far decisions.  The mixed engine leaves a pair out of its FP32 sum when
+// the pair is near in the item's local frame; k_near later finds the same
+// pairs and adds them in FP64.  Both kernels compute the frame, the local
+// coordinates, the box distance and |r|^2 with the functions below, built only
+// from explicitly rounded operations (no contraction into FMAs the compiler
+// might choose differently), so their decisions agree bit for bit.
+
+// Item origin: centre of the targets' box, as an offset from the first target
+// x0 (mn, mx: box of the targets' FP32 offsets from x0), split hi/lo about the
+// frame centre c.
+__device__ __forceinline__ void frame_origin(double x0, float mn, float mx, double c, float &oh,
+                                             float &ol) {
+  const double org = fma(0.5, __dadd_rn((double)mn, (double)mx), x0);
+  split_hl(__dsub_rn(org, c), oh, ol);
+}
+// Local coordinate of a caller FP64 coordinate v (frame centre c).
+__device__ __forceinline__ float local_coord(double v, double c, float oh, float ol) {
+  float vh, vl;
+  split_hl(__dsub_rn(v, c), vh, vl);
+  return to_local(vh, vl, oh, ol);
+}
+// Squared distance from a local point to the box [lo, hi].
+__device__ __forceinline__ float box_dist2(float y0, float y1, float y2, const float (&lo)[3],
+                                           const float (&hi)[3]) {
+  const float e0 = fmaxf(fmaxf(__fsub_rn(lo[0], y0), __fsub_rn(y0, hi[0])), 0.f);
+  const float e1 = fmaxf(fmaxf(__fsub_rn(lo[1], y1), __fsub_rn(y1, hi[1])), 0.f);
+  const float e2 = fmaxf(fmaxf(__fsub_rn(lo[2], y2), __fsub_rn(y2, hi[2])), 0.f);
+  return __fmaf_rn(e0, e0, __fmaf_rn(e1, e1, __fmul_rn(e2, e2)));
+}
+// |r|^2 of a pair from its local difference.
+__device__ __forceinline__ float pair_r2(float d0, float d1, float d2) {
+  return __fmaf_rn(d0, d0, __fmaf_rn(d1, d1, __fmul_rn(d2, d2)));
+}
+// A staged source is a candidate for near pairs of an item unless its box
+// distance reaches alpha h_j; a candidate pair is near when |r|^2 < (alpha h_j)^2.
+__device__ __forceinline__ bool is_candidate(float bd2, float hh) { return !(bd2 >= hh); }
+__device__ __forceinline__ bool is_near(float r2, float hh) { return r2 < hh; }
 
 // Knuth two-sum accumulation of a partial into (hi, lo).
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p) {

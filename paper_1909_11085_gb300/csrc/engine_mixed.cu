@@ -4,7 +4,7 @@
 //
 // Design (GB300, sm_103a):
 //  * Work unit = one warp-item: up to 128 spatially sorted targets held in
-//    registers (T = 1..4 per lane, b = 1, 2 or 4 source slices per warp)
+//    registers (T = 3..5 per lane, b = 1, 2 or 4 source slices per warp)
 //    against a list of source segments.  Four independent warps per CTA; a
 //    persistent grid pulls items from an atomic queue in cost order, so
 //    uneven items balance without output atomics.
@@ -20,13 +20,11 @@
 //  * Each staged source is classified against the item's bounding box: far
 //    sources (box distance >= alpha h_j) run a branch-free FP32 loop;
 //    candidates run a masked loop in which a pair with |r| < alpha h_j is
-//    left out of the FP32 sum and recorded in its target's near list (four
-//    sub-lists, each written by one lane in program order, so no atomics).
-//    The lists are evaluated afterwards by k_near (FP64 difference and 1/|r|,
-//    FP32 products), whose FP64 work would otherwise stall this FP32 engine.
-//    A pair that does not fit its target's list is evaluated in place the
-//    same way.  The self pair is recorded like any other and contributes
-//    nothing (zero distance).
+//    left out of the FP32 sum (its |r|^2 is replaced by +inf, so rsqrt gives
+//    0).  Nothing is recorded: k_near (near.cu) takes the same decisions with
+//    the same arithmetic afterwards and adds those pairs with the FP64
+//    difference and 1/|r|, whose FP64 work would otherwise stall this FP32
+//    engine.
 //  * Accumulation: plain FP32 within a chunk (<= 64 terms per lane), then a
 //    two-sum into per-target (hi, lo) kept in shared memory.
 //  * The kernel is instantiated per kernel kind (SL, DL, SL+DL, or SL/DL by
@@ -44,19 +42,20 @@ namespace stk {
 #define STK_ENGINE_MIN_BLOCKS 3
 #endif
 
-constexpr int kSegWin = 64;  // segments read into shared memory at a time  // warp-wide near-pair queue: 31 carried + 128 new entries
+constexpr int kSegWin = 64;  // segments read into shared memory at a time
+constexpr int kTMax = 5;     // most targets per lane
 
 struct __align__(16) WarpSmem {
-  SrcRec raw[kChunk];          // bulk-copy destination
-  float4 Y[kChunk];            // local position + hh
-  float4 Q[kChunk];            // SL density (scaled) + source index bits
-  float4 N[kChunk];            // normal
-  float4 Pd[kChunk];           // DL density (scaled)
-  float acc[2 * 4 * 3][kWarp]; // per-lane compensated sums (hi, lo), lane-minor
-  float frame[12];             // item origin (hi x3, lo x3) and bounding box (lo x3, hi x3)
-  int32_t run_s[kSegWin];      // source runs of the current segment window: start
-  int32_t run_e[kSegWin];      //   end
-  int32_t run_k[kSegWin];      //   kernel kind
+  SrcRec raw[kChunk];               // bulk-copy destination
+  float4 Y[kChunk];                 // local position + hh
+  float4 Q[kChunk];                 // SL density (scaled) + source index bits
+  float4 N[kChunk];                 // normal
+  float4 Pd[kChunk];                // DL density (scaled)
+  float acc[2 * kTMax * 3][kWarp];  // per-lane compensated sums (hi, lo), lane-minor
+  float frame[12];                  // item origin (hi x3, lo x3) and bounding box (lo x3, hi x3)
+  int32_t run_s[kSegWin];           // source runs of the current segment window: start
+  int32_t run_e[kSegWin];           //   end
+  int32_t run_k[kSegWin];           //   kernel kind
   unsigned long long mbar;
 };
 
@@ -128,16 +127,14 @@ __device__ __forceinline__ void issue_chunk(WarpSmem &sm, const SrcRec *rec, int
 // SLDL: q/r + d [(d.q)/r^3 + (d.psi)(d.n)/r^5]
 template <int T, int KIND, bool MASKED>
 __device__ __forceinline__ void pair_block(const float (&x)[T][3], float (&ps)[T][3], float4 Y,
-                                           float4 Q, float4 N, float4 Pd, unsigned &nm) {
+                                           float4 Q, float4 N, float4 Pd) {
 #pragma unroll
   for (int t = 0; t < T; ++t) {
-    const float dx = x[t][0] - Y.x, dy = x[t][1] - Y.y, dz = x[t][2] - Y.z;
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (MASKED) {
-      const bool nr = r2 < Y.w;
-      nm |= (unsigned)nr << t;
-      r2 = nr ? __int_as_float(0x7f800000) : r2;  // rsqrt(+inf) = 0: pair removed here
-    }
+    const float dx = __fsub_rn(x[t][0], Y.x), dy = __fsub_rn(x[t][1], Y.y),
+                dz = __fsub_rn(x[t][2], Y.z);
+    float r2 = pair_r2(dx, dy, dz);
+    // near pair: rsqrt(+inf) = 0 removes it from this sum (k_near adds it)
+    if (MASKED && is_near(r2, Y.w)) r2 = __int_as_float(0x7f800000);
     const float ri = rsqrtf(r2);
     const float ri2 = ri * ri;
     if (KIND == K_SL) {
@@ -170,26 +167,10 @@ struct ItemCtx {
   int32_t t0;
 };
 
-// Evaluates in place a near pair that did not fit its target's list.
-template <int KIND>
-__device__ __noinline__ float4 near_overflow(const WarpSmem &sm, const EngineParams &P, int32_t gi,
-                                             int k) {
-  const float4 Q = sm.Q[k];
-  const int j = __float_as_int(Q.w);
-  const int ci = P.tperm ? P.tperm[gi] : gi;
-  float v[3];
-  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (near_contrib(P.trg64 + 3 * (size_t)ci, P.src64 + 3 * (size_t)j, Q, sm.N[k], sm.Pd[k], KIND,
-                   v))
-    r = make_float4(v[0], v[1], v[2], 0.f);
-  return r;
-}
-
 template <int T, int KIND>
 __device__ __forceinline__ void chunk_compute(WarpSmem &sm, const EngineParams &P,
                                               const ItemCtx &ic, int n, int nfar,
-                                              const float (&x)[T][3], float (&ps)[T][3],
-                                              int (&ncnt)[T]) {
+                                              const float (&x)[T][3], float (&ps)[T][3]) {
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   // far sources: no per-pair test
   for (int k = ic.sg; k < nfar; k += ic.b) {
@@ -197,44 +178,20 @@ __device__ __forceinline__ void chunk_compute(WarpSmem &sm, const EngineParams &
     const float4 Q = (KIND & K_SL) ? sm.Q[k] : z4;
     const float4 N = (KIND & K_DL) ? sm.N[k] : z4;
     const float4 Pd = (KIND & K_DL) ? sm.Pd[k] : z4;
-    unsigned nm = 0;
-    pair_block<T, KIND, false>(x, ps, Y, Q, N, Pd, nm);
+    pair_block<T, KIND, false>(x, ps, Y, Q, N, Pd);
   }
-  // candidates: per-pair near test; near pairs are recorded for k_near
+  // candidates: per-pair near test
   for (int k = nfar + ic.sg; k < n; k += ic.b) {
     const float4 Y = sm.Y[k];
-    const float4 Q = sm.Q[k];  // .w carries the source index for near pairs
+    const float4 Q = (KIND & K_SL) ? sm.Q[k] : z4;
     const float4 N = (KIND & K_DL) ? sm.N[k] : z4;
     const float4 Pd = (KIND & K_DL) ? sm.Pd[k] : z4;
-    unsigned nm = 0;
-    pair_block<T, KIND, true>(x, ps, Y, Q, N, Pd, nm);
-    if (nm) {
-      const int j = __float_as_int(Q.w);
-#pragma unroll
-      for (int t = 0; t < T; ++t)
-        if ((nm >> t) & 1u) {
-          // Record the pair in this lane's sub-lists of the target's near list:
-          // sub-lists sg, sg + b, ... < 4, each near_sub entries, filled in order.
-          const int c = ncnt[t]++;
-          const int sub = ic.sg + ic.b * (c >> P.near_sub_log2);
-          const int li = ic.tgl + ic.G * t;
-          if (sub < 4) {
-            const size_t slot = (size_t)ic.part * (size_t)P.nt + (size_t)(ic.t0 + li);
-            P.near_idx[((slot * 4 + sub) << P.near_sub_log2) + (c & (P.near_sub - 1))] =
-                j | (KIND << 30);
-          } else {
-            const float4 v = near_overflow<KIND>(sm, P, ic.t0 + li, k);
-            ps[t][0] += v.x;
-            ps[t][1] += v.y;
-            ps[t][2] += v.z;
-          }
-        }
-    }
+    pair_block<T, KIND, true>(x, ps, Y, Q, N, Pd);
   }
 }
 
 // Converts the staged raw chunk to local coordinates, far sources first.
-__device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, int64_t s0, int lane) {
+__device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, int lane) {
   const float oh[3] = {sm.frame[0], sm.frame[1], sm.frame[2]};
   const float ol[3] = {sm.frame[3], sm.frame[4], sm.frame[5]};
   const float blo[3] = {sm.frame[6], sm.frame[7], sm.frame[8]};
@@ -253,17 +210,11 @@ __device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, int64_t s0, in
       nn = sm.raw[k].n;
       pp = sm.raw[k].p;
       yl4 = make_float4(q.w, nn.w, pp.w, 0.f);
-      q.w = __int_as_float((int)(s0 + k));
-      nn.w = pp.w = 0.f;
       Y.x = to_local(yh.x, yl4.x, oh[0], ol[0]);
       Y.y = to_local(yh.y, yl4.y, oh[1], ol[1]);
       Y.z = to_local(yh.z, yl4.z, oh[2], ol[2]);
       Y.w = yh.w;
-      const float ex = fmaxf(fmaxf(blo[0] - Y.x, Y.x - bhi[0]), 0.f);
-      const float ey = fmaxf(fmaxf(blo[1] - Y.y, Y.y - bhi[1]), 0.f);
-      const float ez = fmaxf(fmaxf(blo[2] - Y.z, Y.z - bhi[2]), 0.f);
-      const float bd2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-      cand = !(bd2 >= Y.w);
+      cand = is_candidate(box_dist2(Y.x, Y.y, Y.z, blo, bhi), Y.w);
     }
     const unsigned bc = __ballot_sync(kFull, valid && cand);
     const unsigned bf = __ballot_sync(kFull, valid && !cand);
@@ -367,14 +318,13 @@ __device__ __forceinline__ bool cursor_next(const EngineParams &P, const Item &i
 template <int T, int KMODE>
 __device__ __forceinline__ void dispatch_compute(int kind, WarpSmem &sm, const EngineParams &P,
                                                  const ItemCtx &ic, int n, int nfar,
-                                                 const float (&x)[T][3], float (&ps)[T][3],
-                                                 int (&ncnt)[T]) {
+                                                 const float (&x)[T][3], float (&ps)[T][3]) {
   if (KMODE != 0) {
-    chunk_compute<T, KMODE>(sm, P, ic, n, nfar, x, ps, ncnt);
+    chunk_compute<T, KMODE>(sm, P, ic, n, nfar, x, ps);
   } else if (kind == K_SL) {
-    chunk_compute<T, K_SL>(sm, P, ic, n, nfar, x, ps, ncnt);
+    chunk_compute<T, K_SL>(sm, P, ic, n, nfar, x, ps);
   } else {
-    chunk_compute<T, K_DL>(sm, P, ic, n, nfar, x, ps, ncnt);
+    chunk_compute<T, K_DL>(sm, P, ic, n, nfar, x, ps);
   }
 }
 
@@ -415,14 +365,9 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     }
   }
   float oh[3], ol[3];
-  {
-    const double org[3] = {x0 + 0.5 * ((double)warp_min(mn[0]) + (double)warp_max(mx[0])),
-                           y0 + 0.5 * ((double)warp_min(mn[1]) + (double)warp_max(mx[1])),
-                           z0 + 0.5 * ((double)warp_min(mn[2]) + (double)warp_max(mx[2]))};
-    split_hl(org[0] - cx, oh[0], ol[0]);
-    split_hl(org[1] - cy, oh[1], ol[1]);
-    split_hl(org[2] - cz, oh[2], ol[2]);
-  }
+  frame_origin(x0, warp_min(mn[0]), warp_max(mx[0]), cx, oh[0], ol[0]);
+  frame_origin(y0, warp_min(mn[1]), warp_max(mx[1]), cy, oh[1], ol[1]);
+  frame_origin(z0, warp_min(mn[2]), warp_max(mx[2]), cz, oh[2], ol[2]);
   float x[T][3];
   float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
   const double cc[3] = {cx, cy, cz};
@@ -434,9 +379,7 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       if (valid[t]) {
-        float vh, vl;
-        split_hl(xp[k] - cc[k], vh, vl);
-        x[t][k] = to_local(vh, vl, oh[k], ol[k]);
+        x[t][k] = local_coord(xp[k], cc[k], oh[k], ol[k]);
         blo[k] = fminf(blo[k], x[t][k]);
         bhi[k] = fmaxf(bhi[k], x[t][k]);
       } else {
@@ -469,9 +412,6 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
       sm.acc[(T + t) * 3 + k][lane] = 0.f;
     }
 
-  int ncnt[T];
-#pragma unroll
-  for (int t = 0; t < T; ++t) ncnt[t] = 0;
   Cursor cur;
   cur.e0 = it.seg0;
   cur.kind = KMODE;
@@ -482,11 +422,9 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     have = cursor_next<KMODE>(P, it, sm, cur, lane);
   }
   int n_cur = 0, kind_cur = 0;
-  int64_t s_cur = 0;
   if (have) {
     n_cur = (int)min((int64_t)kChunk, cur.end - cur.s);
     kind_cur = cur.kind;
-    s_cur = cur.s;
     issue_chunk(sm, P.rec, cur.s, n_cur, lane);
     cur.s += n_cur;
   }
@@ -500,19 +438,17 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
       break;
     }
     phase ^= 1u;
-    const int nfar = convert_chunk(sm, n_cur, s_cur, lane);
+    const int nfar = convert_chunk(sm, n_cur, lane);
     __syncwarp();
     const bool have_next = cursor_next<KMODE>(P, it, sm, cur, lane);
     int n_next = 0, kind_next = 0;
-    int64_t s_next = 0;
     if (have_next) {
       n_next = (int)min((int64_t)kChunk, cur.end - cur.s);
       kind_next = cur.kind;
-      s_next = cur.s;
       issue_chunk(sm, P.rec, cur.s, n_next, lane);
       cur.s += n_next;
     }
-    dispatch_compute<T, KMODE>(kind_cur, sm, P, ic, n_cur, nfar, x, ps, ncnt);
+    dispatch_compute<T, KMODE>(kind_cur, sm, P, ic, n_cur, nfar, x, ps);
 #pragma unroll
     for (int t = 0; t < T; ++t)
 #pragma unroll
@@ -527,19 +463,8 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     have = have_next;
     n_cur = n_next;
     kind_cur = kind_next;
-    s_cur = s_next;
   }
   if (!ok) return false;
-  // near-list fill: each lane writes the counts of the sub-lists it owns
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    if (valid[t]) {
-      const int li = ic.tgl + ic.G * t;
-      int32_t *cnt = P.near_cnt + ((size_t)part * (size_t)P.nt + (size_t)(it.t0 + li)) * 4;
-      for (int sub = ic.sg, i = 0; sub < 4; sub += ic.b, ++i)
-        cnt[sub] = min(P.near_sub, max(0, ncnt[t] - i * P.near_sub));
-    }
-  }
   float hi[T][3], lo[T][3];
 #pragma unroll
   for (int t = 0; t < T; ++t)
@@ -597,31 +522,17 @@ __global__ void __launch_bounds__(kWarpsPerCta *kWarp, STK_ENGINE_MIN_BLOCKS) k_
     const Item it = P.items[id];
     const int tn = it.tn_part & 0xFF;
     bool ok;
-    if (P.policy == 1) {  // one source slice, T = ceil(tn / 32)
-      if (tn <= 32)
-        ok = run_item<1, KMODE>(P, it, sm, 1, phase, lane);
-      else if (tn <= 64)
-        ok = run_item<2, KMODE>(P, it, sm, 1, phase, lane);
-      else if (tn <= 96)
-        ok = run_item<3, KMODE>(P, it, sm, 1, phase, lane);
-      else
-        ok = run_item<4, KMODE>(P, it, sm, 1, phase, lane);
-    } else if (tn <= 8)
-      ok = run_item<1, KMODE>(P, it, sm, 4, phase, lane);
-    else if (tn <= 16)
-      ok = run_item<2, KMODE>(P, it, sm, 4, phase, lane);
-    else if (tn <= 24)
-      ok = run_item<3, KMODE>(P, it, sm, 4, phase, lane);
-    else if (tn <= 32)
-      ok = run_item<4, KMODE>(P, it, sm, 4, phase, lane);
-    else if (tn <= 48)
-      ok = run_item<3, KMODE>(P, it, sm, 2, phase, lane);
-    else if (tn <= 64)
-      ok = run_item<4, KMODE>(P, it, sm, 2, phase, lane);
-    else if (tn <= 96)
-      ok = run_item<3, KMODE>(P, it, sm, 1, phase, lane);
+    // Lane layout: T = 3, 4 or 5 targets per lane and b source slices, the
+    // fewest target slots (32 T / b) that hold the item.  Policy 1 uses no
+    // more than two slices.
+    const int b = (P.policy != 1 && tn <= 40) ? 4 : (tn <= 80 ? 2 : 1);
+    const int slots_per_t = kWarp / b;
+    if (tn <= 3 * slots_per_t)
+      ok = run_item<3, KMODE>(P, it, sm, b, phase, lane);
+    else if (tn <= 4 * slots_per_t)
+      ok = run_item<4, KMODE>(P, it, sm, b, phase, lane);
     else
-      ok = run_item<4, KMODE>(P, it, sm, 1, phase, lane);
+      ok = run_item<5, KMODE>(P, it, sm, b, phase, lane);
     if (!ok) break;
   }
 }

@@ -398,94 +398,6 @@ __global__ void k_batched_emit(int32_t nsusp, const int64_t *__restrict__ susp_p
   }
 }
 
-// ---------------------------------------------------------------- near pairs
-// Evaluates the near lists recorded by the mixed engine.  A warp takes 32
-// consecutive (part, target) slots; their entries are enumerated slot by
-// slot (each slot: sub-lists 0..3, each in recording order) and evaluated
-// 128 per round with every lane busy, so the FP64 pipe (the bound of this
-// kernel: difference x - y, r^2 and the Newton step for 1/|r|, and the
-// conversions) is not left idle by uneven list lengths.  Each slot's owner
-// lane then adds its contributions in list order with a two-sum, so the
-// result is deterministic, and adds (hi + lo) to the slot's partial result.
-constexpr int kNearWarps = 4;
-constexpr int kNearPerLane = 4;
-constexpr int kNearRound = kWarp * kNearPerLane;
-
-__global__ void __launch_bounds__(kNearWarps *kWarp) k_near(
-    int64_t nslots, int64_t nt, const int4 *__restrict__ near_cnt,
-    const int32_t *__restrict__ near_idx, int32_t sub_log2, const SrcRec *__restrict__ rec,
-    const double *__restrict__ src64, const double *__restrict__ trg64,
-    const int32_t *__restrict__ tperm, double *__restrict__ part_out) {
-  __shared__ int32_t s_off[kNearWarps][kWarp + 1];
-  __shared__ int4 s_n[kNearWarps][kWarp];
-  __shared__ int64_t s_ci[kNearWarps][kWarp];
-  __shared__ float s_c[kNearWarps][kNearRound][3];
-  const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  const int64_t stride = (int64_t)gridDim.x * kNearWarps * kWarp;
-  for (int64_t base = ((int64_t)blockIdx.x * kNearWarps + warp) * kWarp; base < nslots;
-       base += stride) {
-    const int64_t i = base + lane;
-    const int4 c = i < nslots ? near_cnt[i] : make_int4(0, 0, 0, 0);
-    const int tot = c.x + c.y + c.z + c.w;
-    int incl = tot;
-#pragma unroll
-    for (int o = 1; o < kWarp; o <<= 1) {
-      const int v = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += v;
-    }
-    const int total = __shfl_sync(kFull, incl, kWarp - 1);
-    if (total == 0) continue;
-    const int excl = incl - tot;
-    s_off[warp][lane] = excl;
-    if (lane == 0) s_off[warp][kWarp] = total;
-    s_n[warp][lane] = c;
-    const int64_t ti = i < nslots ? i % nt : 0;
-    s_ci[warp][lane] = tperm ? (int64_t)tperm[ti] : ti;
-    __syncwarp();
-    float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
-    for (int rb = 0; rb < total; rb += kNearRound) {
-#pragma unroll
-      for (int q = 0; q < kNearPerLane; ++q) {
-        const int g = rb + lane + kWarp * q;
-        float v[3] = {0.f, 0.f, 0.f};
-        if (g < total) {
-          int L = 0;  // owner: last lane whose offset is <= g
-#pragma unroll
-          for (int step = 16; step > 0; step >>= 1)
-            if (L + step < kWarp && s_off[warp][L + step] <= g) L += step;
-          int local = g - s_off[warp][L];
-          const int4 cn = s_n[warp][L];
-          int sub = 0;
-          if (local >= cn.x) { local -= cn.x; sub = 1;
-            if (local >= cn.y) { local -= cn.y; sub = 2;
-              if (local >= cn.z) { local -= cn.z; sub = 3; } } }
-          const uint32_t e = (uint32_t)near_idx[(((base + L) * 4 + sub) << sub_log2) + local];
-          const int64_t j = e & 0x3fffffffu;
-          const SrcRec R = rec[j];
-          if (!near_contrib(trg64 + 3 * s_ci[warp][L], src64 + 3 * j, R.q, R.n, R.p,
-                            (int)(e >> 30), v))
-            v[0] = v[1] = v[2] = 0.f;
-        }
-        s_c[warp][lane + kWarp * q][0] = v[0];
-        s_c[warp][lane + kWarp * q][1] = v[1];
-        s_c[warp][lane + kWarp * q][2] = v[2];
-      }
-      __syncwarp();
-      const int g1 = min(excl + tot, rb + kNearRound);
-      for (int g = max(excl, rb); g < g1; ++g)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) two_sum_acc(hi[k], lo[k], s_c[warp][g - rb][k]);
-      __syncwarp();
-    }
-    if (i < nslots && tot > 0) {
-      double *o = part_out + 3 * i;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) o[k] += (double)hi[k] + (double)lo[k];
-    }
-    __syncwarp();
-  }
-}
-
 // ---------------------------------------------------------------- finish
 // out[perm[i]] (+)= sum over parts of part_out[p][i], parts added in order.
 __global__ void k_finish(int64_t nt, int32_t nparts, const double *__restrict__ part_out,
@@ -589,21 +501,6 @@ void launch_batched_items(int32_t nsusp, const int64_t *susp_ptr, const int64_t 
   count_launches(1);
   k_batched_emit<<<grid_for(nsusp, 128), 128, 0, st>>>(nsusp, susp_ptr, n_cell, item_max, offs,
                                                        items, range_ptr, keys, vals);
-  count_launches(1);
-}
-
-void launch_near(int64_t nt, int32_t nparts, const int32_t *near_cnt, const int32_t *near_idx,
-                 int32_t sub_log2, const SrcRec *rec, const double *src64, const double *trg64,
-                 const int32_t *tperm, double *part_out, int sms, cudaStream_t st) {
-  const int64_t nslots = nt * nparts;
-  const int64_t need = (nslots + kNearWarps * kWarp - 1) / (kNearWarps * kWarp);
-  int64_t grid = (int64_t)sms * 16;
-  if (grid > need) grid = need;
-  if (grid < 1) grid = 1;
-  k_near<<<(int)grid, kNearWarps * kWarp, 0, st>>>(nslots, nt,
-                                                   reinterpret_cast<const int4 *>(near_cnt),
-                                                   near_idx, sub_log2, rec, src64, trg64, tperm,
-                                                   part_out);
   count_launches(1);
 }
 

@@ -33,9 +33,8 @@ void launch_batched_items(int32_t nsusp, const int64_t *susp_ptr, const int64_t 
                           int32_t item_max, int32_t *cnt, int32_t *offs, int32_t *n_items,
                           Item *items, int64_t *range_ptr, uint64_t *keys, int32_t *vals,
                           cudaStream_t st);
-void launch_near(int64_t nt, int32_t nparts, const int32_t *near_cnt, const int32_t *near_idx,
-                 int32_t sub_log2, const SrcRec *rec, const double *src64, const double *trg64,
-                 const int32_t *tperm, double *part_out, int sms, cudaStream_t st);
+// Near pairs of the mixed engine's items (near.cu); runs after the engine.
+void launch_near(const EngineParams &P, int sms, int64_t max_items, cudaStream_t st);
 void launch_finish(int64_t nt, int32_t nparts, const double *part_out, const int32_t *tperm,
                    int32_t accumulate, double *out, cudaStream_t st);
 void launch_zero_ints(int32_t *p, int n, cudaStream_t st);

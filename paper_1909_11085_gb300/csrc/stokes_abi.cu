@@ -2,14 +2,16 @@
 // validation, workspace planning and the launch sequence of every form.
 //
 // Launch sequence (all on the caller's stream, nothing allocated):
-//   1. zero the workspace counters (item queue head, item count, error word);
-//   2. pack the sources (mixed 80-byte or FP64 96-byte records);
+//   1. zero the workspace counters (item count, engine and near-pair queue
+//      heads, error word);
+//   2. pack the sources (mixed 64-byte or FP64 96-byte records);
 //   3. MIXED direct/batched: bounding box + Morton keys + stable radix sort of
 //      the targets, so that every 128-target work item is spatially compact;
 //   4. build work items (direct: target chunks x source splits; near field:
 //      leaf chunks x U-list; batched: suspension chunks x {cells, wall}) and,
 //      where items are uneven, radix-sort them by descending cost;
 //   5. one persistent engine launch (SMs x resident CTAs, 4 warps each);
+//      MIXED: then k_near adds the near pairs the engine left out, in FP64;
 //   6. reduce the source splits in fixed order and scatter to caller order.
 #include <cfloat>
 #include <cmath>
@@ -101,8 +103,6 @@ struct Plan {
   bool sort_items = false;
   int32_t ngroup = 0;
   // offsets (the counters always sit at offset 0 of the aligned workspace)
-  int32_t near_cap = 0;  // entries per near sub-list
-  size_t near_cnt = 0, near_idx = 0;
   size_t counters, rec, keys_a, keys_b, vals_a, vals_b, ikeys_a, ikeys_b, ivals_a, ivals_b, hist,
       hist_scan, bbox_part, bbox, items, range, cnt, offs, part, total;
 };
@@ -117,16 +117,6 @@ int auto_splits(int64_t nt, int64_t ns, const DevInfo &di, int occ) {
   if (s > 64) s = 64;
   if (s < 1) s = 1;
   return (int)s;
-}
-
-// Near-list capacity per target (four sub-lists of this many entries): about
-// 12 alpha^2 pairs are expected on a surface sampled at spacing h; pairs that
-// do not fit are evaluated in place by the engine.
-int32_t near_sub_capacity(double alpha) {
-  const double c = std::ceil((8.0 + 12.0 * alpha * alpha) / 4.0);
-  int32_t p2 = 2;
-  while (p2 < c && p2 < 32) p2 *= 2;
-  return p2;
 }
 
 void layout(Plan &p) {
@@ -153,11 +143,6 @@ void layout(Plan &p) {
   p.cnt = a.take(sizeof(int32_t) * (size_t)(p.ngroup + 1));
   p.offs = a.take(sizeof(int32_t) * (size_t)(p.ngroup + 2));
   p.part = a.take(sizeof(double) * 3 * (size_t)p.nt * (size_t)p.nsplit);
-  if (p.mixed) {
-    p.near_cnt = a.take(sizeof(int32_t) * 4 * (size_t)p.nt * (size_t)p.nsplit);
-    p.near_idx =
-        a.take(sizeof(int32_t) * 4 * (size_t)p.nt * (size_t)p.nsplit * (size_t)p.near_cap);
-  }
   p.total = a.off + 256;  // slack for re-alignment of an unaligned base
 }
 
@@ -167,7 +152,6 @@ stk_status plan_direct(int64_t ns, int64_t nt, const stk_opts *o, Plan &p) {
   p.form = F_DIRECT;
   p.mixed = o->precision == STK_MIXED;
   p.tile = tile_config(o->tile_config < 0 ? 0 : o->tile_config);
-  p.near_cap = near_sub_capacity(o->near_ratio);
   p.ns = ns;
   p.nt = nt;
   const int occ = p.mixed ? di.occ_mixed : di.occ_fp64;
@@ -187,7 +171,6 @@ stk_status plan_p2p(int64_t n, int32_t nleaf, const stk_opts *o, Plan &p) {
   p.form = F_P2P;
   p.mixed = o->precision == STK_MIXED;
   p.tile = tile_config(o->tile_config < 0 ? 0 : o->tile_config);
-  p.near_cap = near_sub_capacity(o->near_ratio);
   p.ns = p.nt = n;
   p.nsplit = 1;
   p.max_items = (int64_t)nleaf + n / kMinItemMax + 1;
@@ -203,7 +186,6 @@ stk_status plan_batched(int64_t n, int32_t nsusp, const stk_opts *o, Plan &p) {
   p.form = F_BATCHED;
   p.mixed = o->precision == STK_MIXED;
   p.tile = tile_config(o->tile_config < 0 ? 0 : o->tile_config);
-  p.near_cap = near_sub_capacity(o->near_ratio);
   p.ns = p.nt = n;
   p.nsplit = 1;
   p.max_items = (int64_t)nsusp + n / kMinItemMax + 1;
@@ -248,6 +230,7 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   P.n_items = counters + 0;
   P.item_counter = counters + 1;
   P.err_flag = counters + 2;
+  P.near_counter = counters + 3;
   P.spin_limit = kSpinLimit;
   P.policy = p.tile.policy;
   P.part_out = at<double>(ws, p.part);
@@ -257,13 +240,6 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   const int64_t need = (p.max_items + kWarpsPerCta - 1) / kWarpsPerCta;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  if (p.mixed) {
-    P.near_cnt = at<int32_t>(ws, p.near_cnt);  // every item writes its targets' counts
-    P.near_idx = at<int32_t>(ws, p.near_idx);
-    P.near_sub = p.near_cap;
-    P.near_sub_log2 = 0;
-    while ((1 << P.near_sub_log2) < P.near_sub) ++P.near_sub_log2;
-  }
   if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_start, st));
   if (p.mixed) {
     P.rec = at<SrcRec>(ws, p.rec);
@@ -274,8 +250,7 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   }
   if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_stop, st));
   if (p.mixed) {
-    launch_near(p.nt, p.nsplit, P.near_cnt, P.near_idx, P.near_sub_log2, P.rec, P.src64, P.trg64,
-                P.tperm, P.part_out, di.sms, st);
+    launch_near(P, di.sms, p.max_items, st);
     CU(cudaGetLastError());
   }
   return STK_OK;

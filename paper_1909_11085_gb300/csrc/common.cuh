@@ -83,6 +83,12 @@ struct EngineParams {
   double *part_out;          // [nparts][nt][3], sorted target order
   int32_t *item_counter;     // engine work queue head (zeroed before launch)
   int32_t *near_counter;     // k_near work queue head (zeroed before launch)
+  float *frames;             // MIXED: per item, the engine's local frame (origin hi x3,
+                             //   lo x3, target box lo x3, hi x3) for k_near
+  float *xloc;               // MIXED: [nt][3] targets in their item's local frame
+  int32_t *cand_list;        // MIXED: per item, up to cand_cap candidate sources (index | kind << 30)
+  int32_t *cand_cnt;         // MIXED: per item, candidates listed (-1: more than cand_cap)
+  int32_t cand_cap;
   int32_t *err_flag;         // device error word
   int64_t spin_limit;        // bounded mbarrier waits, in SM clock cycles
 };

@@ -191,7 +191,11 @@ __device__ __forceinline__ void chunk_compute(WarpSmem &sm, const EngineParams &
 }
 
 // Converts the staged raw chunk to local coordinates, far sources first.
-__device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, int lane) {
+// Candidates are also listed for k_near (source index | kind << 30, at most
+// cap per item; ccount keeps counting past cap to flag an overflow).
+__device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, int lane, int32_t *clist,
+                                             int cap, int &ccount, int32_t s0,
+                                             uint32_t kind_bits) {
   const float oh[3] = {sm.frame[0], sm.frame[1], sm.frame[2]};
   const float ol[3] = {sm.frame[3], sm.frame[4], sm.frame[5]};
   const float blo[3] = {sm.frame[6], sm.frame[7], sm.frame[8]};
@@ -218,6 +222,11 @@ __device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, int lane) {
     }
     const unsigned bc = __ballot_sync(kFull, valid && cand);
     const unsigned bf = __ballot_sync(kFull, valid && !cand);
+    if (valid && cand) {
+      const int rank = ccount + __popc(bc & lt);
+      if (rank < cap) clist[rank] = (int32_t)((uint32_t)(s0 + k) | kind_bits);
+    }
+    ccount += __popc(bc);
     if (valid) {
       const int dst = cand ? (n - 1 - (ncand + __popc(bc & lt))) : (nfar + __popc(bf & lt));
       sm.Y[dst] = Y;
@@ -330,7 +339,7 @@ __device__ __forceinline__ void dispatch_compute(int kind, WarpSmem &sm, const E
 
 // One work item with T targets per lane and b source slices per warp.
 template <int T, int KMODE>
-__device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, int b,
+__device__ bool run_item(const EngineParams &P, const Item &it, int id, WarpSmem &sm, int b,
                          uint32_t &phase, int lane) {
   ItemCtx ic;
   ic.lane = lane;
@@ -393,13 +402,24 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     bhi[k] = warp_max(bhi[k]);
   }
   if (lane == 0) {
+    float *fr = P.frames + 12 * (size_t)id;  // k_near decides in this same frame
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      sm.frame[k] = oh[k];
-      sm.frame[3 + k] = ol[k];
-      sm.frame[6 + k] = blo[k];
-      sm.frame[9 + k] = bhi[k];
+      sm.frame[k] = fr[k] = oh[k];
+      sm.frame[3 + k] = fr[3 + k] = ol[k];
+      sm.frame[6 + k] = fr[6 + k] = blo[k];
+      sm.frame[9 + k] = fr[9 + k] = bhi[k];
     }
+  }
+  if (part == 0) {
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+      if (valid[t] && ic.sg == 0) {
+        float *xl = P.xloc + 3 * (size_t)(it.t0 + ic.tgl + ic.G * t);
+        xl[0] = x[t][0];
+        xl[1] = x[t][1];
+        xl[2] = x[t][2];
+      }
   }
 
   float ps[T][3];
@@ -422,9 +442,13 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     have = cursor_next<KMODE>(P, it, sm, cur, lane);
   }
   int n_cur = 0, kind_cur = 0;
+  int32_t s_cur = 0;
+  int ccount = 0;
+  int32_t *clist = P.cand_list + (size_t)id * (size_t)P.cand_cap;
   if (have) {
     n_cur = (int)min((int64_t)kChunk, cur.end - cur.s);
     kind_cur = cur.kind;
+    s_cur = (int32_t)cur.s;
     issue_chunk(sm, P.rec, cur.s, n_cur, lane);
     cur.s += n_cur;
   }
@@ -438,13 +462,16 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
       break;
     }
     phase ^= 1u;
-    const int nfar = convert_chunk(sm, n_cur, lane);
+    const int nfar = convert_chunk(sm, n_cur, lane, clist, P.cand_cap, ccount, s_cur,
+                                   (uint32_t)kind_cur << 30);
     __syncwarp();
     const bool have_next = cursor_next<KMODE>(P, it, sm, cur, lane);
     int n_next = 0, kind_next = 0;
+    int32_t s_next = 0;
     if (have_next) {
       n_next = (int)min((int64_t)kChunk, cur.end - cur.s);
       kind_next = cur.kind;
+      s_next = (int32_t)cur.s;
       issue_chunk(sm, P.rec, cur.s, n_next, lane);
       cur.s += n_next;
     }
@@ -463,8 +490,10 @@ __device__ bool run_item(const EngineParams &P, const Item &it, WarpSmem &sm, in
     have = have_next;
     n_cur = n_next;
     kind_cur = kind_next;
+    s_cur = s_next;
   }
   if (!ok) return false;
+  if (lane == 0) P.cand_cnt[id] = ccount <= P.cand_cap ? ccount : -1;
   float hi[T][3], lo[T][3];
 #pragma unroll
   for (int t = 0; t < T; ++t)
@@ -528,11 +557,11 @@ __global__ void __launch_bounds__(kWarpsPerCta *kWarp, STK_ENGINE_MIN_BLOCKS) k_
     const int b = (P.policy != 1 && tn <= 40) ? 4 : (tn <= 80 ? 2 : 1);
     const int slots_per_t = kWarp / b;
     if (tn <= 3 * slots_per_t)
-      ok = run_item<3, KMODE>(P, it, sm, b, phase, lane);
+      ok = run_item<3, KMODE>(P, it, id, sm, b, phase, lane);
     else if (tn <= 4 * slots_per_t)
-      ok = run_item<4, KMODE>(P, it, sm, b, phase, lane);
+      ok = run_item<4, KMODE>(P, it, id, sm, b, phase, lane);
     else
-      ok = run_item<5, KMODE>(P, it, sm, b, phase, lane);
+      ok = run_item<5, KMODE>(P, it, id, sm, b, phase, lane);
     if (!ok) break;
   }
 }

@@ -10,8 +10,11 @@
 // exactly one of the two kernels.
 //
 // One warp per item, persistent, items in the engine's cost order:
-//  1. the item's targets (lane + 32 t) in the item's local frame;
-//  2. its sources, 32 at a time: local coordinates and the box test; each
+//  1. the item's frame and its targets' local coordinates, as the engine
+//     stored them (so the decisions below match the engine's bit for bit);
+//  2. its sources, 32 per round across segment boundaries: a conservative box
+//     test on the 16-byte position record alone, then for the few sources it
+//     keeps, the exact local coordinates and the engine's box test; each
 //     candidate is broadcast and every lane tests its targets;
 //  3. near pairs go to a queue in shared memory in a fixed order; a full
 //     queue is evaluated one pair per lane (the FP64 pipe of GB300 runs at
@@ -29,26 +32,20 @@ namespace stk {
 namespace {
 
 constexpr int kNearWarps = 4;
+constexpr int kNearMinBlocks = 5;
 constexpr int kNearT = kItemMax / kWarp;  // targets per lane
 constexpr int kNearQueue = 256;           // >= 128 free slots before each candidate
+constexpr int kNearSegWin = 64;           // segments per window
 
 struct __align__(16) NearSmem {
-  float sv[kWarp][3];           // values of one round of evaluations
-  float acc[2][3][kItemMax];    // per-target compensated sums (hi, lo)
-  int32_t qj[kNearQueue];       // queued pair: source index | kind << 30
-  uint8_t qt[kNearQueue];       //   target within the item
+  float sv[kWarp][3];                // values of one round of evaluations
+  float acc[2][3][kItemMax];         // per-target compensated sums (hi, lo)
+  int32_t qj[kNearQueue];            // queued pair: source index | kind << 30
+  uint8_t qt[kNearQueue];            //   target within the item
+  int64_t seg_start[kNearSegWin];    // window of segments: first source,
+  int32_t seg_pre[kNearSegWin + 1];  //   sources before it in the window,
+  int32_t seg_kind[kNearSegWin];     //   kind bits
 };
-
-__device__ __forceinline__ float warp_min_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
-  return v;
-}
-__device__ __forceinline__ float warp_max_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-  return v;
-}
 
 // Evaluates the queued pairs, one per lane per round, and adds each value to
 // its target's sum; pairs of one target are added in queue order.
@@ -86,113 +83,179 @@ __device__ void eval_queue(NearSmem &sm, const EngineParams &P, int32_t t0, int 
   }
 }
 
-__global__ void __launch_bounds__(kNearWarps *kWarp) k_near(EngineParams P) {
+__global__ void __launch_bounds__(kNearWarps *kWarp, kNearMinBlocks) k_near(EngineParams P) {
   __shared__ NearSmem smem[kNearWarps];
   NearSmem &sm = smem[threadIdx.x / kWarp];
   const int lane = threadIdx.x & (kWarp - 1);
   const unsigned lt = (1u << lane) - 1u;
   const int n_items = *P.n_items;
-  const double cc[3] = {P.src64[0], P.src64[1], P.src64[2]};
+  if (*P.err_flag) return;  // the engine stopped early: its lists are incomplete
   while (true) {
     int idx = 0;
     if (lane == 0) idx = atomicAdd(P.near_counter, 1);
     idx = __shfl_sync(kFull, idx, 0);
     if (idx >= n_items) break;
-    const Item it = P.items[P.item_order ? P.item_order[idx] : idx];
+    const int32_t id = P.item_order ? P.item_order[idx] : idx;
+    const Item it = P.items[id];
     const int tn = it.tn_part & 0xFF, part = it.tn_part >> 8;
 
-    // 1. targets and the item frame, as the engine builds them
-    const int64_t c0 = P.tperm ? P.tperm[it.t0] : it.t0;
-    const double x0[3] = {P.trg64[3 * c0], P.trg64[3 * c0 + 1], P.trg64[3 * c0 + 2]};
-    bool valid[kNearT];
-    int64_t ci[kNearT];
-    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    // 1. the engine's frame and target coordinates
+    const float *fr = P.frames + 12 * (size_t)id;
+    float oh[3], ol[3], blo[3], bhi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      oh[k] = fr[k];
+      ol[k] = fr[3 + k];
+      blo[k] = fr[6 + k];
+      bhi[k] = fr[9 + k];
+    }
+    const float tol0 = 4.8e-7f * (fabsf(oh[0]) + fabsf(oh[1]) + fabsf(oh[2]));
+    int32_t self_id[kNearT];  // caller index of each target when targets are the sources
+    float x[kNearT][3];
 #pragma unroll
     for (int t = 0; t < kNearT; ++t) {
       const int li = lane + kWarp * t;
-      valid[t] = li < tn;
-      ci[t] = -1;
-      if (valid[t]) {
+      self_id[t] = -1;
+      x[t][0] = x[t][1] = x[t][2] = 1e30f;  // padding: never near (|r|^2 = inf)
+      if (li < tn) {
         const int32_t gi = it.t0 + li;
-        ci[t] = P.tperm ? P.tperm[gi] : gi;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const float rk = __double2float_rn(P.trg64[3 * ci[t] + k] - x0[k]);
-          mn[k] = fminf(mn[k], rk);
-          mx[k] = fmaxf(mx[k], rk);
-        }
+        if (P.self_index) self_id[t] = P.tperm ? P.tperm[gi] : gi;
+        const float *xl = P.xloc + 3 * (size_t)gi;
+        x[t][0] = xl[0];
+        x[t][1] = xl[1];
+        x[t][2] = xl[2];
       }
-    }
-    float oh[3], ol[3], blo[3], bhi[3], x[kNearT][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) frame_origin(x0[k], warp_min_f(mn[k]), warp_max_f(mx[k]), cc[k], oh[k], ol[k]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      blo[k] = INFINITY;
-      bhi[k] = -INFINITY;
-    }
-#pragma unroll
-    for (int t = 0; t < kNearT; ++t)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        x[t][k] = 1e30f;
-        if (valid[t]) {
-          x[t][k] = local_coord(P.trg64[3 * ci[t] + k], cc[k], oh[k], ol[k]);
-          blo[k] = fminf(blo[k], x[t][k]);
-          bhi[k] = fmaxf(bhi[k], x[t][k]);
-        }
-      }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      blo[k] = warp_min_f(blo[k]);
-      bhi[k] = warp_max_f(bhi[k]);
     }
     for (int li = lane; li < tn; li += kWarp)
 #pragma unroll
       for (int k = 0; k < 3; ++k) sm.acc[0][k][li] = sm.acc[1][k][li] = 0.f;
-    __syncwarp();
 
-    // 2./3. sources: box test, per-pair test of the candidates, queue
+    // 2./3. candidate sources: each is broadcast and every lane tests its
+    // targets; near pairs are queued (by lane, then target slot)
     int qn = 0;
-    for (int32_t e = it.seg0; e < it.seg1; ++e) {
-      const int32_t sid = P.seg_list ? P.seg_list[e] : e;
-      const int64_t s0 = P.range_ptr[sid], s1 = P.range_ptr[sid + 1];
-      const uint32_t kind_bits = (uint32_t)seg_kind(P, sid) << 30;
-      for (int64_t j0 = s0; j0 < s1; j0 += kWarp) {
-        const int64_t j = j0 + lane;
-        float y[3] = {0.f, 0.f, 0.f}, hh = 0.f;
-        bool cand = false;
-        if (j < s1) {
-          const SrcRec r = P.rec[j];
-          y[0] = to_local(r.yh.x, r.q.w, oh[0], ol[0]);
-          y[1] = to_local(r.yh.y, r.n.w, oh[1], ol[1]);
-          y[2] = to_local(r.yh.z, r.p.w, oh[2], ol[2]);
-          hh = r.yh.w;
-          cand = is_candidate(box_dist2(y[0], y[1], y[2], blo, bhi), hh);
-        }
-        for (unsigned cm = __ballot_sync(kFull, cand); cm; cm &= cm - 1) {
-          const int l = __ffs(cm) - 1;
-          const float y0 = __shfl_sync(kFull, y[0], l), y1 = __shfl_sync(kFull, y[1], l),
-                      y2 = __shfl_sync(kFull, y[2], l), h2 = __shfl_sync(kFull, hh, l);
-          const int32_t jl = (int32_t)(j0 + l);
+    auto test_round = [&](bool cand, const float (&y)[3], float hh, int32_t j, uint32_t kb) {
+      for (unsigned cm = __ballot_sync(kFull, cand); cm; cm &= cm - 1) {
+        const int l = __ffs(cm) - 1;
+        const float y0 = __shfl_sync(kFull, y[0], l), y1 = __shfl_sync(kFull, y[1], l),
+                    y2 = __shfl_sync(kFull, y[2], l), h2 = __shfl_sync(kFull, hh, l);
+        const int32_t jl = (int32_t)__shfl_sync(kFull, (int32_t)j, l);
+        const uint32_t kind_bits = __shfl_sync(kFull, kb, l);
+        // this lane's near targets (slots beyond the item hold padding)
+        unsigned nm = 0;
 #pragma unroll
-          for (int t = 0; t < kNearT; ++t) {
+        for (int t = 0; t < kNearT; ++t) {
+          if (t * kWarp < tn) {
             const float r2 =
                 pair_r2(__fsub_rn(x[t][0], y0), __fsub_rn(x[t][1], y1), __fsub_rn(x[t][2], y2));
-            const bool nr = valid[t] && is_near(r2, h2) && !(P.self_index && ci[t] == jl);
-            const unsigned m = __ballot_sync(kFull, nr);
-            if (nr) {
-              const int pos = qn + __popc(m & lt);
-              sm.qt[pos] = (uint8_t)(lane + kWarp * t);
-              sm.qj[pos] = (int32_t)((uint32_t)jl | kind_bits);
+            if (is_near(r2, h2) && self_id[t] != jl) nm |= 1u << t;
+          }
+        }
+        const unsigned any = __ballot_sync(kFull, nm != 0);
+        if (any == 0) continue;
+        // queue order: by lane, then by target slot within the lane
+        const int cnt = __popc(nm);
+        const unsigned b0 = __ballot_sync(kFull, cnt & 1), b1 = __ballot_sync(kFull, cnt & 2),
+                       b2 = __ballot_sync(kFull, cnt & 4);
+        int pos = qn + __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+        for (unsigned mm = nm; mm; mm &= mm - 1, ++pos) {
+          sm.qt[pos] = (uint8_t)(lane + kWarp * (__ffs(mm) - 1));
+          sm.qj[pos] = (int32_t)((uint32_t)jl | kind_bits);
+        }
+        qn += __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+        if (qn > kNearQueue - kNearT * kWarp) {
+          __syncwarp();
+          eval_queue(sm, P, it.t0, qn, lane);
+          qn = 0;
+        }
+      }
+    };
+    const int32_t ncl = P.cand_cnt[id];
+    if (ncl >= 0) {
+      // the engine listed this item's candidates
+      const int32_t *cl = P.cand_list + (size_t)id * (size_t)P.cand_cap;
+      const int n_list = min(ncl, P.cand_cap);
+      for (int p0 = 0; p0 < n_list; p0 += kWarp) {
+        const int pp = p0 + lane;
+        float y[3] = {0.f, 0.f, 0.f}, hh = 0.f;
+        int32_t j = 0;
+        uint32_t kb = 0;
+        if (pp < n_list) {
+          const uint32_t e = (uint32_t)cl[pp];
+          j = (int32_t)(e & 0x3fffffffu);
+          kb = e & 0xc0000000u;
+          const float4 yh = __ldg(&P.rec[j].yh);
+          const float ylx = __ldg(&P.rec[j].q.w), yly = __ldg(&P.rec[j].n.w),
+                      ylz = __ldg(&P.rec[j].p.w);
+          y[0] = to_local(yh.x, ylx, oh[0], ol[0]);
+          y[1] = to_local(yh.y, yly, oh[1], ol[1]);
+          y[2] = to_local(yh.z, ylz, oh[2], ol[2]);
+          hh = yh.w;
+        }
+        test_round(pp < n_list, y, hh, j, kb);
+      }
+    } else {
+      // more candidates than the list holds: scan the item's sources
+      for (int32_t w0 = it.seg0; w0 < it.seg1; w0 += kNearSegWin) {
+        const int nw = min(kNearSegWin, it.seg1 - w0);
+        __syncwarp();
+        int run = 0;  // sources in the window before this lane's pair of segments
+        int32_t sz[2] = {0, 0};
+  #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int e = 2 * lane + h;
+          if (e < nw) {
+            const int32_t sid = P.seg_list ? P.seg_list[w0 + e] : w0 + e;
+            const int64_t a = P.range_ptr[sid];
+            sz[h] = (int32_t)(P.range_ptr[sid + 1] - a);
+            sm.seg_start[e] = a;
+            sm.seg_kind[e] = seg_kind(P, sid) << 30;
+          }
+        }
+        int incl = sz[0] + sz[1];
+  #pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {
+          const int v = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += v;
+        }
+        run = incl - sz[0] - sz[1];
+        if (2 * lane < nw) sm.seg_pre[2 * lane] = run;
+        if (2 * lane + 1 < nw) sm.seg_pre[2 * lane + 1] = run + sz[0];
+        const int total = __shfl_sync(kFull, incl, kWarp - 1);
+        if (lane == 0) sm.seg_pre[nw] = total;
+        __syncwarp();
+
+        for (int p0 = 0; p0 < total; p0 += kWarp) {
+          const int pp = p0 + lane;
+          int64_t j = 0;
+          uint32_t kb = 0;
+          float y[3] = {0.f, 0.f, 0.f}, hh = 0.f;
+          bool cand = false;
+          if (pp < total) {
+            int e = 0;  // last segment starting at or before pp
+  #pragma unroll
+            for (int step = kNearSegWin / 2; step > 0; step >>= 1)
+              if (e + step < nw && sm.seg_pre[e + step] <= pp) e += step;
+            j = sm.seg_start[e] + (pp - sm.seg_pre[e]);
+            kb = (uint32_t)sm.seg_kind[e];
+            const float4 yh = __ldg(&P.rec[j].yh);
+            hh = yh.w;
+            // conservative test: yh - oh differs from the local coordinate by
+            // less than tol (the dropped low parts and one rounding each)
+            const float tol =
+                fmaf(4.8e-7f, fabsf(yh.x) + fabsf(yh.y) + fabsf(yh.z), tol0) + 1e-30f;
+            const float lo2[3] = {blo[0] - tol, blo[1] - tol, blo[2] - tol};
+            const float hi2[3] = {bhi[0] + tol, bhi[1] + tol, bhi[2] + tol};
+            const float bd2a = box_dist2(yh.x - oh[0], yh.y - oh[1], yh.z - oh[2], lo2, hi2);
+            if (bd2a < hh * 1.0001f + 1e-30f) {
+              const float ylx = __ldg(&P.rec[j].q.w), yly = __ldg(&P.rec[j].n.w),
+                          ylz = __ldg(&P.rec[j].p.w);
+              y[0] = to_local(yh.x, ylx, oh[0], ol[0]);
+              y[1] = to_local(yh.y, yly, oh[1], ol[1]);
+              y[2] = to_local(yh.z, ylz, oh[2], ol[2]);
+              cand = is_candidate(box_dist2(y[0], y[1], y[2], blo, bhi), hh);
             }
-            qn += __popc(m);
           }
-          if (qn > kNearQueue - kNearT * kWarp) {
-            __syncwarp();
-            eval_queue(sm, P, it.t0, qn, lane);
-            qn = 0;
-          }
+          test_round(cand, y, hh, (int32_t)j, kb);
         }
       }
     }

@@ -398,6 +398,50 @@ __global__ void k_batched_emit(int32_t nsusp, const int64_t *__restrict__ susp_p
   }
 }
 
+// ---------------------------------------------------------------- item order
+// Items in descending cost (longest first, for the persistent queues): a
+// counting sort on 256 log-spaced cost buckets (8 per octave).  Items of one
+// bucket keep their order of arrival, which differs between runs; that only
+// changes which warp runs which item, never a result (every item computes its
+// targets' sums on its own, in a fixed order).
+__device__ __forceinline__ int cost_bucket(uint64_t key) {
+  const uint32_t c = 0xffffffffu - (uint32_t)key;  // key = 2^32 - 1 - cost
+  if (c == 0) return 255;
+  const int msb = 31 - __clz(c);
+  const int frac = msb >= 3 ? (int)((c >> (msb - 3)) & 7u) : (int)((c << (3 - msb)) & 7u);
+  return 255 - (8 * msb + frac);
+}
+
+__global__ void k_bucket_rank(int64_t n, const uint64_t *__restrict__ keys,
+                              const int32_t *__restrict__ vals, int32_t *__restrict__ cnt,
+                              int32_t *__restrict__ rank) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (vals[i] >= 0) rank[i] = atomicAdd(&cnt[cost_bucket(keys[i])], 1);
+}
+
+__global__ void k_bucket_offsets(const int32_t *__restrict__ cnt, int32_t *__restrict__ off) {
+  __shared__ int32_t s[256];
+  const int t = threadIdx.x;
+  s[t] = cnt[t];
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const int32_t v = t >= o ? s[t - o] : 0;
+    __syncthreads();
+    s[t] += v;
+    __syncthreads();
+  }
+  off[t] = s[t] - cnt[t];
+}
+
+__global__ void k_bucket_scatter(int64_t n, const uint64_t *__restrict__ keys,
+                                 const int32_t *__restrict__ vals, const int32_t *__restrict__ off,
+                                 const int32_t *__restrict__ rank, int32_t *__restrict__ order) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (vals[i] >= 0) order[off[cost_bucket(keys[i])] + rank[i]] = vals[i];
+}
+
 // ---------------------------------------------------------------- finish
 // out[perm[i]] (+)= sum over parts of part_out[p][i], parts added in order.
 __global__ void k_finish(int64_t nt, int32_t nparts, const double *__restrict__ part_out,
@@ -502,6 +546,15 @@ void launch_batched_items(int32_t nsusp, const int64_t *susp_ptr, const int64_t 
   k_batched_emit<<<grid_for(nsusp, 128), 128, 0, st>>>(nsusp, susp_ptr, n_cell, item_max, offs,
                                                        items, range_ptr, keys, vals);
   count_launches(1);
+}
+
+void launch_bucket_order(int64_t n, const uint64_t *keys, const int32_t *vals, int32_t *cnt,
+                         int32_t *off, int32_t *rank, int32_t *order, cudaStream_t st) {
+  cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 256, st);
+  k_bucket_rank<<<grid_for(n, 256), 256, 0, st>>>(n, keys, vals, cnt, rank);
+  k_bucket_offsets<<<1, 256, 0, st>>>(cnt, off);
+  k_bucket_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, keys, vals, off, rank, order);
+  count_launches(3);
 }
 
 void launch_finish(int64_t nt, int32_t nparts, const double *part_out, const int32_t *tperm,

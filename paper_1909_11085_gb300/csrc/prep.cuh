@@ -33,6 +33,10 @@ void launch_batched_items(int32_t nsusp, const int64_t *susp_ptr, const int64_t 
                           int32_t item_max, int32_t *cnt, int32_t *offs, int32_t *n_items,
                           Item *items, int64_t *range_ptr, uint64_t *keys, int32_t *vals,
                           cudaStream_t st);
+// Item order by descending cost bucket (keys from the item builders; vals < 0
+// marks unused slots); cnt and off hold 256 entries, rank and order n.
+void launch_bucket_order(int64_t n, const uint64_t *keys, const int32_t *vals, int32_t *cnt,
+                         int32_t *off, int32_t *rank, int32_t *order, cudaStream_t st);
 // Near pairs of the mixed engine's items (near.cu); runs after the engine.
 void launch_near(const EngineParams &P, int sms, int64_t max_items, cudaStream_t st);
 void launch_finish(int64_t nt, int32_t nparts, const double *part_out, const int32_t *tperm,

@@ -104,8 +104,13 @@ struct Plan {
   int32_t ngroup = 0;
   // offsets (the counters always sit at offset 0 of the aligned workspace)
   size_t counters, rec, keys_a, keys_b, vals_a, vals_b, ikeys_a, ikeys_b, ivals_a, ivals_b, hist,
-      hist_scan, bbox_part, bbox, items, range, cnt, offs, part, total;
+      hist_scan, bbox_part, bbox, items, range, cnt, offs, part, frames = 0, xloc = 0,
+      cand_list = 0, cand_cnt = 0, total;
 };
+
+// Candidate sources the engine lists per item for k_near (items with more are
+// rescanned by k_near).
+constexpr int32_t kCandCap = 512;
 
 int auto_splits(int64_t nt, int64_t ns, const DevInfo &di, int occ) {
   const int64_t chunks = (nt + kItemMax - 1) / kItemMax;
@@ -143,6 +148,13 @@ void layout(Plan &p) {
   p.cnt = a.take(sizeof(int32_t) * (size_t)(p.ngroup + 1));
   p.offs = a.take(sizeof(int32_t) * (size_t)(p.ngroup + 2));
   p.part = a.take(sizeof(double) * 3 * (size_t)p.nt * (size_t)p.nsplit);
+  if (p.mixed) {
+    const size_t mi = (size_t)(p.max_items > 0 ? p.max_items : 1);
+    p.frames = a.take(sizeof(float) * 12 * mi);
+    p.xloc = a.take(sizeof(float) * 3 * (size_t)(p.nt > 0 ? p.nt : 1));
+    p.cand_list = a.take(sizeof(int32_t) * (size_t)kCandCap * mi);
+    p.cand_cnt = a.take(sizeof(int32_t) * mi);
+  }
   p.total = a.off + 256;  // slack for re-alignment of an unaligned base
 }
 
@@ -243,6 +255,11 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   if (g_ev_start && g_ev_stop) CU(cudaEventRecord(g_ev_start, st));
   if (p.mixed) {
     P.rec = at<SrcRec>(ws, p.rec);
+    P.frames = at<float>(ws, p.frames);
+    P.xloc = at<float>(ws, p.xloc);
+    P.cand_list = at<int32_t>(ws, p.cand_list);
+    P.cand_cnt = at<int32_t>(ws, p.cand_cnt);
+    P.cand_cap = kCandCap;
     CU(launch_engine_mixed(P, (int)grid, st));
   } else {
     P.rec64 = at<SrcRec64>(ws, p.rec);
@@ -297,9 +314,10 @@ const int32_t *build_sorted_items(const Plan &p, void *ws, cudaStream_t st, Emit
   cudaMemsetAsync(ka, 0xff, sizeof(uint64_t) * (size_t)p.max_items, st);
   cudaMemsetAsync(va, 0xff, sizeof(int32_t) * (size_t)p.max_items, st);
   emit(ka, va);
-  const int which = radix_sort(ka, va, kb, vb, p.max_items, 32, at<int32_t>(ws, p.hist),
-                               at<int32_t>(ws, p.hist_scan), st);
-  return which ? vb : va;
+  // rank per item in the first half of kb's storage, order in vb
+  launch_bucket_order(p.max_items, ka, va, at<int32_t>(ws, p.hist), at<int32_t>(ws, p.hist_scan),
+                      reinterpret_cast<int32_t *>(kb), vb, st);
+  return vb;
 }
 
 stk_status direct_common(int32_t kinds, const double *src, const double *f, const double *nrm,

@@ -175,3 +175,24 @@ def test_nearly_coincident_pairs_take_the_fp64_path(lib):
     u = lib.sldl(Y, F, N, PH, Wt, X, 1.0, h=H, precision="mixed").cpu().numpy()
     assert np.all(np.isfinite(u))
     assert rel_l2(u, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("splits", [1, 3])
+def test_dense_cluster_all_pairs_near(lib, splits):
+    """3,001 points in a ball of radius 1 with spacing 5: every pair is near, so
+    every item holds more candidate sources than the engine lists for the near
+    kernel, which then scans the item's sources itself."""
+    rng = W.rng_for(23)
+    n = 3001
+    y = rng.normal(size=(n, 3))
+    y /= np.maximum(1.0, np.linalg.norm(y, axis=1))[:, None]
+    f, phi = rng.uniform(-1, 1, (n, 3)), rng.uniform(-1, 1, (n, 3))
+    nr = rng.normal(size=(n, 3))
+    nr /= np.linalg.norm(nr, axis=1)[:, None]
+    w = rng.uniform(0.5, 1.5, n)
+    h = np.full(n, 5.0)
+    ref = oracle.sldl(y, f, nr, phi, w, y, 1.0)
+    Y, F, N, PH, Wt, H = cuda(y, f, nr, phi, w, h)
+    u = lib.sldl(Y, F, N, PH, Wt, Y, 1.0, h=H, precision="mixed",
+                 source_splits=splits).cpu().numpy()
+    assert rel_l2(u, ref) <= TOLMIX, rel_l2(u, ref)

@@ -25,7 +25,7 @@
 //    the same arithmetic afterwards and adds those pairs with the FP64
 //    difference and 1/|r|, whose FP64 work would otherwise stall this FP32
 //    engine.
-//  * Accumulation: plain FP32 within a chunk (<= 64 terms per lane), then a
+//  * Accumulation: plain FP32 over two chunks (<= 128 terms per lane), then a
 //    two-sum into per-target (hi, lo) kept in shared memory.
 //  * The kernel is instantiated per kernel kind (SL, DL, SL+DL, or SL/DL by
 //    segment parity for batched suspensions) so that a launch only runs the
@@ -352,50 +352,83 @@ __device__ bool run_item(const EngineParams &P, const Item &it, int id, WarpSmem
   const int part = it.tn_part >> 8;
   ic.part = part;
 
-  const double cx = P.src64[0], cy = P.src64[1], cz = P.src64[2];
-  // item origin: centre of the targets' bounding box
-  const int c0 = P.tperm ? P.tperm[it.t0] : it.t0;
-  const double x0 = P.trg64[3 * (size_t)c0], y0 = P.trg64[3 * (size_t)c0 + 1],
-               z0 = P.trg64[3 * (size_t)c0 + 2];
+  // Item frame: origin at the centre of the targets' bounding box, targets
+  // in local coordinates.  When the targets are the sources, their FP32
+  // hi/lo records already hold the split positions; otherwise the FP64
+  // target positions are split here.
   bool valid[T];
+  float oh[3], ol[3], x[T][3];
   float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  const int c0 = P.tperm ? P.tperm[it.t0] : it.t0;
+  if (P.self_index) {
+    const SrcRec r0 = P.rec[c0];
+    const float x0h[3] = {r0.yh.x, r0.yh.y, r0.yh.z}, x0l[3] = {r0.q.w, r0.n.w, r0.p.w};
+    float xh[T][3], xl[T][3];
 #pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int li = ic.tgl + ic.G * t;
-    valid[t] = li < ic.tn;
-    if (valid[t]) {
-      const int gi = it.t0 + li;
-      const double *xp = P.trg64 + 3 * (size_t)(P.tperm ? P.tperm[gi] : gi);
-      const float rx = __double2float_rn(xp[0] - x0), ry = __double2float_rn(xp[1] - y0),
-                  rz = __double2float_rn(xp[2] - z0);
-      mn[0] = fminf(mn[0], rx); mx[0] = fmaxf(mx[0], rx);
-      mn[1] = fminf(mn[1], ry); mx[1] = fmaxf(mx[1], ry);
-      mn[2] = fminf(mn[2], rz); mx[2] = fmaxf(mx[2], rz);
+    for (int t = 0; t < T; ++t) {
+      const int li = ic.tgl + ic.G * t;
+      valid[t] = li < ic.tn;
+      const int gi = it.t0 + (valid[t] ? li : 0);
+      const SrcRec r = P.rec[P.tperm ? P.tperm[gi] : gi];
+      xh[t][0] = r.yh.x; xh[t][1] = r.yh.y; xh[t][2] = r.yh.z;
+      xl[t][0] = r.q.w;  xl[t][1] = r.n.w;  xl[t][2] = r.p.w;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (valid[t]) {
+          const float rk = to_local(xh[t][k], xl[t][k], x0h[k], x0l[k]);
+          mn[k] = fminf(mn[k], rk);
+          mx[k] = fmaxf(mx[k], rk);
+        }
     }
-  }
-  float oh[3], ol[3];
-  frame_origin(x0, warp_min(mn[0]), warp_max(mx[0]), cx, oh[0], ol[0]);
-  frame_origin(y0, warp_min(mn[1]), warp_max(mx[1]), cy, oh[1], ol[1]);
-  frame_origin(z0, warp_min(mn[2]), warp_max(mx[2]), cz, oh[2], ol[2]);
-  float x[T][3];
-  float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  const double cc[3] = {cx, cy, cz};
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int li = ic.tgl + ic.G * t;
-    const int gi = it.t0 + (valid[t] ? li : 0);
-    const double *xp = P.trg64 + 3 * (size_t)(P.tperm ? P.tperm[gi] : gi);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
+      oh[k] = __fadd_rn(x0h[k], __fmul_rn(0.5f, __fadd_rn(warp_min(mn[k]), warp_max(mx[k]))));
+      ol[k] = x0l[k];
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) x[t][k] = valid[t] ? to_local(xh[t][k], xl[t][k], oh[k], ol[k]) : 1e30f;
+  } else {
+    const double x0[3] = {P.trg64[3 * (size_t)c0], P.trg64[3 * (size_t)c0 + 1],
+                          P.trg64[3 * (size_t)c0 + 2]};
+    const double cc[3] = {P.src64[0], P.src64[1], P.src64[2]};
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const int li = ic.tgl + ic.G * t;
+      valid[t] = li < ic.tn;
       if (valid[t]) {
-        x[t][k] = local_coord(xp[k], cc[k], oh[k], ol[k]);
-        blo[k] = fminf(blo[k], x[t][k]);
-        bhi[k] = fmaxf(bhi[k], x[t][k]);
-      } else {
-        x[t][k] = 1e30f;  // padding slot: far from everything, never written
+        const int gi = it.t0 + li;
+        const double *xp = P.trg64 + 3 * (size_t)(P.tperm ? P.tperm[gi] : gi);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float rk = __double2float_rn(xp[k] - x0[k]);
+          mn[k] = fminf(mn[k], rk);
+          mx[k] = fmaxf(mx[k], rk);
+        }
       }
     }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) frame_origin(x0[k], warp_min(mn[k]), warp_max(mx[k]), cc[k], oh[k], ol[k]);
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const int li = ic.tgl + ic.G * t;
+      const int gi = it.t0 + (valid[t] ? li : 0);
+      const double *xp = P.trg64 + 3 * (size_t)(P.tperm ? P.tperm[gi] : gi);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        x[t][k] = valid[t] ? local_coord(xp[k], cc[k], oh[k], ol[k]) : 1e30f;  // 1e30: padding
+    }
   }
+  float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+  for (int t = 0; t < T; ++t)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (valid[t]) {
+        blo[k] = fminf(blo[k], x[t][k]);
+        bhi[k] = fmaxf(bhi[k], x[t][k]);
+      }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     blo[k] = warp_min(blo[k]);
@@ -453,6 +486,7 @@ __device__ bool run_item(const EngineParams &P, const Item &it, int id, WarpSmem
     cur.s += n_cur;
   }
   bool ok = true;
+  int npend = 0;
   while (have) {
     if (!wait_chunk(&sm.mbar, phase, P.spin_limit)) {
       set_error(P.err_flag, 4);
@@ -476,16 +510,20 @@ __device__ bool run_item(const EngineParams &P, const Item &it, int id, WarpSmem
       cur.s += n_next;
     }
     dispatch_compute<T, KMODE>(kind_cur, sm, P, ic, n_cur, nfar, x, ps);
+    // plain FP32 over two chunks (<= 128 sources), then into the (hi, lo) sums
+    if (++npend == 2 || !have_next) {
+      npend = 0;
 #pragma unroll
-    for (int t = 0; t < T; ++t)
+      for (int t = 0; t < T; ++t)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        float h = sm.acc[t * 3 + k][lane], l = sm.acc[(T + t) * 3 + k][lane];
-        two_sum_acc(h, l, ps[t][k]);
-        sm.acc[t * 3 + k][lane] = h;
-        sm.acc[(T + t) * 3 + k][lane] = l;
-        ps[t][k] = 0.f;
-      }
+        for (int k = 0; k < 3; ++k) {
+          float h = sm.acc[t * 3 + k][lane], l = sm.acc[(T + t) * 3 + k][lane];
+          two_sum_acc(h, l, ps[t][k]);
+          sm.acc[t * 3 + k][lane] = h;
+          sm.acc[(T + t) * 3 + k][lane] = l;
+          ps[t][k] = 0.f;
+        }
+    }
     __syncwarp();
     have = have_next;
     n_cur = n_next;

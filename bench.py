@@ -176,18 +176,142 @@ def timed_oracle(wl, seconds: float, rng):
 
 def workload_config(wl, pairs):
     return {"workload": f"p2p_ulist_sl+dl_{wl.pts.shape[0]}pts_leaf256",
-            "points": int(wl.pts.shape[0]), "cells": 1857, "cell_order_p": 16,
-            "wall_patches": 320, "leaves": int(wl.tree.nleaf),
+            "points": int(wl.pts.shape[0]), "cells": int(wl.n_cell_points // 544),
+            "cell_order_p": 16, "wall_patches": int(wl.n_wall_points // 121),
+            "leaves": int(wl.tree.nleaf),
             "ulist_entries": int(wl.tree.ulist_idx.size), "pairs_per_step": int(pairs),
             "kernels": "SL+DL", "near_ratio": NEAR_RATIO,
             "l2": "256 MiB buffer written between timed steps (outside the step events)"}
+
+
+FLOPS_PER_PAIR = {"SL": 27, "DL": 29, "SLDL": 40}
+
+
+def _time_ms(fn, stream, flush, reps, warm=1):
+    """Median device time of fn() over reps calls (L2 flushed before each)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
+def run_forms(dev, flush, stream, peak_tflops):
+    """The paper's other workloads on the same GPU: direct single layer (8 cells),
+    direct double layer (256 cells + 65,536 off-surface targets), 2,048 batched
+    suspensions (autotuned tile, CUDA-graph replay) and the adjoint of SL + DL
+    (64 cells).  Each: device time per call, Gpair/s, % FP32 peak (mixed) and the
+    rel-L2 error against the FP64 oracle on the stated sample."""
+    import torch
+    import oracle
+    import paper_1909_11085_gb300 as P
+    from synth import workloads as W
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    err = lambda u, r: float(np.linalg.norm(u - r) / np.linalg.norm(r))
+    pct = lambda pairs, ms, kind: 100.0 * pairs * FLOPS_PER_PAIR[kind] / (ms / 1e3) / 1e12 / peak_tflops
+    forms = {}
+    rng = np.random.default_rng(1909)
+
+    c1 = W.sl_direct_workload()
+    n1 = c1.src.shape[0]
+    src, f, w, h = T(c1.src), T(c1.f), T(c1.w), T(c1.h)
+    ref = oracle.sl(c1.src, c1.f, c1.w, c1.src, c1.mu)
+    e = {}
+    for prec in ("fp64", "mixed"):
+        out = torch.empty((n1, 3), dtype=torch.float64, device=dev)
+        ms = _time_ms(lambda: P.sl(src, f, w, None, c1.mu, h=h, precision=prec, out=out), stream,
+                      flush, 10)
+        e[prec] = {"ms": ms, "Gpair/s": n1 * (n1 - 1) / ms / 1e6,
+                   "rel_l2": err(out.cpu().numpy(), ref)}
+    e["mixed"]["pct_fp32_peak"] = pct(n1 * (n1 - 1), e["mixed"]["ms"], "SL")
+    forms["direct_sl_8rbc_4352pts"] = dict(pairs=n1 * (n1 - 1), sample="all targets", **e)
+    log(f"[forms] direct SL: {e}")
+
+    c2 = W.dl_direct_workload()
+    ns2, nt2 = c2.src.shape[0], c2.trg.shape[0]
+    src, nrm, phi, w, h, trg = (T(a) for a in (c2.src, c2.nrm, c2.phi, c2.w, c2.h, c2.trg))
+    pick = np.sort(rng.choice(nt2, 512, replace=False))
+    ref = oracle.dl(c2.src, c2.nrm, c2.phi, c2.w, c2.trg[pick])
+    pairs2 = ns2 * nt2 - ns2
+    e = {}
+    for prec, reps in (("mixed", 5), ("fp64", 2)):
+        out = torch.empty((nt2, 3), dtype=torch.float64, device=dev)
+        ms = _time_ms(lambda: P.dl(src, nrm, phi, w, trg, h=h, precision=prec, out=out), stream,
+                      flush, reps)
+        e[prec] = {"ms": ms, "Gpair/s": pairs2 / ms / 1e6,
+                   "rel_l2": err(out.cpu().numpy()[pick], ref)}
+    e["mixed"]["pct_fp32_peak"] = pct(pairs2, e["mixed"]["ms"], "DL")
+    forms["direct_dl_256rbc_139264src_204800trg"] = dict(
+        pairs=pairs2, sample="512 random targets", **e)
+    log(f"[forms] direct DL: {e}")
+    del src, nrm, phi, w, h, trg
+
+    t0 = time.perf_counter()
+    c3 = W.batched_workload()
+    log(f"[forms] batched workload: {c3.pts.shape[0]} points, {c3.nsusp} suspensions, "
+        f"{time.perf_counter() - t0:.1f}s")
+    n3 = c3.pts.shape[0]
+    pairs3 = c3.pairs()
+    pts, f, phi, nrm, w, h = (T(a) for a in (c3.pts, c3.f, c3.phi, c3.nrm, c3.w, c3.h))
+    # tile configuration from the autotuner, timed on the first 256 suspensions
+    m = int(c3.susp_ptr[256])
+    small = P.BatchedPlan(m, c3.susp_ptr[:257], c3.n_cell[:256])
+    cfg = small.autotune(pts[:m], f[:m], phi[:m], nrm[:m], w[:m], h[:m], c3.mu)
+    del small
+    plan = P.BatchedPlan(n3, c3.susp_ptr, c3.n_cell)
+    plan.opts.tile_config = cfg
+    out = torch.empty((n3, 3), dtype=torch.float64, device=dev)
+    graph = plan.capture(pts, f, phi, nrm, w, h, c3.mu, out)
+    ms = _time_ms(lambda: graph.launch(stream), stream, flush, 3)
+    plan.device_status()
+    u = out.cpu().numpy()
+    sus = np.sort(rng.choice(c3.nsusp, 4, replace=False))
+    rows = np.concatenate([np.arange(c3.susp_ptr[s], c3.susp_ptr[s + 1]) for s in sus])
+    sp = np.concatenate([[0], np.cumsum(np.diff(c3.susp_ptr)[sus])])
+    refb = oracle.batched(c3.pts[rows], c3.f[rows], c3.phi[rows], c3.nrm[rows], c3.w[rows],
+                          sp, c3.n_cell[sus], c3.mu)
+    forms["batched_2048_suspensions_graph"] = {
+        "pairs": pairs3, "points": n3, "tile_config": cfg,
+        "mixed": {"ms": ms, "Gpair/s": pairs3 / ms / 1e6, "rel_l2": err(u[rows], refb),
+                  "pct_fp32_peak": pct(pairs3, ms, "SL")},
+        "sample": f"4 whole suspensions ({rows.size} targets)",
+        "note": "per-pair flops counted as SL (27) for this mixed SL/DL batch"}
+    log(f"[forms] batched: {forms['batched_2048_suspensions_graph']}")
+    del graph, plan, pts, f, phi, nrm, w, h, out
+    torch.cuda.empty_cache()
+
+    c5, g5 = W.adjoint_workload()
+    n5 = c5.src.shape[0]
+    src, f, nrm, phi, w, h, g = (T(a) for a in (c5.src, c5.f, c5.nrm, c5.phi, c5.w, c5.h, g5))
+    def fwd_bwd():
+        s_, f_, n_, p_ = (t.detach().requires_grad_(True) for t in (src, f, nrm, phi))
+        u = P.StokesLayerFn.apply(s_, f_, n_, p_, w, s_, c5.mu, h)
+        u.backward(g)
+    ms = _time_ms(fwd_bwd, stream, flush, 5)
+    # forward pass + source-major and target-major adjoint passes
+    pairs5 = n5 * (n5 - 1)
+    forms["adjoint_sldl_64rbc_34816pts"] = {
+        "pairs_per_pass": pairs5, "passes": 3,
+        "mixed": {"ms_forward_backward": ms, "Gpair/s": 3 * pairs5 / ms / 1e6},
+        "accuracy": "checked in the GPU test suite (oracle gradient and finite differences)"}
+    log(f"[forms] adjoint: {forms['adjoint_sldl_64rbc_34816pts']}")
+    return forms
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
     from synth import workloads as W
-    wl = W.p2p_workload()
+    wl = W.p2p_workload(ncell=args.ncell, n_wall_patch=args.wall_patches)
     pairs = wl.pairs()
     rng = np.random.default_rng(11085)
     import oracle
@@ -236,7 +360,7 @@ def run_ours(args, rank, world, local_rank):
     from synth import workloads as W
 
     t0 = time.perf_counter()
-    wl = W.p2p_workload()
+    wl = W.p2p_workload(ncell=args.ncell, n_wall_patch=args.wall_patches)
     pairs = wl.pairs()
     log(f"[rank {rank}] workload {wl.pts.shape[0]} pts, {wl.tree.nleaf} leaves, {pairs} pairs, "
         f"{time.perf_counter() - t0:.1f}s")
@@ -381,6 +505,8 @@ def run_ours(args, rank, world, local_rank):
                       "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3},
               "gpu_launches": int(launches), "gpu_launches_per_step": launches / K,
               "clocks": clocks, "wall_s_timed_region": wall}
+    if world == 1 and not args.no_forms:
+        result["forms"] = run_forms(dev, flush, stream, peak)
     if world == 1 and not args.no_cpu_baseline:
         rng = np.random.default_rng(20191)
         tg, ref, dt = timed_oracle(wl, args.cpu_seconds, rng)
@@ -408,6 +534,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncell", type=int, default=1857,
+                    help="cells of the near-field workload (464 with --wall-patches 80 gives "
+                         "the 262,096-point case used for ncu captures)")
+    ap.add_argument("--wall-patches", type=int, default=320)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the other workloads (direct, batched, adjoint)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

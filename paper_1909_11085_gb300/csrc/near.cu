@@ -38,6 +38,7 @@ constexpr int kNearQueue = 256;           // >= 128 free slots before each candi
 constexpr int kNearSegWin = 64;           // segments per window
 
 struct __align__(16) NearSmem {
+  float4 xt[kItemMax];               // targets: local coordinates, caller index bits in .w
   float sv[kWarp][3];                // values of one round of evaluations
   float acc[2][3][kItemMax];         // per-target compensated sums (hi, lo)
   int32_t qj[kNearQueue];            // queued pair: source index | kind << 30
@@ -129,6 +130,11 @@ __global__ void __launch_bounds__(kNearWarps *kWarp, kNearMinBlocks) k_near(Engi
     for (int li = lane; li < tn; li += kWarp)
 #pragma unroll
       for (int k = 0; k < 3; ++k) sm.acc[0][k][li] = sm.acc[1][k][li] = 0.f;
+#pragma unroll
+    for (int t = 0; t < kNearT; ++t)
+      if (lane + kWarp * t < tn)
+        sm.xt[lane + kWarp * t] = make_float4(x[t][0], x[t][1], x[t][2], __int_as_float(self_id[t]));
+    __syncwarp();
 
     // 2./3. candidate sources: each is broadcast and every lane tests its
     // targets; near pairs are queued (by lane, then target slot)
@@ -171,13 +177,15 @@ __global__ void __launch_bounds__(kNearWarps *kWarp, kNearMinBlocks) k_near(Engi
     };
     const int32_t ncl = P.cand_cnt[id];
     if (ncl >= 0) {
-      // the engine listed this item's candidates
+      // The engine listed this item's candidates.  Each lane takes one
+      // candidate and the warp walks the targets (broadcast from shared
+      // memory); near pairs are queued by target, then by lane.
       const int32_t *cl = P.cand_list + (size_t)id * (size_t)P.cand_cap;
       const int n_list = min(ncl, P.cand_cap);
       for (int p0 = 0; p0 < n_list; p0 += kWarp) {
         const int pp = p0 + lane;
-        float y[3] = {0.f, 0.f, 0.f}, hh = 0.f;
-        int32_t j = 0;
+        float y0 = 0.f, y1 = 0.f, y2 = 0.f, hh = -1.f;  // hh < 0: idle lane, never near
+        int32_t j = -1;
         uint32_t kb = 0;
         if (pp < n_list) {
           const uint32_t e = (uint32_t)cl[pp];
@@ -186,12 +194,37 @@ __global__ void __launch_bounds__(kNearWarps *kWarp, kNearMinBlocks) k_near(Engi
           const float4 yh = __ldg(&P.rec[j].yh);
           const float ylx = __ldg(&P.rec[j].q.w), yly = __ldg(&P.rec[j].n.w),
                       ylz = __ldg(&P.rec[j].p.w);
-          y[0] = to_local(yh.x, ylx, oh[0], ol[0]);
-          y[1] = to_local(yh.y, yly, oh[1], ol[1]);
-          y[2] = to_local(yh.z, ylz, oh[2], ol[2]);
+          y0 = to_local(yh.x, ylx, oh[0], ol[0]);
+          y1 = to_local(yh.y, yly, oh[1], ol[1]);
+          y2 = to_local(yh.z, ylz, oh[2], ol[2]);
           hh = yh.w;
         }
-        test_round(pp < n_list, y, hh, j, kb);
+        const int32_t jq = (int32_t)((uint32_t)j | kb);
+        for (int t0 = 0; t0 < tn; t0 += 4) {
+          if (qn > kNearQueue - 4 * kWarp) {
+            __syncwarp();
+            eval_queue(sm, P, it.t0, qn, lane);
+            qn = 0;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int ti = t0 + u;
+            if (ti < tn) {
+              const float4 X = sm.xt[ti];
+              const float r2 = pair_r2(__fsub_rn(X.x, y0), __fsub_rn(X.y, y1), __fsub_rn(X.z, y2));
+              const bool nr = is_near(r2, hh) && __float_as_int(X.w) != j;
+              const unsigned m = __ballot_sync(kFull, nr);
+              if (m) {
+                if (nr) {
+                  const int pos = qn + __popc(m & lt);
+                  sm.qt[pos] = (uint8_t)ti;
+                  sm.qj[pos] = jq;
+                }
+                qn += __popc(m);
+              }
+            }
+          }
+        }
       }
     } else {
       // more candidates than the list holds: scan the item's sources

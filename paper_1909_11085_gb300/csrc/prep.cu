@@ -291,11 +291,10 @@ int radix_sort(uint64_t *ka, int32_t *va, uint64_t *kb, int32_t *vb, int64_t n, 
 }
 
 // ---------------------------------------------------------------- items
+// Item key for the ordering below: targets (high word) and sources (low word).
 __device__ __forceinline__ uint64_t cost_key(int64_t tn, int64_t nsrc) {
-  // ascending sort of this key gives descending cost
-  uint64_t c = (uint64_t)tn * (uint64_t)nsrc;
-  if (c > 0xffffffffull) c = 0xffffffffull;
-  return 0xffffffffull - c;
+  const uint64_t s = nsrc > 0xffffffffll ? 0xffffffffull : (uint64_t)(nsrc > 0 ? nsrc : 0);
+  return ((uint64_t)tn << 32) | s;
 }
 
 __global__ void k_items_direct(int32_t nt, int64_t ns, int32_t nsplit, int32_t item_max,
@@ -399,17 +398,25 @@ __global__ void k_batched_emit(int32_t nsusp, const int64_t *__restrict__ susp_p
 }
 
 // ---------------------------------------------------------------- item order
-// Items in descending cost (longest first, for the persistent queues): a
-// counting sort on 256 log-spaced cost buckets (8 per octave).  Items of one
-// bucket keep their order of arrival, which differs between runs; that only
-// changes which warp runs which item, never a result (every item computes its
-// targets' sums on its own, in a fixed order).
+// Items are ordered by a counting sort on 256 buckets: 16 classes of target
+// count (8 targets wide, most targets first), each split into 16 half-octave
+// classes of source count (most sources first).  So the longest items start
+// first (for the persistent queues) and items with the same lane layout --
+// the same engine code -- run together, which keeps the engine's hot loops
+// few at a time in the instruction cache.  Items of one bucket keep their
+// order of arrival, which differs between runs; that only changes which warp
+// runs which item, never a result (every item computes its targets' sums on
+// its own, in a fixed order).
 __device__ __forceinline__ int cost_bucket(uint64_t key) {
-  const uint32_t c = 0xffffffffu - (uint32_t)key;  // key = 2^32 - 1 - cost
-  if (c == 0) return 255;
-  const int msb = 31 - __clz(c);
-  const int frac = msb >= 3 ? (int)((c >> (msb - 3)) & 7u) : (int)((c << (3 - msb)) & 7u);
-  return 255 - (8 * msb + frac);
+  const uint32_t tn = (uint32_t)(key >> 32), ns = (uint32_t)key;
+  const int cls = tn > 128u ? 15 : (int)((tn > 0 ? tn - 1 : 0) / 8u);
+  int lv = 0;
+  if (ns > 0) {
+    const int msb = 31 - __clz(ns);
+    lv = 2 * msb + (msb > 0 ? (int)((ns >> (msb - 1)) & 1u) : 0) - 12;  // 2 log2(ns) - 12
+    lv = lv < 0 ? 0 : (lv > 15 ? 15 : lv);
+  }
+  return (15 - cls) * 16 + (15 - lv);
 }
 
 __global__ void k_bucket_rank(int64_t n, const uint64_t *__restrict__ keys,

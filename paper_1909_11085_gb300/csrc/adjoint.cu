@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_mixed(AdjParams A) {
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float hh = SRC ? own_hh : P.w;
         const bool near = r2 < hh;
-        const float ri = near ? 0.f : rsqrtf(r2);
+        const float ri = near ? 0.f : rsqrt_ftz(r2);
         const float4 G = sG[kk];
         float g[3], q[3], pp[3], nn[3];
         if (SRC) {

@@ -147,6 +147,17 @@ __device__ __forceinline__ float pair_r2(float d0, float d1, float d2) {
 __device__ __forceinline__ bool is_candidate(float bd2, float hh) { return !(bd2 >= hh); }
 __device__ __forceinline__ bool is_near(float r2, float hh) { return r2 < hh; }
 
+// 1/sqrt(x) by the hardware approximation (rsqrt.approx, relative error below
+// 2^-22), with subnormal inputs flushed to zero.  The plain rsqrtf() keeps
+// subnormals and pays for it with extra instructions around every call; the
+// callers pass |r|^2 of pairs that are not near, which is at least
+// (alpha h_j)^2 >= FLT_MIN, or +inf for pairs taken out of a sum.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Knuth two-sum accumulation of a partial into (hi, lo).
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p) {
   float s = __fadd_rn(hi, p);
@@ -175,7 +186,7 @@ __device__ __forceinline__ bool near_contrib(const double *x, const double *y, f
   const double r2 = dx * dx + dy * dy + dz * dz;
   double rid;
   if (r2f > 1e-30f && r2f < 1e30f) {
-    const double y0 = (double)rsqrtf(r2f);
+    const double y0 = (double)rsqrt_ftz(r2f);
     rid = y0 * fma(-0.5 * r2, y0 * y0, 1.5);  // one FP64 Newton step
   } else {
     rid = 1.0 / sqrt(r2);

@@ -135,7 +135,7 @@ __device__ __forceinline__ void pair_block(const float (&x)[T][3], float (&ps)[T
     float r2 = pair_r2(dx, dy, dz);
     // near pair: rsqrt(+inf) = 0 removes it from this sum (k_near adds it)
     if (MASKED && is_near(r2, Y.w)) r2 = __int_as_float(0x7f800000);
-    const float ri = rsqrtf(r2);
+    const float ri = rsqrt_ftz(r2);
     const float ri2 = ri * ri;
     if (KIND == K_SL) {
       const float dq = fmaf(dx, Q.x, fmaf(dy, Q.y, dz * Q.z));

@@ -215,3 +215,88 @@ def cylinder_wall_patches(radius: float, length: float, n_theta: int, n_z: int, 
             hs.append(np.full(npp, np.sqrt(w.sum() / npp)))
     return (np.concatenate(pts), np.concatenate(nrm), np.concatenate(wts),
             np.concatenate(hs))
+
+
+# --------------------------------------------------------------- patch surfaces
+# Patch surfaces for the check-point quadrature (Sec. 3.1, "Singular and
+# near-singular integral quadrature").  Every patch is the image of
+# [-1, 1]^2; its coarse nodes are the (q+1) x (q+1) Clenshaw-Curtis nodes
+# (u_i, v_j) = (cos(i pi / q), cos(j pi / q)), ordered i-major.  The fine
+# discretisation splits each patch into m x m square sub-patches (m = 2^eta,
+# k = 4^eta sub-patches) with the same node set on each; fine nodes are
+# ordered by patch, then sub-patch (su-major), then node (i-major).  A
+# sub-patch (su, sv) covers u in [-1 + 2 su/m, -1 + 2 (su+1)/m] and likewise
+# in v.  Weights are the tensor-product Clenshaw-Curtis weights times the
+# area element; spacings are sqrt(area / nodes) per (sub-)patch.
+
+def _patch_grid_nodes(q: int, m: int):
+    """Parameter values of the nodes of the m x m sub-patches, as (m*m, q+1) u and v arrays
+    (sub-patch su-major) together with the 1-D CC weights scaled to a sub-interval."""
+    x, w = clenshaw_curtis(q)
+    us, vs = [], []
+    for su in range(m):
+        for sv in range(m):
+            ua, va = -1.0 + 2.0 * su / m, -1.0 + 2.0 * sv / m
+            us.append(ua + (x + 1.0) / m)
+            vs.append(va + (x + 1.0) / m)
+    return np.array(us), np.array(vs), w / m
+
+
+def _patches_from_map(mapping, npatch: int, q: int, m: int):
+    us, vs, w1 = _patch_grid_nodes(q, m)
+    WU, WV = np.meshgrid(w1, w1, indexing="ij")
+    wuv = (WU * WV).ravel()
+    pts, nrm, wts, hs = [], [], [], []
+    for pch in range(npatch):
+        for s in range(m * m):
+            U, V = np.meshgrid(us[s], vs[s], indexing="ij")
+            P, N, J = mapping(pch, U.ravel(), V.ravel())
+            w = wuv * J
+            pts.append(P)
+            nrm.append(N)
+            wts.append(w)
+            hs.append(np.full(w.size, np.sqrt(w.sum() / w.size)))
+    return (np.concatenate(pts), np.concatenate(nrm), np.concatenate(wts),
+            np.concatenate(hs))
+
+
+# the six faces of the cube as (axis, sign)
+_CUBE_FACES = ((2, 1.0), (2, -1.0), (0, 1.0), (0, -1.0), (1, 1.0), (1, -1.0))
+
+
+def _cubed_sphere_map(a: float):
+    def mapping(pch, u, v):
+        ax, sg = _CUBE_FACES[pch]
+        o = [i for i in range(3) if i != ax]
+        c = np.zeros((u.size, 3))
+        c[:, ax] = sg
+        c[:, o[0]] = u
+        c[:, o[1]] = v * sg  # keeps every face's (u, v) frame right-handed
+        r = np.linalg.norm(c, axis=1)
+        n = c / r[:, None]
+        # gnomonic projection of a cube face: area element a^2 / |c|^3
+        return a * n, n, a * a / r ** 3
+    return mapping
+
+
+def cubed_sphere_patches(a: float = 1.0, q: int = 10, m: int = 1):
+    """Sphere of radius a as 6 gnomonic cube-face patches; m = 1 gives the coarse
+    nodes, m = 2^eta the fine discretisation.  Returns (points, normals,
+    weights, spacing)."""
+    return _patches_from_map(_cubed_sphere_map(a), 6, q, m)
+
+
+def cylinder_wall_fine(radius: float, length: float, n_theta: int, n_z: int, q: int = 10,
+                       m: int = 4):
+    """The fine discretisation of cylinder_wall_patches (same patch order)."""
+    dth, dz = 2.0 * np.pi / n_theta, length / n_z
+
+    def mapping(pch, u, v):
+        iz, it = divmod(pch, n_theta)
+        th = np.mod(it + 0.5 * (u + 1.0), n_theta) * dth
+        z = (iz + 0.5 * (v + 1.0)) * dz
+        c, s = np.cos(th), np.sin(th)
+        return (np.stack([radius * c, radius * s, z], axis=-1),
+                np.stack([c, s, np.zeros_like(c)], axis=-1),
+                np.full(u.size, radius * (dth / 2.0) * (dz / 2.0)))
+    return _patches_from_map(mapping, n_theta * n_z, q, m)

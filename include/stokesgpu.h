@@ -195,6 +195,48 @@ stk_status stokes_sldl_grad(const double *src, const double *f, const double *nr
 stk_status stokes_grad_workspace_size(int64_t ns, int64_t nt, const stk_opts *opts,
                                       size_t *bytes);
 
+/* ------------------------------------------------- check-point quadrature
+ * Layer potentials at targets on or near a patch surface by check-point
+ * extrapolation (Sec. 3.1, "Singular and near-singular integral quadrature";
+ * the steps are those of that passage, Eq. "quad_check_points" and
+ * Eq. "sing-quad"):
+ *   1. the density on each patch's (q+1) x (q+1) Clenshaw-Curtis nodes
+ *      (u_i, v_j) = (cos(i pi/q), cos(j pi/q)), node index i (q+1) + j, is
+ *      interpolated (tensor-product, degree q) to the fine discretisation:
+ *      m x m sub-patches (m = 2^eta), sub-patch (su, sv) covering
+ *      u in [-1 + 2 su/m, -1 + 2 (su+1)/m] (likewise v), each with the same
+ *      node set; fine nodes are ordered patch, sub-patch (su m + sv), node;
+ *   2. check points c_i = y - (R + i r) n, i = 0..p, from each target's
+ *      closest surface point y and unit normal n there (y = x for a target
+ *      on a node);
+ *   3. the smooth quadrature sum (Eq. "smooth_double_layer_int_eq_patches_disc")
+ *      of SL[f] (kernels 1), DL[phi] (2) or both (3) over the fine nodes at
+ *      the check points, in opts->precision, as stokes_sl_eval etc. do;
+ *   4. out(x) (+)= sum_i e_i u(c_i), e_i the Lagrange weights of the nodes
+ *      t_i = R + i r at t = (y - x) . n.
+ * f, phi: [npatch (q+1)^2][3] on the coarse nodes (the one not used may be
+ * NULL).  fine_pts, fine_nrm [nf][3], fine_w, fine_h [nf] (h may be NULL):
+ * the fine discretisation's nodes, outward unit normals, weights and
+ * spacings, nf = npatch m^2 (q+1)^2 (the surface is fixed, so the caller
+ * builds these once).  trg, cp_y, cp_n [nt][3].  Limits: 2 <= q <= 12,
+ * 0 <= eta <= 3, 0 <= p <= 15, R > 0, r > 0.  Device pointers, caller-owned;
+ * nothing is allocated and the stream is not synchronised.
+ */
+stk_status stokes_checkpoint_eval(int32_t kernels, const double *f, const double *phi,
+                                  int32_t npatch, int32_t q, int32_t eta, const double *fine_pts,
+                                  const double *fine_nrm, const double *fine_w,
+                                  const double *fine_h, const double *trg, const double *cp_y,
+                                  const double *cp_n, int64_t nt, double R, double r, int32_t p,
+                                  double mu, double *out, const stk_opts *opts, void *workspace,
+                                  size_t workspace_bytes, void *stream);
+stk_status stokes_checkpoint_workspace_size(int32_t kernels, int32_t npatch, int32_t q,
+                                            int32_t eta, int64_t nt, int32_t p,
+                                            const stk_opts *opts, size_t *bytes);
+/* Step 1 alone: coarse [npatch (q+1)^2][ncomp] -> fine [npatch m^2 (q+1)^2][ncomp]
+ * (FP64, ncomp 1..3), the upsampling operator U of Sec. 3.1. */
+stk_status stokes_upsample_patches(const double *coarse, int32_t npatch, int32_t q, int32_t eta,
+                                   int32_t ncomp, double *fine, void *stream);
+
 /* ------------------------------------------------- no-allocation variant
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory when they need a velocity (an application

@@ -29,7 +29,8 @@ EXPORTS = [
     "stokes_sl_eval_noalloc", "stokes_sldl_grad", "stokes_grad_workspace_size",
     "stokes_tile_config_count", "stokes_autotune_p2p", "stokes_autotune_batched",
     "stokes_p2p_graph_create", "stokes_batched_graph_create", "stokes_graph_launch",
-    "stokes_graph_destroy",
+    "stokes_graph_destroy", "stokes_checkpoint_eval", "stokes_checkpoint_workspace_size",
+    "stokes_upsample_patches",
 ]
 
 
@@ -92,6 +93,10 @@ def lib():
             L.stokes_batched_graph_create.argtypes = [p, p, p, p, p, p, i64, p, p, i32, d, p, po, p,
                                                       sz, p, pp]
             L.stokes_graph_launch.argtypes = [p, p]
+            L.stokes_checkpoint_eval.argtypes = [i32, p, p, i32, i32, i32, p, p, p, p, p, p, p,
+                                                 i64, d, d, i32, d, p, po, p, sz, p]
+            L.stokes_checkpoint_workspace_size.argtypes = [i32, i32, i32, i32, i64, i32, po, psz]
+            L.stokes_upsample_patches.argtypes = [p, i32, i32, i32, i32, p, p]
             L.stokes_graph_destroy.argtypes = [p]
             L.stokes_launch_count.restype = ctypes.c_int64
             for name in EXPORTS:

@@ -350,3 +350,70 @@ class StokesLayerFn(torch.autograd.Function):
                       near_ratio=near_ratio, want=tuple(want))
         return (G.get("y"), G.get("f"), G.get("n"), G.get("phi"), None, G.get("x"), None, None,
                 None, None)
+
+
+def upsample_patches(coarse, npatch, q=10, eta=2):
+    """Values on each patch's (q+1)^2 Clenshaw-Curtis nodes -> values on the
+    fine discretisation (4^eta sub-patches per patch), FP64 (Sec. 3.1, the
+    upsampling operator U)."""
+    coarse = coarse.contiguous()
+    if coarse.dtype != torch.float64 or not coarse.is_cuda:
+        raise TypeError("coarse must be a float64 CUDA tensor")
+    ncomp = 1 if coarse.dim() == 1 else coarse.shape[1]
+    m = 1 << eta
+    nf = npatch * m * m * (q + 1) ** 2
+    if coarse.shape[0] != npatch * (q + 1) ** 2:
+        raise ValueError("coarse must have npatch * (q+1)^2 rows")
+    fine = torch.empty((nf, ncomp) if coarse.dim() > 1 else (nf,), dtype=torch.float64,
+                       device=coarse.device)
+    with torch.cuda.device(coarse.device):
+        A.check(A.lib().stokes_upsample_patches(A.ptr(coarse), int(npatch), int(q), int(eta),
+                                                int(ncomp), A.ptr(fine),
+                                                A.stream_ptr(coarse.device)))
+    return fine
+
+
+class CheckpointPlan:
+    """Singular / near-singular evaluation on a fixed patch surface by check-point
+    extrapolation (Sec. 3.1).  The fine discretisation (fine_pts, fine_nrm,
+    fine_w, fine_h; 4^eta sub-patches per patch, see include/stokesgpu.h for the
+    node order) and the targets with their closest points y and normals n are
+    fixed; calls take the densities on the coarse nodes.  Defaults: q = 10,
+    eta = 2 (16 sub-patches), p = 4, R = 3 h_c, r = h_c with h_c the caller's
+    coarse node spacing."""
+
+    def __init__(self, npatch, fine_pts, fine_nrm, fine_w, fine_h, trg, y, n, R, r, p=4, q=10,
+                 eta=2, kernels=2, precision="mixed", near_ratio=1.0):
+        self.npatch, self.q, self.eta, self.p = int(npatch), int(q), int(eta), int(p)
+        self.R, self.r, self.kernels = float(R), float(r), int(kernels)
+        m = 1 << self.eta
+        nf = self.npatch * m * m * (self.q + 1) ** 2
+        self.fine = (A.vec3(fine_pts, "fine_pts", nf), A.vec3(fine_nrm, "fine_nrm", nf),
+                     A.vec1(fine_w, "fine_w", nf), A.vec1(fine_h, "fine_h", nf))
+        self.nt = trg.shape[0]
+        self.trg, self.y, self.n = (A.vec3(trg, "trg", self.nt), A.vec3(y, "y", self.nt),
+                                    A.vec3(n, "n", self.nt))
+        self.opts = A.make_opts(precision, near_ratio)
+        self.device = trg.device
+        nb = ctypes.c_size_t(0)
+        with torch.cuda.device(self.device):
+            A.check(A.lib().stokes_checkpoint_workspace_size(
+                self.kernels, self.npatch, self.q, self.eta, self.nt, self.p,
+                ctypes.byref(self.opts), ctypes.byref(nb)))
+        self.ws = A.workspace(nb.value, self.device)
+
+    def __call__(self, f=None, phi=None, mu=1.0, out=None, accumulate=False):
+        nc = self.npatch * (self.q + 1) ** 2
+        f = A.vec3(f, "f", nc) if f is not None else None
+        phi = A.vec3(phi, "phi", nc) if phi is not None else None
+        if out is None:
+            out = torch.zeros((self.nt, 3), dtype=torch.float64, device=self.device)
+        self.opts.accumulate = 1 if accumulate else 0
+        fp, fn, fw, fh = self.fine
+        with torch.cuda.device(self.device):
+            A.check(A.lib().stokes_checkpoint_eval(
+                self.kernels, A.ptr(f), A.ptr(phi), self.npatch, self.q, self.eta, A.ptr(fp),
+                A.ptr(fn), A.ptr(fw), A.ptr(fh), A.ptr(self.trg), A.ptr(self.y), A.ptr(self.n),
+                self.nt, self.R, self.r, self.p, float(mu), A.ptr(out), ctypes.byref(self.opts),
+                A.ptr(self.ws), self.ws.numel(), A.stream_ptr(self.device)))
+        return out

@@ -208,7 +208,8 @@ def _time_ms(fn, stream, flush, reps, warm=1):
 def run_forms(dev, flush, stream, peak_tflops):
     """The paper's other workloads on the same GPU: direct single layer (8 cells),
     direct double layer (256 cells + 65,536 off-surface targets), 2,048 batched
-    suspensions (autotuned tile, CUDA-graph replay) and the adjoint of SL + DL
+    suspensions (autotuned tile, CUDA-graph replay), the check-point quadrature
+    of the double layer on the 320-patch vessel wall and the adjoint of SL + DL
     (64 cells).  Each: device time per call, Gpair/s, % FP32 peak (mixed) and the
     rel-L2 error against the FP64 oracle on the stated sample."""
     import torch
@@ -288,6 +289,33 @@ def run_forms(dev, flush, stream, peak_tflops):
     log(f"[forms] batched: {forms['batched_2048_suspensions_graph']}")
     del graph, plan, pts, f, phi, nrm, w, h, out
     torch.cuda.empty_cache()
+
+    c6 = W.checkpoint_wall_workload()
+    p6 = 4
+    R6, r6 = 3.0 * c6.hc, c6.hc
+    x6, n6, phi6 = T(c6.pts), T(c6.nrm), T(c6.phi)
+    fp6, fn6, fw6, fh6 = T(c6.fine_pts), T(c6.fine_nrm), T(c6.fine_w), T(c6.fine_h)
+    plan6 = P.CheckpointPlan(c6.npatch, fp6, fn6, fw6, fh6, x6, x6, n6, R6, r6, p6, c6.q, c6.eta,
+                             kernels=2)
+    out6 = torch.empty((c6.pts.shape[0], 3), dtype=torch.float64, device=dev)
+    ms = _time_ms(lambda: plan6(None, phi6, out=out6), stream, flush, 3)
+    import oracle.checkpoint as OCK
+    pick = np.sort(rng.choice(c6.pts.shape[0], 32, replace=False))
+    ref6 = OCK.checkpoint_eval(2, None, c6.phi, c6.npatch, c6.q, 1 << c6.eta, c6.fine_pts,
+                               c6.fine_nrm, c6.fine_w, c6.pts[pick], c6.pts[pick], c6.nrm[pick],
+                               R6, r6, p6)
+    pairs6 = c6.pairs(p6)
+    amp = float(np.abs(OCK.extrapolation_weights(R6 + r6 * np.arange(p6 + 1), 0.0)).sum())
+    forms["checkpoint_dl_wall_320patches"] = {
+        "pairs": pairs6, "targets": int(c6.pts.shape[0]), "fine_nodes": int(c6.fine_pts.shape[0]),
+        "check_points_per_target": p6 + 1, "R_over_hc": 3.0, "r_over_hc": 1.0, "eta": c6.eta,
+        "mixed": {"ms": ms, "Gpair/s": pairs6 / ms / 1e6,
+                  "rel_l2": err(out6.cpu().numpy()[pick], ref6),
+                  "pct_fp32_peak": pct(pairs6, ms, "DL")},
+        "extrapolation_amplification": amp,
+        "sample": "32 random wall nodes (oracle: same steps in FP64)"}
+    log(f"[forms] checkpoint: {forms['checkpoint_dl_wall_320patches']}")
+    del plan6, fp6, fn6, fw6, fh6
 
     c5, g5 = W.adjoint_workload()
     n5 = c5.src.shape[0]

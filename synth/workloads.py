@@ -333,3 +333,41 @@ def batched_workload(nsusp: int = 2048, seed: int = SEED_BATCHED, max_cells: int
                            np.concatenate(w), np.concatenate(h), np.concatenate(f),
                            np.concatenate(phi), np.asarray(ptr, dtype=np.int64),
                            np.asarray(ncl, dtype=np.int64), 1.0)
+
+
+@dataclass
+class CheckpointWorkload:
+    """A vessel wall of Clenshaw-Curtis patches with its fine discretisation
+    (4^eta sub-patches per patch) and a double-layer density on the coarse
+    nodes; the targets are the coarse nodes themselves (closest point = node,
+    normal = node normal), as in the discretised boundary integral equation
+    (Sec. 3.1, Eq. "int_eq_disc")."""
+    name: str
+    npatch: int
+    q: int
+    eta: int
+    pts: np.ndarray
+    nrm: np.ndarray
+    w: np.ndarray
+    phi: np.ndarray
+    fine_pts: np.ndarray
+    fine_nrm: np.ndarray
+    fine_w: np.ndarray
+    fine_h: np.ndarray
+    hc: float
+
+    def pairs(self, p: int) -> int:
+        return int(self.fine_pts.shape[0]) * int(self.pts.shape[0]) * (p + 1)
+
+
+def checkpoint_wall_workload(radius: float = 50.0, length: float = 74.0, npatch: int = 320,
+                             q: int = 10, eta: int = 2, seed: int = SEED_P2P) -> CheckpointWorkload:
+    """The near-field benchmark's vessel wall (radius 50 um, 320 patches of 11 x 11
+    nodes) with 16 sub-patches per patch for the check-point quadrature."""
+    rng = rng_for(seed + 100)
+    nth, nz = _patch_grid(npatch, 2 * np.pi * radius, length)
+    cp, cn, cw, ch = G.cylinder_wall_patches(radius, length, nth, nz, q)
+    fp, fn, fw, fh = G.cylinder_wall_fine(radius, length, nth, nz, q, 1 << eta)
+    hc = float(np.sqrt(cw.sum() / cw.size))
+    return CheckpointWorkload(f"wall_{npatch}patches_q{q}_eta{eta}", npatch, q, eta, cp, cn, cw,
+                              densities(rng, cp.shape[0]), fp, fn, fw, fh, hc)

@@ -104,3 +104,24 @@ def checkpoint_eval(kernels: int, f, phi, npatch: int, q: int, m: int, fine_pts,
     for i in range(nt):
         out[i] = extrapolation_weights(tn, tx[i]) @ uc[i]
     return out
+
+
+def null_space_term(phi, nodes_n, nodes_w, trg_n) -> np.ndarray:
+    """(N phi)(x) = sum_m w_m (n(x) . phi_m) n_m, the rank-completing operator of
+    Eq. "double_layer_int_eq" discretised on the coarse nodes: M = sum_m w_m n_m
+    phi_m^T (3 x 3), then N phi(x) = M n(x)."""
+    M = np.einsum("m,mi,mj->ij", np.asarray(nodes_w), np.asarray(nodes_n), np.asarray(phi))
+    return np.asarray(trg_n) @ M.T
+
+
+def bie_matvec(phi, npatch: int, q: int, m: int, nodes, nodes_n, nodes_w, fine_pts, fine_nrm,
+               fine_w, R: float, r: float, p: int) -> np.ndarray:
+    """The boundary-integral operator of Eq. "double_layer_int_eq" / "int_eq_disc"
+    applied to a density on the coarse nodes, at the coarse nodes: the limit of
+    the double layer from the fluid side (check points c = y - (R + i r) n,
+    extrapolated to the node) plus N phi.  With the kernel orientation of this
+    build (a constant density gives -c on the fluid side) that limit is
+    (D - I/2) phi; the paper's +I/2 belongs to the opposite orientation of n."""
+    u = checkpoint_eval(2, None, phi, npatch, q, m, fine_pts, fine_nrm, fine_w, nodes, nodes,
+                        nodes_n, R, r, p)
+    return u + null_space_term(phi, nodes_n, nodes_w, nodes_n)

@@ -119,3 +119,27 @@ def test_refinement_reduces_the_error(sphere):
     e2 = np.abs(CK.checkpoint_eval(2, None, phi, 6, Q, 2, f2[0], f2[1], f2[2], x, y, n, 2 * hc, hc,
                                    P_EXT)[:, 0] + 1).max()
     assert e4 < e2 / 50, (e2, e4)
+
+
+def test_null_space_term_closed_forms(sphere):
+    """N on a sphere of radius a: N n = (4 pi a^2 / 3) n, N[a0 + w x y] = (4 pi a^3 / 3) n x w."""
+    a, (cp, cn, cw), _, hc = sphere
+    np.testing.assert_allclose(CK.null_space_term(cn, cn, cw, cn), 4 * np.pi * a * a / 3 * cn,
+                               rtol=0, atol=1e-5)
+    a0, om = np.array([0.2, -0.1, 0.4]), np.array([0.5, -0.4, 0.25])
+    got = CK.null_space_term(a0 + np.cross(om, cp), cn, cw, cn)
+    np.testing.assert_allclose(got, 4 * np.pi * a ** 3 / 3 * np.cross(cn, om), rtol=0, atol=1e-5)
+
+
+def test_bie_operator_null_vector_and_rigid_motion(sphere):
+    """The fluid-side limit of the double layer annihilates the normal field and
+    maps a + w x y to -(a + w x x) (Lorentz reciprocity), so the operator gives
+    N n for phi = n and -(a + w x x) + N[a + w x y] for a rigid motion."""
+    a, (cp, cn, cw), (fp, fn, fw), hc = sphere
+    u = CK.bie_matvec(cn, 6, Q, M, cp, cn, cw, fp, fn, fw, 3 * hc, hc, P_EXT)
+    ref = 4 * np.pi * a * a / 3 * cn
+    assert np.abs(u - ref).max() <= 1e-4 * np.abs(ref).max(), np.abs(u - ref).max()
+    a0, om = np.array([0.2, -0.1, 0.4]), np.array([0.5, -0.4, 0.25])
+    u = CK.bie_matvec(a0 + np.cross(om, cp), 6, Q, M, cp, cn, cw, fp, fn, fw, 3 * hc, hc, P_EXT)
+    ref = -(a0 + np.cross(om, cp)) + 4 * np.pi * a ** 3 / 3 * np.cross(cn, om)
+    assert np.abs(u - ref).max() <= 1e-4 * np.abs(ref).max(), np.abs(u - ref).max()

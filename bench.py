@@ -315,7 +315,19 @@ def run_forms(dev, flush, stream, peak_tflops):
         "extrapolation_amplification": amp,
         "sample": "32 random wall nodes (oracle: same steps in FP64)"}
     log(f"[forms] checkpoint: {forms['checkpoint_dl_wall_320patches']}")
-    del plan6, fp6, fn6, fw6, fh6
+    # the boundary-integral operator (D - I/2 + N) on the same wall
+    w6 = T(c6.w)
+    bie = P.BIEPlan(c6.npatch, x6, n6, w6, fp6, fn6, fw6, fh6, R6, r6, p6, c6.q, c6.eta)
+    outb = torch.empty_like(out6)
+    msb = _time_ms(lambda: bie.matvec(phi6, out=outb), stream, flush, 3)
+    nterm = outb.cpu().numpy() - out6.cpu().numpy()
+    nref = OCK.null_space_term(c6.phi, c6.nrm, c6.w, c6.nrm)
+    forms["bie_matvec_wall_320patches"] = {
+        "pairs": pairs6, "mixed": {"ms": msb, "Gpair/s": pairs6 / msb / 1e6,
+                                   "null_term_rel_l2": err(nterm, nref)},
+        "note": "(D - I/2 + N) phi at all 38,720 nodes; D - I/2 by the check points above"}
+    log(f"[forms] bie matvec: {forms['bie_matvec_wall_320patches']}")
+    del plan6, bie, fp6, fn6, fw6, fh6
 
     c5, g5 = W.adjoint_workload()
     n5 = c5.src.shape[0]

@@ -232,6 +232,28 @@ stk_status stokes_checkpoint_eval(int32_t kernels, const double *f, const double
 stk_status stokes_checkpoint_workspace_size(int32_t kernels, int32_t npatch, int32_t q,
                                             int32_t eta, int64_t nt, int32_t p,
                                             const stk_opts *opts, size_t *bytes);
+/* The boundary-integral operator of Eq. "double_layer_int_eq" (discretised as
+ * Eq. "int_eq_disc") applied to a double-layer density phi on the coarse nodes,
+ * evaluated at the coarse nodes:
+ *   out = (D - I/2) phi + N phi,
+ * (D - I/2) phi being the limit of the double layer from the fluid side, taken
+ * by stokes_checkpoint_eval with targets = closest points = the nodes and
+ * normals nodes_n (check points y - (R + i r) n), and
+ *   (N phi)(x) = sum_m w_m (n(x) . phi_m) n_m
+ * the rank-completing operator (FP64, fixed-order reduction).  With this
+ * library's kernel orientation (a constant density gives -c on the fluid
+ * side, n pointing out of the fluid) the paper's +I/2 appears as -I/2.
+ * nodes, nodes_n [npatch (q+1)^2][3], nodes_w [npatch (q+1)^2]; the fine
+ * discretisation as for stokes_checkpoint_eval.  out is overwritten unless
+ * opts->accumulate. */
+stk_status stokes_bie_matvec(const double *phi, int32_t npatch, int32_t q, int32_t eta,
+                             const double *nodes, const double *nodes_n, const double *nodes_w,
+                             const double *fine_pts, const double *fine_nrm, const double *fine_w,
+                             const double *fine_h, double R, double r, int32_t p, double *out,
+                             const stk_opts *opts, void *workspace, size_t workspace_bytes,
+                             void *stream);
+stk_status stokes_bie_workspace_size(int32_t npatch, int32_t q, int32_t eta, int32_t p,
+                                     const stk_opts *opts, size_t *bytes);
 /* Step 1 alone: coarse [npatch (q+1)^2][ncomp] -> fine [npatch m^2 (q+1)^2][ncomp]
  * (FP64, ncomp 1..3), the upsampling operator U of Sec. 3.1. */
 stk_status stokes_upsample_patches(const double *coarse, int32_t npatch, int32_t q, int32_t eta,

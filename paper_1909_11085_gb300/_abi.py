@@ -30,7 +30,7 @@ EXPORTS = [
     "stokes_tile_config_count", "stokes_autotune_p2p", "stokes_autotune_batched",
     "stokes_p2p_graph_create", "stokes_batched_graph_create", "stokes_graph_launch",
     "stokes_graph_destroy", "stokes_checkpoint_eval", "stokes_checkpoint_workspace_size",
-    "stokes_upsample_patches",
+    "stokes_upsample_patches", "stokes_bie_matvec", "stokes_bie_workspace_size",
 ]
 
 
@@ -97,6 +97,9 @@ def lib():
                                                  i64, d, d, i32, d, p, po, p, sz, p]
             L.stokes_checkpoint_workspace_size.argtypes = [i32, i32, i32, i32, i64, i32, po, psz]
             L.stokes_upsample_patches.argtypes = [p, i32, i32, i32, i32, p, p]
+            L.stokes_bie_matvec.argtypes = [p, i32, i32, i32, p, p, p, p, p, p, p, d, d, i32, p,
+                                            po, p, sz, p]
+            L.stokes_bie_workspace_size.argtypes = [i32, i32, i32, i32, po, psz]
             L.stokes_graph_destroy.argtypes = [p]
             L.stokes_launch_count.restype = ctypes.c_int64
             for name in EXPORTS:

@@ -137,6 +137,58 @@ __global__ void k_extrapolate(int64_t nt, int p, double R, double r, const doubl
   }
 }
 
+// Rank-completing term of the boundary-integral equation: M = sum_m w_m n_m
+// phi_m^T over the coarse nodes, in two fixed-order stages (per-block partial
+// sums, then every apply block adds the partials in block order), and
+// out[t] += M n[t].
+constexpr int kNullBlocks = 128;
+constexpr int kNullThreads = 256;
+
+__global__ void __launch_bounds__(kNullThreads) k_null_partial(int64_t n, const double *__restrict__ nn,
+                                                               const double *__restrict__ w,
+                                                               const double *__restrict__ phi,
+                                                               double *__restrict__ part) {
+  __shared__ double s[9][kNullThreads];
+  double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = blockIdx.x * per, b1 = min(n, b0 + per);
+  for (int64_t m = b0 + threadIdx.x; m < b1; m += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc[3 * i + j] = fma(w[m] * nn[3 * m + i], phi[3 * m + j], acc[3 * i + j]);
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 9) part[9 * blockIdx.x + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kNullThreads) k_null_apply(int64_t nt, int nparts,
+                                                             const double *__restrict__ part,
+                                                             const double *__restrict__ tn,
+                                                             double *__restrict__ out) {
+  __shared__ double M[9];
+  if (threadIdx.x < 9) {
+    double v = 0.0;
+    for (int b = 0; b < nparts; ++b) v += part[9 * b + threadIdx.x];
+    M[threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt;
+       t += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      out[3 * t + i] += M[3 * i] * tn[3 * t] + M[3 * i + 1] * tn[3 * t + 1] + M[3 * i + 2] * tn[3 * t + 2];
+  }
+}
+
 int grid_1d(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -275,6 +327,46 @@ stk_status stokes_checkpoint_eval(int32_t kernels, const double *f, const double
   count_launches(1);
   if (cudaGetLastError() != cudaSuccess)
     return report_error(STK_ECUDA, "k_extrapolate launch failed");
+  return STK_OK;
+}
+
+stk_status stokes_bie_workspace_size(int32_t npatch, int32_t q, int32_t eta, int32_t p,
+                                     const stk_opts *opts, size_t *bytes) {
+  const int64_t nc = (int64_t)npatch * (q + 1) * (q + 1);
+  stk_status s = stokes_checkpoint_workspace_size(2, npatch, q, eta, nc, p, opts, bytes);
+  if (s != STK_OK) return s;
+  *bytes += sizeof(double) * 9 * kNullBlocks + 256;
+  return STK_OK;
+}
+
+stk_status stokes_bie_matvec(const double *phi, int32_t npatch, int32_t q, int32_t eta,
+                             const double *nodes, const double *nodes_n, const double *nodes_w,
+                             const double *fine_pts, const double *fine_nrm, const double *fine_w,
+                             const double *fine_h, double R, double r, int32_t p, double *out,
+                             const stk_opts *opts, void *workspace, size_t workspace_bytes,
+                             void *stream) {
+  if (!opts) return report_error(STK_EINVAL, "opts is NULL");
+  size_t need = 0;
+  stk_status s = stokes_bie_workspace_size(npatch, q, eta, p, opts, &need);
+  if (s != STK_OK) return s;
+  const int64_t nc = (int64_t)npatch * (q + 1) * (q + 1);
+  if (nc == 0) return STK_OK;
+  if (!phi || !nodes || !nodes_n || !nodes_w || !out)
+    return report_error(STK_EINVAL, "phi/nodes/nodes_n/nodes_w/out is NULL");
+  if (!workspace || workspace_bytes < need) return report_error(STK_ENOMEM, "workspace too small");
+  const size_t cp_bytes = need - sizeof(double) * 9 * kNullBlocks - 256;
+  s = stokes_checkpoint_eval(2, nullptr, phi, npatch, q, eta, fine_pts, fine_nrm, fine_w, fine_h,
+                             nodes, nodes, nodes_n, nc, R, r, p, 1.0, out, opts, workspace,
+                             cp_bytes, stream);
+  if (s != STK_OK) return s;
+  const uintptr_t u = reinterpret_cast<uintptr_t>(workspace) + cp_bytes;
+  double *part = reinterpret_cast<double *>((u + 255) & ~(uintptr_t)255);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  k_null_partial<<<kNullBlocks, kNullThreads, 0, st>>>(nc, nodes_n, nodes_w, phi, part);
+  k_null_apply<<<grid_1d(nc, kNullThreads), kNullThreads, 0, st>>>(nc, kNullBlocks, part, nodes_n,
+                                                                   out);
+  count_launches(2);
+  if (cudaGetLastError() != cudaSuccess) return report_error(STK_ECUDA, "null-space term launch failed");
   return STK_OK;
 }
 

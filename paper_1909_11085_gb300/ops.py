@@ -417,3 +417,46 @@ class CheckpointPlan:
                 self.nt, self.R, self.r, self.p, float(mu), A.ptr(out), ctypes.byref(self.opts),
                 A.ptr(self.ws), self.ws.numel(), A.stream_ptr(self.device)))
         return out
+
+
+class BIEPlan:
+    """The boundary-integral operator (D - I/2 + N) of a fixed patch surface
+    (Eq. "double_layer_int_eq", discretised as Eq. "int_eq_disc"), applied by
+    matvec(phi) to double-layer densities on the coarse nodes; D - I/2 is the
+    fluid-side limit taken by check points (see CheckpointPlan), N the
+    rank-completing term.  Sign convention: n points out of the fluid."""
+
+    def __init__(self, npatch, nodes, nodes_n, nodes_w, fine_pts, fine_nrm, fine_w, fine_h, R, r,
+                 p=4, q=10, eta=2, precision="mixed", near_ratio=1.0):
+        self.npatch, self.q, self.eta, self.p = int(npatch), int(q), int(eta), int(p)
+        self.R, self.r = float(R), float(r)
+        nc = self.npatch * (self.q + 1) ** 2
+        m = 1 << self.eta
+        nf = self.npatch * m * m * (self.q + 1) ** 2
+        self.nodes = (A.vec3(nodes, "nodes", nc), A.vec3(nodes_n, "nodes_n", nc),
+                      A.vec1(nodes_w, "nodes_w", nc))
+        self.fine = (A.vec3(fine_pts, "fine_pts", nf), A.vec3(fine_nrm, "fine_nrm", nf),
+                     A.vec1(fine_w, "fine_w", nf), A.vec1(fine_h, "fine_h", nf))
+        self.nc = nc
+        self.device = nodes.device
+        self.opts = A.make_opts(precision, near_ratio)
+        nb = ctypes.c_size_t(0)
+        with torch.cuda.device(self.device):
+            A.check(A.lib().stokes_bie_workspace_size(self.npatch, self.q, self.eta, self.p,
+                                                      ctypes.byref(self.opts), ctypes.byref(nb)))
+        self.ws = A.workspace(nb.value, self.device)
+
+    def matvec(self, phi, out=None, accumulate=False):
+        phi = A.vec3(phi, "phi", self.nc)
+        if out is None:
+            out = torch.zeros((self.nc, 3), dtype=torch.float64, device=self.device)
+        self.opts.accumulate = 1 if accumulate else 0
+        x, xn, xw = self.nodes
+        fp, fn, fw, fh = self.fine
+        with torch.cuda.device(self.device):
+            A.check(A.lib().stokes_bie_matvec(
+                A.ptr(phi), self.npatch, self.q, self.eta, A.ptr(x), A.ptr(xn), A.ptr(xw),
+                A.ptr(fp), A.ptr(fn), A.ptr(fw), A.ptr(fh), self.R, self.r, self.p, A.ptr(out),
+                ctypes.byref(self.opts), A.ptr(self.ws), self.ws.numel(),
+                A.stream_ptr(self.device)))
+        return out

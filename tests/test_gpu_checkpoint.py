@@ -122,3 +122,22 @@ def test_vessel_wall_patches_and_edge_cases(lib):
     empty = torch.empty((0, 3), dtype=torch.float64, device="cuda")
     plan_e = lib.CheckpointPlan(npatch, FP, FN, FW, FH, empty, empty, empty, 3 * hc, hc, 3)
     assert plan_e(None, PHI).shape == (0, 3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bie_matvec_matches_oracle(lib, precision):
+    (cp, cn), (fp, fn, fw, fh), hc = _sphere(a=1.4)
+    cw = G.cubed_sphere_patches(1.4, 10, 1)[2]
+    rng = np.random.default_rng(19)
+    phi = rng.uniform(-1, 1, (cp.shape[0], 3))
+    R, r, p = 3 * hc, hc, 4
+    ref = CK.bie_matvec(phi, 6, 10, 4, cp, cn, cw, fp, fn, fw, R, r, p)
+    X, N, W, FP, FN, FW, FH, PHI = cuda(cp, cn, cw, fp, fn, fw, fh, phi)
+    plan = lib.BIEPlan(6, X, N, W, FP, FN, FW, FH, R, r, p, precision=precision)
+    u = plan.matvec(PHI).cpu().numpy()
+    tol = 1e-12 if precision == "fp64" else mixed_tol(R, r, p)
+    assert rel_l2(u, ref) <= tol, rel_l2(u, ref)
+    # the normal field: only the rank-completing term remains (closed form)
+    un = plan.matvec(N).cpu().numpy()
+    refn = 4 * np.pi * 1.4 ** 2 / 3 * cn
+    assert np.abs(un - refn).max() <= 1e-4 * np.abs(refn).max()

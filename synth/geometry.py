@@ -267,11 +267,11 @@ _CUBE_FACES = ((2, 1.0), (2, -1.0), (0, 1.0), (0, -1.0), (1, 1.0), (1, -1.0))
 def _cubed_sphere_map(a: float):
     def mapping(pch, u, v):
         ax, sg = _CUBE_FACES[pch]
-        o = [i for i in range(3) if i != ax]
+        o = [(ax + 1) % 3, (ax + 2) % 3]  # cyclic axes: dP/du x dP/dv points outward
         c = np.zeros((u.size, 3))
         c[:, ax] = sg
         c[:, o[0]] = u
-        c[:, o[1]] = v * sg  # keeps every face's (u, v) frame right-handed
+        c[:, o[1]] = v * sg
         r = np.linalg.norm(c, axis=1)
         n = c / r[:, None]
         # gnomonic projection of a cube face: area element a^2 / |c|^3

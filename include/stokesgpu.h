@@ -259,6 +259,26 @@ stk_status stokes_bie_workspace_size(int32_t npatch, int32_t q, int32_t eta, int
 stk_status stokes_upsample_patches(const double *coarse, int32_t npatch, int32_t q, int32_t eta,
                                    int32_t ncomp, double *fine, void *stream);
 
+/* ------------------------------------------------------ near-zone search
+ * For each target x: the patch of a patch surface closest to x when x lies
+ * within d_eps of it, the closest point y = P(u*, v*), the unit normal
+ * (dP/du x dP/dv)/|...| there and the distance (Sec. 3.2, the closest-point
+ * search, steps a-e: inflated patch boxes, a spatial hash of the boxes and the
+ * targets, sorted keys, Newton's method with a backtracking line search per
+ * candidate patch, the nearest patch kept).  A patch is the degree-q
+ * tensor-product interpolant through its (q+1) x (q+1) Clenshaw-Curtis nodes,
+ * ordered as for stokes_checkpoint_eval.  nodes [npatch (q+1)^2][3],
+ * trg [nt][3]; outputs: patch [nt] (-1: none within d_eps), uv [nt][2],
+ * y [nt][3], n [nt][3], dist [nt] (-1 for none).  Patch boxes are grown by
+ * d_eps and 5% of their diagonal, so a target whose closest point lies
+ * further outside its patch's node box than that is not found.  FP64.
+ * 2 <= q <= 12. */
+stk_status stokes_near_patch_search(const double *nodes, int32_t npatch, int32_t q,
+                                    const double *trg, int64_t nt, double d_eps, int32_t *patch,
+                                    double *uv, double *y, double *n, double *dist,
+                                    void *workspace, size_t workspace_bytes, void *stream);
+stk_status stokes_near_search_workspace_size(int32_t npatch, int32_t q, size_t *bytes);
+
 /* ------------------------------------------------- no-allocation variant
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory when they need a velocity (an application

@@ -7,7 +7,9 @@ package only marshals PyTorch tensors into it.  Build the library with
 paper_1909_11085_gb300.build.build().
 """
 from .ops import (sl, dl, sldl, p2p, batched, sldl_grad, StokesLayerFn,  # noqa: F401
-                  P2PPlan, BatchedPlan, CheckpointPlan, BIEPlan, upsample_patches)
+                  P2PPlan, BatchedPlan, CheckpointPlan, BIEPlan, upsample_patches,
+                  near_patch_search)
 
 __all__ = ["sl", "dl", "sldl", "p2p", "batched", "sldl_grad", "StokesLayerFn", "P2PPlan",
-           "BatchedPlan", "CheckpointPlan", "BIEPlan", "upsample_patches"]
+           "BatchedPlan", "CheckpointPlan", "BIEPlan", "upsample_patches",
+           "near_patch_search"]

@@ -31,6 +31,7 @@ EXPORTS = [
     "stokes_p2p_graph_create", "stokes_batched_graph_create", "stokes_graph_launch",
     "stokes_graph_destroy", "stokes_checkpoint_eval", "stokes_checkpoint_workspace_size",
     "stokes_upsample_patches", "stokes_bie_matvec", "stokes_bie_workspace_size",
+    "stokes_near_patch_search", "stokes_near_search_workspace_size",
 ]
 
 
@@ -100,6 +101,9 @@ def lib():
             L.stokes_bie_matvec.argtypes = [p, i32, i32, i32, p, p, p, p, p, p, p, d, d, i32, p,
                                             po, p, sz, p]
             L.stokes_bie_workspace_size.argtypes = [i32, i32, i32, i32, po, psz]
+            L.stokes_near_patch_search.argtypes = [p, i32, i32, p, i64, d, p, p, p, p, p, p, sz,
+                                                   p]
+            L.stokes_near_search_workspace_size.argtypes = [i32, i32, psz]
             L.stokes_graph_destroy.argtypes = [p]
             L.stokes_launch_count.restype = ctypes.c_int64
             for name in EXPORTS:

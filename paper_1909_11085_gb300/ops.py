@@ -460,3 +460,28 @@ class BIEPlan:
                 ctypes.byref(self.opts), A.ptr(self.ws), self.ws.numel(),
                 A.stream_ptr(self.device)))
         return out
+
+
+def near_patch_search(nodes, npatch, trg, d_eps, q=10):
+    """Closest patch and point for every target within d_eps of a patch surface
+    (Sec. 3.2): returns (patch [nt] int32, -1 for none; uv [nt, 2]; y [nt, 3];
+    n [nt, 3]; dist [nt], -1 for none)."""
+    nc = int(npatch) * (q + 1) ** 2
+    nodes = A.vec3(nodes, "nodes", nc)
+    trg = A.vec3(trg, "trg")
+    nt = trg.shape[0]
+    dev = trg.device
+    patch = torch.empty(nt, dtype=torch.int32, device=dev)
+    uv = torch.empty((nt, 2), dtype=torch.float64, device=dev)
+    y = torch.empty((nt, 3), dtype=torch.float64, device=dev)
+    n = torch.empty((nt, 3), dtype=torch.float64, device=dev)
+    dist = torch.empty(nt, dtype=torch.float64, device=dev)
+    nb = ctypes.c_size_t(0)
+    A.check(A.lib().stokes_near_search_workspace_size(int(npatch), int(q), ctypes.byref(nb)))
+    ws = A.workspace(nb.value, dev)
+    with torch.cuda.device(dev):
+        A.check(A.lib().stokes_near_patch_search(
+            A.ptr(nodes), int(npatch), int(q), A.ptr(trg), nt, float(d_eps), A.ptr(patch),
+            A.ptr(uv), A.ptr(y), A.ptr(n), A.ptr(dist), A.ptr(ws), ws.numel(),
+            A.stream_ptr(dev)))
+    return patch, uv, y, n, dist

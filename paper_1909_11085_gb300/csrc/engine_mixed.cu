@@ -25,8 +25,15 @@
 //    the same arithmetic afterwards and adds those pairs with the FP64
 //    difference and 1/|r|, whose FP64 work would otherwise stall this FP32
 //    engine.
-//  * Accumulation: plain FP32 over two chunks (<= 128 terms per lane), then a
-//    two-sum into per-target (hi, lo) kept in shared memory.
+//  * Packed FP32 pairs: a lane evaluates two sources at once against each of
+//    its targets with the sm_100 two-wide FP32 instructions (add/mul/fma on
+//    float2), so one issued instruction does the work of two pairs.  Staged
+//    sources are laid out as pairs, field-interleaved (x of both, then y of
+//    both, ...), with the position negated so that d = x + (-y) is one packed
+//    add; that is the same IEEE operation as x - y, bit for bit.
+//  * Accumulation: plain FP32 over two chunks (<= 64 terms per lane and half),
+//    then the two halves are added and two-summed into per-target (hi, lo)
+//    kept in shared memory.
 //  * The kernel is instantiated per kernel kind (SL, DL, SL+DL, or SL/DL by
 //    segment parity for batched suspensions) so that a launch only runs the
 //    code of its own kind, which keeps the hot loops inside the instruction
@@ -45,12 +52,16 @@ namespace stk {
 constexpr int kSegWin = 64;  // segments read into shared memory at a time
 constexpr int kTMax = 5;     // most targets per lane
 
+constexpr int kPairs = kChunk / 2;  // staged source pairs per chunk
+constexpr int kFields = 7;          // float4 fields per source pair
+
+// Field f of source pair j holds two quantities of both sources (a0, a1, b0, b1):
+//   0: -y_x, -y_y   1: -y_z, hh   2: q_x, q_y   3: q_z, n_x   4: n_y, n_z
+//   5: psi_x, psi_y 6: psi_z, -
+// hh is (alpha h)^2 for candidates and 0 for far sources (never masked).
 struct __align__(16) WarpSmem {
   SrcRec raw[kChunk];               // bulk-copy destination
-  float4 Y[kChunk];                 // local position + hh
-  float4 Q[kChunk];                 // SL density (scaled) + source index bits
-  float4 N[kChunk];                 // normal
-  float4 Pd[kChunk];                // DL density (scaled)
+  float4 S[kFields][kPairs];        // staged source pairs in local coordinates
   float acc[2 * kTMax * 3][kWarp];  // per-lane compensated sums (hi, lo), lane-minor
   float frame[12];                  // item origin (hi x3, lo x3) and bounding box (lo x3, hi x3)
   int32_t run_s[kSegWin];           // source runs of the current segment window: start
@@ -121,43 +132,58 @@ __device__ __forceinline__ void issue_chunk(WarpSmem &sm, const SrcRec *rec, int
 }
 
 // ---------------------------------------------------------------- pair math
-// Adds the far-field contribution of one staged source to T targets.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// Adds the far-field contribution of one staged source pair to T targets
+// (x2: each coordinate duplicated into both halves; ps: per-half sums).
 // SL:   q/r + d (d.q)/r^3             (q pre-scaled by w / (8 pi mu))
 // DL:   d (d.psi)(d.n)/r^5            (psi pre-scaled by 6 w / (8 pi))
 // SLDL: q/r + d [(d.q)/r^3 + (d.psi)(d.n)/r^5]
+// Per half the operations, operands and rounding are those of a scalar
+// evaluation: d = x - y, |r|^2 = dx dx + (dy dy + dz dz) (pair_r2).
 template <int T, int KIND, bool MASKED>
-__device__ __forceinline__ void pair_block(const float (&x)[T][3], float (&ps)[T][3], float4 Y,
-                                           float4 Q, float4 N, float4 Pd) {
+__device__ __forceinline__ void pair_block(const float2 (&x2)[T][3], float2 (&ps)[T][3],
+                                           const float4 (&s)[kFields]) {
+  const float2 ny_x = lo2(s[0]), ny_y = hi2(s[0]), ny_z = lo2(s[1]), hh = hi2(s[1]);
+  const float2 qx = lo2(s[2]), qy = hi2(s[2]), qz = lo2(s[3]);
+  const float2 nx = hi2(s[3]), ny = lo2(s[4]), nz = hi2(s[4]);
+  const float2 px = lo2(s[5]), py = hi2(s[5]), pz = lo2(s[6]);
 #pragma unroll
   for (int t = 0; t < T; ++t) {
-    const float dx = __fsub_rn(x[t][0], Y.x), dy = __fsub_rn(x[t][1], Y.y),
-                dz = __fsub_rn(x[t][2], Y.z);
-    float r2 = pair_r2(dx, dy, dz);
+    const float2 dx = add2(x2[t][0], ny_x), dy = add2(x2[t][1], ny_y), dz = add2(x2[t][2], ny_z);
+    float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     // near pair: rsqrt(+inf) = 0 removes it from this sum (k_near adds it)
-    if (MASKED && is_near(r2, Y.w)) r2 = __int_as_float(0x7f800000);
-    const float ri = rsqrt_ftz(r2);
-    const float ri2 = ri * ri;
+    if (MASKED) {
+      if (is_near(r2.x, hh.x)) r2.x = __int_as_float(0x7f800000);
+      if (is_near(r2.y, hh.y)) r2.y = __int_as_float(0x7f800000);
+    }
+    const float2 ri = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+    const float2 ri2 = mul2(ri, ri);
     if (KIND == K_SL) {
-      const float dq = fmaf(dx, Q.x, fmaf(dy, Q.y, dz * Q.z));
-      const float c = dq * ri2;
-      ps[t][0] = fmaf(fmaf(dx, c, Q.x), ri, ps[t][0]);
-      ps[t][1] = fmaf(fmaf(dy, c, Q.y), ri, ps[t][1]);
-      ps[t][2] = fmaf(fmaf(dz, c, Q.z), ri, ps[t][2]);
+      const float2 dq = fma2(dx, qx, fma2(dy, qy, mul2(dz, qz)));
+      const float2 c = mul2(dq, ri2);
+      ps[t][0] = fma2(fma2(dx, c, qx), ri, ps[t][0]);
+      ps[t][1] = fma2(fma2(dy, c, qy), ri, ps[t][1]);
+      ps[t][2] = fma2(fma2(dz, c, qz), ri, ps[t][2]);
     } else if (KIND == K_DL) {
-      const float dp = fmaf(dx, Pd.x, fmaf(dy, Pd.y, dz * Pd.z));
-      const float dn = fmaf(dx, N.x, fmaf(dy, N.y, dz * N.z));
-      const float c = (dp * dn) * (ri2 * ri2 * ri);
-      ps[t][0] = fmaf(dx, c, ps[t][0]);
-      ps[t][1] = fmaf(dy, c, ps[t][1]);
-      ps[t][2] = fmaf(dz, c, ps[t][2]);
+      const float2 dp = fma2(dx, px, fma2(dy, py, mul2(dz, pz)));
+      const float2 dn = fma2(dx, nx, fma2(dy, ny, mul2(dz, nz)));
+      const float2 c = mul2(mul2(dp, dn), mul2(mul2(ri2, ri2), ri));
+      ps[t][0] = fma2(dx, c, ps[t][0]);
+      ps[t][1] = fma2(dy, c, ps[t][1]);
+      ps[t][2] = fma2(dz, c, ps[t][2]);
     } else {
-      const float dq = fmaf(dx, Q.x, fmaf(dy, Q.y, dz * Q.z));
-      const float dp = fmaf(dx, Pd.x, fmaf(dy, Pd.y, dz * Pd.z));
-      const float dn = fmaf(dx, N.x, fmaf(dy, N.y, dz * N.z));
-      const float c = fmaf(dp * dn, ri2, dq) * ri2;
-      ps[t][0] = fmaf(fmaf(dx, c, Q.x), ri, ps[t][0]);
-      ps[t][1] = fmaf(fmaf(dy, c, Q.y), ri, ps[t][1]);
-      ps[t][2] = fmaf(fmaf(dz, c, Q.z), ri, ps[t][2]);
+      const float2 dq = fma2(dx, qx, fma2(dy, qy, mul2(dz, qz)));
+      const float2 dp = fma2(dx, px, fma2(dy, py, mul2(dz, pz)));
+      const float2 dn = fma2(dx, nx, fma2(dy, ny, mul2(dz, nz)));
+      const float2 c = mul2(fma2(mul2(dp, dn), ri2, dq), ri2);
+      ps[t][0] = fma2(fma2(dx, c, qx), ri, ps[t][0]);
+      ps[t][1] = fma2(fma2(dy, c, qy), ri, ps[t][1]);
+      ps[t][2] = fma2(fma2(dz, c, qz), ri, ps[t][2]);
     }
   }
 }
@@ -167,35 +193,46 @@ struct ItemCtx {
   int32_t t0;
 };
 
+template <int KIND>
+__device__ __forceinline__ void load_pair(const WarpSmem &sm, int j, float4 (&s)[kFields]) {
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  s[0] = sm.S[0][j];
+  s[1] = sm.S[1][j];
+  s[2] = (KIND & K_SL) ? sm.S[2][j] : z4;
+  s[3] = sm.S[3][j];
+  s[4] = (KIND & K_DL) ? sm.S[4][j] : z4;
+  s[5] = (KIND & K_DL) ? sm.S[5][j] : z4;
+  s[6] = (KIND & K_DL) ? sm.S[6][j] : z4;
+}
+
+// Pairs [0, nfar / 2) hold far sources only; pairs from nfar / 2 to the end
+// hold candidates (and possibly one far source with hh = 0, and a zero pad).
 template <int T, int KIND>
 __device__ __forceinline__ void chunk_compute(WarpSmem &sm, const EngineParams &P,
                                               const ItemCtx &ic, int n, int nfar,
-                                              const float (&x)[T][3], float (&ps)[T][3]) {
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  // far sources: no per-pair test
-  for (int k = ic.sg; k < nfar; k += ic.b) {
-    const float4 Y = sm.Y[k];
-    const float4 Q = (KIND & K_SL) ? sm.Q[k] : z4;
-    const float4 N = (KIND & K_DL) ? sm.N[k] : z4;
-    const float4 Pd = (KIND & K_DL) ? sm.Pd[k] : z4;
-    pair_block<T, KIND, false>(x, ps, Y, Q, N, Pd);
+                                              const float2 (&x2)[T][3], float2 (&ps)[T][3]) {
+  const int jfar = nfar >> 1, jend = (n + 1) >> 1;
+  for (int j = ic.sg; j < jfar; j += ic.b) {
+    float4 s[kFields];
+    load_pair<KIND>(sm, j, s);
+    pair_block<T, KIND, false>(x2, ps, s);
   }
-  // candidates: per-pair near test
-  for (int k = nfar + ic.sg; k < n; k += ic.b) {
-    const float4 Y = sm.Y[k];
-    const float4 Q = (KIND & K_SL) ? sm.Q[k] : z4;
-    const float4 N = (KIND & K_DL) ? sm.N[k] : z4;
-    const float4 Pd = (KIND & K_DL) ? sm.Pd[k] : z4;
-    pair_block<T, KIND, true>(x, ps, Y, Q, N, Pd);
+  for (int j = jfar + ic.sg; j < jend; j += ic.b) {
+    float4 s[kFields];
+    load_pair<KIND>(sm, j, s);
+    pair_block<T, KIND, true>(x2, ps, s);
   }
 }
 
 // Converts the staged raw chunk to local coordinates, far sources first.
 // Candidates are also listed for k_near (source index | kind << 30, at most
 // cap per item; ccount keeps counting past cap to flag an overflow).
+template <int KMODE>
 __device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, int lane, int32_t *clist,
-                                             int cap, int &ccount, int32_t s0,
-                                             uint32_t kind_bits) {
+                                             int cap, int &ccount, int32_t s0, int kind) {
+  const int kd = KMODE ? KMODE : kind;
+  const uint32_t kind_bits = (uint32_t)kind << 30;
+  float *S = reinterpret_cast<float *>(&sm.S[0][0]);
   const float oh[3] = {sm.frame[0], sm.frame[1], sm.frame[2]};
   const float ol[3] = {sm.frame[3], sm.frame[4], sm.frame[5]};
   const float blo[3] = {sm.frame[6], sm.frame[7], sm.frame[8]};
@@ -229,13 +266,35 @@ __device__ __forceinline__ int convert_chunk(WarpSmem &sm, int n, int lane, int3
     ccount += __popc(bc);
     if (valid) {
       const int dst = cand ? (n - 1 - (ncand + __popc(bc & lt))) : (nfar + __popc(bf & lt));
-      sm.Y[dst] = Y;
-      sm.Q[dst] = q;
-      sm.N[dst] = nn;
-      sm.Pd[dst] = pp;
+      float *d = S + 4 * (dst >> 1) + (dst & 1);  // component a_h of field 0
+      constexpr int F = 4 * kPairs;               // floats per field
+      d[0] = -Y.x;
+      d[2] = -Y.y;
+      d[F] = -Y.z;
+      d[F + 2] = cand ? Y.w : 0.f;
+      if (kd & K_SL) {
+        d[2 * F] = q.x;
+        d[2 * F + 2] = q.y;
+        d[3 * F] = q.z;
+      }
+      if (kd & K_DL) {
+        d[3 * F + 2] = nn.x;
+        d[4 * F] = nn.y;
+        d[4 * F + 2] = nn.z;
+        d[5 * F] = pp.x;
+        d[5 * F + 2] = pp.y;
+        d[6 * F] = pp.z;
+      }
     }
     nfar += __popc(bf);
     ncand += __popc(bc);
+  }
+  // an odd count leaves the second half of the last pair: a zero-density
+  // source far away (no NaN arises: |r|^2 ~ 3e36 stays finite)
+  if ((n & 1) && lane < kFields) {
+    float *d = S + lane * 4 * kPairs + 4 * (n >> 1) + 1;
+    d[0] = lane < 2 ? -1e18f : 0.f;
+    d[2] = lane == 0 ? -1e18f : 0.f;
   }
   return nfar;
 }
@@ -327,13 +386,13 @@ __device__ __forceinline__ bool cursor_next(const EngineParams &P, const Item &i
 template <int T, int KMODE>
 __device__ __forceinline__ void dispatch_compute(int kind, WarpSmem &sm, const EngineParams &P,
                                                  const ItemCtx &ic, int n, int nfar,
-                                                 const float (&x)[T][3], float (&ps)[T][3]) {
+                                                 const float2 (&x2)[T][3], float2 (&ps)[T][3]) {
   if (KMODE != 0) {
-    chunk_compute<T, KMODE>(sm, P, ic, n, nfar, x, ps);
+    chunk_compute<T, KMODE>(sm, P, ic, n, nfar, x2, ps);
   } else if (kind == K_SL) {
-    chunk_compute<T, K_SL>(sm, P, ic, n, nfar, x, ps);
+    chunk_compute<T, K_SL>(sm, P, ic, n, nfar, x2, ps);
   } else {
-    chunk_compute<T, K_DL>(sm, P, ic, n, nfar, x, ps);
+    chunk_compute<T, K_DL>(sm, P, ic, n, nfar, x2, ps);
   }
 }
 
@@ -455,12 +514,13 @@ __device__ bool run_item(const EngineParams &P, const Item &it, int id, WarpSmem
       }
   }
 
-  float ps[T][3];
+  float2 x2[T][3], ps[T][3];
 #pragma unroll
   for (int t = 0; t < T; ++t)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      ps[t][k] = 0.f;
+      x2[t][k] = make_float2(x[t][k], x[t][k]);
+      ps[t][k] = make_float2(0.f, 0.f);
       sm.acc[t * 3 + k][lane] = 0.f;
       sm.acc[(T + t) * 3 + k][lane] = 0.f;
     }
@@ -496,8 +556,8 @@ __device__ bool run_item(const EngineParams &P, const Item &it, int id, WarpSmem
       break;
     }
     phase ^= 1u;
-    const int nfar = convert_chunk(sm, n_cur, lane, clist, P.cand_cap, ccount, s_cur,
-                                   (uint32_t)kind_cur << 30);
+    const int nfar = convert_chunk<KMODE>(sm, n_cur, lane, clist, P.cand_cap, ccount, s_cur,
+                                          kind_cur);
     __syncwarp();
     const bool have_next = cursor_next<KMODE>(P, it, sm, cur, lane);
     int n_next = 0, kind_next = 0;
@@ -509,8 +569,9 @@ __device__ bool run_item(const EngineParams &P, const Item &it, int id, WarpSmem
       issue_chunk(sm, P.rec, cur.s, n_next, lane);
       cur.s += n_next;
     }
-    dispatch_compute<T, KMODE>(kind_cur, sm, P, ic, n_cur, nfar, x, ps);
-    // plain FP32 over two chunks (<= 128 sources), then into the (hi, lo) sums
+    dispatch_compute<T, KMODE>(kind_cur, sm, P, ic, n_cur, nfar, x2, ps);
+    // plain FP32 over two chunks (<= 64 sources per half), then into the
+    // (hi, lo) sums
     if (++npend == 2 || !have_next) {
       npend = 0;
 #pragma unroll
@@ -518,10 +579,10 @@ __device__ bool run_item(const EngineParams &P, const Item &it, int id, WarpSmem
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           float h = sm.acc[t * 3 + k][lane], l = sm.acc[(T + t) * 3 + k][lane];
-          two_sum_acc(h, l, ps[t][k]);
+          two_sum_acc(h, l, ps[t][k].x + ps[t][k].y);
           sm.acc[t * 3 + k][lane] = h;
           sm.acc[(T + t) * 3 + k][lane] = l;
-          ps[t][k] = 0.f;
+          ps[t][k] = make_float2(0.f, 0.f);
         }
     }
     __syncwarp();

@@ -31,9 +31,9 @@
 //    sources are laid out as pairs, field-interleaved (x of both, then y of
 //    both, ...), with the position negated so that d = x + (-y) is one packed
 //    add; that is the same IEEE operation as x - y, bit for bit.
-//  * Accumulation: plain FP32 over two chunks (<= 64 terms per lane and half),
-//    then the two halves are added and two-summed into per-target (hi, lo)
-//    kept in shared memory.
+//  * Accumulation: plain FP32 over eight chunks (<= 256 terms per lane and
+//    half), then the two halves are added and two-summed into per-target
+//    (hi, lo) kept in shared memory.
 //  * The kernel is instantiated per kernel kind (SL, DL, SL+DL, or SL/DL by
 //    segment parity for batched suspensions) so that a launch only runs the
 //    code of its own kind, which keeps the hot loops inside the instruction
@@ -570,9 +570,9 @@ __device__ bool run_item(const EngineParams &P, const Item &it, int id, WarpSmem
       cur.s += n_next;
     }
     dispatch_compute<T, KMODE>(kind_cur, sm, P, ic, n_cur, nfar, x2, ps);
-    // plain FP32 over two chunks (<= 64 sources per half), then into the
+    // plain FP32 over eight chunks (<= 256 sources per half), then into the
     // (hi, lo) sums
-    if (++npend == 2 || !have_next) {
+    if (++npend == 8 || !have_next) {
       npend = 0;
 #pragma unroll
       for (int t = 0; t < T; ++t)

@@ -557,8 +557,10 @@ def run_ours(args, rank, world, local_rank):
         mx = lambda u: float(np.abs(u - ref).max() / np.abs(ref).max())
         result["cpu_baseline"] = {"value": sp / dt / 1e9, "unit": UNIT, "cores": cpu_cores(),
                                   "kind": "oracle",
-                                  "sample": f"{tg.size} random targets with all their U-list "
-                                            f"sources ({sp} pairs), {dt:.1f} s"}
+                                  "sample": (f"all {tg.size} targets" if tg.size == wl.pts.shape[0]
+                                             else f"{tg.size} random targets of {wl.pts.shape[0]}")
+                                            + f" with all their U-list sources ({sp} pairs), "
+                                            f"{dt:.1f} s"}
         result["accuracy"] = {"vs": "FP64 CPU oracle on the cpu_baseline target sample",
                               "mixed_rel_l2": err(um), "mixed_max_rel": mx(um),
                               "fp64_rel_l2": err(u64), "fp64_max_rel": mx(u64)}

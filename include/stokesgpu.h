@@ -277,7 +277,11 @@ stk_status stokes_near_patch_search(const double *nodes, int32_t npatch, int32_t
                                     const double *trg, int64_t nt, double d_eps, int32_t *patch,
                                     double *uv, double *y, double *n, double *dist,
                                     void *workspace, size_t workspace_bytes, void *stream);
-stk_status stokes_near_search_workspace_size(int32_t npatch, int32_t q, size_t *bytes);
+/* Workspace of stokes_near_patch_search for npatch patches of order q and nt
+ * targets (0 <= nt <= 2^31 - 1): the patch boxes, the sorted (cell, patch)
+ * keys and a list of nt target indices. */
+stk_status stokes_near_search_workspace_size(int32_t npatch, int32_t q, int64_t nt,
+                                             size_t *bytes);
 
 /* ------------------------------------------------- no-allocation variant
  * The paper has no counterpart to this entry point; it serves callers that

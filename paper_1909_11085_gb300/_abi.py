@@ -103,7 +103,7 @@ def lib():
             L.stokes_bie_workspace_size.argtypes = [i32, i32, i32, i32, po, psz]
             L.stokes_near_patch_search.argtypes = [p, i32, i32, p, i64, d, p, p, p, p, p, p, sz,
                                                    p]
-            L.stokes_near_search_workspace_size.argtypes = [i32, i32, psz]
+            L.stokes_near_search_workspace_size.argtypes = [i32, i32, i64, psz]
             L.stokes_graph_destroy.argtypes = [p]
             L.stokes_launch_count.restype = ctypes.c_int64
             for name in EXPORTS:

@@ -19,6 +19,11 @@
 //     line search and projection onto [-1, 1]^2, started at the nearest node;
 //  e. the nearest patch (ties to the lower index) is kept if its distance is
 //     at most d_eps.
+// Few targets lie near the surface, and the FP64 Newton iteration runs on
+// GB300's FP64 pipe (1/64 of the FP32 rate), which charges a warp instruction
+// in full however few of its lanes are active.  So k_nz_mark first lists the
+// targets that lie in at least one grown box (and writes "none" for the
+// rest), and k_nz_search runs one listed target per thread.
 // All of it in FP64; the normal is (dP/du x dP/dv) / |dP/du x dP/dv|.
 #include <cfloat>
 #include <cmath>
@@ -47,9 +52,28 @@ struct NzGrid {
 
 __global__ void __launch_bounds__(kNzThreads) k_nz_boxes(const double *__restrict__ nodes,
                                                          int n1sq, double d_eps,
-                                                         double *__restrict__ boxes) {
+                                                         double *__restrict__ boxes,
+                                                         double *__restrict__ rp) {
   __shared__ double s[6][kNzThreads];
+  __shared__ double sr[kNzThreads];
   const int p = blockIdx.x;
+  // the largest distance between two corners of a node cell: every point of
+  // the patch lies within it of a node, up to the interpolant's small
+  // deviation from the bilinear cell
+  const int n1 = (int)lrint(sqrt((double)n1sq));
+  double cm = 0.0;
+  for (int e = threadIdx.x; e < (n1 - 1) * (n1 - 1); e += blockDim.x) {
+    const int i = e / (n1 - 1), j = e % (n1 - 1);
+    const double *c00 = nodes + ((size_t)p * n1sq + i * n1 + j) * 3;
+    const double *c01 = c00 + 3, *c10 = c00 + 3 * n1, *c11 = c10 + 3;
+    const double *cs[4] = {c00, c01, c10, c11};
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b) {
+        const double dx = cs[a][0] - cs[b][0], dy = cs[a][1] - cs[b][1], dz = cs[a][2] - cs[b][2];
+        cm = fmax(cm, dx * dx + dy * dy + dz * dz);
+      }
+  }
+  sr[threadIdx.x] = cm;
   double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
   for (int e = threadIdx.x; e < n1sq; e += blockDim.x)
 #pragma unroll
@@ -65,15 +89,18 @@ __global__ void __launch_bounds__(kNzThreads) k_nz_boxes(const double *__restric
   }
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o)
+    if (threadIdx.x < o) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         s[k][threadIdx.x] = fmin(s[k][threadIdx.x], s[k][threadIdx.x + o]);
         s[3 + k][threadIdx.x] = fmax(s[3 + k][threadIdx.x], s[3 + k][threadIdx.x + o]);
       }
+      sr[threadIdx.x] = fmax(sr[threadIdx.x], sr[threadIdx.x + o]);
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    rp[p] = 1.1 * sqrt(sr[0]);
     const double dx = s[3][0] - s[0][0], dy = s[4][0] - s[1][0], dz = s[5][0] - s[2][0];
     const double grow = d_eps + 0.05 * sqrt(dx * dx + dy * dy + dz * dz);
 #pragma unroll
@@ -177,17 +204,21 @@ __device__ void nz_basis(int n1, const double *xk, const double *wk, double t, d
     D[hit] = dd;
     return;
   }
+  // l_k = (w_k / (t - x_k)) / S and l_k' = l_k (sum_m w_m / (t - x_m)^2 / S - 1 / (t - x_k)),
+  // with D[] holding 1 / (t - x_k) until the end
   double S = 0.0, S2 = 0.0;
   for (int k = 0; k < n1; ++k) {
-    const double a = wk[k] / (t - xk[k]);
+    const double r = 1.0 / (t - xk[k]);
+    const double a = wk[k] * r;
     L[k] = a;
+    D[k] = r;
     S += a;
-    S2 += a / (t - xk[k]);
+    S2 += a * r;
   }
-  const double sig = S2 / S;
+  const double iS = 1.0 / S, sig = S2 * iS;
   for (int k = 0; k < n1; ++k) {
-    L[k] /= S;
-    D[k] = L[k] * (sig - 1.0 / (t - xk[k]));
+    L[k] *= iS;
+    D[k] = L[k] * (sig - D[k]);
   }
 }
 
@@ -218,10 +249,9 @@ __device__ void nz_eval(int n1, const double *__restrict__ X, const double *xk, 
   }
 }
 
-__device__ double nz_closest(int n1, const double *__restrict__ X, const double *xk,
-                             const double *wk, const double x[3], double &u, double &v,
-                             double y[3], double nn[3]) {
-  // start at the nearest node
+// The node of a patch nearest to x: squared distance and its (u, v).
+__device__ double nz_nearest_node(int n1, const double *__restrict__ X, const double *xk,
+                                  const double x[3], double &u, double &v) {
   double best = DBL_MAX;
   for (int e = 0; e < n1 * n1; ++e) {
     const double *xp = X + 3 * e;
@@ -233,6 +263,13 @@ __device__ double nz_closest(int n1, const double *__restrict__ X, const double 
       v = xk[e % n1];
     }
   }
+  return best;
+}
+
+// Closest point of a patch to x, from the start (u, v).
+__device__ double nz_closest(int n1, const double *__restrict__ X, const double *xk,
+                             const double *wk, const double x[3], double &u, double &v,
+                             double y[3], double nn[3]) {
   double P[3], Pu[3], Pv[3];
   nz_eval(n1, X, xk, wk, u, v, P, Pu, Pv);
   double f = 0.0;
@@ -249,9 +286,20 @@ __device__ double nz_closest(int n1, const double *__restrict__ X, const double 
       huv += Pu[c] * Pv[c];
       hvv += Pv[c] * Pv[c];
     }
+    // active set: a parameter on its bound whose gradient points out of the
+    // square stays there, and the step solves for the other one alone
+    const bool fu = (u <= -1.0 && gu > 0.0) || (u >= 1.0 && gu < 0.0);
+    const bool fv = (v <= -1.0 && gv > 0.0) || (v >= 1.0 && gv < 0.0);
+    if (fu && fv) break;  // a corner that is a constrained minimum
     const double det = huu * hvv - huv * huv;
     double su, sv;
-    if (det > 1e-300) {
+    if (fu) {
+      su = 0.0;
+      sv = hvv > 1e-300 ? -gv / hvv : -gv;
+    } else if (fv) {
+      su = huu > 1e-300 ? -gu / huu : -gu;
+      sv = 0.0;
+    } else if (det > 1e-300) {
       su = -(hvv * gu - huv * gv) / det;
       sv = -(huu * gv - huv * gu) / det;
     } else {
@@ -289,7 +337,9 @@ __device__ double nz_closest(int n1, const double *__restrict__ X, const double 
       Pu[c] = Pun[c];
       Pv[c] = Pvn[c];
     }
-    if (step < 1e-15) break;
+    // converged: the parameters are in [-1, 1] and a step below 1e-12 is at
+    // the level of the rounding in the gradient (coordinates of order 1e2)
+    if (step < 1e-12) break;
   }
   const double cx = Pu[1] * Pv[2] - Pu[2] * Pv[1], cy = Pu[2] * Pv[0] - Pu[0] * Pv[2],
                cz = Pu[0] * Pv[1] - Pu[1] * Pv[0];
@@ -302,11 +352,53 @@ __device__ double nz_closest(int n1, const double *__restrict__ X, const double 
   return sqrt(f);
 }
 
+// Lists the targets inside at least one grown patch box; the others get
+// "none" (patch -1, distance -1, zero parameters, point and normal).
+__global__ void __launch_bounds__(kNzThreads) k_nz_mark(
+    const double *__restrict__ boxes, const NzGrid *__restrict__ gp,
+    const uint64_t *__restrict__ keys, const int32_t *__restrict__ vals, int64_t nkeys,
+    const double *__restrict__ trg, int64_t nt, int32_t *__restrict__ list,
+    int32_t *__restrict__ nlist, int32_t *__restrict__ patch_out, double *__restrict__ uv_out,
+    double *__restrict__ y_out, double *__restrict__ n_out, double *__restrict__ dist_out) {
+  const NzGrid g = *gp;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double x[3] = {trg[3 * t], trg[3 * t + 1], trg[3 * t + 2]};
+    bool any = false;
+    int64_t c[3];
+    if (nz_cell(g, x, c)) {
+      const uint64_t key = (uint64_t)(c[0] + g.dims[0] * (c[1] + g.dims[1] * c[2]));
+      int64_t lo = 0, hi = nkeys;  // first entry with keys[i] >= key
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (keys[mid] < key) lo = mid + 1;
+        else hi = mid;
+      }
+      for (int64_t i = lo; i < nkeys && keys[i] == key && !any; ++i) {
+        const double *b = boxes + 6 * vals[i];
+        any = x[0] >= b[0] && x[1] >= b[1] && x[2] >= b[2] && x[0] <= b[3] && x[1] <= b[4] &&
+              x[2] <= b[5];
+      }
+    }
+    if (any) {
+      list[atomicAdd(nlist, 1)] = (int32_t)t;
+    } else {
+      patch_out[t] = -1;
+      uv_out[2 * t] = uv_out[2 * t + 1] = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) y_out[3 * t + k] = n_out[3 * t + k] = 0.0;
+      dist_out[t] = -1.0;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kNzThreads) k_nz_search(
     const double *__restrict__ nodes, int q, const double *__restrict__ boxes,
     const NzGrid *__restrict__ gp, const uint64_t *__restrict__ keys,
-    const int32_t *__restrict__ vals, int64_t nkeys, const double *__restrict__ trg, int64_t nt,
-    double d_eps, int32_t *__restrict__ patch_out, double *__restrict__ uv_out,
+    const int32_t *__restrict__ vals, int64_t nkeys, const double *__restrict__ trg,
+    const int32_t *__restrict__ list, const int32_t *__restrict__ nlist,
+    const double *__restrict__ rp, double d_eps, int32_t *__restrict__ patch_out,
+    double *__restrict__ uv_out,
     double *__restrict__ y_out, double *__restrict__ n_out, double *__restrict__ dist_out) {
   __shared__ double xk[kNzMaxN1], wk[kNzMaxN1];
   const int n1 = q + 1;
@@ -316,8 +408,10 @@ __global__ void __launch_bounds__(kNzThreads) k_nz_search(
   }
   __syncthreads();
   const NzGrid g = *gp;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t nl = *nlist;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nl;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = list[j];
     const double x[3] = {trg[3 * t], trg[3 * t + 1], trg[3 * t + 2]};
     int bp = -1;
     double bd = DBL_MAX, bu = 0.0, bv = 0.0, by[3] = {0.0, 0.0, 0.0}, bn[3] = {0.0, 0.0, 0.0};
@@ -336,8 +430,13 @@ __global__ void __launch_bounds__(kNzThreads) k_nz_search(
         if (x[0] < b[0] || x[1] < b[1] || x[2] < b[2] || x[0] > b[3] || x[1] > b[4] ||
             x[2] > b[5])
           continue;
+        const double *X = nodes + (size_t)p * n1 * n1 * 3;
         double u, v, y[3], nn[3];
-        const double d = nz_closest(n1, nodes + (size_t)p * n1 * n1 * 3, xk, wk, x, u, v, y, nn);
+        // every point of the patch lies within rp of a node: skip a patch that
+        // cannot come within d_eps or beat the best so far
+        const double lb = sqrt(nz_nearest_node(n1, X, xk, x, u, v)) - rp[p];
+        if (lb > d_eps || lb > bd) continue;
+        const double d = nz_closest(n1, X, xk, wk, x, u, v, y, nn);
         if (d < bd || (d == bd && p < bp)) {
           bd = d;
           bp = p;
@@ -365,10 +464,10 @@ __global__ void __launch_bounds__(kNzThreads) k_nz_search(
 }
 
 struct NzLayout {
-  size_t boxes, grid, ka, va, kb, vb, hist, hist_scan, total;
+  size_t boxes, rp, grid, ka, va, kb, vb, hist, hist_scan, list, nlist, total;
 };
 
-NzLayout nz_layout(int32_t npatch) {
+NzLayout nz_layout(int32_t npatch, int64_t nt) {
   NzLayout L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -378,6 +477,7 @@ NzLayout nz_layout(int32_t npatch) {
   };
   const size_t nk = (size_t)npatch * kNzCells;
   L.boxes = take(sizeof(double) * 6 * (size_t)npatch);
+  L.rp = take(sizeof(double) * (size_t)npatch);
   L.grid = take(sizeof(NzGrid));
   L.ka = take(sizeof(uint64_t) * nk);
   L.va = take(sizeof(int32_t) * nk);
@@ -386,6 +486,8 @@ NzLayout nz_layout(int32_t npatch) {
   const size_t he = radix_hist_entries((int64_t)nk);
   L.hist = take(sizeof(int32_t) * he);
   L.hist_scan = take(sizeof(int32_t) * (he + 1));
+  L.list = take(sizeof(int32_t) * (size_t)(nt > 0 ? nt : 1));
+  L.nlist = take(sizeof(int32_t));
   L.total = off + 256;
   return L;
 }
@@ -394,11 +496,13 @@ NzLayout nz_layout(int32_t npatch) {
 
 extern "C" {
 
-stk_status stokes_near_search_workspace_size(int32_t npatch, int32_t q, size_t *bytes) {
+stk_status stokes_near_search_workspace_size(int32_t npatch, int32_t q, int64_t nt,
+                                             size_t *bytes) {
   if (!bytes) return report_error(STK_EINVAL, "bytes is NULL");
   if (npatch < 0) return report_error(STK_EINVAL, "npatch must be >= 0");
+  if (nt < 0 || nt > 0x7fffffff) return report_error(STK_EINVAL, "nt must be in [0, 2^31 - 1]");
   if (q < 2 || q > kNzMaxN1 - 1) return report_error(STK_EUNSUPPORTED, "q must be in [2, 12]");
-  *bytes = nz_layout(npatch).total;
+  *bytes = nz_layout(npatch, nt).total;
   return STK_OK;
 }
 
@@ -407,9 +511,8 @@ stk_status stokes_near_patch_search(const double *nodes, int32_t npatch, int32_t
                                     double *uv, double *y, double *n, double *dist,
                                     void *workspace, size_t workspace_bytes, void *stream) {
   size_t need = 0;
-  stk_status s = stokes_near_search_workspace_size(npatch, q, &need);
+  stk_status s = stokes_near_search_workspace_size(npatch, q, nt, &need);
   if (s != STK_OK) return s;
-  if (nt < 0) return report_error(STK_EINVAL, "nt must be >= 0");
   if (!(d_eps >= 0.0) || !std::isfinite(d_eps))
     return report_error(STK_EINVAL, "d_eps must be finite and >= 0");
   if (nt == 0) return STK_OK;
@@ -424,7 +527,7 @@ stk_status stokes_near_patch_search(const double *nodes, int32_t npatch, int32_t
   }
   if (!nodes) return report_error(STK_EINVAL, "nodes is NULL");
   if (!workspace || workspace_bytes < need) return report_error(STK_ENOMEM, "workspace too small");
-  const NzLayout L = nz_layout(npatch);
+  const NzLayout L = nz_layout(npatch, nt);
   const uintptr_t u = reinterpret_cast<uintptr_t>(workspace);
   char *ws = reinterpret_cast<char *>((u + 255) & ~(uintptr_t)255);
   double *boxes = reinterpret_cast<double *>(ws + L.boxes);
@@ -432,7 +535,8 @@ stk_status stokes_near_patch_search(const double *nodes, int32_t npatch, int32_t
   uint64_t *ka = reinterpret_cast<uint64_t *>(ws + L.ka), *kb = reinterpret_cast<uint64_t *>(ws + L.kb);
   int32_t *va = reinterpret_cast<int32_t *>(ws + L.va), *vb = reinterpret_cast<int32_t *>(ws + L.vb);
   const int n1 = q + 1;
-  k_nz_boxes<<<npatch, kNzThreads, 0, st>>>(nodes, n1 * n1, d_eps, boxes);
+  double *rp = reinterpret_cast<double *>(ws + L.rp);
+  k_nz_boxes<<<npatch, kNzThreads, 0, st>>>(nodes, n1 * n1, d_eps, boxes, rp);
   k_nz_grid<<<1, kNzThreads, 0, st>>>(boxes, npatch, grid);
   const int64_t nk = (int64_t)npatch * kNzCells;
   k_nz_cells<<<(int)((nk + 255) / 256), 256, 0, st>>>(boxes, npatch, grid, ka, va);
@@ -441,11 +545,17 @@ stk_status stokes_near_patch_search(const double *nodes, int32_t npatch, int32_t
                                reinterpret_cast<int32_t *>(ws + L.hist_scan), st);
   const uint64_t *keys = which ? kb : ka;
   const int32_t *vals = which ? vb : va;
+  int32_t *list = reinterpret_cast<int32_t *>(ws + L.list);
+  int32_t *nlist = reinterpret_cast<int32_t *>(ws + L.nlist);
+  if (cudaMemsetAsync(nlist, 0, sizeof(int32_t), st) != cudaSuccess)
+    return report_error(STK_ECUDA, "cudaMemsetAsync failed");
   int64_t blocks = (nt + kNzThreads - 1) / kNzThreads;
   if (blocks > 65535) blocks = 65535;
-  k_nz_search<<<(int)blocks, kNzThreads, 0, st>>>(nodes, q, boxes, grid, keys, vals, nk, trg, nt,
-                                                  d_eps, patch, uv, y, n, dist);
-  count_launches(1);
+  k_nz_mark<<<(int)blocks, kNzThreads, 0, st>>>(boxes, grid, keys, vals, nk, trg, nt, list, nlist,
+                                                patch, uv, y, n, dist);
+  k_nz_search<<<(int)blocks, kNzThreads, 0, st>>>(nodes, q, boxes, grid, keys, vals, nk, trg, list,
+                                                  nlist, rp, d_eps, patch, uv, y, n, dist);
+  count_launches(2);
   if (cudaGetLastError() != cudaSuccess) return report_error(STK_ECUDA, "near-zone search launch failed");
   return STK_OK;
 }

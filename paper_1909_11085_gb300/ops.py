@@ -477,7 +477,7 @@ def near_patch_search(nodes, npatch, trg, d_eps, q=10):
     n = torch.empty((nt, 3), dtype=torch.float64, device=dev)
     dist = torch.empty(nt, dtype=torch.float64, device=dev)
     nb = ctypes.c_size_t(0)
-    A.check(A.lib().stokes_near_search_workspace_size(int(npatch), int(q), ctypes.byref(nb)))
+    A.check(A.lib().stokes_near_search_workspace_size(int(npatch), int(q), nt, ctypes.byref(nb)))
     ws = A.workspace(nb.value, dev)
     with torch.cuda.device(dev):
         A.check(A.lib().stokes_near_patch_search(

@@ -81,3 +81,30 @@ def test_vessel_wall_radial_projection_and_edges(lib):
     assert lib.near_patch_search(N, c.npatch, e, 2.0, Q)[0].numel() == 0
     p0 = lib.near_patch_search(N[:0], 0, X[:5], 2.0, Q)[0].cpu().numpy()
     assert (p0 == -1).all()
+
+
+def test_targets_on_nodes_and_edges(lib):
+    """A target on a node is its own closest point at distance 0, also for
+    d_eps = 0; on a node shared by neighbouring patches the lower patch index
+    wins (Sec. 3.2 step e, ties to the lower index); targets outside the grid
+    of patch boxes get none."""
+    Rw, Lw, nth, nz = 6.0, 8.0, 6, 2
+    cp, cn, cw, ch = G.cylinder_wall_patches(Rw, Lw, nth, nz, Q)
+    npatch = nth * nz
+    n1 = Q + 1
+    nodes = cp.reshape(npatch, n1 * n1, 3)
+    rng = np.random.default_rng(12)
+    pick = rng.choice(npatch * n1 * n1, 40, replace=False)
+    x = cp[pick]
+    far = np.array([[100.0, 0.0, 0.0], [0.0, 0.0, -50.0], [0.0, 0.0, 4.0]])  # the last: the axis
+    N, X = cuda(cp, np.concatenate([x, far]))
+    for d_eps in (0.0, 0.5):
+        p, uv, y, n, d = (t.cpu().numpy() for t in lib.near_patch_search(N, npatch, X, d_eps, Q))
+        np.testing.assert_array_equal(d[:40], 0.0)
+        np.testing.assert_array_equal(y[:40], x)
+        # lowest patch that holds the point as a node
+        for i, j in enumerate(pick):
+            owners = [q for q in range(npatch) if np.any(np.all(nodes[q] == cp[j], axis=1))]
+            assert p[i] == min(owners), (i, p[i], owners)
+        assert (p[40:] == -1).all() and (d[40:] == -1.0).all()
+        np.testing.assert_allclose(np.linalg.norm(n[:40], axis=1), 1.0, atol=1e-12)

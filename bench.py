@@ -535,12 +535,71 @@ def run_ours(args, rank, world, local_rank):
         if i >= 2:
             e2e.append((a, b))
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e) / len(e2e)
+    serial_ms = sum(a.elapsed_time(b) for a, b in e2e) / len(e2e)
+
+    # the same steps as a stream of inputs: the host -> device copies of step
+    # i + 1 run on a copy stream while step i computes (two plans and two sets
+    # of device buffers, taken in turn); every step still copies its own
+    # inputs in and its result out, and the time is steps / total time
+    plans = [plan, P.P2PPlan(n, t.leaf_ptr, t.ulist_ptr, t.ulist_idx, 3, "mixed", NEAR_RATIO, dev)]
+    dbufs = [dbuf, {k: torch.empty_like(v, device=dev) for k, v in host.items()}]
+    outs = [out, torch.empty_like(out)]
+    out_hosts = [out_host, torch.empty_like(out_host).pin_memory()]
+    plans[1](dbufs[0]["pts"], dbufs[0]["f"], dbufs[0]["phi"], dbufs[0]["nrm"], dbufs[0]["w"],
+             dbufs[0]["h"], wl.mu, outs[1])  # first call of the second plan, untimed
+    cstream = torch.cuda.Stream(dev)
+    done = [None, None]
+
+    def copy_in(sidx):
+        with torch.cuda.stream(cstream):
+            if done[sidx] is not None:
+                cstream.wait_event(done[sidx])  # the buffers' previous step has finished
+            for k, v in host.items():
+                dbufs[sidx][k].copy_(v, non_blocking=True)
+            plans[sidx].leaf_ptr.copy_(host_lists["leaf_ptr"], non_blocking=True)
+            plans[sidx].ulist_ptr.copy_(host_lists["ulist_ptr"], non_blocking=True)
+            plans[sidx].ulist_idx.copy_(host_lists["ulist_idx"], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(cstream)
+        return ev
+
+    Kp = max(4, min(K, 40))
+    dstream = torch.cuda.Stream(dev)  # device -> host reads of the results
+    read = [None, None]
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    cstream.wait_event(p0)
+    copied = copy_in(0)
+    for i in range(Kp):
+        sidx = i % 2
+        stream.wait_event(copied)
+        if read[sidx] is not None:
+            stream.wait_event(read[sidx])  # the result buffer's previous read is done
+        copied = copy_in(1 - sidx) if i + 1 < Kp else None
+        b_ = dbufs[sidx]
+        plans[sidx](b_["pts"], b_["f"], b_["phi"], b_["nrm"], b_["w"], b_["h"], wl.mu, outs[sidx])
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        done[sidx] = ev
+        with torch.cuda.stream(dstream):
+            dstream.wait_event(ev)
+            out_hosts[sidx].copy_(outs[sidx], non_blocking=True)
+            rv = torch.cuda.Event()
+            rv.record(dstream)
+            read[sidx] = rv
+    stream.wait_event(read[(Kp - 1) % 2])
+    p1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = p0.elapsed_time(p1) / Kp
+    # both buffer sets computed the same inputs: a copy that raced its step
+    # would show as different bits
+    same_bits = bool(torch.equal(out_hosts[0], out_hosts[1]))
     e2e_s = e2e_ms / 1e3
     if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        tt = torch.tensor([e2e_s, serial_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+        e2e_s, serial_ms = float(tt[0].item()), float(tt[1].item())
     e2e_val = pairs * world / e2e_s / 1e9
 
     # roofline of the dominant kernel (FP32 ALU bound)
@@ -569,7 +628,12 @@ def run_ours(args, rank, world, local_rank):
                            "frac_at_sampled_clock": at_clock},
               "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": K64},
               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                      "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3},
+                      "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
+                      "steps": Kp, "serial_ms_per_step": serial_ms,
+                      "results_identical_across_buffers": same_bits,
+                      "overlap": "host->device copies of step i+1 and the device->host read "
+                                 "of step i-1 on their own streams during step i; the serial "
+                                 "figure copies, computes and reads back one step at a time"},
               "gpu_launches": int(launches), "gpu_launches_per_step": launches / K,
               "clocks": clocks, "wall_s_timed_region": wall}
     if world == 1 and not args.no_forms:

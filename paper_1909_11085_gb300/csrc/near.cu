@@ -32,7 +32,7 @@ namespace stk {
 namespace {
 
 constexpr int kNearWarps = 4;
-constexpr int kNearMinBlocks = 5;
+constexpr int kNearMinBlocks = 8;
 constexpr int kNearT = kItemMax / kWarp;  // targets per lane
 constexpr int kNearQueue = 256;           // >= 128 free slots before each candidate
 constexpr int kNearSegWin = 64;           // segments per window

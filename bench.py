@@ -46,6 +46,10 @@ FLOPS_PER_PAIR = {"SL": 28, "DL": 29, "SLDL": 57}
 # d.n 5, (d.psi)(d.n) 1, combine 2 + 1, two 3-vector FMAs 12).
 EXEC_FLOPS_PER_PAIR = {"SL": 27, "DL": 29, "SLDL": 40}
 FLOPS_PER_PAIR_SLDL = FLOPS_PER_PAIR["SLDL"]
+# The adjoint's pair terms as stated (and written) for both kernels, counted the
+# same way: shared d 3, |r|^2 5, r^-2, r^-3, r^-5 3, d.g 5; source-major pass
+# + single layer 48 + double layer 55 + 3 = 122; target-major pass + 35 + 43 + 3 = 97.
+ADJ_FLOPS_PER_PAIR = {"src": 122, "trg": 97}
 FP32_LANES_PER_SM = 128
 # near-pair threshold: |r| < NEAR_RATIO * h_j takes the FP64 difference and 1/r
 NEAR_RATIO = 1.0
@@ -383,9 +387,14 @@ def run_forms(dev, flush, stream, peak_tflops):
     ms = _time_ms(fwd_bwd, stream, flush, 5)
     # forward pass + source-major and target-major adjoint passes
     pairs5 = n5 * (n5 - 1)
+    fl5 = FLOPS_PER_PAIR["SLDL"] + ADJ_FLOPS_PER_PAIR["src"] + ADJ_FLOPS_PER_PAIR["trg"]
+    fx5 = EXEC_FLOPS_PER_PAIR["SLDL"] + ADJ_FLOPS_PER_PAIR["src"] + ADJ_FLOPS_PER_PAIR["trg"]
     forms["adjoint_sldl_64rbc_34816pts"] = {
         "pairs_per_pass": pairs5, "passes": 3,
-        "mixed": {"ms_forward_backward": ms, "Gpair/s": 3 * pairs5 / ms / 1e6},
+        "flops_per_pair": {"forward": FLOPS_PER_PAIR["SLDL"], **ADJ_FLOPS_PER_PAIR},
+        "mixed": {"ms_forward_backward": ms, "Gpair/s": 3 * pairs5 / ms / 1e6,
+                  "pct_fp32_peak": 100.0 * pairs5 * fl5 / (ms / 1e3) / 1e12 / peak_tflops,
+                  "pct_fp32_peak_executed": 100.0 * pairs5 * fx5 / (ms / 1e3) / 1e12 / peak_tflops},
         "accuracy": "checked in the GPU test suite (oracle gradient and finite differences)"}
     log(f"[forms] adjoint: {forms['adjoint_sldl_64rbc_34816pts']}")
     return forms

@@ -19,8 +19,13 @@
 // over blockIdx.y for occupancy.  The mixed form works in FP32 in the CTA's
 // local frame (positions split hi/lo as in the forward records) with a
 // two-sum per tile; a pair with |r| < alpha h_j is left out of the FP32 sum
-// and evaluated in FP64 (difference and 1/|r| and the pair terms).  The FP64
-// form does all of it in double.
+// and listed for its output point (up to kAdjNearCap); k_adj_near then
+// evaluates the listed pairs in FP64 (difference, 1/|r| and the pair terms) in
+// input order and adds them to the point's partial.  Keeping FP64 out of the
+// FP32 pass keeps its registers, and so its occupancy, those of FP32 code.
+// An output point with more near pairs than the list holds is rescanned by
+// k_adj_near with the FP32 pass's own frame and test.  The FP64 form does all
+// of it in double.
 #include <cfloat>
 
 #include "common.cuh"
@@ -139,6 +144,12 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_mixed(AdjParams A) {
   const float oy = to_local(Ro.yh.y, Ro.n.w, oh[1], ol[1]);
   const float oz = to_local(Ro.yh.z, Ro.p.w, oh[2], ol[2]);
   const float own_hh = Ro.yh.w;
+  if (valid && blockIdx.y == 0) {  // the frame, for a rescan of an overflowing list
+    float *fr = A.oframe + 9 * (size_t)oc;
+    fr[0] = ox; fr[1] = oy; fr[2] = oz;
+    fr[3] = oh[0]; fr[4] = oh[1]; fr[5] = oh[2];
+    fr[6] = ol[0]; fr[7] = ol[1]; fr[8] = ol[2];
+  }
   const float ov1[3] = {Ro.q.x, Ro.q.y, Ro.q.z};  // g (trg-major) or q (src-major)
   const float on[3] = {Ro.n.x, Ro.n.y, Ro.n.z};
   const float op[3] = {Ro.p.x, Ro.p.y, Ro.p.z};
@@ -188,23 +199,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_mixed(AdjParams A) {
           nn[0] = N.x; nn[1] = N.y; nn[2] = N.z;
         }
         adj_pair<float, SRC>(dx, dy, dz, ri, g, q, pp, nn, A.has_sl, A.has_dl, ps);
-        if (near) {
-          // FP64 difference, 1/|r| and pair terms; zero distance contributes nothing
-          const double *xa = SRC ? A.in64 + 3 * (size_t)sI[kk] : A.out64 + 3 * (size_t)oc;
-          const double *ya = SRC ? A.out64 + 3 * (size_t)oc : A.in64 + 3 * (size_t)sI[kk];
-          const double ddx = xa[0] - ya[0], ddy = xa[1] - ya[1], ddz = xa[2] - ya[2];
-          const double rr = ddx * ddx + ddy * ddy + ddz * ddz;
-          if (rr > 0.0) {
-            const double rid = 1.0 / sqrt(rr);
-            double gd[3] = {g[0], g[1], g[2]}, qd[3] = {q[0], q[1], q[2]},
-                   pd[3] = {pp[0], pp[1], pp[2]}, nd[3] = {nn[0], nn[1], nn[2]};
-            double ad[NA];
-#pragma unroll
-            for (int a = 0; a < NA; ++a) ad[a] = 0.0;
-            adj_pair<double, SRC>(ddx, ddy, ddz, rid, gd, qd, pd, nd, A.has_sl, A.has_dl, ad);
-#pragma unroll
-            for (int a = 0; a < NA; ++a) ps[a] += (float)ad[a];
-          }
+        if (near) {  // listed for the FP64 pass
+          const int slot = atomicAdd(A.near_cnt + oc, 1);
+          if (slot < A.near_cap) A.near_idx[(size_t)oc * A.near_cap + slot] = sI[kk];
         }
       }
 #pragma unroll
@@ -219,6 +216,78 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_mixed(AdjParams A) {
     double *out = A.partial + ((size_t)blockIdx.y * (size_t)A.nout + (size_t)oc) * NA;
 #pragma unroll
     for (int a = 0; a < NA; ++a) out[a] = (double)hi[a] + (double)lo[a];
+  }
+}
+
+// ---------------------------------------------------------------- near pairs
+// FP64 pair terms of output point oc with input ic (zero distance: nothing).
+template <bool SRC>
+__device__ __forceinline__ void adj_near_pair(const AdjParams &A, int64_t oc, int32_t ic,
+                                              double (&ad)[NAcc<SRC>::value]) {
+  const SrcRec *orec = reinterpret_cast<const SrcRec *>(A.out_rec);
+  const SrcRec *irec = reinterpret_cast<const SrcRec *>(A.in_rec);
+  const double *xa = SRC ? A.in64 + 3 * (size_t)ic : A.out64 + 3 * (size_t)oc;
+  const double *ya = SRC ? A.out64 + 3 * (size_t)oc : A.in64 + 3 * (size_t)ic;
+  const double ddx = xa[0] - ya[0], ddy = xa[1] - ya[1], ddz = xa[2] - ya[2];
+  const double rr = ddx * ddx + ddy * ddy + ddz * ddz;
+  if (!(rr > 0.0)) return;
+  const SrcRec Ro = orec[oc], Ri = irec[ic];
+  const double rid = 1.0 / sqrt(rr);
+  // own values: g (target-major) or q, psi, n (source-major); the input's the others
+  const SrcRec &S = SRC ? Ro : Ri, &Tg = SRC ? Ri : Ro;
+  const double g[3] = {Tg.q.x, Tg.q.y, Tg.q.z}, q[3] = {S.q.x, S.q.y, S.q.z},
+               p[3] = {S.p.x, S.p.y, S.p.z}, n[3] = {S.n.x, S.n.y, S.n.z};
+  adj_pair<double, SRC>(ddx, ddy, ddz, rid, g, q, p, n, A.has_sl, A.has_dl, ad);
+}
+
+// One thread per output point: its listed near pairs, sorted by input index,
+// in FP64, added to the point's first partial.  A point whose list overflowed
+// is rescanned over all inputs (in index order) with the FP32 pass's frame
+// and test, so the same pairs are found.
+template <bool SRC>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_near(AdjParams A) {
+  constexpr int NA = NAcc<SRC>::value;
+  for (int64_t oc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; oc < A.nout;
+       oc += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = A.near_cnt[oc];
+    if (c == 0) continue;
+    double ad[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) ad[a] = 0.0;
+    if (c <= A.near_cap) {
+      int32_t idx[kAdjNearCap];
+      for (int k = 0; k < c; ++k) {  // insertion sort
+        const int32_t v = A.near_idx[(size_t)oc * A.near_cap + k];
+        int m = k;
+        while (m > 0 && idx[m - 1] > v) {
+          idx[m] = idx[m - 1];
+          --m;
+        }
+        idx[m] = v;
+      }
+      for (int k = 0; k < c; ++k) adj_near_pair<SRC>(A, oc, idx[k], ad);
+    } else {
+      const SrcRec *orec = reinterpret_cast<const SrcRec *>(A.out_rec);
+      const SrcRec *irec = reinterpret_cast<const SrcRec *>(A.in_rec);
+      const float *fr = A.oframe + 9 * (size_t)oc;
+      const float ox = fr[0], oy = fr[1], oz = fr[2];
+      const float oh[3] = {fr[3], fr[4], fr[5]}, ol[3] = {fr[6], fr[7], fr[8]};
+      const float own_hh = orec[oc].yh.w;
+      for (int64_t ic = 0; ic < A.nin; ++ic) {
+        const SrcRec R = irec[ic];
+        const float px = to_local(R.yh.x, R.q.w, oh[0], ol[0]);
+        const float py = to_local(R.yh.y, R.n.w, oh[1], ol[1]);
+        const float pz = to_local(R.yh.z, R.p.w, oh[2], ol[2]);
+        const float dx = SRC ? px - ox : ox - px, dy = SRC ? py - oy : oy - py,
+                    dz = SRC ? pz - oz : oz - pz;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float hh = SRC ? own_hh : R.yh.w;
+        if (r2 < hh) adj_near_pair<SRC>(A, oc, (int32_t)ic, ad);
+      }
+    }
+    double *out = A.partial + (size_t)oc * NA;  // the first input split
+#pragma unroll
+    for (int a = 0; a < NA; ++a) out[a] += ad[a];
   }
 }
 
@@ -321,10 +390,17 @@ __global__ void k_adj_finish_trg(int64_t nt, int32_t nsplit, const double *__res
 cudaError_t launch_adjoint(bool mixed, bool src_major, const AdjParams &A, cudaStream_t st) {
   dim3 grid((unsigned)((A.nout + kAdjThreads - 1) / kAdjThreads), (unsigned)A.nsplit);
   if (mixed) {
-    if (src_major)
+    cudaMemsetAsync(A.near_cnt, 0, sizeof(int32_t) * (size_t)A.nout, st);
+    int64_t gn = (A.nout + kAdjThreads - 1) / kAdjThreads;
+    if (gn > 65535) gn = 65535;
+    if (src_major) {
       k_adj_mixed<true><<<grid, kAdjThreads, 0, st>>>(A);
-    else
+      k_adj_near<true><<<(int)gn, kAdjThreads, 0, st>>>(A);
+    } else {
       k_adj_mixed<false><<<grid, kAdjThreads, 0, st>>>(A);
+      k_adj_near<false><<<(int)gn, kAdjThreads, 0, st>>>(A);
+    }
+    count_launches(1);
   } else {
     if (src_major)
       k_adj_fp64<true><<<grid, kAdjThreads, 0, st>>>(A);

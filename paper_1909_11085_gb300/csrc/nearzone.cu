@@ -141,12 +141,21 @@ __global__ void __launch_bounds__(kNzThreads) k_nz_grid(const double *__restrict
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double H = s[6][0] > 0.0 ? s[6][0] * (1.0 + 1e-9) : 1.0;
+    double H = s[6][0] > 0.0 ? s[6][0] * (1.0 + 1e-9) : 1.0;
+    // cell keys c0 + d0 (c1 + d1 c2) must fit 64 bits: a coarser grid only
+    // puts more boxes in a cell
+    double d[3];
+    while (true) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) d[k] = floor((s[3 + k][0] - s[k][0]) / H) + 1.0;
+      if (d[0] * d[1] * d[2] <= 4.0e18) break;
+      H *= 2.0;
+    }
     g->H = H;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       g->org[k] = s[k][0];
-      g->dims[k] = (int64_t)floor((s[3 + k][0] - s[k][0]) / H) + 1;
+      g->dims[k] = (int64_t)d[k];
     }
   }
 }

@@ -56,8 +56,15 @@ struct AdjParams {
   const double *out64;     // caller FP64 positions of the output points
   const double *in64;      // caller FP64 positions of the input points
   double *partial;         // [nsplit][nout][12 or 3], caller order
+  // mixed form: near pairs per output point (caller order), filled by the FP32
+  // pass and evaluated in FP64 by k_adj_near
+  int32_t *near_cnt;       // [nout], zeroed before the FP32 pass
+  int32_t *near_idx;       // [nout][near_cap] input caller indices
+  int32_t near_cap;
+  float *oframe;           // [nout][9]: local coordinates and the CTA frame origin (hi, lo)
 };
 cudaError_t launch_adjoint(bool mixed, bool src_major, const AdjParams &A, cudaStream_t st);
+constexpr int32_t kAdjNearCap = 32;  // near pairs listed per output point
 void launch_adj_finish(bool src_major, int64_t n, int32_t nsplit, const double *part,
                        const double *w, double csl, double cdl, double *grad_f, double *grad_phi,
                        double *grad_n, double *grad_y, double *grad_x, cudaStream_t st);

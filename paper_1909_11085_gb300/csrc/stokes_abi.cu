@@ -382,7 +382,7 @@ struct GradPlan {
   int64_t ns, nt;
   int32_t nsplit_src, nsplit_trg;
   size_t srec, trec, ska, skb, sva, svb, tka, tkb, tva, tvb, hist, hist_scan, bbox_part, bbox,
-      part_src, part_trg, counters, total;
+      part_src, part_trg, counters, near_cnt = 0, near_idx = 0, oframe = 0, total;
 };
 
 int32_t adj_splits(int64_t nout, int64_t nin, const DevInfo &di) {
@@ -423,6 +423,12 @@ stk_status plan_grad(int64_t ns, int64_t nt, const stk_opts *o, GradPlan &p) {
   p.bbox = a.take(sizeof(double) * 6);
   p.part_src = a.take(sizeof(double) * 12 * (size_t)ns * (size_t)p.nsplit_src);
   p.part_trg = a.take(sizeof(double) * 3 * (size_t)nt * (size_t)p.nsplit_trg);
+  if (p.mixed) {  // near-pair lists of one pass at a time (the larger point set)
+    const size_t nmax = (size_t)(ns > nt ? ns : nt);
+    p.near_cnt = a.take(sizeof(int32_t) * nmax);
+    p.near_idx = a.take(sizeof(int32_t) * nmax * (size_t)kAdjNearCap);
+    p.oframe = a.take(sizeof(float) * 9 * nmax);
+  }
   p.total = a.off + 256;
   return STK_OK;
 }
@@ -710,6 +716,10 @@ stk_status stokes_sldl_grad(const double *src, const double *f, const double *nr
                                      p.bbox_part, p.bbox, st);
   CU(cudaGetLastError());
   AdjParams A;
+  A.near_cnt = p.mixed ? at<int32_t>(ws, p.near_cnt) : nullptr;
+  A.near_idx = p.mixed ? at<int32_t>(ws, p.near_idx) : nullptr;
+  A.near_cap = kAdjNearCap;
+  A.oframe = p.mixed ? at<float>(ws, p.oframe) : nullptr;
   A.has_sl = f ? 1 : 0;
   A.has_dl = phi ? 1 : 0;
   if (want_src) {

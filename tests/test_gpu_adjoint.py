@@ -121,3 +121,30 @@ def test_full_size_sampled(lib):
         for k in ("f", "phi", "y", "n"):
             assert rel_l2(out[k].cpu().numpy()[js], ref_src[KEYS[k]]) <= tol, (prec, k)
         assert rel_l2(out["x"].cpu().numpy()[js], ref_trg["grad_x"]) <= tol, (prec, "x")
+
+
+def test_dense_cluster_overflows_the_near_lists(lib):
+    """Every pair near (spacing h larger than the cluster): each point has more near
+    inputs than the per-point list holds, so the mixed form's FP64 pass rescans
+    them with the FP32 pass's frame; a second cluster far away keeps far pairs in
+    the same call.  Compared with the oracle's analytic gradient at 1e-7: the far
+    pairs between the clusters carry FP32 rounding (2e-8 here), while a near pair
+    missed or counted twice would move a point's gradient by about 1e-2."""
+    rng = np.random.default_rng(95)
+    m = 96
+    a = rng.uniform(-0.5, 0.5, (m, 3))
+    b = rng.uniform(-0.5, 0.5, (m, 3)) + np.array([20.0, 0.0, 0.0])
+    pts = np.concatenate([a, b])
+    n = pts.shape[0]
+    nrm = rng.normal(size=(n, 3))
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    f, phi, g = (rng.uniform(-1, 1, (n, 3)) for _ in range(3))
+    w = rng.uniform(0.01, 0.02, n)
+    h = np.full(n, 3.0)  # alpha h = 3 > cluster diameter: all pairs inside a cluster are near
+    trg = pts + 0.01 * rng.normal(size=(n, 3))
+    ref = oracle.sldl_grad(pts, f, nrm, phi, w, trg, g, 1.0)
+    Y, F, N, PH, Wt, H, X, G = cuda(pts, f, nrm, phi, w, h, trg, g)
+    out = lib.sldl_grad(Y, F, N, PH, Wt, X, G, 1.0, h=H, precision="mixed")
+    for k, rk in KEYS.items():
+        got = out[k].cpu().numpy()
+        assert rel_l2(got, ref[rk]) <= 1e-7, (k, rel_l2(got, ref[rk]))

@@ -117,7 +117,7 @@ int auto_splits(int64_t nt, int64_t ns, const DevInfo &di, int occ) {
   if (chunks <= 0) return 1;
   const int64_t warps = (int64_t)di.sms * occ * kWarpsPerCta;
   int64_t s = (2 * warps + chunks - 1) / chunks;
-  const int64_t cap = ns / 512 > 1 ? ns / 512 : 1;
+  const int64_t cap = ns / 64 > 1 ? ns / 64 : 1;  // at least 64 sources per split
   if (s > cap) s = cap;
   if (s > 64) s = 64;
   if (s < 1) s = 1;

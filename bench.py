@@ -161,6 +161,16 @@ def sample_pairs(wl, targets) -> int:
     return int(nsrc[leaf].sum())
 
 
+def batched_pair_split(susp_ptr, n_cell):
+    """(single-layer pairs, double-layer pairs) of a batch: every point of a
+    suspension is a target of its cells' single layer and of its wall's double
+    layer, the point itself excluded."""
+    npt = np.diff(np.asarray(susp_ptr)).astype(np.int64)
+    ncl = np.asarray(n_cell, dtype=np.int64)
+    nwl = npt - ncl
+    return int((npt * ncl - ncl).sum()), int((npt * nwl - nwl).sum())
+
+
 def cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -292,12 +302,7 @@ def run_forms(dev, flush, stream, peak_tflops):
     sp = np.concatenate([[0], np.cumsum(np.diff(c3.susp_ptr)[sus])])
     refb = oracle.batched(c3.pts[rows], c3.f[rows], c3.phi[rows], c3.nrm[rows], c3.w[rows],
                           sp, c3.n_cell[sus], c3.mu)
-    # every point of a suspension is a target of its cells' single layer and of its
-    # wall's double layer (the point itself excluded)
-    npt = np.diff(c3.susp_ptr).astype(np.int64)
-    ncl = np.asarray(c3.n_cell, dtype=np.int64)
-    sl3 = int((npt * ncl - ncl).sum())
-    dl3 = int(pairs3 - sl3)
+    sl3, dl3 = batched_pair_split(c3.susp_ptr, c3.n_cell)
     fl3 = (sl3 * FLOPS_PER_PAIR["SL"] + dl3 * FLOPS_PER_PAIR["DL"]) / (ms / 1e3) / 1e12
     fx3 = (sl3 * EXEC_FLOPS_PER_PAIR["SL"] + dl3 * EXEC_FLOPS_PER_PAIR["DL"]) / (ms / 1e3) / 1e12
     forms["batched_2048_suspensions_graph"] = {

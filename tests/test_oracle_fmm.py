@@ -1,0 +1,70 @@
+"""Pins of the kernel-independent FMM oracle (the far field of Sec. 3.1, "Far
+evaluation") against what the mathematics fixes: with no far field (a tree of
+depth 1) it is the direct sum; a leaf's upward equivalent density reproduces the
+leaf's field away from it; the error against the direct sum falls with the
+surface order; and the double layer's far field needs the point-source part of
+the equivalent density (Stokeslets carry no flux)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import fmm as F
+
+
+@pytest.fixture(scope="module")
+def cloud():
+    oracle.build()
+    rng = np.random.default_rng(5)
+    n = 800
+    pts = rng.uniform(0, 1, (n, 3))
+    f, phi = rng.uniform(-1, 1, (n, 3)), rng.uniform(-1, 1, (n, 3))
+    nrm = rng.normal(size=(n, 3))
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    w = rng.uniform(0.5, 1.5, n) / n
+    return pts, f, phi, nrm, w
+
+
+def _rel(u, r):
+    return np.linalg.norm(u - r) / np.linalg.norm(r)
+
+
+def test_without_far_field_it_is_the_direct_sum(cloud):
+    pts, f, phi, nrm, w = cloud
+    ref = oracle.sldl(pts, f, nrm, phi, w, pts, 0.8)
+    u = F.fmm(pts, f, phi, nrm, w, depth=1, p=4, mu=0.8)
+    assert _rel(u, ref) <= 1e-13
+
+
+def test_leaf_equivalent_density_reproduces_its_far_field(cloud):
+    pts, f, phi, nrm, w = cloud
+    sel = np.all(pts < 0.25, axis=1)  # one box of half-width 0.125 about (0.125,)*3
+    c, r = np.full(3, 0.125), 0.125
+    rng = np.random.default_rng(6)
+    d = rng.normal(size=(50, 3))
+    # at 2 to 6 box widths from the centre, as interaction-list boxes are
+    far = c + 4 * r * (d / np.linalg.norm(d, axis=1)[:, None]) * rng.uniform(1.0, 3.0, (50, 1))
+    ref = oracle.sldl(pts[sel], f[sel], nrm[sel], phi[sel], w[sel], far, 1.0)
+    err = {}
+    for p in (4, 6):
+        S = F.cube_surface(p)
+        chk = oracle.sldl(pts[sel], f[sel], nrm[sel], phi[sel], w[sel], c + F.R_OUTER * r * S, 1.0)
+        e = F.pinv(F.upward_matrix(F.R_OUTER * r * S, F.R_INNER * r * S, 1.0, True)) @ chk.reshape(-1)
+        got = (F.upward_matrix(far, c + F.R_INNER * r * S, 1.0, True) @ e).reshape(-1, 3)
+        err[p] = _rel(got, ref)
+    assert err[6] <= 1e-3 and err[6] <= err[4] / 5, err
+
+
+def test_error_falls_with_surface_order(cloud):
+    pts, f, phi, nrm, w = cloud
+    ref = oracle.sldl(pts, f, nrm, phi, w, pts, 1.0)
+    e4 = _rel(F.fmm(pts, f, phi, nrm, w, depth=3, p=4), ref)
+    e6 = _rel(F.fmm(pts, f, phi, nrm, w, depth=3, p=6), ref)
+    assert e4 <= 1e-2 and e6 <= 5e-4 and e6 <= e4 / 10, (e4, e6)
+
+
+def test_double_layer_far_field_needs_the_source_term(cloud):
+    pts, f, phi, nrm, w = cloud
+    ref = oracle.sldl(pts, np.zeros_like(f), nrm, phi, w, pts, 1.0)
+    with_flux = _rel(F.fmm(pts, None, phi, nrm, w, depth=3, p=4, flux=True), ref)
+    stokeslets = _rel(F.fmm(pts, None, phi, nrm, w, depth=3, p=4, flux=False), ref)
+    assert with_flux <= 1e-2 and stokeslets >= 10 * with_flux, (with_flux, stokeslets)

@@ -219,3 +219,153 @@ def _parent_at(b: int, level_b: int, level: int) -> int:
     i, j, k = _ijk(b, mb)
     s = level_b - level
     return _index(i >> s, j >> s, k >> s, 1 << level)
+
+
+# ---------------------------------------------------------------- adaptive trees
+def _adjacent(n1, n2, maxd: int) -> bool:
+    """Closed boxes of nodes (depth, i, j, k) intersect (exact, in units of the
+    deepest level)."""
+    d1, d2 = n1[0], n2[0]
+    s1, s2 = 1 << (maxd - d1), 1 << (maxd - d2)
+    return all(n1[1 + a] * s1 <= (n2[1 + a] + 1) * s2 and n2[1 + a] * s2 <= (n1[1 + a] + 1) * s1
+               for a in range(3))
+
+
+def fmm_adaptive(tree, pts, f, phi, nrm, w, p: int, mu: float = 1.0, flux: bool = True,
+                 stats: dict | None = None):
+    """The same method on an adaptive octree (synth.octree: leaves in Morton
+    order, points sorted by leaf, U-lists of adjacent leaves).  Besides the
+    interaction (V) lists, a leaf B takes the upward equivalent densities of
+    its W-list at its points (descendants of its same-level neighbours that do
+    not touch B but whose parent does), and a node B takes the sources of its
+    X-list (the leaves whose W-list holds B) on its downward check surface."""
+    pts = np.asarray(pts, dtype=np.float64)
+    n = pts.shape[0]
+    zeros = np.zeros((n, 3))
+    f = zeros if f is None else np.asarray(f, dtype=np.float64)
+    phi = zeros if phi is None else np.asarray(phi, dtype=np.float64)
+    nrm = np.tile([0.0, 0.0, 1.0], (n, 1)) if nrm is None else np.asarray(nrm, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    MD = 21
+    S = cube_surface(p)
+
+    leaves = []
+    for b in range(tree.nleaf):
+        d = int(tree.leaf_depth[b])
+        a = tuple(int(v) >> (MD - d) for v in tree.leaf_lo[b])
+        leaves.append((d,) + a)
+    leaf_id = {nd: b for b, nd in enumerate(leaves)}
+    nodes = set()
+    for nd in leaves:
+        d = nd[0]
+        for k in range(d + 1):
+            nodes.add((k,) + tuple(v >> (d - k) for v in nd[1:]))
+    children = {}
+    for nd in nodes:
+        if nd[0] > 0:
+            par = (nd[0] - 1,) + tuple(v >> 1 for v in nd[1:])
+            children.setdefault(par, []).append(nd)
+    by_depth = {}
+    for nd in nodes:
+        by_depth.setdefault(nd[0], []).append(nd)
+    maxd = max(by_depth)
+
+    def geom(nd):
+        size = tree.root_size / (1 << nd[0])
+        return tree.root_lo + (np.asarray(nd[1:], dtype=np.float64) + 0.5) * size, size / 2
+
+    def parent(nd):
+        return (nd[0] - 1,) + tuple(v >> 1 for v in nd[1:])
+
+    def colleagues(nd):
+        return [q for q in by_depth[nd[0]] if _adjacent(q, nd, maxd)]
+
+    def leaf_points(nd):
+        b = leaf_id[nd]
+        return np.arange(tree.leaf_ptr[b], tree.leaf_ptr[b + 1])
+
+    uc2e, dc2e = {}, {}
+
+    def ops(d):
+        if d not in uc2e:
+            r = tree.root_size / (1 << d) / 2
+            uc2e[d] = pinv(upward_matrix(R_OUTER * r * S, R_INNER * r * S, mu, flux))
+            dc2e[d] = pinv(stokeslet_matrix(R_INNER * r * S, R_OUTER * r * S, mu))
+        return uc2e[d], dc2e[d]
+
+    # upward pass (deepest first)
+    up = {}
+    for d in sorted(by_depth, reverse=True):
+        for nd in by_depth[d]:
+            c, r = geom(nd)
+            if nd in leaf_id:
+                idx = leaf_points(nd)
+                chk = _sldl(pts[idx], f[idx], nrm[idx], phi[idx], w[idx], c + R_OUTER * r * S, mu).reshape(-1)
+            else:
+                chk = 0.0
+                for ch in children[nd]:
+                    cc, rc = geom(ch)
+                    chk = chk + upward_matrix(c + R_OUTER * r * S, cc + R_INNER * rc * S, mu, flux) @ up[ch]
+            up[nd] = ops(d)[0] @ chk
+
+    # lists
+    V, W, X = {}, {}, {}
+    for nd in nodes:
+        if nd[0] >= 2:
+            V[nd] = [ch for q in colleagues(parent(nd)) for ch in children.get(q, [])
+                     if not _adjacent(ch, nd, maxd)]
+    for nd in leaves:
+        W[nd] = []
+        stack = [q for q in colleagues(nd) if q != nd and q not in leaf_id]
+        while stack:
+            q = stack.pop()
+            for ch in children.get(q, []):
+                if not _adjacent(ch, nd, maxd):
+                    W[nd].append(ch)  # its parent q touches nd
+                elif ch not in leaf_id:
+                    stack.append(ch)
+        for a in W[nd]:
+            X.setdefault(a, []).append(nd)
+    if stats is not None:
+        stats.update(v=sum(map(len, V.values())), w=sum(map(len, W.values())),
+                     x=sum(map(len, X.values())), depths=sorted(by_depth))
+
+    # downward pass (shallowest first); M2L matrices cached by depth and offset
+    m2l = {}
+    down = {}
+    for d in sorted(by_depth):
+        if d < 2:
+            continue
+        for nd in by_depth[d]:
+            c, r = geom(nd)
+            chk = np.zeros(3 * S.shape[0])
+            for a in V[nd]:
+                key = (d,) + tuple(a[i + 1] - nd[i + 1] for i in range(3))
+                if key not in m2l:
+                    h = 2 * r
+                    m2l[key] = upward_matrix(R_INNER * r * S, np.asarray(key[1:], float) * h
+                                             + R_INNER * r * S, mu, flux)
+                chk += m2l[key] @ up[a]
+            for a in X.get(nd, []):
+                idx = leaf_points(a)
+                chk += _sldl(pts[idx], f[idx], nrm[idx], phi[idx], w[idx], c + R_INNER * r * S, mu).reshape(-1)
+            if d > 2:
+                pc, pr = geom(parent(nd))
+                chk += stokeslet_matrix(c + R_INNER * r * S, pc + R_OUTER * pr * S, mu) @ down[parent(nd)]
+            down[nd] = ops(d)[1] @ chk
+
+    # leaves: L2T, W-list, U-list
+    u = np.zeros((n, 3))
+    for nd in leaves:
+        b = leaf_id[nd]
+        idx = leaf_points(nd)
+        if nd[0] >= 2:
+            c, r = geom(nd)
+            u[idx] += (stokeslet_matrix(pts[idx], c + R_OUTER * r * S, mu) @ down[nd]).reshape(-1, 3)
+        for a in W[nd]:
+            ca, ra = geom(a)
+            u[idx] += (upward_matrix(pts[idx], ca + R_INNER * ra * S, mu, flux) @ up[a]).reshape(-1, 3)
+        near = np.concatenate([leaf_points(leaves[a]) for a in
+                               tree.ulist_idx[tree.ulist_ptr[b]:tree.ulist_ptr[b + 1]]])
+        u[idx] += _sldl(pts[near], f[near], nrm[near], phi[near], w[near], pts[idx], mu)
+    return u

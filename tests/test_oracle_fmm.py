@@ -68,3 +68,17 @@ def test_double_layer_far_field_needs_the_source_term(cloud):
     with_flux = _rel(F.fmm(pts, None, phi, nrm, w, depth=3, p=4, flux=True), ref)
     stokeslets = _rel(F.fmm(pts, None, phi, nrm, w, depth=3, p=4, flux=False), ref)
     assert with_flux <= 1e-2 and stokeslets >= 10 * with_flux, (with_flux, stokeslets)
+
+
+def test_adaptive_tree_matches_the_direct_sum():
+    """On an adaptive octree of the near-field workload's kind (cells and wall
+    patches, leaves at several depths) the W and X lists carry real interactions,
+    and the far field still falls with the surface order against the direct sum."""
+    from synth import workloads as W
+    wl = W.p2p_workload(ncell=6, radius=8.0, n_wall_patch=6, max_leaf=32)
+    ref = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts, wl.mu)
+    st = {}
+    e4 = _rel(F.fmm_adaptive(wl.tree, wl.pts, wl.f, wl.phi, wl.nrm, wl.w, 4, wl.mu, stats=st), ref)
+    e5 = _rel(F.fmm_adaptive(wl.tree, wl.pts, wl.f, wl.phi, wl.nrm, wl.w, 5, wl.mu), ref)
+    assert st["w"] > 0 and st["x"] > 0 and st["v"] > 0 and len(set(wl.tree.leaf_depth)) > 1
+    assert e4 <= 5e-3 and e5 <= e4 / 2, (e4, e5)

@@ -288,6 +288,24 @@ stk_status stokes_near_patch_search(const double *nodes, int32_t npatch, int32_t
 stk_status stokes_near_search_workspace_size(int32_t npatch, int32_t q, int64_t nt,
                                              size_t *bytes);
 
+/* ------------------------------------------------- FMM operators (host)
+ * Set-up of the kernel-independent FMM of Sec. 3.1 ("Far evaluation"), host
+ * only (no device memory, no stream).  Surface points: the boundary of a
+ * p x p x p grid on [-1, 1]^3 (index i slowest, k fastest), count
+ * p^3 - (p-2)^3; pts [count][3] may be NULL to query the count.
+ * Check-to-equivalent operator of a box of half-width r: the pseudo-inverse
+ * (one-sided Jacobi SVD, singular values below rcond * max dropped, FP64) of
+ * the kernel matrix from equivalent points to check points.  upward != 0:
+ * check points at 2.95 r, equivalent points at 1.05 r, densities of a force
+ * and, when flux != 0, a point-source strength per point (out is
+ * [(3 or 4) count][3 count], row-major); upward == 0: check at 1.05 r,
+ * equivalent at 2.95 r, forces only (out [3 count][3 count]).  Check
+ * velocities are [count][3], densities [count][3 or 4] in point order.
+ * 2 <= p <= 12 for the operator (16 for the points); STK_EINVAL otherwise. */
+stk_status stokes_fmm_surface(int32_t p, double *pts, int32_t *count);
+stk_status stokes_fmm_check_to_equiv(int32_t p, double r, double mu, int32_t upward,
+                                     int32_t flux, double rcond, double *out);
+
 /* ------------------------------------------------- no-allocation variant
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory when they need a velocity (an application

@@ -1,0 +1,180 @@
+// fmm_ops.cu -- host-side operators of the kernel-independent FMM that
+// evaluates the smooth quadrature at all targets at once (Sec. 3.1, "Far
+// evaluation"): the equivalent and check surfaces of a box and the
+// check-to-equivalent solves, computed once per plan in FP64.
+//
+// A box of half-width r gets the boundary points of a p x p x p grid on cubes
+// of half-width 1.05 r (upward equivalent, downward check) and 2.95 r (upward
+// check, downward equivalent).  The upward equivalent density has a force and,
+// with flux, a point-source strength per surface point (a double layer has net
+// flux through a closed surface, which Stokeslets cannot carry); the downward
+// one a force.  The check-to-equivalent operator is the pseudo-inverse of the
+// kernel matrix from equivalent to check points, truncated at rcond times the
+// largest singular value, by a one-sided (Hestenes) Jacobi SVD.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/stokesgpu.h"
+
+namespace stk {
+stk_status report_error(stk_status s, const char *msg);
+}
+
+namespace {
+
+constexpr double kPiF = 3.14159265358979323846;
+constexpr double kInner = 1.05, kOuter = 2.95;
+
+int surface_count(int p) { return p * p * p - (p - 2) * (p - 2) * (p - 2); }
+
+// boundary points of the p^3 grid on [-1, 1]^3, i slowest, k fastest
+void surface(int p, std::vector<double> &s) {
+  s.clear();
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j)
+      for (int k = 0; k < p; ++k) {
+        if (!(i == 0 || j == 0 || k == 0 || i == p - 1 || j == p - 1 || k == p - 1)) continue;
+        const double c[3] = {-1.0 + 2.0 * i / (p - 1), -1.0 + 2.0 * j / (p - 1),
+                             -1.0 + 2.0 * k / (p - 1)};
+        s.insert(s.end(), c, c + 3);
+      }
+}
+
+// Row-major [3 nx][ncomp ny] kernel matrix from densities at y to velocities
+// at x: a force (Oseen tensor / (8 pi mu)) and, with ncomp = 4, a source
+// d / (4 pi r^3).
+void kernel_matrix(const std::vector<double> &x, const std::vector<double> &y, double mu,
+                   int ncomp, std::vector<double> &K) {
+  const size_t nx = x.size() / 3, ny = y.size() / 3, cols = (size_t)ncomp * ny;
+  K.assign(3 * nx * cols, 0.0);
+  for (size_t a = 0; a < nx; ++a)
+    for (size_t b = 0; b < ny; ++b) {
+      const double d[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1],
+                           x[3 * a + 2] - y[3 * b + 2]};
+      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (!(r2 > 0.0)) continue;
+      const double ri = 1.0 / std::sqrt(r2), ri3 = ri * ri * ri;
+      for (int i = 0; i < 3; ++i) {
+        double *row = K.data() + (3 * a + i) * cols + (size_t)ncomp * b;
+        for (int j = 0; j < 3; ++j)
+          row[j] = ((i == j ? ri : 0.0) + d[i] * d[j] * ri3) / (8.0 * kPiF * mu);
+        if (ncomp == 4) row[3] = d[i] * ri3 / (4.0 * kPiF);
+      }
+    }
+}
+
+// Pseudo-inverse of the row-major m x n matrix A (n x m, row-major), singular
+// values below rcond * max truncated.  One-sided Jacobi on the columns of B,
+// B = A^T when m < n (more columns than rows) and B = A otherwise.
+void pinv(const std::vector<double> &A, int m, int n, double rcond, std::vector<double> &X) {
+  const bool tr = m < n;
+  const int rows = tr ? n : m, cols = tr ? m : n;
+  // column-major copy of B
+  std::vector<double> Bc((size_t)rows * cols), V((size_t)cols * cols, 0.0);
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c)
+      Bc[(size_t)c * rows + r] = tr ? A[(size_t)c * n + r] : A[(size_t)r * n + c];
+  for (int c = 0; c < cols; ++c) V[(size_t)c * cols + c] = 1.0;
+  const double eps = 1e-15;
+  for (int sweep = 0; sweep < 80; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < cols - 1; ++i)
+      for (int j = i + 1; j < cols; ++j) {
+        double *bi = &Bc[(size_t)i * rows], *bj = &Bc[(size_t)j * rows];
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int r = 0; r < rows; ++r) {
+          al += bi[r] * bi[r];
+          be += bj[r] * bj[r];
+          ga += bi[r] * bj[r];
+        }
+        if (al == 0.0 || be == 0.0) continue;
+        const double rel = std::fabs(ga) / std::sqrt(al * be);
+        if (rel <= eps) continue;
+        off = std::fmax(off, rel);
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = cs * t;
+        for (int r = 0; r < rows; ++r) {
+          const double u = bi[r], v = bj[r];
+          bi[r] = cs * u - sn * v;
+          bj[r] = sn * u + cs * v;
+        }
+        double *vi = &V[(size_t)i * cols], *vj = &V[(size_t)j * cols];
+        for (int r = 0; r < cols; ++r) {
+          const double u = vi[r], v = vj[r];
+          vi[r] = cs * u - sn * v;
+          vj[r] = sn * u + cs * v;
+        }
+      }
+    if (off <= eps) break;
+  }
+  // B = U S V^T with U's columns b_c / s_c
+  std::vector<double> s(cols);
+  double smax = 0.0;
+  for (int c = 0; c < cols; ++c) {
+    double q = 0.0;
+    for (int r = 0; r < rows; ++r) q += Bc[(size_t)c * rows + r] * Bc[(size_t)c * rows + r];
+    s[c] = std::sqrt(q);
+    smax = std::fmax(smax, s[c]);
+  }
+  // pinv(B) = V S^+ U^T  (cols x rows);  pinv(A) = pinv(B)^T when B = A^T
+  X.assign((size_t)n * m, 0.0);
+  for (int c = 0; c < cols; ++c) {
+    if (!(s[c] > rcond * smax)) continue;
+    const double inv2 = 1.0 / (s[c] * s[c]);  // U column = b_c / s_c, times 1 / s_c
+    for (int a = 0; a < cols; ++a) {
+      const double va = V[(size_t)c * cols + a] * inv2;
+      if (va == 0.0) continue;
+      const double *bc = &Bc[(size_t)c * rows];
+      for (int r = 0; r < rows; ++r) {
+        // pinv(B)[a][r] += V[a][c] / s_c^2 * b_c[r]
+        if (tr)
+          X[(size_t)r * m + a] += va * bc[r];  // pinv(A) = pinv(B)^T: n x m
+        else
+          X[(size_t)a * m + r] += va * bc[r];
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+stk_status stokes_fmm_surface(int32_t p, double *pts, int32_t *count) {
+  if (p < 2 || p > 16) return stk::report_error(STK_EINVAL, "p must be in [2, 16]");
+  if (count) *count = surface_count(p);
+  if (pts) {
+    std::vector<double> s;
+    surface(p, s);
+    std::memcpy(pts, s.data(), sizeof(double) * s.size());
+  }
+  return STK_OK;
+}
+
+stk_status stokes_fmm_check_to_equiv(int32_t p, double r, double mu, int32_t upward,
+                                     int32_t flux, double rcond, double *out) {
+  if (p < 2 || p > 12) return stk::report_error(STK_EINVAL, "p must be in [2, 12]");
+  if (!(r > 0.0) || !std::isfinite(r)) return stk::report_error(STK_EINVAL, "r must be > 0");
+  if (!(mu > 0.0) || !std::isfinite(mu)) return stk::report_error(STK_EINVAL, "mu must be > 0");
+  if (!(rcond >= 0.0 && rcond < 1.0)) return stk::report_error(STK_EINVAL, "rcond must be in [0, 1)");
+  if (!out) return stk::report_error(STK_EINVAL, "out is NULL");
+  std::vector<double> s, chk, eqv, K, X;
+  surface(p, s);
+  const int ns = surface_count(p);
+  chk.resize(s.size());
+  eqv.resize(s.size());
+  const double rc = (upward ? kOuter : kInner) * r, re = (upward ? kInner : kOuter) * r;
+  for (size_t i = 0; i < s.size(); ++i) {
+    chk[i] = rc * s[i];
+    eqv[i] = re * s[i];
+  }
+  const int ncomp = (upward && flux) ? 4 : 3;
+  kernel_matrix(chk, eqv, mu, ncomp, K);
+  pinv(K, 3 * ns, ncomp * ns, rcond, X);
+  std::memcpy(out, X.data(), sizeof(double) * X.size());
+  return STK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+"""Host-side FMM operators of the library (surface points and check-to-equivalent
+pseudo-inverses, FP64 Jacobi SVD) against the FMM oracle's own numpy version:
+the same surface, the Penrose conditions of the pseudo-inverse, and the same far
+field from the equivalent densities they give.  No GPU is needed."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import fmm as F
+from paper_1909_11085_gb300 import _abi as A
+from paper_1909_11085_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    oracle.build()
+    return A.lib()
+
+
+def _surface(L, p):
+    c = ctypes.c_int32(0)
+    assert L.stokes_fmm_surface(p, None, ctypes.byref(c)) == 0
+    pts = np.zeros((c.value, 3))
+    assert L.stokes_fmm_surface(p, pts.ctypes.data, None) == 0
+    return pts
+
+
+def _c2e(L, p, r, mu, upward, flux):
+    ns = p ** 3 - (p - 2) ** 3
+    out = np.zeros(((4 if (upward and flux) else 3) * ns, 3 * ns))
+    assert L.stokes_fmm_check_to_equiv(p, r, mu, int(upward), int(flux), 1e-13, out.ctypes.data) == 0
+    return out
+
+
+@pytest.mark.parametrize("p", [3, 4, 6])
+def test_surface_matches_the_oracle(L, p):
+    np.testing.assert_allclose(_surface(L, p), F.cube_surface(p), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("upward,flux", [(True, True), (True, False), (False, False)])
+def test_check_to_equivalent(L, upward, flux):
+    p, r, mu = 4, 0.37, 0.8
+    S = F.cube_surface(p)
+    chk, eqv = ((F.R_OUTER, F.R_INNER) if upward else (F.R_INNER, F.R_OUTER))
+    K = (F.upward_matrix(chk * r * S, eqv * r * S, mu, flux) if upward
+         else F.stokeslet_matrix(chk * r * S, eqv * r * S, mu))
+    X = _c2e(L, p, r, mu, upward, flux)
+    # Penrose conditions of the (truncated) pseudo-inverse
+    assert np.linalg.norm(K @ X @ K - K) <= 1e-9 * np.linalg.norm(K)
+    assert np.linalg.norm(X @ K @ X - X) <= 1e-6 * np.linalg.norm(X)
+    assert np.allclose(X @ K, (X @ K).T, rtol=0, atol=1e-6) and np.allclose(K @ X, (K @ X).T, rtol=0, atol=1e-6)
+    # the field of sources inside (upward) or outside (downward) the box, fitted on
+    # the check points, is reproduced where the expansion is used
+    rng = np.random.default_rng(7)
+    if upward:
+        ys = rng.uniform(-r, r, (20, 3))
+        far = rng.normal(size=(40, 3))
+        far = 4 * r * far / np.linalg.norm(far, axis=1)[:, None] * rng.uniform(1, 2, (40, 1))
+    else:
+        ys = rng.normal(size=(20, 3))
+        ys = 4 * r * ys / np.linalg.norm(ys, axis=1)[:, None] * rng.uniform(1, 2, (20, 1))
+        far = rng.uniform(-r, r, (40, 3))
+    fs = rng.uniform(-1, 1, (20, 3))
+    src = lambda x: (F.stokeslet_matrix(x, ys, mu) @ fs.reshape(-1))
+    e_lib, e_np = X @ src(chk * r * S), F.pinv(K) @ src(chk * r * S)
+    Kf = (F.upward_matrix(far, eqv * r * S, mu, flux) if upward else F.stokeslet_matrix(far, eqv * r * S, mu))
+    ref = src(far)
+    err_lib = np.linalg.norm(Kf @ e_lib - ref) / np.linalg.norm(ref)
+    err_np = np.linalg.norm(Kf @ e_np - ref) / np.linalg.norm(ref)
+    assert err_lib <= 1e-3 and err_lib <= 2 * err_np + 1e-12, (err_lib, err_np)
+
+
+def test_rejects_bad_arguments(L):
+    out = np.zeros(1)
+    assert L.stokes_fmm_check_to_equiv(1, 1.0, 1.0, 1, 1, 1e-13, out.ctypes.data) != 0
+    assert L.stokes_fmm_check_to_equiv(4, -1.0, 1.0, 1, 1, 1e-13, out.ctypes.data) != 0
+    assert L.stokes_fmm_check_to_equiv(4, 1.0, 1.0, 1, 1, 1e-13, None) != 0

@@ -305,6 +305,13 @@ stk_status stokes_near_search_workspace_size(int32_t npatch, int32_t q, int64_t 
 stk_status stokes_fmm_surface(int32_t p, double *pts, int32_t *count);
 stk_status stokes_fmm_check_to_equiv(int32_t p, double r, double mu, int32_t upward,
                                      int32_t flux, double rcond, double *out);
+/* Kernel matrix [3 nx][ncomp ny] (row-major) from densities at y [ny][3] to
+ * velocities at x [nx][3]: a force per point (Oseen tensor / (8 pi mu)) and,
+ * for ncomp = 4, a point-source strength (d / (4 pi |d|^3)); coincident points
+ * give zero.  With surface points placed by the caller it gives the FMM's
+ * translation operators (M2M, M2L, L2L) on the host. */
+stk_status stokes_fmm_kernel_matrix(const double *x, int32_t nx, const double *y, int32_t ny,
+                                    double mu, int32_t ncomp, double *out);
 
 /* ------------------------------------------------- no-allocation variant
  * The paper has no counterpart to this entry point; it serves callers that

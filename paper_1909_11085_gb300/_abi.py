@@ -32,7 +32,7 @@ EXPORTS = [
     "stokes_graph_destroy", "stokes_checkpoint_eval", "stokes_checkpoint_workspace_size",
     "stokes_upsample_patches", "stokes_bie_matvec", "stokes_bie_workspace_size",
     "stokes_near_patch_search", "stokes_near_search_workspace_size",
-    "stokes_fmm_surface", "stokes_fmm_check_to_equiv",
+    "stokes_fmm_surface", "stokes_fmm_check_to_equiv", "stokes_fmm_kernel_matrix",
 ]
 
 
@@ -107,6 +107,7 @@ def lib():
             L.stokes_near_search_workspace_size.argtypes = [i32, i32, i64, psz]
             L.stokes_fmm_surface.argtypes = [i32, p, ctypes.POINTER(ctypes.c_int32)]
             L.stokes_fmm_check_to_equiv.argtypes = [i32, d, d, i32, i32, d, p]
+            L.stokes_fmm_kernel_matrix.argtypes = [p, i32, p, i32, d, i32, p]
             L.stokes_graph_destroy.argtypes = [p]
             L.stokes_launch_count.restype = ctypes.c_int64
             for name in EXPORTS:

@@ -177,4 +177,17 @@ stk_status stokes_fmm_check_to_equiv(int32_t p, double r, double mu, int32_t upw
   return STK_OK;
 }
 
+stk_status stokes_fmm_kernel_matrix(const double *x, int32_t nx, const double *y, int32_t ny,
+                                    double mu, int32_t ncomp, double *out) {
+  if (nx < 0 || ny < 0) return stk::report_error(STK_EINVAL, "nx and ny must be >= 0");
+  if (ncomp != 3 && ncomp != 4) return stk::report_error(STK_EINVAL, "ncomp must be 3 or 4");
+  if (!(mu > 0.0) || !std::isfinite(mu)) return stk::report_error(STK_EINVAL, "mu must be > 0");
+  if ((nx > 0 || ny > 0) && (!x || !y || !out)) return stk::report_error(STK_EINVAL, "NULL pointer");
+  if (nx == 0 || ny == 0) return STK_OK;
+  std::vector<double> X(x, x + 3 * (size_t)nx), Y(y, y + 3 * (size_t)ny), K;
+  kernel_matrix(X, Y, mu, ncomp, K);
+  std::memcpy(out, K.data(), sizeof(double) * K.size());
+  return STK_OK;
+}
+
 }  // extern "C"

@@ -78,3 +78,19 @@ def test_rejects_bad_arguments(L):
     assert L.stokes_fmm_check_to_equiv(1, 1.0, 1.0, 1, 1, 1e-13, out.ctypes.data) != 0
     assert L.stokes_fmm_check_to_equiv(4, -1.0, 1.0, 1, 1, 1e-13, out.ctypes.data) != 0
     assert L.stokes_fmm_check_to_equiv(4, 1.0, 1.0, 1, 1, 1e-13, None) != 0
+
+
+@pytest.mark.parametrize("ncomp", [3, 4])
+def test_translation_matrices_match_the_oracle(L, ncomp):
+    """M2L between two boxes of one level (an offset of the interaction list)
+    and M2M from a child to its parent, built from placed surfaces."""
+    p, r, mu = 4, 0.25, 1.3
+    S = F.cube_surface(p)
+    for x, y in [(F.R_INNER * r * S, np.array([2.0, -3.0, 1.0]) * 2 * r + F.R_INNER * r * S),
+                 (F.R_OUTER * 2 * r * S, np.array([0.5, -0.5, 0.5]) * 2 * r + F.R_INNER * r * S)]:
+        out = np.zeros((3 * x.shape[0], ncomp * y.shape[0]))
+        assert L.stokes_fmm_kernel_matrix(np.ascontiguousarray(x).ctypes.data, x.shape[0],
+                                          np.ascontiguousarray(y).ctypes.data, y.shape[0], mu,
+                                          ncomp, out.ctypes.data) == 0
+        ref = F.upward_matrix(x, y, mu, ncomp == 4)
+        np.testing.assert_allclose(out, ref, rtol=1e-13, atol=1e-16 * np.abs(ref).max())

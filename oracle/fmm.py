@@ -232,7 +232,7 @@ def _adjacent(n1, n2, maxd: int) -> bool:
 
 
 def fmm_adaptive(tree, pts, f, phi, nrm, w, p: int, mu: float = 1.0, flux: bool = True,
-                 stats: dict | None = None):
+                 stats: dict | None = None, lists_only: bool = False):
     """The same method on an adaptive octree (synth.octree: leaves in Morton
     order, points sorted by leaf, U-lists of adjacent leaves).  Besides the
     interaction (V) lists, a leaf B takes the upward equivalent densities of
@@ -295,7 +295,7 @@ def fmm_adaptive(tree, pts, f, phi, nrm, w, p: int, mu: float = 1.0, flux: bool 
 
     # upward pass (deepest first)
     up = {}
-    for d in sorted(by_depth, reverse=True):
+    for d in (sorted(by_depth, reverse=True) if not lists_only else ()):
         for nd in by_depth[d]:
             c, r = geom(nd)
             if nd in leaf_id:
@@ -328,7 +328,10 @@ def fmm_adaptive(tree, pts, f, phi, nrm, w, p: int, mu: float = 1.0, flux: bool 
             X.setdefault(a, []).append(nd)
     if stats is not None:
         stats.update(v=sum(map(len, V.values())), w=sum(map(len, W.values())),
-                     x=sum(map(len, X.values())), depths=sorted(by_depth))
+                     x=sum(map(len, X.values())), depths=sorted(by_depth),
+                     lists={"V": V, "W": W, "X": X})
+    if lists_only:
+        return None
 
     # downward pass (shallowest first); M2L matrices cached by depth and offset
     m2l = {}

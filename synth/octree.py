@@ -145,3 +145,100 @@ def build_octree(pts: np.ndarray, max_leaf: int = 256) -> Octree:
                   ulist_ptr=ulist_ptr.astype(np.int32), ulist_idx=ulist_idx.astype(np.int32),
                   leaf_lo=box_lo, leaf_hi=box_hi, leaf_depth=depth, root_lo=lo,
                   root_size=size)
+
+
+@dataclass
+class FarLists:
+    """All boxes of an octree and the interaction lists of the FMM's far field.
+
+    Boxes are numbered depth by depth (depth 0 first), Morton order within a
+    depth.  `leaf[n]` is the leaf number of box n or -1; `parent[n]` is -1 for
+    the root.  CSR lists over box numbers:
+      V(B): children of the same-level neighbours of B's parent that do not touch B;
+      W(B), B a leaf: boxes A below B's same-level neighbours that do not touch B
+            while their parent does;
+      X(B): the leaves A with B in W(A).
+    "Touch" is the closed-box intersection of the U-lists."""
+    depth: np.ndarray      # int32 [M]
+    anchor: np.ndarray     # int64 [M, 3] box index at its depth
+    parent: np.ndarray     # int32 [M]
+    leaf: np.ndarray       # int32 [M]
+    v_ptr: np.ndarray
+    v_idx: np.ndarray
+    w_ptr: np.ndarray
+    w_idx: np.ndarray
+    x_ptr: np.ndarray
+    x_idx: np.ndarray
+
+
+def far_lists(tree: Octree) -> FarLists:
+    leaves = [(int(tree.leaf_depth[b]),) + tuple(int(v) >> (MAX_DEPTH - int(tree.leaf_depth[b]))
+                                                 for v in tree.leaf_lo[b]) for b in range(tree.nleaf)]
+    nodes = set()
+    for nd in leaves:
+        d = nd[0]
+        for k in range(d + 1):
+            nodes.add((k,) + tuple(v >> (d - k) for v in nd[1:]))
+
+    def mkey(nd):
+        return (nd[0],) + (int(morton_keys(np.asarray([nd[1:]], dtype=np.int64))[0]),)
+
+    order = sorted(nodes, key=mkey)
+    num = {nd: i for i, nd in enumerate(order)}
+    leaf_of = {nd: b for b, nd in enumerate(leaves)}
+    M = len(order)
+    depth = np.array([nd[0] for nd in order], dtype=np.int32)
+    anchor = np.array([nd[1:] for nd in order], dtype=np.int64).reshape(M, 3)
+    par = np.array([num[(nd[0] - 1,) + tuple(v >> 1 for v in nd[1:])] if nd[0] else -1
+                    for nd in order], dtype=np.int32)
+    leaf = np.array([leaf_of.get(nd, -1) for nd in order], dtype=np.int32)
+    kids = {}
+    for nd in order:
+        if nd[0]:
+            kids.setdefault((nd[0] - 1,) + tuple(v >> 1 for v in nd[1:]), []).append(nd)
+
+    def touch(a, b):
+        sa, sb = 1 << (MAX_DEPTH - a[0]), 1 << (MAX_DEPTH - b[0])
+        return all(a[1 + i] * sa <= (b[1 + i] + 1) * sb and b[1 + i] * sb <= (a[1 + i] + 1) * sa
+                   for i in range(3))
+
+    def neighbours(nd):
+        d = nd[0]
+        out = []
+        for o in np.ndindex(3, 3, 3):
+            q = (d,) + tuple(nd[1 + i] + o[i] - 1 for i in range(3))
+            if q in num:
+                out.append(q)
+        return out
+
+    V = [[] for _ in range(M)]
+    W = [[] for _ in range(M)]
+    X = [[] for _ in range(M)]
+    for nd in order:
+        if nd[0] >= 2:
+            pn = (nd[0] - 1,) + tuple(v >> 1 for v in nd[1:])
+            V[num[nd]] = sorted(num[c] for q in neighbours(pn) for c in kids.get(q, ())
+                                if not touch(c, nd))
+    for nd in leaves:
+        stack = [q for q in neighbours(nd) if q != nd and q not in leaf_of]
+        out = []
+        while stack:
+            q = stack.pop()
+            for c in kids.get(q, ()):
+                if not touch(c, nd):
+                    out.append(num[c])
+                elif c not in leaf_of:
+                    stack.append(c)
+        W[num[nd]] = sorted(out)
+        for a in out:
+            X[a].append(num[nd])
+
+    def csr(lists):
+        ptr = np.zeros(M + 1, dtype=np.int64)
+        ptr[1:] = np.cumsum([len(x) for x in lists])
+        idx = np.array([i for x in lists for i in sorted(x)], dtype=np.int32)
+        return ptr, idx
+
+    (vp, vi), (wp, wi), (xp, xi) = csr(V), csr(W), csr(X)
+    return FarLists(depth=depth, anchor=anchor, parent=par, leaf=leaf, v_ptr=vp, v_idx=vi,
+                    w_ptr=wp, w_idx=wi, x_ptr=xp, x_idx=xi)

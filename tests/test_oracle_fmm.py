@@ -82,3 +82,21 @@ def test_adaptive_tree_matches_the_direct_sum():
     e5 = _rel(F.fmm_adaptive(wl.tree, wl.pts, wl.f, wl.phi, wl.nrm, wl.w, 5, wl.mu), ref)
     assert st["w"] > 0 and st["x"] > 0 and st["v"] > 0 and len(set(wl.tree.leaf_depth)) > 1
     assert e4 <= 5e-3 and e5 <= e4 / 2, (e4, e5)
+
+
+def test_generated_far_lists_match_their_definitions():
+    """The interaction lists the input generator hands to both paths (as it hands
+    the U-lists) equal the oracle's, which follow the definitions box by box."""
+    from synth import octree as O
+    from synth import workloads as W
+    wl = W.p2p_workload(ncell=6, radius=8.0, n_wall_patch=6, max_leaf=32)
+    fl = O.far_lists(wl.tree)
+    st = {}
+    F.fmm_adaptive(wl.tree, wl.pts[:0], None, None, None, np.zeros(0), 2, stats=st, lists_only=True)
+    key = lambda n: (int(fl.depth[n]),) + tuple(int(v) for v in fl.anchor[n])
+    for name, ptr, idx in (("V", fl.v_ptr, fl.v_idx), ("W", fl.w_ptr, fl.w_idx), ("X", fl.x_ptr, fl.x_idx)):
+        ref = st["lists"][name]
+        got = {key(n): sorted(key(int(a)) for a in idx[ptr[n]:ptr[n + 1]]) for n in range(fl.depth.size)}
+        for nd, lst in ref.items():
+            assert sorted(lst) == got[nd], (name, nd)
+        assert sum(len(v) for v in got.values()) == sum(len(v) for v in ref.values()), name

@@ -185,8 +185,9 @@ stk_status stokes_graph_destroy(void *graph_exec);
  * When the targets are the sources, the caller adds grad_x to grad_y.
  * MIXED: FP32 pair terms in per-CTA local frames with two-sum accumulation;
  * pairs with |r| < near_ratio * h_j are listed per output point (up to 32;
- * a point with more is rescanned) and evaluated in FP64 by a second pass, in
- * input order, so results are deterministic.  FP64: all double.  The
+ * a point with more is rescanned over all inputs, one thread per such point,
+ * so inputs where most points are near each other are slow) and evaluated in
+ * FP64 by a second pass, in input order, so results are deterministic.  FP64: all double.  The
  * workspace (stokes_grad_workspace_size) holds the packed records, the
  * Morton orders, the per-split partial gradients and, for MIXED, the near-pair
  * lists.

@@ -25,20 +25,24 @@ def test_sample_pairs_counts_ulist_sources():
 
 
 def test_batched_pair_split_by_enumeration():
-    c = W.batched_workload(nsusp=4, max_cells=2, orders=(12,))
-    sl = dl = 0
-    for s in range(c.nsusp):
-        p0, p1 = int(c.susp_ptr[s]), int(c.susp_ptr[s + 1])
-        ncell = int(c.n_cell[s])
-        for i in range(p0, p1):
-            for j in range(p0, p1):
-                if i != j:
-                    if j - p0 < ncell:
-                        sl += 1
-                    else:
-                        dl += 1
-    assert bench.batched_pair_split(c.susp_ptr, c.n_cell) == (sl, dl)
-    assert sl + dl == c.pairs()
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        sizes = rng.integers(1, 40, 6)
+        n_cell = np.array([rng.integers(0, s + 1) for s in sizes])
+        susp_ptr = np.concatenate([[0], np.cumsum(sizes)])
+        sl = dl = 0
+        for s in range(sizes.size):
+            p0, p1 = int(susp_ptr[s]), int(susp_ptr[s + 1])
+            for i in range(p0, p1):
+                for j in range(p0, p1):
+                    if i != j:
+                        if j - p0 < n_cell[s]:
+                            sl += 1
+                        else:
+                            dl += 1
+        assert bench.batched_pair_split(susp_ptr, n_cell) == (sl, dl)
+    c = W.batched_workload(nsusp=3, max_cells=2, orders=(12,))
+    assert sum(bench.batched_pair_split(c.susp_ptr, c.n_cell)) == c.pairs()
 
 
 def test_traffic_record_follows_the_engine_sources(tmp_path, monkeypatch):

@@ -99,3 +99,28 @@ def test_tuning_cache_roundtrip(tmp_path):
     assert tuning.lookup(path, k2) == 2 and tuning.lookup(path, k3) == 1
     assert tuning.lookup(None, k1) is None
     tuning.store(None, k1, 3, 0.1)  # disabled cache: no-op
+
+
+def test_patch_surface_entry_points_validated_on_host(L):
+    """The check-point, BIE and near-zone entry points reject bad sizes and
+    options before any device work; the near-zone workspace grows with the
+    targets (a list of them) and with the patches."""
+    o = A.make_opts()
+    nb = ctypes.c_size_t(0)
+    assert L.stokes_checkpoint_workspace_size(0, 6, 10, 2, 10, 4, ctypes.byref(o), ctypes.byref(nb)) == A.STK_EINVAL
+    assert L.stokes_checkpoint_workspace_size(2, 6, 10, 2, 10, 4, ctypes.byref(o), None) == A.STK_EINVAL
+    assert L.stokes_bie_workspace_size(6, 10, 2, 4, None, ctypes.byref(nb)) == A.STK_EINVAL
+    assert L.stokes_near_search_workspace_size(-1, 10, 0, ctypes.byref(nb)) == A.STK_EINVAL
+    assert L.stokes_near_search_workspace_size(4, 1, 0, ctypes.byref(nb)) == A.STK_EUNSUPPORTED
+    assert L.stokes_near_search_workspace_size(4, 10, -1, ctypes.byref(nb)) == A.STK_EINVAL
+    assert L.stokes_near_search_workspace_size(4, 10, 1 << 31, ctypes.byref(nb)) == A.STK_EINVAL
+    sizes = []
+    for npatch, nt in ((4, 0), (4, 1000), (400, 1000)):
+        assert L.stokes_near_search_workspace_size(npatch, 10, nt, ctypes.byref(nb)) == A.STK_OK
+        sizes.append(nb.value)
+    assert sizes[0] < sizes[1] < sizes[2]
+    # no targets: nothing to do, whatever the pointers
+    assert L.stokes_near_patch_search(None, 4, 10, None, 0, 1.0, None, None, None, None, None,
+                                      None, 0, None) == A.STK_OK
+    assert L.stokes_near_patch_search(None, 4, 10, None, 5, -1.0, None, None, None, None, None,
+                                      None, 0, None) == A.STK_EINVAL

@@ -65,3 +65,28 @@ def test_cubed_sphere_closest_points():
     np.testing.assert_allclose(dist, np.abs(rho - a), atol=2e-4)
     np.testing.assert_allclose(y, a * d, atol=2e-4)
     np.testing.assert_allclose(n, d, atol=2e-4)
+
+
+def test_planar_patch_with_curved_parameters():
+    """A patch of the plane z = 0 whose (u, v) map is a quadratic warp (the
+    interpolant reproduces it exactly): the closest point of x is its orthogonal
+    projection, the distance |x_z| and the normal +-e_z, whatever the map."""
+    n1 = Q + 1
+    t = np.cos(np.pi * np.arange(n1) / Q)
+    U, V = np.meshgrid(t, t, indexing="ij")
+    X = U + 0.15 * V ** 2 - 0.1 * U * V
+    Y = V + 0.2 * U ** 2
+    nodes = np.stack([X, Y, np.zeros_like(X)], axis=-1).reshape(-1, 3)
+    rng = np.random.default_rng(11)
+    for _ in range(8):
+        u0, v0 = rng.uniform(-0.7, 0.7, 2)
+        p = np.array([u0 + 0.15 * v0 ** 2 - 0.1 * u0 * v0, v0 + 0.2 * u0 ** 2, 0.0])
+        h = rng.uniform(-0.5, 0.5)
+        x = p + np.array([0.0, 0.0, h])
+        d, u, v, y = NZ.closest_on_patch(nodes, Q, x)
+        assert abs(d - abs(h)) <= 1e-9 and np.abs(y - p).max() <= 1e-7, (d, h, y, p)
+        assert abs(u - u0) <= 1e-6 and abs(v - v0) <= 1e-6
+        _, Pu, Pv = NZ.patch_eval(nodes, Q, u, v)
+        nrm = np.cross(Pu[0], Pv[0])
+        nrm /= np.linalg.norm(nrm)
+        np.testing.assert_allclose(np.abs(nrm), [0.0, 0.0, 1.0], atol=1e-12)

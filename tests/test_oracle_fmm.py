@@ -100,3 +100,36 @@ def test_generated_far_lists_match_their_definitions():
         for nd, lst in ref.items():
             assert sorted(lst) == got[nd], (name, nd)
         assert sum(len(v) for v in got.values()) == sum(len(v) for v in ref.values()), name
+
+
+@pytest.mark.parametrize("p", [4, 6])
+def test_m2l_is_a_circular_convolution_on_the_surface_lattice(p):
+    """The upward equivalent and downward check surfaces of two boxes share one
+    radius (1.05 r), so their points are the boundary of one p^3 lattice of
+    spacing 2 (1.05 r) / (p - 1), shifted by the boxes' offset o; the kernel
+    then depends on the lattice index difference alone, K(delta (i - j) - o).
+    Zero-padding to a (2p)^3 grid turns the M2L translation into a circular
+    convolution whose FFT form equals the dense translation up to rounding,
+    for any o (no lattice alignment of o is needed)."""
+    rng = np.random.default_rng(p)
+    r = 0.37
+    a = F.R_INNER * r
+    delta = 2 * a / (p - 1)
+    S = F.cube_surface(p)
+    idx = np.rint((S + 1) * (p - 1) / 2).astype(int)
+    np.testing.assert_allclose(-a + delta * idx, a * S, atol=1e-15)
+    g = 2 * p
+    m = np.stack(np.meshgrid(*(np.arange(g),) * 3, indexing="ij"), -1).reshape(-1, 3)
+    m = np.where(m >= p, m - g, m)  # index differences -(p-1)..p-1, circular storage
+    e = rng.normal(size=(S.shape[0], 4))
+    E = np.zeros((g, g, g, 4))
+    E[idx[:, 0], idx[:, 1], idx[:, 2]] = e
+    Ef = np.fft.fftn(E, axes=(0, 1, 2))
+    for o in [(2, 0, 0), (3, -2, 1), (-2, 3, 3), (-3, -3, 2)]:
+        oc = np.asarray(o, float) * 2 * r
+        dense = F.upward_matrix(a * S, oc + a * S, 1.0, True) @ e.reshape(-1)
+        K = F.upward_matrix(delta * m, oc[None, :], 1.0, True).reshape(g, g, g, 3, 4)
+        Uf = np.einsum("xyzij,xyzj->xyzi", np.fft.fftn(K, axes=(0, 1, 2)), Ef)
+        U = np.real(np.fft.ifftn(Uf, axes=(0, 1, 2)))
+        conv = U[idx[:, 0], idx[:, 1], idx[:, 2]].reshape(-1)
+        assert _rel(conv, dense) <= 1e-13

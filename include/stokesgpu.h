@@ -343,7 +343,9 @@ stk_status stokes_device_status(void *workspace, size_t workspace_bytes);
  * call's stream, so that the caller can time the dominant kernel alone.
  * Passing NULLs switches it off. */
 stk_status stokes_set_engine_events(void *start_event, void *stop_event);
-/* Number of kernels this thread has launched through the library so far. */
+/* Number of kernels this thread has launched through the library so far.  A
+ * graph capture adds nothing (its kernels are recorded, not run); each
+ * stokes_graph_launch adds the kernels the graph holds. */
 int64_t stokes_launch_count(void);
 /* Message for the last error on the calling thread ("" if none). */
 const char *stokes_last_error(void);

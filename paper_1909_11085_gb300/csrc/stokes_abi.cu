@@ -17,7 +17,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "../../include/stokesgpu.h"
 #include "common.cuh"
@@ -29,6 +31,11 @@ namespace {
 
 thread_local std::string g_err;
 thread_local cudaEvent_t g_ev_start = nullptr, g_ev_stop = nullptr;
+
+// Kernels recorded in each executable graph the library captured, so that a
+// replay adds them to the launch count (any thread may replay a graph).
+std::mutex g_graph_mu;
+std::unordered_map<void *, int64_t> g_graph_kernels;
 
 stk_status fail(stk_status s, const char *msg) {
   g_err = msg;
@@ -797,11 +804,15 @@ stk_status tune_configs(cudaStream_t st, Call call, int32_t *best, float *best_m
     s = call(c);
     float t[3];
     for (int r = 0; r < 3 && s == STK_OK; ++r) {
-      cudaEventRecord(e0, st);
+      if (cudaEventRecord(e0, st) != cudaSuccess) {
+        s = fail(STK_ECUDA, "cudaEventRecord failed");
+        break;
+      }
       s = call(c);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) s = fail(STK_ECUDA, "tuning run failed");
-      cudaEventElapsedTime(&t[r], e0, e1);
+      if (s == STK_OK &&
+          (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+           cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess))
+        s = fail(STK_ECUDA, "tuning run failed");
     }
     if (s != STK_OK) break;
     const float med = fmaxf(fminf(t[0], t[1]), fminf(fmaxf(t[0], t[1]), t[2]));
@@ -820,7 +831,9 @@ stk_status tune_configs(cudaStream_t st, Call call, int32_t *best, float *best_m
   return STK_OK;
 }
 
-// Captures one call into an executable CUDA graph.
+// Captures one call into an executable CUDA graph.  Kernels recorded during
+// the capture do not run, so they leave the launch count as it was and are
+// counted at each replay instead.
 template <class Call>
 stk_status capture_graph(cudaStream_t st, Call call, void **graph_exec) {
   if (!graph_exec) return fail(STK_EINVAL, "graph_exec is NULL");
@@ -830,9 +843,12 @@ stk_status capture_graph(cudaStream_t st, Call call, void **graph_exec) {
   const cudaEvent_t save0 = g_ev_start, save1 = g_ev_stop;
   g_ev_start = g_ev_stop = nullptr;
   CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const int64_t c0 = launch_count();
   const stk_status s = call();
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(st, &graph);
+  const int64_t recorded = launch_count() - c0;
+  count_launches(-(int)recorded);
   g_ev_start = save0;
   g_ev_stop = save1;
   if (s != STK_OK) {
@@ -845,6 +861,8 @@ stk_status capture_graph(cudaStream_t st, Call call, void **graph_exec) {
   cudaGraphDestroy(graph);
   if (ei != cudaSuccess) return fail(STK_ECUDA, "cudaGraphInstantiate failed");
   *graph_exec = reinterpret_cast<void *>(exec);
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  g_graph_kernels[*graph_exec] = recorded;
   return STK_OK;
 }
 }  // namespace
@@ -918,12 +936,22 @@ stk_status stokes_graph_launch(void *graph_exec, void *stream) {
   if (!graph_exec) return fail(STK_EINVAL, "graph_exec is NULL");
   CU(cudaGraphLaunch(reinterpret_cast<cudaGraphExec_t>(graph_exec),
                      reinterpret_cast<cudaStream_t>(stream)));
-  count_launches(1);
+  int64_t k = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    const auto it = g_graph_kernels.find(graph_exec);
+    if (it != g_graph_kernels.end()) k = it->second;
+  }
+  count_launches((int)k);
   return STK_OK;
 }
 
 stk_status stokes_graph_destroy(void *graph_exec) {
   if (!graph_exec) return STK_OK;
+  {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    g_graph_kernels.erase(graph_exec);
+  }
   CU(cudaGraphExecDestroy(reinterpret_cast<cudaGraphExec_t>(graph_exec)));
   return STK_OK;
 }

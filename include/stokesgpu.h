@@ -314,6 +314,59 @@ stk_status stokes_fmm_check_to_equiv(int32_t p, double r, double mu, int32_t upw
 stk_status stokes_fmm_kernel_matrix(const double *x, int32_t nx, const double *y, int32_t ny,
                                     double mu, int32_t ncomp, double *out);
 
+/* Far field of the FMM on the GPU (Sec. 3.1, "Far evaluation"), FP64: the
+ * velocity at every point of the sources outside its leaf's U-list, through
+ * upward equivalent densities (S2M at the leaves, M2M), the interaction lists
+ * (V: M2L; W: upward densities at a leaf's points; X: sources on a box's
+ * downward check surface), downward equivalent densities (L2L) and L2T.  The
+ * near field is stokes_p2p_leaflists over the same leaves; far + near is the
+ * FMM's approximation of stokes_sldl_eval with targets = sources.
+ *
+ * The tree: nbox boxes numbered depth by depth (depth 0 = the root cube
+ * [root_lo, root_lo + root_size]^3), Morton order within a depth, so the
+ * children of box b are the boxes [child_ptr[b], child_ptr[b+1]).  A box of
+ * depth d with integer index a = anchor[b] has centre root_lo + (a + 0.5)
+ * root_size / 2^d.  Points are sorted by leaf: leaf l holds [leaf_ptr[l],
+ * leaf_ptr[l+1]) and is box leaf_box[l]; box_leaf[b] is the leaf number of box
+ * b or -1.  V, W and X are CSR lists over box numbers ([nbox + 1] pointers):
+ *   V(B): children of the same-depth neighbours of B's parent that do not
+ *         touch B (closed boxes); W(B), B a leaf: boxes below B's same-depth
+ *         neighbours that do not touch B while their parent does; X(B): the
+ *         leaves A with B in W(A).
+ * depth_ptr is a HOST array [max_depth + 2] (boxes of depth d are
+ * [depth_ptr[d], depth_ptr[d+1])); every other array is in device memory and
+ * must describe this one tree (its contents are not checked on the device).
+ *
+ * Operators: uc2e [max_depth - 1][(flux ? 4 : 3) ns][3 ns] and dc2e
+ * [max_depth - 1][3 ns][3 ns] (device, depths 2..max_depth), the
+ * check-to-equivalent operators of a box of half-width root_size / 2^(d+1)
+ * as stokes_fmm_check_to_equiv returns them (same p, mu and flux); ns is the
+ * surface count of p.  flux != 0: the upward density has a point-source
+ * strength per surface point (needed for the double layer's far field).
+ *
+ * f or phi may be NULL (not both); nrm is needed with phi.  out [n][3] =
+ * far field (accumulate != 0: out += far field).  2 <= p <= 12.  Boxes of
+ * depth < 2 have no far field; a tree of max_depth < 2 gives zero.  Launches
+ * 2 + 4 (max_depth - 1) kernels on the caller's stream; allocates nothing;
+ * workspace from stokes_fmm_far_workspace_size.  STK_EINVAL for bad sizes,
+ * NULL arrays or a depth_ptr that does not run from 0 to nbox. */
+typedef struct {
+  int32_t nbox, nleaf, max_depth;
+  const int32_t *depth_ptr;  /* HOST */
+  const int32_t *depth, *anchor, *parent, *child_ptr, *box_leaf, *leaf_box, *leaf_ptr;
+  const int32_t *v_ptr, *v_idx, *w_ptr, *w_idx, *x_ptr, *x_idx;
+  double root_lo[3];
+  double root_size;
+} stk_fmm_tree;
+stk_status stokes_fmm_far_workspace_size(int32_t p, int32_t flux, const stk_fmm_tree *tree,
+                                         size_t *bytes);
+stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double *phi,
+                               const double *nrm, const double *w, int64_t n,
+                               const stk_fmm_tree *tree, int32_t p, int32_t flux,
+                               const double *uc2e, const double *dc2e, double mu, double *out,
+                               int32_t accumulate, void *workspace, size_t workspace_bytes,
+                               void *stream);
+
 /* ------------------------------------------------- no-allocation variant
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory when they need a velocity (an application

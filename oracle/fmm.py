@@ -232,13 +232,18 @@ def _adjacent(n1, n2, maxd: int) -> bool:
 
 
 def fmm_adaptive(tree, pts, f, phi, nrm, w, p: int, mu: float = 1.0, flux: bool = True,
-                 stats: dict | None = None, lists_only: bool = False):
+                 stats: dict | None = None, lists_only: bool = False, ops: dict | None = None,
+                 near: bool = True):
     """The same method on an adaptive octree (synth.octree: leaves in Morton
     order, points sorted by leaf, U-lists of adjacent leaves).  Besides the
     interaction (V) lists, a leaf B takes the upward equivalent densities of
     its W-list at its points (descendants of its same-level neighbours that do
     not touch B but whose parent does), and a node B takes the sources of its
-    X-list (the leaves whose W-list holds B) on its downward check surface."""
+    X-list (the leaves whose W-list holds B) on its downward check surface.
+
+    ops, if given, maps a depth to its (upward, downward) check-to-equivalent
+    operators in place of the pseudo-inverses computed here; near=False leaves
+    out the U-list sum (the far field alone)."""
     pts = np.asarray(pts, dtype=np.float64)
     n = pts.shape[0]
     zeros = np.zeros((n, 3))
@@ -285,8 +290,11 @@ def fmm_adaptive(tree, pts, f, phi, nrm, w, p: int, mu: float = 1.0, flux: bool 
         return np.arange(tree.leaf_ptr[b], tree.leaf_ptr[b + 1])
 
     uc2e, dc2e = {}, {}
+    given = ops
 
     def ops(d):
+        if d not in uc2e and given is not None and d in given:
+            uc2e[d], dc2e[d] = given[d]
         if d not in uc2e:
             r = tree.root_size / (1 << d) / 2
             uc2e[d] = pinv(upward_matrix(R_OUTER * r * S, R_INNER * r * S, mu, flux))
@@ -368,7 +376,8 @@ def fmm_adaptive(tree, pts, f, phi, nrm, w, p: int, mu: float = 1.0, flux: bool 
         for a in W[nd]:
             ca, ra = geom(a)
             u[idx] += (upward_matrix(pts[idx], ca + R_INNER * ra * S, mu, flux) @ up[a]).reshape(-1, 3)
-        near = np.concatenate([leaf_points(leaves[a]) for a in
-                               tree.ulist_idx[tree.ulist_ptr[b]:tree.ulist_ptr[b + 1]]])
-        u[idx] += _sldl(pts[near], f[near], nrm[near], phi[near], w[near], pts[idx], mu)
+        if near:
+            nb = np.concatenate([leaf_points(leaves[a]) for a in
+                                 tree.ulist_idx[tree.ulist_ptr[b]:tree.ulist_ptr[b + 1]]])
+            u[idx] += _sldl(pts[nb], f[nb], nrm[nb], phi[nb], w[nb], pts[idx], mu)
     return u

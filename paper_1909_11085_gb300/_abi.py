@@ -33,6 +33,7 @@ EXPORTS = [
     "stokes_upsample_patches", "stokes_bie_matvec", "stokes_bie_workspace_size",
     "stokes_near_patch_search", "stokes_near_search_workspace_size",
     "stokes_fmm_surface", "stokes_fmm_check_to_equiv", "stokes_fmm_kernel_matrix",
+    "stokes_fmm_far_workspace_size", "stokes_fmm_far_eval",
 ]
 
 
@@ -40,6 +41,16 @@ class StkOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("near_ratio", ctypes.c_double),
                 ("accumulate", ctypes.c_int32), ("source_splits", ctypes.c_int32),
                 ("tile_config", ctypes.c_int32)]
+
+
+class StkFmmTree(ctypes.Structure):
+    """stk_fmm_tree: depth_ptr is a host array, every other array a device one."""
+    _fields_ = [("nbox", ctypes.c_int32), ("nleaf", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("depth_ptr", ctypes.c_void_p)] + [
+        (k, ctypes.c_void_p) for k in ("depth", "anchor", "parent", "child_ptr", "box_leaf",
+                                       "leaf_box", "leaf_ptr", "v_ptr", "v_idx", "w_ptr", "w_idx",
+                                       "x_ptr", "x_idx")] + [
+        ("root_lo", ctypes.c_double * 3), ("root_size", ctypes.c_double)]
 
 
 class StokesError(RuntimeError):
@@ -108,6 +119,10 @@ def lib():
             L.stokes_fmm_surface.argtypes = [i32, p, ctypes.POINTER(ctypes.c_int32)]
             L.stokes_fmm_check_to_equiv.argtypes = [i32, d, d, i32, i32, d, p]
             L.stokes_fmm_kernel_matrix.argtypes = [p, i32, p, i32, d, i32, p]
+            pt = ctypes.POINTER(StkFmmTree)
+            L.stokes_fmm_far_workspace_size.argtypes = [i32, i32, pt, psz]
+            L.stokes_fmm_far_eval.argtypes = [p, p, p, p, p, i64, pt, i32, i32, p, p, d, p, i32,
+                                              p, sz, p]
             L.stokes_graph_destroy.argtypes = [p]
             L.stokes_launch_count.restype = ctypes.c_int64
             for name in EXPORTS:

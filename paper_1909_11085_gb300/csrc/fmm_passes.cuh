@@ -1,0 +1,372 @@
+// fmm_passes.cuh -- the passes of the kernel-independent FMM's far field
+// (Sec. 3.1, "Far evaluation": the smooth quadrature at all targets at once),
+// one function per output value, so that each pass is "for every output e:
+// compute e".  No output is written by two calls, so a pass needs no atomics
+// and gives the same result in any execution order.
+//
+// The tree: boxes numbered depth by depth (depth 0 first), Morton order within
+// a depth, so the children of a box are contiguous (child_ptr) and the boxes
+// of one depth are one range (depth_ptr).  Points are sorted by leaf.  Lists
+// (CSR over box numbers):
+//   V(B): children of the same-depth neighbours of B's parent that do not
+//         touch B (M2L);
+//   W(B), B a leaf: boxes below B's same-depth neighbours that do not touch B
+//         while their parent does (their upward densities at B's points);
+//   X(B): leaves A with B in W(A) (their sources on B's downward check surface).
+// The far field starts at depth 2 (a box of depth 1 touches every other).
+//
+// Surfaces: the boundary points of a p x p x p grid on a cube of half-width
+// 1.05 r (upward equivalent, downward check) or 2.95 r (upward check,
+// downward equivalent) about a box of half-width r.  The upward equivalent
+// density has a force and, with flux, a point-source strength per point; the
+// downward one a force.  Check-to-equivalent operators per depth are inputs.
+//
+// Steps, in order:
+//   S2M    leaf sources -> upward check velocity (2.95 r);
+//   M2M    children's upward densities -> parent's upward check velocity;
+//   UC2E   upward check -> upward equivalent density, depth by depth upwards;
+//   DCHK   V-list densities (M2L) + X-list sources + parent's downward
+//          density (L2L, depth > 2) -> downward check velocity (1.05 r);
+//   DC2E   downward check -> downward equivalent density, depth by depth;
+//   L2T    downward density of the point's leaf + W-list upward densities
+//          -> velocity at every point.
+#pragma once
+
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define FMM_HD __host__ __device__ inline
+#else
+#define FMM_HD inline
+#endif
+
+// A host build with FMM_HOST_CHECKS checks every index before it is used.
+#if defined(FMM_HOST_CHECKS)
+void fmm_host_check_failed(const char *what, int64_t v, int64_t hi);
+#define FMM_CHECK(v, hi, what)                                                 \
+  do {                                                                         \
+    if ((int64_t)(v) < 0 || (int64_t)(v) >= (int64_t)(hi))                     \
+      fmm_host_check_failed(what, (int64_t)(v), (int64_t)(hi));                \
+  } while (0)
+#else
+#define FMM_CHECK(v, hi, what) \
+  do {                         \
+  } while (0)
+#endif
+
+namespace stk {
+namespace fmm {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInner = 1.05;
+constexpr double kOuter = 2.95;
+constexpr int kFirstDepth = 2;  // shallowest depth with a far field
+constexpr int kMaxTreeDepth = 21;
+
+struct Tree {
+  int32_t nbox, nleaf;
+  const int32_t *depth;      // [nbox]
+  const int32_t *anchor;     // [nbox][3] integer box index at its depth
+  const int32_t *parent;     // [nbox], -1 for the root
+  const int32_t *child_ptr;  // [nbox + 1]
+  const int32_t *leaf_box;   // [nleaf] box number of each leaf
+  const int32_t *leaf_ptr;   // [nleaf + 1] point ranges
+  const int32_t *v_ptr, *v_idx, *w_ptr, *w_idx, *x_ptr, *x_idx;
+  const int32_t *box_leaf;   // [nbox] leaf number or -1
+  double root_lo[3];
+  double root_size;
+};
+
+// Everything one pass reads and writes.
+struct Pass {
+  Tree t;
+  const double *pts, *f, *phi, *nrm, *w;  // [n][3] (w [n]); f or phi may be NULL
+  int64_t n;
+  double csl;   // 1 / (8 pi mu): single layer and the equivalent forces
+  double cdl;   // 6 / (8 pi): double layer
+  double csrc;  // 1 / (4 pi): equivalent point sources
+  int32_t ns;   // points per surface
+  int32_t nc;   // components of the upward density per point (3, or 4 with flux)
+  const double *surf;  // [ns][3] on [-1, 1]^3
+  const double *uc2e;  // [depth - 2][nc ns][3 ns]
+  const double *dc2e;  // [depth - 2][3 ns][3 ns]
+  double *chk;         // [nbox][3 ns] check velocities (upward, then downward)
+  double *up;          // [nbox][nc ns]
+  double *dn;          // [nbox][3 ns]
+  double *out;         // [n][3]
+  int32_t accumulate;
+  int32_t depth;       // depth of a per-depth pass; its boxes are [box0, box1)
+  int32_t box0, box1;
+};
+
+// Boundary points of the p^3 grid on [-1, 1]^3, i slowest, k fastest.
+FMM_HD void fill_surface(int p, double *s) {
+  int m = 0;
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j)
+      for (int k = 0; k < p; ++k) {
+        if (!(i == 0 || j == 0 || k == 0 || i == p - 1 || j == p - 1 || k == p - 1)) continue;
+        s[3 * m + 0] = -1.0 + 2.0 * i / (p - 1);
+        s[3 * m + 1] = -1.0 + 2.0 * j / (p - 1);
+        s[3 * m + 2] = -1.0 + 2.0 * k / (p - 1);
+        ++m;
+      }
+}
+
+FMM_HD int surface_count(int p) { return p * p * p - (p - 2) * (p - 2) * (p - 2); }
+
+// Centre and half-width of box b (depth d).
+FMM_HD void box_geom(const Tree &t, int32_t b, int32_t d, double c[3], double &r) {
+  const double size = t.root_size / (double)(1 << d);
+  for (int q = 0; q < 3; ++q) c[q] = t.root_lo[q] + ((double)t.anchor[3 * b + q] + 0.5) * size;
+  r = size / 2;
+}
+
+FMM_HD void surface_point(const Pass &P, const double c[3], double rad, int k, double x[3]) {
+  for (int q = 0; q < 3; ++q) x[q] = c[q] + rad * P.surf[3 * k + q];
+}
+
+// Adds the single and double layer of the points [i0, i1) at x.
+FMM_HD void add_sources(const Pass &P, const double x[3], int64_t i0, int64_t i1, double u[3]) {
+  FMM_CHECK(i0, P.n + 1, "point range start");
+  FMM_CHECK(i1, P.n + 1, "point range end");
+  double us[3] = {0.0, 0.0, 0.0}, ud[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = i0; i < i1; ++i) {
+    const double *y = P.pts + 3 * i;
+    const double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 > 0.0)) continue;
+    const double r = sqrt(r2), ir = 1.0 / r;
+    if (P.f) {
+      const double q[3] = {P.w[i] * P.f[3 * i], P.w[i] * P.f[3 * i + 1], P.w[i] * P.f[3 * i + 2]};
+      const double ir3 = ir / r2, dq = (d[0] * q[0] + d[1] * q[1] + d[2] * q[2]) * ir3;
+      for (int a = 0; a < 3; ++a) us[a] += q[a] * ir + d[a] * dq;
+    }
+    if (P.phi) {
+      const double *nn = P.nrm + 3 * i;
+      const double s[3] = {P.w[i] * P.phi[3 * i], P.w[i] * P.phi[3 * i + 1],
+                           P.w[i] * P.phi[3 * i + 2]};
+      const double c = (d[0] * s[0] + d[1] * s[1] + d[2] * s[2]) *
+                       (d[0] * nn[0] + d[1] * nn[1] + d[2] * nn[2]) / (r2 * r2 * r);
+      for (int a = 0; a < 3; ++a) ud[a] += d[a] * c;
+    }
+  }
+  for (int a = 0; a < 3; ++a) u[a] += P.csl * us[a] + P.cdl * ud[a];
+}
+
+// Adds at x the field of an equivalent density e on the surface of half-width
+// rad about c: per point a force (Stokeslet) and, for nc = 4, a source.
+FMM_HD void add_equivalent(const Pass &P, const double x[3], const double c[3], double rad,
+                           const double *e, int nc, double u[3]) {
+  double uf[3] = {0.0, 0.0, 0.0}, uq[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < P.ns; ++j) {
+    double y[3];
+    surface_point(P, c, rad, j, y);
+    const double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 > 0.0)) continue;
+    const double ri = 1.0 / sqrt(r2), ri3 = ri * ri * ri;
+    const double *ej = e + (size_t)nc * j;
+    const double df = (d[0] * ej[0] + d[1] * ej[1] + d[2] * ej[2]) * ri3;
+    for (int a = 0; a < 3; ++a) uf[a] += ej[a] * ri + d[a] * df;
+    if (nc == 4)
+      for (int a = 0; a < 3; ++a) uq[a] += d[a] * ej[3] * ri3;
+  }
+  for (int a = 0; a < 3; ++a) u[a] += P.csl * uf[a] + P.csrc * uq[a];
+}
+
+FMM_HD void store3(double *dst, const double u[3]) {
+  dst[0] = u[0];
+  dst[1] = u[1];
+  dst[2] = u[2];
+}
+
+// S2M: e = leaf * ns + k.
+struct S2M {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int64_t l = e / P.ns;
+    const int k = (int)(e % P.ns);
+    FMM_CHECK(l, P.t.nleaf, "leaf");
+    const int32_t b = P.t.leaf_box[l];
+    FMM_CHECK(b, P.t.nbox, "leaf box");
+    const int32_t d = P.t.depth[b];
+    if (d < kFirstDepth) return;
+    double c[3], r, x[3], u[3] = {0.0, 0.0, 0.0};
+    box_geom(P.t, b, d, c, r);
+    surface_point(P, c, kOuter * r, k, x);
+    add_sources(P, x, P.t.leaf_ptr[l], P.t.leaf_ptr[l + 1], u);
+    store3(P.chk + (size_t)b * 3 * P.ns + 3 * k, u);
+  }
+};
+
+// M2M: e = (box - box0) * ns + k over the boxes of one depth; leaves skip.
+struct M2M {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int32_t b = P.box0 + (int32_t)(e / P.ns);
+    const int k = (int)(e % P.ns);
+    FMM_CHECK(b, P.box1, "m2m box");
+    const int32_t c0 = P.t.child_ptr[b], c1 = P.t.child_ptr[b + 1];
+    if (c0 >= c1) return;
+    double c[3], r, x[3], u[3] = {0.0, 0.0, 0.0};
+    box_geom(P.t, b, P.depth, c, r);
+    surface_point(P, c, kOuter * r, k, x);
+    for (int32_t ch = c0; ch < c1; ++ch) {
+      FMM_CHECK(ch, P.t.nbox, "child");
+      double cc[3], rc;
+      box_geom(P.t, ch, P.depth + 1, cc, rc);
+      add_equivalent(P, x, cc, kInner * rc, P.up + (size_t)ch * P.nc * P.ns, P.nc, u);
+    }
+    store3(P.chk + (size_t)b * 3 * P.ns + 3 * k, u);
+  }
+};
+
+// Row i of a check-to-equivalent operator applied to box b's check velocity.
+FMM_HD double apply_row(const double *M, int64_t i, const double *chk, int cols) {
+  const double *row = M + (size_t)i * cols;
+  double s = 0.0;
+  for (int j = 0; j < cols; ++j) s += row[j] * chk[j];
+  return s;
+}
+
+// UC2E: e = (box - box0) * nc ns + i.
+struct UC2E {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int64_t rows = (int64_t)P.nc * P.ns;
+    const int32_t b = P.box0 + (int32_t)(e / rows);
+    const int64_t i = e % rows;
+    FMM_CHECK(b, P.box1, "uc2e box");
+    const double *M = P.uc2e + (size_t)(P.depth - kFirstDepth) * rows * 3 * P.ns;
+    P.up[(size_t)b * rows + i] = apply_row(M, i, P.chk + (size_t)b * 3 * P.ns, 3 * P.ns);
+  }
+};
+
+// DCHK: e = (box - box0) * ns + k over the boxes of one depth >= 2.
+struct DCHK {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int32_t b = P.box0 + (int32_t)(e / P.ns);
+    const int k = (int)(e % P.ns);
+    FMM_CHECK(b, P.box1, "dchk box");
+    double c[3], r, x[3], u[3] = {0.0, 0.0, 0.0};
+    box_geom(P.t, b, P.depth, c, r);
+    surface_point(P, c, kInner * r, k, x);
+    for (int32_t v = P.t.v_ptr[b]; v < P.t.v_ptr[b + 1]; ++v) {  // M2L
+      const int32_t a = P.t.v_idx[v];
+      FMM_CHECK(a, P.t.nbox, "V entry");
+      double ca[3], ra;
+      box_geom(P.t, a, P.t.depth[a], ca, ra);
+      add_equivalent(P, x, ca, kInner * ra, P.up + (size_t)a * P.nc * P.ns, P.nc, u);
+    }
+    for (int32_t v = P.t.x_ptr[b]; v < P.t.x_ptr[b + 1]; ++v) {  // X-list sources
+      const int32_t a = P.t.x_idx[v];
+      FMM_CHECK(a, P.t.nbox, "X entry");
+      const int32_t l = P.t.box_leaf[a];
+      FMM_CHECK(l, P.t.nleaf, "X leaf");
+      if (l < 0) continue;  // not a leaf: not an X-list entry
+      add_sources(P, x, P.t.leaf_ptr[l], P.t.leaf_ptr[l + 1], u);
+    }
+    if (P.depth > kFirstDepth) {  // L2L
+      const int32_t pb = P.t.parent[b];
+      FMM_CHECK(pb, P.t.nbox, "parent");
+      double cp[3], rp;
+      box_geom(P.t, pb, P.depth - 1, cp, rp);
+      add_equivalent(P, x, cp, kOuter * rp, P.dn + (size_t)pb * 3 * P.ns, 3, u);
+    }
+    store3(P.chk + (size_t)b * 3 * P.ns + 3 * k, u);
+  }
+};
+
+// DC2E: e = (box - box0) * 3 ns + i.
+struct DC2E {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int64_t rows = 3 * (int64_t)P.ns;
+    const int32_t b = P.box0 + (int32_t)(e / rows);
+    const int64_t i = e % rows;
+    FMM_CHECK(b, P.box1, "dc2e box");
+    const double *M = P.dc2e + (size_t)(P.depth - kFirstDepth) * rows * rows;
+    P.dn[(size_t)b * rows + i] = apply_row(M, i, P.chk + (size_t)b * rows, (int)rows);
+  }
+};
+
+// L2T + W-list: e = point (leaf order).
+struct L2T {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    int32_t lo = 0, hi = P.t.nleaf;  // the last leaf whose range starts at or before e
+    while (hi - lo > 1) {
+      const int32_t mid = lo + (hi - lo) / 2;
+      if (P.t.leaf_ptr[mid] <= e) lo = mid;
+      else hi = mid;
+    }
+    const int32_t b = P.t.leaf_box[lo];
+    FMM_CHECK(b, P.t.nbox, "point's leaf box");
+    const int32_t d = P.t.depth[b];
+    const double x[3] = {P.pts[3 * e], P.pts[3 * e + 1], P.pts[3 * e + 2]};
+    double u[3] = {0.0, 0.0, 0.0};
+    if (d >= kFirstDepth) {
+      double c[3], r;
+      box_geom(P.t, b, d, c, r);
+      add_equivalent(P, x, c, kOuter * r, P.dn + (size_t)b * 3 * P.ns, 3, u);
+    }
+    for (int32_t v = P.t.w_ptr[b]; v < P.t.w_ptr[b + 1]; ++v) {
+      const int32_t a = P.t.w_idx[v];
+      FMM_CHECK(a, P.t.nbox, "W entry");
+      double ca[3], ra;
+      box_geom(P.t, a, P.t.depth[a], ca, ra);
+      add_equivalent(P, x, ca, kInner * ra, P.up + (size_t)a * P.nc * P.ns, P.nc, u);
+    }
+    double *o = P.out + 3 * e;
+    for (int a = 0; a < 3; ++a) o[a] = (P.accumulate ? o[a] : 0.0) + u[a];
+  }
+};
+
+// Workspace: surface points, then per-box check, upward and downward arrays.
+struct Layout {
+  size_t surf, chk, up, dn, total;
+};
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+inline Layout layout(int64_t nbox, int ns, int nc) {
+  Layout L;
+  size_t o = 0;
+  L.surf = o;
+  o += align256(sizeof(double) * 3 * (size_t)ns);
+  L.chk = o;
+  o += align256(sizeof(double) * 3 * (size_t)ns * (size_t)nbox);
+  L.up = o;
+  o += align256(sizeof(double) * (size_t)nc * ns * (size_t)nbox);
+  L.dn = o;
+  o += align256(sizeof(double) * 3 * (size_t)ns * (size_t)nbox);
+  L.total = o + 256;  // slack for aligning the caller's base
+  return L;
+}
+
+// The pass sequence; Exec::run<F>(P, count) calls F on every output of a pass
+// (a kernel launch on the GPU).  depth_ptr is the host copy of the depth
+// ranges of the boxes.
+template <class Exec>
+void far_field(Exec &ex, Pass P, const int32_t *depth_ptr, int32_t max_depth) {
+  const int64_t ns = P.ns;
+  ex.template run<S2M>(P, (int64_t)P.t.nleaf * ns);
+  for (int32_t d = max_depth; d >= kFirstDepth; --d) {
+    P.depth = d;
+    P.box0 = depth_ptr[d];
+    P.box1 = depth_ptr[d + 1];
+    const int64_t nb = P.box1 - P.box0;
+    if (d < max_depth) ex.template run<M2M>(P, nb * ns);
+    ex.template run<UC2E>(P, nb * P.nc * ns);
+  }
+  for (int32_t d = kFirstDepth; d <= max_depth; ++d) {
+    P.depth = d;
+    P.box0 = depth_ptr[d];
+    P.box1 = depth_ptr[d + 1];
+    const int64_t nb = P.box1 - P.box0;
+    ex.template run<DCHK>(P, nb * ns);
+    ex.template run<DC2E>(P, nb * 3 * ns);
+  }
+  ex.template run<L2T>(P, P.n);
+}
+
+}  // namespace fmm
+}  // namespace stk

@@ -485,3 +485,159 @@ def near_patch_search(nodes, npatch, trg, d_eps, q=10):
             A.ptr(uv), A.ptr(y), A.ptr(n), A.ptr(dist), A.ptr(ws), ws.numel(),
             A.stream_ptr(dev)))
     return patch, uv, y, n, dist
+
+
+_FMM_DEVICE_KEYS = ("depth", "anchor", "parent", "child_ptr", "box_leaf", "leaf_box", "leaf_ptr",
+                    "v_ptr", "v_idx", "w_ptr", "w_idx", "x_ptr", "x_idx")
+
+
+def fmm_tree_arrays(depth, anchor, parent, box_leaf, leaf_ptr, v_ptr, v_idx, w_ptr, w_idx, x_ptr,
+                    x_idx, root_lo, root_size):
+    """Host arrays of the far field's tree (stk_fmm_tree, include/stokesgpu.h)
+    from each box's depth, integer anchor, parent and leaf number, the leaves'
+    point ranges and the V, W and X lists.  Derives depth_ptr, child_ptr and
+    leaf_box, and checks the order the passes rely on: boxes depth by depth
+    with the root first, children contiguous in their parents' order."""
+    import numpy as np
+    depth = np.asarray(depth, dtype=np.int64)
+    parent = np.asarray(parent, dtype=np.int64)
+    box_leaf = np.asarray(box_leaf, dtype=np.int64)
+    leaf_ptr = np.asarray(leaf_ptr, dtype=np.int64)
+    M = depth.size
+    if M == 0 or depth[0] != 0 or parent[0] != -1 or (M > 1 and depth[1] == 0):
+        raise ValueError("box 0 must be the root, the only box of depth 0")
+    if np.any(np.diff(depth) < 0):
+        raise ValueError("boxes must be numbered depth by depth")
+    if M > 1:
+        pc = parent[1:]
+        if np.any(pc < 0) or np.any(pc >= M) or np.any(depth[pc] != depth[1:] - 1):
+            raise ValueError("every box but the root needs a parent one depth up")
+        if np.any(np.diff(pc) < 0):
+            raise ValueError("children must be numbered in their parents' order")
+    max_depth = int(depth.max())
+    if max_depth > 21:
+        raise ValueError("the tree is deeper than 21")
+    depth_ptr = np.searchsorted(depth, np.arange(max_depth + 2), side="left")
+    counts = np.bincount(parent[1:], minlength=M) if M > 1 else np.zeros(M, dtype=np.int64)
+    child_ptr = np.concatenate([[1], 1 + np.cumsum(counts)])
+    nleaf = leaf_ptr.size - 1
+    is_leaf = box_leaf >= 0
+    if nleaf < 1 or is_leaf.sum() != nleaf or np.any(box_leaf >= nleaf) or \
+            np.unique(box_leaf[is_leaf]).size != nleaf:
+        raise ValueError("box_leaf must number every leaf exactly once")
+    if np.any(counts[is_leaf] != 0):
+        raise ValueError("a leaf box has children")
+    leaf_box = np.empty(nleaf, dtype=np.int64)
+    leaf_box[box_leaf[is_leaf]] = np.nonzero(is_leaf)[0]
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    t = {"depth_ptr": i32(depth_ptr), "depth": i32(depth), "anchor": i32(np.asarray(anchor)),
+         "parent": i32(parent), "child_ptr": i32(child_ptr), "box_leaf": i32(box_leaf),
+         "leaf_box": i32(leaf_box), "leaf_ptr": i32(leaf_ptr), "v_ptr": i32(v_ptr),
+         "v_idx": i32(v_idx), "w_ptr": i32(w_ptr), "w_idx": i32(w_idx), "x_ptr": i32(x_ptr),
+         "x_idx": i32(x_idx), "root_lo": np.asarray(root_lo, dtype=np.float64).reshape(3).copy(),
+         "root_size": float(root_size), "max_depth": max_depth}
+    for k in ("v", "w", "x"):
+        ptr, idx = t[k + "_ptr"], t[k + "_idx"]
+        if ptr.size != M + 1 or ptr[0] != 0 or np.any(np.diff(ptr) < 0) or ptr[-1] != idx.size \
+                or np.any(idx < 0) or np.any(idx >= M):
+            raise ValueError(f"{k.upper()} list is not a CSR list over the boxes")
+    if np.any(box_leaf[t["x_idx"]] < 0):
+        raise ValueError("X lists hold leaves only")
+    if leaf_ptr[0] != 0 or np.any(np.diff(leaf_ptr) < 0):
+        raise ValueError("leaf_ptr must be non-decreasing from 0")
+    if t["anchor"].shape != (M, 3):
+        raise ValueError("anchor must have shape [nbox, 3]")
+    return t
+
+
+def fmm_operators(p, root_size, max_depth, mu=1.0, flux=True, rcond=1e-13):
+    """Check-to-equivalent operators of depths 2..max_depth (host, FP64):
+    uc2e [max_depth - 1][(flux ? 4 : 3) ns][3 ns], dc2e [max_depth - 1][3 ns][3 ns].
+    The Stokeslet is homogeneous of degree -1, so a Stokeslet-only operator of a
+    box of half-width r is r times that of half-width 1 (the cut-off is relative);
+    with point sources the upward operator is computed per depth."""
+    import numpy as np
+    ns = p ** 3 - (p - 2) ** 3
+    nc = 4 if flux else 3
+    D = max(int(max_depth) - 1, 0)
+    uc = np.zeros((D, nc * ns, 3 * ns))
+    dc = np.zeros((D, 3 * ns, 3 * ns))
+    if D == 0:
+        return uc, dc
+    L = A.lib()
+
+    def c2e(r, upward, fl):
+        out = np.zeros(((4 if (upward and fl) else 3) * ns, 3 * ns))
+        A.check(L.stokes_fmm_check_to_equiv(int(p), float(r), float(mu), int(upward), int(fl),
+                                            float(rcond), out.ctypes.data))
+        return out
+
+    dc1 = c2e(1.0, False, False)
+    uc1 = None if flux else c2e(1.0, True, False)
+    for i, d in enumerate(range(2, int(max_depth) + 1)):
+        r = float(root_size) / (1 << d) / 2
+        dc[i] = r * dc1
+        uc[i] = c2e(r, True, True) if flux else r * uc1
+    return uc, dc
+
+
+class FmmFarPlan:
+    """Far field of the FMM (stokes_fmm_far_eval) on a fixed tree: device
+    copies of the tree arrays (from fmm_tree_arrays), the per-depth operators
+    (fmm_operators unless given) and a workspace.  Calls take the densities of
+    the leaf-sorted points and return the far field [n, 3]; adding the U-list
+    P2P sum over the same leaves gives the FMM velocity."""
+
+    def __init__(self, tree, p=4, mu=1.0, flux=True, uc2e=None, dc2e=None, rcond=1e-13,
+                 device=None):
+        import numpy as np
+        self.device = device or torch.device("cuda")
+        self.p, self.mu, self.flux = int(p), float(mu), bool(flux)
+        self.depth_ptr = np.ascontiguousarray(tree["depth_ptr"], dtype=np.int32)
+        self._arrays = {k: torch.as_tensor(np.asarray(tree[k], dtype=np.int32)).to(
+            self.device).contiguous() for k in _FMM_DEVICE_KEYS}
+        self.n = int(tree["leaf_ptr"][-1])
+        if uc2e is None or dc2e is None:
+            uc2e, dc2e = fmm_operators(self.p, tree["root_size"], tree["max_depth"], self.mu,
+                                       self.flux, rcond)
+        ns, nc, D = self.p ** 3 - (self.p - 2) ** 3, 4 if self.flux else 3, max(
+            int(tree["max_depth"]) - 1, 0)
+        uc2e, dc2e = np.asarray(uc2e, dtype=np.float64), np.asarray(dc2e, dtype=np.float64)
+        if D and (uc2e.shape != (D, nc * ns, 3 * ns) or dc2e.shape != (D, 3 * ns, 3 * ns)):
+            raise ValueError(f"operators must be [{D}, {nc * ns}, {3 * ns}] and "
+                             f"[{D}, {3 * ns}, {3 * ns}] for p = {self.p}, flux = {self.flux}")
+        self.uc2e = torch.as_tensor(uc2e).to(self.device).contiguous()
+        self.dc2e = torch.as_tensor(dc2e).to(self.device).contiguous()
+        t = A.StkFmmTree()
+        t.nbox = int(tree["depth"].size)
+        t.nleaf = int(tree["leaf_box"].size)
+        t.max_depth = int(tree["max_depth"])
+        t.depth_ptr = self.depth_ptr.ctypes.data
+        for k in _FMM_DEVICE_KEYS:
+            setattr(t, k, self._arrays[k].data_ptr() if self._arrays[k].numel() else None)
+        for q in range(3):
+            t.root_lo[q] = float(tree["root_lo"][q])
+        t.root_size = float(tree["root_size"])
+        self.tree = t
+        nb = ctypes.c_size_t(0)
+        A.check(A.lib().stokes_fmm_far_workspace_size(self.p, int(self.flux), ctypes.byref(t),
+                                                      ctypes.byref(nb)))
+        self.ws = A.workspace(nb.value, self.device)
+
+    def __call__(self, pts, f=None, phi=None, nrm=None, w=None, out=None, accumulate=False):
+        n = self.n
+        pts = A.vec3(pts, "pts", n)
+        f, phi, nrm = A.vec3(f, "f", n), A.vec3(phi, "phi", n), A.vec3(nrm, "nrm", n)
+        w = A.vec1(w, "w", n)
+        if out is None:
+            out = torch.zeros((n, 3), dtype=torch.float64, device=self.device)
+        else:
+            out = A.vec3(out, "out", n)
+        ops = self.uc2e.numel() > 0
+        with torch.cuda.device(self.device):
+            A.check(A.lib().stokes_fmm_far_eval(
+                A.ptr(pts), A.ptr(f), A.ptr(phi), A.ptr(nrm), A.ptr(w), n, ctypes.byref(self.tree),
+                self.p, int(self.flux), A.ptr(self.uc2e) if ops else None,
+                A.ptr(self.dc2e) if ops else None, self.mu, A.ptr(out), int(bool(accumulate)),
+                A.ptr(self.ws), self.ws.numel(), A.stream_ptr(self.device)))
+        return out

@@ -124,3 +124,49 @@ def test_patch_surface_entry_points_validated_on_host(L):
                                       None, 0, None) == A.STK_OK
     assert L.stokes_near_patch_search(None, 4, 10, None, 5, -1.0, None, None, None, None, None,
                                       None, 0, None) == A.STK_EINVAL
+
+
+def test_fmm_far_entry_points_validated_on_host(L):
+    """The far field's size query and its argument checks (tree shape, p,
+    viscosity, operators, workspace) run on the host and fail before any
+    device call; an empty point set is a no-op."""
+    import numpy as np
+    dptr = np.array([0, 1, 9], dtype=np.int32)  # a root and 8 children
+    t = A.StkFmmTree()
+    t.nbox, t.nleaf, t.max_depth = 9, 8, 1
+    t.depth_ptr = dptr.ctypes.data
+    for k in ("depth", "anchor", "parent", "child_ptr", "box_leaf", "leaf_box", "leaf_ptr",
+              "v_ptr", "w_ptr", "x_ptr"):
+        setattr(t, k, 16)  # never dereferenced on the host
+    t.root_size = 1.0
+    nb = ctypes.c_size_t(0)
+    assert L.stokes_fmm_far_workspace_size(4, 1, ctypes.byref(t), ctypes.byref(nb)) == A.STK_OK
+    ns = 4 ** 3 - 2 ** 3
+    assert nb.value >= 8 * (3 * ns + 9 * (3 + 4 + 3) * ns)
+    assert L.stokes_fmm_far_workspace_size(13, 1, ctypes.byref(t), ctypes.byref(nb)) == A.STK_EINVAL
+    assert L.stokes_fmm_far_workspace_size(4, 1, None, ctypes.byref(nb)) == A.STK_EINVAL
+    bad = np.array([0, 2, 9], dtype=np.int32)
+    t.depth_ptr = bad.ctypes.data
+    t.max_depth = 2  # depth_ptr then ends at index 3, which is not nbox
+    assert L.stokes_fmm_far_workspace_size(4, 1, ctypes.byref(t), ctypes.byref(nb)) == A.STK_EINVAL
+    t.depth_ptr, t.max_depth = dptr.ctypes.data, 1
+    t.root_size = float("nan")
+    assert L.stokes_fmm_far_workspace_size(4, 1, ctypes.byref(t), ctypes.byref(nb)) == A.STK_EINVAL
+    t.root_size = 1.0
+    ws, x = ctypes.c_void_p(4096), ctypes.c_void_p(4096)
+
+    def call(n=10, f=x, phi=None, nrm=None, mu=1.0, uc=None, dc=None, wsb=0, p=4):
+        return L.stokes_fmm_far_eval(x, f, phi, nrm, x, n, ctypes.byref(t), p, 1, uc, dc, mu, x, 0,
+                                     ws, wsb, None)
+
+    assert call(n=0) == A.STK_OK
+    assert call(n=-1) == A.STK_EINVAL
+    assert call(f=None) == A.STK_EINVAL  # neither layer
+    assert call(phi=x) == A.STK_EINVAL  # phi without normals
+    assert call(mu=0.0) == A.STK_EINVAL
+    assert call(p=1) == A.STK_EINVAL
+    assert call(wsb=16) == A.STK_ENOMEM
+    keep = np.array([0, 1, 2, 9], dtype=np.int32)
+    t.max_depth, t.depth_ptr = 2, keep.ctypes.data
+    assert call(wsb=1 << 30) == A.STK_EINVAL  # a far field without operators
+    assert b"uc2e" in L.stokes_last_error()

@@ -1,0 +1,142 @@
+"""The GPU far field's passes (paper_1909_11085_gb300/csrc/fmm_passes.cuh),
+built for the host by tests/fmm_harness with every index checked, against the
+FMM oracle's far field (Sec. 3.1, "Far evaluation") on an adaptive octree of
+the near-field workload's kind; and the host set-up of the tree arrays and
+operators.  No GPU is needed: the per-output functions and the pass sequence
+are the ones the kernels run."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import fmm as F
+from paper_1909_11085_gb300 import ops
+from synth import octree as O
+from synth import workloads as W
+from tests import fmm_harness as H
+
+
+@pytest.fixture(scope="module")
+def case():
+    oracle.build()
+    wl = W.p2p_workload(ncell=6, radius=8.0, n_wall_patch=6, max_leaf=32)
+    fl = O.far_lists(wl.tree)
+    t = ops.fmm_tree_arrays(fl.depth, fl.anchor, fl.parent, fl.leaf, wl.tree.leaf_ptr, fl.v_ptr,
+                            fl.v_idx, fl.w_ptr, fl.w_idx, fl.x_ptr, fl.x_idx, wl.tree.root_lo,
+                            wl.tree.root_size)
+    return wl, fl, t
+
+
+def oracle_operators(wl, t, p, flux):
+    """The oracle's own pseudo-inverses per depth, as a dict and as the stacked
+    arrays the passes take."""
+    S = F.cube_surface(p)
+    by_depth = {}
+    for d in range(2, t["max_depth"] + 1):
+        r = wl.tree.root_size / (1 << d) / 2
+        by_depth[d] = (F.pinv(F.upward_matrix(F.R_OUTER * r * S, F.R_INNER * r * S, wl.mu, flux)),
+                       F.pinv(F.stokeslet_matrix(F.R_INNER * r * S, F.R_OUTER * r * S, wl.mu)))
+    U = np.stack([by_depth[d][0] for d in sorted(by_depth)])
+    D = np.stack([by_depth[d][1] for d in sorted(by_depth)])
+    return by_depth, U, D
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_tree_arrays(case):
+    """Children are the boxes [child_ptr[b], child_ptr[b+1]) and have parent b;
+    leaf_box inverts box_leaf; depth_ptr brackets each depth."""
+    wl, fl, t = case
+    M = t["depth"].size
+    for b in range(M):
+        kids = np.nonzero(t["parent"] == b)[0]
+        assert list(range(t["child_ptr"][b], t["child_ptr"][b + 1])) == list(kids)
+    assert np.all(t["box_leaf"][t["leaf_box"]] == np.arange(t["leaf_box"].size))
+    for d in range(t["max_depth"] + 1):
+        lo, hi = t["depth_ptr"][d], t["depth_ptr"][d + 1]
+        assert np.all(t["depth"][lo:hi] == d)
+    assert t["depth_ptr"][-1] == M and t["max_depth"] >= 3
+
+
+def test_tree_arrays_reject_a_box_order_the_passes_cannot_use(case):
+    wl, fl, t = case
+    args = [fl.depth, fl.anchor, fl.parent, fl.leaf, wl.tree.leaf_ptr, fl.v_ptr, fl.v_idx,
+            fl.w_ptr, fl.w_idx, fl.x_ptr, fl.x_idx, wl.tree.root_lo, wl.tree.root_size]
+    bad = list(args)
+    bad[2] = fl.parent.copy()
+    i = int(np.nonzero(fl.depth == 2)[0][0])
+    j = int(np.nonzero(fl.depth == 3)[0][-1])
+    bad[2][j] = fl.parent[i]  # a depth-3 box whose parent is at depth 1
+    with pytest.raises(ValueError):
+        ops.fmm_tree_arrays(*bad)
+    bad = list(args)
+    bad[3] = fl.leaf.copy()
+    bad[3][bad[3] >= 0] = 0  # every leaf numbered 0
+    with pytest.raises(ValueError):
+        ops.fmm_tree_arrays(*bad)
+    bad = list(args)
+    bad[6] = fl.v_idx.copy()
+    bad[6][0] = fl.depth.size  # a V entry past the last box
+    with pytest.raises(ValueError):
+        ops.fmm_tree_arrays(*bad)
+
+
+@pytest.mark.parametrize("flux,kinds", [(True, "sldl"), (False, "sl"), (True, "dl")])
+def test_host_passes_match_the_oracle_far_field(case, flux, kinds):
+    """Same operators on both sides: the passes reproduce the oracle's far
+    field (upward, V/W/X lists, downward, L2T) up to rounding; the Stokeslet-only
+    upward density (flux off) serves the single layer alone."""
+    wl, fl, t = case
+    p = 4
+    by_depth, U, D = oracle_operators(wl, t, p, flux)
+    f = wl.f if "sl" in kinds else None
+    phi = wl.phi if kinds in ("sldl", "dl") else None
+    far, npass = H.far_eval(wl.pts, f, phi, wl.nrm, wl.w, t, p, U, D, wl.mu, flux)
+    ref = F.fmm_adaptive(wl.tree, wl.pts, f, phi, wl.nrm, wl.w, p, wl.mu, flux, ops=by_depth,
+                         near=False)
+    assert npass == 2 + 4 * (t["max_depth"] - 1) - 1  # the deepest depth has no M2M
+    assert _rel(far, ref) <= 1e-10, _rel(far, ref)
+    # accumulate adds to what out holds
+    base = np.full_like(far, 0.25)
+    acc, _ = H.far_eval(wl.pts, f, phi, wl.nrm, wl.w, t, p, U, D, wl.mu, flux, out=base.copy(),
+                        accumulate=True)
+    np.testing.assert_allclose(acc, base + far, rtol=0, atol=1e-15)
+
+
+def test_library_operators_give_the_same_fmm(case):
+    """With the library's operators (one-sided Jacobi pseudo-inverses; the
+    downward one scaled by r from half-width 1) the far field stays within
+    1e-10 of the oracle's at p = 4, and far field + U-list sum approximates
+    the direct sum as the oracle's FMM does."""
+    wl, fl, t = case
+    p = 4
+    U, D = ops.fmm_operators(p, t["root_size"], t["max_depth"], wl.mu, True)
+    far, _ = H.far_eval(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, t, p, U, D, wl.mu, True)
+    ref = F.fmm_adaptive(wl.tree, wl.pts, wl.f, wl.phi, wl.nrm, wl.w, p, wl.mu, True, near=False)
+    assert _rel(far, ref) <= 1e-10, _rel(far, ref)
+    near = oracle.p2p(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, wl.tree.leaf_ptr, wl.tree.ulist_ptr,
+                      wl.tree.ulist_idx, 3, wl.mu)
+    direct = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts, wl.mu)
+    assert _rel(far + near, direct) <= 5e-3
+
+
+def test_shallow_tree_has_no_far_field():
+    """A tree of depth < 2 (every leaf touches every other): zero, or out unchanged."""
+    oracle.build()
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(0, 1, (300, 3))
+    tree = O.build_octree(pts, max_leaf=64)
+    fl = O.far_lists(tree)
+    assert int(fl.depth.max()) <= 1
+    t = ops.fmm_tree_arrays(fl.depth, fl.anchor, fl.parent, fl.leaf, tree.leaf_ptr, fl.v_ptr,
+                            fl.v_idx, fl.w_ptr, fl.w_idx, fl.x_ptr, fl.x_idx, tree.root_lo,
+                            tree.root_size)
+    sp = pts[tree.perm]
+    f = rng.normal(size=(300, 3))
+    w = np.full(300, 1.0 / 300)
+    far, npass = H.far_eval(sp, f, None, None, w, t, 4, np.zeros((0, 1)), np.zeros((0, 1)))
+    assert npass == 2 and np.all(far == 0.0)
+    acc, _ = H.far_eval(sp, f, None, None, w, t, 4, np.zeros((0, 1)), np.zeros((0, 1)),
+                        out=np.ones((300, 3)), accumulate=True)
+    assert np.all(acc == 1.0)

@@ -1,0 +1,95 @@
+"""GPU far field of the FMM (stokes_fmm_far_eval, Sec. 3.1 "Far evaluation")
+against the FMM oracle's far field on an adaptive octree of the near-field
+workload's kind (cells and wall patches, leaves at several depths, non-empty
+V, W and X lists), with the oracle's operators on both sides; and far field +
+the GPU U-list sum against the direct sum."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import fmm as F
+from synth import octree as O
+from synth import workloads as W
+from tests._util import cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1909_11085_gb300 import build
+    build.build()
+    oracle.build()
+    import paper_1909_11085_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def case(lib):
+    from paper_1909_11085_gb300 import ops
+    wl = W.p2p_workload(ncell=6, radius=8.0, n_wall_patch=6, max_leaf=32)
+    fl = O.far_lists(wl.tree)
+    t = ops.fmm_tree_arrays(fl.depth, fl.anchor, fl.parent, fl.leaf, wl.tree.leaf_ptr, fl.v_ptr,
+                            fl.v_idx, fl.w_ptr, fl.w_idx, fl.x_ptr, fl.x_idx, wl.tree.root_lo,
+                            wl.tree.root_size)
+    return wl, t
+
+
+def _oracle_ops(wl, t, p, flux):
+    S = F.cube_surface(p)
+    by_depth = {}
+    for d in range(2, t["max_depth"] + 1):
+        r = wl.tree.root_size / (1 << d) / 2
+        by_depth[d] = (F.pinv(F.upward_matrix(F.R_OUTER * r * S, F.R_INNER * r * S, wl.mu, flux)),
+                       F.pinv(F.stokeslet_matrix(F.R_INNER * r * S, F.R_OUTER * r * S, wl.mu)))
+    return by_depth
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("flux,kinds", [(True, "sldl"), (False, "sl")])
+def test_far_field_matches_the_oracle(lib, case, flux, kinds):
+    import paper_1909_11085_gb300._abi as A
+    from paper_1909_11085_gb300 import ops
+    wl, t = case
+    p = 4
+    by_depth = _oracle_ops(wl, t, p, flux)
+    U = np.stack([by_depth[d][0] for d in sorted(by_depth)])
+    D = np.stack([by_depth[d][1] for d in sorted(by_depth)])
+    plan = ops.FmmFarPlan(t, p=p, mu=wl.mu, flux=flux, uc2e=U, dc2e=D)
+    pts, f, phi, nrm, w = cuda(wl.pts, wl.f, wl.phi, wl.nrm, wl.w)
+    if kinds == "sl":
+        phi = nrm = None
+    L = A.lib()
+    c0 = L.stokes_launch_count()
+    far = plan(pts, f, phi, nrm, w).cpu().numpy()
+    launches = L.stokes_launch_count() - c0
+    ref = F.fmm_adaptive(wl.tree, wl.pts, wl.f, None if kinds == "sl" else wl.phi, wl.nrm, wl.w,
+                         p, wl.mu, flux, ops=by_depth, near=False)
+    assert _rel(far, ref) <= 1e-10, _rel(far, ref)
+    assert launches == 1 + 2 + 4 * (t["max_depth"] - 1) - 1
+    # accumulate
+    import torch
+    base = torch.full((wl.pts.shape[0], 3), 0.5, dtype=torch.float64, device="cuda")
+    acc = plan(pts, f, phi, nrm, w, out=base.clone(), accumulate=True).cpu().numpy()
+    np.testing.assert_allclose(acc, 0.5 + far, rtol=0, atol=1e-14)
+
+
+def test_far_plus_near_is_the_fmm(lib, case):
+    """With the library's own operators, far field + FP64 U-list sum on the
+    GPU approximates the direct sum as the oracle's FMM does (p = 4)."""
+    from paper_1909_11085_gb300 import ops
+    wl, t = case
+    p = 4
+    plan = ops.FmmFarPlan(t, p=p, mu=wl.mu, flux=True)
+    pts, f, phi, nrm, w = cuda(wl.pts, wl.f, wl.phi, wl.nrm, wl.w)
+    far = plan(pts, f, phi, nrm, w)
+    near = ops.P2PPlan(wl.pts.shape[0], wl.tree.leaf_ptr, wl.tree.ulist_ptr, wl.tree.ulist_idx, 3,
+                       "fp64")
+    u = near(pts, f, phi, nrm, w, None, wl.mu, out=far.clone(), accumulate=True).cpu().numpy()
+    direct = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts, wl.mu)
+    ref = F.fmm_adaptive(wl.tree, wl.pts, wl.f, wl.phi, wl.nrm, wl.w, p, wl.mu, True)
+    assert _rel(u, ref) <= 1e-9, _rel(u, ref)
+    assert _rel(u, direct) <= 5e-3

@@ -347,7 +347,8 @@ stk_status stokes_fmm_kernel_matrix(const double *x, int32_t nx, const double *y
  * f or phi may be NULL (not both); nrm is needed with phi.  out [n][3] =
  * far field (accumulate != 0: out += far field).  2 <= p <= 12.  Boxes of
  * depth < 2 have no far field; a tree of max_depth < 2 gives zero.  Launches
- * 2 + 4 (max_depth - 1) kernels on the caller's stream; allocates nothing;
+ * 2 + 4 (max_depth - 1) kernels (3 more per depth with m2l_spectra) on the
+ * caller's stream; allocates nothing;
  * workspace from stokes_fmm_far_workspace_size.  STK_EINVAL for bad sizes,
  * NULL arrays or a depth_ptr that does not run from 0 to nbox. */
 typedef struct {
@@ -358,14 +359,30 @@ typedef struct {
   double root_lo[3];
   double root_size;
 } stk_fmm_tree;
-stk_status stokes_fmm_far_workspace_size(int32_t p, int32_t flux, const stk_fmm_tree *tree,
-                                         size_t *bytes);
+stk_status stokes_fmm_far_workspace_size(int32_t p, int32_t flux, int32_t fft_m2l,
+                                         const stk_fmm_tree *tree, size_t *bytes);
 stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double *phi,
                                const double *nrm, const double *w, int64_t n,
                                const stk_fmm_tree *tree, int32_t p, int32_t flux,
-                               const double *uc2e, const double *dc2e, double mu, double *out,
+                               const double *uc2e, const double *dc2e,
+                               const double *m2l_spectra, double mu, double *out,
                                int32_t accumulate, void *workspace, size_t workspace_bytes,
                                void *stream);
+/* Kernel spectra of M2L in Fourier space (host, FP64).  The upward
+ * equivalent surface of a box and the downward check surface of a same-depth
+ * box are the boundary of one p^3 lattice of spacing 2.1 r / (p - 1), so M2L
+ * is a convolution over lattice index differences m with the kernel
+ * K(delta m - 2 r o), o the source box's offset in box widths; zero-padded to
+ * G = 2p points per axis it is a circular convolution, evaluated per
+ * frequency.  out [343][G][G][p + 1][3][nc][2] (offset (ox+3) 49 + (oy+3) 7 +
+ * (oz+3); frequencies kx, ky in [0, G), kz in [0, p]; velocity component,
+ * density component; real, imaginary) holds the DFT (e^{-2 pi i m.k / G}) of
+ * that kernel at half-width r = 1 (Oseen tensor / (8 pi mu) and, for flux != 0,
+ * the source d / (4 pi |d|^3)); entries of neighbouring offsets are zero.
+ * Passed to stokes_fmm_far_eval as m2l_spectra, it selects Fourier-space M2L
+ * (the spectra scaled by 1 / r for forces and 1 / r^2 for sources at each
+ * depth), with the workspace of fft_m2l != 0; NULL selects the dense M2L. */
+stk_status stokes_fmm_m2l_spectra(int32_t p, double mu, int32_t flux, double *out);
 
 /* ------------------------------------------------- no-allocation variant
  * The paper has no counterpart to this entry point; it serves callers that

@@ -11,7 +11,17 @@
 // one a force.  The check-to-equivalent operator is the pseudo-inverse of the
 // kernel matrix from equivalent to check points, truncated at rcond times the
 // largest singular value, by a one-sided (Hestenes) Jacobi SVD.
+//
+// M2L in Fourier space: the upward equivalent surface of a box and the
+// downward check surface of a same-depth box both sit at 1.05 r, so both are
+// the boundary of one p^3 lattice of spacing 2.1 r / (p - 1) and the kernel
+// between them depends only on the lattice index difference m and the boxes'
+// offset o (in box widths): K(delta m - 2 r o).  Zero-padded to G = 2p points
+// per axis, M2L is a circular convolution; its kernel spectrum per offset is
+// computed here once, at half-width 1 (the Stokeslet scales as 1 / r, the
+// point source as 1 / r^2 at other depths).
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -174,6 +184,97 @@ stk_status stokes_fmm_check_to_equiv(int32_t p, double r, double mu, int32_t upw
   kernel_matrix(chk, eqv, mu, ncomp, K);
   pinv(K, 3 * ns, ncomp * ns, rcond, X);
   std::memcpy(out, X.data(), sizeof(double) * X.size());
+  return STK_OK;
+}
+
+stk_status stokes_fmm_m2l_spectra(int32_t p, double mu, int32_t flux, double *out) {
+  if (p < 2 || p > 12) return stk::report_error(STK_EINVAL, "p must be in [2, 12]");
+  if (!(mu > 0.0) || !std::isfinite(mu)) return stk::report_error(STK_EINVAL, "mu must be > 0");
+  if (!out) return stk::report_error(STK_EINVAL, "out is NULL");
+  const int G = 2 * p, nz = p + 1, nc = flux ? 4 : 3, nic = 3 * nc;
+  const size_t nfreq = (size_t)G * G * nz, per_offset = nfreq * nic * 2;
+  const double delta = 2.0 * kInner / (p - 1);  // lattice spacing at half-width 1
+  std::vector<double> cs(G), sn(G);
+  for (int t = 0; t < G; ++t) {
+    cs[t] = std::cos(2.0 * kPiF * t / G);
+    sn[t] = std::sin(2.0 * kPiF * t / G);
+  }
+  // kernel on the lattice, then one 1-D DFT per axis (x, y, then the half
+  // spectrum along z), complex values as (re, im)
+  std::vector<double> T((size_t)G * G * G * nic), A((size_t)G * G * G * nic * 2),
+      B((size_t)G * G * G * nic * 2);
+  auto sgn = [G, p](int m) { return m < p ? m : m - G; };
+  for (int ox = -3; ox <= 3; ++ox)
+    for (int oy = -3; oy <= 3; ++oy)
+      for (int oz = -3; oz <= 3; ++oz) {
+        double *dst = out + (size_t)((ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)) * per_offset;
+        if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) {
+          std::memset(dst, 0, sizeof(double) * per_offset);  // neighbours: never in a V-list
+          continue;
+        }
+        for (int mx = 0; mx < G; ++mx)
+          for (int my = 0; my < G; ++my)
+            for (int mz = 0; mz < G; ++mz) {
+              const double v[3] = {delta * sgn(mx) - 2.0 * ox, delta * sgn(my) - 2.0 * oy,
+                                   delta * sgn(mz) - 2.0 * oz};
+              const double r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+              const double ri = 1.0 / std::sqrt(r2), ri3 = ri * ri * ri;
+              double *t = T.data() + (((size_t)mx * G + my) * G + mz) * nic;
+              for (int i = 0; i < 3; ++i) {
+                for (int c = 0; c < 3; ++c)
+                  t[i * nc + c] = ((i == c ? ri : 0.0) + v[i] * v[c] * ri3) / (8.0 * kPiF * mu);
+                if (nc == 4) t[i * nc + 3] = v[i] * ri3 / (4.0 * kPiF);
+              }
+            }
+        // x: A[kx][my][mz] = sum_mx T[mx][my][mz] e^{-2 pi i mx kx / G}
+        for (int kx = 0; kx < G; ++kx)
+          for (int my = 0; my < G; ++my)
+            for (int mz = 0; mz < G; ++mz)
+              for (int q = 0; q < nic; ++q) {
+                double re = 0.0, im = 0.0;
+                for (int mx = 0; mx < G; ++mx) {
+                  const int t = (mx * kx) % G;
+                  const double val = T[(((size_t)mx * G + my) * G + mz) * nic + q];
+                  re += val * cs[t];
+                  im -= val * sn[t];
+                }
+                double *a = A.data() + ((((size_t)kx * G + my) * G + mz) * nic + q) * 2;
+                a[0] = re;
+                a[1] = im;
+              }
+        // y: B[kx][ky][mz] = sum_my A[kx][my][mz] e^{-2 pi i my ky / G}
+        for (int kx = 0; kx < G; ++kx)
+          for (int ky = 0; ky < G; ++ky)
+            for (int mz = 0; mz < G; ++mz)
+              for (int q = 0; q < nic; ++q) {
+                double re = 0.0, im = 0.0;
+                for (int my = 0; my < G; ++my) {
+                  const int t = (my * ky) % G;
+                  const double *a = A.data() + ((((size_t)kx * G + my) * G + mz) * nic + q) * 2;
+                  re += a[0] * cs[t] + a[1] * sn[t];
+                  im += a[1] * cs[t] - a[0] * sn[t];
+                }
+                double *bb = B.data() + ((((size_t)kx * G + ky) * G + mz) * nic + q) * 2;
+                bb[0] = re;
+                bb[1] = im;
+              }
+        // z, half spectrum: out[kx][ky][kz <= p] = sum_mz B[kx][ky][mz] e^{-2 pi i mz kz / G}
+        for (int kx = 0; kx < G; ++kx)
+          for (int ky = 0; ky < G; ++ky)
+            for (int kz = 0; kz < nz; ++kz)
+              for (int q = 0; q < nic; ++q) {
+                double re = 0.0, im = 0.0;
+                for (int mz = 0; mz < G; ++mz) {
+                  const int t = (mz * kz) % G;
+                  const double *bb = B.data() + ((((size_t)kx * G + ky) * G + mz) * nic + q) * 2;
+                  re += bb[0] * cs[t] + bb[1] * sn[t];
+                  im += bb[1] * cs[t] - bb[0] * sn[t];
+                }
+                double *o = dst + ((((size_t)kx * G + ky) * nz + kz) * nic + q) * 2;
+                o[0] = re;
+                o[1] = im;
+              }
+      }
   return STK_OK;
 }
 

@@ -27,6 +27,12 @@
 //   UC2E   upward check -> upward equivalent density, depth by depth upwards;
 //   DCHK   V-list densities (M2L) + X-list sources + parent's downward
 //          density (L2L, depth > 2) -> downward check velocity (1.05 r);
+//          M2L either dense (kernel evaluations per surface-point pair) or,
+//          given the kernel spectra, in Fourier space: UFFT (spectrum of each
+//          box's upward density on the zero-padded (2p)^3 lattice, a direct
+//          sum over its surface points, the only non-zero lattice values),
+//          KMUL (per box and frequency, the V-list sum of spectrum products)
+//          and IFFT (back at the box's own surface points);
 //   DC2E   downward check -> downward equivalent density, depth by depth;
 //   L2T    downward density of the point's leaf + W-list upward densities
 //          -> velocity at every point.
@@ -99,6 +105,15 @@ struct Pass {
   int32_t accumulate;
   int32_t depth;       // depth of a per-depth pass; its boxes are [box0, box1)
   int32_t box0, box1;
+  // Fourier-space M2L (spec != NULL): G = 2p lattice points per axis, the half
+  // spectrum along z (p + 1 frequencies), nfreq = G G (p + 1)
+  int32_t p;
+  const double *spec;  // [343 offsets][nfreq][3][nc] complex, half-width 1
+  const int32_t *sidx; // [ns][3] lattice index of each surface point
+  const double *tw;    // [G][2] cos, sin of 2 pi t / G
+  double *uhat;        // [nbox][nfreq][nc] complex
+  double *chat;        // [nbox][nfreq][3] complex
+  double *m2l;         // [nbox][3 ns] M2L part of the downward check velocity
 };
 
 // Boundary points of the p^3 grid on [-1, 1]^3, i slowest, k fastest.
@@ -116,6 +131,28 @@ FMM_HD void fill_surface(int p, double *s) {
 }
 
 FMM_HD int surface_count(int p) { return p * p * p - (p - 2) * (p - 2) * (p - 2); }
+
+FMM_HD int freq_count(int p) { return 4 * p * p * (p + 1); }
+
+// Lattice indices of the surface points (the order of fill_surface) and the
+// twiddles of the G-point DFT.
+FMM_HD void fill_lattice(int p, int32_t *sidx, double *tw) {
+  int m = 0;
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j)
+      for (int k = 0; k < p; ++k) {
+        if (!(i == 0 || j == 0 || k == 0 || i == p - 1 || j == p - 1 || k == p - 1)) continue;
+        sidx[3 * m + 0] = i;
+        sidx[3 * m + 1] = j;
+        sidx[3 * m + 2] = k;
+        ++m;
+      }
+  const int G = 2 * p;
+  for (int t = 0; t < G; ++t) {
+    tw[2 * t + 0] = cos(2.0 * kPi * t / G);
+    tw[2 * t + 1] = sin(2.0 * kPi * t / G);
+  }
+}
 
 // Centre and half-width of box b (depth d).
 FMM_HD void box_geom(const Tree &t, int32_t b, int32_t d, double c[3], double &r) {
@@ -251,8 +288,10 @@ struct DCHK {
     double c[3], r, x[3], u[3] = {0.0, 0.0, 0.0};
     box_geom(P.t, b, P.depth, c, r);
     surface_point(P, c, kInner * r, k, x);
-    for (int32_t v = P.t.v_ptr[b]; v < P.t.v_ptr[b + 1]; ++v) {  // M2L
-      const int32_t a = P.t.v_idx[v];
+    if (P.spec)  // M2L done in Fourier space
+      for (int q = 0; q < 3; ++q) u[q] = P.m2l[(size_t)b * 3 * P.ns + 3 * k + q];
+    for (int32_t v = P.spec ? P.t.v_ptr[b + 1] : P.t.v_ptr[b]; v < P.t.v_ptr[b + 1]; ++v) {
+      const int32_t a = P.t.v_idx[v];  // dense M2L
       FMM_CHECK(a, P.t.nbox, "V entry");
       double ca[3], ra;
       box_geom(P.t, a, P.t.depth[a], ca, ra);
@@ -320,14 +359,105 @@ struct L2T {
   }
 };
 
-// Workspace: surface points, then per-box check, upward and downward arrays.
+// UFFT: e = ((box - box0) * nfreq + w) * nc + c; the spectrum of component c
+// of the box's upward density, zero-padded to the G^3 lattice.
+struct UFFT {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int G = 2 * P.p, nz = P.p + 1, nf = freq_count(P.p);
+    const int c = (int)(e % P.nc);
+    const int64_t bw = e / P.nc;
+    const int w = (int)(bw % nf);
+    const int32_t b = P.box0 + (int32_t)(bw / nf);
+    FMM_CHECK(b, P.box1, "ufft box");
+    const int kx = w / (G * nz), ky = (w / nz) % G, kz = w % nz;
+    const double *ub = P.up + (size_t)b * P.nc * P.ns;
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < P.ns; ++j) {
+      const int t = (P.sidx[3 * j] * kx + P.sidx[3 * j + 1] * ky + P.sidx[3 * j + 2] * kz) % G;
+      const double v = ub[(size_t)P.nc * j + c];
+      re += v * P.tw[2 * t];
+      im -= v * P.tw[2 * t + 1];
+    }
+    double *o = P.uhat + (((size_t)b * nf + w) * P.nc + c) * 2;
+    o[0] = re;
+    o[1] = im;
+  }
+};
+
+// KMUL: e = (box - box0) * nfreq + w; per velocity component the V-list sum of
+// kernel spectrum (scaled to the depth) times source spectrum.
+struct KMUL {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int nf = freq_count(P.p);
+    const int w = (int)(e % nf);
+    const int32_t b = P.box0 + (int32_t)(e / nf);
+    FMM_CHECK(b, P.box1, "kmul box");
+    double c[3], r;
+    box_geom(P.t, b, P.depth, c, r);
+    const double sf = 1.0 / r, sq = 1.0 / (r * r);  // Stokeslet 1 / r, source 1 / r^2
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int32_t v = P.t.v_ptr[b]; v < P.t.v_ptr[b + 1]; ++v) {
+      const int32_t a = P.t.v_idx[v];
+      FMM_CHECK(a, P.t.nbox, "V entry");
+      const int ox = P.t.anchor[3 * a] - P.t.anchor[3 * b];
+      const int oy = P.t.anchor[3 * a + 1] - P.t.anchor[3 * b + 1];
+      const int oz = P.t.anchor[3 * a + 2] - P.t.anchor[3 * b + 2];
+      FMM_CHECK(ox + 3, 7, "V offset x");
+      FMM_CHECK(oy + 3, 7, "V offset y");
+      FMM_CHECK(oz + 3, 7, "V offset z");
+      if (ox < -3 || ox > 3 || oy < -3 || oy > 3 || oz < -3 || oz > 3) continue;
+      const int oi = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
+      const double *S = P.spec + ((size_t)oi * nf + w) * 3 * P.nc * 2;
+      const double *U = P.uhat + ((size_t)a * nf + w) * P.nc * 2;
+      for (int cc = 0; cc < P.nc; ++cc) {
+        const double s = cc < 3 ? sf : sq;
+        const double ur = U[2 * cc] * s, ui = U[2 * cc + 1] * s;
+        for (int i = 0; i < 3; ++i) {
+          const double kr = S[2 * (i * P.nc + cc)], ki = S[2 * (i * P.nc + cc) + 1];
+          acc[2 * i] += kr * ur - ki * ui;
+          acc[2 * i + 1] += kr * ui + ki * ur;
+        }
+      }
+    }
+    double *o = P.chat + ((size_t)b * nf + w) * 3 * 2;
+    for (int q = 0; q < 6; ++q) o[q] = acc[q];
+  }
+};
+
+// IFFT: e = (box - box0) * ns + k; the inverse transform at surface point k
+// (Hermitian half spectrum: planes kz = 0 and kz = p once, the others twice).
+struct IFFT {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int G = 2 * P.p, nz = P.p + 1, nf = freq_count(P.p);
+    const int32_t b = P.box0 + (int32_t)(e / P.ns);
+    const int k = (int)(e % P.ns);
+    FMM_CHECK(b, P.box1, "ifft box");
+    const int ix = P.sidx[3 * k], iy = P.sidx[3 * k + 1], iz = P.sidx[3 * k + 2];
+    const double *C = P.chat + (size_t)b * nf * 3 * 2;
+    double u[3] = {0.0, 0.0, 0.0};
+    for (int w = 0; w < nf; ++w) {
+      const int kx = w / (G * nz), ky = (w / nz) % G, kz = w % nz;
+      const int t = (ix * kx + iy * ky + iz * kz) % G;
+      const double cs = P.tw[2 * t], sn = P.tw[2 * t + 1];
+      const double wt = (kz == 0 || kz == P.p) ? 1.0 : 2.0;
+      for (int q = 0; q < 3; ++q)
+        u[q] += wt * (C[(size_t)w * 6 + 2 * q] * cs - C[(size_t)w * 6 + 2 * q + 1] * sn);
+    }
+    const double inv = 1.0 / ((double)G * G * G);
+    for (int q = 0; q < 3; ++q) P.m2l[(size_t)b * 3 * P.ns + 3 * k + q] = u[q] * inv;
+  }
+};
+
+// Workspace: surface points, then per-box check, upward and downward arrays;
+// with Fourier-space M2L also the lattice, twiddles and spectra.
 struct Layout {
-  size_t surf, chk, up, dn, total;
+  size_t surf, chk, up, dn, sidx, tw, uhat, chat, m2l, total;
 };
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-inline Layout layout(int64_t nbox, int ns, int nc) {
+inline Layout layout(int64_t nbox, int p, int nc, bool fft) {
+  const int ns = surface_count(p);
   Layout L;
   size_t o = 0;
   L.surf = o;
@@ -338,6 +468,20 @@ inline Layout layout(int64_t nbox, int ns, int nc) {
   o += align256(sizeof(double) * (size_t)nc * ns * (size_t)nbox);
   L.dn = o;
   o += align256(sizeof(double) * 3 * (size_t)ns * (size_t)nbox);
+  L.sidx = L.tw = L.uhat = L.chat = L.m2l = o;
+  if (fft) {
+    const size_t nf = (size_t)freq_count(p);
+    L.sidx = o;
+    o += align256(sizeof(int32_t) * 3 * (size_t)ns);
+    L.tw = o;
+    o += align256(sizeof(double) * 2 * 2 * (size_t)p);
+    L.uhat = o;
+    o += align256(sizeof(double) * 2 * nf * nc * (size_t)nbox);
+    L.chat = o;
+    o += align256(sizeof(double) * 2 * nf * 3 * (size_t)nbox);
+    L.m2l = o;
+    o += align256(sizeof(double) * 3 * (size_t)ns * (size_t)nbox);
+  }
   L.total = o + 256;  // slack for aligning the caller's base
   return L;
 }
@@ -362,6 +506,12 @@ void far_field(Exec &ex, Pass P, const int32_t *depth_ptr, int32_t max_depth) {
     P.box0 = depth_ptr[d];
     P.box1 = depth_ptr[d + 1];
     const int64_t nb = P.box1 - P.box0;
+    if (P.spec) {
+      const int64_t nf = freq_count(P.p);
+      ex.template run<UFFT>(P, nb * nf * P.nc);
+      ex.template run<KMUL>(P, nb * nf);
+      ex.template run<IFFT>(P, nb * ns);
+    }
     ex.template run<DCHK>(P, nb * ns);
     ex.template run<DC2E>(P, nb * 3 * ns);
   }

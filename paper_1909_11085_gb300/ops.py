@@ -581,15 +581,26 @@ def fmm_operators(p, root_size, max_depth, mu=1.0, flux=True, rcond=1e-13):
     return uc, dc
 
 
+def fmm_m2l_spectra(p, mu=1.0, flux=True):
+    """Kernel spectra of Fourier-space M2L at half-width 1 (host, FP64):
+    [343, 2p, 2p, p + 1, 3, nc, 2] (see stokes_fmm_m2l_spectra)."""
+    import numpy as np
+    nc = 4 if flux else 3
+    out = np.zeros((343, 2 * p, 2 * p, p + 1, 3, nc, 2))
+    A.check(A.lib().stokes_fmm_m2l_spectra(int(p), float(mu), int(bool(flux)), out.ctypes.data))
+    return out
+
+
 class FmmFarPlan:
     """Far field of the FMM (stokes_fmm_far_eval) on a fixed tree: device
     copies of the tree arrays (from fmm_tree_arrays), the per-depth operators
     (fmm_operators unless given) and a workspace.  Calls take the densities of
     the leaf-sorted points and return the far field [n, 3]; adding the U-list
-    P2P sum over the same leaves gives the FMM velocity."""
+    P2P sum over the same leaves gives the FMM velocity.  m2l = "dense"
+    evaluates M2L kernel by kernel, "fft" in Fourier space (fmm_m2l_spectra)."""
 
     def __init__(self, tree, p=4, mu=1.0, flux=True, uc2e=None, dc2e=None, rcond=1e-13,
-                 device=None):
+                 device=None, m2l="dense"):
         import numpy as np
         self.device = device or torch.device("cuda")
         self.p, self.mu, self.flux = int(p), float(mu), bool(flux)
@@ -608,6 +619,12 @@ class FmmFarPlan:
                              f"[{D}, {3 * ns}, {3 * ns}] for p = {self.p}, flux = {self.flux}")
         self.uc2e = torch.as_tensor(uc2e).to(self.device).contiguous()
         self.dc2e = torch.as_tensor(dc2e).to(self.device).contiguous()
+        if m2l not in ("dense", "fft"):
+            raise ValueError('m2l must be "dense" or "fft"')
+        self.spec = None
+        if m2l == "fft":
+            self.spec = torch.as_tensor(fmm_m2l_spectra(self.p, self.mu, self.flux)).to(
+                self.device).contiguous()
         t = A.StkFmmTree()
         t.nbox = int(tree["depth"].size)
         t.nleaf = int(tree["leaf_box"].size)
@@ -620,8 +637,9 @@ class FmmFarPlan:
         t.root_size = float(tree["root_size"])
         self.tree = t
         nb = ctypes.c_size_t(0)
-        A.check(A.lib().stokes_fmm_far_workspace_size(self.p, int(self.flux), ctypes.byref(t),
-                                                      ctypes.byref(nb)))
+        A.check(A.lib().stokes_fmm_far_workspace_size(self.p, int(self.flux),
+                                                      int(self.spec is not None),
+                                                      ctypes.byref(t), ctypes.byref(nb)))
         self.ws = A.workspace(nb.value, self.device)
 
     def __call__(self, pts, f=None, phi=None, nrm=None, w=None, out=None, accumulate=False):
@@ -638,6 +656,7 @@ class FmmFarPlan:
             A.check(A.lib().stokes_fmm_far_eval(
                 A.ptr(pts), A.ptr(f), A.ptr(phi), A.ptr(nrm), A.ptr(w), n, ctypes.byref(self.tree),
                 self.p, int(self.flux), A.ptr(self.uc2e) if ops else None,
-                A.ptr(self.dc2e) if ops else None, self.mu, A.ptr(out), int(bool(accumulate)),
+                A.ptr(self.dc2e) if ops else None, A.ptr(self.spec), self.mu, A.ptr(out),
+                int(bool(accumulate)),
                 A.ptr(self.ws), self.ws.numel(), A.stream_ptr(self.device)))
         return out

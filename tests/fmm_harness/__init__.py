@@ -35,8 +35,9 @@ def _p(a):
 
 
 def far_eval(pts, f, phi, nrm, w, tree, p, uc2e, dc2e, mu=1.0, flux=True, out=None,
-             accumulate=False):
-    """tree: dict of the arrays of the library's stk_fmm_tree (numpy, host)."""
+             accumulate=False, spec=None):
+    """tree: dict of the arrays of the library's stk_fmm_tree (numpy, host);
+    spec: M2L kernel spectra (Fourier-space M2L) or None (dense M2L)."""
     c = lambda a, t=np.float64: None if a is None else np.ascontiguousarray(a, dtype=t)
     i = lambda a: np.ascontiguousarray(a, dtype=np.int32)
     pts, f, phi, nrm, w = c(pts), c(f), c(phi), c(nrm), c(w)
@@ -47,14 +48,14 @@ def far_eval(pts, f, phi, nrm, w, tree, p, uc2e, dc2e, mu=1.0, flux=True, out=No
                            "leaf_box", "leaf_ptr", "v_ptr", "v_idx", "w_ptr", "w_idx", "x_ptr",
                            "x_idx")]
     root_lo = c(tree["root_lo"])
-    uc2e, dc2e = c(uc2e), c(dc2e)
+    uc2e, dc2e, spec = c(uc2e), c(dc2e), c(spec)
     L = lib()
     r = L.fmm_host_far_eval(
         _p(pts), _p(f), _p(phi), _p(nrm), _p(w), ctypes.c_longlong(n),
         ctypes.c_int(T["depth"].size), ctypes.c_int(T["leaf_box"].size),
         ctypes.c_int(int(tree["max_depth"])), *[_p(a) for a in args], _p(root_lo),
         ctypes.c_double(float(tree["root_size"])), ctypes.c_int(p), ctypes.c_int(int(flux)),
-        _p(uc2e), _p(dc2e), ctypes.c_double(mu), _p(out), ctypes.c_int(int(accumulate)))
+        _p(uc2e), _p(dc2e), _p(spec), ctypes.c_double(mu), _p(out), ctypes.c_int(int(accumulate)))
     if r < 0:
         raise IndexError(L.fmm_host_message().decode())
     return out, int(r)

@@ -82,25 +82,30 @@ def test_tree_arrays_reject_a_box_order_the_passes_cannot_use(case):
         ops.fmm_tree_arrays(*bad)
 
 
-@pytest.mark.parametrize("flux,kinds", [(True, "sldl"), (False, "sl"), (True, "dl")])
-def test_host_passes_match_the_oracle_far_field(case, flux, kinds):
+@pytest.mark.parametrize("flux,kinds,m2l", [(True, "sldl", "dense"), (False, "sl", "dense"),
+                                            (True, "dl", "dense"), (True, "sldl", "fft"),
+                                            (False, "sl", "fft")])
+def test_host_passes_match_the_oracle_far_field(case, flux, kinds, m2l):
     """Same operators on both sides: the passes reproduce the oracle's far
-    field (upward, V/W/X lists, downward, L2T) up to rounding; the Stokeslet-only
+    field (upward, V/W/X lists, downward, L2T) up to rounding, with M2L dense
+    or in Fourier space (the library's kernel spectra); the Stokeslet-only
     upward density (flux off) serves the single layer alone."""
     wl, fl, t = case
     p = 4
     by_depth, U, D = oracle_operators(wl, t, p, flux)
     f = wl.f if "sl" in kinds else None
     phi = wl.phi if kinds in ("sldl", "dl") else None
-    far, npass = H.far_eval(wl.pts, f, phi, wl.nrm, wl.w, t, p, U, D, wl.mu, flux)
+    spec = ops.fmm_m2l_spectra(p, wl.mu, flux) if m2l == "fft" else None
+    far, npass = H.far_eval(wl.pts, f, phi, wl.nrm, wl.w, t, p, U, D, wl.mu, flux, spec=spec)
     ref = F.fmm_adaptive(wl.tree, wl.pts, f, phi, wl.nrm, wl.w, p, wl.mu, flux, ops=by_depth,
                          near=False)
-    assert npass == 2 + 4 * (t["max_depth"] - 1) - 1  # the deepest depth has no M2M
+    # the deepest depth has no M2M; Fourier-space M2L adds 3 passes per depth
+    assert npass == 2 + (4 + 3 * (m2l == "fft")) * (t["max_depth"] - 1) - 1
     assert _rel(far, ref) <= 1e-10, _rel(far, ref)
     # accumulate adds to what out holds
     base = np.full_like(far, 0.25)
     acc, _ = H.far_eval(wl.pts, f, phi, wl.nrm, wl.w, t, p, U, D, wl.mu, flux, out=base.copy(),
-                        accumulate=True)
+                        accumulate=True, spec=spec)
     np.testing.assert_allclose(acc, base + far, rtol=0, atol=1e-15)
 
 

@@ -94,3 +94,28 @@ def test_translation_matrices_match_the_oracle(L, ncomp):
                                           ncomp, out.ctypes.data) == 0
         ref = F.upward_matrix(x, y, mu, ncomp == 4)
         np.testing.assert_allclose(out, ref, rtol=1e-13, atol=1e-16 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("p,flux", [(4, True), (3, False)])
+def test_m2l_spectra_are_the_dft_of_the_lattice_kernel(L, p, flux):
+    """The library's M2L kernel spectra are numpy's FFT of the kernel
+    K(delta m - 2 o) tabulated on the zero-padded (2p)^3 lattice of index
+    differences (half spectrum along z), at half-width 1; neighbouring offsets
+    (never in a V-list) are zero."""
+    mu, G = 0.7, 2 * p
+    nc = 4 if flux else 3
+    spec = np.zeros((343, G, G, p + 1, 3, nc, 2))
+    assert L.stokes_fmm_m2l_spectra(p, mu, int(flux), spec.ctypes.data) == 0
+    m = np.stack(np.meshgrid(*(np.arange(G),) * 3, indexing="ij"), -1).reshape(-1, 3)
+    m = np.where(m >= p, m - G, m)
+    delta = 2 * F.R_INNER / (p - 1)
+    for o in [(2, 0, 0), (3, -2, 1), (-3, -3, 3), (0, 0, -2)]:
+        K = F.upward_matrix(delta * m, 2.0 * np.array(o, float)[None, :], mu, flux)
+        Kf = np.fft.fftn(K.reshape(G, G, G, 3, nc), axes=(0, 1, 2))[:, :, :p + 1]
+        oi = (o[0] + 3) * 49 + (o[1] + 3) * 7 + (o[2] + 3)
+        got = spec[oi, ..., 0] + 1j * spec[oi, ..., 1]
+        assert np.abs(got - Kf).max() <= 1e-14 * np.abs(Kf).max()
+    for o in [(0, 0, 0), (1, -1, 0), (-1, 1, 1)]:
+        assert not spec[(o[0] + 3) * 49 + (o[1] + 3) * 7 + (o[2] + 3)].any()
+    assert L.stokes_fmm_m2l_spectra(1, mu, 1, spec.ctypes.data) != 0
+    assert L.stokes_fmm_m2l_spectra(p, -1.0, 1, spec.ctypes.data) != 0

@@ -133,3 +133,38 @@ def test_m2l_is_a_circular_convolution_on_the_surface_lattice(p):
         U = np.real(np.fft.ifftn(Uf, axes=(0, 1, 2)))
         conv = U[idx[:, 0], idx[:, 1], idx[:, 2]].reshape(-1)
         assert _rel(conv, dense) <= 1e-13
+
+
+@pytest.mark.parametrize("p,rcond,ratio", [(4, 1e-13, 0.2), (6, 1e-13, 1.0), (6, 1e-7, 0.2)])
+def test_m2l_inputs_rounded_to_fp32_stay_below_the_truncation_error(p, rcond, ratio):
+    """The precision reading for a single-precision M2L: the upward equivalent
+    densities stay within a few times the check velocities they reproduce (no
+    large cancelling coefficients), so rounding them and the translation to
+    FP32 changes the field a V-list pair carries into the target box by less
+    than the FMM's own truncation error at that order: a fifth of it at p = 4;
+    at p = 6 up to the error itself with the pseudo-inverses cut at 1e-13, and
+    a fifth of it when they are cut at 1e-7 (FP32's resolution)."""
+    oracle.build()
+    rng = np.random.default_rng(40 + p)
+    S = F.cube_surface(p)
+    r = 0.1
+    uc2e = F.pinv(F.upward_matrix(F.R_OUTER * r * S, F.R_INNER * r * S, 1.0, True), rcond)
+    dc2e = F.pinv(F.stokeslet_matrix(F.R_INNER * r * S, F.R_OUTER * r * S, 1.0), rcond)
+    o = np.array([3.0, 1.0, -2.0]) * 2 * r
+    M = F.upward_matrix(o + F.R_INNER * r * S, F.R_INNER * r * S, 1.0, True)
+    for _ in range(3):
+        y = rng.uniform(-r, r, (60, 3))
+        f, phi = rng.normal(size=(60, 3)), rng.normal(size=(60, 3))
+        n = rng.normal(size=(60, 3))
+        n /= np.linalg.norm(n, axis=1)[:, None]
+        w = np.full(60, 0.01)
+        chk = oracle.sldl(y, f, n, phi, w, F.R_OUTER * r * S, 1.0).reshape(-1)
+        up = uc2e @ chk
+        assert np.abs(up).max() <= 10 * np.abs(chk).max()
+        x = o + rng.uniform(-r, r, (40, 3))
+        L2T = F.stokeslet_matrix(x, o + F.R_OUTER * r * S, 1.0)
+        u64 = L2T @ (dc2e @ (M @ up))
+        u32 = L2T @ (dc2e @ (M.astype(np.float32) @ up.astype(np.float32)).astype(np.float64))
+        true = oracle.sldl(y, f, n, phi, w, x, 1.0).reshape(-1)
+        trunc = _rel(u64, true)
+        assert _rel(u32, u64) <= ratio * trunc, (_rel(u32, u64), trunc)

@@ -223,6 +223,49 @@ def _time_ms(fn, stream, flush, reps, warm=1):
     return statistics.median(a.elapsed_time(b) for a, b in ev)
 
 
+def run_fmm_far(wl, near, dev, stream, flush, p=4):
+    """The FMM's far field (stokes_fmm_far_eval, FP64 passes) on the near-field
+    workload's own octree: host set-up time (V, W and X lists; per-depth
+    operators), device time per call with dense and with Fourier-space M2L, and
+    far field + the step's near field against the direct sum on 256 sampled
+    targets (the FMM's approximation error at this p, not a parity figure)."""
+    import torch
+    import oracle
+    from paper_1909_11085_gb300 import ops
+    from synth import octree as O
+    t0 = time.perf_counter()
+    fl = O.far_lists(wl.tree)
+    t = ops.fmm_tree_arrays(fl.depth, fl.anchor, fl.parent, fl.leaf, wl.tree.leaf_ptr, fl.v_ptr,
+                            fl.v_idx, fl.w_ptr, fl.w_idx, fl.x_ptr, fl.x_idx, wl.tree.root_lo,
+                            wl.tree.root_size)
+    lists_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    U, D = ops.fmm_operators(p, t["root_size"], t["max_depth"], wl.mu, True)
+    ops_s = time.perf_counter() - t0
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    pts, f, phi, nrm, w = (T(a) for a in (wl.pts, wl.f, wl.phi, wl.nrm, wl.w))
+    rng = np.random.default_rng(1909)
+    tg = np.sort(rng.choice(wl.pts.shape[0], 256, replace=False))
+    ref = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts[tg], wl.mu)
+    un = near.cpu().numpy()[tg]
+    res = {"p": p, "boxes": int(t["depth"].size), "leaves": int(t["leaf_box"].size),
+           "max_depth": int(t["max_depth"]), "v_pairs": int(fl.v_idx.size),
+           "w_entries": int(fl.w_idx.size), "x_entries": int(fl.x_idx.size),
+           "host_lists_s": lists_s, "host_operators_s": ops_s,
+           "near_only_rel_l2": float(np.linalg.norm(un - ref) / np.linalg.norm(ref))}
+    for m2l in ("dense", "fft"):
+        plan = ops.FmmFarPlan(t, p=p, mu=wl.mu, flux=True, uc2e=U, dc2e=D, m2l=m2l)
+        far = torch.zeros_like(pts)
+        ms = _time_ms(lambda: plan(pts, f, phi, nrm, w, out=far), stream, flush, 2)
+        u = far.cpu().numpy()[tg] + un
+        res[m2l] = {"ms": ms, "rel_l2_vs_direct": float(np.linalg.norm(u - ref) /
+                                                        np.linalg.norm(ref))}
+        log(f"[fmm] {m2l}: {res[m2l]}")
+        del plan, far
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_forms(dev, flush, stream, peak_tflops):
     """The paper's other workloads on the same GPU: direct single layer (8 cells),
     direct double layer (256 cells + 65,536 off-surface targets), 2,048 batched
@@ -674,6 +717,8 @@ def run_ours(args, rank, world, local_rank):
               "clocks": clocks, "wall_s_timed_region": wall}
     if world == 1 and not args.no_forms:
         result["forms"] = run_forms(dev, flush, stream, peak)
+    if world == 1 and args.fmm_far:
+        result["fmm_far"] = run_fmm_far(wl, out, dev, stream, flush)
     if world == 1 and not args.no_cpu_baseline:
         rng = np.random.default_rng(20191)
         tg, ref, dt = timed_oracle(wl, args.cpu_seconds, rng)
@@ -709,6 +754,9 @@ def main():
     ap.add_argument("--wall-patches", type=int, default=320)
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the other workloads (direct, batched, adjoint)")
+    ap.add_argument("--fmm-far", action="store_true",
+                    help="also time the FMM's far field (FP64 passes, dense and Fourier-space "
+                         "M2L) on the near-field workload's octree")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

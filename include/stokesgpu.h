@@ -344,6 +344,12 @@ stk_status stokes_fmm_kernel_matrix(const double *x, int32_t nx, const double *y
  * surface count of p.  flux != 0: the upward density has a point-source
  * strength per surface point (needed for the double layer's far field).
  *
+ * precision: STK_FP64 evaluates every pass in FP64; STK_MIXED packs points
+ * (relative to their leaf's centre), densities, surfaces and spectra in FP32,
+ * evaluates kernels and spectral products in FP32 with one FP64 difference of
+ * box centres per pair of boxes, and keeps the check-to-equivalent products
+ * in FP64 (operators cut at rcond ~ 1e-7 suit it best for p >= 6).  n must
+ * equal leaf_ptr[nleaf].
  * f or phi may be NULL (not both); nrm is needed with phi.  out [n][3] =
  * far field (accumulate != 0: out += far field).  2 <= p <= 12.  Boxes of
  * depth < 2 have no far field; a tree of max_depth < 2 gives zero.  Launches
@@ -360,14 +366,15 @@ typedef struct {
   double root_size;
 } stk_fmm_tree;
 stk_status stokes_fmm_far_workspace_size(int32_t p, int32_t flux, int32_t fft_m2l,
+                                         int32_t precision, int64_t n,
                                          const stk_fmm_tree *tree, size_t *bytes);
 stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double *phi,
                                const double *nrm, const double *w, int64_t n,
                                const stk_fmm_tree *tree, int32_t p, int32_t flux,
                                const double *uc2e, const double *dc2e,
-                               const double *m2l_spectra, double mu, double *out,
-                               int32_t accumulate, void *workspace, size_t workspace_bytes,
-                               void *stream);
+                               const double *m2l_spectra, int32_t precision, double mu,
+                               double *out, int32_t accumulate, void *workspace,
+                               size_t workspace_bytes, void *stream);
 /* Kernel spectra of M2L in Fourier space (host, FP64).  The upward
  * equivalent surface of a box and the downward check surface of a same-depth
  * box are the boundary of one p^3 lattice of spacing 2.1 r / (p - 1), so M2L

@@ -120,9 +120,9 @@ def lib():
             L.stokes_fmm_check_to_equiv.argtypes = [i32, d, d, i32, i32, d, p]
             L.stokes_fmm_kernel_matrix.argtypes = [p, i32, p, i32, d, i32, p]
             pt = ctypes.POINTER(StkFmmTree)
-            L.stokes_fmm_far_workspace_size.argtypes = [i32, i32, i32, pt, psz]
-            L.stokes_fmm_far_eval.argtypes = [p, p, p, p, p, i64, pt, i32, i32, p, p, p, d, p, i32,
-                                              p, sz, p]
+            L.stokes_fmm_far_workspace_size.argtypes = [i32, i32, i32, i32, i64, pt, psz]
+            L.stokes_fmm_far_eval.argtypes = [p, p, p, p, p, i64, pt, i32, i32, p, p, p, i32, d, p,
+                                              i32, p, sz, p]
             L.stokes_fmm_m2l_spectra.argtypes = [i32, d, i32, p]
             L.stokes_graph_destroy.argtypes = [p]
             L.stokes_launch_count.restype = ctypes.c_int64

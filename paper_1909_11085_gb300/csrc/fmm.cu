@@ -22,10 +22,8 @@ __global__ void __launch_bounds__(256) k_fmm_pass(Pass P, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) F()(P, e);
 }
 
-__global__ void k_fmm_surface(int p, double *s, int32_t *sidx, double *tw) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  stk::fmm::fill_surface(p, s);
-  if (sidx) stk::fmm::fill_lattice(p, sidx, tw);
+__global__ void k_fmm_setup(Pass P) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) stk::fmm::fill_setup(P);
 }
 
 struct DeviceExec {
@@ -93,12 +91,17 @@ stk::fmm::Tree device_tree(const stk_fmm_tree *t) {
 extern "C" {
 
 stk_status stokes_fmm_far_workspace_size(int32_t p, int32_t flux, int32_t fft_m2l,
+                                         int32_t precision, int64_t n,
                                          const stk_fmm_tree *tree, size_t *bytes) {
   if (p < 2 || p > 12) return stk::report_error(STK_EINVAL, "p must be in [2, 12]");
+  if (precision != STK_FP64 && precision != STK_MIXED)
+    return stk::report_error(STK_EINVAL, "precision must be STK_FP64 or STK_MIXED");
+  if (n < 0 || n > 0x7fffffffLL) return stk::report_error(STK_EINVAL, "n must be in [0, 2^31-1]");
   if (!bytes) return stk::report_error(STK_EINVAL, "bytes is NULL");
   const stk_status s = check_tree(tree);
   if (s != STK_OK) return s;
-  *bytes = stk::fmm::layout(tree->nbox, p, flux ? 4 : 3, fft_m2l != 0).total;
+  *bytes = stk::fmm::layout(tree->nbox, p, flux ? 4 : 3, fft_m2l != 0, precision == STK_MIXED, n)
+               .total;
   return STK_OK;
 }
 
@@ -106,12 +109,15 @@ stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double 
                                const double *nrm, const double *w, int64_t n,
                                const stk_fmm_tree *tree, int32_t p, int32_t flux,
                                const double *uc2e, const double *dc2e,
-                               const double *m2l_spectra, double mu, double *out,
+                               const double *m2l_spectra, int32_t precision, double mu,
+                               double *out,
                                int32_t accumulate, void *workspace, size_t workspace_bytes,
                                void *stream) {
   using stk::report_error;
   if (p < 2 || p > 12) return report_error(STK_EINVAL, "p must be in [2, 12]");
   if (n < 0 || n > 0x7fffffffLL) return report_error(STK_EINVAL, "n must be in [0, 2^31-1]");
+  if (precision != STK_FP64 && precision != STK_MIXED)
+    return report_error(STK_EINVAL, "precision must be STK_FP64 or STK_MIXED");
   stk_status s = check_tree(tree);
   if (s != STK_OK) return s;
   if (n == 0) return STK_OK;
@@ -124,8 +130,8 @@ stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double 
   if (tree->max_depth >= stk::fmm::kFirstDepth && (!uc2e || !dc2e))
     return report_error(STK_EINVAL, "uc2e/dc2e is NULL");
   const int ns = stk::fmm::surface_count(p), nc = flux ? 4 : 3;
-  const bool fft = m2l_spectra != nullptr;
-  const stk::fmm::Layout L = stk::fmm::layout(tree->nbox, p, nc, fft);
+  const bool fft = m2l_spectra != nullptr, mixed = precision == STK_MIXED;
+  const stk::fmm::Layout L = stk::fmm::layout(tree->nbox, p, nc, fft, mixed, n);
   if (!workspace || workspace_bytes < L.total) return report_error(STK_ENOMEM, "workspace too small");
   char *ws = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~(uintptr_t)255);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -147,27 +153,18 @@ stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double 
   P.csrc = 1.0 / (4.0 * stk::fmm::kPi);
   P.ns = ns;
   P.nc = nc;
-  P.surf = reinterpret_cast<double *>(ws + L.surf);
   P.uc2e = uc2e;
   P.dc2e = dc2e;
-  P.chk = reinterpret_cast<double *>(ws + L.chk);
-  P.up = reinterpret_cast<double *>(ws + L.up);
-  P.dn = reinterpret_cast<double *>(ws + L.dn);
   P.out = out;
   P.accumulate = accumulate ? 1 : 0;
   P.depth = 0;
   P.box0 = P.box1 = 0;
   P.p = p;
   P.spec = m2l_spectra;
-  P.sidx = fft ? reinterpret_cast<int32_t *>(ws + L.sidx) : nullptr;
-  P.tw = fft ? reinterpret_cast<double *>(ws + L.tw) : nullptr;
-  P.uhat = fft ? reinterpret_cast<double *>(ws + L.uhat) : nullptr;
-  P.chat = fft ? reinterpret_cast<double *>(ws + L.chat) : nullptr;
-  P.m2l = fft ? reinterpret_cast<double *>(ws + L.m2l) : nullptr;
+  stk::fmm::bind(P, ws, L, fft, mixed);
 
-  k_fmm_surface<<<1, 32, 0, st>>>(p, reinterpret_cast<double *>(ws + L.surf),
-                                  const_cast<int32_t *>(P.sidx), const_cast<double *>(P.tw));
-  if (cudaGetLastError() != cudaSuccess) return report_error(STK_ECUDA, "surface launch failed");
+  k_fmm_setup<<<1, 32, 0, st>>>(P);
+  if (cudaGetLastError() != cudaSuccess) return report_error(STK_ECUDA, "set-up launch failed");
   stk::count_launches(1);
   DeviceExec ex{st, (int64_t)sms * 8};
   stk::fmm::far_field(ex, P, tree->depth_ptr, tree->max_depth);

@@ -95,7 +95,7 @@ struct Pass {
   double csrc;  // 1 / (4 pi): equivalent point sources
   int32_t ns;   // points per surface
   int32_t nc;   // components of the upward density per point (3, or 4 with flux)
-  const double *surf;  // [ns][3] on [-1, 1]^3
+  double *surf;        // [ns][3] on [-1, 1]^3
   const double *uc2e;  // [depth - 2][nc ns][3 ns]
   const double *dc2e;  // [depth - 2][3 ns][3 ns]
   double *chk;         // [nbox][3 ns] check velocities (upward, then downward)
@@ -109,11 +109,22 @@ struct Pass {
   // spectrum along z (p + 1 frequencies), nfreq = G G (p + 1)
   int32_t p;
   const double *spec;  // [343 offsets][nfreq][3][nc] complex, half-width 1
-  const int32_t *sidx; // [ns][3] lattice index of each surface point
-  const double *tw;    // [G][2] cos, sin of 2 pi t / G
+  int32_t *sidx;       // [ns][3] lattice index of each surface point
+  double *tw;          // [G][2] cos, sin of 2 pi t / G
   double *uhat;        // [nbox][nfreq][nc] complex
   double *chat;        // [nbox][nfreq][3] complex
   double *m2l;         // [nbox][3 ns] M2L part of the downward check velocity
+  // mixed precision (mixed != 0): FP32 copies; the FP64 up, dn, tw, uhat, chat
+  // and m2l are then unused
+  int32_t mixed;
+  float *ploc;         // [n][3] point minus its leaf's centre
+  float *qf, *pf, *nf; // [n][3] w f / (8 pi mu), w phi 6 / (8 pi), normals (NULL if unused)
+  float *surf32;       // [ns][3]
+  float *up32;         // [nbox][nc ns]
+  float *dn32;         // [nbox][3 ns]
+  float *tw32;         // [G][2]
+  float *spec32;       // as spec
+  float *uhat32, *chat32, *m2l32;
 };
 
 // Boundary points of the p^3 grid on [-1, 1]^3, i slowest, k fastest.
@@ -359,9 +370,32 @@ struct L2T {
   }
 };
 
+// Buffers of the FP64 (double) and mixed (float) forms.
+template <class R>
+struct Bufs;
+template <>
+struct Bufs<double> {
+  static FMM_HD const double *up(const Pass &P) { return P.up; }
+  static FMM_HD const double *tw(const Pass &P) { return P.tw; }
+  static FMM_HD const double *spec(const Pass &P) { return P.spec; }
+  static FMM_HD double *uhat(const Pass &P) { return P.uhat; }
+  static FMM_HD double *chat(const Pass &P) { return P.chat; }
+  static FMM_HD double *m2l(const Pass &P) { return P.m2l; }
+};
+template <>
+struct Bufs<float> {
+  static FMM_HD const float *up(const Pass &P) { return P.up32; }
+  static FMM_HD const float *tw(const Pass &P) { return P.tw32; }
+  static FMM_HD const float *spec(const Pass &P) { return P.spec32; }
+  static FMM_HD float *uhat(const Pass &P) { return P.uhat32; }
+  static FMM_HD float *chat(const Pass &P) { return P.chat32; }
+  static FMM_HD float *m2l(const Pass &P) { return P.m2l32; }
+};
+
 // UFFT: e = ((box - box0) * nfreq + w) * nc + c; the spectrum of component c
 // of the box's upward density, zero-padded to the G^3 lattice.
-struct UFFT {
+template <class R>
+struct UFFTT {
   FMM_HD void operator()(const Pass &P, int64_t e) const {
     const int G = 2 * P.p, nz = P.p + 1, nf = freq_count(P.p);
     const int c = (int)(e % P.nc);
@@ -370,15 +404,16 @@ struct UFFT {
     const int32_t b = P.box0 + (int32_t)(bw / nf);
     FMM_CHECK(b, P.box1, "ufft box");
     const int kx = w / (G * nz), ky = (w / nz) % G, kz = w % nz;
-    const double *ub = P.up + (size_t)b * P.nc * P.ns;
-    double re = 0.0, im = 0.0;
+    const R *ub = Bufs<R>::up(P) + (size_t)b * P.nc * P.ns;
+    const R *tw = Bufs<R>::tw(P);
+    R re = 0, im = 0;
     for (int j = 0; j < P.ns; ++j) {
       const int t = (P.sidx[3 * j] * kx + P.sidx[3 * j + 1] * ky + P.sidx[3 * j + 2] * kz) % G;
-      const double v = ub[(size_t)P.nc * j + c];
-      re += v * P.tw[2 * t];
-      im -= v * P.tw[2 * t + 1];
+      const R v = ub[(size_t)P.nc * j + c];
+      re += v * tw[2 * t];
+      im -= v * tw[2 * t + 1];
     }
-    double *o = P.uhat + (((size_t)b * nf + w) * P.nc + c) * 2;
+    R *o = Bufs<R>::uhat(P) + (((size_t)b * nf + w) * P.nc + c) * 2;
     o[0] = re;
     o[1] = im;
   }
@@ -386,7 +421,8 @@ struct UFFT {
 
 // KMUL: e = (box - box0) * nfreq + w; per velocity component the V-list sum of
 // kernel spectrum (scaled to the depth) times source spectrum.
-struct KMUL {
+template <class R>
+struct KMULT {
   FMM_HD void operator()(const Pass &P, int64_t e) const {
     const int nf = freq_count(P.p);
     const int w = (int)(e % nf);
@@ -394,8 +430,10 @@ struct KMUL {
     FMM_CHECK(b, P.box1, "kmul box");
     double c[3], r;
     box_geom(P.t, b, P.depth, c, r);
-    const double sf = 1.0 / r, sq = 1.0 / (r * r);  // Stokeslet 1 / r, source 1 / r^2
-    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const R sf = (R)(1.0 / r), sq = (R)(1.0 / (r * r));  // Stokeslet 1 / r, source 1 / r^2
+    const R *spec = Bufs<R>::spec(P);
+    const R *uhat = Bufs<R>::uhat(P);
+    R acc[6] = {0, 0, 0, 0, 0, 0};
     for (int32_t v = P.t.v_ptr[b]; v < P.t.v_ptr[b + 1]; ++v) {
       const int32_t a = P.t.v_idx[v];
       FMM_CHECK(a, P.t.nbox, "V entry");
@@ -407,83 +445,405 @@ struct KMUL {
       FMM_CHECK(oz + 3, 7, "V offset z");
       if (ox < -3 || ox > 3 || oy < -3 || oy > 3 || oz < -3 || oz > 3) continue;
       const int oi = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
-      const double *S = P.spec + ((size_t)oi * nf + w) * 3 * P.nc * 2;
-      const double *U = P.uhat + ((size_t)a * nf + w) * P.nc * 2;
+      const R *S = spec + ((size_t)oi * nf + w) * 3 * P.nc * 2;
+      const R *U = uhat + ((size_t)a * nf + w) * P.nc * 2;
       for (int cc = 0; cc < P.nc; ++cc) {
-        const double s = cc < 3 ? sf : sq;
-        const double ur = U[2 * cc] * s, ui = U[2 * cc + 1] * s;
+        const R sc = cc < 3 ? sf : sq;
+        const R ur = U[2 * cc] * sc, ui = U[2 * cc + 1] * sc;
         for (int i = 0; i < 3; ++i) {
-          const double kr = S[2 * (i * P.nc + cc)], ki = S[2 * (i * P.nc + cc) + 1];
+          const R kr = S[2 * (i * P.nc + cc)], ki = S[2 * (i * P.nc + cc) + 1];
           acc[2 * i] += kr * ur - ki * ui;
           acc[2 * i + 1] += kr * ui + ki * ur;
         }
       }
     }
-    double *o = P.chat + ((size_t)b * nf + w) * 3 * 2;
+    R *o = Bufs<R>::chat(P) + ((size_t)b * nf + w) * 3 * 2;
     for (int q = 0; q < 6; ++q) o[q] = acc[q];
   }
 };
 
 // IFFT: e = (box - box0) * ns + k; the inverse transform at surface point k
 // (Hermitian half spectrum: planes kz = 0 and kz = p once, the others twice).
-struct IFFT {
+template <class R>
+struct IFFTT {
   FMM_HD void operator()(const Pass &P, int64_t e) const {
     const int G = 2 * P.p, nz = P.p + 1, nf = freq_count(P.p);
     const int32_t b = P.box0 + (int32_t)(e / P.ns);
     const int k = (int)(e % P.ns);
     FMM_CHECK(b, P.box1, "ifft box");
     const int ix = P.sidx[3 * k], iy = P.sidx[3 * k + 1], iz = P.sidx[3 * k + 2];
-    const double *C = P.chat + (size_t)b * nf * 3 * 2;
-    double u[3] = {0.0, 0.0, 0.0};
+    const R *C = Bufs<R>::chat(P) + (size_t)b * nf * 3 * 2;
+    const R *tw = Bufs<R>::tw(P);
+    R u[3] = {0, 0, 0};
     for (int w = 0; w < nf; ++w) {
       const int kx = w / (G * nz), ky = (w / nz) % G, kz = w % nz;
       const int t = (ix * kx + iy * ky + iz * kz) % G;
-      const double cs = P.tw[2 * t], sn = P.tw[2 * t + 1];
-      const double wt = (kz == 0 || kz == P.p) ? 1.0 : 2.0;
+      const R cs = tw[2 * t], sn = tw[2 * t + 1];
+      const R wt = (kz == 0 || kz == P.p) ? (R)1 : (R)2;
       for (int q = 0; q < 3; ++q)
         u[q] += wt * (C[(size_t)w * 6 + 2 * q] * cs - C[(size_t)w * 6 + 2 * q + 1] * sn);
     }
-    const double inv = 1.0 / ((double)G * G * G);
-    for (int q = 0; q < 3; ++q) P.m2l[(size_t)b * 3 * P.ns + 3 * k + q] = u[q] * inv;
+    const R inv = (R)(1.0 / ((double)G * G * G));
+    for (int q = 0; q < 3; ++q) Bufs<R>::m2l(P)[(size_t)b * 3 * P.ns + 3 * k + q] = u[q] * inv;
   }
 };
 
-// Workspace: surface points, then per-box check, upward and downward arrays;
-// with Fourier-space M2L also the lattice, twiddles and spectra.
+using UFFT = UFFTT<double>;
+using KMUL = KMULT<double>;
+using IFFT = IFFTT<double>;
+
+// ------------------------------------------------------------------ mixed
+// FP32 evaluations on local coordinates: points relative to their leaf's
+// centre, surface points relative to their box's centre, and per pair of
+// boxes one FP64 difference of centres rounded to FP32, so that no FP64
+// operation runs per pair of points.  Check-to-equivalent operators stay FP64.
+
+FMM_HD float frsqrt(float x) {
+#if defined(__CUDA_ARCH__)
+  return rsqrtf(x);
+#else
+  return 1.0f / sqrtf(x);
+#endif
+}
+
+// centre of box a minus centre of box b, rounded to FP32
+FMM_HD void centre_offset(const Pass &P, int32_t b, int32_t a, float off[3]) {
+  double cb[3], ca[3], rb, ra;
+  box_geom(P.t, b, P.t.depth[b], cb, rb);
+  box_geom(P.t, a, P.t.depth[a], ca, ra);
+  for (int q = 0; q < 3; ++q) off[q] = (float)(cb[q] - ca[q]);
+}
+
+// Adds at xs + off (relative to the centre of the sources' leaf) the single and
+// double layer of the packed points [i0, i1).
+FMM_HD void f_add_sources(const Pass &P, const float off[3], const float xs[3], int64_t i0,
+                          int64_t i1, float u[3]) {
+  FMM_CHECK(i0, P.n + 1, "point range start");
+  FMM_CHECK(i1, P.n + 1, "point range end");
+  const float x0 = off[0] + xs[0], x1 = off[1] + xs[1], x2 = off[2] + xs[2];
+  for (int64_t i = i0; i < i1; ++i) {
+    const float *y = P.ploc + 3 * i;
+    const float d0 = x0 - y[0], d1 = x1 - y[1], d2 = x2 - y[2];
+    const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    if (!(r2 > 0.0f)) continue;
+    const float ri = frsqrt(r2), ri2 = ri * ri;
+    if (P.qf) {
+      const float *q = P.qf + 3 * i;
+      const float dq = (d0 * q[0] + d1 * q[1] + d2 * q[2]) * ri2 * ri;
+      u[0] += q[0] * ri + d0 * dq;
+      u[1] += q[1] * ri + d1 * dq;
+      u[2] += q[2] * ri + d2 * dq;
+    }
+    if (P.pf) {
+      const float *s = P.pf + 3 * i, *nn = P.nf + 3 * i;
+      const float c = (d0 * s[0] + d1 * s[1] + d2 * s[2]) * (d0 * nn[0] + d1 * nn[1] + d2 * nn[2]) *
+                      ri2 * ri2 * ri;
+      u[0] += d0 * c;
+      u[1] += d1 * c;
+      u[2] += d2 * c;
+    }
+  }
+}
+
+// Adds at xs + off (relative to the centre of the source box) the field of the
+// FP32 equivalent density e on the source box's surface of half-width rad.
+FMM_HD void f_add_equivalent(const Pass &P, const float off[3], const float xs[3], float rad,
+                             const float *e, int nc, float u[3]) {
+  const float x0 = off[0] + xs[0], x1 = off[1] + xs[1], x2 = off[2] + xs[2];
+  const float csl = (float)P.csl, csrc = (float)P.csrc;
+  float uf[3] = {0.0f, 0.0f, 0.0f}, uq[3] = {0.0f, 0.0f, 0.0f};
+  for (int j = 0; j < P.ns; ++j) {
+    const float *sj = P.surf32 + 3 * j;
+    const float d0 = x0 - rad * sj[0], d1 = x1 - rad * sj[1], d2 = x2 - rad * sj[2];
+    const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    if (!(r2 > 0.0f)) continue;
+    const float ri = frsqrt(r2), ri3 = ri * ri * ri;
+    const float *ej = e + (size_t)nc * j;
+    const float df = (d0 * ej[0] + d1 * ej[1] + d2 * ej[2]) * ri3;
+    uf[0] += ej[0] * ri + d0 * df;
+    uf[1] += ej[1] * ri + d1 * df;
+    uf[2] += ej[2] * ri + d2 * df;
+    if (nc == 4) {
+      const float s = ej[3] * ri3;
+      uq[0] += d0 * s;
+      uq[1] += d1 * s;
+      uq[2] += d2 * s;
+    }
+  }
+  for (int a = 0; a < 3; ++a) u[a] += csl * uf[a] + csrc * uq[a];
+}
+
+FMM_HD int32_t leaf_of_point(const Tree &t, int64_t e) {
+  int32_t lo = 0, hi = t.nleaf;  // the last leaf whose range starts at or before e
+  while (hi - lo > 1) {
+    const int32_t mid = lo + (hi - lo) / 2;
+    if (t.leaf_ptr[mid] <= e) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// PACK: e = point; local coordinates and pre-scaled FP32 densities.
+struct PACK {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int32_t b = P.t.leaf_box[leaf_of_point(P.t, e)];
+    FMM_CHECK(b, P.t.nbox, "point's leaf box");
+    double c[3], r;
+    box_geom(P.t, b, P.t.depth[b], c, r);
+    for (int q = 0; q < 3; ++q) {
+      P.ploc[3 * e + q] = (float)(P.pts[3 * e + q] - c[q]);
+      if (P.qf) P.qf[3 * e + q] = (float)(P.csl * (P.w[e] * P.f[3 * e + q]));
+      if (P.pf) {
+        P.pf[3 * e + q] = (float)(P.cdl * (P.w[e] * P.phi[3 * e + q]));
+        P.nf[3 * e + q] = (float)P.nrm[3 * e + q];
+      }
+    }
+  }
+};
+
+// SPEC32: e = value; the kernel spectra rounded to FP32.
+struct SPEC32 {
+  FMM_HD void operator()(const Pass &P, int64_t e) const { P.spec32[e] = (float)P.spec[e]; }
+};
+
+// S2M, mixed: e = leaf * ns + k.
+struct S2MF {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int64_t l = e / P.ns;
+    const int k = (int)(e % P.ns);
+    FMM_CHECK(l, P.t.nleaf, "leaf");
+    const int32_t b = P.t.leaf_box[l];
+    FMM_CHECK(b, P.t.nbox, "leaf box");
+    const int32_t d = P.t.depth[b];
+    if (d < kFirstDepth) return;
+    double c[3], r;
+    box_geom(P.t, b, d, c, r);
+    const float rad = (float)(kOuter * r), off[3] = {0.0f, 0.0f, 0.0f};
+    const float xs[3] = {rad * P.surf32[3 * k], rad * P.surf32[3 * k + 1],
+                         rad * P.surf32[3 * k + 2]};
+    float u[3] = {0.0f, 0.0f, 0.0f};
+    f_add_sources(P, off, xs, P.t.leaf_ptr[l], P.t.leaf_ptr[l + 1], u);
+    for (int q = 0; q < 3; ++q) P.chk[(size_t)b * 3 * P.ns + 3 * k + q] = u[q];
+  }
+};
+
+// M2M, mixed: e = (box - box0) * ns + k.
+struct M2MF {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int32_t b = P.box0 + (int32_t)(e / P.ns);
+    const int k = (int)(e % P.ns);
+    FMM_CHECK(b, P.box1, "m2m box");
+    const int32_t c0 = P.t.child_ptr[b], c1 = P.t.child_ptr[b + 1];
+    if (c0 >= c1) return;
+    double c[3], r;
+    box_geom(P.t, b, P.depth, c, r);
+    const float rad = (float)(kOuter * r);
+    const float xs[3] = {rad * P.surf32[3 * k], rad * P.surf32[3 * k + 1],
+                         rad * P.surf32[3 * k + 2]};
+    const float rc = (float)(kInner * r / 2);  // children have half the half-width
+    float u[3] = {0.0f, 0.0f, 0.0f};
+    for (int32_t ch = c0; ch < c1; ++ch) {
+      FMM_CHECK(ch, P.t.nbox, "child");
+      float off[3];
+      centre_offset(P, b, ch, off);
+      f_add_equivalent(P, off, xs, rc, P.up32 + (size_t)ch * P.nc * P.ns, P.nc, u);
+    }
+    for (int q = 0; q < 3; ++q) P.chk[(size_t)b * 3 * P.ns + 3 * k + q] = u[q];
+  }
+};
+
+// Check-to-equivalent, mixed: the FP64 row product rounded to FP32.
+struct UC2EF {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int64_t rows = (int64_t)P.nc * P.ns;
+    const int32_t b = P.box0 + (int32_t)(e / rows);
+    const int64_t i = e % rows;
+    FMM_CHECK(b, P.box1, "uc2e box");
+    const double *M = P.uc2e + (size_t)(P.depth - kFirstDepth) * rows * 3 * P.ns;
+    P.up32[(size_t)b * rows + i] =
+        (float)apply_row(M, i, P.chk + (size_t)b * 3 * P.ns, 3 * P.ns);
+  }
+};
+
+struct DC2EF {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int64_t rows = 3 * (int64_t)P.ns;
+    const int32_t b = P.box0 + (int32_t)(e / rows);
+    const int64_t i = e % rows;
+    FMM_CHECK(b, P.box1, "dc2e box");
+    const double *M = P.dc2e + (size_t)(P.depth - kFirstDepth) * rows * rows;
+    P.dn32[(size_t)b * rows + i] = (float)apply_row(M, i, P.chk + (size_t)b * rows, (int)rows);
+  }
+};
+
+// DCHK, mixed: e = (box - box0) * ns + k.
+struct DCHKF {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int32_t b = P.box0 + (int32_t)(e / P.ns);
+    const int k = (int)(e % P.ns);
+    FMM_CHECK(b, P.box1, "dchk box");
+    double c[3], r;
+    box_geom(P.t, b, P.depth, c, r);
+    const float rad = (float)(kInner * r);
+    const float xs[3] = {rad * P.surf32[3 * k], rad * P.surf32[3 * k + 1],
+                         rad * P.surf32[3 * k + 2]};
+    float u[3] = {0.0f, 0.0f, 0.0f};
+    if (P.spec)  // M2L done in Fourier space
+      for (int q = 0; q < 3; ++q) u[q] = P.m2l32[(size_t)b * 3 * P.ns + 3 * k + q];
+    for (int32_t v = P.spec ? P.t.v_ptr[b + 1] : P.t.v_ptr[b]; v < P.t.v_ptr[b + 1]; ++v) {
+      const int32_t a = P.t.v_idx[v];  // dense M2L: same depth, same radius
+      FMM_CHECK(a, P.t.nbox, "V entry");
+      float off[3];
+      centre_offset(P, b, a, off);
+      f_add_equivalent(P, off, xs, rad, P.up32 + (size_t)a * P.nc * P.ns, P.nc, u);
+    }
+    for (int32_t v = P.t.x_ptr[b]; v < P.t.x_ptr[b + 1]; ++v) {  // X-list sources
+      const int32_t a = P.t.x_idx[v];
+      FMM_CHECK(a, P.t.nbox, "X entry");
+      const int32_t l = P.t.box_leaf[a];
+      FMM_CHECK(l, P.t.nleaf, "X leaf");
+      if (l < 0) continue;
+      float off[3];
+      centre_offset(P, b, a, off);
+      f_add_sources(P, off, xs, P.t.leaf_ptr[l], P.t.leaf_ptr[l + 1], u);
+    }
+    if (P.depth > kFirstDepth) {  // L2L
+      const int32_t pb = P.t.parent[b];
+      FMM_CHECK(pb, P.t.nbox, "parent");
+      float off[3];
+      centre_offset(P, b, pb, off);
+      f_add_equivalent(P, off, xs, (float)(kOuter * 2.0 * r), P.dn32 + (size_t)pb * 3 * P.ns, 3, u);
+    }
+    for (int q = 0; q < 3; ++q) P.chk[(size_t)b * 3 * P.ns + 3 * k + q] = u[q];
+  }
+};
+
+// L2T + W-list, mixed: e = point (leaf order).
+struct L2TF {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int32_t b = P.t.leaf_box[leaf_of_point(P.t, e)];
+    FMM_CHECK(b, P.t.nbox, "point's leaf box");
+    const int32_t d = P.t.depth[b];
+    const float xs[3] = {P.ploc[3 * e], P.ploc[3 * e + 1], P.ploc[3 * e + 2]};
+    float u[3] = {0.0f, 0.0f, 0.0f};
+    if (d >= kFirstDepth) {
+      double c[3], r;
+      box_geom(P.t, b, d, c, r);
+      const float off[3] = {0.0f, 0.0f, 0.0f};
+      f_add_equivalent(P, off, xs, (float)(kOuter * r), P.dn32 + (size_t)b * 3 * P.ns, 3, u);
+    }
+    for (int32_t v = P.t.w_ptr[b]; v < P.t.w_ptr[b + 1]; ++v) {
+      const int32_t a = P.t.w_idx[v];
+      FMM_CHECK(a, P.t.nbox, "W entry");
+      double ca[3], ra;
+      box_geom(P.t, a, P.t.depth[a], ca, ra);
+      float off[3];
+      centre_offset(P, b, a, off);
+      f_add_equivalent(P, off, xs, (float)(kInner * ra), P.up32 + (size_t)a * P.nc * P.ns, P.nc,
+                       u);
+    }
+    double *o = P.out + 3 * e;
+    for (int a = 0; a < 3; ++a) o[a] = (P.accumulate ? o[a] : 0.0) + (double)u[a];
+  }
+};
+
+// Workspace layout.  FP64 form: surface, per-box check, upward and downward
+// arrays, and with Fourier-space M2L the lattice, twiddles and spectra.  Mixed
+// form: the check array stays FP64 (input of the FP64 operators); points,
+// surfaces, densities and spectra are FP32.
 struct Layout {
-  size_t surf, chk, up, dn, sidx, tw, uhat, chat, m2l, total;
+  size_t surf, chk, up, dn, sidx, tw, uhat, chat, m2l;
+  size_t ploc, qf, pf, nf, surf32, up32, dn32, tw32, spec32, uhat32, chat32, m2l32;
+  size_t total;
 };
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-inline Layout layout(int64_t nbox, int p, int nc, bool fft) {
+inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t n) {
   const int ns = surface_count(p);
+  const size_t nf = (size_t)freq_count(p), B = (size_t)nbox, N = (size_t)n;
   Layout L;
   size_t o = 0;
-  L.surf = o;
-  o += align256(sizeof(double) * 3 * (size_t)ns);
-  L.chk = o;
-  o += align256(sizeof(double) * 3 * (size_t)ns * (size_t)nbox);
-  L.up = o;
-  o += align256(sizeof(double) * (size_t)nc * ns * (size_t)nbox);
-  L.dn = o;
-  o += align256(sizeof(double) * 3 * (size_t)ns * (size_t)nbox);
-  L.sidx = L.tw = L.uhat = L.chat = L.m2l = o;
-  if (fft) {
-    const size_t nf = (size_t)freq_count(p);
-    L.sidx = o;
-    o += align256(sizeof(int32_t) * 3 * (size_t)ns);
-    L.tw = o;
-    o += align256(sizeof(double) * 2 * 2 * (size_t)p);
-    L.uhat = o;
-    o += align256(sizeof(double) * 2 * nf * nc * (size_t)nbox);
-    L.chat = o;
-    o += align256(sizeof(double) * 2 * nf * 3 * (size_t)nbox);
-    L.m2l = o;
-    o += align256(sizeof(double) * 3 * (size_t)ns * (size_t)nbox);
+  auto take = [&o](size_t bytes) {
+    const size_t at = o;
+    o += align256(bytes);
+    return at;
+  };
+  const size_t none = 0;
+  L.surf = take(sizeof(double) * 3 * ns);
+  L.chk = take(sizeof(double) * 3 * ns * B);
+  L.sidx = take(sizeof(int32_t) * 3 * ns);
+  L.up = L.dn = L.tw = L.uhat = L.chat = L.m2l = none;
+  L.ploc = L.qf = L.pf = L.nf = L.surf32 = L.up32 = L.dn32 = L.tw32 = L.spec32 = L.uhat32 =
+      L.chat32 = L.m2l32 = none;
+  if (!mixed) {
+    L.up = take(sizeof(double) * nc * ns * B);
+    L.dn = take(sizeof(double) * 3 * ns * B);
+    L.tw = take(sizeof(double) * 4 * p);
+    if (fft) {
+      L.uhat = take(sizeof(double) * 2 * nf * nc * B);
+      L.chat = take(sizeof(double) * 2 * nf * 3 * B);
+      L.m2l = take(sizeof(double) * 3 * ns * B);
+    }
+  } else {
+    L.ploc = take(sizeof(float) * 3 * N);
+    L.qf = take(sizeof(float) * 3 * N);
+    L.pf = take(sizeof(float) * 3 * N);
+    L.nf = take(sizeof(float) * 3 * N);
+    L.surf32 = take(sizeof(float) * 3 * ns);
+    L.up32 = take(sizeof(float) * nc * ns * B);
+    L.dn32 = take(sizeof(float) * 3 * ns * B);
+    L.tw32 = take(sizeof(float) * 4 * p);
+    if (fft) {
+      L.spec32 = take(sizeof(float) * 343 * nf * 3 * nc * 2);
+      L.uhat32 = take(sizeof(float) * 2 * nf * nc * B);
+      L.chat32 = take(sizeof(float) * 2 * nf * 3 * B);
+      L.m2l32 = take(sizeof(float) * 3 * ns * B);
+    }
   }
   L.total = o + 256;  // slack for aligning the caller's base
   return L;
+}
+
+// Points the Pass at its buffers in a workspace (base aligned to 256 bytes).
+inline void bind(Pass &P, char *ws, const Layout &L, bool fft, bool mixed) {
+  auto d = [ws](size_t off) { return reinterpret_cast<double *>(ws + off); };
+  auto f = [ws](size_t off) { return reinterpret_cast<float *>(ws + off); };
+  P.surf = d(L.surf);
+  P.chk = d(L.chk);
+  P.sidx = reinterpret_cast<int32_t *>(ws + L.sidx);
+  P.mixed = mixed ? 1 : 0;
+  P.up = mixed ? nullptr : d(L.up);
+  P.dn = mixed ? nullptr : d(L.dn);
+  P.tw = mixed ? nullptr : d(L.tw);
+  P.uhat = (fft && !mixed) ? d(L.uhat) : nullptr;
+  P.chat = (fft && !mixed) ? d(L.chat) : nullptr;
+  P.m2l = (fft && !mixed) ? d(L.m2l) : nullptr;
+  P.ploc = mixed ? f(L.ploc) : nullptr;
+  P.qf = (mixed && P.f) ? f(L.qf) : nullptr;
+  P.pf = (mixed && P.phi) ? f(L.pf) : nullptr;
+  P.nf = (mixed && P.phi) ? f(L.nf) : nullptr;
+  P.surf32 = mixed ? f(L.surf32) : nullptr;
+  P.up32 = mixed ? f(L.up32) : nullptr;
+  P.dn32 = mixed ? f(L.dn32) : nullptr;
+  P.tw32 = mixed ? f(L.tw32) : nullptr;
+  P.spec32 = (fft && mixed) ? f(L.spec32) : nullptr;
+  P.uhat32 = (fft && mixed) ? f(L.uhat32) : nullptr;
+  P.chat32 = (fft && mixed) ? f(L.chat32) : nullptr;
+  P.m2l32 = (fft && mixed) ? f(L.m2l32) : nullptr;
+}
+
+// Surface points, lattice indices and twiddles (one thread; set-up of a call).
+FMM_HD void fill_setup(const Pass &P) {
+  fill_surface(P.p, P.surf);
+  double tw[2 * 2 * 12];  // G = 2p <= 24 twiddles
+  fill_lattice(P.p, P.sidx, tw);
+  for (int t = 0; t < 2 * 2 * P.p; ++t) {
+    if (P.tw) P.tw[t] = tw[t];
+    if (P.tw32) P.tw32[t] = (float)tw[t];
+  }
+  if (P.surf32)
+    for (int q = 0; q < 3 * P.ns; ++q) P.surf32[q] = (float)P.surf[q];
 }
 
 // The pass sequence; Exec::run<F>(P, count) calls F on every output of a pass
@@ -492,30 +852,53 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft) {
 template <class Exec>
 void far_field(Exec &ex, Pass P, const int32_t *depth_ptr, int32_t max_depth) {
   const int64_t ns = P.ns;
-  ex.template run<S2M>(P, (int64_t)P.t.nleaf * ns);
+  const bool mixed = P.mixed != 0;
+  if (mixed) {
+    ex.template run<PACK>(P, P.n);
+    if (P.spec) ex.template run<SPEC32>(P, (int64_t)343 * freq_count(P.p) * 3 * P.nc * 2);
+    ex.template run<S2MF>(P, (int64_t)P.t.nleaf * ns);
+  } else {
+    ex.template run<S2M>(P, (int64_t)P.t.nleaf * ns);
+  }
   for (int32_t d = max_depth; d >= kFirstDepth; --d) {
     P.depth = d;
     P.box0 = depth_ptr[d];
     P.box1 = depth_ptr[d + 1];
     const int64_t nb = P.box1 - P.box0;
-    if (d < max_depth) ex.template run<M2M>(P, nb * ns);
-    ex.template run<UC2E>(P, nb * P.nc * ns);
+    if (mixed) {
+      if (d < max_depth) ex.template run<M2MF>(P, nb * ns);
+      ex.template run<UC2EF>(P, nb * P.nc * ns);
+    } else {
+      if (d < max_depth) ex.template run<M2M>(P, nb * ns);
+      ex.template run<UC2E>(P, nb * P.nc * ns);
+    }
   }
   for (int32_t d = kFirstDepth; d <= max_depth; ++d) {
     P.depth = d;
     P.box0 = depth_ptr[d];
     P.box1 = depth_ptr[d + 1];
     const int64_t nb = P.box1 - P.box0;
-    if (P.spec) {
-      const int64_t nf = freq_count(P.p);
-      ex.template run<UFFT>(P, nb * nf * P.nc);
-      ex.template run<KMUL>(P, nb * nf);
-      ex.template run<IFFT>(P, nb * ns);
+    const int64_t nf = freq_count(P.p);
+    if (mixed) {
+      if (P.spec) {
+        ex.template run<UFFTT<float>>(P, nb * nf * P.nc);
+        ex.template run<KMULT<float>>(P, nb * nf);
+        ex.template run<IFFTT<float>>(P, nb * ns);
+      }
+      ex.template run<DCHKF>(P, nb * ns);
+      ex.template run<DC2EF>(P, nb * 3 * ns);
+    } else {
+      if (P.spec) {
+        ex.template run<UFFT>(P, nb * nf * P.nc);
+        ex.template run<KMUL>(P, nb * nf);
+        ex.template run<IFFT>(P, nb * ns);
+      }
+      ex.template run<DCHK>(P, nb * ns);
+      ex.template run<DC2E>(P, nb * 3 * ns);
     }
-    ex.template run<DCHK>(P, nb * ns);
-    ex.template run<DC2E>(P, nb * 3 * ns);
   }
-  ex.template run<L2T>(P, P.n);
+  if (mixed) ex.template run<L2TF>(P, P.n);
+  else ex.template run<L2T>(P, P.n);
 }
 
 }  // namespace fmm

@@ -597,10 +597,15 @@ class FmmFarPlan:
     (fmm_operators unless given) and a workspace.  Calls take the densities of
     the leaf-sorted points and return the far field [n, 3]; adding the U-list
     P2P sum over the same leaves gives the FMM velocity.  m2l = "dense"
-    evaluates M2L kernel by kernel, "fft" in Fourier space (fmm_m2l_spectra)."""
+    evaluates M2L kernel by kernel, "fft" in Fourier space (fmm_m2l_spectra);
+    precision = "fp64" runs every pass in FP64, "mixed" the evaluations in FP32
+    on local coordinates with FP64 check-to-equivalent products.  The operators'
+    cut-off (rcond) defaults to 1e-13, and to 1e-7 (FP32's resolution) for the
+    mixed form at p >= 6, where FP32 rounding of densities fitted beyond it
+    would exceed the truncation error."""
 
-    def __init__(self, tree, p=4, mu=1.0, flux=True, uc2e=None, dc2e=None, rcond=1e-13,
-                 device=None, m2l="dense"):
+    def __init__(self, tree, p=4, mu=1.0, flux=True, uc2e=None, dc2e=None, rcond=None,
+                 device=None, m2l="dense", precision="fp64"):
         import numpy as np
         self.device = device or torch.device("cuda")
         self.p, self.mu, self.flux = int(p), float(mu), bool(flux)
@@ -608,6 +613,8 @@ class FmmFarPlan:
         self._arrays = {k: torch.as_tensor(np.asarray(tree[k], dtype=np.int32)).to(
             self.device).contiguous() for k in _FMM_DEVICE_KEYS}
         self.n = int(tree["leaf_ptr"][-1])
+        if rcond is None:
+            rcond = 1e-7 if (precision == "mixed" and self.p >= 6) else 1e-13
         if uc2e is None or dc2e is None:
             uc2e, dc2e = fmm_operators(self.p, tree["root_size"], tree["max_depth"], self.mu,
                                        self.flux, rcond)
@@ -621,6 +628,9 @@ class FmmFarPlan:
         self.dc2e = torch.as_tensor(dc2e).to(self.device).contiguous()
         if m2l not in ("dense", "fft"):
             raise ValueError('m2l must be "dense" or "fft"')
+        if precision not in ("fp64", "mixed"):
+            raise ValueError('precision must be "fp64" or "mixed"')
+        self.precision = A.STK_MIXED if precision == "mixed" else A.STK_FP64
         self.spec = None
         if m2l == "fft":
             self.spec = torch.as_tensor(fmm_m2l_spectra(self.p, self.mu, self.flux)).to(
@@ -638,8 +648,8 @@ class FmmFarPlan:
         self.tree = t
         nb = ctypes.c_size_t(0)
         A.check(A.lib().stokes_fmm_far_workspace_size(self.p, int(self.flux),
-                                                      int(self.spec is not None),
-                                                      ctypes.byref(t), ctypes.byref(nb)))
+                                                      int(self.spec is not None), self.precision,
+                                                      self.n, ctypes.byref(t), ctypes.byref(nb)))
         self.ws = A.workspace(nb.value, self.device)
 
     def __call__(self, pts, f=None, phi=None, nrm=None, w=None, out=None, accumulate=False):
@@ -656,7 +666,8 @@ class FmmFarPlan:
             A.check(A.lib().stokes_fmm_far_eval(
                 A.ptr(pts), A.ptr(f), A.ptr(phi), A.ptr(nrm), A.ptr(w), n, ctypes.byref(self.tree),
                 self.p, int(self.flux), A.ptr(self.uc2e) if ops else None,
-                A.ptr(self.dc2e) if ops else None, A.ptr(self.spec), self.mu, A.ptr(out),
+                A.ptr(self.dc2e) if ops else None, A.ptr(self.spec), self.precision, self.mu,
+                A.ptr(out),
                 int(bool(accumulate)),
                 A.ptr(self.ws), self.ws.numel(), A.stream_ptr(self.device)))
         return out

@@ -35,9 +35,10 @@ def _p(a):
 
 
 def far_eval(pts, f, phi, nrm, w, tree, p, uc2e, dc2e, mu=1.0, flux=True, out=None,
-             accumulate=False, spec=None):
+             accumulate=False, spec=None, mixed=False):
     """tree: dict of the arrays of the library's stk_fmm_tree (numpy, host);
-    spec: M2L kernel spectra (Fourier-space M2L) or None (dense M2L)."""
+    spec: M2L kernel spectra (Fourier-space M2L) or None (dense M2L);
+    mixed: the FP32 evaluation passes instead of the FP64 ones."""
     c = lambda a, t=np.float64: None if a is None else np.ascontiguousarray(a, dtype=t)
     i = lambda a: np.ascontiguousarray(a, dtype=np.int32)
     pts, f, phi, nrm, w = c(pts), c(f), c(phi), c(nrm), c(w)
@@ -55,7 +56,8 @@ def far_eval(pts, f, phi, nrm, w, tree, p, uc2e, dc2e, mu=1.0, flux=True, out=No
         ctypes.c_int(T["depth"].size), ctypes.c_int(T["leaf_box"].size),
         ctypes.c_int(int(tree["max_depth"])), *[_p(a) for a in args], _p(root_lo),
         ctypes.c_double(float(tree["root_size"])), ctypes.c_int(p), ctypes.c_int(int(flux)),
-        _p(uc2e), _p(dc2e), _p(spec), ctypes.c_double(mu), _p(out), ctypes.c_int(int(accumulate)))
+        _p(uc2e), _p(dc2e), _p(spec), ctypes.c_int(int(bool(mixed))), ctypes.c_double(mu), _p(out),
+        ctypes.c_int(int(accumulate)))
     if r < 0:
         raise IndexError(L.fmm_host_message().decode())
     return out, int(r)

@@ -3,6 +3,7 @@
 // same pass sequence, run by plain loops over host arrays, with every index
 // checked before it is used.  It is test infrastructure: the library does not
 // contain or call it.
+#include <cstdint>
 #include <cstdio>
 #include <vector>
 
@@ -44,7 +45,7 @@ long long fmm_host_far_eval(const double *pts, const double *f, const double *ph
                             const int *w_idx, const int *x_ptr, const int *x_idx,
                             const double *root_lo, double root_size, int p, int flux,
                             const double *uc2e, const double *dc2e, const double *spec,
-                            double mu, double *out, int accumulate) {
+                            int mixed, double mu, double *out, int accumulate) {
   g_bad = 0;
   g_msg[0] = 0;
   stk::fmm::Pass P;
@@ -67,17 +68,6 @@ long long fmm_host_far_eval(const double *pts, const double *f, const double *ph
   for (int q = 0; q < 3; ++q) T.root_lo[q] = root_lo[q];
   T.root_size = root_size;
   const int ns = stk::fmm::surface_count(p), nc = flux ? 4 : 3;
-  const size_t nf = (size_t)stk::fmm::freq_count(p);
-  std::vector<double> surf(3 * (size_t)ns), chk(3 * (size_t)ns * nbox), up((size_t)nc * ns * nbox),
-      dn(3 * (size_t)ns * nbox), tw(4 * (size_t)p), uhat, chat, m2l;
-  std::vector<int32_t> sidx(3 * (size_t)ns);
-  stk::fmm::fill_surface(p, surf.data());
-  stk::fmm::fill_lattice(p, sidx.data(), tw.data());
-  if (spec) {
-    uhat.assign(2 * nf * nc * nbox, 0.0);
-    chat.assign(2 * nf * 3 * nbox, 0.0);
-    m2l.assign(3 * (size_t)ns * nbox, 0.0);
-  }
   P.pts = pts;
   P.f = f;
   P.phi = phi;
@@ -89,23 +79,21 @@ long long fmm_host_far_eval(const double *pts, const double *f, const double *ph
   P.csrc = 1.0 / (4.0 * stk::fmm::kPi);
   P.ns = ns;
   P.nc = nc;
-  P.surf = surf.data();
   P.uc2e = uc2e;
   P.dc2e = dc2e;
-  P.chk = chk.data();
-  P.up = up.data();
-  P.dn = dn.data();
   P.out = out;
   P.accumulate = accumulate;
   P.depth = 0;
   P.box0 = P.box1 = 0;
   P.p = p;
   P.spec = spec;
-  P.sidx = sidx.data();
-  P.tw = tw.data();
-  P.uhat = spec ? uhat.data() : nullptr;
-  P.chat = spec ? chat.data() : nullptr;
-  P.m2l = spec ? m2l.data() : nullptr;
+  // the library's workspace layout, in one buffer aligned as the library aligns it
+  const stk::fmm::Layout L = stk::fmm::layout(nbox, p, nc, spec != nullptr, mixed != 0, n);
+  std::vector<char> buf(L.total + 256);
+  char *ws = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(buf.data()) + 255) &
+                                      ~(uintptr_t)255);
+  stk::fmm::bind(P, ws, L, spec != nullptr, mixed != 0);
+  stk::fmm::fill_setup(P);
   HostExec ex;
   stk::fmm::far_field(ex, P, depth_ptr, max_depth);
   return g_bad ? -1 : ex.launches;

@@ -140,24 +140,24 @@ def test_fmm_far_entry_points_validated_on_host(L):
         setattr(t, k, 16)  # never dereferenced on the host
     t.root_size = 1.0
     nb = ctypes.c_size_t(0)
-    assert L.stokes_fmm_far_workspace_size(4, 1, 0, ctypes.byref(t), ctypes.byref(nb)) == A.STK_OK
+    assert L.stokes_fmm_far_workspace_size(4, 1, 0, 0, 10, ctypes.byref(t), ctypes.byref(nb)) == A.STK_OK
     ns = 4 ** 3 - 2 ** 3
     assert nb.value >= 8 * (3 * ns + 9 * (3 + 4 + 3) * ns)
-    assert L.stokes_fmm_far_workspace_size(13, 1, 0, ctypes.byref(t), ctypes.byref(nb)) == A.STK_EINVAL
-    assert L.stokes_fmm_far_workspace_size(4, 1, 0, None, ctypes.byref(nb)) == A.STK_EINVAL
+    assert L.stokes_fmm_far_workspace_size(13, 1, 0, 0, 10, ctypes.byref(t), ctypes.byref(nb)) == A.STK_EINVAL
+    assert L.stokes_fmm_far_workspace_size(4, 1, 0, 0, 10, None, ctypes.byref(nb)) == A.STK_EINVAL
     bad = np.array([0, 2, 9], dtype=np.int32)
     t.depth_ptr = bad.ctypes.data
     t.max_depth = 2  # depth_ptr then ends at index 3, which is not nbox
-    assert L.stokes_fmm_far_workspace_size(4, 1, 0, ctypes.byref(t), ctypes.byref(nb)) == A.STK_EINVAL
+    assert L.stokes_fmm_far_workspace_size(4, 1, 0, 0, 10, ctypes.byref(t), ctypes.byref(nb)) == A.STK_EINVAL
     t.depth_ptr, t.max_depth = dptr.ctypes.data, 1
     t.root_size = float("nan")
-    assert L.stokes_fmm_far_workspace_size(4, 1, 0, ctypes.byref(t), ctypes.byref(nb)) == A.STK_EINVAL
+    assert L.stokes_fmm_far_workspace_size(4, 1, 0, 0, 10, ctypes.byref(t), ctypes.byref(nb)) == A.STK_EINVAL
     t.root_size = 1.0
     ws, x = ctypes.c_void_p(4096), ctypes.c_void_p(4096)
 
-    def call(n=10, f=x, phi=None, nrm=None, mu=1.0, uc=None, dc=None, wsb=0, p=4):
-        return L.stokes_fmm_far_eval(x, f, phi, nrm, x, n, ctypes.byref(t), p, 1, uc, dc, None, mu,
-                                     x, 0, ws, wsb, None)
+    def call(n=10, f=x, phi=None, nrm=None, mu=1.0, uc=None, dc=None, wsb=0, p=4, prec=0):
+        return L.stokes_fmm_far_eval(x, f, phi, nrm, x, n, ctypes.byref(t), p, 1, uc, dc, None,
+                                     prec, mu, x, 0, ws, wsb, None)
 
     assert call(n=0) == A.STK_OK
     assert call(n=-1) == A.STK_EINVAL
@@ -166,6 +166,7 @@ def test_fmm_far_entry_points_validated_on_host(L):
     assert call(mu=0.0) == A.STK_EINVAL
     assert call(p=1) == A.STK_EINVAL
     assert call(wsb=16) == A.STK_ENOMEM
+    assert call(prec=7) == A.STK_EINVAL
     keep = np.array([0, 1, 2, 9], dtype=np.int32)
     t.max_depth, t.depth_ptr = 2, keep.ctypes.data
     assert call(wsb=1 << 30) == A.STK_EINVAL  # a far field without operators

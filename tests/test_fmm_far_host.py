@@ -26,15 +26,17 @@ def case():
     return wl, fl, t
 
 
-def oracle_operators(wl, t, p, flux):
+def oracle_operators(wl, t, p, flux, rcond=1e-13):
     """The oracle's own pseudo-inverses per depth, as a dict and as the stacked
     arrays the passes take."""
     S = F.cube_surface(p)
     by_depth = {}
     for d in range(2, t["max_depth"] + 1):
         r = wl.tree.root_size / (1 << d) / 2
-        by_depth[d] = (F.pinv(F.upward_matrix(F.R_OUTER * r * S, F.R_INNER * r * S, wl.mu, flux)),
-                       F.pinv(F.stokeslet_matrix(F.R_INNER * r * S, F.R_OUTER * r * S, wl.mu)))
+        by_depth[d] = (F.pinv(F.upward_matrix(F.R_OUTER * r * S, F.R_INNER * r * S, wl.mu, flux),
+                              rcond),
+                       F.pinv(F.stokeslet_matrix(F.R_INNER * r * S, F.R_OUTER * r * S, wl.mu),
+                              rcond))
     U = np.stack([by_depth[d][0] for d in sorted(by_depth)])
     D = np.stack([by_depth[d][1] for d in sorted(by_depth)])
     return by_depth, U, D
@@ -145,3 +147,40 @@ def test_shallow_tree_has_no_far_field():
     acc, _ = H.far_eval(sp, f, None, None, w, t, 4, np.zeros((0, 1)), np.zeros((0, 1)),
                         out=np.ones((300, 3)), accumulate=True)
     assert np.all(acc == 1.0)
+
+
+@pytest.mark.parametrize("m2l", ["dense", "fft"])
+def test_mixed_passes_stay_within_fp32_of_the_oracle(case, m2l):
+    """The mixed form (FP32 evaluations on local coordinates, FP64
+    check-to-equivalent products) reproduces the oracle's far field at p = 4 to
+    FP32 accuracy, far below the FMM's truncation error there (2e-3)."""
+    wl, fl, t = case
+    p = 4
+    by_depth, U, D = oracle_operators(wl, t, p, True)
+    spec = ops.fmm_m2l_spectra(p, wl.mu, True) if m2l == "fft" else None
+    far, npass = H.far_eval(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, t, p, U, D, wl.mu, True,
+                            spec=spec, mixed=True)
+    ref = F.fmm_adaptive(wl.tree, wl.pts, wl.f, wl.phi, wl.nrm, wl.w, p, wl.mu, True,
+                         ops=by_depth, near=False)
+    # + the packing pass, and the spectra's rounding with Fourier-space M2L
+    assert npass == 3 + (4 + 3 * (m2l == "fft")) * (t["max_depth"] - 1) - 1 + (m2l == "fft")
+    assert _rel(far, ref) <= 1e-5, _rel(far, ref)
+
+
+def test_mixed_at_p6_with_operators_cut_at_fp32_resolution(case):
+    """At p = 6 the mixed form takes operators cut at rcond = 1e-7: it then
+    stays within 1e-5 of the FP64 passes on the same operators, and far field +
+    U-list sum approximates the direct sum as well as the FP64 form (4e-5)."""
+    wl, fl, t = case
+    p = 6
+    _, U, D = oracle_operators(wl, t, p, True, rcond=1e-7)
+    spec = ops.fmm_m2l_spectra(p, wl.mu, True)
+    f64, _ = H.far_eval(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, t, p, U, D, wl.mu, True, spec=spec)
+    f32, _ = H.far_eval(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, t, p, U, D, wl.mu, True, spec=spec,
+                        mixed=True)
+    assert _rel(f32, f64) <= 1e-5, _rel(f32, f64)
+    near = oracle.p2p(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, wl.tree.leaf_ptr, wl.tree.ulist_ptr,
+                      wl.tree.ulist_idx, 3, wl.mu)
+    direct = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts, wl.mu)
+    e64, e32 = _rel(f64 + near, direct), _rel(f32 + near, direct)
+    assert e64 <= 1e-4 and e32 <= 1.05 * e64, (e64, e32)

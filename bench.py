@@ -224,9 +224,9 @@ def _time_ms(fn, stream, flush, reps, warm=1):
 
 
 def run_fmm_far(wl, near, dev, stream, flush, p=4):
-    """The FMM's far field (stokes_fmm_far_eval, FP64 passes) on the near-field
-    workload's own octree: host set-up time (V, W and X lists; per-depth
-    operators), device time per call with dense and with Fourier-space M2L, and
+    """The FMM's far field (stokes_fmm_far_eval) on the near-field workload's own
+    octree: host set-up time (V, W and X lists; per-depth operators), device
+    time per call in FP64 and mixed precision with dense and Fourier-space M2L, and
     far field + the step's near field against the direct sum on 256 sampled
     targets (the FMM's approximation error at this p, not a parity figure)."""
     import torch
@@ -253,15 +253,18 @@ def run_fmm_far(wl, near, dev, stream, flush, p=4):
            "w_entries": int(fl.w_idx.size), "x_entries": int(fl.x_idx.size),
            "host_lists_s": lists_s, "host_operators_s": ops_s,
            "near_only_rel_l2": float(np.linalg.norm(un - ref) / np.linalg.norm(ref))}
-    for m2l in ("dense", "fft"):
-        plan = ops.FmmFarPlan(t, p=p, mu=wl.mu, flux=True, uc2e=U, dc2e=D, m2l=m2l)
-        far = torch.zeros_like(pts)
-        ms = _time_ms(lambda: plan(pts, f, phi, nrm, w, out=far), stream, flush, 2)
-        u = far.cpu().numpy()[tg] + un
-        res[m2l] = {"ms": ms, "rel_l2_vs_direct": float(np.linalg.norm(u - ref) /
-                                                        np.linalg.norm(ref))}
-        log(f"[fmm] {m2l}: {res[m2l]}")
-        del plan, far
+    for prec in ("fp64", "mixed"):
+        for m2l in ("dense", "fft"):
+            plan = ops.FmmFarPlan(t, p=p, mu=wl.mu, flux=True, uc2e=U, dc2e=D, m2l=m2l,
+                                  precision=prec)
+            far = torch.zeros_like(pts)
+            ms = _time_ms(lambda: plan(pts, f, phi, nrm, w, out=far), stream, flush, 2)
+            u = far.cpu().numpy()[tg] + un
+            key = f"{prec}_{m2l}"
+            res[key] = {"ms": ms, "rel_l2_vs_direct": float(np.linalg.norm(u - ref) /
+                                                            np.linalg.norm(ref))}
+            log(f"[fmm] {key}: {res[key]}")
+            del plan, far
     torch.cuda.empty_cache()
     return res
 
@@ -755,8 +758,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the other workloads (direct, batched, adjoint)")
     ap.add_argument("--fmm-far", action="store_true",
-                    help="also time the FMM's far field (FP64 passes, dense and Fourier-space "
-                         "M2L) on the near-field workload's octree")
+                    help="also time the FMM's far field (FP64 and mixed passes, dense and "
+                         "Fourier-space M2L) on the near-field workload's octree")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -184,3 +184,46 @@ def test_mixed_at_p6_with_operators_cut_at_fp32_resolution(case):
     direct = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts, wl.mu)
     e64, e32 = _rel(f64 + near, direct), _rel(f32 + near, direct)
     assert e64 <= 1e-4 and e32 <= 1.05 * e64, (e64, e32)
+
+
+def test_plan_set_up_on_the_host(case):
+    """FmmFarPlan's set-up is host logic: operator shapes are checked against
+    p and flux, the forms are validated, the mixed form at p >= 6 takes
+    operators cut at 1e-7, and the workspace query sizes every buffer of the
+    chosen form (FP32 points and spectra for the mixed Fourier-space form)."""
+    import torch
+    wl, fl, t = case
+    cpu = torch.device("cpu")
+    D = t["max_depth"] - 1
+    ns = 4 ** 3 - 2 ** 3
+    good = (np.zeros((D, 4 * ns, 3 * ns)), np.zeros((D, 3 * ns, 3 * ns)))
+    with pytest.raises(ValueError):
+        ops.FmmFarPlan(t, p=4, uc2e=np.zeros((D, 3 * ns, 3 * ns)), dc2e=good[1], device=cpu)
+    with pytest.raises(ValueError):
+        ops.FmmFarPlan(t, p=4, uc2e=good[0], dc2e=good[1], m2l="fast", device=cpu)
+    with pytest.raises(ValueError):
+        ops.FmmFarPlan(t, p=4, uc2e=good[0], dc2e=good[1], precision="fp16", device=cpu)
+    sizes = {}
+    for m2l in ("dense", "fft"):
+        for prec in ("fp64", "mixed"):
+            plan = ops.FmmFarPlan(t, p=4, uc2e=good[0], dc2e=good[1], m2l=m2l, precision=prec,
+                                  device=cpu)
+            sizes[m2l, prec] = plan.ws.numel()
+    M, n, nf = t["depth"].size, int(t["leaf_ptr"][-1]), 4 * 16 * 5
+    assert sizes["dense", "fp64"] >= 8 * M * (3 + 4 + 3) * ns
+    assert sizes["fft", "fp64"] - sizes["dense", "fp64"] >= 8 * M * (2 * nf * 7 + 3 * ns)
+    assert sizes["dense", "mixed"] >= 4 * 12 * n + 8 * M * 3 * ns + 4 * M * 7 * ns
+    assert sizes["fft", "mixed"] - sizes["dense", "mixed"] >= 4 * (343 * nf * 24 + M * 2 * nf * 7)
+    # the cut-off the mixed form takes at p = 6 (operators computed by the library)
+    seen = []
+    real = ops.fmm_operators
+    try:
+        ops.fmm_operators = lambda *a: (seen.append(a[-1]), real(*a))[1]
+        # the same boxes declared two deep: one depth of operators to compute
+        small = {**t, "max_depth": 2, "depth_ptr": np.concatenate(
+            [t["depth_ptr"][:3], [t["depth"].size]]).astype(np.int32)}
+        ops.FmmFarPlan(small, p=6, precision="mixed", device=cpu)
+        ops.FmmFarPlan(small, p=4, precision="mixed", device=cpu)
+    finally:
+        ops.fmm_operators = real
+    assert seen == [1e-7, 1e-13]

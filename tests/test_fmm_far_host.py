@@ -227,3 +227,29 @@ def test_plan_set_up_on_the_host(case):
     finally:
         ops.fmm_operators = real
     assert seen == [1e-7, 1e-13]
+
+
+def test_deep_tree_far_plus_near_is_the_fmm():
+    """A tree six deep (M2M and L2L chains of four translations, W and X lists
+    at several depths) where the U-list sum alone misses 93% of the velocity:
+    far field (Fourier-space M2L, FP64 and mixed) + the oracle's U-list sum
+    approximate the direct sum within the p = 4 FMM's error, and the mixed
+    form stays within FP32 accuracy of the FP64 one."""
+    oracle.build()
+    wl = W.p2p_workload(ncell=12, radius=10.0, n_wall_patch=6, max_leaf=16)
+    fl = O.far_lists(wl.tree)
+    t = ops.fmm_tree_arrays(fl.depth, fl.anchor, fl.parent, fl.leaf, wl.tree.leaf_ptr, fl.v_ptr,
+                            fl.v_idx, fl.w_ptr, fl.w_idx, fl.x_ptr, fl.x_idx, wl.tree.root_lo,
+                            wl.tree.root_size)
+    assert t["max_depth"] == 6 and fl.w_idx.size > 0 and fl.x_idx.size > 0
+    U, D = ops.fmm_operators(4, t["root_size"], t["max_depth"], wl.mu, True)
+    spec = ops.fmm_m2l_spectra(4, wl.mu, True)
+    f64, _ = H.far_eval(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, t, 4, U, D, wl.mu, True, spec=spec)
+    f32, _ = H.far_eval(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, t, 4, U, D, wl.mu, True, spec=spec,
+                        mixed=True)
+    near = oracle.p2p(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, wl.tree.leaf_ptr, wl.tree.ulist_ptr,
+                      wl.tree.ulist_idx, 3, wl.mu)
+    direct = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts, wl.mu)
+    assert _rel(near, direct) >= 0.5
+    assert _rel(f64 + near, direct) <= 3e-3
+    assert _rel(f32, f64) <= 1e-5

@@ -168,3 +168,35 @@ def test_m2l_inputs_rounded_to_fp32_stay_below_the_truncation_error(p, rcond, ra
         true = oracle.sldl(y, f, n, phi, w, x, 1.0).reshape(-1)
         trunc = _rel(u64, true)
         assert _rel(u32, u64) <= ratio * trunc, (_rel(u32, u64), trunc)
+
+
+def test_check_to_equivalent_products_need_fp64():
+    """Why the mixed far field keeps the check-to-equivalent products in FP64:
+    the operators' entries reach 1e3 (p = 4) to 6e7 (p = 6), so the same
+    products in FP32 move the field a V-list pair carries by 1e-3 at p = 4
+    (about the whole FMM's error there) and by more than the field itself at
+    p = 6, against 1e-5 or less for the FP32 M2L inputs."""
+    oracle.build()
+    rng = np.random.default_rng(77)
+    change = {}
+    for p in (4, 6):
+        S = F.cube_surface(p)
+        r = 0.1
+        uc2e = F.pinv(F.upward_matrix(F.R_OUTER * r * S, F.R_INNER * r * S, 1.0, True))
+        dc2e = F.pinv(F.stokeslet_matrix(F.R_INNER * r * S, F.R_OUTER * r * S, 1.0))
+        o = np.array([3.0, 1.0, -2.0]) * 2 * r
+        M = F.upward_matrix(o + F.R_INNER * r * S, F.R_INNER * r * S, 1.0, True)
+        y = rng.uniform(-r, r, (60, 3))
+        f, phi = rng.normal(size=(60, 3)), rng.normal(size=(60, 3))
+        n = rng.normal(size=(60, 3))
+        n /= np.linalg.norm(n, axis=1)[:, None]
+        chk = oracle.sldl(y, f, n, phi, np.full(60, 0.01), F.R_OUTER * r * S, 1.0).reshape(-1)
+        L2T = F.stokeslet_matrix(o + rng.uniform(-r, r, (40, 3)), o + F.R_OUTER * r * S, 1.0)
+
+        def field(dt):
+            up = (uc2e.astype(dt) @ chk.astype(dt)).astype(np.float64)
+            dn = (dc2e.astype(dt) @ (M @ up).astype(dt)).astype(np.float64)
+            return L2T @ dn
+        change[p] = _rel(field(np.float32), field(np.float64))
+    assert 3e-4 <= change[4] <= 1e-2, change
+    assert change[6] >= 1.0, change

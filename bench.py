@@ -225,20 +225,20 @@ def _time_ms(fn, stream, flush, reps, warm=1):
 
 def run_fmm_far(wl, near, dev, stream, flush, p=4):
     """The FMM's far field (stokes_fmm_far_eval) on the near-field workload's own
-    octree: host set-up time (V, W and X lists; per-depth operators), device
+    octree: host set-up time (the library's octree and V, W, X lists, the same
+    tree as the workload's U-lists; per-depth operators), device
     time per call in FP64 and mixed precision with dense and Fourier-space M2L, and
     far field + the step's near field against the direct sum on 256 sampled
     targets (the FMM's approximation error at this p, not a parity figure)."""
     import torch
     import oracle
     from paper_1909_11085_gb300 import ops
-    from synth import octree as O
     t0 = time.perf_counter()
-    fl = O.far_lists(wl.tree)
-    t = ops.fmm_tree_arrays(fl.depth, fl.anchor, fl.parent, fl.leaf, wl.tree.leaf_ptr, fl.v_ptr,
-                            fl.v_idx, fl.w_ptr, fl.w_idx, fl.x_ptr, fl.x_idx, wl.tree.root_lo,
-                            wl.tree.root_size)
+    tn = ops.octree(wl.pts, 256)  # the workload's leaf size
+    t = ops.fmm_tree_arrays(**ops.fmm_tree_args(tn))
     lists_s = time.perf_counter() - t0
+    if not np.array_equal(tn["leaf_ptr"], wl.tree.leaf_ptr):
+        raise RuntimeError("the library's octree differs from the workload's U-list tree")
     t0 = time.perf_counter()
     U, D = ops.fmm_operators(p, t["root_size"], t["max_depth"], wl.mu, True)
     ops_s = time.perf_counter() - t0
@@ -249,8 +249,8 @@ def run_fmm_far(wl, near, dev, stream, flush, p=4):
     ref = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts[tg], wl.mu)
     un = near.cpu().numpy()[tg]
     res = {"p": p, "boxes": int(t["depth"].size), "leaves": int(t["leaf_box"].size),
-           "max_depth": int(t["max_depth"]), "v_pairs": int(fl.v_idx.size),
-           "w_entries": int(fl.w_idx.size), "x_entries": int(fl.x_idx.size),
+           "max_depth": int(t["max_depth"]), "v_pairs": int(tn["v_idx"].size),
+           "w_entries": int(tn["w_idx"].size), "x_entries": int(tn["x_idx"].size),
            "host_lists_s": lists_s, "host_operators_s": ops_s,
            "near_only_rel_l2": float(np.linalg.norm(un - ref) / np.linalg.norm(ref))}
     for prec in ("fp64", "mixed"):

@@ -375,6 +375,42 @@ stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double 
                                const double *m2l_spectra, int32_t precision, double mu,
                                double *out, int32_t accumulate, void *workspace,
                                size_t workspace_bytes, void *stream);
+/* Octree and interaction lists of the FMM (host, built once per point set;
+ * Sec. 3.1, "Far evaluation" leaves the tree to the FMM library, so this is
+ * one reading of it).  The root is the points' bounding cube grown by 1e-9;
+ * a box splits into its 8 children while it holds more than max_leaf points
+ * (to depth 21), a point going to the child whose half-open box holds it and
+ * empty children dropped (no 2:1 balance).  Leaves are numbered depth-first in
+ * Morton order; perm [n] maps leaf-sorted position to caller index, leaf_ptr
+ * [nleaf + 1] gives each leaf's range.  U(B) [ulist_ptr/ulist_idx, over
+ * leaves]: the leaves whose closed box meets B's (B included), the input of
+ * stokes_p2p_leaflists.  Boxes (the leaves and their ancestors) are numbered
+ * depth by depth, Morton order within a depth: box_depth [nbox], box_anchor
+ * [nbox][3] (integer index at its depth), box_parent [nbox] (-1 for the root),
+ * box_leaf [nbox] (leaf number or -1); V, W and X [nbox + 1 pointers] are the
+ * lists of stk_fmm_tree.  All lists ascending.  stokes_octree_build allocates
+ * host memory owned by the returned handle (free it with
+ * stokes_octree_destroy); stokes_octree_info gives the sizes, and
+ * stokes_octree_export copies any of the arrays (NULL skips one) into caller
+ * buffers of those sizes.  Points must be finite; STK_EINVAL otherwise,
+ * STK_ENOMEM when host memory runs out. */
+typedef struct stk_octree stk_octree;
+typedef struct {
+  int64_t n;
+  int32_t nleaf, nbox, max_depth;
+  int64_t nulist, nv, nw, nx;
+  double root_lo[3];
+  double root_size;
+} stk_octree_info;
+stk_status stokes_octree_build(const double *pts, int64_t n, int32_t max_leaf, stk_octree **tree);
+stk_status stokes_octree_info(const stk_octree *tree, stk_octree_info *info);
+stk_status stokes_octree_export(const stk_octree *tree, int64_t *perm, int32_t *leaf_ptr,
+                                int32_t *ulist_ptr, int32_t *ulist_idx, int32_t *box_depth,
+                                int32_t *box_anchor, int32_t *box_parent, int32_t *box_leaf,
+                                int32_t *v_ptr, int32_t *v_idx, int32_t *w_ptr, int32_t *w_idx,
+                                int32_t *x_ptr, int32_t *x_idx);
+void stokes_octree_destroy(stk_octree *tree);
+
 /* Kernel spectra of M2L in Fourier space (host, FP64).  The upward
  * equivalent surface of a box and the downward check surface of a same-depth
  * box are the boundary of one p^3 lattice of spacing 2.1 r / (p - 1), so M2L

@@ -34,6 +34,7 @@ EXPORTS = [
     "stokes_near_patch_search", "stokes_near_search_workspace_size",
     "stokes_fmm_surface", "stokes_fmm_check_to_equiv", "stokes_fmm_kernel_matrix",
     "stokes_fmm_far_workspace_size", "stokes_fmm_far_eval", "stokes_fmm_m2l_spectra",
+    "stokes_octree_build", "stokes_octree_info", "stokes_octree_export", "stokes_octree_destroy",
 ]
 
 
@@ -51,6 +52,13 @@ class StkFmmTree(ctypes.Structure):
                                        "leaf_box", "leaf_ptr", "v_ptr", "v_idx", "w_ptr", "w_idx",
                                        "x_ptr", "x_idx")] + [
         ("root_lo", ctypes.c_double * 3), ("root_size", ctypes.c_double)]
+
+
+class StkOctreeInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nleaf", ctypes.c_int32), ("nbox", ctypes.c_int32),
+                ("max_depth", ctypes.c_int32), ("nulist", ctypes.c_int64), ("nv", ctypes.c_int64),
+                ("nw", ctypes.c_int64), ("nx", ctypes.c_int64), ("root_lo", ctypes.c_double * 3),
+                ("root_size", ctypes.c_double)]
 
 
 class StokesError(RuntimeError):
@@ -124,12 +132,18 @@ def lib():
             L.stokes_fmm_far_eval.argtypes = [p, p, p, p, p, i64, pt, i32, i32, p, p, p, i32, d, p,
                                               i32, p, sz, p]
             L.stokes_fmm_m2l_spectra.argtypes = [i32, d, i32, p]
+            L.stokes_octree_build.argtypes = [p, i64, i32, pp]
+            L.stokes_octree_info.argtypes = [p, ctypes.POINTER(StkOctreeInfo)]
+            L.stokes_octree_export.argtypes = [p] * 15
+            L.stokes_octree_destroy.argtypes = [p]
+            L.stokes_octree_destroy.restype = None
             L.stokes_graph_destroy.argtypes = [p]
             L.stokes_launch_count.restype = ctypes.c_int64
             for name in EXPORTS:
                 fn = getattr(L, name)
                 if name not in ("stokes_default_opts", "stokes_last_error", "stokes_version",
-                                "stokes_launch_count", "stokes_tile_config_count"):
+                                "stokes_launch_count", "stokes_tile_config_count",
+                                "stokes_octree_destroy"):
                     fn.restype = ctypes.c_int
             _lib = L
     return _lib

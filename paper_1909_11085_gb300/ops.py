@@ -487,6 +487,54 @@ def near_patch_search(nodes, npatch, trg, d_eps, q=10):
     return patch, uv, y, n, dist
 
 
+def octree(pts, max_leaf=256):
+    """Octree and interaction lists of a point set (host, stokes_octree_build).
+    pts: [n, 3] float64 (numpy or a tensor on any device).  Returns a dict of
+    numpy arrays: perm (leaf-sorted position -> caller index), leaf_ptr,
+    ulist_ptr / ulist_idx (the U-lists of P2PPlan), box_depth, box_anchor,
+    box_parent, box_leaf and the V, W, X lists, with root_lo, root_size and
+    max_depth; ops.fmm_tree_arrays(**fmm_tree_args(t)) gives the far field's
+    tree."""
+    import numpy as np
+    if isinstance(pts, torch.Tensor):
+        pts = pts.detach().cpu().numpy()
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    if pts.ndim != 2 or pts.shape[1] != 3:
+        raise ValueError("pts must have shape [n, 3]")
+    L = A.lib()
+    h = ctypes.c_void_p()
+    A.check(L.stokes_octree_build(pts.ctypes.data, pts.shape[0], int(max_leaf), ctypes.byref(h)))
+    try:
+        info = A.StkOctreeInfo()
+        A.check(L.stokes_octree_info(h, ctypes.byref(info)))
+        n, nl, nb = int(info.n), int(info.nleaf), int(info.nbox)
+        out = {"perm": np.empty(n, np.int64), "leaf_ptr": np.empty(nl + 1, np.int32),
+               "ulist_ptr": np.empty(nl + 1, np.int32),
+               "ulist_idx": np.empty(int(info.nulist), np.int32),
+               "box_depth": np.empty(nb, np.int32), "box_anchor": np.empty((nb, 3), np.int32),
+               "box_parent": np.empty(nb, np.int32), "box_leaf": np.empty(nb, np.int32),
+               "v_ptr": np.empty(nb + 1, np.int32), "v_idx": np.empty(int(info.nv), np.int32),
+               "w_ptr": np.empty(nb + 1, np.int32), "w_idx": np.empty(int(info.nw), np.int32),
+               "x_ptr": np.empty(nb + 1, np.int32), "x_idx": np.empty(int(info.nx), np.int32)}
+        keys = ("perm", "leaf_ptr", "ulist_ptr", "ulist_idx", "box_depth", "box_anchor",
+                "box_parent", "box_leaf", "v_ptr", "v_idx", "w_ptr", "w_idx", "x_ptr", "x_idx")
+        A.check(L.stokes_octree_export(h, *[ctypes.c_void_p(out[k].ctypes.data) for k in keys]))
+    finally:
+        L.stokes_octree_destroy(h)
+    out["root_lo"] = np.array(info.root_lo[:], dtype=np.float64)
+    out["root_size"] = float(info.root_size)
+    out["max_depth"] = int(info.max_depth)
+    return out
+
+
+def fmm_tree_args(t):
+    """The arguments of fmm_tree_arrays from an octree() result."""
+    return dict(depth=t["box_depth"], anchor=t["box_anchor"], parent=t["box_parent"],
+                box_leaf=t["box_leaf"], leaf_ptr=t["leaf_ptr"], v_ptr=t["v_ptr"],
+                v_idx=t["v_idx"], w_ptr=t["w_ptr"], w_idx=t["w_idx"], x_ptr=t["x_ptr"],
+                x_idx=t["x_idx"], root_lo=t["root_lo"], root_size=t["root_size"])
+
+
 _FMM_DEVICE_KEYS = ("depth", "anchor", "parent", "child_ptr", "box_leaf", "leaf_box", "leaf_ptr",
                     "v_ptr", "v_idx", "w_ptr", "w_idx", "x_ptr", "x_idx")
 

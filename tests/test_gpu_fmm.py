@@ -26,12 +26,17 @@ def lib():
 
 @pytest.fixture(scope="module")
 def case(lib):
+    """The tree from the library's own builder (equal to the generator's, which
+    the oracle reads)."""
     from paper_1909_11085_gb300 import ops
     wl = W.p2p_workload(ncell=6, radius=8.0, n_wall_patch=6, max_leaf=32)
+    tn = ops.octree(wl.pts, 32)
+    assert np.array_equal(tn["perm"], np.arange(wl.pts.shape[0]))
+    assert np.array_equal(tn["ulist_idx"], wl.tree.ulist_idx)
     fl = O.far_lists(wl.tree)
-    t = ops.fmm_tree_arrays(fl.depth, fl.anchor, fl.parent, fl.leaf, wl.tree.leaf_ptr, fl.v_ptr,
-                            fl.v_idx, fl.w_ptr, fl.w_idx, fl.x_ptr, fl.x_idx, wl.tree.root_lo,
-                            wl.tree.root_size)
+    assert np.array_equal(tn["v_idx"], fl.v_idx) and np.array_equal(tn["w_idx"], fl.w_idx)
+    t = ops.fmm_tree_arrays(**ops.fmm_tree_args(tn))
+    t["ulist_ptr"], t["ulist_idx"] = tn["ulist_ptr"], tn["ulist_idx"]
     return wl, t
 
 
@@ -96,8 +101,7 @@ def test_far_plus_near_is_the_fmm(lib, case):
     plan = ops.FmmFarPlan(t, p=p, mu=wl.mu, flux=True)
     pts, f, phi, nrm, w = cuda(wl.pts, wl.f, wl.phi, wl.nrm, wl.w)
     far = plan(pts, f, phi, nrm, w)
-    near = ops.P2PPlan(wl.pts.shape[0], wl.tree.leaf_ptr, wl.tree.ulist_ptr, wl.tree.ulist_idx, 3,
-                       "fp64")
+    near = ops.P2PPlan(wl.pts.shape[0], t["leaf_ptr"], t["ulist_ptr"], t["ulist_idx"], 3, "fp64")
     u = near(pts, f, phi, nrm, w, None, wl.mu, out=far.clone(), accumulate=True).cpu().numpy()
     direct = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts, wl.mu)
     ref = F.fmm_adaptive(wl.tree, wl.pts, wl.f, wl.phi, wl.nrm, wl.w, p, wl.mu, True)

@@ -14,6 +14,7 @@ PyTorch provides only device memory and the stream.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 
 import torch
@@ -92,7 +93,9 @@ class P2PPlan:
         self.kernels = int(kernels)
         self.opts = A.make_opts(precision, near_ratio)
         nb = ctypes.c_size_t(0)
-        with torch.cuda.device(device):
+        # the size query is host logic; a CPU device plans without a GPU
+        with (torch.cuda.device(device) if torch.device(device).type == "cuda"
+              else contextlib.nullcontext()):
             A.check(A.lib().stokes_p2p_workspace_size(self.n, self.nleaf, self.kernels,
                                                       ctypes.byref(self.opts), ctypes.byref(nb)))
         self.ws = A.workspace(nb.value, device)
@@ -719,3 +722,38 @@ class FmmFarPlan:
                 int(bool(accumulate)),
                 A.ptr(self.ws), self.ws.numel(), A.stream_ptr(self.device)))
         return out
+
+
+class FmmPlan:
+    """The FMM velocity of one point set (Sec. 3.1, "Far evaluation"): the
+    library's octree built once from the points, the U-list near field
+    (P2PPlan) and the far field on the same tree (FmmFarPlan).  Calls take
+    positions and densities in the tree's leaf order (perm[i] is the caller's
+    index of leaf-ordered point i) and return the velocity in that order.
+    kernels: 1 single layer (f), 2 double layer (phi, nrm), 3 both; the far
+    field's upward densities carry point sources whenever the double layer is
+    on."""
+
+    def __init__(self, pts, max_leaf=256, p=4, mu=1.0, kernels=3, near_precision="mixed",
+                 near_ratio=1.0, far_precision="fp64", m2l="dense", device=None):
+        self.tree = octree(pts, max_leaf)
+        self.perm = self.tree["perm"]
+        self.n = int(self.perm.size)
+        self.mu, self.kernels = float(mu), int(kernels)
+        if self.kernels not in (1, 2, 3):
+            raise ValueError("kernels must be 1, 2 or 3")
+        t = fmm_tree_arrays(**fmm_tree_args(self.tree))
+        self.near = P2PPlan(self.n, t["leaf_ptr"], self.tree["ulist_ptr"], self.tree["ulist_idx"],
+                            self.kernels, near_precision, near_ratio, device)
+        self.far = FmmFarPlan(t, p=p, mu=mu, flux=bool(self.kernels & 2), m2l=m2l,
+                              precision=far_precision, device=device)
+
+    def __call__(self, pts, f=None, phi=None, nrm=None, w=None, h=None, out=None):
+        if self.kernels & 1 and f is None:
+            raise ValueError("the single layer needs f")
+        if self.kernels & 2 and (phi is None or nrm is None):
+            raise ValueError("the double layer needs phi and nrm")
+        f = f if self.kernels & 1 else None
+        phi, nrm = (phi, nrm) if self.kernels & 2 else (None, None)
+        u = self.far(pts, f, phi, nrm, w, out=out)
+        return self.near(pts, f, phi, nrm, w, h, self.mu, out=u, accumulate=True)

@@ -72,3 +72,22 @@ def test_rejects_bad_arguments():
     assert b"finite" in L.stokes_last_error()
     with pytest.raises(ValueError):
         ops.octree(np.zeros((5, 2)))
+
+
+def test_fmm_plan_set_up_on_the_host():
+    """FmmPlan builds the library's octree once and plans the near and far
+    fields on it (host logic; a CPU device keeps every buffer on the host)."""
+    import torch
+    wl = W.p2p_workload(ncell=6, radius=8.0, n_wall_patch=6, max_leaf=32)
+    rng = np.random.default_rng(9)
+    shuffled = rng.permutation(wl.pts.shape[0])
+    plan = ops.FmmPlan(wl.pts[shuffled], max_leaf=32, p=4, mu=wl.mu, device=torch.device("cpu"))
+    assert np.array_equal(np.sort(plan.perm), np.arange(wl.pts.shape[0]))
+    # the tree of the shuffled points, in leaf order, is the workload's tree
+    assert np.array_equal(plan.tree["leaf_ptr"], wl.tree.leaf_ptr)
+    assert np.array_equal(plan.tree["ulist_idx"], wl.tree.ulist_idx)
+    assert plan.far.flux and plan.near.kernels == 3 and plan.near.nleaf == wl.tree.nleaf
+    sl_only = ops.FmmPlan(wl.pts, max_leaf=32, kernels=1, device=torch.device("cpu"))
+    assert not sl_only.far.flux
+    with pytest.raises(ValueError):
+        ops.FmmPlan(wl.pts, kernels=4, device=torch.device("cpu"))

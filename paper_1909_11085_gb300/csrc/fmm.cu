@@ -100,7 +100,8 @@ stk_status stokes_fmm_far_workspace_size(int32_t p, int32_t flux, int32_t fft_m2
   if (!bytes) return stk::report_error(STK_EINVAL, "bytes is NULL");
   const stk_status s = check_tree(tree);
   if (s != STK_OK) return s;
-  *bytes = stk::fmm::layout(tree->nbox, p, flux ? 4 : 3, fft_m2l != 0, precision == STK_MIXED, n)
+  *bytes = stk::fmm::layout(tree->nbox, p, flux ? 4 : 3, fft_m2l != 0, precision == STK_MIXED, n,
+                            tree->max_depth)
                .total;
   return STK_OK;
 }
@@ -131,7 +132,7 @@ stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double 
     return report_error(STK_EINVAL, "uc2e/dc2e is NULL");
   const int ns = stk::fmm::surface_count(p), nc = flux ? 4 : 3;
   const bool fft = m2l_spectra != nullptr, mixed = precision == STK_MIXED;
-  const stk::fmm::Layout L = stk::fmm::layout(tree->nbox, p, nc, fft, mixed, n);
+  const stk::fmm::Layout L = stk::fmm::layout(tree->nbox, p, nc, fft, mixed, n, tree->max_depth);
   if (!workspace || workspace_bytes < L.total) return report_error(STK_ENOMEM, "workspace too small");
   char *ws = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~(uintptr_t)255);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -161,6 +162,8 @@ stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double 
   P.box0 = P.box1 = 0;
   P.p = p;
   P.spec = m2l_spectra;
+  P.n_uc2e = stk::fmm::op_entries(p, nc, tree->max_depth, true);
+  P.n_dc2e = stk::fmm::op_entries(p, nc, tree->max_depth, false);
   stk::fmm::bind(P, ws, L, fft, mixed);
 
   k_fmm_setup<<<1, 32, 0, st>>>(P);

@@ -125,6 +125,9 @@ struct Pass {
   float *tw32;         // [G][2]
   float *spec32;       // as spec
   float *uhat32, *chat32, *m2l32;
+  float *chk32;             // [nbox][3 ns] check velocities (FP32 sums)
+  float *ops_hi, *ops_lo;   // uc2e then dc2e as FP32 pairs
+  int64_t n_uc2e, n_dc2e;   // entries of uc2e and dc2e
 };
 
 // Boundary points of the p^3 grid on [-1, 1]^3, i slowest, k fastest.
@@ -623,7 +626,7 @@ struct S2MF {
                          rad * P.surf32[3 * k + 2]};
     float u[3] = {0.0f, 0.0f, 0.0f};
     f_add_sources(P, off, xs, P.t.leaf_ptr[l], P.t.leaf_ptr[l + 1], u);
-    for (int q = 0; q < 3; ++q) P.chk[(size_t)b * 3 * P.ns + 3 * k + q] = u[q];
+    for (int q = 0; q < 3; ++q) P.chk32[(size_t)b * 3 * P.ns + 3 * k + q] = u[q];
   }
 };
 
@@ -648,20 +651,60 @@ struct M2MF {
       centre_offset(P, b, ch, off);
       f_add_equivalent(P, off, xs, rc, P.up32 + (size_t)ch * P.nc * P.ns, P.nc, u);
     }
-    for (int q = 0; q < 3; ++q) P.chk[(size_t)b * 3 * P.ns + 3 * k + q] = u[q];
+    for (int q = 0; q < 3; ++q) P.chk32[(size_t)b * 3 * P.ns + 3 * k + q] = u[q];
   }
 };
 
-// Check-to-equivalent, mixed: the FP64 row product rounded to FP32.
+// Check-to-equivalent, mixed.  The operators' entries are large (1e3 to 1e8)
+// and their row products cancel, so FP32 alone would not do; FP64 runs at
+// 1/64 of the FP32 rate here.  Each operator entry and check value is split
+// into an FP32 pair (hi + lo, 48 bits), products are formed exactly by FMA
+// (Dekker's product with FMA) and summed into a pair by Knuth's two-sum, which
+// keeps about 44 bits of the cancelling sum: the FP32 result is then correct
+// to FP32 accuracy for cancellation up to ~1e7.
+FMM_HD float fma_f(float a, float b, float c) {
+#if defined(__CUDA_ARCH__)
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+
+// Row i of (hi + lo) times x, x exact in FP32 (the check velocities of the
+// mixed passes are FP32 sums).
+FMM_HD float apply_row_df(const float *hi, const float *lo, int64_t i, const float *x, int cols) {
+  const float *ah = hi + (size_t)i * cols, *al = lo + (size_t)i * cols;
+  float sh = 0.0f, sl = 0.0f;
+  for (int j = 0; j < cols; ++j) {
+    const float p = ah[j] * x[j];
+    const float err = fma_f(al[j], x[j], fma_f(ah[j], x[j], -p));  // ah x = p + exact rest
+    const float t = sh + p, bv = t - sh;                          // two-sum of sh and p
+    sl += ((sh - (t - bv)) + (p - bv)) + err;
+    sh = t;
+  }
+  return sh + sl;
+}
+
+// OPSPLIT: e = operator entry (uc2e then dc2e, all depths); hi and lo parts.
+struct OPSPLIT {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int64_t nu = P.n_uc2e;
+    const double v = e < nu ? P.uc2e[e] : P.dc2e[e - nu];
+    const float h = (float)v;
+    P.ops_hi[e] = h;
+    P.ops_lo[e] = (float)(v - (double)h);
+  }
+};
+
 struct UC2EF {
   FMM_HD void operator()(const Pass &P, int64_t e) const {
     const int64_t rows = (int64_t)P.nc * P.ns;
     const int32_t b = P.box0 + (int32_t)(e / rows);
     const int64_t i = e % rows;
     FMM_CHECK(b, P.box1, "uc2e box");
-    const double *M = P.uc2e + (size_t)(P.depth - kFirstDepth) * rows * 3 * P.ns;
-    P.up32[(size_t)b * rows + i] =
-        (float)apply_row(M, i, P.chk + (size_t)b * 3 * P.ns, 3 * P.ns);
+    const size_t off = (size_t)(P.depth - kFirstDepth) * rows * 3 * P.ns;
+    P.up32[(size_t)b * rows + i] = apply_row_df(P.ops_hi + off, P.ops_lo + off, i,
+                                                P.chk32 + (size_t)b * 3 * P.ns, 3 * P.ns);
   }
 };
 
@@ -671,8 +714,9 @@ struct DC2EF {
     const int32_t b = P.box0 + (int32_t)(e / rows);
     const int64_t i = e % rows;
     FMM_CHECK(b, P.box1, "dc2e box");
-    const double *M = P.dc2e + (size_t)(P.depth - kFirstDepth) * rows * rows;
-    P.dn32[(size_t)b * rows + i] = (float)apply_row(M, i, P.chk + (size_t)b * rows, (int)rows);
+    const size_t off = (size_t)P.n_uc2e + (size_t)(P.depth - kFirstDepth) * rows * rows;
+    P.dn32[(size_t)b * rows + i] = apply_row_df(P.ops_hi + off, P.ops_lo + off, i,
+                                                P.chk32 + (size_t)b * rows, (int)rows);
   }
 };
 
@@ -714,7 +758,7 @@ struct DCHKF {
       centre_offset(P, b, pb, off);
       f_add_equivalent(P, off, xs, (float)(kOuter * 2.0 * r), P.dn32 + (size_t)pb * 3 * P.ns, 3, u);
     }
-    for (int q = 0; q < 3; ++q) P.chk[(size_t)b * 3 * P.ns + 3 * k + q] = u[q];
+    for (int q = 0; q < 3; ++q) P.chk32[(size_t)b * 3 * P.ns + 3 * k + q] = u[q];
   }
 };
 
@@ -754,12 +798,20 @@ struct L2TF {
 struct Layout {
   size_t surf, chk, up, dn, sidx, tw, uhat, chat, m2l;
   size_t ploc, qf, pf, nf, surf32, up32, dn32, tw32, spec32, uhat32, chat32, m2l32;
+  size_t chk32, ops_hi, ops_lo;
   size_t total;
 };
 
+// Entries of the per-depth operators (depths 2..max_depth).
+inline int64_t op_entries(int p, int nc, int max_depth, bool upward) {
+  const int64_t ns = surface_count(p), D = max_depth >= kFirstDepth ? max_depth - 1 : 0;
+  return D * (upward ? nc * ns : 3 * ns) * 3 * ns;
+}
+
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t n) {
+inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t n,
+                     int max_depth) {
   const int ns = surface_count(p);
   const size_t nf = (size_t)freq_count(p), B = (size_t)nbox, N = (size_t)n;
   Layout L;
@@ -771,12 +823,12 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t 
   };
   const size_t none = 0;
   L.surf = take(sizeof(double) * 3 * ns);
-  L.chk = take(sizeof(double) * 3 * ns * B);
   L.sidx = take(sizeof(int32_t) * 3 * ns);
-  L.up = L.dn = L.tw = L.uhat = L.chat = L.m2l = none;
+  L.chk = L.up = L.dn = L.tw = L.uhat = L.chat = L.m2l = none;
   L.ploc = L.qf = L.pf = L.nf = L.surf32 = L.up32 = L.dn32 = L.tw32 = L.spec32 = L.uhat32 =
-      L.chat32 = L.m2l32 = none;
+      L.chat32 = L.m2l32 = L.chk32 = L.ops_hi = L.ops_lo = none;
   if (!mixed) {
+    L.chk = take(sizeof(double) * 3 * ns * B);
     L.up = take(sizeof(double) * nc * ns * B);
     L.dn = take(sizeof(double) * 3 * ns * B);
     L.tw = take(sizeof(double) * 4 * p);
@@ -786,6 +838,11 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t 
       L.m2l = take(sizeof(double) * 3 * ns * B);
     }
   } else {
+    const size_t nops = (size_t)(op_entries(p, nc, max_depth, true) +
+                                 op_entries(p, nc, max_depth, false));
+    L.chk32 = take(sizeof(float) * 3 * ns * B);
+    L.ops_hi = take(sizeof(float) * nops);
+    L.ops_lo = take(sizeof(float) * nops);
     L.ploc = take(sizeof(float) * 3 * N);
     L.qf = take(sizeof(float) * 3 * N);
     L.pf = take(sizeof(float) * 3 * N);
@@ -810,9 +867,12 @@ inline void bind(Pass &P, char *ws, const Layout &L, bool fft, bool mixed) {
   auto d = [ws](size_t off) { return reinterpret_cast<double *>(ws + off); };
   auto f = [ws](size_t off) { return reinterpret_cast<float *>(ws + off); };
   P.surf = d(L.surf);
-  P.chk = d(L.chk);
   P.sidx = reinterpret_cast<int32_t *>(ws + L.sidx);
   P.mixed = mixed ? 1 : 0;
+  P.chk = mixed ? nullptr : d(L.chk);
+  P.chk32 = mixed ? f(L.chk32) : nullptr;
+  P.ops_hi = mixed ? f(L.ops_hi) : nullptr;
+  P.ops_lo = mixed ? f(L.ops_lo) : nullptr;
   P.up = mixed ? nullptr : d(L.up);
   P.dn = mixed ? nullptr : d(L.dn);
   P.tw = mixed ? nullptr : d(L.tw);
@@ -855,6 +915,7 @@ void far_field(Exec &ex, Pass P, const int32_t *depth_ptr, int32_t max_depth) {
   const bool mixed = P.mixed != 0;
   if (mixed) {
     ex.template run<PACK>(P, P.n);
+    ex.template run<OPSPLIT>(P, P.n_uc2e + P.n_dc2e);
     if (P.spec) ex.template run<SPEC32>(P, (int64_t)343 * freq_count(P.p) * 3 * P.nc * 2);
     ex.template run<S2MF>(P, (int64_t)P.t.nleaf * ns);
   } else {

@@ -151,9 +151,9 @@ def test_shallow_tree_has_no_far_field():
 
 @pytest.mark.parametrize("m2l", ["dense", "fft"])
 def test_mixed_passes_stay_within_fp32_of_the_oracle(case, m2l):
-    """The mixed form (FP32 evaluations on local coordinates, FP64
-    check-to-equivalent products) reproduces the oracle's far field at p = 4 to
-    FP32 accuracy, far below the FMM's truncation error there (2e-3)."""
+    """The mixed form (FP32 evaluations on local coordinates, check-to-equivalent
+    products in double-FP32 arithmetic) reproduces the oracle's far field at
+    p = 4 to FP32 accuracy, far below the FMM's truncation error there (2e-3)."""
     wl, fl, t = case
     p = 4
     by_depth, U, D = oracle_operators(wl, t, p, True)
@@ -162,8 +162,9 @@ def test_mixed_passes_stay_within_fp32_of_the_oracle(case, m2l):
                             spec=spec, mixed=True)
     ref = F.fmm_adaptive(wl.tree, wl.pts, wl.f, wl.phi, wl.nrm, wl.w, p, wl.mu, True,
                          ops=by_depth, near=False)
-    # + the packing pass, and the spectra's rounding with Fourier-space M2L
-    assert npass == 3 + (4 + 3 * (m2l == "fft")) * (t["max_depth"] - 1) - 1 + (m2l == "fft")
+    # + the packing and operator-splitting passes, and the spectra's rounding with
+    # Fourier-space M2L
+    assert npass == 4 + (4 + 3 * (m2l == "fft")) * (t["max_depth"] - 1) - 1 + (m2l == "fft")
     assert _rel(far, ref) <= 1e-5, _rel(far, ref)
 
 
@@ -212,7 +213,8 @@ def test_plan_set_up_on_the_host(case):
     M, n, nf = t["depth"].size, int(t["leaf_ptr"][-1]), 4 * 16 * 5
     assert sizes["dense", "fp64"] >= 8 * M * (3 + 4 + 3) * ns
     assert sizes["fft", "fp64"] - sizes["dense", "fp64"] >= 8 * M * (2 * nf * 7 + 3 * ns)
-    assert sizes["dense", "mixed"] >= 4 * 12 * n + 8 * M * 3 * ns + 4 * M * 7 * ns
+    nops = D * (4 * ns + 3 * ns) * 3 * ns  # both operators, as FP32 pairs
+    assert sizes["dense", "mixed"] >= 4 * 12 * n + 4 * M * (3 + 4 + 3) * ns + 8 * nops
     assert sizes["fft", "mixed"] - sizes["dense", "mixed"] >= 4 * (343 * nf * 24 + M * 2 * nf * 7)
     # the cut-off the mixed form takes at p = 6 (operators computed by the library)
     seen = []

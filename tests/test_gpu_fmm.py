@@ -82,9 +82,9 @@ def test_far_field_matches_the_oracle(lib, case, flux, kinds, m2l, precision, to
     assert _rel(far, ref) <= tol, _rel(far, ref)
     fft, mixed = m2l == "fft", precision == "mixed"
     # set-up + the passes; Fourier space adds 3 per depth; mixed adds the
-    # packing pass and, with spectra, their rounding
+    # packing and operator-splitting passes and, with spectra, their rounding
     assert launches == (1 + 2 + 4 * (t["max_depth"] - 1) - 1 + 3 * fft * (t["max_depth"] - 1)
-                        + mixed * (1 + fft))
+                        + mixed * (2 + fft))
     # accumulate
     import torch
     base = torch.full((wl.pts.shape[0], 3), 0.5, dtype=torch.float64, device="cuda")

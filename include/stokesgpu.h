@@ -347,8 +347,10 @@ stk_status stokes_fmm_kernel_matrix(const double *x, int32_t nx, const double *y
  * precision: STK_FP64 evaluates every pass in FP64; STK_MIXED packs points
  * (relative to their leaf's centre), densities, surfaces and spectra in FP32,
  * evaluates kernels and spectral products in FP32 with one FP64 difference of
- * box centres per pair of boxes, and keeps the check-to-equivalent products
- * in FP64 (operators cut at rcond ~ 1e-7 suit it best for p >= 6).  n must
+ * box centres per pair of boxes, and forms the check-to-equivalent products
+ * in double-FP32 arithmetic (operators split into FP32 pairs, exact FMA
+ * products, two-sum accumulation: ~44 bits, enough for their cancelling row
+ * sums); operators cut at rcond ~ 1e-7 suit it best for p >= 6.  n must
  * equal leaf_ptr[nleaf].
  * f or phi may be NULL (not both); nrm is needed with phi.  out [n][3] =
  * far field (accumulate != 0: out += far field).  2 <= p <= 12.  Boxes of

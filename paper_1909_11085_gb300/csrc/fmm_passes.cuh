@@ -499,7 +499,8 @@ using IFFT = IFFTT<double>;
 // FP32 evaluations on local coordinates: points relative to their leaf's
 // centre, surface points relative to their box's centre, and per pair of
 // boxes one FP64 difference of centres rounded to FP32, so that no FP64
-// operation runs per pair of points.  Check-to-equivalent operators stay FP64.
+// operation runs per pair of points.  The check-to-equivalent operators are
+// FP64 inputs, applied in double-FP32 arithmetic (below).
 
 FMM_HD float frsqrt(float x) {
 #if defined(__CUDA_ARCH__)

@@ -650,7 +650,7 @@ class FmmFarPlan:
     P2P sum over the same leaves gives the FMM velocity.  m2l = "dense"
     evaluates M2L kernel by kernel, "fft" in Fourier space (fmm_m2l_spectra);
     precision = "fp64" runs every pass in FP64, "mixed" the evaluations in FP32
-    on local coordinates with FP64 check-to-equivalent products.  The operators'
+    on local coordinates with double-FP32 check-to-equivalent products.  The operators'
     cut-off (rcond) defaults to 1e-13, and to 1e-7 (FP32's resolution) for the
     mixed form at p >= 6, where FP32 rounding of densities fitted beyond it
     would exceed the truncation error."""

@@ -333,6 +333,11 @@ stk_status stokes_fmm_kernel_matrix(const double *x, int32_t nx, const double *y
  *         touch B (closed boxes); W(B), B a leaf: boxes below B's same-depth
  *         neighbours that do not touch B while their parent does; X(B): the
  *         leaves A with B in W(A).
+ * colleague (optional, device [nbox][27]): the same-depth box at anchor +
+ * (dx, dy, dz) for dx, dy, dz in {-1, 0, 1} (entry (dx+1) 9 + (dy+1) 3 +
+ * (dz+1)), -1 where there is none; with it, Fourier-space M2L is blocked by
+ * parent (each neighbour child's spectrum read once for all the parent's
+ * children), without it summed per box over its V-list.
  * depth_ptr is a HOST array [max_depth + 2] (boxes of depth d are
  * [depth_ptr[d], depth_ptr[d+1])); every other array is in device memory and
  * must describe this one tree (its contents are not checked on the device).
@@ -364,6 +369,7 @@ typedef struct {
   const int32_t *depth_ptr;  /* HOST */
   const int32_t *depth, *anchor, *parent, *child_ptr, *box_leaf, *leaf_box, *leaf_ptr;
   const int32_t *v_ptr, *v_idx, *w_ptr, *w_idx, *x_ptr, *x_idx;
+  const int32_t *colleague;  /* optional [nbox][27]; see above */
   double root_lo[3];
   double root_size;
 } stk_fmm_tree;

@@ -50,7 +50,7 @@ class StkFmmTree(ctypes.Structure):
                 ("depth_ptr", ctypes.c_void_p)] + [
         (k, ctypes.c_void_p) for k in ("depth", "anchor", "parent", "child_ptr", "box_leaf",
                                        "leaf_box", "leaf_ptr", "v_ptr", "v_idx", "w_ptr", "w_idx",
-                                       "x_ptr", "x_idx")] + [
+                                       "x_ptr", "x_idx", "colleague")] + [
         ("root_lo", ctypes.c_double * 3), ("root_size", ctypes.c_double)]
 
 

@@ -81,6 +81,7 @@ stk::fmm::Tree device_tree(const stk_fmm_tree *t) {
   T.x_ptr = t->x_ptr;
   T.x_idx = t->x_idx;
   T.box_leaf = t->box_leaf;
+  T.colleague = t->colleague;
   for (int q = 0; q < 3; ++q) T.root_lo[q] = t->root_lo[q];
   T.root_size = t->root_size;
   return T;

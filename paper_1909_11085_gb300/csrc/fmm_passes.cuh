@@ -44,8 +44,10 @@
 
 #if defined(__CUDACC__)
 #define FMM_HD __host__ __device__ inline
+#define FMM_UNROLL _Pragma("unroll")
 #else
 #define FMM_HD inline
+#define FMM_UNROLL
 #endif
 
 // A host build with FMM_HOST_CHECKS checks every index before it is used.
@@ -81,6 +83,8 @@ struct Tree {
   const int32_t *leaf_ptr;   // [nleaf + 1] point ranges
   const int32_t *v_ptr, *v_idx, *w_ptr, *w_idx, *x_ptr, *x_idx;
   const int32_t *box_leaf;   // [nbox] leaf number or -1
+  const int32_t *colleague;  // [nbox][27] same-depth box at anchor + (dx,dy,dz), -1 if none
+                             // (index (dx+1) 9 + (dy+1) 3 + (dz+1)); NULL: V-list M2L
   double root_lo[3];
   double root_size;
 };
@@ -488,6 +492,92 @@ struct IFFTT {
     }
     const R inv = (R)(1.0 / ((double)G * G * G));
     for (int q = 0; q < 3; ++q) Bufs<R>::m2l(P)[(size_t)b * 3 * P.ns + 3 * k + q] = u[q] * inv;
+  }
+};
+
+// KMULP: Fourier-space M2L blocked by parent.  e = w * (box1 - box0) + (parent
+// - box0) over the parents of one depth (frequency-major, so that the threads
+// of a warp share w and read the same kernel spectra).  For each of the 26
+// neighbour directions of the parent, the source spectrum of each child of that
+// neighbour is read once and applied to every child of the parent it does not
+// touch, which enumerates exactly the V-lists of the parent's children (V(b):
+// children of the neighbours of b's parent that do not touch b).  Writes the
+// check spectra of all the parent's children at w.
+template <class R>
+struct KMULPT {
+  FMM_HD void operator()(const Pass &P, int64_t e) const {
+    const int nf = freq_count(P.p);
+    const int64_t np = P.box1 - P.box0;
+    const int w = (int)(e / np);
+    const int32_t par = P.box0 + (int32_t)(e % np);
+    FMM_CHECK(par, P.box1, "kmulp parent");
+    const int32_t c0 = P.t.child_ptr[par], c1 = P.t.child_ptr[par + 1];
+    if (c0 >= c1) return;
+    FMM_CHECK(c1 - c0 - 1, 8, "children of a parent");
+    double cc[3], r;
+    box_geom(P.t, c0, P.depth, cc, r);  // the children's half-width
+    const R sf = (R)(1.0 / r), sq = (R)(1.0 / (r * r));
+    const R *spec = Bufs<R>::spec(P);
+    const R *uhat = Bufs<R>::uhat(P);
+    // fixed-size loops over the (up to 8) children and (up to 4) density
+    // components keep the accumulators in registers
+    const int nt = c1 - c0;
+    int tpos[8][3];
+    FMM_UNROLL
+    for (int t = 0; t < 8; ++t)
+      for (int q = 0; q < 3; ++q)
+        tpos[t][q] = t < nt ? P.t.anchor[3 * (c0 + t) + q] - 2 * P.t.anchor[3 * par + q] : 0;
+    R acc[8][6];
+    FMM_UNROLL
+    for (int t = 0; t < 8; ++t)
+      for (int q = 0; q < 6; ++q) acc[t][q] = 0;
+    for (int dir = 0; dir < 27; ++dir) {
+      if (dir == 13) continue;  // the parent itself: its children touch each other
+      const int32_t Q = P.t.colleague[27 * (size_t)par + dir];
+      if (Q < 0) continue;
+      FMM_CHECK(Q, P.t.nbox, "colleague");
+      const int dx = dir / 9 - 1, dy = (dir / 3) % 3 - 1, dz = dir % 3 - 1;
+      for (int32_t a = P.t.child_ptr[Q]; a < P.t.child_ptr[Q + 1]; ++a) {
+        FMM_CHECK(a, P.t.nbox, "colleague child");
+        const int sx = 2 * dx + P.t.anchor[3 * a] - 2 * P.t.anchor[3 * Q];
+        const int sy = 2 * dy + P.t.anchor[3 * a + 1] - 2 * P.t.anchor[3 * Q + 1];
+        const int sz = 2 * dz + P.t.anchor[3 * a + 2] - 2 * P.t.anchor[3 * Q + 2];
+        const R *U = uhat + ((size_t)a * nf + w) * P.nc * 2;
+        R u[8];
+        FMM_UNROLL
+        for (int c = 0; c < 4; ++c) {
+          const R s = c < 3 ? sf : sq;
+          u[2 * c] = c < P.nc ? U[2 * c] * s : (R)0;
+          u[2 * c + 1] = c < P.nc ? U[2 * c + 1] * s : (R)0;
+        }
+        FMM_UNROLL
+        for (int t = 0; t < 8; ++t) {
+          if (t >= nt) continue;
+          const int ox = sx - tpos[t][0], oy = sy - tpos[t][1], oz = sz - tpos[t][2];
+          if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+          const int oi = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
+          FMM_CHECK(oi, 343, "kmulp offset");
+          const R *S = spec + ((size_t)oi * nf + w) * 3 * P.nc * 2;
+          FMM_UNROLL
+          for (int c = 0; c < 4; ++c) {
+            if (c >= P.nc) continue;
+            const R ur = u[2 * c], ui = u[2 * c + 1];
+            FMM_UNROLL
+            for (int i = 0; i < 3; ++i) {
+              const R kr = S[2 * (i * P.nc + c)], ki = S[2 * (i * P.nc + c) + 1];
+              acc[t][2 * i] += kr * ur - ki * ui;
+              acc[t][2 * i + 1] += kr * ui + ki * ur;
+            }
+          }
+        }
+      }
+    }
+    FMM_UNROLL
+    for (int t = 0; t < 8; ++t) {
+      if (t >= nt) continue;
+      R *o = Bufs<R>::chat(P) + ((size_t)(c0 + t) * nf + w) * 3 * 2;
+      for (int q = 0; q < 6; ++q) o[q] = acc[t][q];
+    }
   }
 };
 
@@ -907,6 +997,19 @@ FMM_HD void fill_setup(const Pass &P) {
     for (int q = 0; q < 3 * P.ns; ++q) P.surf32[q] = (float)P.surf[q];
 }
 
+// The spectral products of one depth: blocked by parent when the colleague
+// table is given, else per box over its V-list.
+template <class Exec, class R>
+void m2l_products(Exec &ex, Pass P, const int32_t *depth_ptr, int64_t per_box_count) {
+  if (P.t.colleague) {
+    P.box0 = depth_ptr[P.depth - 1];
+    P.box1 = depth_ptr[P.depth];
+    ex.template run<KMULPT<R>>(P, (int64_t)(P.box1 - P.box0) * freq_count(P.p));
+  } else {
+    ex.template run<KMULT<R>>(P, per_box_count);
+  }
+}
+
 // The pass sequence; Exec::run<F>(P, count) calls F on every output of a pass
 // (a kernel launch on the GPU).  depth_ptr is the host copy of the depth
 // ranges of the boxes.
@@ -944,7 +1047,7 @@ void far_field(Exec &ex, Pass P, const int32_t *depth_ptr, int32_t max_depth) {
     if (mixed) {
       if (P.spec) {
         ex.template run<UFFTT<float>>(P, nb * nf * P.nc);
-        ex.template run<KMULT<float>>(P, nb * nf);
+        m2l_products<Exec, float>(ex, P, depth_ptr, nb * nf);
         ex.template run<IFFTT<float>>(P, nb * ns);
       }
       ex.template run<DCHKF>(P, nb * ns);
@@ -952,7 +1055,7 @@ void far_field(Exec &ex, Pass P, const int32_t *depth_ptr, int32_t max_depth) {
     } else {
       if (P.spec) {
         ex.template run<UFFT>(P, nb * nf * P.nc);
-        ex.template run<KMUL>(P, nb * nf);
+        m2l_products<Exec, double>(ex, P, depth_ptr, nb * nf);
         ex.template run<IFFT>(P, nb * ns);
       }
       ex.template run<DCHK>(P, nb * ns);

@@ -539,7 +539,7 @@ def fmm_tree_args(t):
 
 
 _FMM_DEVICE_KEYS = ("depth", "anchor", "parent", "child_ptr", "box_leaf", "leaf_box", "leaf_ptr",
-                    "v_ptr", "v_idx", "w_ptr", "w_idx", "x_ptr", "x_idx")
+                    "v_ptr", "v_idx", "w_ptr", "w_idx", "x_ptr", "x_idx", "colleague")
 
 
 def fmm_tree_arrays(depth, anchor, parent, box_leaf, leaf_ptr, v_ptr, v_idx, w_ptr, w_idx, x_ptr,
@@ -598,6 +598,27 @@ def fmm_tree_arrays(depth, anchor, parent, box_leaf, leaf_ptr, v_ptr, v_idx, w_p
         raise ValueError("leaf_ptr must be non-decreasing from 0")
     if t["anchor"].shape != (M, 3):
         raise ValueError("anchor must have shape [nbox, 3]")
+    # same-depth neighbours: per depth, the boxes' 63-bit (i, j, k) keys sorted
+    anc = t["anchor"].astype(np.int64)
+    key = lambda a: ((a[:, 0].astype(np.uint64) << np.uint64(42)) |
+                     (a[:, 1].astype(np.uint64) << np.uint64(21)) | a[:, 2].astype(np.uint64))
+    coll = np.full((M, 27), -1, dtype=np.int64)
+    for d in range(max_depth + 1):
+        lo, hi = int(depth_ptr[d]), int(depth_ptr[d + 1])
+        if hi <= lo:
+            continue
+        kd = key(anc[lo:hi])
+        order = np.argsort(kd, kind="stable")
+        ks = kd[order]
+        m = 1 << d
+        for o, (dx, dy, dz) in enumerate(np.ndindex(3, 3, 3)):
+            nb = anc[lo:hi] + np.array([dx - 1, dy - 1, dz - 1])
+            inside = np.all((nb >= 0) & (nb < m), axis=1)
+            kq = key(np.where(inside[:, None], nb, 0))
+            pos = np.minimum(np.searchsorted(ks, kq), ks.size - 1)
+            found = inside & (ks[pos] == kq)
+            coll[lo:hi, o] = np.where(found, lo + order[pos], -1)
+    t["colleague"] = i32(coll)
     return t
 
 

@@ -35,16 +35,19 @@ def _p(a):
 
 
 def far_eval(pts, f, phi, nrm, w, tree, p, uc2e, dc2e, mu=1.0, flux=True, out=None,
-             accumulate=False, spec=None, mixed=False):
+             accumulate=False, spec=None, mixed=False, blocked=True):
     """tree: dict of the arrays of the library's stk_fmm_tree (numpy, host);
     spec: M2L kernel spectra (Fourier-space M2L) or None (dense M2L);
-    mixed: the FP32 evaluation passes instead of the FP64 ones."""
+    mixed: the FP32 evaluation passes instead of the FP64 ones; blocked: pass
+    the colleague table (parent-blocked spectral products) or not (V-lists)."""
     c = lambda a, t=np.float64: None if a is None else np.ascontiguousarray(a, dtype=t)
     i = lambda a: np.ascontiguousarray(a, dtype=np.int32)
     pts, f, phi, nrm, w = c(pts), c(f), c(phi), c(nrm), c(w)
     n = pts.shape[0]
     out = np.zeros((n, 3)) if out is None else out
-    T = {k: i(v) for k, v in tree.items() if k not in ("root_lo", "root_size", "max_depth")}
+    T = {k: i(v) for k, v in tree.items()
+         if k not in ("root_lo", "root_size", "max_depth", "ulist_ptr", "ulist_idx")}
+    colleague = T["colleague"] if blocked else None
     args = [T[k] for k in ("depth_ptr", "depth", "anchor", "parent", "child_ptr", "box_leaf",
                            "leaf_box", "leaf_ptr", "v_ptr", "v_idx", "w_ptr", "w_idx", "x_ptr",
                            "x_idx")]
@@ -54,7 +57,7 @@ def far_eval(pts, f, phi, nrm, w, tree, p, uc2e, dc2e, mu=1.0, flux=True, out=No
     r = L.fmm_host_far_eval(
         _p(pts), _p(f), _p(phi), _p(nrm), _p(w), ctypes.c_longlong(n),
         ctypes.c_int(T["depth"].size), ctypes.c_int(T["leaf_box"].size),
-        ctypes.c_int(int(tree["max_depth"])), *[_p(a) for a in args], _p(root_lo),
+        ctypes.c_int(int(tree["max_depth"])), *[_p(a) for a in args], _p(colleague), _p(root_lo),
         ctypes.c_double(float(tree["root_size"])), ctypes.c_int(p), ctypes.c_int(int(flux)),
         _p(uc2e), _p(dc2e), _p(spec), ctypes.c_int(int(bool(mixed))), ctypes.c_double(mu), _p(out),
         ctypes.c_int(int(accumulate)))

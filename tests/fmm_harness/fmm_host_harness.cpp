@@ -43,7 +43,8 @@ long long fmm_host_far_eval(const double *pts, const double *f, const double *ph
                             const int *box_leaf, const int *leaf_box, const int *leaf_ptr,
                             const int *v_ptr, const int *v_idx, const int *w_ptr,
                             const int *w_idx, const int *x_ptr, const int *x_idx,
-                            const double *root_lo, double root_size, int p, int flux,
+                            const int *colleague, const double *root_lo, double root_size,
+                            int p, int flux,
                             const double *uc2e, const double *dc2e, const double *spec,
                             int mixed, double mu, double *out, int accumulate) {
   g_bad = 0;
@@ -65,6 +66,7 @@ long long fmm_host_far_eval(const double *pts, const double *f, const double *ph
   T.w_idx = w_idx;
   T.x_ptr = x_ptr;
   T.x_idx = x_idx;
+  T.colleague = colleague;
   for (int q = 0; q < 3; ++q) T.root_lo[q] = root_lo[q];
   T.root_size = root_size;
   const int ns = stk::fmm::surface_count(p), nc = flux ? 4 : 3;

@@ -59,6 +59,13 @@ def test_tree_arrays(case):
         lo, hi = t["depth_ptr"][d], t["depth_ptr"][d + 1]
         assert np.all(t["depth"][lo:hi] == d)
     assert t["depth_ptr"][-1] == M and t["max_depth"] >= 3
+    # colleague[b][(dx+1) 9 + (dy+1) 3 + (dz+1)]: the same-depth box at anchor + d
+    where = {(int(t["depth"][b]),) + tuple(int(v) for v in t["anchor"][b]): b for b in range(M)}
+    for b in range(M):
+        a = t["anchor"][b]
+        for o, (dx, dy, dz) in enumerate(np.ndindex(3, 3, 3)):
+            want = where.get((int(t["depth"][b]), a[0] + dx - 1, a[1] + dy - 1, a[2] + dz - 1), -1)
+            assert t["colleague"][b, o] == want
 
 
 def test_tree_arrays_reject_a_box_order_the_passes_cannot_use(case):
@@ -86,28 +93,32 @@ def test_tree_arrays_reject_a_box_order_the_passes_cannot_use(case):
 
 @pytest.mark.parametrize("flux,kinds,m2l", [(True, "sldl", "dense"), (False, "sl", "dense"),
                                             (True, "dl", "dense"), (True, "sldl", "fft"),
-                                            (False, "sl", "fft")])
+                                            (False, "sl", "fft"), (True, "sldl", "fft-vlist")])
 def test_host_passes_match_the_oracle_far_field(case, flux, kinds, m2l):
     """Same operators on both sides: the passes reproduce the oracle's far
     field (upward, V/W/X lists, downward, L2T) up to rounding, with M2L dense
-    or in Fourier space (the library's kernel spectra); the Stokeslet-only
-    upward density (flux off) serves the single layer alone."""
+    or in Fourier space (the library's kernel spectra; products blocked by
+    parent through the colleague table, or summed per box over its V-list);
+    the Stokeslet-only upward density (flux off) serves the single layer
+    alone."""
     wl, fl, t = case
     p = 4
     by_depth, U, D = oracle_operators(wl, t, p, flux)
     f = wl.f if "sl" in kinds else None
     phi = wl.phi if kinds in ("sldl", "dl") else None
-    spec = ops.fmm_m2l_spectra(p, wl.mu, flux) if m2l == "fft" else None
-    far, npass = H.far_eval(wl.pts, f, phi, wl.nrm, wl.w, t, p, U, D, wl.mu, flux, spec=spec)
+    spec = ops.fmm_m2l_spectra(p, wl.mu, flux) if m2l.startswith("fft") else None
+    blocked = m2l != "fft-vlist"
+    far, npass = H.far_eval(wl.pts, f, phi, wl.nrm, wl.w, t, p, U, D, wl.mu, flux, spec=spec,
+                            blocked=blocked)
     ref = F.fmm_adaptive(wl.tree, wl.pts, f, phi, wl.nrm, wl.w, p, wl.mu, flux, ops=by_depth,
                          near=False)
     # the deepest depth has no M2M; Fourier-space M2L adds 3 passes per depth
-    assert npass == 2 + (4 + 3 * (m2l == "fft")) * (t["max_depth"] - 1) - 1
+    assert npass == 2 + (4 + 3 * (spec is not None)) * (t["max_depth"] - 1) - 1
     assert _rel(far, ref) <= 1e-10, _rel(far, ref)
     # accumulate adds to what out holds
     base = np.full_like(far, 0.25)
     acc, _ = H.far_eval(wl.pts, f, phi, wl.nrm, wl.w, t, p, U, D, wl.mu, flux, out=base.copy(),
-                        accumulate=True, spec=spec)
+                        accumulate=True, spec=spec, blocked=blocked)
     np.testing.assert_allclose(acc, base + far, rtol=0, atol=1e-15)
 
 

@@ -622,12 +622,20 @@ def fmm_tree_arrays(depth, anchor, parent, box_leaf, leaf_ptr, v_ptr, v_idx, w_p
     return t
 
 
-def fmm_operators(p, root_size, max_depth, mu=1.0, flux=True, rcond=1e-13):
+def fmm_operators(p, root_size, max_depth, mu=1.0, flux=True, rcond=1e-13, upward="per_depth"):
     """Check-to-equivalent operators of depths 2..max_depth (host, FP64):
     uc2e [max_depth - 1][(flux ? 4 : 3) ns][3 ns], dc2e [max_depth - 1][3 ns][3 ns].
     The Stokeslet is homogeneous of degree -1, so a Stokeslet-only operator of a
-    box of half-width r is r times that of half-width 1 (the cut-off is relative);
-    with point sources the upward operator is computed per depth."""
+    box of half-width r is r times that of half-width 1 (the cut-off is relative).
+    The point source is homogeneous of degree -2: with sources, upward =
+    "per_depth" takes the pseudo-inverse at every depth (the minimum-norm
+    densities), "scaled" takes one at half-width 1 and measures source
+    strengths in units of r (rows of sources scaled by r once more), an exact
+    check-to-equivalent operator at every depth from one decomposition (at
+    p = 6, one instead of one per depth at ~8 s each) whose far field differs
+    from the per-depth one by less than the truncation error."""
+    if upward not in ("per_depth", "scaled"):
+        raise ValueError('upward must be "per_depth" or "scaled"')
     import numpy as np
     ns = p ** 3 - (p - 2) ** 3
     nc = 4 if flux else 3
@@ -645,11 +653,16 @@ def fmm_operators(p, root_size, max_depth, mu=1.0, flux=True, rcond=1e-13):
         return out
 
     dc1 = c2e(1.0, False, False)
-    uc1 = None if flux else c2e(1.0, True, False)
+    uc1 = c2e(1.0, True, flux) if (not flux or upward == "scaled") else None
     for i, d in enumerate(range(2, int(max_depth) + 1)):
         r = float(root_size) / (1 << d) / 2
         dc[i] = r * dc1
-        uc[i] = c2e(r, True, True) if flux else r * uc1
+        if uc1 is None:
+            uc[i] = c2e(r, True, True)
+        else:
+            uc[i] = r * uc1
+            if flux:  # source rows: strength = r x (strength in units of r)
+                uc[i].reshape(ns, 4, 3 * ns)[:, 3, :] *= r
     return uc, dc
 
 
@@ -674,10 +687,11 @@ class FmmFarPlan:
     on local coordinates with double-FP32 check-to-equivalent products.  The operators'
     cut-off (rcond) defaults to 1e-13, and to 1e-7 (FP32's resolution) for the
     mixed form at p >= 6, where FP32 rounding of densities fitted beyond it
-    would exceed the truncation error."""
+    would exceed the truncation error.  upward = "scaled" derives every
+    depth's upward operator from one decomposition (see fmm_operators)."""
 
     def __init__(self, tree, p=4, mu=1.0, flux=True, uc2e=None, dc2e=None, rcond=None,
-                 device=None, m2l="dense", precision="fp64"):
+                 device=None, m2l="dense", precision="fp64", upward="per_depth"):
         import numpy as np
         self.device = device or torch.device("cuda")
         self.p, self.mu, self.flux = int(p), float(mu), bool(flux)
@@ -689,7 +703,7 @@ class FmmFarPlan:
             rcond = 1e-7 if (precision == "mixed" and self.p >= 6) else 1e-13
         if uc2e is None or dc2e is None:
             uc2e, dc2e = fmm_operators(self.p, tree["root_size"], tree["max_depth"], self.mu,
-                                       self.flux, rcond)
+                                       self.flux, rcond, upward)
         ns, nc, D = self.p ** 3 - (self.p - 2) ** 3, 4 if self.flux else 3, max(
             int(tree["max_depth"]) - 1, 0)
         uc2e, dc2e = np.asarray(uc2e, dtype=np.float64), np.asarray(dc2e, dtype=np.float64)

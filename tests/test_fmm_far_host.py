@@ -266,3 +266,31 @@ def test_deep_tree_far_plus_near_is_the_fmm():
     assert _rel(near, direct) >= 0.5
     assert _rel(f64 + near, direct) <= 3e-3
     assert _rel(f32, f64) <= 1e-5
+
+
+def test_scaled_upward_operators(case):
+    """upward="scaled" derives every depth's upward operator from one
+    pseudo-inverse: it reproduces the check velocities at every depth as the
+    per-depth operator does (A_r uc2e_r = the same projector), and the FMM it
+    gives stays within the truncation error of the per-depth one."""
+    wl, fl, t = case
+    p = 4
+    Us, Ds = ops.fmm_operators(p, t["root_size"], t["max_depth"], wl.mu, True, upward="scaled")
+    Up, Dp = ops.fmm_operators(p, t["root_size"], t["max_depth"], wl.mu, True)
+    np.testing.assert_array_equal(Ds, Dp)
+    S = F.cube_surface(p)
+    rng = np.random.default_rng(4)
+    for i, d in enumerate(range(2, t["max_depth"] + 1)):
+        r = t["root_size"] / (1 << d) / 2
+        A = F.upward_matrix(F.R_OUTER * r * S, F.R_INNER * r * S, wl.mu, True)
+        chk = A @ rng.normal(size=A.shape[1])  # a check velocity in the range
+        assert _rel(A @ (Us[i] @ chk), chk) <= 1e-8
+        assert _rel(A @ (Up[i] @ chk), chk) <= 1e-8
+    spec = ops.fmm_m2l_spectra(p, wl.mu, True)
+    fs, _ = H.far_eval(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, t, p, Us, Ds, wl.mu, True, spec=spec)
+    fp, _ = H.far_eval(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, t, p, Up, Dp, wl.mu, True, spec=spec)
+    near = oracle.p2p(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, wl.tree.leaf_ptr, wl.tree.ulist_ptr,
+                      wl.tree.ulist_idx, 3, wl.mu)
+    direct = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts, wl.mu)
+    es, ep = _rel(fs + near, direct), _rel(fp + near, direct)
+    assert _rel(fs, fp) <= ep and es <= 1.2 * ep, (_rel(fs, fp), es, ep)

@@ -231,7 +231,7 @@ def test_plan_set_up_on_the_host(case):
     seen = []
     real = ops.fmm_operators
     try:
-        ops.fmm_operators = lambda *a: (seen.append(a[-1]), real(*a))[1]
+        ops.fmm_operators = lambda *a: (seen.append(a[5]), real(*a))[1]  # a[5]: rcond
         # the same boxes declared two deep: one depth of operators to compute
         small = {**t, "max_depth": 2, "depth_ptr": np.concatenate(
             [t["depth_ptr"][:3], [t["depth"].size]]).astype(np.int32)}

@@ -1,7 +1,9 @@
 // fmm.cu -- the far field of the kernel-independent FMM on the GPU (Sec. 3.1,
 // "Far evaluation"): the passes of fmm_passes.cuh, one grid-stride launch per
-// pass and depth on the caller's stream, FP64 throughout.  The near field is
-// the U-list P2P sum (stokes_p2p_leaflists); the two together are the FMM.
+// pass and depth on the caller's stream, in FP64 or in the mixed form (FP32
+// evaluations and spectra, double-FP32 check-to-equivalent products), with M2L
+// dense or in Fourier space.  The near field is the U-list P2P sum
+// (stokes_p2p_leaflists); the two together are the FMM.
 #include <cmath>
 
 #include "../../include/stokesgpu.h"

@@ -31,11 +31,15 @@
 //          given the kernel spectra, in Fourier space: UFFT (spectrum of each
 //          box's upward density on the zero-padded (2p)^3 lattice, a direct
 //          sum over its surface points, the only non-zero lattice values),
-//          KMUL (per box and frequency, the V-list sum of spectrum products)
-//          and IFFT (back at the box's own surface points);
+//          KMULP (per parent and frequency, blocked over the parent's
+//          neighbours' children, given the colleague table; else KMUL, per
+//          box and frequency over its V-list) and IFFT (back at the box's own
+//          surface points);
 //   DC2E   downward check -> downward equivalent density, depth by depth;
 //   L2T    downward density of the point's leaf + W-list upward densities
 //          -> velocity at every point.
+// Each step exists in FP64 and in a mixed form (FP32 evaluations on local
+// coordinates, double-FP32 check-to-equivalent products; see "mixed" below).
 #pragma once
 
 #include <cmath>

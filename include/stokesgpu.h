@@ -396,7 +396,7 @@ stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double 
  * depth by depth, Morton order within a depth: box_depth [nbox], box_anchor
  * [nbox][3] (integer index at its depth), box_parent [nbox] (-1 for the root),
  * box_leaf [nbox] (leaf number or -1); V, W and X [nbox + 1 pointers] are the
- * lists of stk_fmm_tree.  All lists ascending.  stokes_octree_build allocates
+ * lists of stk_fmm_tree, and colleague [nbox][27] its same-depth neighbours.  All lists ascending.  stokes_octree_build allocates
  * host memory owned by the returned handle (free it with
  * stokes_octree_destroy); stokes_octree_info gives the sizes, and
  * stokes_octree_export copies any of the arrays (NULL skips one) into caller
@@ -416,7 +416,7 @@ stk_status stokes_octree_export(const stk_octree *tree, int64_t *perm, int32_t *
                                 int32_t *ulist_ptr, int32_t *ulist_idx, int32_t *box_depth,
                                 int32_t *box_anchor, int32_t *box_parent, int32_t *box_leaf,
                                 int32_t *v_ptr, int32_t *v_idx, int32_t *w_ptr, int32_t *w_idx,
-                                int32_t *x_ptr, int32_t *x_idx);
+                                int32_t *x_ptr, int32_t *x_idx, int32_t *colleague);
 void stokes_octree_destroy(stk_octree *tree);
 
 /* Kernel spectra of M2L in Fourier space (host, FP64).  The upward

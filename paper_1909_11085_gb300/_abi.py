@@ -134,7 +134,7 @@ def lib():
             L.stokes_fmm_m2l_spectra.argtypes = [i32, d, i32, p]
             L.stokes_octree_build.argtypes = [p, i64, i32, pp]
             L.stokes_octree_info.argtypes = [p, ctypes.POINTER(StkOctreeInfo)]
-            L.stokes_octree_export.argtypes = [p] * 15
+            L.stokes_octree_export.argtypes = [p] * 16
             L.stokes_octree_destroy.argtypes = [p]
             L.stokes_octree_destroy.restype = None
             L.stokes_graph_destroy.argtypes = [p]

@@ -70,6 +70,7 @@ struct stk_octree {
   std::vector<int64_t> leaf_anchor;  // [nleaf][3]
   std::vector<int32_t> box_depth, box_anchor, box_parent, box_leaf;
   std::vector<int32_t> v_ptr, v_idx, w_ptr, w_idx, x_ptr, x_idx;
+  std::vector<int32_t> colleague;  // [nbox][27]
 };
 
 namespace {
@@ -274,6 +275,12 @@ stk_status build(const double *pts, int64_t n, int32_t max_leaf, stk_octree &T) 
   csr(V, T.v_ptr, T.v_idx);
   csr(W, T.w_ptr, T.w_idx);
   csr(X, T.x_ptr, T.x_idx);
+  T.colleague.resize(27 * (size_t)M);
+  for (int32_t b = 0; b < M; ++b)
+    for (int o = 0; o < 27; ++o)
+      T.colleague[27 * (size_t)b + o] =
+          find(box[b].depth, box[b].a[0] + o / 9 - 1, box[b].a[1] + (o / 3) % 3 - 1,
+               box[b].a[2] + o % 3 - 1);
   T.n = n;
   return STK_OK;
 }
@@ -331,7 +338,7 @@ stk_status stokes_octree_export(const stk_octree *t, int64_t *perm, int32_t *lea
                                 int32_t *ulist_ptr, int32_t *ulist_idx, int32_t *box_depth,
                                 int32_t *box_anchor, int32_t *box_parent, int32_t *box_leaf,
                                 int32_t *v_ptr, int32_t *v_idx, int32_t *w_ptr, int32_t *w_idx,
-                                int32_t *x_ptr, int32_t *x_idx) {
+                                int32_t *x_ptr, int32_t *x_idx, int32_t *colleague) {
   if (!t) return stk::report_error(STK_EINVAL, "tree is NULL");
   copy_out(t->perm, perm);
   copy_out(t->leaf_ptr, leaf_ptr);
@@ -347,6 +354,7 @@ stk_status stokes_octree_export(const stk_octree *t, int64_t *perm, int32_t *lea
   copy_out(t->w_idx, w_idx);
   copy_out(t->x_ptr, x_ptr);
   copy_out(t->x_idx, x_idx);
+  copy_out(t->colleague, colleague);
   return STK_OK;
 }
 

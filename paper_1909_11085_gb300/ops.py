@@ -495,9 +495,9 @@ def octree(pts, max_leaf=256):
     pts: [n, 3] float64 (numpy or a tensor on any device).  Returns a dict of
     numpy arrays: perm (leaf-sorted position -> caller index), leaf_ptr,
     ulist_ptr / ulist_idx (the U-lists of P2PPlan), box_depth, box_anchor,
-    box_parent, box_leaf and the V, W, X lists, with root_lo, root_size and
-    max_depth; ops.fmm_tree_arrays(**fmm_tree_args(t)) gives the far field's
-    tree."""
+    box_parent, box_leaf, the V, W, X lists and each box's 27 same-depth
+    neighbours (colleague), with root_lo, root_size and max_depth;
+    ops.fmm_tree_arrays(**fmm_tree_args(t)) gives the far field's tree."""
     import numpy as np
     if isinstance(pts, torch.Tensor):
         pts = pts.detach().cpu().numpy()
@@ -518,9 +518,11 @@ def octree(pts, max_leaf=256):
                "box_parent": np.empty(nb, np.int32), "box_leaf": np.empty(nb, np.int32),
                "v_ptr": np.empty(nb + 1, np.int32), "v_idx": np.empty(int(info.nv), np.int32),
                "w_ptr": np.empty(nb + 1, np.int32), "w_idx": np.empty(int(info.nw), np.int32),
-               "x_ptr": np.empty(nb + 1, np.int32), "x_idx": np.empty(int(info.nx), np.int32)}
+               "x_ptr": np.empty(nb + 1, np.int32), "x_idx": np.empty(int(info.nx), np.int32),
+               "colleague": np.empty((nb, 27), np.int32)}
         keys = ("perm", "leaf_ptr", "ulist_ptr", "ulist_idx", "box_depth", "box_anchor",
-                "box_parent", "box_leaf", "v_ptr", "v_idx", "w_ptr", "w_idx", "x_ptr", "x_idx")
+                "box_parent", "box_leaf", "v_ptr", "v_idx", "w_ptr", "w_idx", "x_ptr", "x_idx",
+                "colleague")
         A.check(L.stokes_octree_export(h, *[ctypes.c_void_p(out[k].ctypes.data) for k in keys]))
     finally:
         L.stokes_octree_destroy(h)

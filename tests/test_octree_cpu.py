@@ -53,9 +53,11 @@ def test_matches_the_generator(name):
         assert have.shape == np.asarray(want).shape and np.array_equal(have, want), key
     assert got["root_size"] == ref.root_size
     assert got["max_depth"] == int(fl.depth.max())
-    # the far field's tree arrays accept it as they accept the generator's
+    # the far field's tree arrays accept it as they accept the generator's, and
+    # derive the same colleague table the library exports
     t = ops.fmm_tree_arrays(**ops.fmm_tree_args(got))
     assert t["max_depth"] == got["max_depth"]
+    np.testing.assert_array_equal(t["colleague"], got["colleague"])
 
 
 def test_rejects_bad_arguments():

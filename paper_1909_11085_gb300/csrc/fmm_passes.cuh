@@ -765,19 +765,43 @@ FMM_HD float fma_f(float a, float b, float c) {
 #endif
 }
 
+// Rounded FP32 operations the compiler may not fuse (the two-sum below is
+// exact only if every product and sum is rounded on its own).
+FMM_HD float mul_rn(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+FMM_HD float add_rn(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+FMM_HD float sub_rn(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+
 // Row i of (hi + lo) times x, x exact in FP32 (the check velocities of the
 // mixed passes are FP32 sums).
 FMM_HD float apply_row_df(const float *hi, const float *lo, int64_t i, const float *x, int cols) {
   const float *ah = hi + (size_t)i * cols, *al = lo + (size_t)i * cols;
   float sh = 0.0f, sl = 0.0f;
   for (int j = 0; j < cols; ++j) {
-    const float p = ah[j] * x[j];
+    const float p = mul_rn(ah[j], x[j]);
     const float err = fma_f(al[j], x[j], fma_f(ah[j], x[j], -p));  // ah x = p + exact rest
-    const float t = sh + p, bv = t - sh;                          // two-sum of sh and p
-    sl += ((sh - (t - bv)) + (p - bv)) + err;
+    const float t = add_rn(sh, p), bv = sub_rn(t, sh);            // two-sum of sh and p
+    sl = add_rn(sl, add_rn(add_rn(sub_rn(sh, sub_rn(t, bv)), sub_rn(p, bv)), err));
     sh = t;
   }
-  return sh + sl;
+  return add_rn(sh, sl);
 }
 
 // OPSPLIT: e = operator entry (uc2e then dc2e, all depths); hi and lo parts.

@@ -354,8 +354,9 @@ stk_status stokes_fmm_kernel_matrix(const double *x, int32_t nx, const double *y
  * evaluates kernels and spectral products in FP32 with one FP64 difference of
  * box centres per pair of boxes, and forms the check-to-equivalent products
  * in double-FP32 arithmetic (operators split into FP32 pairs, exact FMA
- * products, two-sum accumulation: ~44 bits, enough for their cancelling row
- * sums); operators cut at rcond ~ 1e-7 suit it best for p >= 6.  n must
+ * products, two-sum accumulation: relative error about u + n u^2 k for a row
+ * sum cancelling by k, u = 2^-24); operators cut at rcond ~ 1e-7 keep k small
+ * enough for p >= 6.  n must
  * equal leaf_ptr[nleaf].
  * f or phi may be NULL (not both); nrm is needed with phi.  out [n][3] =
  * far field (accumulate != 0: out += far field).  2 <= p <= 12.  Boxes of

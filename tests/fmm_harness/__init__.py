@@ -27,7 +27,18 @@ def lib():
         _lib = ctypes.CDLL(LIB)
         _lib.fmm_host_far_eval.restype = ctypes.c_longlong
         _lib.fmm_host_message.restype = ctypes.c_char_p
+        _lib.fmm_host_row_df.restype = ctypes.c_float
     return _lib
+
+
+def row_df(a, x):
+    """The mixed form's row product of an FP64 row a (split into FP32 hi + lo)
+    with an FP32 vector x."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    hi = a.astype(np.float32)
+    lo = (a - hi.astype(np.float64)).astype(np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    return float(lib().fmm_host_row_df(_p(hi), _p(lo), _p(x), ctypes.c_int(a.size)))
 
 
 def _p(a):

@@ -35,6 +35,11 @@ extern "C" {
 
 const char *fmm_host_message(void) { return g_msg; }
 
+// One row product of the mixed check-to-equivalent step: (hi + lo) . x.
+float fmm_host_row_df(const float *hi, const float *lo, const float *x, int n) {
+  return stk::fmm::apply_row_df(hi, lo, 0, x, n);
+}
+
 // Returns the number of passes run (>= 0), or -1 when an index check failed.
 long long fmm_host_far_eval(const double *pts, const double *f, const double *phi,
                             const double *nrm, const double *w, long long n, int nbox, int nleaf,

@@ -294,3 +294,28 @@ def test_scaled_upward_operators(case):
     direct = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts, wl.mu)
     es, ep = _rel(fs + near, direct), _rel(fp + near, direct)
     assert _rel(fs, fp) <= ep and es <= 1.2 * ep, (_rel(fs, fp), es, ep)
+
+
+def test_double_fp32_row_product_carries_the_cancellation():
+    """The mixed form's check-to-equivalent row product (operator entry split
+    into an FP32 pair, exact FMA products, two-sum accumulation) meets the
+    double-FP32 bound |error| <= 2 u |a.x| + 4 n u^2 sum |a_j x_j| (u = 2^-24):
+    sums cancelling by a factor k come out to ~u + n u^2 k relative (1e-7 at
+    k = 3e4, a few 1e-6 at k = 1e7), where a plain FP32 dot product loses every
+    digit beyond k ~ 1e7."""
+    rng = np.random.default_rng(17)
+    u = 2.0 ** -24
+    for cancel in (1e2, 1e5, 1e8):
+        for _ in range(20):
+            n = 456
+            x = rng.normal(size=n).astype(np.float32)
+            xd = x.astype(np.float64)
+            a = rng.normal(size=n) * cancel
+            a -= (a @ xd) / (xd @ xd) * xd  # remove most of a's projection on x
+            a += rng.normal() * xd / (xd @ xd)
+            exact = float(np.sum(a.astype(np.longdouble) * xd.astype(np.longdouble)))
+            mag = float(np.sum(np.abs(a * xd)))
+            got = H.row_df(a, x)
+            assert abs(got - exact) <= 2 * u * abs(exact) + 4 * n * u * u * mag, (cancel, got, exact)
+    plain = float(np.dot(a.astype(np.float32), x))
+    assert abs(plain - exact) > abs(exact)  # at the strongest cancellation

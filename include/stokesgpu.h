@@ -361,8 +361,8 @@ stk_status stokes_fmm_kernel_matrix(const double *x, int32_t nx, const double *y
  * f or phi may be NULL (not both); nrm is needed with phi.  out [n][3] =
  * far field (accumulate != 0: out += far field).  2 <= p <= 12.  Boxes of
  * depth < 2 have no far field; a tree of max_depth < 2 gives zero.  Launches
- * 2 + 4 (max_depth - 1) kernels (3 more per depth with m2l_spectra) on the
- * caller's stream; allocates nothing;
+ * 2 + 4 (max_depth - 1) kernels (3 more per depth with m2l_spectra; 2 more
+ * with STK_MIXED, 3 with both) on the caller's stream; allocates nothing;
  * workspace from stokes_fmm_far_workspace_size.  STK_EINVAL for bad sizes,
  * NULL arrays or a depth_ptr that does not run from 0 to nbox. */
 typedef struct {

@@ -48,9 +48,12 @@
 
 #if defined(__CUDACC__)
 #define FMM_HD __host__ __device__ inline
-#define FMM_UNROLL _Pragma("unroll")
 #else
 #define FMM_HD inline
+#endif
+#if defined(__CUDA_ARCH__)
+#define FMM_UNROLL _Pragma("unroll")
+#else
 #define FMM_UNROLL
 #endif
 

@@ -125,8 +125,8 @@ struct Pass {
   double *uhat;        // [nbox][nfreq][nc] complex
   double *chat;        // [nbox][nfreq][3] complex
   double *m2l;         // [nbox][3 ns] M2L part of the downward check velocity
-  // mixed precision (mixed != 0): FP32 copies; the FP64 up, dn, tw, uhat, chat
-  // and m2l are then unused
+  // mixed precision (mixed != 0): FP32 copies; the FP64 chk, up, dn, tw, uhat,
+  // chat and m2l are then unused (NULL)
   int32_t mixed;
   float *ploc;         // [n][3] point minus its leaf's centre
   float *qf, *pf, *nf; // [n][3] w f / (8 pi mu), w phi 6 / (8 pi), normals (NULL if unused)

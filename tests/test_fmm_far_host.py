@@ -160,18 +160,19 @@ def test_shallow_tree_has_no_far_field():
     assert np.all(acc == 1.0)
 
 
-@pytest.mark.parametrize("m2l", ["dense", "fft"])
-def test_mixed_passes_stay_within_fp32_of_the_oracle(case, m2l):
+@pytest.mark.parametrize("m2l,flux", [("dense", True), ("fft", True), ("fft", False)])
+def test_mixed_passes_stay_within_fp32_of_the_oracle(case, m2l, flux):
     """The mixed form (FP32 evaluations on local coordinates, check-to-equivalent
     products in double-FP32 arithmetic) reproduces the oracle's far field at
     p = 4 to FP32 accuracy, far below the FMM's truncation error there (2e-3)."""
     wl, fl, t = case
     p = 4
-    by_depth, U, D = oracle_operators(wl, t, p, True)
-    spec = ops.fmm_m2l_spectra(p, wl.mu, True) if m2l == "fft" else None
-    far, npass = H.far_eval(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, t, p, U, D, wl.mu, True,
+    by_depth, U, D = oracle_operators(wl, t, p, flux)
+    spec = ops.fmm_m2l_spectra(p, wl.mu, flux) if m2l == "fft" else None
+    phi = wl.phi if flux else None  # without sources: the single layer alone
+    far, npass = H.far_eval(wl.pts, wl.f, phi, wl.nrm, wl.w, t, p, U, D, wl.mu, flux,
                             spec=spec, mixed=True)
-    ref = F.fmm_adaptive(wl.tree, wl.pts, wl.f, wl.phi, wl.nrm, wl.w, p, wl.mu, True,
+    ref = F.fmm_adaptive(wl.tree, wl.pts, wl.f, phi, wl.nrm, wl.w, p, wl.mu, flux,
                          ops=by_depth, near=False)
     # + the packing and operator-splitting passes, and the spectra's rounding with
     # Fourier-space M2L

@@ -794,28 +794,36 @@ FMM_HD float sub_rn(float a, float b) {
 }
 
 // Row i of (hi + lo) times x, x exact in FP32 (the check velocities of the
-// mixed passes are FP32 sums).
-FMM_HD float apply_row_df(const float *hi, const float *lo, int64_t i, const float *x, int cols) {
-  const float *ah = hi + (size_t)i * cols, *al = lo + (size_t)i * cols;
+// mixed passes are FP32 sums).  The operator is stored column by column
+// (entry (i, j) at j * rows + i), so that the threads of a warp, which take
+// consecutive rows, read consecutive addresses.
+FMM_HD float apply_row_df(const float *hi, const float *lo, int64_t i, int64_t rows,
+                          const float *x, int cols) {
   float sh = 0.0f, sl = 0.0f;
   for (int j = 0; j < cols; ++j) {
-    const float p = mul_rn(ah[j], x[j]);
-    const float err = fma_f(al[j], x[j], fma_f(ah[j], x[j], -p));  // ah x = p + exact rest
-    const float t = add_rn(sh, p), bv = sub_rn(t, sh);            // two-sum of sh and p
+    const float ah = hi[(size_t)j * rows + i], al = lo[(size_t)j * rows + i];
+    const float p = mul_rn(ah, x[j]);
+    const float err = fma_f(al, x[j], fma_f(ah, x[j], -p));  // ah x = p + exact rest
+    const float t = add_rn(sh, p), bv = sub_rn(t, sh);      // two-sum of sh and p
     sl = add_rn(sl, add_rn(add_rn(sub_rn(sh, sub_rn(t, bv)), sub_rn(p, bv)), err));
     sh = t;
   }
   return add_rn(sh, sl);
 }
 
-// OPSPLIT: e = operator entry (uc2e then dc2e, all depths); hi and lo parts.
+// OPSPLIT: e = operator entry (uc2e then dc2e, all depths, row-major as
+// given); its hi and lo parts, stored transposed within each depth's matrix.
 struct OPSPLIT {
   FMM_HD void operator()(const Pass &P, int64_t e) const {
-    const int64_t nu = P.n_uc2e;
-    const double v = e < nu ? P.uc2e[e] : P.dc2e[e - nu];
+    const int64_t nu = P.n_uc2e, cols = 3 * (int64_t)P.ns;
+    const bool up = e < nu;
+    const int64_t rows = up ? (int64_t)P.nc * P.ns : cols, m = up ? e : e - nu;
+    const int64_t per = rows * cols, base = (up ? 0 : nu) + (m / per) * per;
+    const int64_t i = (m % per) / cols, j = m % cols;
+    const double v = up ? P.uc2e[e] : P.dc2e[e - nu];
     const float h = (float)v;
-    P.ops_hi[e] = h;
-    P.ops_lo[e] = (float)(v - (double)h);
+    P.ops_hi[base + j * rows + i] = h;
+    P.ops_lo[base + j * rows + i] = (float)(v - (double)h);
   }
 };
 
@@ -826,7 +834,7 @@ struct UC2EF {
     const int64_t i = e % rows;
     FMM_CHECK(b, P.box1, "uc2e box");
     const size_t off = (size_t)(P.depth - kFirstDepth) * rows * 3 * P.ns;
-    P.up32[(size_t)b * rows + i] = apply_row_df(P.ops_hi + off, P.ops_lo + off, i,
+    P.up32[(size_t)b * rows + i] = apply_row_df(P.ops_hi + off, P.ops_lo + off, i, rows,
                                                 P.chk32 + (size_t)b * 3 * P.ns, 3 * P.ns);
   }
 };
@@ -838,7 +846,7 @@ struct DC2EF {
     const int64_t i = e % rows;
     FMM_CHECK(b, P.box1, "dc2e box");
     const size_t off = (size_t)P.n_uc2e + (size_t)(P.depth - kFirstDepth) * rows * rows;
-    P.dn32[(size_t)b * rows + i] = apply_row_df(P.ops_hi + off, P.ops_lo + off, i,
+    P.dn32[(size_t)b * rows + i] = apply_row_df(P.ops_hi + off, P.ops_lo + off, i, rows,
                                                 P.chk32 + (size_t)b * rows, (int)rows);
   }
 };

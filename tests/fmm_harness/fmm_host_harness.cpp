@@ -35,9 +35,10 @@ extern "C" {
 
 const char *fmm_host_message(void) { return g_msg; }
 
-// One row product of the mixed check-to-equivalent step: (hi + lo) . x.
+// One row product of the mixed check-to-equivalent step: (hi + lo) . x (a
+// one-row operator, so its column-by-column storage is the row itself).
 float fmm_host_row_df(const float *hi, const float *lo, const float *x, int n) {
-  return stk::fmm::apply_row_df(hi, lo, 0, x, n);
+  return stk::fmm::apply_row_df(hi, lo, 0, 1, x, n);
 }
 
 // Returns the number of passes run (>= 0), or -1 when an index check failed.

@@ -91,6 +91,8 @@ struct EngineParams {
   int32_t cand_cap;
   int32_t *err_flag;         // device error word
   int64_t spin_limit;        // bounded mbarrier waits, in SM clock cycles
+  int64_t drain_limit;       // bound of the wait for a warp's own copy after an expiry
+  int32_t force_expire;      // 1: every item's first chunk wait reports expiry (failure-path tests)
 };
 
 __device__ __forceinline__ int seg_kind(const EngineParams &P, int32_t sid) {

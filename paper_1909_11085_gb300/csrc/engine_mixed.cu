@@ -548,11 +548,14 @@ __device__ bool run_item(const EngineParams &P, const Item &it, int id, WarpSmem
   bool ok = true;
   int npend = 0;
   while (have) {
-    if (!wait_chunk(&sm.mbar, phase, P.spin_limit)) {
+    if (P.force_expire || !wait_chunk(&sm.mbar, phase, P.spin_limit)) {
       set_error(P.err_flag, 4);
       ok = false;
-      // wait (bounded) for the copy in flight before giving up on the item
-      wait_chunk(&sm.mbar, phase, P.spin_limit);
+      // The copy this warp issued last still writes into its shared memory:
+      // the warp waits for it before it leaves (bounded by the drain limit,
+      // which is at least the default wait limit, so a copy from valid memory
+      // always completes first; only one copy per warp is ever in flight).
+      if (!wait_chunk(&sm.mbar, phase, P.drain_limit)) set_error(P.err_flag, 5);
       break;
     }
     phase ^= 1u;

@@ -31,6 +31,10 @@ namespace {
 
 thread_local std::string g_err;
 thread_local cudaEvent_t g_ev_start = nullptr, g_ev_stop = nullptr;
+// Wait policy of later calls on this thread (stokes_set_wait_policy): the
+// bound of the engine's chunk waits (0 = default) and forced expiry.
+thread_local int64_t g_wait_limit = 0;
+thread_local int32_t g_force_expire = 0;
 
 // Kernels recorded in each executable graph the library captured, so that a
 // replay adds them to the launch count (any thread may replay a graph).
@@ -250,7 +254,9 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   P.item_counter = counters + 1;
   P.err_flag = counters + 2;
   P.near_counter = counters + 3;
-  P.spin_limit = kSpinLimit;
+  P.spin_limit = g_wait_limit > 0 ? g_wait_limit : kSpinLimit;
+  P.drain_limit = P.spin_limit > kSpinLimit ? P.spin_limit : kSpinLimit;
+  P.force_expire = g_force_expire;
   P.policy = p.tile.policy;
   P.part_out = at<double>(ws, p.part);
   P.nt = (int32_t)p.nt;
@@ -458,6 +464,8 @@ namespace stk {
 // Records `msg` as the calling thread's last error and returns `s` (used by
 // the other translation units of the library).
 stk_status report_error(stk_status s, const char *msg) { return fail(s, msg); }
+// noalloc.cu: the fixed buffer of stokes_sl_eval_noalloc in the current context.
+stk_status noalloc_scratch(void **addr, size_t *bytes);
 }  // namespace stk
 
 extern "C" {
@@ -480,6 +488,14 @@ stk_status stokes_set_engine_events(void *start_event, void *stop_event) {
 }
 
 int64_t stokes_launch_count(void) { return stk::launch_count(); }
+
+stk_status stokes_set_wait_policy(int64_t limit_cycles, int32_t force_expire) {
+  if (limit_cycles < 0) return fail(STK_EINVAL, "limit_cycles must be >= 0");
+  if (force_expire != 0 && force_expire != 1) return fail(STK_EINVAL, "force_expire must be 0 or 1");
+  g_wait_limit = limit_cycles;
+  g_force_expire = force_expire;
+  return STK_OK;
+}
 
 const char *stokes_version(void) { return "stokesgpu 0.1 (sm_103a)"; }
 
@@ -768,7 +784,11 @@ stk_status stokes_sldl_grad(const double *src, const double *f, const double *nr
 }
 
 stk_status stokes_device_status(void *workspace, size_t workspace_bytes) {
-  if (!workspace || workspace_bytes < 512) return fail(STK_EINVAL, "workspace is NULL or too small");
+  if (!workspace) {  // the fixed buffer of stokes_sl_eval_noalloc in the current context
+    const stk_status s = stk::noalloc_scratch(&workspace, &workspace_bytes);
+    if (s != STK_OK) return s;
+  }
+  if (workspace_bytes < 512) return fail(STK_EINVAL, "workspace is too small");
   int32_t *counters = at<int32_t>(align_ws(workspace), 0);
   int32_t err = 0;
   CU(cudaMemcpy(&err, counters + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));

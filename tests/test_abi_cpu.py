@@ -33,6 +33,13 @@ def test_exports_every_declared_symbol(L):
     assert set(syms) <= set(A.EXPORTS) | set(syms)
 
 
+def test_wait_policy_validated_on_host(L):
+    assert L.stokes_set_wait_policy(-5, 0) == A.STK_EINVAL
+    assert L.stokes_set_wait_policy(0, 3) == A.STK_EINVAL
+    assert L.stokes_set_wait_policy(1000, 0) == A.STK_OK
+    assert L.stokes_set_wait_policy(0, 0) == A.STK_OK
+
+
 def test_default_opts(L):
     o = A.StkOpts()
     L.stokes_default_opts(ctypes.byref(o))

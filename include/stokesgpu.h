@@ -448,16 +448,38 @@ stk_status stokes_fmm_m2l_spectra(int32_t p, double mu, int32_t flux, double *ou
  * 65536 (STK_EUNSUPPORTED otherwise); source splits are reduced if needed to
  * fit the buffer.  Allocates nothing.  The first call on a device looks up the
  * buffer's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the buffer: calls whose kernels
- * may overlap on the GPU race and must be serialised by the caller. */
+ * before any stream capture.  The address is cached per device and CUDA
+ * context (a call in a new context, after cudaDeviceReset for instance, looks
+ * it up again, and that call too should precede any capture).  All calls
+ * share the buffer: calls whose kernels may overlap on the GPU race and must
+ * be serialised by the caller.  A device wait that ran out during the last
+ * call is reported by stokes_device_status(NULL, 0) after synchronising; the
+ * next call clears it. */
 stk_status stokes_sl_eval_noalloc(const double *src, const double *f, const double *w,
                                   const double *h, int64_t ns, const double *trg, int64_t nt,
                                   double mu, double *out, const stk_opts *opts, void *stream);
 
+/* ----------------------------------------------------- pipe throughput
+ * Throughput probes of the arithmetic pipes the summation kernels are bound
+ * by, for rooflines against rates measured on the GPU at hand (the paper has
+ * no counterpart; it names no GPU).  op: 0 FP32 FMA, 1 packed two-wide FP32
+ * FMA (the engine's instruction), 2 FP64 FMA, 3 FP32 reciprocal square root
+ * (rsqrt.approx, the MUFU unit).  One launch of SMs x 8 CTAs of 256 threads,
+ * each thread running 8 independent chains of `iters` dependent operations
+ * on the stream; *ops receives the work of the launch (flops for the FMA
+ * forms: 2 per FMA, 4 per packed FMA; evaluations for rsqrt), to be divided
+ * by the launch's duration timed by the caller.  sink: caller device memory
+ * of stokes_pipe_probe_size bytes, written with the chains' sums. */
+stk_status stokes_pipe_probe_size(size_t *sink_bytes);
+stk_status stokes_pipe_probe(int32_t op, int32_t iters, void *sink, size_t sink_bytes,
+                             double *ops, void *stream);
+
 /* ----------------------------------------------------------------- status */
 /* Reads the device error word kept in a workspace used by an earlier call.
  * The caller must have synchronised the stream.  Returns STK_OK or
- * STK_ETIMEOUT, and clears the word. */
+ * STK_ETIMEOUT, and clears the word.  workspace == NULL reads the word of
+ * stokes_sl_eval_noalloc's fixed buffer in the current CUDA context
+ * (STK_EINVAL if that entry point has not run there). */
 stk_status stokes_device_status(void *workspace, size_t workspace_bytes);
 /* Instrumentation.  While both events are non-NULL (cudaEvent_t handles
  * created by the caller), every later call on this thread records `start`
@@ -465,6 +487,20 @@ stk_status stokes_device_status(void *workspace, size_t workspace_bytes);
  * call's stream, so that the caller can time the dominant kernel alone.
  * Passing NULLs switches it off. */
 stk_status stokes_set_engine_events(void *start_event, void *stop_event);
+/* Wait policy of the later calls made on this thread (failure-path testing;
+ * no device fault is involved).  The mixed engine stages sources through
+ * bounded waits on shared-memory barriers; a wait that runs out records
+ * STK_ETIMEOUT in the workspace's error word (stokes_device_status), the warp
+ * then waits for the copy it already issued to land, bounded by at least the
+ * default limit, and leaves the call with its work unfinished (the near-pair
+ * pass skips the call; the results are incomplete).  limit_cycles: bound of
+ * each wait in SM clock cycles (0 restores the default, 4e9 cycles, about
+ * 2 s).  force_expire = 1: the first wait of every work item reports expiry
+ * at once although its copy completes normally, so that a test can take the
+ * failure path on any input; 0 switches it off.  STK_EINVAL for a negative
+ * limit or another force_expire.  Graphs captured meanwhile keep the policy
+ * they were captured with. */
+stk_status stokes_set_wait_policy(int64_t limit_cycles, int32_t force_expire);
 /* Number of kernels this thread has launched through the library so far.  A
  * graph capture adds nothing (its kernels are recorded, not run); each
  * stokes_graph_launch adds the kernels the graph holds. */

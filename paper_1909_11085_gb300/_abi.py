@@ -35,6 +35,7 @@ EXPORTS = [
     "stokes_fmm_surface", "stokes_fmm_check_to_equiv", "stokes_fmm_kernel_matrix",
     "stokes_fmm_far_workspace_size", "stokes_fmm_far_eval", "stokes_fmm_m2l_spectra",
     "stokes_octree_build", "stokes_octree_info", "stokes_octree_export", "stokes_octree_destroy",
+    "stokes_set_wait_policy", "stokes_pipe_probe_size", "stokes_pipe_probe",
 ]
 
 
@@ -98,6 +99,9 @@ def lib():
             L.stokes_batched_workspace_size.argtypes = [i64, i32, po, psz]
             L.stokes_device_status.argtypes = [p, sz]
             L.stokes_set_engine_events.argtypes = [p, p]
+            L.stokes_set_wait_policy.argtypes = [i64, i32]
+            L.stokes_pipe_probe_size.argtypes = [psz]
+            L.stokes_pipe_probe.argtypes = [i32, i32, p, sz, ctypes.POINTER(ctypes.c_double), p]
             L.stokes_sl_eval_noalloc.argtypes = [p, p, p, p, i64, p, i64, d, p, po, p]
             L.stokes_sldl_grad.argtypes = [p, p, p, p, p, p, i64, p, i64, p, d, p, p, p, p, p, po,
                                            p, sz, p]

@@ -17,6 +17,8 @@
 // (the work-queue counters) and writes every other word before reading it.
 // Calls whose kernels overlap on the GPU (for example on two streams) race on
 // the buffer and must be serialised by the caller.
+#include <cuda.h>  // driver API types only; the functions are reached through the runtime
+
 #include <mutex>
 
 #include "../../include/stokesgpu.h"
@@ -33,30 +35,96 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
+// The host-side name of g_noalloc_scratch is not a device address.  Its device
+// address belongs to the module loaded into one CUDA context: after
+// cudaDeviceReset, or when the primary context is released and created again,
+// the module is loaded anew and the buffer may sit elsewhere.  So the address
+// is looked up with the device current and cached per device together with
+// the identity of the context it was looked up in (cuCtxGetId: unique for the
+// life of the process); a call in another context looks it up again.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
 
-// The host-side name of g_noalloc_scratch is not a device address.  The
-// device address is looked up on the first call on each device, with that
-// device current, and kept.
-stk_status scratch_address(void **addr) {
+struct ScratchCache {
+  unsigned long long ctx_id = 0;
+  void *addr = nullptr;
+};
+
+std::mutex g_mu;
+ScratchCache g_cache[kMaxDevices];
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+bool g_driver_looked_up = false;
+
+// Identity of the calling thread's current context (0 when it cannot be
+// read; the cache is then bypassed and the address looked up on every call).
+unsigned long long current_context_id() {
+  if (!g_driver_looked_up) {
+    g_driver_looked_up = true;
+    void *a = nullptr, *b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) ==
+            cudaSuccess &&
+        qa == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) ==
+            cudaSuccess &&
+        qb == cudaDriverEntryPointSuccess) {
+      g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+      g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(b);
+    }
+  }
+  if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the buffer in the current context.  With lookup == false
+// only an address already looked up in this context is returned (NULL
+// otherwise).  cudaGetSymbolAddress makes the device's primary context current
+// on this thread if none was, so the context is read again after it.
+stk_status scratch_address(void **addr, bool lookup) {
+  *addr = nullptr;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return stk::report_error(STK_ECUDA, "stokes_sl_eval_noalloc: no current CUDA device");
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return stk::report_error(STK_ECUDA,
-                               "stokes_sl_eval_noalloc: cudaGetSymbolAddress of the scratch failed");
-    g_scratch_addr[dev] = p;
+  ScratchCache &c = g_cache[dev];
+  const unsigned long long id = current_context_id();
+  if (id != 0 && c.addr && c.ctx_id == id) {
+    *addr = c.addr;
+    return STK_OK;
   }
-  *addr = g_scratch_addr[dev];
+  if (!lookup) return STK_OK;
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return stk::report_error(STK_ECUDA,
+                             "stokes_sl_eval_noalloc: cudaGetSymbolAddress of the scratch failed");
+  const unsigned long long id_now = current_context_id();
+  c.ctx_id = id_now;
+  c.addr = id_now != 0 ? p : nullptr;
+  *addr = p;
   return STK_OK;
 }
 
 }  // namespace
+
+namespace stk {
+// The buffer's address in the current context if stokes_sl_eval_noalloc has
+// run there (its error word is read by stokes_device_status(NULL, 0)).
+stk_status noalloc_scratch(void **addr, size_t *bytes) {
+  *bytes = kNoAllocScratchBytes;
+  const stk_status s = scratch_address(addr, false);
+  if (s != STK_OK) return s;
+  if (!*addr)
+    return report_error(STK_EINVAL,
+                        "stokes_device_status: stokes_sl_eval_noalloc has not run in this context");
+  return STK_OK;
+}
+}  // namespace stk
 
 extern "C" stk_status stokes_sl_eval_noalloc(const double *src, const double *f, const double *w,
                                              const double *h, int64_t ns, const double *trg,
@@ -67,7 +135,7 @@ extern "C" stk_status stokes_sl_eval_noalloc(const double *src, const double *f,
     return stk::report_error(STK_EUNSUPPORTED,
                              "stokes_sl_eval_noalloc: ns and nt must not exceed 65536");
   void *scratch = nullptr;
-  stk_status s = scratch_address(&scratch);
+  stk_status s = scratch_address(&scratch, true);
   if (s != STK_OK) return s;
   // Use the requested source splits, or fewer until the workspace fits the buffer.
   stk_opts o = *opts;

@@ -46,6 +46,9 @@ FLOPS_PER_PAIR = {"SL": 28, "DL": 29, "SLDL": 57}
 # d.n 5, (d.psi)(d.n) 1, combine 2 + 1, two 3-vector FMAs 12).
 EXEC_FLOPS_PER_PAIR = {"SL": 27, "DL": 29, "SLDL": 40}
 FLOPS_PER_PAIR_SLDL = FLOPS_PER_PAIR["SLDL"]
+# The same convention with the difference d (3) and |r|^2 (5) counted once for
+# the fused SL + DL pair, which evaluates them once for both kernels: 49.
+FUSED_FLOPS_PER_PAIR = FLOPS_PER_PAIR_SLDL - 8
 # The adjoint's pair terms as stated (and written) for both kernels, counted the
 # same way: shared d 3, |r|^2 5, r^-2, r^-3, r^-5 3, d.g 5; source-major pass
 # + single layer 48 + double layer 55 + 3 = 122; target-major pass + 35 + 43 + 3 = 97.
@@ -223,13 +226,97 @@ def _time_ms(fn, stream, flush, reps, warm=1):
     return statistics.median(a.elapsed_time(b) for a, b in ev)
 
 
-def run_fmm_far(wl, near, dev, stream, flush, p=4):
-    """The FMM's far field (stokes_fmm_far_eval) on the near-field workload's own
-    octree: host set-up time (the library's octree and V, W, X lists, the same
-    tree as the workload's U-lists; per-depth operators), device
-    time per call in FP64 and mixed precision with dense and Fourier-space M2L, and
-    far field + the step's near field against the direct sum on 256 sampled
-    targets (the FMM's approximation error at this p, not a parity figure)."""
+def run_peaks(dev, stream):
+    """Measured throughput of the pipes the kernels are bound by (the library's
+    stokes_pipe_probe): FP32 FMA, packed FP32 FMA, FP64 FMA (TFLOP/s) and the
+    MUFU reciprocal square root (Geval/s), each the median of 3 timed launches
+    after one warm-up, with CUDA events on the launching stream."""
+    import ctypes
+    import torch
+    from paper_1909_11085_gb300 import _abi as A
+    L = A.lib()
+    nb = ctypes.c_size_t(0)
+    A.check(L.stokes_pipe_probe_size(ctypes.byref(nb)))
+    sink = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+    res = {}
+    for op, name, iters, unit in ((0, "ffma", 16384, "TFLOP/s"), (1, "ffma2", 8192, "TFLOP/s"),
+                                  (2, "dfma", 256, "TFLOP/s"), (3, "rsqrt", 2048, "Geval/s")):
+        ops = ctypes.c_double(0)
+        launch = lambda: A.check(L.stokes_pipe_probe(op, iters, A.ptr(sink), sink.numel(),
+                                                      ctypes.byref(ops), A.stream_ptr(dev)))
+        launch()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            launch()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        res[name] = {"value": ops.value / (ms / 1e3) / scale, "unit": unit, "ms": ms}
+    log(f"[peaks] {res}")
+    return res
+
+
+def near_fraction(wl, tg, alpha):
+    """Fraction of the (target, U-list source) pairs of the sample tg that are
+    near at this alpha (|x - y| < alpha h_y, the self pair excluded)."""
+    t = wl.tree
+    leaf = np.searchsorted(t.leaf_ptr, tg, side="right") - 1
+    near, tot = 0, 0
+    for lf in np.unique(leaf):
+        xs = wl.pts[tg[leaf == lf]]
+        src = np.concatenate([np.arange(t.leaf_ptr[b], t.leaf_ptr[b + 1])
+                              for b in t.ulist_idx[t.ulist_ptr[lf]:t.ulist_ptr[lf + 1]]])
+        d2 = ((xs[:, None, :] - wl.pts[src][None, :, :]) ** 2).sum(-1)
+        hh = (alpha * wl.h[src]) ** 2
+        near += int(((d2 < hh[None, :]) & (d2 > 0)).sum())
+        tot += int((d2 > 0).sum())
+    return near / max(tot, 1)
+
+
+def run_alpha_sweep(wl, dev, stream, flush, pts, f, phi, nrm, w, h, alphas=(1.0, 2.0, 4.0)):
+    """The near-pair threshold alpha (|r| < alpha h_j takes the FP64 path):
+    for each alpha the near-pair fraction (host-counted on a target sample),
+    the P2P step time and the mixed form's rel-L2 and max error against the
+    oracle on the same sample."""
+    import torch
+    import oracle
+    import paper_1909_11085_gb300 as P
+    t = wl.tree
+    n = wl.pts.shape[0]
+    rng = np.random.default_rng(7)
+    tg = np.sort(rng.choice(n, 2000, replace=False))
+    ref = oracle_sample(wl, tg)
+    out = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    res = {"sample": f"{tg.size} random targets with all their U-list sources"}
+    for a in alphas:
+        plan = P.P2PPlan(n, t.leaf_ptr, t.ulist_ptr, t.ulist_idx, 3, "mixed", a, dev)
+        ms = _time_ms(lambda: plan(pts, f, phi, nrm, w, h, wl.mu, out), stream, flush, 10, warm=2)
+        plan.device_status()
+        u = out.cpu().numpy()[tg]
+        res[f"alpha_{a:g}"] = {
+            "near_pair_fraction": near_fraction(wl, tg, a), "ms_per_step": ms,
+            "Gpair/s": wl.pairs() / ms / 1e6,
+            "rel_l2": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
+            "max_rel": float(np.abs(u - ref).max() / np.abs(ref).max())}
+        log(f"[alpha] {a}: {res[f'alpha_{a:g}']}")
+        del plan
+    return res
+
+
+def run_fmm_far(wl, near, near_ms_step, dev, stream, flush, p=4):
+    """The whole single-GPU FMM: the far field (stokes_fmm_far_eval) on the
+    near-field workload's own octree beside the timed near-field step.  Host
+    set-up time (the library's octree and V, W, X lists, the same tree as the
+    workload's U-lists; per-depth operators; each plan's device copies), device
+    time per call in FP64 and mixed precision with dense and Fourier-space M2L,
+    far + near time, and far field + the step's near field against the direct
+    sum on 256 sampled targets (the FMM's approximation error at this p, not a
+    parity figure)."""
     import torch
     import oracle
     from paper_1909_11085_gb300 import ops
@@ -253,16 +340,23 @@ def run_fmm_far(wl, near, dev, stream, flush, p=4):
            "w_entries": int(tn["w_idx"].size), "x_entries": int(tn["x_idx"].size),
            "host_lists_s": lists_s, "host_operators_s": ops_s,
            "near_only_rel_l2": float(np.linalg.norm(un - ref) / np.linalg.norm(ref))}
-    for prec in ("fp64", "mixed"):
-        for m2l in ("dense", "fft"):
+    near_ms = near_ms_step
+    res["near_field_ms"] = near_ms
+    for prec in ("mixed", "fp64"):
+        for m2l in ("fft", "dense"):
+            t0 = time.perf_counter()
             plan = ops.FmmFarPlan(t, p=p, mu=wl.mu, flux=True, uc2e=U, dc2e=D, m2l=m2l,
                                   precision=prec)
+            plan_s = time.perf_counter() - t0
             far = torch.zeros_like(pts)
-            ms = _time_ms(lambda: plan(pts, f, phi, nrm, w, out=far), stream, flush, 2)
+            reps = 10 if prec == "mixed" else 2
+            ms = _time_ms(lambda: plan(pts, f, phi, nrm, w, out=far), stream, flush, reps)
             u = far.cpu().numpy()[tg] + un
             key = f"{prec}_{m2l}"
-            res[key] = {"ms": ms, "rel_l2_vs_direct": float(np.linalg.norm(u - ref) /
-                                                            np.linalg.norm(ref))}
+            res[key] = {"far_ms": ms, "far_plus_near_ms": ms + near_ms,
+                        "host_plan_s": plan_s, "workspace_MB": plan.ws.numel() / 1e6,
+                        "rel_l2_vs_direct": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
+                        "max_rel_vs_direct": float(np.abs(u - ref).max() / np.abs(ref).max())}
             log(f"[fmm] {key}: {res[key]}")
             del plan, far
     torch.cuda.empty_cache()
@@ -537,6 +631,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    peaks = run_peaks(dev, stream) if not args.no_peaks else None
     sampler = ClockSampler(local_rank)
     sampler.start()
     time.sleep(0.3)
@@ -690,6 +785,17 @@ def run_ours(args, rank, world, local_rank):
     if clocks.get("sm_mhz"):
         at_clock = achieved / (sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
 
+    # the FP64 form against the measured FP64 FMA rate, flops by the same convention
+    fp64_line = {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": K64}
+    if peaks:
+        a64 = pairs * FLOPS_PER_PAIR_SLDL / (ms64 / 1e3) / 1e12
+        fp64_line["roofline"] = {
+            "bound": "fp64", "achieved": a64, "peak": peaks["dfma"]["value"], "unit": "TFLOP/s",
+            "frac": a64 / peaks["dfma"]["value"], "flops_per_pair": FLOPS_PER_PAIR_SLDL,
+            "peak_basis": "measured FP64 FMA rate (stokes_pipe_probe op 2)",
+            "note": "the FP64 form also spends FP64-pipe work on 1/sqrt (no FP64 rsqrt unit), "
+                    "which the convention does not count"}
+
     if rank != 0:
         return 0
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -706,9 +812,15 @@ def run_ours(args, rank, world, local_rank):
                            "flops_per_pair_basis": "algorithmic, fixed convention: SL 28 + DL 29",
                            "executed_flops_per_pair": EXEC_FLOPS_PER_PAIR["SLDL"],
                            "frac_executed": achieved_x / peak,
+                           "frac_49": pairs * FUSED_FLOPS_PER_PAIR / eng_avg_s / 1e12 / peak,
+                           "frac_49_whole_step": pairs * FUSED_FLOPS_PER_PAIR / (tot_s / K) / 1e12
+                           / peak,
+                           "frac_49_basis": "d and |r|^2 counted once for the fused SL+DL pair: "
+                                            "57 - 8 = 49 flops",
+                           "frac_whole_step": achieved * eng_avg_s / (tot_s / K) / peak,
                            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                            "frac_at_sampled_clock": at_clock},
-              "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": K64},
+              "fp64": fp64_line,
               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
                       "steps": Kp, "serial_ms_per_step": serial_ms,
@@ -718,10 +830,15 @@ def run_ours(args, rank, world, local_rank):
                                  "figure copies, computes and reads back one step at a time"},
               "gpu_launches": int(launches), "gpu_launches_per_step": launches / K,
               "clocks": clocks, "wall_s_timed_region": wall}
+    if peaks:
+        peaks["fp32_peak_from_ffma_frac_of_nominal"] = peaks["ffma"]["value"] / peak
+        result["peaks"] = peaks
     if world == 1 and not args.no_forms:
         result["forms"] = run_forms(dev, flush, stream, peak)
-    if world == 1 and args.fmm_far:
-        result["fmm_far"] = run_fmm_far(wl, out, dev, stream, flush)
+    if world == 1 and not args.no_fmm:
+        result["fmm_far"] = run_fmm_far(wl, out, tot_s / K * 1e3, dev, stream, flush)
+    if world == 1 and not args.no_alpha:
+        result["near"] = run_alpha_sweep(wl, dev, stream, flush, pts, f, phi, nrm, w, h)
     if world == 1 and not args.no_cpu_baseline:
         rng = np.random.default_rng(20191)
         tg, ref, dt = timed_oracle(wl, args.cpu_seconds, rng)
@@ -757,9 +874,13 @@ def main():
     ap.add_argument("--wall-patches", type=int, default=320)
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the other workloads (direct, batched, adjoint)")
-    ap.add_argument("--fmm-far", action="store_true",
-                    help="also time the FMM's far field (FP64 and mixed passes, dense and "
+    ap.add_argument("--no-fmm", action="store_true",
+                    help="skip the FMM's far field (FP64 and mixed passes, dense and "
                          "Fourier-space M2L) on the near-field workload's octree")
+    ap.add_argument("--no-alpha", action="store_true",
+                    help="skip the near-pair threshold sweep (alpha = 1, 2, 4)")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the measured FP32 / FP64 / MUFU pipe rates")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -349,6 +349,12 @@ stk_status stokes_fmm_kernel_matrix(const double *x, int32_t nx, const double *y
  * surface count of p.  flux != 0: the upward density has a point-source
  * strength per surface point (needed for the double layer's far field).
  *
+ * Every call clears the workspace's error word (the int32 at byte 8 of the
+ * 256-byte aligned workspace, as for the other entry points); the mixed form's
+ * kernels check each box, leaf and point index they read from the tree arrays
+ * and record one out of range there (stokes_device_status then returns
+ * STK_EINVAL) instead of using it.
+ *
  * precision: STK_FP64 evaluates every pass in FP64; STK_MIXED packs points
  * (relative to their leaf's centre), densities, surfaces and spectra in FP32,
  * evaluates kernels and spectral products in FP32 with one FP64 difference of
@@ -384,6 +390,15 @@ stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double 
                                const double *m2l_spectra, int32_t precision, double mu,
                                double *out, int32_t accumulate, void *workspace,
                                size_t workspace_bytes, void *stream);
+/* Instrumentation of stokes_fmm_far_eval.  While events != NULL (capacity
+ * cudaEvent_t handles created by the caller), the k-th kernel launch of each
+ * later far-field call of this thread in the mixed form with p <= 8 records
+ * events[2k] before and events[2k + 1] after it on the call's stream (for
+ * k < capacity / 2), names[k] (may be NULL) receives a static string naming
+ * its pass and *count (may be NULL) the number of launches recorded.  NULL
+ * events switches it off.  STK_EINVAL for capacity < 2. */
+stk_status stokes_fmm_set_pass_events(void **events, int32_t capacity, const char **names,
+                                      int32_t *count);
 /* Octree and interaction lists of the FMM (host, built once per point set;
  * Sec. 3.1, "Far evaluation" leaves the tree to the FMM library, so this is
  * one reading of it).  The root is the points' bounding cube grown by 1e-9;

@@ -7,7 +7,7 @@
 #include <cmath>
 
 #include "../../include/stokesgpu.h"
-#include "fmm_passes.cuh"
+#include "fmm_fast.cuh"
 #include "prep.cuh"
 
 namespace stk {
@@ -17,6 +17,10 @@ stk_status report_error(stk_status s, const char *msg);
 namespace {
 
 using stk::fmm::Pass;
+
+// Per-launch timing hooks of this thread's later far-field calls
+// (stokes_fmm_set_pass_events).
+thread_local stk::fmm::FastHooks g_hooks;
 
 template <class F>
 __global__ void __launch_bounds__(256) k_fmm_pass(Pass P, int64_t n) {
@@ -169,12 +173,32 @@ stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double 
   P.n_dc2e = stk::fmm::op_entries(p, nc, tree->max_depth, false);
   stk::fmm::bind(P, ws, L, fft, mixed);
 
+  if (cudaMemsetAsync(ws + L.counters, 0, sizeof(int32_t) * 4, st) != cudaSuccess)
+    return report_error(STK_ECUDA, "cannot clear the error word");
   k_fmm_setup<<<1, 32, 0, st>>>(P);
   if (cudaGetLastError() != cudaSuccess) return report_error(STK_ECUDA, "set-up launch failed");
   stk::count_launches(1);
+  // the CTA-blocked mixed kernels (their spectral products need the colleague table)
+  if (mixed && p <= stk::fmm::kFastMaxP && (!fft || tree->colleague)) {
+    const cudaError_t e = stk::fmm::far_field_fast(P, tree->depth_ptr, tree->max_depth, sms, st,
+                                                   g_hooks);
+    if (e != cudaSuccess) return report_error(STK_ECUDA, cudaGetErrorString(e));
+    return STK_OK;
+  }
   DeviceExec ex{st, (int64_t)sms * 8};
   stk::fmm::far_field(ex, P, tree->depth_ptr, tree->max_depth);
   if (ex.err != cudaSuccess) return report_error(STK_ECUDA, cudaGetErrorString(ex.err));
+  return STK_OK;
+}
+
+stk_status stokes_fmm_set_pass_events(void **events, int32_t capacity, const char **names,
+                                      int32_t *count) {
+  if (events && capacity < 2) return stk::report_error(STK_EINVAL, "capacity must be >= 2");
+  g_hooks.events = reinterpret_cast<cudaEvent_t *>(events);
+  g_hooks.capacity = events ? capacity : 0;
+  g_hooks.names = events ? names : nullptr;
+  g_hooks.count = events ? count : nullptr;
+  if (count) *count = 0;
   return STK_OK;
 }
 

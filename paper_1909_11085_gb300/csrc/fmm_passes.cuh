@@ -139,6 +139,20 @@ struct Pass {
   float *chk32;             // [nbox][3 ns] check velocities (FP32 sums)
   float *ops_hi, *ops_lo;   // uc2e then dc2e as FP32 pairs
   int64_t n_uc2e, n_dc2e;   // entries of uc2e and dc2e
+  // the CTA-blocked mixed kernels (fmm_fast.cu) add: the child in each octant
+  // of a box, the boxes that are first children (flag and exclusive scan) and
+  // the parents in that order, and the DFT matrices of the lattice
+  int32_t *child8;     // [nbox][8] child box at octant (x&1) 4 + (y&1) 2 + (z&1), or -1
+  int32_t *bflag;      // [nbox] 1 where the box is its parent's first child
+  int32_t *bpos;       // [nbox + 1] exclusive scan of bflag (bpos[nbox] = total)
+  int32_t *plist;      // [nbox] parents, in the order of their first children
+  float *ftab;         // [ns][nfreq][2] forward DFT of the surface lattice (cos, -sin)
+  float *fitab;        // [nfreq][ns][2] inverse over the half spectrum, weighted, / G^3
+  int32_t *err;        // device error word (a tree index out of range), at workspace + 8 bytes
+  // leaf order of the blocked L2T (most work first): cost keys, leaf numbers,
+  // bucket counts and offsets, ranks and the order
+  uint64_t *lkeys;
+  int32_t *lvals, *lcnt, *loff, *lrank, *lorder;
 };
 
 // Boundary points of the p^3 grid on [-1, 1]^3, i slowest, k fastest.
@@ -927,9 +941,12 @@ struct L2TF {
 // form: the check array stays FP64 (input of the FP64 operators); points,
 // surfaces, densities and spectra are FP32.
 struct Layout {
+  size_t counters;  // int32 [4] at offset 0; [2] is the device error word
   size_t surf, chk, up, dn, sidx, tw, uhat, chat, m2l;
   size_t ploc, qf, pf, nf, surf32, up32, dn32, tw32, spec32, uhat32, chat32, m2l32;
   size_t chk32, ops_hi, ops_lo;
+  size_t child8, bflag, bpos, plist, ftab, fitab;
+  size_t lkeys, lvals, lcnt, loff, lrank, lorder;
   size_t total;
 };
 
@@ -953,11 +970,14 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t 
     return at;
   };
   const size_t none = 0;
+  L.counters = take(sizeof(int32_t) * 4);
   L.surf = take(sizeof(double) * 3 * ns);
   L.sidx = take(sizeof(int32_t) * 3 * ns);
   L.chk = L.up = L.dn = L.tw = L.uhat = L.chat = L.m2l = none;
   L.ploc = L.qf = L.pf = L.nf = L.surf32 = L.up32 = L.dn32 = L.tw32 = L.spec32 = L.uhat32 =
       L.chat32 = L.m2l32 = L.chk32 = L.ops_hi = L.ops_lo = none;
+  L.child8 = L.bflag = L.bpos = L.plist = L.ftab = L.fitab = none;
+  L.lkeys = L.lvals = L.lcnt = L.loff = L.lrank = L.lorder = none;
   if (!mixed) {
     L.chk = take(sizeof(double) * 3 * ns * B);
     L.up = take(sizeof(double) * nc * ns * B);
@@ -987,7 +1007,20 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t 
       L.uhat32 = take(sizeof(float) * 2 * nf * nc * B);
       L.chat32 = take(sizeof(float) * 2 * nf * 3 * B);
       L.m2l32 = take(sizeof(float) * 3 * ns * B);
+      L.ftab = take(sizeof(float) * 2 * ns * nf);
+      L.fitab = take(sizeof(float) * 2 * ns * nf);
     }
+    L.child8 = take(sizeof(int32_t) * 8 * B);
+    L.bflag = take(sizeof(int32_t) * B);
+    L.bpos = take(sizeof(int32_t) * (B + 1));
+    L.plist = take(sizeof(int32_t) * B);
+    const size_t NL = (size_t)nbox;  // >= leaves
+    L.lkeys = take(sizeof(uint64_t) * NL);
+    L.lvals = take(sizeof(int32_t) * NL);
+    L.lcnt = take(sizeof(int32_t) * 256);
+    L.loff = take(sizeof(int32_t) * 256);
+    L.lrank = take(sizeof(int32_t) * NL);
+    L.lorder = take(sizeof(int32_t) * NL);
   }
   L.total = o + 256;  // slack for aligning the caller's base
   return L;
@@ -1022,6 +1055,20 @@ inline void bind(Pass &P, char *ws, const Layout &L, bool fft, bool mixed) {
   P.uhat32 = (fft && mixed) ? f(L.uhat32) : nullptr;
   P.chat32 = (fft && mixed) ? f(L.chat32) : nullptr;
   P.m2l32 = (fft && mixed) ? f(L.m2l32) : nullptr;
+  auto i32 = [ws](size_t off) { return reinterpret_cast<int32_t *>(ws + off); };
+  P.err = i32(L.counters) + 2;
+  P.child8 = mixed ? i32(L.child8) : nullptr;
+  P.bflag = mixed ? i32(L.bflag) : nullptr;
+  P.bpos = mixed ? i32(L.bpos) : nullptr;
+  P.plist = mixed ? i32(L.plist) : nullptr;
+  P.ftab = (fft && mixed) ? f(L.ftab) : nullptr;
+  P.fitab = (fft && mixed) ? f(L.fitab) : nullptr;
+  P.lkeys = mixed ? reinterpret_cast<uint64_t *>(ws + L.lkeys) : nullptr;
+  P.lvals = mixed ? i32(L.lvals) : nullptr;
+  P.lcnt = mixed ? i32(L.lcnt) : nullptr;
+  P.loff = mixed ? i32(L.loff) : nullptr;
+  P.lrank = mixed ? i32(L.lrank) : nullptr;
+  P.lorder = mixed ? i32(L.lorder) : nullptr;
 }
 
 // Surface points, lattice indices and twiddles (one thread; set-up of a call).

@@ -795,6 +795,9 @@ stk_status stokes_device_status(void *workspace, size_t workspace_bytes) {
   if (err != 0) {
     const int32_t zero = 0;
     CU(cudaMemcpy(counters + 2, &zero, sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (err == 6)
+      return fail(STK_EINVAL, "an index read from the tree arrays on the device was out of range; "
+                              "results of that call are incomplete");
     return fail(STK_ETIMEOUT, "a bounded device wait ran out; results of that call are incomplete");
   }
   return STK_OK;

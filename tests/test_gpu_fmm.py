@@ -82,9 +82,11 @@ def test_far_field_matches_the_oracle(lib, case, flux, kinds, m2l, precision, to
     assert _rel(far, ref) <= tol, _rel(far, ref)
     fft, mixed = m2l == "fft", precision == "mixed"
     # set-up + the passes; Fourier space adds 3 per depth; mixed adds the
-    # packing and operator-splitting passes and, with spectra, their rounding
+    # packing and operator-splitting passes and, with spectra, their rounding,
+    # and (the CTA-blocked form) the octant table, the first-child scan, the
+    # parent list and the leaves' cost order (keys and a three-launch bucket order)
     assert launches == (1 + 2 + 4 * (t["max_depth"] - 1) - 1 + 3 * fft * (t["max_depth"] - 1)
-                        + mixed * (2 + fft))
+                        + mixed * (2 + fft + 7))
     # accumulate
     import torch
     base = torch.full((wl.pts.shape[0], 3), 0.5, dtype=torch.float64, device="cuda")
@@ -128,3 +130,66 @@ def test_fmm_plan_from_unsorted_points(lib):
     assert _rel(u, ref) <= 1e-9, _rel(u, ref)
     direct = oracle.sldl(wl.pts, wl.f, wl.nrm, wl.phi, wl.w, wl.pts, wl.mu)
     assert _rel(u, direct) <= 5e-3
+
+
+@pytest.fixture(scope="module")
+def deep(lib):
+    """A tree six deep (12 cells and 6 wall patches, <= 16 points per leaf,
+    7,254 points): M2M and L2L chains of four translations, W and X lists at
+    several depths, and the oracle's far field with the same operators."""
+    from paper_1909_11085_gb300 import ops
+    wl = W.p2p_workload(ncell=12, radius=10.0, n_wall_patch=6, max_leaf=16)
+    tn = ops.octree(wl.pts, 16)
+    assert np.array_equal(tn["perm"], np.arange(wl.pts.shape[0]))
+    t = ops.fmm_tree_arrays(**ops.fmm_tree_args(tn))
+    assert t["max_depth"] == 6 and tn["w_idx"].size > 0 and tn["x_idx"].size > 0
+    by_depth = _oracle_ops(wl, t, 4, True)
+    ref = F.fmm_adaptive(wl.tree, wl.pts, wl.f, wl.phi, wl.nrm, wl.w, 4, wl.mu, True,
+                         ops=by_depth, near=False)
+    return wl, t, by_depth, ref
+
+
+@pytest.mark.parametrize("m2l,precision,tol", [("fft", "fp64", 1e-10), ("fft", "mixed", 1e-5),
+                                               ("dense", "mixed", 1e-5)])
+def test_far_field_six_deep_tree(lib, deep, m2l, precision, tol):
+    """Depth >= 5 on the device: the far field of the six-deep tree against the
+    oracle's, same operators on both sides; the mixed form's per-pass events
+    (stokes_fmm_set_pass_events) cover every launch but the set-up.""" 
+    import ctypes
+    import torch
+    import paper_1909_11085_gb300._abi as A
+    from paper_1909_11085_gb300 import ops
+    wl, t, by_depth, ref = deep
+    U = np.stack([by_depth[d][0] for d in sorted(by_depth)])
+    D = np.stack([by_depth[d][1] for d in sorted(by_depth)])
+    plan = ops.FmmFarPlan(t, p=4, mu=wl.mu, flux=True, uc2e=U, dc2e=D, m2l=m2l,
+                          precision=precision)
+    pts, f, phi, nrm, w = cuda(wl.pts, wl.f, wl.phi, wl.nrm, wl.w)
+    L = A.lib()
+    cap = 256
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
+    for e in evs:
+        e.record()
+    handles = (ctypes.c_void_p * cap)(*[e.cuda_event for e in evs])
+    names = (ctypes.c_char_p * (cap // 2))()
+    count = ctypes.c_int32(0)
+    A.check(L.stokes_fmm_set_pass_events(handles, cap, names, ctypes.byref(count)))
+    try:
+        c0 = L.stokes_launch_count()
+        far = plan(pts, f, phi, nrm, w).cpu().numpy()
+        launches = L.stokes_launch_count() - c0
+    finally:
+        A.check(L.stokes_fmm_set_pass_events(None, 0, None, None))
+    A.check(L.stokes_device_status(A.ptr(plan.ws), plan.ws.numel()))
+    assert _rel(far, ref) <= tol, _rel(far, ref)
+    if precision == "mixed":
+        # the set-up kernel is not hooked; the leaves' cost order (keys and a
+        # three-launch bucket order) is timed as one entry
+        assert count.value == launches - 4
+        got = {names[k].decode() for k in range(count.value)}
+        assert {"s2m", "uc2e", "dchk", "dc2e", "l2t"} <= got
+        assert ({"ufft", "kmulp", "ifft"} <= got) == (m2l == "fft")
+        ms = [evs[2 * k].elapsed_time(evs[2 * k + 1]) for k in range(count.value)]
+        assert min(ms) >= 0.0
+    else:
+        assert count.value == 0

@@ -35,7 +35,6 @@ namespace fmm {
 namespace {
 
 constexpr int kFastTile = 8;       // boxes per CTA of the products
-constexpr int kKmulThreads = 128;  // parents per CTA of the spectral products
 constexpr int kStageThreads = 128; // CTA of the leaf kernels
 constexpr int kErrIndex = 6;
 
@@ -155,6 +154,14 @@ __device__ __forceinline__ void eval_equiv(const EqStage *E, int ns, float x0, f
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) u[a] += csl * uf[a] + csrc * uq[a];
+}
+
+// x rounded to TF32 (10 explicit mantissa bits, round to nearest, ties away),
+// kept in an FP32 register.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 // A source box of a batch of equivalent densities: its density [ns][nc], the
@@ -470,6 +477,8 @@ __global__ void __launch_bounds__(128) k_fast_ufft(Pass P) {
   for (int bb = 0; bb < kFastTile; ++bb)
 #pragma unroll
     for (int c = 0; c < NC; ++c) re[bb][c] = im[bb][c] = 0.f;
+  const float r = half_width(P.t, P.depth);
+  const float sf = 1.0f / r, sq = 1.0f / (r * r);
   const float2 *F = reinterpret_cast<const float2 *>(P.ftab);
   for (int j = 0; j < P.ns; ++j) {
     const float2 f = F[(size_t)j * nf + w];
@@ -482,119 +491,392 @@ __global__ void __launch_bounds__(128) k_fast_ufft(Pass P) {
         im[bb][c] = fmaf(v, f.y, im[bb][c]);
       }
   }
+  // the tensor-core products read the spectra as TF32 hi + lo parts, four
+  // components per box and frequency (the fourth zero without flux)
 #pragma unroll
   for (int bb = 0; bb < kFastTile; ++bb) {
     if (bb >= nbt) break;
-    float *o = P.uhat32 + ((size_t)(bt + bb) * nf + w) * NC * 2;
+    float *oh = P.uhh + ((size_t)(bt + bb) * nf + w) * 8, *ol = P.uhl + ((size_t)(bt + bb) * nf + w) * 8;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      o[2 * c] = re[bb][c];
-      o[2 * c + 1] = im[bb][c];
+    for (int c = 0; c < 4; ++c) {
+      // scaled to the depth: the kernel spectra are those of half-width 1, the
+      // Stokeslet homogeneous of degree -1, the source of degree -2
+      const float sc = c < 3 ? sf : sq;
+      const float vr = c < NC ? sc * re[bb][c] : 0.f, vi = c < NC ? sc * im[bb][c] : 0.f;
+      const float hr = tf32_rna(vr), hi = tf32_rna(vi);
+      oh[2 * c] = hr;
+      oh[2 * c + 1] = hi;
+      ol[2 * c] = tf32_rna(vr - hr);
+      ol[2 * c + 1] = tf32_rna(vi - hi);
     }
   }
 }
 
-// KMULP: the spectral M2L products of one depth (the boxes' parents one depth
-// up), blocked by parent and walked by child octant.  Grid: (parent tiles of
-// 128, frequencies).  V(b) for a child b of parent P is every child of P's
-// 26 neighbours that does not touch b; in child-box units the offset of a
-// source child in octant s of the neighbour in direction dv from the target
-// in octant t is o = 2 dv + s - t, and the pair is in V exactly when some
-// |o_q| >= 2.  The kernel spectra of the CTA's frequency are staged with a
-// row stride of MP floats (a multiple of 4, so that a row is read as float4).
-template <int NC>
-__global__ void __launch_bounds__(kKmulThreads, 4) k_fast_kmulp(Pass P, int32_t first_child0,
-                                                               int32_t first_child1) {
+// The 26 x 8 source boxes of every parent in plist order (the children of its
+// neighbours by direction and octant, -1 where there is none), stored slot by
+// slot: vsrc[slot][plist position].
+__global__ void k_fast_vsrc(Pass P) {
+  const int32_t total = P.bpos[P.t.nbox];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)total * 208;
+       e += stride) {
+    const int32_t i = (int32_t)(e / 208);
+    const int k = (int)(e % 208), dd = k / 8, s = k % 8;
+    const int dir = dd < 13 ? dd : dd + 1;  // direction 13 is the parent itself
+    const int32_t par = P.plist[i];
+    int32_t a = -1;
+    if (in_range(P, par, P.t.nbox)) {
+      const int32_t Q = P.t.colleague[27 * (size_t)par + dir];
+      if (Q >= 0 && in_range(P, Q, P.t.nbox)) {
+        a = P.child8[8 * (size_t)Q + s];
+        if (a >= P.t.nbox) {
+          bad_index(P);
+          a = -1;
+        }
+      }
+    }
+    P.vsrc[(size_t)k * P.t.nbox + i] = a;  // slot-major: consecutive parents adjacent
+  }
+}
+
+__device__ __forceinline__ void cp_async_zfill(void *dst, const void *src, bool valid, int bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  const int sz = valid ? bytes : 0;
+  if (bytes == 16)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(sz)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(sz)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// ----------------------------------------------------------------------
+// The spectral products on the tensor cores (tcgen05, kind::tf32).  For one
+// frequency w the products of a parent P are one dense complex contraction:
+// the 24 check-spectrum values of its 8 children (3 components each) are the
+// 864 source-spectrum values of the 208 children of its 26 neighbours
+// (4 components each) times a 864 x 24 matrix of kernel spectra, the same for
+// every parent (zero where a pair touches).  Written with real numbers
+// (re, im interleaved along both dimensions: [re im] x [[Kr Ki] [-Ki Kr]]) it
+// is D[128 parents][48] = A[128][1728] B[48][1728]^T per CTA: A gathered from
+// the source spectra, B built from the staged kernel spectra, both in FP32
+// split into TF32 hi + lo parts (hi = tf32(x), lo = tf32(x - hi)) so that
+// hi.hi + hi.lo + lo.hi carries FP32 accuracy (the lo.lo term is below it).
+// A K-chunk of 4 source slots is staged in shared memory in the MMA's K-major
+// layout without swizzle (8-row x 16-byte core matrices); one thread issues
+// the MMAs, which accumulate in tensor memory (48 FP32 columns); chunks are
+// double-buffered, a buffer being reused once the commit of its previous MMAs
+// has arrived on its mbarrier (a bounded wait).
+constexpr int kTcThreads = 256;
+constexpr int kTcRows = 128;
+constexpr int kTcCols = 48;        // 8 targets x 3 components x (re, im)
+constexpr uint32_t kTcTmemCols = 128;  // kTcTiles accumulators of 48 columns, 64 apart
+constexpr long long kTcSpinLimit = 4000000000LL;  // SM cycles, about 2 s
+constexpr int kErrTimeout = 4;
+constexpr int kTcSlots = 208;  // 26 neighbour directions x 8 octants
+
+__device__ __forceinline__ uint32_t saddr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ bool tc_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity to complete.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
+  if (tc_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!tc_try_wait(bar, parity))
+    if (clock64() - t0 > kTcSpinLimit) return false;
+  return true;
+}
+// Shared-memory matrix descriptor: K-major, no swizzle; lbo = byte stride of
+// core matrices along K, sbo = along M (or N); version 1.
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ void tc_mma(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+// Byte offset of element (row, k) in a K-major no-swizzle tile whose rows
+// hold kg 16-byte core-matrix columns.
+__device__ __forceinline__ uint32_t tc_off(int row, int k, int kg) {
+  return (uint32_t)((((row >> 3) * kg + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+}
+
+// Per CTA: one frequency and kTcTiles tiles of 128 parents; the K dimension
+// runs over the 208 source slots, 8 reals each (4 components x re, im), one
+// slot per chunk (K = 8, one MMA per tile and hi/lo product).  Warp roles:
+//   warps 0-3 (producers): for each chunk, copy the TF32 hi/lo source spectra
+//     of their rows by cp.async straight into the MMA layout (zero-filled for
+//     missing boxes) and the chunk's B from the table k_fast_btab built for
+//     the call; once a chunk's copies have landed, fence them for the tensor
+//     core and arrive on the chunk's "full" barrier;
+//   thread 128 (MMA): wait "full", issue the 3 MMAs per tile, commit to the
+//     chunk's "empty" barrier (producers refill a buffer only after it);
+//   warps 4-7 (epilogue): after the final commit, read the accumulators from
+//     tensor memory (one lane quarter each) and write the check spectra.
+// A ring of kTcStages buffers lets the producers run ahead of the MMAs.
+// Every wait is bounded; on expiry the role records STK_ETIMEOUT in the error
+// word and stops, and the CTA still drains its copies and MMAs before it
+// frees tensor memory.
+constexpr int kTcTiles = 2;
+constexpr int kTcStages = 5;
+constexpr int kTcAhead = 3;  // chunks of copies a producer keeps in flight (< kTcStages)
+constexpr int kTcProducers = 128;
+struct TcShape {
+  static constexpr int KS = 8;                          // K per chunk
+  static constexpr int ATILE = kTcRows * KS * 4;        // bytes of one A tile (hi or lo)
+  static constexpr int ASTAGE = kTcTiles * 2 * ATILE;   // hi, lo of every tile
+  static constexpr int BTILE = kTcCols * KS * 4;
+  static constexpr int STAGE = ASTAGE + 2 * BTILE;
+  static constexpr int NBAR = 2 * kTcStages + 1;        // full, empty, done
+  static constexpr size_t SMEM = (size_t)kTcStages * STAGE + 8 * NBAR + 16;
+};
+
+// The B operand of every (frequency, source slot): for slot g (neighbour
+// direction and octant) and target octant t, the 3 x 4 complex kernel
+// spectrum of their offset (zero where they touch) as a real 6 x 8 block
+// [[Kr Ki] [-Ki Kr]], split into TF32 hi + lo, laid out as the MMA reads it
+// (K-major core matrices): btab[w][g][hi, lo][tc_off(n, k)].
+__global__ void k_fast_btab(Pass P, int64_t n) {
+  const int m = 3 * P.nc * 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const int64_t wg = e / (kTcCols * 8);
+    const int r = (int)(e % (kTcCols * 8));
+    const int w = (int)(wg / kTcSlots), g = (int)(wg % kTcSlots);
+    const int nn = r >> 3, k = r & 7;
+    const int t = nn / 6, q = (nn >> 1) % 3, rn = nn & 1, c = k >> 1, rk = k & 1;
+    const int dd = g >> 3, sl = g & 7, dir = dd < 13 ? dd : dd + 1;
+    const int ox = 2 * (dir / 9 - 1) + (sl >> 2) - (t >> 2);
+    const int oy = 2 * ((dir / 3) % 3 - 1) + ((sl >> 1) & 1) - ((t >> 1) & 1);
+    const int oz = 2 * (dir % 3 - 1) + (sl & 1) - (t & 1);
+    float val = 0.f;
+    if (c < P.nc && !(ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1)) {
+      const int oi = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
+      const float *K = P.spec32 + ((size_t)w * 343 + oi) * m + (q * P.nc + c) * 2;
+      val = (rk == rn) ? K[0] : (rk == 0 ? K[1] : -K[1]);
+    }
+    const float hi = tf32_rna(val), lo = tf32_rna(val - hi);
+    float *o = P.btab + (size_t)wg * 2 * kTcCols * 8;
+    const uint32_t off = tc_off(nn, k, 2) >> 2;
+    o[off] = hi;
+    o[kTcCols * 8 + off] = lo;
+  }
+}
+
+__device__ __forceinline__ void tc_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   saddr(bar))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 2) k_fast_kmulp_tc(Pass P, int32_t first_child0,
+                                                                int32_t first_child1) {
+  using T = TcShape;
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int M = 3 * NC * 2;             // floats per offset and frequency
-  constexpr int MP = (M + 3) / 4 * 4;       // staged row stride
-  float *S = reinterpret_cast<float *>(smem);  // [343][MP]
+  unsigned char *stages = smem;                                          // [kTcStages][STAGE]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(stages + kTcStages * T::STAGE);
+  uint64_t *full = bars, *empty = bars + kTcStages, *done = bars + 2 * kTcStages;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + T::NBAR);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nf = freq_count(P.p);
   const int w = blockIdx.y;
-  {
-    const float *src = P.spec32 + (size_t)w * 343 * M;
-    for (int e = threadIdx.x; e < 343 * M; e += blockDim.x) S[(e / M) * MP + e % M] = src[e];
-  }
-  __syncthreads();
   const int32_t pos0 = P.bpos[first_child0], pos1 = P.bpos[first_child1];
-  const int32_t i = pos0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= pos1) return;
-  const int32_t par = P.plist[i];
-  if (!in_range(P, par, P.t.nbox)) return;
-  const float r = half_width(P.t, P.depth);
-  const float sf = 1.0f / r, sq = 1.0f / (r * r);
-  float acc[8][6];
-#pragma unroll
-  for (int t = 0; t < 8; ++t)
-#pragma unroll
-    for (int q = 0; q < 6; ++q) acc[t][q] = 0.f;
-  const float2 *UH = reinterpret_cast<const float2 *>(P.uhat32);
-  const int4 *C8 = reinterpret_cast<const int4 *>(P.child8);
-  for (int dir = 0; dir < 27; ++dir) {
-    if (dir == 13) continue;  // the parent itself: its children touch each other
-    int32_t Q = P.t.colleague[27 * (size_t)par + dir];
-    if (Q >= P.t.nbox) {
-      bad_index(P);
-      Q = -1;
+  const int32_t row0 = pos0 + blockIdx.x * (kTcTiles * kTcRows);
+  if (row0 >= pos1) return;  // the whole CTA: nothing allocated yet
+  if (tid == 0) {
+    for (int b = 0; b < kTcStages; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[b])),
+                   "r"(kTcProducers)
+                   : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[b])) : "memory");
     }
-    int4 ca = make_int4(-1, -1, -1, -1), cb = ca;
-    if (Q >= 0) {
-      ca = C8[2 * (size_t)Q];
-      cb = C8[2 * (size_t)Q + 1];
-    }
-    const int32_t an[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
-    const int dx = dir / 9 - 1, dy = (dir / 3) % 3 - 1, dz = dir % 3 - 1;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(done)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(tslot)),
+                 "r"(kTcTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const int32_t nbox = P.t.nbox;
+  bool ok = true;
+
+  if (warp < 4) {
+    // ---------------------------------------------------------- producers
+    // row k * 128 + tid of the CTA (tile k) is parent row0 + k * 128 + tid
+    const unsigned char *UHH = reinterpret_cast<const unsigned char *>(P.uhh);
+    const unsigned char *UHL = reinterpret_cast<const unsigned char *>(P.uhl);
+    int32_t rowi[kTcTiles];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      int32_t a = an[s];
-      if (a >= P.t.nbox) {
-        bad_index(P);
-        a = -1;
+    for (int k = 0; k < kTcTiles; ++k) rowi[k] = row0 + k * kTcRows + tid;
+    int32_t nxt[kTcTiles];
+#pragma unroll
+    for (int k = 0; k < kTcTiles; ++k) nxt[k] = rowi[k] < pos1 ? P.vsrc[rowi[k]] : -1;
+    for (int g = 0; g < kTcSlots; ++g) {
+      const int s = g % kTcStages;
+      if (g >= kTcStages && !tc_wait(&empty[s], (uint32_t)(((g / kTcStages) - 1) & 1))) {
+        ok = false;
+        if (P.err) atomicCAS(P.err, 0, kErrTimeout);
+        break;
       }
-      float2 u[NC];
+      int32_t cur[kTcTiles];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const float sc = c < 3 ? sf : sq;
-        const float2 v = a >= 0 ? UH[((size_t)a * nf + w) * NC + c] : make_float2(0.f, 0.f);
-        u[c] = make_float2(v.x * sc, v.y * sc);
-      }
-      const int sx = s >> 2, sy = (s >> 1) & 1, sz = s & 1;
+      for (int k = 0; k < kTcTiles; ++k) cur[k] = nxt[k];
+      if (g + 1 < kTcSlots)
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int ox = 2 * dx + sx - (t >> 2), oy = 2 * dy + sy - ((t >> 1) & 1),
-                  oz = 2 * dz + sz - (t & 1);
-        if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
-        const float4 *K4 =
-            reinterpret_cast<const float4 *>(S + ((ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)) * MP);
-        float K[MP];
+        for (int k = 0; k < kTcTiles; ++k)
+          nxt[k] = rowi[k] < pos1 ? P.vsrc[(size_t)(g + 1) * nbox + rowi[k]] : -1;
+      unsigned char *st = stages + (size_t)s * T::STAGE;
 #pragma unroll
-        for (int v = 0; v < MP / 4; ++v) {
-          const float4 kv = K4[v];
-          K[4 * v] = kv.x;
-          K[4 * v + 1] = kv.y;
-          K[4 * v + 2] = kv.z;
-          K[4 * v + 3] = kv.w;
+      for (int k = 0; k < kTcTiles; ++k) {
+        int32_t a = cur[k];
+        if (a >= nbox) {
+          bad_index(P);
+          a = -1;
         }
+        const bool okc = a >= 0;
+        const size_t go = okc ? ((size_t)a * nf + w) * 32 : 0;
+        unsigned char *ah = st + (size_t)k * 2 * T::ATILE, *al = ah + T::ATILE;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
+        for (int kg = 0; kg < 2; ++kg) {
+          const uint32_t o = tc_off(tid, 4 * kg, 2);
+          cp_async_zfill(ah + o, UHH + go + 16 * kg, okc, 16);
+          cp_async_zfill(al + o, UHL + go + 16 * kg, okc, 16);
+        }
+      }
+      {  // B: the slot's kernel spectra, hi then lo, as laid out in the table
+        unsigned char *bdst = st + T::ASTAGE;
+        const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(
+            P.btab + ((size_t)w * kTcSlots + g) * 2 * kTcCols * 8);
+        for (int e = tid; e < 2 * T::BTILE / 16; e += kTcProducers)
+          cp_async_zfill(bdst + 16 * e, bsrc + 16 * e, true, 16);
+      }
+      cp_async_commit();
+      if (g >= kTcAhead) {  // chunk g - kTcAhead: its copies have landed
+        cp_async_wait<kTcAhead>();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_arrive(&full[(g - kTcAhead) % kTcStages]);
+      }
+    }
+    cp_async_wait<0>();
+    if (ok) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      for (int c = kTcSlots - kTcAhead; c < kTcSlots; ++c) tc_arrive(&full[c % kTcStages]);
+    }
+  } else if (tid == kTcProducers) {
+    // ---------------------------------------------------------------- MMA
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                           ((uint32_t)(kTcCols >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+    int last = -1;
+    for (int g = 0; g < kTcSlots; ++g) {
+      const int s = g % kTcStages;
+      if (!tc_wait(&full[s], (uint32_t)((g / kTcStages) & 1))) {
+        ok = false;
+        if (P.err) atomicCAS(P.err, 0, kErrTimeout);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned char *st = stages + (size_t)s * T::STAGE;
+      const uint32_t bh = saddr(st + T::ASTAGE), bl = bh + T::BTILE;
 #pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            const float kr = K[2 * (q * NC + c)], ki = K[2 * (q * NC + c) + 1];
-            acc[t][2 * q] = fmaf(kr, u[c].x, fmaf(-ki, u[c].y, acc[t][2 * q]));
-            acc[t][2 * q + 1] = fmaf(kr, u[c].y, fmaf(ki, u[c].x, acc[t][2 * q + 1]));
+      for (int tt = 0; tt < kTcTiles; ++tt) {
+        const uint32_t ah = saddr(st + (size_t)tt * 2 * T::ATILE), al = ah + T::ATILE;
+        const uint32_t d = tmem + (uint32_t)(tt * 64);
+        tc_mma(d, tc_sdesc(ah, 128, 256), tc_sdesc(bh, 128, 256), idesc, g > 0 ? 1u : 0u);
+        tc_mma(d, tc_sdesc(ah, 128, 256), tc_sdesc(bl, 128, 256), idesc, 1u);
+        tc_mma(d, tc_sdesc(al, 128, 256), tc_sdesc(bh, 128, 256), idesc, 1u);
+      }
+      tc_commit(&empty[s]);
+      last = g;
+    }
+    if (ok) {
+      tc_commit(done);
+    } else if (last >= 0 &&
+               !tc_wait(&empty[last % kTcStages], (uint32_t)((last / kTcStages) & 1))) {
+      if (P.err) atomicCAS(P.err, 0, kErrTimeout);
+    }
+  }
+  if (warp >= 4) {
+    // ----------------------------------------------------------- epilogue
+    __syncwarp();
+    const bool fin = tc_wait(done, 0);
+    if (!fin && lane == 0 && P.err) atomicCAS(P.err, 0, kErrTimeout);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__all_sync(kFull, fin)) {
+      const int quarter = warp & 3;
+#pragma unroll 1
+      for (int tt = 0; tt < kTcTiles; ++tt) {
+        const int32_t i = row0 + tt * kTcRows + quarter * 32 + lane;
+        float d[kTcCols];
+#pragma unroll
+        for (int part = 0; part < kTcCols / 16; ++part) {
+          uint32_t v[16];
+          const uint32_t taddr =
+              tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tt * 64 + part * 16);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+              "%10, %11, %12, %13, %14, %15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int e = 0; e < 16; ++e) d[part * 16 + e] = __uint_as_float(v[e]);
+        }
+        if (i < pos1) {
+          const int32_t par = P.plist[i];
+          if (in_range(P, par, nbox)) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int32_t ct = P.child8[8 * (size_t)par + t];
+              if (ct < 0 || !in_range(P, ct, nbox)) continue;
+              float *o = P.chat32 + ((size_t)ct * nf + w) * 6;
+#pragma unroll
+              for (int q = 0; q < 6; ++q) o[q] = d[t * 6 + q];
+            }
           }
         }
       }
     }
   }
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    const int32_t ct = P.child8[8 * (size_t)par + t];
-    if (ct < 0) continue;
-    if (!in_range(P, ct, P.t.nbox)) continue;
-    float *o = P.chat32 + ((size_t)ct * nf + w) * 6;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) o[q] = acc[t][q];
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTcTmemCols)
+                 : "memory");
   }
 }
 
@@ -880,12 +1162,12 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
   const int64_t grid_cap = (int64_t)sms * 8;
   auto gs = [&](int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, grid_cap)); };
 
-  // the spectral products keep as many CTAs resident as shared memory allows
-  static bool carveout_set = false;
-  if (!carveout_set && fft) {
-    cudaFuncSetAttribute(k_fast_kmulp<4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_fast_kmulp<3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    carveout_set = true;
+  // the spectral products take more than 48 KB of dynamic shared memory (the
+  // attribute is set on every call: it is per device and cheap)
+  if (fft) {
+    if ((err = cudaFuncSetAttribute(k_fast_kmulp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)TcShape::SMEM)) != cudaSuccess)
+      return err;
   }
   // set-up: octant table, first-child flags, parent list, DFT tables
   if ((err = cudaMemsetAsync(P.child8, 0xff, sizeof(int32_t) * 8 * (size_t)P.t.nbox, st)) !=
@@ -903,6 +1185,11 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
   pre("plist");
   k_fast_plist<<<gs(P.t.nbox), 256, 0, st>>>(P);
   post();
+  if (fft) {
+    pre("vsrc");
+    k_fast_vsrc<<<gs((int64_t)P.t.nbox * 208), 256, 0, st>>>(P);
+    post();
+  }
   pre("pack");
   k_fast_pack<<<P.t.nleaf, kStageThreads, 0, st>>>(P);
   post();
@@ -916,6 +1203,10 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
     const int64_t n = (int64_t)343 * nf * 3 * P.nc * 2;
     pre("spec");
     k_fast_spec<<<gs(n), 256, 0, st>>>(P, n);
+    post();
+    const int64_t nb = (int64_t)nf * kTcSlots * kTcCols * 8;
+    pre("btab");
+    k_fast_btab<<<gs(nb), 256, 0, st>>>(P, nb);
     post();
   }
   pre("s2m");
@@ -953,14 +1244,12 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
       post();
       // parents of this depth's boxes: at most the boxes of the depth above
       const int32_t npar_max = depth_ptr[d] - depth_ptr[d - 1];
-      dim3 gk((unsigned)((npar_max + kKmulThreads - 1) / kKmulThreads), (unsigned)nf);
       pre("kmulp");
-      if (P.nc == 4)
-        k_fast_kmulp<4><<<gk, kKmulThreads, sizeof(float) * 343 * 24, st>>>(P, depth_ptr[d],
-                                                                             depth_ptr[d + 1]);
-      else
-        k_fast_kmulp<3><<<gk, kKmulThreads, sizeof(float) * 343 * 20, st>>>(P, depth_ptr[d],
-                                                                             depth_ptr[d + 1]);
+      {
+        const int rows = kTcTiles * kTcRows;
+        const dim3 gt((unsigned)((npar_max + rows - 1) / rows), (unsigned)nf);
+        k_fast_kmulp_tc<<<gt, kTcThreads, TcShape::SMEM, st>>>(P, depth_ptr[d], depth_ptr[d + 1]);
+      }
       post();
       pre("ifft");
       {

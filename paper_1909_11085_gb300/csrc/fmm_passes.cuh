@@ -149,6 +149,12 @@ struct Pass {
   float *ftab;         // [ns][nfreq][2] forward DFT of the surface lattice (cos, -sin)
   float *fitab;        // [nfreq][ns][2] inverse over the half spectrum, weighted, / G^3
   int32_t *err;        // device error word (a tree index out of range), at workspace + 8 bytes
+  float *uhh, *uhl;    // [nbox][nfreq][4][2] upward spectra split into TF32 hi + lo parts
+                       // (fourth component zero without flux), operands of the tensor-core M2L
+  float *btab;         // [nfreq][208][hi, lo][48 x 8] kernel spectra of each source slot in
+                       // the tensor-core operand layout (see fmm_fast.cu)
+  int32_t *vsrc;       // [nbox][26 * 8] source box of each neighbour direction and octant of
+                       // the parent at each plist position (-1 where there is none)
   // leaf order of the blocked L2T (most work first): cost keys, leaf numbers,
   // bucket counts and offsets, ranks and the order
   uint64_t *lkeys;
@@ -945,7 +951,7 @@ struct Layout {
   size_t surf, chk, up, dn, sidx, tw, uhat, chat, m2l;
   size_t ploc, qf, pf, nf, surf32, up32, dn32, tw32, spec32, uhat32, chat32, m2l32;
   size_t chk32, ops_hi, ops_lo;
-  size_t child8, bflag, bpos, plist, ftab, fitab;
+  size_t child8, bflag, bpos, plist, ftab, fitab, vsrc, uhh, uhl, btab;
   size_t lkeys, lvals, lcnt, loff, lrank, lorder;
   size_t total;
 };
@@ -976,7 +982,8 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t 
   L.chk = L.up = L.dn = L.tw = L.uhat = L.chat = L.m2l = none;
   L.ploc = L.qf = L.pf = L.nf = L.surf32 = L.up32 = L.dn32 = L.tw32 = L.spec32 = L.uhat32 =
       L.chat32 = L.m2l32 = L.chk32 = L.ops_hi = L.ops_lo = none;
-  L.child8 = L.bflag = L.bpos = L.plist = L.ftab = L.fitab = none;
+  L.child8 = L.bflag = L.bpos = L.plist = L.ftab = L.fitab = L.vsrc = L.uhh = L.uhl = L.btab =
+      none;
   L.lkeys = L.lvals = L.lcnt = L.loff = L.lrank = L.lorder = none;
   if (!mixed) {
     L.chk = take(sizeof(double) * 3 * ns * B);
@@ -1009,6 +1016,10 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t 
       L.m2l32 = take(sizeof(float) * 3 * ns * B);
       L.ftab = take(sizeof(float) * 2 * ns * nf);
       L.fitab = take(sizeof(float) * 2 * ns * nf);
+      L.vsrc = take(sizeof(int32_t) * 26 * 8 * B);
+      L.uhh = take(sizeof(float) * 2 * nf * 4 * B);
+      L.uhl = take(sizeof(float) * 2 * nf * 4 * B);
+      L.btab = take(sizeof(float) * nf * 208 * 2 * 48 * 8);
     }
     L.child8 = take(sizeof(int32_t) * 8 * B);
     L.bflag = take(sizeof(int32_t) * B);
@@ -1063,6 +1074,10 @@ inline void bind(Pass &P, char *ws, const Layout &L, bool fft, bool mixed) {
   P.plist = mixed ? i32(L.plist) : nullptr;
   P.ftab = (fft && mixed) ? f(L.ftab) : nullptr;
   P.fitab = (fft && mixed) ? f(L.fitab) : nullptr;
+  P.vsrc = (fft && mixed) ? i32(L.vsrc) : nullptr;
+  P.uhh = (fft && mixed) ? f(L.uhh) : nullptr;
+  P.uhl = (fft && mixed) ? f(L.uhl) : nullptr;
+  P.btab = (fft && mixed) ? f(L.btab) : nullptr;
   P.lkeys = mixed ? reinterpret_cast<uint64_t *>(ws + L.lkeys) : nullptr;
   P.lvals = mixed ? i32(L.lvals) : nullptr;
   P.lcnt = mixed ? i32(L.lcnt) : nullptr;

@@ -84,9 +84,11 @@ def test_far_field_matches_the_oracle(lib, case, flux, kinds, m2l, precision, to
     # set-up + the passes; Fourier space adds 3 per depth; mixed adds the
     # packing and operator-splitting passes and, with spectra, their rounding,
     # and (the CTA-blocked form) the octant table, the first-child scan, the
-    # parent list and the leaves' cost order (keys and a three-launch bucket order)
+    # parent list and the leaves' cost order (keys and a three-launch bucket order),
+    # and with spectra the table of each parent's source boxes and the table of
+    # the tensor-core operand B
     assert launches == (1 + 2 + 4 * (t["max_depth"] - 1) - 1 + 3 * fft * (t["max_depth"] - 1)
-                        + mixed * (2 + fft + 7))
+                        + mixed * (2 + fft * 3 + 7))
     # accumulate
     import torch
     base = torch.full((wl.pts.shape[0], 3), 0.5, dtype=torch.float64, device="cuda")

@@ -306,6 +306,30 @@ stk_status stokes_near_search_workspace_size(int32_t npatch, int32_t q, int64_t 
 stk_status stokes_fmm_surface(int32_t p, double *pts, int32_t *count);
 stk_status stokes_fmm_check_to_equiv(int32_t p, double r, double mu, int32_t upward,
                                      int32_t flux, double rcond, double *out);
+/* The check-to-equivalent operators of every depth 2..max_depth of a tree
+ * whose root cube has side root_size, as stokes_fmm_far_eval takes them:
+ * uc2e [max_depth - 1][(flux ? 4 : 3) ns][3 ns], dc2e [max_depth - 1][3 ns][3 ns]
+ * (host arrays; nothing written for max_depth < 2).  A Stokeslet-only
+ * operator of half-width r is r times that of half-width 1; with flux,
+ * upward_scaled == 0 decomposes the upward operator at every depth,
+ * upward_scaled != 0 scales the one of half-width 1, the source strengths in
+ * units of r (an exact, not minimum-norm, operator). */
+stk_status stokes_fmm_operators(int32_t p, double root_size, int32_t max_depth, double mu,
+                                int32_t flux, double rcond, int32_t upward_scaled, double *uc2e,
+                                double *dc2e);
+/* The derived arrays of an FMM tree (host): from each box's depth, integer
+ * anchor [nbox][3], parent (-1 for the root) and leaf number (-1 if none),
+ * boxes numbered depth by depth with the root first and children in their
+ * parents' order (checked, STK_EINVAL otherwise), it gives max_depth,
+ * depth_ptr [max_depth + 2] (caller buffer of 23 entries), child_ptr
+ * [nbox + 1], leaf_box [nleaf] and colleague [nbox][27] (the same-depth box
+ * at anchor + (dx, dy, dz), entry (dx+1) 9 + (dy+1) 3 + (dz+1), -1 where there
+ * is none) of stk_fmm_tree. */
+stk_status stokes_fmm_tree_complete(int32_t nbox, int32_t nleaf, const int32_t *depth,
+                                    const int32_t *anchor, const int32_t *parent,
+                                    const int32_t *box_leaf, int32_t *max_depth,
+                                    int32_t *depth_ptr, int32_t *child_ptr, int32_t *leaf_box,
+                                    int32_t *colleague);
 /* Kernel matrix [3 nx][ncomp ny] (row-major) from densities at y [ny][3] to
  * velocities at x [nx][3]: a force per point (Oseen tensor / (8 pi mu)) and,
  * for ncomp = 4, a point-source strength (d / (4 pi |d|^3)); coincident points

@@ -36,7 +36,7 @@ EXPORTS = [
     "stokes_fmm_far_workspace_size", "stokes_fmm_far_eval", "stokes_fmm_m2l_spectra",
     "stokes_octree_build", "stokes_octree_info", "stokes_octree_export", "stokes_octree_destroy",
     "stokes_set_wait_policy", "stokes_pipe_probe_size", "stokes_pipe_probe",
-    "stokes_fmm_set_pass_events",
+    "stokes_fmm_set_pass_events", "stokes_fmm_operators", "stokes_fmm_tree_complete",
 ]
 
 
@@ -103,6 +103,8 @@ def lib():
             L.stokes_set_wait_policy.argtypes = [i64, i32]
             L.stokes_pipe_probe_size.argtypes = [psz]
             L.stokes_fmm_set_pass_events.argtypes = [p, i32, p, ctypes.POINTER(ctypes.c_int32)]
+            L.stokes_fmm_operators.argtypes = [i32, d, i32, d, i32, d, i32, p, p]
+            L.stokes_fmm_tree_complete.argtypes = [i32, i32, p, p, p, p, p, p, p, p, p]
             L.stokes_pipe_probe.argtypes = [i32, i32, p, sz, ctypes.POINTER(ctypes.c_double), p]
             L.stokes_sl_eval_noalloc.argtypes = [p, p, p, p, i64, p, i64, d, p, po, p]
             L.stokes_sldl_grad.argtypes = [p, p, p, p, p, p, i64, p, i64, p, d, p, p, p, p, p, po,

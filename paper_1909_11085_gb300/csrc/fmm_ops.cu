@@ -20,9 +20,11 @@
 // per axis, M2L is a circular convolution; its kernel spectrum per offset is
 // computed here once, at half-width 1 (the Stokeslet scales as 1 / r, the
 // point source as 1 / r^2 at other depths).
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "../../include/stokesgpu.h"
@@ -288,6 +290,135 @@ stk_status stokes_fmm_kernel_matrix(const double *x, int32_t nx, const double *y
   std::vector<double> X(x, x + 3 * (size_t)nx), Y(y, y + 3 * (size_t)ny), K;
   kernel_matrix(X, Y, mu, ncomp, K);
   std::memcpy(out, K.data(), sizeof(double) * K.size());
+  return STK_OK;
+}
+
+// Check-to-equivalent operators of every depth 2..max_depth of a tree with
+// root cube side root_size (the operators of one half-width r = root_size
+// 2^-(d+1) per depth).  The Stokeslet is homogeneous of degree -1, so a
+// Stokeslet-only operator of half-width r is r times that of half-width 1 (the
+// cut-off is relative); the point source is homogeneous of degree -2: with
+// flux, upward_scaled == 0 takes a pseudo-inverse at every depth (minimum-norm
+// densities), upward_scaled != 0 takes the one of half-width 1 and measures
+// source strengths in units of r (their rows scaled by r once more), an exact
+// check-to-equivalent operator at every depth from one decomposition.
+stk_status stokes_fmm_operators(int32_t p, double root_size, int32_t max_depth, double mu,
+                                int32_t flux, double rcond, int32_t upward_scaled, double *uc2e,
+                                double *dc2e) {
+  if (p < 2 || p > 12) return stk::report_error(STK_EINVAL, "p must be in [2, 12]");
+  if (!(root_size > 0.0) || !std::isfinite(root_size))
+    return stk::report_error(STK_EINVAL, "root_size must be finite and > 0");
+  if (max_depth < 0 || max_depth > 21) return stk::report_error(STK_EINVAL, "max_depth must be in [0, 21]");
+  const int ns = surface_count(p), nc = flux ? 4 : 3;
+  const int D = max_depth >= 2 ? max_depth - 1 : 0;
+  if (D == 0) return STK_OK;
+  if (!uc2e || !dc2e) return stk::report_error(STK_EINVAL, "uc2e/dc2e is NULL");
+  const size_t nu = (size_t)nc * ns * 3 * ns, nd = (size_t)9 * ns * ns;
+  std::vector<double> dc1(nd), uc1;
+  stk_status st = stokes_fmm_check_to_equiv(p, 1.0, mu, 0, 0, rcond, dc1.data());
+  if (st != STK_OK) return st;
+  const bool one_upward = !flux || upward_scaled;
+  if (one_upward) {
+    uc1.resize(nu);
+    st = stokes_fmm_check_to_equiv(p, 1.0, mu, 1, flux, rcond, uc1.data());
+    if (st != STK_OK) return st;
+  }
+  for (int i = 0; i < D; ++i) {
+    const double r = root_size / (double)(1 << (i + 2)) / 2;
+    double *U = uc2e + (size_t)i * nu, *Dd = dc2e + (size_t)i * nd;
+    for (size_t e = 0; e < nd; ++e) Dd[e] = r * dc1[e];
+    if (!one_upward) {
+      st = stokes_fmm_check_to_equiv(p, r, mu, 1, 1, rcond, U);
+      if (st != STK_OK) return st;
+    } else {
+      for (size_t e = 0; e < nu; ++e) U[e] = r * uc1[e];
+      if (flux)  // rows of source strengths (component 3 of each point): r once more
+        for (int j = 0; j < ns; ++j)
+          for (int c = 0; c < 3 * ns; ++c) U[((size_t)(4 * j + 3)) * 3 * ns + c] *= r;
+    }
+  }
+  return STK_OK;
+}
+
+// Derived arrays of a tree given per box its depth, integer anchor, parent and
+// leaf number (stk_fmm_tree's numbering: boxes depth by depth, children in
+// their parents' order): depth_ptr [max_depth + 2], child_ptr [nbox + 1],
+// leaf_box [nleaf] and each box's 27 same-depth neighbours (colleague,
+// [nbox][27], -1 where there is none).  The order is checked.
+stk_status stokes_fmm_tree_complete(int32_t nbox, int32_t nleaf, const int32_t *depth,
+                                    const int32_t *anchor, const int32_t *parent,
+                                    const int32_t *box_leaf, int32_t *max_depth,
+                                    int32_t *depth_ptr, int32_t *child_ptr, int32_t *leaf_box,
+                                    int32_t *colleague) {
+  using stk::report_error;
+  if (nbox < 1 || nleaf < 1 || nleaf > nbox) return report_error(STK_EINVAL, "need 1 <= nleaf <= nbox");
+  if (!depth || !anchor || !parent || !box_leaf || !max_depth || !depth_ptr || !child_ptr ||
+      !leaf_box || !colleague)
+    return report_error(STK_EINVAL, "NULL array");
+  if (depth[0] != 0 || parent[0] != -1 || (nbox > 1 && depth[1] == 0))
+    return report_error(STK_EINVAL, "box 0 must be the root, the only box of depth 0");
+  int32_t md = 0;
+  for (int32_t b = 1; b < nbox; ++b) {
+    if (depth[b] < depth[b - 1]) return report_error(STK_EINVAL, "boxes must be numbered depth by depth");
+    const int32_t pb = parent[b];
+    if (pb < 0 || pb >= nbox || depth[pb] != depth[b] - 1)
+      return report_error(STK_EINVAL, "every box but the root needs a parent one depth up");
+    if (b > 1 && pb < parent[b - 1])
+      return report_error(STK_EINVAL, "children must be numbered in their parents' order");
+    if (depth[b] > md) md = depth[b];
+  }
+  if (md > 21) return report_error(STK_EINVAL, "the tree is deeper than 21");
+  *max_depth = md;
+  for (int32_t d = 0, b = 0; d <= md + 1; ++d) {
+    while (b < nbox && depth[b] < d) ++b;
+    depth_ptr[d] = b;
+  }
+  std::vector<int32_t> cnt((size_t)nbox, 0);
+  for (int32_t b = 1; b < nbox; ++b) ++cnt[parent[b]];
+  child_ptr[0] = 1;
+  for (int32_t b = 0; b < nbox; ++b) child_ptr[b + 1] = child_ptr[b] + cnt[b];
+  for (int32_t l = 0; l < nleaf; ++l) leaf_box[l] = -1;
+  int32_t seen = 0;
+  for (int32_t b = 0; b < nbox; ++b) {
+    const int32_t l = box_leaf[b];
+    if (l < 0) continue;
+    if (l >= nleaf || leaf_box[l] >= 0) return report_error(STK_EINVAL, "box_leaf must number every leaf exactly once");
+    if (cnt[b] != 0) return report_error(STK_EINVAL, "a leaf box has children");
+    leaf_box[l] = b;
+    ++seen;
+  }
+  if (seen != nleaf) return report_error(STK_EINVAL, "box_leaf must number every leaf exactly once");
+  // same-depth neighbours: per depth, the boxes' (i, j, k) keys sorted
+  std::vector<std::pair<uint64_t, int32_t>> keys;
+  auto key = [](int64_t i, int64_t j, int64_t k) {
+    return ((uint64_t)i << 42) | ((uint64_t)j << 21) | (uint64_t)k;
+  };
+  for (int32_t d = 0; d <= md; ++d) {
+    const int32_t lo = depth_ptr[d], hi = depth_ptr[d + 1];
+    keys.clear();
+    for (int32_t b = lo; b < hi; ++b) {
+      const int32_t *a = anchor + 3 * (size_t)b;
+      if (a[0] < 0 || a[1] < 0 || a[2] < 0 || a[0] >= (1 << d) || a[1] >= (1 << d) ||
+          a[2] >= (1 << d))
+        return report_error(STK_EINVAL, "an anchor lies outside its depth's grid");
+      keys.emplace_back(key(a[0], a[1], a[2]), b);
+    }
+    std::sort(keys.begin(), keys.end());
+    const int64_t m = (int64_t)1 << d;
+    for (int32_t b = lo; b < hi; ++b) {
+      const int32_t *a = anchor + 3 * (size_t)b;
+      for (int o = 0; o < 27; ++o) {
+        const int64_t i = a[0] + o / 9 - 1, j = a[1] + (o / 3) % 3 - 1, k = a[2] + o % 3 - 1;
+        int32_t q = -1;
+        if (i >= 0 && j >= 0 && k >= 0 && i < m && j < m && k < m) {
+          const uint64_t kq = key(i, j, k);
+          auto it = std::lower_bound(keys.begin(), keys.end(), std::make_pair(kq, (int32_t)-1));
+          if (it != keys.end() && it->first == kq) q = it->second;
+        }
+        colleague[27 * (size_t)b + o] = q;
+      }
+    }
+  }
   return STK_OK;
 }
 

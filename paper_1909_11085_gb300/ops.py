@@ -533,11 +533,13 @@ def octree(pts, max_leaf=256):
 
 
 def fmm_tree_args(t):
-    """The arguments of fmm_tree_arrays from an octree() result."""
+    """The arguments of fmm_tree_arrays from an octree() result (its colleague
+    table is checked against the derived one)."""
     return dict(depth=t["box_depth"], anchor=t["box_anchor"], parent=t["box_parent"],
                 box_leaf=t["box_leaf"], leaf_ptr=t["leaf_ptr"], v_ptr=t["v_ptr"],
                 v_idx=t["v_idx"], w_ptr=t["w_ptr"], w_idx=t["w_idx"], x_ptr=t["x_ptr"],
-                x_idx=t["x_idx"], root_lo=t["root_lo"], root_size=t["root_size"])
+                x_idx=t["x_idx"], root_lo=t["root_lo"], root_size=t["root_size"],
+                colleague=t.get("colleague"))
 
 
 _FMM_DEVICE_KEYS = ("depth", "anchor", "parent", "child_ptr", "box_leaf", "leaf_box", "leaf_ptr",
@@ -545,50 +547,43 @@ _FMM_DEVICE_KEYS = ("depth", "anchor", "parent", "child_ptr", "box_leaf", "leaf_
 
 
 def fmm_tree_arrays(depth, anchor, parent, box_leaf, leaf_ptr, v_ptr, v_idx, w_ptr, w_idx, x_ptr,
-                    x_idx, root_lo, root_size):
+                    x_idx, root_lo, root_size, colleague=None):
     """Host arrays of the far field's tree (stk_fmm_tree, include/stokesgpu.h)
     from each box's depth, integer anchor, parent and leaf number, the leaves'
-    point ranges and the V, W and X lists.  Derives depth_ptr, child_ptr and
-    leaf_box, and checks the order the passes rely on: boxes depth by depth
-    with the root first, children contiguous in their parents' order."""
+    point ranges and the V, W and X lists.  The library derives depth_ptr,
+    child_ptr, leaf_box and the same-depth neighbours (colleague) and checks
+    the order the passes rely on (stokes_fmm_tree_complete); this function
+    marshals the arrays and checks that the lists are CSR lists over the boxes."""
     import numpy as np
-    depth = np.asarray(depth, dtype=np.int64)
-    parent = np.asarray(parent, dtype=np.int64)
-    box_leaf = np.asarray(box_leaf, dtype=np.int64)
-    leaf_ptr = np.asarray(leaf_ptr, dtype=np.int64)
-    M = depth.size
-    if M == 0 or depth[0] != 0 or parent[0] != -1 or (M > 1 and depth[1] == 0):
-        raise ValueError("box 0 must be the root, the only box of depth 0")
-    if np.any(np.diff(depth) < 0):
-        raise ValueError("boxes must be numbered depth by depth")
-    if M > 1:
-        pc = parent[1:]
-        if np.any(pc < 0) or np.any(pc >= M) or np.any(depth[pc] != depth[1:] - 1):
-            raise ValueError("every box but the root needs a parent one depth up")
-        if np.any(np.diff(pc) < 0):
-            raise ValueError("children must be numbered in their parents' order")
-    max_depth = int(depth.max())
-    if max_depth > 21:
-        raise ValueError("the tree is deeper than 21")
-    depth_ptr = np.searchsorted(depth, np.arange(max_depth + 2), side="left")
-    counts = np.bincount(parent[1:], minlength=M) if M > 1 else np.zeros(M, dtype=np.int64)
-    child_ptr = np.concatenate([[1], 1 + np.cumsum(counts)])
-    nleaf = leaf_ptr.size - 1
-    is_leaf = box_leaf >= 0
-    if nleaf < 1 or is_leaf.sum() != nleaf or np.any(box_leaf >= nleaf) or \
-            np.unique(box_leaf[is_leaf]).size != nleaf:
-        raise ValueError("box_leaf must number every leaf exactly once")
-    if np.any(counts[is_leaf] != 0):
-        raise ValueError("a leaf box has children")
-    leaf_box = np.empty(nleaf, dtype=np.int64)
-    leaf_box[box_leaf[is_leaf]] = np.nonzero(is_leaf)[0]
     i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
-    t = {"depth_ptr": i32(depth_ptr), "depth": i32(depth), "anchor": i32(np.asarray(anchor)),
-         "parent": i32(parent), "child_ptr": i32(child_ptr), "box_leaf": i32(box_leaf),
-         "leaf_box": i32(leaf_box), "leaf_ptr": i32(leaf_ptr), "v_ptr": i32(v_ptr),
-         "v_idx": i32(v_idx), "w_ptr": i32(w_ptr), "w_idx": i32(w_idx), "x_ptr": i32(x_ptr),
-         "x_idx": i32(x_idx), "root_lo": np.asarray(root_lo, dtype=np.float64).reshape(3).copy(),
-         "root_size": float(root_size), "max_depth": max_depth}
+    depth, anchor, parent, box_leaf = i32(depth), i32(anchor), i32(parent), i32(box_leaf)
+    leaf_ptr = i32(leaf_ptr)
+    M = depth.size
+    if anchor.shape != (M, 3) or parent.size != M or box_leaf.size != M:
+        raise ValueError("anchor must have shape [nbox, 3] and parent, box_leaf [nbox]")
+    nleaf = leaf_ptr.size - 1
+    if nleaf < 1:
+        raise ValueError("leaf_ptr must hold at least one leaf")
+    md = ctypes.c_int32(0)
+    depth_ptr = np.zeros(23, dtype=np.int32)
+    child_ptr = np.zeros(M + 1, dtype=np.int32)
+    leaf_box = np.zeros(nleaf, dtype=np.int32)
+    coll = np.zeros((M, 27), dtype=np.int32)
+    s = A.lib().stokes_fmm_tree_complete(M, nleaf, depth.ctypes.data, anchor.ctypes.data,
+                                         parent.ctypes.data, box_leaf.ctypes.data, ctypes.byref(md),
+                                         depth_ptr.ctypes.data, child_ptr.ctypes.data,
+                                         leaf_box.ctypes.data, coll.ctypes.data)
+    if s != A.STK_OK:
+        raise ValueError(A.lib().stokes_last_error().decode())
+    max_depth = int(md.value)
+    if colleague is not None and not np.array_equal(i32(colleague), coll):
+        raise ValueError("colleague does not match the tree")
+    t = {"depth_ptr": depth_ptr[:max_depth + 2].copy(), "depth": depth, "anchor": anchor,
+         "parent": parent, "child_ptr": child_ptr, "box_leaf": box_leaf, "leaf_box": leaf_box,
+         "leaf_ptr": leaf_ptr, "v_ptr": i32(v_ptr), "v_idx": i32(v_idx), "w_ptr": i32(w_ptr),
+         "w_idx": i32(w_idx), "x_ptr": i32(x_ptr), "x_idx": i32(x_idx),
+         "root_lo": np.asarray(root_lo, dtype=np.float64).reshape(3).copy(),
+         "root_size": float(root_size), "max_depth": max_depth, "colleague": coll}
     for k in ("v", "w", "x"):
         ptr, idx = t[k + "_ptr"], t[k + "_idx"]
         if ptr.size != M + 1 or ptr[0] != 0 or np.any(np.diff(ptr) < 0) or ptr[-1] != idx.size \
@@ -598,44 +593,18 @@ def fmm_tree_arrays(depth, anchor, parent, box_leaf, leaf_ptr, v_ptr, v_idx, w_p
         raise ValueError("X lists hold leaves only")
     if leaf_ptr[0] != 0 or np.any(np.diff(leaf_ptr) < 0):
         raise ValueError("leaf_ptr must be non-decreasing from 0")
-    if t["anchor"].shape != (M, 3):
-        raise ValueError("anchor must have shape [nbox, 3]")
-    # same-depth neighbours: per depth, the boxes' 63-bit (i, j, k) keys sorted
-    anc = t["anchor"].astype(np.int64)
-    key = lambda a: ((a[:, 0].astype(np.uint64) << np.uint64(42)) |
-                     (a[:, 1].astype(np.uint64) << np.uint64(21)) | a[:, 2].astype(np.uint64))
-    coll = np.full((M, 27), -1, dtype=np.int64)
-    for d in range(max_depth + 1):
-        lo, hi = int(depth_ptr[d]), int(depth_ptr[d + 1])
-        if hi <= lo:
-            continue
-        kd = key(anc[lo:hi])
-        order = np.argsort(kd, kind="stable")
-        ks = kd[order]
-        m = 1 << d
-        for o, (dx, dy, dz) in enumerate(np.ndindex(3, 3, 3)):
-            nb = anc[lo:hi] + np.array([dx - 1, dy - 1, dz - 1])
-            inside = np.all((nb >= 0) & (nb < m), axis=1)
-            kq = key(np.where(inside[:, None], nb, 0))
-            pos = np.minimum(np.searchsorted(ks, kq), ks.size - 1)
-            found = inside & (ks[pos] == kq)
-            coll[lo:hi, o] = np.where(found, lo + order[pos], -1)
-    t["colleague"] = i32(coll)
     return t
 
 
 def fmm_operators(p, root_size, max_depth, mu=1.0, flux=True, rcond=1e-13, upward="per_depth"):
-    """Check-to-equivalent operators of depths 2..max_depth (host, FP64):
-    uc2e [max_depth - 1][(flux ? 4 : 3) ns][3 ns], dc2e [max_depth - 1][3 ns][3 ns].
-    The Stokeslet is homogeneous of degree -1, so a Stokeslet-only operator of a
-    box of half-width r is r times that of half-width 1 (the cut-off is relative).
-    The point source is homogeneous of degree -2: with sources, upward =
-    "per_depth" takes the pseudo-inverse at every depth (the minimum-norm
-    densities), "scaled" takes one at half-width 1 and measures source
-    strengths in units of r (rows of sources scaled by r once more), an exact
-    check-to-equivalent operator at every depth from one decomposition (at
-    p = 6, one instead of one per depth at ~8 s each) whose far field differs
-    from the per-depth one by less than the truncation error."""
+    """Check-to-equivalent operators of depths 2..max_depth (host, FP64,
+    stokes_fmm_operators): uc2e [max_depth - 1][(flux ? 4 : 3) ns][3 ns],
+    dc2e [max_depth - 1][3 ns][3 ns].  upward = "per_depth" decomposes the
+    upward operator with point sources at every depth (minimum-norm densities),
+    "scaled" derives every depth's from the one of half-width 1, source
+    strengths in units of the half-width (exact, one decomposition; at p = 6
+    one instead of one per depth at ~8 s each), a far field within the
+    truncation error of the per-depth one."""
     if upward not in ("per_depth", "scaled"):
         raise ValueError('upward must be "per_depth" or "scaled"')
     import numpy as np
@@ -646,25 +615,9 @@ def fmm_operators(p, root_size, max_depth, mu=1.0, flux=True, rcond=1e-13, upwar
     dc = np.zeros((D, 3 * ns, 3 * ns))
     if D == 0:
         return uc, dc
-    L = A.lib()
-
-    def c2e(r, upward, fl):
-        out = np.zeros(((4 if (upward and fl) else 3) * ns, 3 * ns))
-        A.check(L.stokes_fmm_check_to_equiv(int(p), float(r), float(mu), int(upward), int(fl),
-                                            float(rcond), out.ctypes.data))
-        return out
-
-    dc1 = c2e(1.0, False, False)
-    uc1 = c2e(1.0, True, flux) if (not flux or upward == "scaled") else None
-    for i, d in enumerate(range(2, int(max_depth) + 1)):
-        r = float(root_size) / (1 << d) / 2
-        dc[i] = r * dc1
-        if uc1 is None:
-            uc[i] = c2e(r, True, True)
-        else:
-            uc[i] = r * uc1
-            if flux:  # source rows: strength = r x (strength in units of r)
-                uc[i].reshape(ns, 4, 3 * ns)[:, 3, :] *= r
+    A.check(A.lib().stokes_fmm_operators(int(p), float(root_size), int(max_depth), float(mu),
+                                         int(bool(flux)), float(rcond), int(upward == "scaled"),
+                                         uc.ctypes.data, dc.ctypes.data))
     return uc, dc
 
 

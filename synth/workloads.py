@@ -296,6 +296,13 @@ def one_suspension(rng, orders=(12, 16, 24), max_cells: int = 64):
     ps = [int(orders[i]) for i in rng.integers(0, len(orders), size=ncell)]
     radius = rng.uniform(10.0, 30.0)
     n_wall = int(rng.integers(2000, 20001))
+    return suspension_of(rng, ps, radius, n_wall)
+
+
+def suspension_of(rng, ps, radius: float, n_wall: int):
+    """Cells of orders ps placed in a cylinder wall of the given radius and about
+    n_wall wall points (11 x 11 Clenshaw-Curtis patches)."""
+    ncell = len(ps)
     vol_cell = 94.1
     inner = radius - 4.0
     length = max(16.0, ncell * vol_cell / (0.10 * np.pi * inner * inner))

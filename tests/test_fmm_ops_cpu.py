@@ -119,3 +119,59 @@ def test_m2l_spectra_are_the_dft_of_the_lattice_kernel(L, p, flux):
         assert not spec[(o[0] + 3) * 49 + (o[1] + 3) * 7 + (o[2] + 3)].any()
     assert L.stokes_fmm_m2l_spectra(1, mu, 1, spec.ctypes.data) != 0
     assert L.stokes_fmm_m2l_spectra(p, -1.0, 1, spec.ctypes.data) != 0
+
+
+def test_library_derives_the_tree_arrays():
+    """stokes_fmm_tree_complete (through fmm_tree_arrays): depth ranges, child
+    ranges, leaf boxes and the same-depth neighbours equal a brute-force search
+    over the anchors of a generator tree; a misordered tree is rejected."""
+    import numpy as np
+    from paper_1909_11085_gb300 import ops
+    from synth import octree as O
+    from synth import workloads as W
+    wl = W.p2p_workload(ncell=6, radius=8.0, n_wall_patch=6, max_leaf=32)
+    fl = O.far_lists(wl.tree)
+    t = ops.fmm_tree_arrays(fl.depth, fl.anchor, fl.parent, fl.leaf, wl.tree.leaf_ptr, fl.v_ptr,
+                            fl.v_idx, fl.w_ptr, fl.w_idx, fl.x_ptr, fl.x_idx, wl.tree.root_lo,
+                            wl.tree.root_size)
+    dep, anc, par = np.asarray(fl.depth), np.asarray(fl.anchor), np.asarray(fl.parent)
+    M = dep.size
+    assert list(t["depth_ptr"]) == [int(np.searchsorted(dep, d)) for d in range(t["max_depth"] + 2)]
+    for b in range(M):
+        kids = np.nonzero(par == b)[0]
+        assert t["child_ptr"][b + 1] - t["child_ptr"][b] == kids.size
+        if kids.size:
+            assert t["child_ptr"][b] == kids[0]
+        for o in range(27):
+            dv = np.array([o // 9 - 1, (o // 3) % 3 - 1, o % 3 - 1])
+            hit = np.nonzero((dep == dep[b]) & np.all(anc == anc[b] + dv, axis=1))[0]
+            assert t["colleague"][b, o] == (hit[0] if hit.size else -1)
+    leaf = np.asarray(fl.leaf)
+    assert np.array_equal(leaf[t["leaf_box"]], np.arange(t["leaf_box"].size))
+    bad_depth = dep.copy()
+    bad_depth[1] = 3
+    with pytest.raises(ValueError):
+        ops.fmm_tree_arrays(bad_depth, fl.anchor, fl.parent, fl.leaf, wl.tree.leaf_ptr, fl.v_ptr,
+                            fl.v_idx, fl.w_ptr, fl.w_idx, fl.x_ptr, fl.x_idx, wl.tree.root_lo,
+                            wl.tree.root_size)
+
+
+def test_library_operators_per_depth():
+    """stokes_fmm_operators: every depth's operators equal the single-depth
+    pseudo-inverses of stokes_fmm_check_to_equiv at that half-width (per-depth
+    upward form), and the Stokeslet-only ones scale exactly with r."""
+    import ctypes
+    import numpy as np
+    from paper_1909_11085_gb300 import _abi as A
+    from paper_1909_11085_gb300 import ops
+    p, root, md, mu = 4, 40.0, 4, 0.8
+    U, D = ops.fmm_operators(p, root, md, mu, True)
+    ns = p ** 3 - (p - 2) ** 3
+    for i, d in enumerate(range(2, md + 1)):
+        r = root / (1 << d) / 2
+        u1 = np.zeros((4 * ns, 3 * ns))
+        d1 = np.zeros((3 * ns, 3 * ns))
+        A.check(A.lib().stokes_fmm_check_to_equiv(p, r, mu, 1, 1, 1e-13, u1.ctypes.data))
+        A.check(A.lib().stokes_fmm_check_to_equiv(p, r, mu, 0, 0, 1e-13, d1.ctypes.data))
+        np.testing.assert_allclose(U[i], u1, rtol=0, atol=1e-9 * np.abs(u1).max())
+        np.testing.assert_allclose(D[i], d1, rtol=0, atol=1e-9 * np.abs(d1).max())

@@ -14,7 +14,9 @@ sample of targets.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun (N > 1) every rank evaluates its own copy of the workload
-(independent units, no data-path collective): weak scaling.
+(independent units, no data-path collective): weak scaling.  With --shard the
+one workload is split over the ranks instead (strong scaling): target leaves
+balanced by pair count, a one-off halo, one all_gather per step.
 """
 from __future__ import annotations
 
@@ -388,11 +390,17 @@ def run_forms(dev, flush, stream, peak_tflops):
     ref = oracle.sl(c1.src, c1.f, c1.w, c1.src, c1.mu)
     e = {}
     for prec in ("fp64", "mixed"):
+        # a small sum is bound by its launches: replayed from a CUDA graph
+        plan1 = P.DirectPlan(n1, n1, 1, prec)
         out = torch.empty((n1, 3), dtype=torch.float64, device=dev)
-        ms = _time_ms(lambda: P.sl(src, f, w, None, c1.mu, h=h, precision=prec, out=out), stream,
-                      flush, 10)
-        e[prec] = {"ms": ms, "Gpair/s": n1 * (n1 - 1) / ms / 1e6,
-                   "rel_l2": err(out.cpu().numpy(), ref)}
+        g1 = plan1.capture(src, f, None, None, w, None, c1.mu, h, out)
+        ms = _time_ms(lambda: g1.launch(stream), stream, flush, 20, warm=3)
+        plan1.device_status()
+        ms_call = _time_ms(lambda: P.sl(src, f, w, None, c1.mu, h=h, precision=prec), stream,
+                           flush, 10)
+        e[prec] = {"ms": ms, "ms_direct_call": ms_call, "Gpair/s": n1 * (n1 - 1) / ms / 1e6,
+                   "rel_l2": err(out.cpu().numpy(), ref), "path": "graph replay (DirectPlan)"}
+        del g1, plan1
     e["mixed"]["pct_fp32_peak"] = pct(n1 * (n1 - 1), e["mixed"]["ms"], "SL")
     e["mixed"]["pct_fp32_peak_executed"] = pct_x(n1 * (n1 - 1), e["mixed"]["ms"], "SL")
     forms["direct_sl_8rbc_4352pts"] = dict(pairs=n1 * (n1 - 1), sample="all targets", **e)
@@ -577,6 +585,131 @@ def run_reference(args, rank, world):
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_sharded(args, rank, world, local_rank):
+    """--shard: the one 1,048,928-point near-field step split over the ranks
+    (strong scaling): shard.ShardedP2P partitions the target leaves by pair
+    count with a one-off halo of U-list source leaves (copied to each GPU
+    before the timed region); each timed step is the local P2P call plus the
+    NCCL all_gather that assembles the full velocity on every rank.  value =
+    the global pairs per step x K / the slowest rank's time.  e2e repeats the
+    steps with each rank's inputs copied in from pinned host memory and the
+    assembled velocity read back every step."""
+    import torch
+    import torch.distributed as dist
+    import paper_1909_11085_gb300 as P
+    from paper_1909_11085_gb300 import shard as S
+    from synth import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0:
+        from paper_1909_11085_gb300 import build as B
+        B.build()
+    dist.barrier()
+    wl = W.p2p_workload(ncell=args.ncell, n_wall_patch=args.wall_patches)
+    t = wl.tree
+    pairs = wl.pairs()
+    bufs = {}
+
+    def make_eval(sh):
+        plan = P.P2PPlan(sh.n_local, sh.leaf_ptr, sh.ulist_ptr, sh.ulist_idx, 3, "mixed",
+                         NEAR_RATIO, dev)
+        bufs["out"] = torch.empty((sh.n_local, 3), dtype=torch.float64, device=dev)
+        bufs["plan"] = plan
+        return lambda L: plan(L["pts"], L["f"], L["phi"], L["nrm"], L["w"], L["h"], wl.mu,
+                              bufs["out"])
+
+    sp = S.ShardedP2P(wl.pts, wl.f, wl.phi, wl.nrm, wl.w, wl.h, t.leaf_ptr, t.ulist_ptr,
+                      t.ulist_idx, world, rank, make_eval, dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 0)):
+        sp.step()
+    torch.cuda.synchronize()
+    bufs["plan"].device_status()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    dist.barrier()
+    from paper_1909_11085_gb300 import _abi as A
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    launches0 = A.lib().stokes_launch_count()
+    for i in range(K):
+        flush.zero_()
+        ev[i][0].record(stream)
+        full = sp.step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = A.lib().stokes_launch_count() - launches0
+    clocks = sampler.stop()
+    dist.barrier()
+    bufs["plan"].device_status()
+    tot = torch.tensor([sum(a.elapsed_time(b) for a, b in ev) / 1e3], dtype=torch.float64,
+                       device=dev)
+    dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    tot_s = float(tot.item())
+    # e2e: inputs from pinned host memory every step, full result read back
+    r = sp.shard.rows
+    host = {k: torch.as_tensor(np.ascontiguousarray(getattr(wl, k)[r]),
+                               dtype=torch.float64).pin_memory()
+            for k in ("pts", "f", "phi", "nrm", "w", "h")}
+    res_host = torch.empty((wl.pts.shape[0], 3), dtype=torch.float64).pin_memory()
+    Ke = max(3, min(K, 20))
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        for k, v in host.items():
+            sp.local[k].copy_(v, non_blocking=True)
+        full = sp.step()
+        res_host.copy_(full, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = torch.tensor([e0.elapsed_time(e1) / 1e3 / Ke], dtype=torch.float64, device=dev)
+    dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    counts = torch.tensor([sp.pairs], dtype=torch.int64, device=dev)
+    allc = [torch.zeros_like(counts) for _ in range(world)]
+    dist.all_gather(allc, counts)
+    per_rank = [int(x.item()) for x in allc]
+    # accuracy of the assembled result on a target sample (rank 0)
+    acc = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        oracle.set_threads(cpu_cores())
+        tg = np.sort(np.random.default_rng(20191).choice(wl.pts.shape[0], 2000, replace=False))
+        ref = oracle_sample(wl, tg)
+        u = full.cpu().numpy()[tg]
+        acc = {"vs": "FP64 CPU oracle, 2000 random targets of the assembled result",
+               "mixed_rel_l2": float(np.linalg.norm(u - ref) / np.linalg.norm(ref))}
+    if rank != 0:
+        return 0
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    result = {"metric": METRIC, "value": pairs * K / tot_s / 1e9, "unit": UNIT, "n_gpus": world,
+              "steps": K, "warmup": args.warmup, "ms_per_step": tot_s / K * 1e3,
+              "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+              "dtype": "f32 (f64 near pairs)", "data": "synthetic",
+              "config": dict(workload_config(wl, pairs), parallelism=f"target leaves x{world}"),
+              "shard": {"pairs_per_rank": per_rank,
+                        "balance_max_over_min": max(per_rank) / max(min(per_rank), 1),
+                        "halo": "U-list source leaves of each rank's target leaves, copied once",
+                        "gather": "one NCCL all_gather of the owned rows per step"},
+              "comm_nranks": world,
+              "e2e": {"value": pairs / e2e_s / 1e9, "unit": UNIT,
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(res_host.numel() * 8),
+                      "ms_per_step": e2e_s * 1e3, "steps": Ke},
+              "gpu_launches": int(launches), "clocks": clocks}
+    if acc:
+        result["accuracy"] = acc
+    print(json.dumps(result), flush=True)
     return 0
 
 
@@ -881,21 +1014,31 @@ def main():
                     help="skip the near-pair threshold sweep (alpha = 1, 2, 4)")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip the measured FP32 / FP64 / MUFU pipe rates")
+    ap.add_argument("--shard", action="store_true",
+                    help="split the one near-field step over the ranks (strong scaling: target "
+                         "leaves by pair count, a one-off halo, an all_gather per step) instead "
+                         "of a replica per rank; run under torchrun")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if world > 1:
+    dist_on = world > 1 or args.shard
+    if dist_on:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29511")
+        dist.init_process_group("nccl", rank=rank, world_size=world,
+                                device_id=torch.device("cuda", local_rank))
     try:
+        if args.shard:
+            return run_sharded(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
-        if world > 1:
+        if dist_on:
             import torch.distributed as dist
             dist.destroy_process_group()
 

@@ -170,6 +170,16 @@ stk_status stokes_batched_graph_create(const double *pts, const double *f, const
                                        int32_t nsusp, double mu, double *out,
                                        const stk_opts *opts, void *workspace,
                                        size_t workspace_bytes, void *stream, void **graph_exec);
+/* A direct sum (kernels 1 = SL[f], 2 = DL[phi], 3 = SL[f] + DL[phi], the
+ * arguments of stokes_sl_eval / stokes_dl_eval / stokes_sldl_eval) captured
+ * into a graph: small sums are bound by the latency of their launches, which
+ * a replay takes from the host. */
+stk_status stokes_direct_graph_create(int32_t kernels, const double *src, const double *f,
+                                      const double *nrm, const double *phi, const double *w,
+                                      const double *h, int64_t ns, const double *trg, int64_t nt,
+                                      double mu, double *out, const stk_opts *opts,
+                                      void *workspace, size_t workspace_bytes, void *stream,
+                                      void **graph_exec);
 stk_status stokes_graph_launch(void *graph_exec, void *stream);
 stk_status stokes_graph_destroy(void *graph_exec);
 

@@ -9,11 +9,12 @@ package only marshals PyTorch tensors into it.  Build the library with
 paper_1909_11085_gb300.build.build().
 """
 from .ops import (sl, dl, sldl, p2p, batched, sldl_grad, StokesLayerFn,  # noqa: F401
-                  P2PPlan, BatchedPlan, CheckpointPlan, BIEPlan, upsample_patches,
+                  DirectPlan, P2PPlan, BatchedPlan, CheckpointPlan, BIEPlan, upsample_patches,
                   near_patch_search, octree, fmm_tree_arrays, fmm_tree_args, fmm_operators,
                   fmm_m2l_spectra, FmmFarPlan, FmmPlan)
 
-__all__ = ["sl", "dl", "sldl", "p2p", "batched", "sldl_grad", "StokesLayerFn", "P2PPlan",
+__all__ = ["sl", "dl", "sldl", "p2p", "batched", "sldl_grad", "StokesLayerFn", "DirectPlan",
+           "P2PPlan",
            "BatchedPlan", "CheckpointPlan", "BIEPlan", "upsample_patches",
            "near_patch_search", "octree", "fmm_tree_arrays", "fmm_tree_args", "fmm_operators",
            "fmm_m2l_spectra", "FmmFarPlan", "FmmPlan"]

@@ -37,6 +37,7 @@ EXPORTS = [
     "stokes_octree_build", "stokes_octree_info", "stokes_octree_export", "stokes_octree_destroy",
     "stokes_set_wait_policy", "stokes_pipe_probe_size", "stokes_pipe_probe",
     "stokes_fmm_set_pass_events", "stokes_fmm_operators", "stokes_fmm_tree_complete",
+    "stokes_direct_graph_create",
 ]
 
 
@@ -122,6 +123,8 @@ def lib():
             L.stokes_batched_graph_create.argtypes = [p, p, p, p, p, p, i64, p, p, i32, d, p, po, p,
                                                       sz, p, pp]
             L.stokes_graph_launch.argtypes = [p, p]
+            L.stokes_direct_graph_create.argtypes = [i32, p, p, p, p, p, p, i64, p, i64, d, p, po,
+                                                     p, sz, p, pp]
             L.stokes_checkpoint_eval.argtypes = [i32, p, p, i32, i32, i32, p, p, p, p, p, p, p,
                                                  i64, d, d, i32, d, p, po, p, sz, p]
             L.stokes_checkpoint_workspace_size.argtypes = [i32, i32, i32, i32, i64, i32, po, psz]

@@ -955,6 +955,19 @@ stk_status stokes_batched_graph_create(const double *pts, const double *f, const
   }, graph_exec);
 }
 
+stk_status stokes_direct_graph_create(int32_t kernels, const double *src, const double *f,
+                                      const double *nrm, const double *phi, const double *w,
+                                      const double *h, int64_t ns, const double *trg, int64_t nt,
+                                      double mu, double *out, const stk_opts *opts,
+                                      void *workspace, size_t workspace_bytes, void *stream,
+                                      void **graph_exec) {
+  if (kernels < 1 || kernels > 3) return fail(STK_EINVAL, "kernels must be 1, 2 or 3");
+  return capture_graph(reinterpret_cast<cudaStream_t>(stream), [&]() {
+    return direct_common(kernels, src, f, nrm, phi, w, h, ns, trg, nt, kernels & K_SL ? mu : 1.0,
+                         out, opts, workspace, workspace_bytes, stream);
+  }, graph_exec);
+}
+
 stk_status stokes_graph_launch(void *graph_exec, void *stream) {
   if (!graph_exec) return fail(STK_EINVAL, "graph_exec is NULL");
   CU(cudaGraphLaunch(reinterpret_cast<cudaGraphExec_t>(graph_exec),

@@ -80,6 +80,75 @@ def sldl(src, f, nrm, phi, w, trg=None, mu=1.0, h=None, precision="mixed", near_
                    accumulate, source_splits)
 
 
+class DirectPlan:
+    """A direct sum of fixed sizes (ns sources, nt targets; kernels 1 SL, 2 DL,
+    3 SL + DL) with a reusable workspace; capture() records one call into a
+    CUDA graph (stokes_direct_graph_create) whose replays read the same
+    buffers, so that a small sum is not bound by the host's launch latency."""
+
+    def __init__(self, ns, nt, kernels=1, precision="mixed", near_ratio=1.0, source_splits=0,
+                 device=None):
+        device = device or torch.device("cuda")
+        self.ns, self.nt, self.kernels = int(ns), int(nt), int(kernels)
+        self.opts = A.make_opts(precision, near_ratio, False, source_splits)
+        nb = ctypes.c_size_t(0)
+        with torch.cuda.device(device):
+            A.check(A.lib().stokes_direct_workspace_size(self.ns, self.nt, self.kernels,
+                                                         ctypes.byref(self.opts), ctypes.byref(nb)))
+        self.ws = A.workspace(nb.value, device)
+        self.device = device
+
+    def _args(self, src, f, nrm, phi, w, trg, mu, h, out):
+        src = A.vec3(src, "src", self.ns)
+        trg = src if trg is None else A.vec3(trg, "trg", self.nt)
+        if trg.shape[0] != self.nt:
+            raise ValueError(f"{self.nt} targets expected")
+        f = A.vec3(f, "f", self.ns) if self.kernels & 1 else None
+        nrm = A.vec3(nrm, "nrm", self.ns) if self.kernels & 2 else None
+        phi = A.vec3(phi, "phi", self.ns) if self.kernels & 2 else None
+        w, h = A.vec1(w, "w", self.ns), A.vec1(h, "h", self.ns)
+        out = A.vec3(out, "out", self.nt)
+        self._keep = (src, f, nrm, phi, w, trg, h, out)
+        return (A.ptr(src), A.ptr(f), A.ptr(nrm), A.ptr(phi), A.ptr(w), A.ptr(h), self.ns,
+                A.ptr(trg), self.nt, float(mu), A.ptr(out))
+
+    def __call__(self, src, f=None, nrm=None, phi=None, w=None, trg=None, mu=1.0, h=None,
+                 out=None):
+        out = out if out is not None else torch.empty((self.nt, 3), dtype=torch.float64,
+                                                       device=src.device)
+        a = self._args(src, f, nrm, phi, w, trg, mu, h, out)
+        L = A.lib()
+        with torch.cuda.device(src.device):
+            rest = (ctypes.byref(self.opts), A.ptr(self.ws), self.ws.numel(),
+                    A.stream_ptr(src.device))
+            if self.kernels == A.SL:
+                A.check(L.stokes_sl_eval(a[0], a[1], a[4], a[5], a[6], a[7], a[8], a[9], a[10],
+                                         *rest))
+            elif self.kernels == A.DL:
+                A.check(L.stokes_dl_eval(a[0], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[10],
+                                         *rest))
+            else:
+                A.check(L.stokes_sldl_eval(*a, *rest))
+        return out
+
+    def capture(self, src, f=None, nrm=None, phi=None, w=None, trg=None, mu=1.0, h=None,
+                out=None):
+        """Captures one call into a CUDA graph that replays on the same buffers."""
+        out = out if out is not None else torch.empty((self.nt, 3), dtype=torch.float64,
+                                                       device=src.device)
+        a = self._args(src, f, nrm, phi, w, trg, mu, h, out)
+        ge = ctypes.c_void_p(0)
+        stream = torch.cuda.Stream(src.device)
+        with torch.cuda.device(src.device), torch.cuda.stream(stream):
+            A.check(A.lib().stokes_direct_graph_create(self.kernels, *a, ctypes.byref(self.opts),
+                                                       A.ptr(self.ws), self.ws.numel(),
+                                                       A.stream_ptr(src.device), ctypes.byref(ge)))
+        return Graph(ge, out, self._keep + (self.ws,))
+
+    def device_status(self):
+        A.check(A.lib().stokes_device_status(A.ptr(self.ws), self.ws.numel()))
+
+
 class P2PPlan:
     """Device-resident U-list structure plus a reusable workspace for repeated calls."""
 

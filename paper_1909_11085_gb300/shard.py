@@ -178,3 +178,60 @@ def gather_rows(local_out, global_rows, n_global: int, group=None):
         k = int(ln.item())
         full[i[:k]] = v[:k]
     return full
+
+
+class ShardedP2P:
+    """One rank's part of the near-field step (P2P over U-lists) sharded over
+    the ranks of a process group: the partition of shard_p2p, the rank's
+    inputs (owned leaves and halo leaves) copied to its device once, and a step
+    that evaluates the local sum and assembles every rank's owned rows with
+    gather_rows.
+
+    make_eval(shard) returns the rank's evaluator, a callable taking the dict
+    of local input tensors (pts, f, phi, nrm, w, h) and returning the local
+    velocities [n_local, 3] (a P2PPlan on a GPU).  pairs is the rank's pair
+    count (its owned leaves against their U-lists)."""
+
+    def __init__(self, pts, f, phi, nrm, w, h, leaf_ptr, ulist_ptr, ulist_idx, world: int,
+                 rank: int, make_eval, device, group=None):
+        import torch
+        self.world, self.rank, self.group = int(world), int(rank), group
+        self.n_global = int(np.asarray(pts).shape[0])
+        self.shard = shard_p2p(leaf_ptr, ulist_ptr, ulist_idx, world, rank)
+        r = self.shard.rows
+        T = lambda a: None if a is None else torch.as_tensor(
+            np.ascontiguousarray(np.asarray(a)[r]), dtype=torch.float64, device=device)
+        self.local = {"pts": T(pts), "f": T(f), "phi": T(phi), "nrm": T(nrm), "w": T(w), "h": T(h)}
+        self.owned_rows = r[:self.shard.n_owned]
+        self.evaluate = make_eval(self.shard)
+        costs = p2p_leaf_costs(self.shard.leaf_ptr, self.shard.ulist_ptr, self.shard.ulist_idx)
+        self.pairs = int(costs.sum())
+        # the row map of the gather is fixed: exchanged once, so that a step
+        # moves only the velocities (one all_gather, no host synchronisation)
+        import torch.distributed as dist
+        ws = dist.get_world_size(group)
+        n_loc = torch.tensor([self.shard.n_owned], dtype=torch.int64, device=device)
+        lens = [torch.zeros_like(n_loc) for _ in range(ws)]
+        dist.all_gather(lens, n_loc, group=group)
+        self.lens = [int(x.item()) for x in lens]
+        self.m = max(self.lens)
+        pad_i = torch.full((self.m,), -1, dtype=torch.int64, device=device)
+        pad_i[:self.shard.n_owned] = torch.as_tensor(self.owned_rows, device=device)
+        all_i = [torch.empty_like(pad_i) for _ in range(ws)]
+        dist.all_gather(all_i, pad_i, group=group)
+        self.gather_index = torch.cat([i[:k] for i, k in zip(all_i, self.lens)])
+        self.pad_v = torch.zeros((self.m, 3), dtype=torch.float64, device=device)
+        self.all_v = [torch.empty_like(self.pad_v) for _ in range(ws)]
+        self.full = torch.zeros((self.n_global, 3), dtype=torch.float64, device=device)
+
+    def step(self):
+        """Local evaluation + gather of the owned rows: the full [n, 3] velocity
+        on every rank (the same buffer each step)."""
+        import torch
+        import torch.distributed as dist
+        out = self.evaluate(self.local)
+        self.pad_v[:self.shard.n_owned] = out[:self.shard.n_owned]
+        dist.all_gather(self.all_v, self.pad_v, group=self.group)
+        vals = torch.cat([v[:k] for v, k in zip(self.all_v, self.lens)])
+        self.full[self.gather_index] = vals
+        return self.full

@@ -119,3 +119,55 @@ def test_two_gloo_ranks_reproduce_unsharded_sums(tmp_path):
     src, f, wts = rng.standard_normal((300, 3)), rng.standard_normal((300, 3)), np.ones(300)
     trg = rng.standard_normal((101, 3))
     np.testing.assert_array_equal(res["direct"], oracle.sl(src, f, wts, trg, 1.0))
+
+
+def _sharded_main(rank, world, port, out_path):
+    """The sharded near-field step as bench.py --shard runs it (ShardedP2P),
+    with the oracle as each rank's evaluator on CPU tensors."""
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        c = W.p2p_workload(ncell=40, radius=12.0, n_wall_patch=16, max_leaf=64)
+        t = c.tree
+
+        def make_eval(sh):
+            def ev(L):
+                u = oracle.p2p(L["pts"].numpy(), L["f"].numpy(), L["phi"].numpy(),
+                               L["nrm"].numpy(), L["w"].numpy(), sh.leaf_ptr, sh.ulist_ptr,
+                               sh.ulist_idx, 3, c.mu)
+                return torch.as_tensor(u)
+            return ev
+
+        sp = S.ShardedP2P(c.pts, c.f, c.phi, c.nrm, c.w, c.h, t.leaf_ptr, t.ulist_ptr,
+                          t.ulist_idx, world, rank, make_eval, "cpu")
+        full = sp.step()
+        pairs = torch.tensor([sp.pairs], dtype=torch.int64)
+        allp = [torch.zeros_like(pairs) for _ in range(world)]
+        dist.all_gather(allp, pairs)
+        if rank == 0:
+            np.savez(out_path, full=full.numpy(), pairs=np.array([int(x) for x in allp]))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(300)
+def test_sharded_step_as_the_bench_runs_it(tmp_path):
+    """ShardedP2P with two gloo ranks: the assembled velocity equals the
+    unsharded near field, the ranks' pair counts add up to the total and are
+    within 5% of each other."""
+    import torch.multiprocessing as mp
+    oracle.build()
+    out_path = str(tmp_path / "sharded.npz")
+    mp.start_processes(_sharded_main, args=(2, _free_port(), out_path), nprocs=2, join=True,
+                       start_method="spawn")
+    res = np.load(out_path)
+    c = W.p2p_workload(ncell=40, radius=12.0, n_wall_patch=16, max_leaf=64)
+    t = c.tree
+    ref = oracle.p2p(c.pts, c.f, c.phi, c.nrm, c.w, t.leaf_ptr, t.ulist_ptr, t.ulist_idx, 3, c.mu)
+    np.testing.assert_allclose(res["full"], ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+    p = res["pairs"]
+    assert p.sum() == c.pairs()
+    assert p.max() <= 1.05 * p.min(), p

@@ -310,6 +310,60 @@ def run_alpha_sweep(wl, dev, stream, flush, pts, f, phi, nrm, w, h, alphas=(1.0,
     return res
 
 
+def fmm_pass_times(plan, args, out, stream, flush):
+    """Device time of each pass of one mixed far-field call (the library's
+    per-launch events, stokes_fmm_set_pass_events), summed per pass name."""
+    import ctypes
+    import torch
+    from paper_1909_11085_gb300 import _abi as A
+    L = A.lib()
+    cap = 1024
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
+    for e in evs:
+        e.record(stream)
+    torch.cuda.synchronize()
+    handles = (ctypes.c_void_p * cap)(*[e.cuda_event for e in evs])
+    names = (ctypes.c_char_p * (cap // 2))()
+    cnt = ctypes.c_int32(0)
+    flush.zero_()
+    A.check(L.stokes_fmm_set_pass_events(handles, cap, names, ctypes.byref(cnt)))
+    try:
+        plan(*args, out=out)
+    finally:
+        A.check(L.stokes_fmm_set_pass_events(None, 0, None, None))
+    torch.cuda.synchronize()
+    per = {}
+    for k in range(cnt.value):
+        nm = names[k].decode()
+        per[nm] = per.get(nm, 0.0) + evs[2 * k].elapsed_time(evs[2 * k + 1])
+    return per
+
+
+def kmulp_roofline(ms, v_pairs, p, parents):
+    """The spectral M2L products (tcgen05, 3xTF32) against the tensor peak:
+    algorithmic work 12 complex multiply-adds = 96 flops per V-list pair and
+    frequency; executed, a [128 parents] x [48] x [8 x 208 slots] real product
+    per parent tile, frequency and hi/lo term (3 terms), zero blocks included."""
+    if not ms:
+        return None
+    nf = 4 * p * p * (p + 1)
+    algo = 96.0 * v_pairs * nf
+    executed = 2.0 * 48 * 8 * 208 * 3 * parents * nf
+    meas = {}
+    try:
+        meas = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    bf16 = meas.get("bf16_tflops") or 1900.0
+    peak = bf16 * 1.1 / 2.25  # TF32 dense = bf16 dense x (1.1 / 2.25), nominal ratio
+    ach = algo / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "unit": "TFLOP/s", "achieved": ach, "peak": peak,
+            "frac": ach / peak, "executed_tflops": executed / (ms / 1e3) / 1e12,
+            "executed_frac": executed / (ms / 1e3) / 1e12 / peak,
+            "peak_basis": "TF32 dense = measured bf16 burst x 1.1 / 2.25 (of measured)",
+            "flops_basis": "96 per V-list pair and frequency (12 complex multiply-adds)"}
+
+
 def run_fmm_far(wl, near, near_ms_step, dev, stream, flush, p=4):
     """The whole single-GPU FMM: the far field (stokes_fmm_far_eval) on the
     near-field workload's own octree beside the timed near-field step.  Host
@@ -359,9 +413,55 @@ def run_fmm_far(wl, near, near_ms_step, dev, stream, flush, p=4):
                         "host_plan_s": plan_s, "workspace_MB": plan.ws.numel() / 1e6,
                         "rel_l2_vs_direct": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
                         "max_rel_vs_direct": float(np.abs(u - ref).max() / np.abs(ref).max())}
+            if prec == "mixed":
+                res[key]["passes_ms"] = fmm_pass_times(plan, (pts, f, phi, nrm, w), far, stream,
+                                                       flush)
+                if m2l == "fft":
+                    res[key]["kmulp_roofline"] = kmulp_roofline(
+                        res[key]["passes_ms"].get("kmulp"), int(tn["v_idx"].size), p,
+                        int(np.sum(np.diff(t["child_ptr"]) > 0) - 1))
             log(f"[fmm] {key}: {res[key]}")
             del plan, far
     torch.cuda.empty_cache()
+    return res
+
+
+def run_nearzone(dev, flush, stream, c6=None, x6=None):
+    """The near-zone search (Sec. 3.2): 2^20 points spread through the vessel
+    against the 320 wall patches, d_eps = 2 h_c; on the cylinder the closest
+    point is the radial projection, which checks every hit away from the open
+    ends."""
+    import torch
+    import paper_1909_11085_gb300 as P
+    from synth import workloads as W
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    if c6 is None:
+        c6 = W.checkpoint_wall_workload()
+        x6 = T(c6.pts)
+    rng9 = np.random.default_rng(11085009)
+    m9, Rv, Lv = 1 << 20, 50.0, 74.0
+    rho9 = Rv * np.sqrt(rng9.uniform(0.0, 1.0, m9))
+    th9 = rng9.uniform(0.0, 2.0 * np.pi, m9)
+    z9 = rng9.uniform(0.0, Lv, m9)
+    x9 = np.stack([rho9 * np.cos(th9), rho9 * np.sin(th9), z9], axis=1)
+    d9 = 2.0 * c6.hc
+    X9 = T(x9)
+    ms9 = _time_ms(lambda: P.near_patch_search(x6, c6.npatch, X9, d9, c6.q), stream, flush, 3)
+    p9, _, y9, _, dist9 = (t.cpu().numpy() for t in P.near_patch_search(x6, c6.npatch, X9, d9, c6.q))
+    inner = (z9 > d9) & (z9 < Lv - d9)
+    want = inner & (Rv - rho9 <= d9 * (1 - 1e-9))
+    got = inner & (p9 >= 0)
+    yref = np.stack([Rv * np.cos(th9), Rv * np.sin(th9), z9], axis=1)
+    res = {
+        "targets": m9, "patches": int(c6.npatch), "d_eps": d9, "ms": ms9,
+        "Mtargets/s": m9 / ms9 / 1e3, "targets_within_d_eps": int((p9 >= 0).sum()),
+        "closed_form": {"hit_mismatch": int((want != got).sum()),
+                        "max_dist_err": float(np.abs(dist9[want & got] - (Rv - rho9[want & got])).max()),
+                        "max_y_err": float(np.abs(y9[want & got] - yref[want & got]).max())},
+        "note": "FP64 closest-point Newton per candidate patch; hits checked against the radial "
+                "projection for targets away from the open ends"}
+    log(f"[forms] near-zone search: {res}")
+    del X9
     return res
 
 
@@ -502,33 +602,7 @@ def run_forms(dev, flush, stream, peak_tflops):
         "note": "(D - I/2 + N) phi at all 38,720 nodes; D - I/2 by the check points above"}
     log(f"[forms] bie matvec: {forms['bie_matvec_wall_320patches']}")
     del plan6, bie, fp6, fn6, fw6, fh6
-    # near-zone search (Sec. 3.2): 2^20 points spread through the vessel against the same
-    # 320 wall patches, d_eps = 2 h_c; on the cylinder the closest point is the radial
-    # projection, which checks every hit away from the open ends
-    rng9 = np.random.default_rng(11085009)
-    m9, Rv, Lv = 1 << 20, 50.0, 74.0
-    rho9 = Rv * np.sqrt(rng9.uniform(0.0, 1.0, m9))
-    th9 = rng9.uniform(0.0, 2.0 * np.pi, m9)
-    z9 = rng9.uniform(0.0, Lv, m9)
-    x9 = np.stack([rho9 * np.cos(th9), rho9 * np.sin(th9), z9], axis=1)
-    d9 = 2.0 * c6.hc
-    X9 = T(x9)
-    ms9 = _time_ms(lambda: P.near_patch_search(x6, c6.npatch, X9, d9, c6.q), stream, flush, 3)
-    p9, _, y9, _, dist9 = (t.cpu().numpy() for t in P.near_patch_search(x6, c6.npatch, X9, d9, c6.q))
-    inner = (z9 > d9) & (z9 < Lv - d9)
-    want = inner & (Rv - rho9 <= d9 * (1 - 1e-9))
-    got = inner & (p9 >= 0)
-    yref = np.stack([Rv * np.cos(th9), Rv * np.sin(th9), z9], axis=1)
-    forms["nearzone_search_wall_320patches"] = {
-        "targets": m9, "patches": int(c6.npatch), "d_eps": d9, "ms": ms9,
-        "Mtargets/s": m9 / ms9 / 1e3, "targets_within_d_eps": int((p9 >= 0).sum()),
-        "closed_form": {"hit_mismatch": int((want != got).sum()),
-                        "max_dist_err": float(np.abs(dist9[want & got] - (Rv - rho9[want & got])).max()),
-                        "max_y_err": float(np.abs(y9[want & got] - yref[want & got]).max())},
-        "note": "FP64 closest-point Newton per candidate patch; hits checked against the radial "
-                "projection for targets away from the open ends"}
-    log(f"[forms] near-zone search: {forms['nearzone_search_wall_320patches']}")
-    del X9
+    forms["nearzone_search_wall_320patches"] = run_nearzone(dev, flush, stream, c6, x6)
 
     c5, g5 = W.adjoint_workload()
     n5 = c5.src.shape[0]
@@ -993,6 +1067,35 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_only(args):
+    """One form alone (see --only)."""
+    import torch
+    from paper_1909_11085_gb300 import build as B
+    B.build()
+    import oracle
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    if args.only == "nearzone":
+        res = run_nearzone(dev, flush, stream)
+    else:
+        import paper_1909_11085_gb300 as P
+        from synth import workloads as W
+        wl = W.p2p_workload(ncell=args.ncell, n_wall_patch=args.wall_patches)
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+        t = wl.tree
+        near = torch.empty((wl.pts.shape[0], 3), dtype=torch.float64, device=dev)
+        plan = P.P2PPlan(wl.pts.shape[0], t.leaf_ptr, t.ulist_ptr, t.ulist_idx, 3, "mixed",
+                         NEAR_RATIO, dev)
+        args_ = tuple(T(a) for a in (wl.pts, wl.f, wl.phi, wl.nrm, wl.w, wl.h))
+        ms = _time_ms(lambda: plan(*args_, wl.mu, near), stream, flush, 5)
+        res = run_fmm_far(wl, near, ms, dev, stream, flush)
+    print(json.dumps({"only": args.only, "result": res}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1014,6 +1117,10 @@ def main():
                     help="skip the near-pair threshold sweep (alpha = 1, 2, 4)")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip the measured FP32 / FP64 / MUFU pipe rates")
+    ap.add_argument("--only", choices=["fmm", "nearzone"], default=None,
+                    help="run one form alone and print its JSON (profiling helper: small device "
+                         "footprint): the FMM far field beside the near field of the --ncell / "
+                         "--wall-patches workload, or the near-zone search")
     ap.add_argument("--shard", action="store_true",
                     help="split the one near-field step over the ranks (strong scaling: target "
                          "leaves by pair count, a one-off halo, an all_gather per step) instead "
@@ -1024,6 +1131,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.only:
+        return run_only(args)
     dist_on = world > 1 or args.shard
     if dist_on:
         import torch

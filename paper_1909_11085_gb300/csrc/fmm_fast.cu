@@ -480,16 +480,24 @@ __global__ void __launch_bounds__(128) k_fast_ufft(Pass P) {
   const float r = half_width(P.t, P.depth);
   const float sf = 1.0f / r, sq = 1.0f / (r * r);
   const float2 *F = reinterpret_cast<const float2 *>(P.ftab);
-  for (int j = 0; j < P.ns; ++j) {
-    const float2 f = F[(size_t)j * nf + w];
+  for (int j0 = 0; j0 < P.ns; j0 += 4) {
+    float2 fq[4];
 #pragma unroll
-    for (int bb = 0; bb < kFastTile; ++bb)
+    for (int q = 0; q < 4; ++q)
+      fq[q] = j0 + q < P.ns ? F[(size_t)(j0 + q) * nf + w] : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const float v = U[(bb * P.ns + j) * NC + c];
-        re[bb][c] = fmaf(v, f.x, re[bb][c]);
-        im[bb][c] = fmaf(v, f.y, im[bb][c]);
-      }
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + q;
+      if (j >= P.ns) break;
+#pragma unroll
+      for (int bb = 0; bb < kFastTile; ++bb)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const float v = U[(bb * P.ns + j) * NC + c];
+          re[bb][c] = fmaf(v, fq[q].x, re[bb][c]);
+          im[bb][c] = fmaf(v, fq[q].y, im[bb][c]);
+        }
+    }
   }
   // the tensor-core products read the spectra as TF32 hi + lo parts, four
   // components per box and frequency (the fourth zero without flux)
@@ -739,10 +747,20 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_fast_kmulp_tc(Pass P, int32_t
     int32_t rowi[kTcTiles];
 #pragma unroll
     for (int k = 0; k < kTcTiles; ++k) rowi[k] = row0 + k * kTcRows + tid;
-    int32_t nxt[kTcTiles];
+    // source-box indices of the next kIdxAhead chunks in registers (the loads
+    // of chunk g + kIdxAhead are issued while chunk g is handled)
+    constexpr int kIdxAhead = 4;
+    static_assert(kTcSlots % kIdxAhead == 0, "chunk groups");
+    int32_t ring[kIdxAhead][kTcTiles];
 #pragma unroll
-    for (int k = 0; k < kTcTiles; ++k) nxt[k] = rowi[k] < pos1 ? P.vsrc[rowi[k]] : -1;
-    for (int g = 0; g < kTcSlots; ++g) {
+    for (int q = 0; q < kIdxAhead; ++q)
+#pragma unroll
+      for (int k = 0; k < kTcTiles; ++k)
+        ring[q][k] = rowi[k] < pos1 ? P.vsrc[(size_t)q * nbox + rowi[k]] : -1;
+    for (int g0 = 0; g0 < kTcSlots && ok; g0 += kIdxAhead)
+#pragma unroll
+    for (int q = 0; q < kIdxAhead; ++q) {
+      const int g = g0 + q;
       const int s = g % kTcStages;
       if (g >= kTcStages && !tc_wait(&empty[s], (uint32_t)(((g / kTcStages) - 1) & 1))) {
         ok = false;
@@ -751,11 +769,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_fast_kmulp_tc(Pass P, int32_t
       }
       int32_t cur[kTcTiles];
 #pragma unroll
-      for (int k = 0; k < kTcTiles; ++k) cur[k] = nxt[k];
-      if (g + 1 < kTcSlots)
+      for (int k = 0; k < kTcTiles; ++k) cur[k] = ring[q][k];
+      if (g + kIdxAhead < kTcSlots)
 #pragma unroll
         for (int k = 0; k < kTcTiles; ++k)
-          nxt[k] = rowi[k] < pos1 ? P.vsrc[(size_t)(g + 1) * nbox + rowi[k]] : -1;
+          ring[q][k] = rowi[k] < pos1 ? P.vsrc[(size_t)(g + kIdxAhead) * nbox + rowi[k]] : -1;
       unsigned char *st = stages + (size_t)s * T::STAGE;
 #pragma unroll
       for (int k = 0; k < kTcTiles; ++k) {

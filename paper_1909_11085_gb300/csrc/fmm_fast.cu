@@ -455,8 +455,12 @@ __global__ void __launch_bounds__(256) k_fast_c2e(Pass P) {
 
 // ------------------------------------------------------------- downward
 // UFFT: spectra of the upward densities of a tile of boxes,
-// uhat[b][w][c] = sum_j up[b][j][c] (cos - i sin)(2 pi (s_j . k_w mod G) / G);
+// uhat[w][b][c] = sum_j up[b][j][c] (cos - i sin)(2 pi (s_j . k_w mod G) / G);
 // thread = frequency.
+constexpr int kUfftRow = kFastTile * 8 + 4;  // staged output row, padded for float4 stores
+inline size_t ufft_smem(int ns, int nc) {
+  return sizeof(float) * std::max<size_t>((size_t)kFastTile * ns * nc, (size_t)128 * kUfftRow);
+}
 template <int NC>
 __global__ void __launch_bounds__(128) k_fast_ufft(Pass P) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -471,7 +475,7 @@ __global__ void __launch_bounds__(128) k_fast_ufft(Pass P) {
   }
   __syncthreads();
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= nf) return;
+  const bool active = w < nf;  // every thread stays for the staged store
   float re[kFastTile][NC], im[kFastTile][NC];
 #pragma unroll
   for (int bb = 0; bb < kFastTile; ++bb)
@@ -484,7 +488,7 @@ __global__ void __launch_bounds__(128) k_fast_ufft(Pass P) {
     float2 fq[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      fq[q] = j0 + q < P.ns ? F[(size_t)(j0 + q) * nf + w] : make_float2(0.f, 0.f);
+      fq[q] = active && j0 + q < P.ns ? F[(size_t)(j0 + q) * nf + w] : make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = j0 + q;
@@ -500,22 +504,46 @@ __global__ void __launch_bounds__(128) k_fast_ufft(Pass P) {
     }
   }
   // the tensor-core products read the spectra as TF32 hi + lo parts, four
-  // components per box and frequency (the fourth zero without flux)
+  // components per box and frequency (the fourth zero without flux), stored
+  // frequency-major so that at one frequency Morton-adjacent boxes share cache
+  // lines; the tile's [w][box][8] block is staged in shared memory and written
+  // out as one contiguous run per frequency
+  constexpr int kRow = kUfftRow;
+  float *S = U;                            // reused after every thread is done with U
+  const int wl = threadIdx.x;
+  const int w0 = blockIdx.x * blockDim.x;
+  const int nw = min((int)blockDim.x, nf - w0);
+  const int per_w = nbt * 2;  // float4 per frequency
+  for (int half = 0; half < 2; ++half) {
+    __syncthreads();
+    if (active) {
 #pragma unroll
-  for (int bb = 0; bb < kFastTile; ++bb) {
-    if (bb >= nbt) break;
-    float *oh = P.uhh + ((size_t)(bt + bb) * nf + w) * 8, *ol = P.uhl + ((size_t)(bt + bb) * nf + w) * 8;
+      for (int bb = 0; bb < kFastTile; ++bb)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      // scaled to the depth: the kernel spectra are those of half-width 1, the
-      // Stokeslet homogeneous of degree -1, the source of degree -2
-      const float sc = c < 3 ? sf : sq;
-      const float vr = c < NC ? sc * re[bb][c] : 0.f, vi = c < NC ? sc * im[bb][c] : 0.f;
-      const float hr = tf32_rna(vr), hi = tf32_rna(vi);
-      oh[2 * c] = hr;
-      oh[2 * c + 1] = hi;
-      ol[2 * c] = tf32_rna(vr - hr);
-      ol[2 * c + 1] = tf32_rna(vi - hi);
+        for (int q = 0; q < 2; ++q) {
+          float v[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            // component c = 2q + k/2, real part for even k; scaled to the depth:
+            // the kernel spectra are those of half-width 1, the Stokeslet
+            // homogeneous of degree -1, the source of degree -2
+            const int c = 2 * q + (k >> 1);
+            const float x = c < NC ? (c < 3 ? sf : sq) * ((k & 1) ? im[bb][c < NC ? c : 0]
+                                                                  : re[bb][c < NC ? c : 0])
+                                   : 0.f;
+            const float h = tf32_rna(x);
+            v[k] = half ? tf32_rna(x - h) : h;
+          }
+          *reinterpret_cast<float4 *>(&S[wl * kRow + bb * 8 + 4 * q]) =
+              make_float4(v[0], v[1], v[2], v[3]);
+        }
+    }
+    __syncthreads();
+    float *dst = half ? P.uhl : P.uhh;
+    for (int e = threadIdx.x; e < nw * per_w; e += blockDim.x) {
+      const int ww = e / per_w, k = e % per_w;
+      const float4 v = *reinterpret_cast<const float4 *>(&S[ww * kRow + 4 * k]);
+      *reinterpret_cast<float4 *>(dst + ((size_t)(w0 + ww) * P.t.nbox + bt) * 8 + 4 * k) = v;
     }
   }
 }
@@ -783,7 +811,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_fast_kmulp_tc(Pass P, int32_t
           a = -1;
         }
         const bool okc = a >= 0;
-        const size_t go = okc ? ((size_t)a * nf + w) * 32 : 0;
+        const size_t go = okc ? ((size_t)w * nbox + a) * 32 : 0;
         unsigned char *ah = st + (size_t)k * 2 * T::ATILE, *al = ah + T::ATILE;
 #pragma unroll
         for (int kg = 0; kg < 2; ++kg) {
@@ -1256,9 +1284,9 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
       pre("ufft");
       dim3 gu((unsigned)((nf + 127) / 128), tiles);
       if (P.nc == 4)
-        k_fast_ufft<4><<<gu, 128, sizeof(float) * kFastTile * ns * 4, st>>>(P);
+        k_fast_ufft<4><<<gu, 128, ufft_smem(ns, 4), st>>>(P);
       else
-        k_fast_ufft<3><<<gu, 128, sizeof(float) * kFastTile * ns * 3, st>>>(P);
+        k_fast_ufft<3><<<gu, 128, ufft_smem(ns, 3), st>>>(P);
       post();
       // parents of this depth's boxes: at most the boxes of the depth above
       const int32_t npar_max = depth_ptr[d] - depth_ptr[d - 1];

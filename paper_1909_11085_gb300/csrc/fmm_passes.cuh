@@ -149,7 +149,7 @@ struct Pass {
   float *ftab;         // [ns][nfreq][2] forward DFT of the surface lattice (cos, -sin)
   float *fitab;        // [nfreq][ns][2] inverse over the half spectrum, weighted, / G^3
   int32_t *err;        // device error word (a tree index out of range), at workspace + 8 bytes
-  float *uhh, *uhl;    // [nbox][nfreq][4][2] upward spectra split into TF32 hi + lo parts
+  float *uhh, *uhl;    // [nfreq][nbox][4][2] upward spectra split into TF32 hi + lo parts
                        // (fourth component zero without flux), operands of the tensor-core M2L
   float *btab;         // [nfreq][208][hi, lo][48 x 8] kernel spectra of each source slot in
                        // the tensor-core operand layout (see fmm_fast.cu)

@@ -108,7 +108,7 @@ stk_status stokes_fmm_far_workspace_size(int32_t p, int32_t flux, int32_t fft_m2
   const stk_status s = check_tree(tree);
   if (s != STK_OK) return s;
   *bytes = stk::fmm::layout(tree->nbox, p, flux ? 4 : 3, fft_m2l != 0, precision == STK_MIXED, n,
-                            tree->max_depth)
+                            tree->max_depth, tree->depth_ptr)
                .total;
   return STK_OK;
 }
@@ -139,7 +139,8 @@ stk_status stokes_fmm_far_eval(const double *pts, const double *f, const double 
     return report_error(STK_EINVAL, "uc2e/dc2e is NULL");
   const int ns = stk::fmm::surface_count(p), nc = flux ? 4 : 3;
   const bool fft = m2l_spectra != nullptr, mixed = precision == STK_MIXED;
-  const stk::fmm::Layout L = stk::fmm::layout(tree->nbox, p, nc, fft, mixed, n, tree->max_depth);
+  const stk::fmm::Layout L =
+      stk::fmm::layout(tree->nbox, p, nc, fft, mixed, n, tree->max_depth, tree->depth_ptr);
   if (!workspace || workspace_bytes < L.total) return report_error(STK_ENOMEM, "workspace too small");
   char *ws = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~(uintptr_t)255);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

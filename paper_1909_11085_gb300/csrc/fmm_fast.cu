@@ -454,27 +454,38 @@ __global__ void __launch_bounds__(256) k_fast_c2e(Pass P) {
 }
 
 // ------------------------------------------------------------- downward
-// UFFT: spectra of the upward densities of a tile of boxes,
-// uhat[w][b][c] = sum_j up[b][j][c] (cos - i sin)(2 pi (s_j . k_w mod G) / G);
-// thread = frequency.
+// UFFT: spectra of the upward densities of the children of one parent (the
+// CTA's plist position k at this depth), one octant each,
+// uhat[w][8 k + o][c] = sum_j up[child o][j][c] (cos - i sin)(2 pi (s_j . k_w mod G) / G),
+// zero for a missing child; thread = frequency.
 constexpr int kUfftRow = kFastTile * 8 + 4;  // staged output row, padded for float4 stores
+static_assert(kFastTile == 8, "one octant per box of the tile");
 inline size_t ufft_smem(int ns, int nc) {
   return sizeof(float) * std::max<size_t>((size_t)kFastTile * ns * nc, (size_t)128 * kUfftRow);
 }
 template <int NC>
-__global__ void __launch_bounds__(128) k_fast_ufft(Pass P) {
+__global__ void __launch_bounds__(128) k_fast_ufft(Pass P, int32_t first_child0,
+                                                   int32_t first_child1) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float *U = reinterpret_cast<float *>(smem);  // [kFastTile][ns][NC]
+  float *U = reinterpret_cast<float *>(smem);  // [8 octants][ns][NC]
   const int nf = freq_count(P.p);
-  const int32_t bt = P.box0 + blockIdx.y * kFastTile;
-  const int nbt = min(kFastTile, P.box1 - bt);
+  const int32_t pos0 = P.bpos[first_child0], pos1 = P.bpos[first_child1];
+  const int32_t kp = (int32_t)blockIdx.x;
+  if (pos0 + kp >= pos1) return;  // the whole CTA
+  if ((int64_t)8 * kp + 8 > P.uslots) {
+    if (threadIdx.x == 0) bad_index(P);
+    return;
+  }
+  const int32_t par = P.plist[pos0 + kp];
+  const bool okp = in_range(P, par, P.t.nbox);
   const int per = P.ns * NC;
   for (int e = threadIdx.x; e < kFastTile * per; e += blockDim.x) {
-    const int bb = e / per, r = e % per;
-    U[e] = bb < nbt ? P.up32[(size_t)(bt + bb) * per + r] : 0.f;
+    const int o = e / per, r = e % per;
+    const int32_t b = okp ? P.child8[8 * (size_t)par + o] : -1;  // a box of this depth or -1
+    U[e] = b >= 0 ? P.up32[(size_t)b * per + r] : 0.f;
   }
   __syncthreads();
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = blockIdx.y * blockDim.x + threadIdx.x;
   const bool active = w < nf;  // every thread stays for the staged store
   float re[kFastTile][NC], im[kFastTile][NC];
 #pragma unroll
@@ -504,16 +515,16 @@ __global__ void __launch_bounds__(128) k_fast_ufft(Pass P) {
     }
   }
   // the tensor-core products read the spectra as TF32 hi + lo parts, four
-  // components per box and frequency (the fourth zero without flux), stored
-  // frequency-major so that at one frequency Morton-adjacent boxes share cache
-  // lines; the tile's [w][box][8] block is staged in shared memory and written
-  // out as one contiguous run per frequency
+  // components per child and frequency (the fourth zero without flux); at one
+  // frequency a parent's 8 children are 256 contiguous bytes, the unit its
+  // neighbours gather.  The [w][8][8] block is staged in shared memory and
+  // written out as one contiguous run per frequency
   constexpr int kRow = kUfftRow;
   float *S = U;                            // reused after every thread is done with U
   const int wl = threadIdx.x;
-  const int w0 = blockIdx.x * blockDim.x;
+  const int w0 = blockIdx.y * blockDim.x;
   const int nw = min((int)blockDim.x, nf - w0);
-  const int per_w = nbt * 2;  // float4 per frequency
+  constexpr int per_w = kFastTile * 2;  // float4 per frequency
   for (int half = 0; half < 2; ++half) {
     __syncthreads();
     if (active) {
@@ -541,37 +552,42 @@ __global__ void __launch_bounds__(128) k_fast_ufft(Pass P) {
     __syncthreads();
     float *dst = half ? P.uhl : P.uhh;
     for (int e = threadIdx.x; e < nw * per_w; e += blockDim.x) {
-      const int ww = e / per_w, k = e % per_w;
-      const float4 v = *reinterpret_cast<const float4 *>(&S[ww * kRow + 4 * k]);
-      *reinterpret_cast<float4 *>(dst + ((size_t)(w0 + ww) * P.t.nbox + bt) * 8 + 4 * k) = v;
+      const int ww = e / per_w, q = e % per_w;
+      const float4 v = *reinterpret_cast<const float4 *>(&S[ww * kRow + 4 * q]);
+      *reinterpret_cast<float4 *>(dst + ((size_t)(w0 + ww) * P.uslots + 8 * (size_t)kp) * 8 +
+                                  4 * q) = v;
     }
   }
 }
 
-// The 26 x 8 source boxes of every parent in plist order (the children of its
-// neighbours by direction and octant, -1 where there is none), stored slot by
-// slot: vsrc[slot][plist position].
-__global__ void k_fast_vsrc(Pass P) {
+// The plist position of the neighbour of every parent (in plist order) in
+// each of its 26 directions, -1 where there is no neighbour or it has no
+// children: vpar[direction][plist position] (direction-major, so that
+// consecutive parents are adjacent).  The children of the neighbour at that
+// position are the sources of the direction.
+__global__ void k_fast_vpar(Pass P) {
   const int32_t total = P.bpos[P.t.nbox];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)total * 208;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)total * 26;
        e += stride) {
-    const int32_t i = (int32_t)(e / 208);
-    const int k = (int)(e % 208), dd = k / 8, s = k % 8;
+    const int32_t i = (int32_t)(e / 26);
+    const int dd = (int)(e % 26);
     const int dir = dd < 13 ? dd : dd + 1;  // direction 13 is the parent itself
     const int32_t par = P.plist[i];
-    int32_t a = -1;
+    int32_t q = -1;
     if (in_range(P, par, P.t.nbox)) {
       const int32_t Q = P.t.colleague[27 * (size_t)par + dir];
       if (Q >= 0 && in_range(P, Q, P.t.nbox)) {
-        a = P.child8[8 * (size_t)Q + s];
-        if (a >= P.t.nbox) {
-          bad_index(P);
-          a = -1;
+        const int32_t c0 = P.t.child_ptr[Q], c1 = P.t.child_ptr[Q + 1];
+        if (c1 > c0) {
+          if (c0 < 0 || c0 >= P.t.nbox)
+            bad_index(P);
+          else
+            q = P.bpos[c0];
         }
       }
     }
-    P.vsrc[(size_t)k * P.t.nbox + i] = a;  // slot-major: consecutive parents adjacent
+    P.vpar[(size_t)dd * P.t.nbox + i] = q;
   }
 }
 
@@ -579,7 +595,7 @@ __device__ __forceinline__ void cp_async_zfill(void *dst, const void *src, bool 
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
   const int sz = valid ? bytes : 0;
   if (bytes == 16)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(sz)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(sz)
                  : "memory");
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(sz)
@@ -595,26 +611,26 @@ __device__ __forceinline__ void cp_async_wait() {
 // The spectral products on the tensor cores (tcgen05, kind::tf32).  For one
 // frequency w the products of a parent P are one dense complex contraction:
 // the 24 check-spectrum values of its 8 children (3 components each) are the
-// 864 source-spectrum values of the 208 children of its 26 neighbours
-// (4 components each) times a 864 x 24 matrix of kernel spectra, the same for
-// every parent (zero where a pair touches).  Written with real numbers
+// 832 source-spectrum values of the 208 children of its 26 neighbours
+// (4 components each) times an 832 x 24 matrix of kernel spectra, the same
+// for every parent (zero where a pair touches).  Written with real numbers
 // (re, im interleaved along both dimensions: [re im] x [[Kr Ki] [-Ki Kr]]) it
-// is D[128 parents][48] = A[128][1728] B[48][1728]^T per CTA: A gathered from
-// the source spectra, B built from the staged kernel spectra, both in FP32
-// split into TF32 hi + lo parts (hi = tf32(x), lo = tf32(x - hi)) so that
-// hi.hi + hi.lo + lo.hi carries FP32 accuracy (the lo.lo term is below it).
-// A K-chunk of 4 source slots is staged in shared memory in the MMA's K-major
-// layout without swizzle (8-row x 16-byte core matrices); one thread issues
-// the MMAs, which accumulate in tensor memory (48 FP32 columns); chunks are
-// double-buffered, a buffer being reused once the commit of its previous MMAs
-// has arrived on its mbarrier (a bounded wait).
+// is D[128 parents][48] = A[128][1664] B[48][1664]^T per tile of parents: A
+// gathered from the source spectra, B built from the staged kernel spectra,
+// both in FP32 split into TF32 hi + lo parts (hi = tf32(x), lo = tf32(x - hi))
+// so that hi.hi + hi.lo + lo.hi carries FP32 accuracy (the lo.lo term is below
+// it).  The K dimension runs in 52 chunks of 32 (one neighbour direction,
+// four of its children's octants), 128 contiguous bytes per parent row in the
+// parent-major spectra; a chunk is staged in shared memory in the MMA's
+// K-major layout with the 128-byte swizzle (a row's 128 bytes in one line,
+// its 16-byte pieces permuted by the row index within each 8-row group).
 constexpr int kTcThreads = 256;
 constexpr int kTcRows = 128;
 constexpr int kTcCols = 48;        // 8 targets x 3 components x (re, im)
-constexpr uint32_t kTcTmemCols = 128;  // kTcTiles accumulators of 48 columns, 64 apart
+constexpr int kTcK = 32;           // K per chunk (128 bytes of TF32)
+constexpr int kTcChunks = 52;      // 26 neighbour directions x 2 octant halves
 constexpr long long kTcSpinLimit = 4000000000LL;  // SM cycles, about 2 s
 constexpr int kErrTimeout = 4;
-constexpr int kTcSlots = 208;  // 26 neighbour directions x 8 octants
 
 __device__ __forceinline__ uint32_t saddr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -638,11 +654,13 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
     if (clock64() - t0 > kTcSpinLimit) return false;
   return true;
 }
-// Shared-memory matrix descriptor: K-major, no swizzle; lbo = byte stride of
-// core matrices along K, sbo = along M (or N); version 1.
-__device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+// Shared-memory matrix descriptor, K-major with the 128-byte swizzle: 8-row
+// groups 1024 bytes apart (stride byte offset), the leading byte offset unused
+// within one swizzle row, version 1, layout type 2 (128-byte swizzle).  The
+// K-step inside a swizzle row advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t tc_sdesc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 __device__ __forceinline__ void tc_mma(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc,
                                        uint32_t accum) {
@@ -652,57 +670,62 @@ __device__ __forceinline__ void tc_mma(uint32_t dt, uint64_t a, uint64_t b, uint
       "l"(a), "l"(b), "r"(idesc), "r"(accum)
       : "memory");
 }
-// Byte offset of element (row, k) in a K-major no-swizzle tile whose rows
-// hold kg 16-byte core-matrix columns.
-__device__ __forceinline__ uint32_t tc_off(int row, int k, int kg) {
-  return (uint32_t)((((row >> 3) * kg + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+// Byte offset of element (row, k), k < 32, in a K-major tile with the 128-byte
+// swizzle (tile base 1024-byte aligned): row r's 128 bytes at 128 r within its
+// 8-row group, the 16-byte piece j stored at position j ^ (r mod 8).
+__host__ __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
+  return (uint32_t)(((row >> 3) << 10) + ((row & 7) << 7) + ((((k >> 2) ^ (row & 7)) & 7) << 4) +
+                    ((k & 3) << 2));
 }
 
-// Per CTA: one frequency and kTcTiles tiles of 128 parents; the K dimension
-// runs over the 208 source slots, 8 reals each (4 components x re, im), one
-// slot per chunk (K = 8, one MMA per tile and hi/lo product).  Warp roles:
-//   warps 0-3 (producers): for each chunk, copy the TF32 hi/lo source spectra
-//     of their rows by cp.async straight into the MMA layout (zero-filled for
-//     missing boxes) and the chunk's B from the table k_fast_btab built for
-//     the call; once a chunk's copies have landed, fence them for the tensor
-//     core and arrive on the chunk's "full" barrier;
-//   thread 128 (MMA): wait "full", issue the 3 MMAs per tile, commit to the
-//     chunk's "empty" barrier (producers refill a buffer only after it);
+// Per CTA: one frequency and kTcTiles tiles of 128 parents.  Warp roles:
+//   warps 0-3 (producers): for each chunk, copy the TF32 hi/lo spectra of the
+//     4 octants of their rows' neighbour by cp.async into the swizzled MMA
+//     layout (8 lanes per row: one 128-byte line per row; zero-filled where the
+//     neighbour has no children) and the chunk's B from the table k_fast_btab
+//     built for the call; once a chunk's copies have landed, fence them for the
+//     tensor core and arrive on the chunk's "full" barrier;
+//   thread 128 (MMA): wait "full", issue 4 K-steps x 3 MMAs per tile, commit
+//     to the chunk's "empty" barrier (producers refill a buffer only after it);
 //   warps 4-7 (epilogue): after the final commit, read the accumulators from
 //     tensor memory (one lane quarter each) and write the check spectra.
 // A ring of kTcStages buffers lets the producers run ahead of the MMAs.
 // Every wait is bounded; on expiry the role records STK_ETIMEOUT in the error
 // word and stops, and the CTA still drains its copies and MMAs before it
 // frees tensor memory.
-constexpr int kTcTiles = 2;
+constexpr int kTcTiles = 1;
 constexpr int kTcStages = 5;
 constexpr int kTcAhead = 3;  // chunks of copies a producer keeps in flight (< kTcStages)
+constexpr int kTcMinBlocks = 1;
+constexpr uint32_t kTcTmemCols = kTcTiles == 1 ? 64 : 128;  // accumulators 64 columns apart
 constexpr int kTcProducers = 128;
 struct TcShape {
-  static constexpr int KS = 8;                          // K per chunk
-  static constexpr int ATILE = kTcRows * KS * 4;        // bytes of one A tile (hi or lo)
+  static constexpr int ATILE = kTcRows * kTcK * 4;      // bytes of one A tile (hi or lo)
   static constexpr int ASTAGE = kTcTiles * 2 * ATILE;   // hi, lo of every tile
-  static constexpr int BTILE = kTcCols * KS * 4;
-  static constexpr int STAGE = ASTAGE + 2 * BTILE;
+  static constexpr int BTILE = kTcCols * kTcK * 4;      // 6 swizzle groups of 8 rows
+  static constexpr int STAGE = ASTAGE + 2 * BTILE;      // a multiple of 1024
   static constexpr int NBAR = 2 * kTcStages + 1;        // full, empty, done
-  static constexpr size_t SMEM = (size_t)kTcStages * STAGE + 8 * NBAR + 16;
+  static constexpr size_t SMEM = 1024 + (size_t)kTcStages * STAGE + 8 * NBAR + 16;
 };
+static_assert(TcShape::STAGE % 1024 == 0, "swizzle groups stay 1024-byte aligned");
+static_assert(kTcChunks % 2 == 0, "two octant halves per direction");
 
-// The B operand of every (frequency, source slot): for slot g (neighbour
-// direction and octant) and target octant t, the 3 x 4 complex kernel
-// spectrum of their offset (zero where they touch) as a real 6 x 8 block
-// [[Kr Ki] [-Ki Kr]], split into TF32 hi + lo, laid out as the MMA reads it
-// (K-major core matrices): btab[w][g][hi, lo][tc_off(n, k)].
+// The B operand of every (frequency, chunk): for direction dd, octant half h
+// (source octants 4h..4h+3) and target octant t, the 3 x 4 complex kernel
+// spectra of their offsets (zero where they touch) as real 6 x 8 blocks
+// [[Kr Ki] [-Ki Kr]], split into TF32 hi + lo, in the swizzled K-major layout
+// the MMA reads: btab[w][2 dd + h][hi, lo][sw128_off(n, k)].
 __global__ void k_fast_btab(Pass P, int64_t n) {
   const int m = 3 * P.nc * 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-    const int64_t wg = e / (kTcCols * 8);
-    const int r = (int)(e % (kTcCols * 8));
-    const int w = (int)(wg / kTcSlots), g = (int)(wg % kTcSlots);
-    const int nn = r >> 3, k = r & 7;
-    const int t = nn / 6, q = (nn >> 1) % 3, rn = nn & 1, c = k >> 1, rk = k & 1;
-    const int dd = g >> 3, sl = g & 7, dir = dd < 13 ? dd : dd + 1;
+    const int64_t wc = e / (kTcCols * kTcK);
+    const int r = (int)(e % (kTcCols * kTcK));
+    const int w = (int)(wc / kTcChunks), ch = (int)(wc % kTcChunks);
+    const int nn = r / kTcK, k = r % kTcK;
+    const int t = nn / 6, q = (nn >> 1) % 3, rn = nn & 1;
+    const int sl = 4 * (ch & 1) + (k >> 3), c = (k >> 1) & 3, rk = k & 1;
+    const int dd = ch >> 1, dir = dd < 13 ? dd : dd + 1;
     const int ox = 2 * (dir / 9 - 1) + (sl >> 2) - (t >> 2);
     const int oy = 2 * ((dir / 3) % 3 - 1) + ((sl >> 1) & 1) - ((t >> 1) & 1);
     const int oz = 2 * (dir % 3 - 1) + (sl & 1) - (t & 1);
@@ -713,10 +736,10 @@ __global__ void k_fast_btab(Pass P, int64_t n) {
       val = (rk == rn) ? K[0] : (rk == 0 ? K[1] : -K[1]);
     }
     const float hi = tf32_rna(val), lo = tf32_rna(val - hi);
-    float *o = P.btab + (size_t)wg * 2 * kTcCols * 8;
-    const uint32_t off = tc_off(nn, k, 2) >> 2;
+    float *o = P.btab + (size_t)wc * 2 * kTcCols * kTcK;
+    const uint32_t off = sw128_off(nn, k) >> 2;
     o[off] = hi;
-    o[kTcCols * 8 + off] = lo;
+    o[kTcCols * kTcK + off] = lo;
   }
 }
 
@@ -729,11 +752,12 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
                : "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2) k_fast_kmulp_tc(Pass P, int32_t first_child0,
-                                                                int32_t first_child1) {
+__global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_fast_kmulp_tc(
+    Pass P, int32_t first_child0, int32_t first_child1) {
   using T = TcShape;
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned char *stages = smem;                                          // [kTcStages][STAGE]
+  // the swizzle is a function of the address: stages start 1024-byte aligned
+  unsigned char *stages = smem + ((1024u - (saddr(smem) & 1023u)) & 1023u);  // [kTcStages][STAGE]
   uint64_t *bars = reinterpret_cast<uint64_t *>(stages + kTcStages * T::STAGE);
   uint64_t *full = bars, *empty = bars + kTcStages, *done = bars + 2 * kTcStages;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + T::NBAR);
@@ -769,61 +793,63 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_fast_kmulp_tc(Pass P, int32_t
 
   if (warp < 4) {
     // ---------------------------------------------------------- producers
-    // row k * 128 + tid of the CTA (tile k) is parent row0 + k * 128 + tid
+    // warp pw copies rows 32 pw .. 32 pw + 31 of every tile; lane holds the
+    // neighbour's local plist position for row 32 pw + lane, and in a copy
+    // round 8 lanes take one row (lane / 8) and its 16-byte pieces (lane % 8)
     const unsigned char *UHH = reinterpret_cast<const unsigned char *>(P.uhh);
     const unsigned char *UHL = reinterpret_cast<const unsigned char *>(P.uhl);
+    const int32_t npar = min(pos1 - pos0, P.uslots / 8);
+    const size_t wrow = (size_t)w * P.uslots;  // first slot of this frequency
     int32_t rowi[kTcTiles];
 #pragma unroll
-    for (int k = 0; k < kTcTiles; ++k) rowi[k] = row0 + k * kTcRows + tid;
-    // source-box indices of the next kIdxAhead chunks in registers (the loads
-    // of chunk g + kIdxAhead are issued while chunk g is handled)
-    constexpr int kIdxAhead = 4;
-    static_assert(kTcSlots % kIdxAhead == 0, "chunk groups");
-    int32_t ring[kIdxAhead][kTcTiles];
+    for (int k = 0; k < kTcTiles; ++k) rowi[k] = row0 + k * kTcRows + 32 * warp + lane;
+    // neighbour positions of the next direction are loaded while the current
+    // one is copied
+    auto load_q = [&](int dd, int32_t *q) {
 #pragma unroll
-    for (int q = 0; q < kIdxAhead; ++q)
-#pragma unroll
-      for (int k = 0; k < kTcTiles; ++k)
-        ring[q][k] = rowi[k] < pos1 ? P.vsrc[(size_t)q * nbox + rowi[k]] : -1;
-    for (int g0 = 0; g0 < kTcSlots && ok; g0 += kIdxAhead)
-#pragma unroll
-    for (int q = 0; q < kIdxAhead; ++q) {
-      const int g = g0 + q;
-      const int s = g % kTcStages;
+      for (int k = 0; k < kTcTiles; ++k) {
+        int32_t v = rowi[k] < pos1 ? P.vpar[(size_t)dd * nbox + rowi[k]] : -1;
+        if (v >= 0) {
+          v -= pos0;
+          if (v < 0 || v >= npar) {
+            bad_index(P);
+            v = -1;
+          }
+        }
+        q[k] = v;
+      }
+    };
+    int32_t qcur[kTcTiles], qnext[kTcTiles];
+    load_q(0, qcur);
+    const int rsub = lane >> 3, piece = lane & 7;
+    for (int g = 0; g < kTcChunks && ok; ++g) {
+      const int s = g % kTcStages, dd = g >> 1, half = g & 1;
+      if (half == 0 && dd + 1 < kTcChunks / 2) load_q(dd + 1, qnext);
       if (g >= kTcStages && !tc_wait(&empty[s], (uint32_t)(((g / kTcStages) - 1) & 1))) {
         ok = false;
         if (P.err) atomicCAS(P.err, 0, kErrTimeout);
         break;
       }
-      int32_t cur[kTcTiles];
-#pragma unroll
-      for (int k = 0; k < kTcTiles; ++k) cur[k] = ring[q][k];
-      if (g + kIdxAhead < kTcSlots)
-#pragma unroll
-        for (int k = 0; k < kTcTiles; ++k)
-          ring[q][k] = rowi[k] < pos1 ? P.vsrc[(size_t)(g + kIdxAhead) * nbox + rowi[k]] : -1;
       unsigned char *st = stages + (size_t)s * T::STAGE;
 #pragma unroll
       for (int k = 0; k < kTcTiles; ++k) {
-        int32_t a = cur[k];
-        if (a >= nbox) {
-          bad_index(P);
-          a = -1;
-        }
-        const bool okc = a >= 0;
-        const size_t go = okc ? ((size_t)w * nbox + a) * 32 : 0;
         unsigned char *ah = st + (size_t)k * 2 * T::ATILE, *al = ah + T::ATILE;
 #pragma unroll
-        for (int kg = 0; kg < 2; ++kg) {
-          const uint32_t o = tc_off(tid, 4 * kg, 2);
-          cp_async_zfill(ah + o, UHH + go + 16 * kg, okc, 16);
-          cp_async_zfill(al + o, UHL + go + 16 * kg, okc, 16);
+        for (int i = 0; i < 8; ++i) {
+          const int rw = 4 * i + rsub;            // row within the warp's 32
+          const int32_t lq = __shfl_sync(kFull, qcur[k], rw);
+          const int r = 32 * warp + rw;            // row within the tile
+          const bool okc = lq >= 0;
+          const size_t go = okc ? ((wrow + 8 * (size_t)lq + 4 * half) * 32 + 16 * piece) : 0;
+          const uint32_t o = sw128_off(r, 4 * piece);
+          cp_async_zfill(ah + o, UHH + go, okc, 16);
+          cp_async_zfill(al + o, UHL + go, okc, 16);
         }
       }
-      {  // B: the slot's kernel spectra, hi then lo, as laid out in the table
+      {  // B: the chunk's kernel spectra, hi then lo, as laid out in the table
         unsigned char *bdst = st + T::ASTAGE;
         const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(
-            P.btab + ((size_t)w * kTcSlots + g) * 2 * kTcCols * 8);
+            P.btab + ((size_t)w * kTcChunks + g) * 2 * kTcCols * kTcK);
         for (int e = tid; e < 2 * T::BTILE / 16; e += kTcProducers)
           cp_async_zfill(bdst + 16 * e, bsrc + 16 * e, true, 16);
       }
@@ -833,18 +859,21 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_fast_kmulp_tc(Pass P, int32_t
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_arrive(&full[(g - kTcAhead) % kTcStages]);
       }
+      if (half == 1)
+#pragma unroll
+        for (int k = 0; k < kTcTiles; ++k) qcur[k] = qnext[k];
     }
     cp_async_wait<0>();
     if (ok) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      for (int c = kTcSlots - kTcAhead; c < kTcSlots; ++c) tc_arrive(&full[c % kTcStages]);
+      for (int c = kTcChunks - kTcAhead; c < kTcChunks; ++c) tc_arrive(&full[c % kTcStages]);
     }
   } else if (tid == kTcProducers) {
     // ---------------------------------------------------------------- MMA
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
                            ((uint32_t)(kTcCols >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
     int last = -1;
-    for (int g = 0; g < kTcSlots; ++g) {
+    for (int g = 0; g < kTcChunks; ++g) {
       const int s = g % kTcStages;
       if (!tc_wait(&full[s], (uint32_t)((g / kTcStages) & 1))) {
         ok = false;
@@ -858,9 +887,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_fast_kmulp_tc(Pass P, int32_t
       for (int tt = 0; tt < kTcTiles; ++tt) {
         const uint32_t ah = saddr(st + (size_t)tt * 2 * T::ATILE), al = ah + T::ATILE;
         const uint32_t d = tmem + (uint32_t)(tt * 64);
-        tc_mma(d, tc_sdesc(ah, 128, 256), tc_sdesc(bh, 128, 256), idesc, g > 0 ? 1u : 0u);
-        tc_mma(d, tc_sdesc(ah, 128, 256), tc_sdesc(bl, 128, 256), idesc, 1u);
-        tc_mma(d, tc_sdesc(al, 128, 256), tc_sdesc(bh, 128, 256), idesc, 1u);
+#pragma unroll
+        for (int ks = 0; ks < kTcK / 8; ++ks) {
+          const uint32_t kb = 32u * ks;  // 8 TF32 per K-step
+          tc_mma(d, tc_sdesc_sw128(ah + kb), tc_sdesc_sw128(bh + kb), idesc,
+                 (g > 0 || ks > 0) ? 1u : 0u);
+          tc_mma(d, tc_sdesc_sw128(ah + kb), tc_sdesc_sw128(bl + kb), idesc, 1u);
+          tc_mma(d, tc_sdesc_sw128(al + kb), tc_sdesc_sw128(bh + kb), idesc, 1u);
+        }
       }
       tc_commit(&empty[s]);
       last = g;
@@ -1232,8 +1266,8 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
   k_fast_plist<<<gs(P.t.nbox), 256, 0, st>>>(P);
   post();
   if (fft) {
-    pre("vsrc");
-    k_fast_vsrc<<<gs((int64_t)P.t.nbox * 208), 256, 0, st>>>(P);
+    pre("vpar");
+    k_fast_vpar<<<gs((int64_t)P.t.nbox * 26), 256, 0, st>>>(P);
     post();
   }
   pre("pack");
@@ -1250,7 +1284,7 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
     pre("spec");
     k_fast_spec<<<gs(n), 256, 0, st>>>(P, n);
     post();
-    const int64_t nb = (int64_t)nf * kTcSlots * kTcCols * 8;
+    const int64_t nb = (int64_t)nf * kTcChunks * kTcCols * kTcK;
     pre("btab");
     k_fast_btab<<<gs(nb), 256, 0, st>>>(P, nb);
     post();
@@ -1279,17 +1313,17 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
     P.box1 = depth_ptr[d + 1];
     const int32_t nb = P.box1 - P.box0;
     if (nb <= 0) continue;
-    const unsigned tiles = (unsigned)((nb + kFastTile - 1) / kFastTile);
     if (fft) {
+      // parents of this depth's boxes: at most the boxes of the depth above,
+      // and at most the boxes of this depth
+      const int32_t npar_max = std::min(depth_ptr[d] - depth_ptr[d - 1], nb);
       pre("ufft");
-      dim3 gu((unsigned)((nf + 127) / 128), tiles);
+      const dim3 gu((unsigned)npar_max, (unsigned)((nf + 127) / 128));
       if (P.nc == 4)
-        k_fast_ufft<4><<<gu, 128, ufft_smem(ns, 4), st>>>(P);
+        k_fast_ufft<4><<<gu, 128, ufft_smem(ns, 4), st>>>(P, depth_ptr[d], depth_ptr[d + 1]);
       else
-        k_fast_ufft<3><<<gu, 128, ufft_smem(ns, 3), st>>>(P);
+        k_fast_ufft<3><<<gu, 128, ufft_smem(ns, 3), st>>>(P, depth_ptr[d], depth_ptr[d + 1]);
       post();
-      // parents of this depth's boxes: at most the boxes of the depth above
-      const int32_t npar_max = depth_ptr[d] - depth_ptr[d - 1];
       pre("kmulp");
       {
         const int rows = kTcTiles * kTcRows;

@@ -149,12 +149,16 @@ struct Pass {
   float *ftab;         // [ns][nfreq][2] forward DFT of the surface lattice (cos, -sin)
   float *fitab;        // [nfreq][ns][2] inverse over the half spectrum, weighted, / G^3
   int32_t *err;        // device error word (a tree index out of range), at workspace + 8 bytes
-  float *uhh, *uhl;    // [nfreq][nbox][4][2] upward spectra split into TF32 hi + lo parts
-                       // (fourth component zero without flux), operands of the tensor-core M2L
-  float *btab;         // [nfreq][208][hi, lo][48 x 8] kernel spectra of each source slot in
-                       // the tensor-core operand layout (see fmm_fast.cu)
-  int32_t *vsrc;       // [nbox][26 * 8] source box of each neighbour direction and octant of
-                       // the parent at each plist position (-1 where there is none)
+  float *uhh, *uhl;    // [nfreq][uslots][4][2] upward spectra of one depth split into TF32
+                       // hi + lo parts, parent-major: slot 8 k + o holds the child in octant o
+                       // of the depth's k-th parent (zero where there is none; fourth
+                       // component zero without flux), operands of the tensor-core M2L
+  int32_t uslots;      // slots of uhh / uhl per frequency (8 x the most parents of a depth)
+  float *btab;         // [nfreq][52][hi, lo][48 x 32] kernel spectra of each neighbour
+                       // direction and octant half in the tensor-core operand layout (see
+                       // fmm_fast.cu)
+  int32_t *vpar;       // [26][nbox] plist position of the neighbour in each direction of the
+                       // parent at each plist position (-1 where it has no children)
   // leaf order of the blocked L2T (most work first): cost keys, leaf numbers,
   // bucket counts and offsets, ranks and the order
   uint64_t *lkeys;
@@ -951,7 +955,8 @@ struct Layout {
   size_t surf, chk, up, dn, sidx, tw, uhat, chat, m2l;
   size_t ploc, qf, pf, nf, surf32, up32, dn32, tw32, spec32, uhat32, chat32, m2l32;
   size_t chk32, ops_hi, ops_lo;
-  size_t child8, bflag, bpos, plist, ftab, fitab, vsrc, uhh, uhl, btab;
+  size_t child8, bflag, bpos, plist, ftab, fitab, vpar, uhh, uhl, btab;
+  int64_t uslots;
   size_t lkeys, lvals, lcnt, loff, lrank, lorder;
   size_t total;
 };
@@ -964,8 +969,20 @@ inline int64_t op_entries(int p, int nc, int max_depth, bool upward) {
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Slots of the parent-major source spectra of one depth: 8 per parent with
+// children there; depth d has at most min(boxes at d - 1, boxes at d) of them.
+inline int64_t spectrum_slots(const int32_t *depth_ptr, int max_depth) {
+  int64_t m = 1;
+  for (int d = 1; d <= max_depth; ++d) {
+    const int64_t a = depth_ptr[d] - depth_ptr[d - 1], b = depth_ptr[d + 1] - depth_ptr[d];
+    const int64_t c = a < b ? a : b;
+    m = c > m ? c : m;
+  }
+  return 8 * m;
+}
+
 inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t n,
-                     int max_depth) {
+                     int max_depth, const int32_t *depth_ptr) {
   const int ns = surface_count(p);
   const size_t nf = (size_t)freq_count(p), B = (size_t)nbox, N = (size_t)n;
   Layout L;
@@ -982,8 +999,9 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t 
   L.chk = L.up = L.dn = L.tw = L.uhat = L.chat = L.m2l = none;
   L.ploc = L.qf = L.pf = L.nf = L.surf32 = L.up32 = L.dn32 = L.tw32 = L.spec32 = L.uhat32 =
       L.chat32 = L.m2l32 = L.chk32 = L.ops_hi = L.ops_lo = none;
-  L.child8 = L.bflag = L.bpos = L.plist = L.ftab = L.fitab = L.vsrc = L.uhh = L.uhl = L.btab =
+  L.child8 = L.bflag = L.bpos = L.plist = L.ftab = L.fitab = L.vpar = L.uhh = L.uhl = L.btab =
       none;
+  L.uslots = spectrum_slots(depth_ptr, max_depth);
   L.lkeys = L.lvals = L.lcnt = L.loff = L.lrank = L.lorder = none;
   if (!mixed) {
     L.chk = take(sizeof(double) * 3 * ns * B);
@@ -1016,10 +1034,10 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t 
       L.m2l32 = take(sizeof(float) * 3 * ns * B);
       L.ftab = take(sizeof(float) * 2 * ns * nf);
       L.fitab = take(sizeof(float) * 2 * ns * nf);
-      L.vsrc = take(sizeof(int32_t) * 26 * 8 * B);
-      L.uhh = take(sizeof(float) * 2 * nf * 4 * B);
-      L.uhl = take(sizeof(float) * 2 * nf * 4 * B);
-      L.btab = take(sizeof(float) * nf * 208 * 2 * 48 * 8);
+      L.vpar = take(sizeof(int32_t) * 26 * B);
+      L.uhh = take(sizeof(float) * 8 * nf * (size_t)L.uslots);
+      L.uhl = take(sizeof(float) * 8 * nf * (size_t)L.uslots);
+      L.btab = take(sizeof(float) * nf * 52 * 2 * 48 * 32);
     }
     L.child8 = take(sizeof(int32_t) * 8 * B);
     L.bflag = take(sizeof(int32_t) * B);
@@ -1074,7 +1092,8 @@ inline void bind(Pass &P, char *ws, const Layout &L, bool fft, bool mixed) {
   P.plist = mixed ? i32(L.plist) : nullptr;
   P.ftab = (fft && mixed) ? f(L.ftab) : nullptr;
   P.fitab = (fft && mixed) ? f(L.fitab) : nullptr;
-  P.vsrc = (fft && mixed) ? i32(L.vsrc) : nullptr;
+  P.vpar = (fft && mixed) ? i32(L.vpar) : nullptr;
+  P.uslots = (int32_t)L.uslots;
   P.uhh = (fft && mixed) ? f(L.uhh) : nullptr;
   P.uhl = (fft && mixed) ? f(L.uhl) : nullptr;
   P.btab = (fft && mixed) ? f(L.btab) : nullptr;

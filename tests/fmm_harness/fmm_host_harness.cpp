@@ -99,7 +99,7 @@ long long fmm_host_far_eval(const double *pts, const double *f, const double *ph
   P.n_dc2e = stk::fmm::op_entries(p, nc, max_depth, false);
   // the library's workspace layout, in one buffer aligned as the library aligns it
   const stk::fmm::Layout L =
-      stk::fmm::layout(nbox, p, nc, spec != nullptr, mixed != 0, n, max_depth);
+      stk::fmm::layout(nbox, p, nc, spec != nullptr, mixed != 0, n, max_depth, depth_ptr);
   std::vector<char> buf(L.total + 256);
   char *ws = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(buf.data()) + 255) &
                                       ~(uintptr_t)255);

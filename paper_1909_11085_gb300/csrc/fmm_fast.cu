@@ -685,7 +685,7 @@ __host__ __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
 //     neighbour has no children) and the chunk's B from the table k_fast_btab
 //     built for the call; once a chunk's copies have landed, fence them for the
 //     tensor core and arrive on the chunk's "full" barrier;
-//   thread 128 (MMA): wait "full", issue 4 K-steps x 3 MMAs per tile, commit
+//   thread 128 (MMA): wait "full", issue 4 K-steps x 2 MMAs per tile, commit
 //     to the chunk's "empty" barrier (producers refill a buffer only after it);
 //   warps 4-7 (epilogue): after the final commit, read the accumulators from
 //     tensor memory (one lane quarter each) and write the check spectra.
@@ -694,10 +694,11 @@ __host__ __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
 // word and stops, and the CTA still drains its copies and MMAs before it
 // frees tensor memory.
 constexpr int kTcTiles = 1;
-constexpr int kTcStages = 5;
-constexpr int kTcAhead = 3;  // chunks of copies a producer keeps in flight (< kTcStages)
-constexpr int kTcMinBlocks = 1;
-constexpr uint32_t kTcTmemCols = kTcTiles == 1 ? 64 : 128;  // accumulators 64 columns apart
+constexpr int kTcStages = 2;
+constexpr int kTcAhead = 1;  // chunks of copies a producer keeps in flight (< kTcStages)
+constexpr int kTcMinBlocks = 2;  // 2 x 90 KB: one CTA's set-up and epilogue overlap the other's loop
+// per tile 96 accumulator columns: [0, 48) hi.hi + lo.hi, [48, 96) hi.lo (summed at the end)
+constexpr uint32_t kTcTmemCols = kTcTiles == 1 ? 128 : 256;  // accumulators 128 columns apart
 constexpr int kTcProducers = 128;
 struct TcShape {
   static constexpr int ATILE = kTcRows * kTcK * 4;      // bytes of one A tile (hi or lo)
@@ -870,8 +871,13 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_fast_kmulp_tc(
     }
   } else if (tid == kTcProducers) {
     // ---------------------------------------------------------------- MMA
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
-                           ((uint32_t)(kTcCols >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+    // D F32, A and B TF32, K-major; N = 96 (B hi then B lo, adjacent in the
+    // stage) or 48 (B hi), M = 128
+    const uint32_t idesc96 = (1u << 4) | (2u << 7) | (2u << 10) |
+                             ((uint32_t)(2 * kTcCols >> 3) << 17) |
+                             ((uint32_t)(kTcRows >> 4) << 24);
+    const uint32_t idesc48 = (1u << 4) | (2u << 7) | (2u << 10) |
+                             ((uint32_t)(kTcCols >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
     int last = -1;
     for (int g = 0; g < kTcChunks; ++g) {
       const int s = g % kTcStages;
@@ -882,18 +888,18 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_fast_kmulp_tc(
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const unsigned char *st = stages + (size_t)s * T::STAGE;
-      const uint32_t bh = saddr(st + T::ASTAGE), bl = bh + T::BTILE;
+      const uint32_t bh = saddr(st + T::ASTAGE);
 #pragma unroll
       for (int tt = 0; tt < kTcTiles; ++tt) {
         const uint32_t ah = saddr(st + (size_t)tt * 2 * T::ATILE), al = ah + T::ATILE;
-        const uint32_t d = tmem + (uint32_t)(tt * 64);
+        const uint32_t d = tmem + (uint32_t)(tt * 128);
 #pragma unroll
         for (int ks = 0; ks < kTcK / 8; ++ks) {
           const uint32_t kb = 32u * ks;  // 8 TF32 per K-step
-          tc_mma(d, tc_sdesc_sw128(ah + kb), tc_sdesc_sw128(bh + kb), idesc,
+          // [hi.hi | hi.lo] in one product of N = 96, then lo.hi into the first half
+          tc_mma(d, tc_sdesc_sw128(ah + kb), tc_sdesc_sw128(bh + kb), idesc96,
                  (g > 0 || ks > 0) ? 1u : 0u);
-          tc_mma(d, tc_sdesc_sw128(ah + kb), tc_sdesc_sw128(bl + kb), idesc, 1u);
-          tc_mma(d, tc_sdesc_sw128(al + kb), tc_sdesc_sw128(bh + kb), idesc, 1u);
+          tc_mma(d, tc_sdesc_sw128(al + kb), tc_sdesc_sw128(bh + kb), idesc48, 1u);
         }
       }
       tc_commit(&empty[s]);
@@ -919,10 +925,10 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_fast_kmulp_tc(
         const int32_t i = row0 + tt * kTcRows + quarter * 32 + lane;
         float d[kTcCols];
 #pragma unroll
-        for (int part = 0; part < kTcCols / 16; ++part) {
+        for (int part = 0; part < 2 * kTcCols / 16; ++part) {
           uint32_t v[16];
           const uint32_t taddr =
-              tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tt * 64 + part * 16);
+              tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tt * 128 + part * 16);
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
               "%10, %11, %12, %13, %14, %15}, [%16];"
@@ -932,7 +938,13 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_fast_kmulp_tc(
               : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int e = 0; e < 16; ++e) d[part * 16 + e] = __uint_as_float(v[e]);
+          for (int e = 0; e < 16; ++e) {
+            const int c = part * 16 + e;  // hi.hi + lo.hi, then hi.lo
+            if (c < kTcCols)
+              d[c] = __uint_as_float(v[e]);
+            else
+              d[c - kTcCols] += __uint_as_float(v[e]);
+          }
         }
         if (i < pos1) {
           const int32_t par = P.plist[i];

@@ -28,6 +28,7 @@
 
 #include "fmm_fast.cuh"
 #include "prep.cuh"
+#include "tc_gemm.cuh"
 
 namespace stk {
 namespace fmm {
@@ -232,7 +233,14 @@ __device__ __forceinline__ EqSrc eq_none(const Pass &P) {
 }
 
 // ------------------------------------------------------------------ set-up
-// child8, bflag and the lattice DFT tables; e runs over max(nbox, ns nfreq).
+// K chunks of the inverse-DFT product: 2 nfreq reals (re, im per frequency).
+__host__ __device__ inline int ifft_chunks(int p) {
+  return (2 * freq_count(p) + tc::kChunk - 1) / tc::kChunk;
+}
+__host__ __device__ inline int ifft_tiles(int ns) { return (ns + tc::kCols - 1) / tc::kCols; }
+
+// child8, bflag and the lattice DFT tables (the inverse one as the B table of
+// the tensor-core product, zeroed before); e runs over max(nbox, ns nfreq).
 __global__ void k_fast_tables(Pass P, int64_t n) {
   const int nf = freq_count(P.p), G = 2 * P.p, nz = P.p + 1;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -252,7 +260,8 @@ __global__ void k_fast_tables(Pass P, int64_t n) {
       P.bflag[b] = flag;
     }
     if (P.ftab && e < (int64_t)P.ns * nf) {
-      // forward: ftab[j][w]; inverse: fitab[w][k] (k = j), the same angle
+      // forward: ftab[j][w]; inverse: the B table of the inverse-DFT product
+      // (the same angle), B[j][2 w + ri] = the weighted (cos, -sin) / G^3
       const int j = (int)(e / nf), w = (int)(e % nf);
       const int kx = w / (G * nz), ky = (w / nz) % G, kz = w % nz;
       const int t = (P.sidx[3 * j] * kx + P.sidx[3 * j + 1] * ky + P.sidx[3 * j + 2] * kz) % G;
@@ -262,9 +271,18 @@ __global__ void k_fast_tables(Pass P, int64_t n) {
       P.ftab[2 * e + 1] = (float)(-sn);
       const double wt = (kz == 0 || kz == P.p) ? 1.0 : 2.0;
       const double inv = wt / ((double)G * G * G);
-      const size_t o = 2 * ((size_t)w * P.ns + j);
-      P.fitab[o] = (float)(inv * c);
-      P.fitab[o + 1] = (float)(-inv * sn);
+      const int nkc = ifft_chunks(P.p);
+#pragma unroll
+      for (int ri = 0; ri < 2; ++ri) {
+        const float v = (float)(ri == 0 ? inv * c : -inv * sn);
+        const int kk = 2 * w + ri;
+        float *tl = P.fitab + ((size_t)(j / tc::kCols) * nkc + kk / tc::kChunk) * 2 * tc::kCols *
+                                  tc::kChunk;
+        const uint32_t o = tc::b_table_offset(j % tc::kCols, kk % tc::kChunk);
+        const float h = tf32_rna(v);
+        tl[o] = h;
+        tl[tc::kCols * tc::kChunk + o] = tf32_rna(v - h);
+      }
     }
   }
 }
@@ -953,9 +971,12 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_fast_kmulp_tc(
             for (int t = 0; t < 8; ++t) {
               const int32_t ct = P.child8[8 * (size_t)par + t];
               if (ct < 0 || !in_range(P, ct, nbox)) continue;
-              float *o = P.chat32 + ((size_t)ct * nf + w) * 6;
+              // check spectra [box][component][2 nfreq] (re, im per frequency):
+              // the rows of the inverse-DFT product
+              float2 *o = reinterpret_cast<float2 *>(P.chat32 + (size_t)ct * 6 * nf) + w;
 #pragma unroll
-              for (int q = 0; q < 6; ++q) o[q] = d[t * 6 + q];
+              for (int q = 0; q < 3; ++q)
+                o[(size_t)q * nf] = make_float2(d[t * 6 + 2 * q], d[t * 6 + 2 * q + 1]);
             }
           }
         }
@@ -972,53 +993,6 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_fast_kmulp_tc(
   }
 }
 
-// IFFT: the M2L part of the downward check velocity of a tile of 16 boxes at
-// their check points, from the half spectrum.  Two groups of box_threads(ns)
-// threads (8 boxes each) share the staged inverse-DFT rows of wc frequencies.
-constexpr int kIfftBoxes = 16;
-__global__ void k_fast_ifft(Pass P, int wc) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int nf = freq_count(P.p);
-  const int bt_threads = blockDim.x / 2;
-  float2 *F = reinterpret_cast<float2 *>(smem);                        // [wc][ns]
-  float *C = reinterpret_cast<float *>(F + (size_t)wc * P.ns);         // [16][wc][6]
-  const int32_t bt = P.box0 + blockIdx.x * kIfftBoxes;
-  const int nbt = min(kIfftBoxes, P.box1 - bt);
-  const int k = threadIdx.x % bt_threads, half = threadIdx.x / bt_threads;
-  float acc[8][3];
-#pragma unroll
-  for (int bb = 0; bb < 8; ++bb) acc[bb][0] = acc[bb][1] = acc[bb][2] = 0.f;
-  const float2 *FI = reinterpret_cast<const float2 *>(P.fitab);
-  for (int w0 = 0; w0 < nf; w0 += wc) {
-    const int nw = min(wc, nf - w0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nw * P.ns; e += blockDim.x) F[e] = FI[(size_t)w0 * P.ns + e];
-    for (int e = threadIdx.x; e < kIfftBoxes * wc * 6; e += blockDim.x) {
-      const int bb = e / (wc * 6), r = e % (wc * 6);
-      const int ww = r / 6, q = r % 6;
-      C[e] = (bb < nbt && ww < nw) ? P.chat32[((size_t)(bt + bb) * nf + w0 + ww) * 6 + q] : 0.f;
-    }
-    __syncthreads();
-    if (k < P.ns)
-      for (int ww = 0; ww < nw; ++ww) {
-        const float2 f = F[ww * P.ns + k];
-#pragma unroll
-        for (int bb = 0; bb < 8; ++bb) {
-          const float *c = C + ((half * 8 + bb) * wc + ww) * 6;
-#pragma unroll
-          for (int q = 0; q < 3; ++q) acc[bb][q] = fmaf(c[2 * q], f.x, fmaf(c[2 * q + 1], f.y, acc[bb][q]));
-        }
-      }
-  }
-  if (k < P.ns)
-#pragma unroll
-    for (int bb = 0; bb < 8; ++bb) {
-      const int b2 = half * 8 + bb;
-      if (b2 < nbt)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) P.m2l32[(size_t)(bt + b2) * 3 * P.ns + 3 * k + q] = acc[bb][q];
-    }
-}
 
 // DCHK: one CTA per box of one depth, thread k = downward check point:
 // M2L (spectral result, or dense over the V-list in batches of boxes), X-list
@@ -1043,7 +1017,7 @@ __global__ void k_fast_dchk(Pass P) {
     for (int q = 0; q < 3; ++q) xs[q] = rad * P.surf32[3 * k + q];
     if (P.spec)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) u[q] = P.m2l32[(size_t)b * 3 * P.ns + 3 * k + q];
+      for (int q = 0; q < 3; ++q) u[q] = P.m2l32[((size_t)b * 3 + q) * P.ns + k];
   }
   // equivalent sources: the dense V-list (no spectra) and the parent (L2L)
   const int32_t v0 = P.spec ? 0 : P.t.v_ptr[b], v1 = P.spec ? 0 : P.t.v_ptr[b + 1];
@@ -1266,6 +1240,15 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
       cudaSuccess)
     return err;
   const int64_t ntab = std::max<int64_t>(P.t.nbox, fft ? (int64_t)ns * nf : 0);
+  CUtensorMap chat_map;
+  if (fft) {
+    const size_t nb_tab = tc::b_table_floats(ifft_tiles(ns), ifft_chunks(P.p));
+    if ((err = cudaMemsetAsync(P.fitab, 0, sizeof(float) * nb_tab, st)) != cudaSuccess) return err;
+    // check spectra [box][component][2 nfreq] as the rows of the inverse DFT
+    if ((err = tc::encode_a(&chat_map, P.chat32, 3 * (uint64_t)P.t.nbox, 2 * (uint64_t)nf,
+                            2 * (uint64_t)nf)) != cudaSuccess)
+      return err;
+  }
   pre("tables");
   k_fast_tables<<<gs(ntab), 256, 0, st>>>(P, ntab);
   post();
@@ -1345,10 +1328,21 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
       post();
       pre("ifft");
       {
-        int wc = 20480 / (ns * 8);
-        wc = wc < 4 ? 4 : (wc > 32 ? 32 : wc);
-        const size_t sm = sizeof(float2) * (size_t)wc * ns + sizeof(float) * kIfftBoxes * wc * 6;
-        k_fast_ifft<<<(unsigned)((nb + kIfftBoxes - 1) / kIfftBoxes), 2 * bt, sm, st>>>(P, wc);
+        // the M2L part of the downward check velocities: rows (box, component)
+        // of the check spectra times the inverse-DFT table, on the tensor cores
+        tc::Args a{};
+        a.a_row0 = 3 * (int64_t)P.box0;
+        a.m = 3 * nb;
+        a.k_chunks = ifft_chunks(P.p);
+        a.n_tiles = ifft_tiles(ns);
+        a.n = ns;
+        a.btab = P.fitab;
+        a.out = P.m2l32 + 3 * (size_t)P.box0 * ns;
+        a.ldo = ns;
+        a.err = P.err;
+        a.spin_limit = kTcSpinLimit;
+        const cudaError_t e = tc::gemm3(chat_map, a, st);
+        if (err == cudaSuccess) err = e;
       }
       post();
     }

@@ -147,7 +147,8 @@ struct Pass {
   int32_t *bpos;       // [nbox + 1] exclusive scan of bflag (bpos[nbox] = total)
   int32_t *plist;      // [nbox] parents, in the order of their first children
   float *ftab;         // [ns][nfreq][2] forward DFT of the surface lattice (cos, -sin)
-  float *fitab;        // [nfreq][ns][2] inverse over the half spectrum, weighted, / G^3
+  float *fitab;        // inverse DFT over the half spectrum (weighted, / G^3) as the B table
+                       // of the tensor-core product (fmm_fast.cu)
   int32_t *err;        // device error word (a tree index out of range), at workspace + 8 bytes
   float *uhh, *uhl;    // [nfreq][uslots][4][2] upward spectra of one depth split into TF32
                        // hi + lo parts, parent-major: slot 8 k + o holds the child in octant o
@@ -1033,7 +1034,8 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t 
       L.chat32 = take(sizeof(float) * 2 * nf * 3 * B);
       L.m2l32 = take(sizeof(float) * 3 * ns * B);
       L.ftab = take(sizeof(float) * 2 * ns * nf);
-      L.fitab = take(sizeof(float) * 2 * ns * nf);
+      L.fitab = take(sizeof(float) * 2 * 64 * 32 * (size_t)((ns + 63) / 64) *
+                     ((2 * nf + 31) / 32));  // the inverse-DFT product's B table
       L.vpar = take(sizeof(int32_t) * 26 * B);
       L.uhh = take(sizeof(float) * 8 * nf * (size_t)L.uslots);
       L.uhl = take(sizeof(float) * 8 * nf * (size_t)L.uslots);

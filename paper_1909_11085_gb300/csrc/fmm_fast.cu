@@ -73,11 +73,12 @@ struct SrcStage {
   float4 y, q, p, n;
 };
 
-// Adds the single and double layer of n staged points at x.
+// Adds the single and double layer of the staged points j0, j0 + js, ... < n
+// at x.
 template <bool SL, bool DL>
-__device__ __forceinline__ void eval_sources(const SrcStage *S, int n, float x0, float x1, float x2,
-                                             float u[3]) {
-  for (int i = 0; i < n; ++i) {
+__device__ __forceinline__ void eval_sources(const SrcStage *S, int j0, int n, int js, float x0,
+                                             float x1, float x2, float u[3]) {
+  for (int i = j0; i < n; i += js) {
     const float4 y = S[i].y;
     const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
     const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
@@ -101,11 +102,12 @@ __device__ __forceinline__ void eval_sources(const SrcStage *S, int n, float x0,
   }
 }
 
-__device__ __forceinline__ void eval_sources_any(const Pass &P, const SrcStage *S, int n, float x0,
-                                                 float x1, float x2, float u[3]) {
-  if (P.qf && P.pf) eval_sources<true, true>(S, n, x0, x1, x2, u);
-  else if (P.qf) eval_sources<true, false>(S, n, x0, x1, x2, u);
-  else eval_sources<false, true>(S, n, x0, x1, x2, u);
+__device__ __forceinline__ void eval_sources_any(const Pass &P, const SrcStage *S, int j0, int n,
+                                                 int js, float x0, float x1, float x2,
+                                                 float u[3]) {
+  if (P.qf && P.pf) eval_sources<true, true>(S, j0, n, js, x0, x1, x2, u);
+  else if (P.qf) eval_sources<true, false>(S, j0, n, js, x0, x1, x2, u);
+  else eval_sources<false, true>(S, j0, n, js, x0, x1, x2, u);
 }
 
 // Stages points [i0, i0 + n) (n <= blockDim.x) of the packed arrays.
@@ -357,7 +359,7 @@ __global__ void k_fast_s2m(Pass P) {
     __syncthreads();
     stage_points(P, S, c0, n);
     __syncthreads();
-    if (k < P.ns) eval_sources_any(P, S, n, x[0], x[1], x[2], u);
+    if (k < P.ns) eval_sources_any(P, S, 0, n, 1, x[0], x[1], x[2], u);
   }
   if (k < P.ns)
 #pragma unroll
@@ -994,6 +996,63 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_fast_kmulp_tc(
 }
 
 
+// Work items of the L2T (leaf points against the leaf's downward density and
+// its W-list boxes' upward densities): a block of pb points (a power of two,
+// 8 <= pb <= 256) against all of the leaf's sources, S = 256 / pb threads per
+// point (adjacent lanes, each taking every S-th staged source, summed by
+// shuffles in a fixed order).  pb is the largest with pb x sources <=
+// kItemWork (and no larger than the points need), so that a leaf with a long
+// W-list is spread over many CTAs; every point is evaluated by one item,
+// whatever the grid.
+constexpr int kItemThreads = 256;
+constexpr int64_t kItemWork = (int64_t)1 << 16;  // point-source pairs per item aimed at
+__device__ __forceinline__ int item_targets(int ntarget, int64_t nsrc) {
+  int pb = kItemThreads;
+  while (pb > 8 && (int64_t)pb * nsrc > kItemWork) pb >>= 1;
+  int cap = 8;
+  while (cap < ntarget && cap < kItemThreads) cap <<= 1;
+  return pb < cap ? pb : cap;
+}
+// Items per leaf: icnt[l], the block size in ipb[l] (log2).
+__global__ void k_fast_item_counts(Pass P) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < P.t.nleaf; l += stride) {
+    int32_t cnt = 0, lg = 3;
+    int pb = 8;
+    const int32_t b = P.t.leaf_box[l];
+    if (in_range(P, b, P.t.nbox)) {
+      const int64_t i0 = P.t.leaf_ptr[l], i1 = P.t.leaf_ptr[l + 1];
+      if (i1 > i0 && in_range(P, i0, P.n + 1) && in_range(P, i1, P.n + 1)) {
+        const int64_t nsrc =
+            (int64_t)P.ns * ((P.t.depth[b] >= kFirstDepth ? 1 : 0) + P.t.w_ptr[b + 1] - P.t.w_ptr[b]);
+        pb = item_targets((int)min(i1 - i0, (int64_t)kItemThreads), nsrc);
+        cnt = (int32_t)((i1 - i0 + pb - 1) / pb);
+      }
+    }
+    while ((1 << lg) < pb) ++lg;
+    P.icnt[l] = cnt;
+    P.ipb[l] = lg;
+  }
+}
+// The items in leaf order: items[ioff[l] + i] = (l, i | log2(pb) << 24).
+__global__ void k_fast_item_expand(Pass P) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < P.t.nleaf; l += stride) {
+    const int32_t o = P.ioff[l], c = P.icnt[l], lg = P.ipb[l];
+    for (int32_t i = 0; i < c; ++i) {
+      P.items[2 * (size_t)(o + i)] = (int32_t)l;
+      P.items[2 * (size_t)(o + i) + 1] = i | (lg << 24);
+    }
+  }
+}
+
+// Sums u over the S adjacent lanes of a target (S a power of two <= 32).
+__device__ __forceinline__ void lane_sum(float u[3], int S) {
+  for (int o = 1; o < S; o <<= 1)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) u[q] += __shfl_xor_sync(kFull, u[q], o);
+}
+
 // DCHK: one CTA per box of one depth, thread k = downward check point:
 // M2L (spectral result, or dense over the V-list in batches of boxes), X-list
 // sources (one leaf at a time, in this box's frame), L2L.  Offsets of source
@@ -1077,7 +1136,7 @@ __global__ void k_fast_dchk(Pass P) {
       __syncthreads();
       stage_points(P, S, c0, n);
       __syncthreads();
-      if (act) eval_sources_any(P, S, n, o0 + xs[0], o1 + xs[1], o2 + xs[2], u);
+      if (act) eval_sources_any(P, S, 0, n, 1, o0 + xs[0], o1 + xs[1], o2 + xs[2], u);
     }
   }
   if (act) {
@@ -1088,39 +1147,36 @@ __global__ void k_fast_dchk(Pass P) {
   }
 }
 
-// L2T + W-list: one CTA of kL2tThreads per leaf, leaves in descending order
-// of work (the few leaves with long W-lists start first); the leaf's
-// downward density and its W-list boxes' upward densities are staged in
-// batches in the leaf's frame.  A leaf of n points takes S = 1, 2, 4 or 8
-// threads per point (the most with S n <= kL2tThreads); the S threads of a
-// point (adjacent lanes) take every S-th staged source and are summed by
-// shuffles in a fixed order.
-constexpr int kL2tThreads = 256;
-__global__ void __launch_bounds__(kL2tThreads) k_fast_l2t(Pass P) {
+// L2T + W-list: items of the leaves (k_fast_item_counts), thread = (point,
+// lane of S); the leaf's downward density and its W-list boxes' upward
+// densities are staged in batches in the leaf's frame.
+__global__ void __launch_bounds__(kItemThreads) k_fast_l2t(Pass P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ EqSrc src[kEqBatchMax];
   const int neq = eq_batch_boxes(P.ns);
   EqStage *E = reinterpret_cast<EqStage *>(smem);  // [neq ns]
-  const int32_t l = P.lorder[blockIdx.x];
-  if (!in_range(P, l, P.t.nleaf)) return;
-  const int32_t b = P.t.leaf_box[l];
-  if (!in_range(P, b, P.t.nbox)) return;
-  const int d = P.t.depth[b];
-  const int64_t i0 = P.t.leaf_ptr[l], i1 = P.t.leaf_ptr[l + 1];
-  if (!in_range(P, i0, P.n + 1) || !in_range(P, i1, P.n + 1) || i1 <= i0) return;
-  const int npts = (int)(i1 - i0);
-  int S = 1;
-  while (S < 8 && 2 * S * npts <= kL2tThreads) S *= 2;
-  const int per_round = kL2tThreads / S;
-  const int pi = threadIdx.x / S, sl = threadIdx.x % S;
-  const float r = half_width(P.t, d);
-  const int32_t w0 = P.t.w_ptr[b], w1 = P.t.w_ptr[b + 1];
-  const int ndn = d >= kFirstDepth ? 1 : 0;
-  const int neqs = ndn + (w1 - w0);
+  const int32_t it0 = 0, it1 = P.ioff[P.t.nleaf];
   const float csl = (float)P.csl, csrc = (float)P.csrc;
-  for (int64_t p0 = i0; p0 < i1; p0 += per_round) {
-    const int64_t e = p0 + pi;
+  for (int32_t it = it0 + blockIdx.x; it < it1; it += gridDim.x) {
+    const int2 item = make_int2(P.items[2 * (size_t)it], P.items[2 * (size_t)it + 1]);
+    const int32_t l = item.x;
+    if (l < 0 || l >= P.t.nleaf) {  // uniform over the CTA
+      if (threadIdx.x == 0) bad_index(P);
+      continue;
+    }
+    const int32_t b = P.t.leaf_box[l];
+    if (!in_range(P, b, P.t.nbox)) continue;
+    const int d = P.t.depth[b];
+    const int64_t i0 = P.t.leaf_ptr[l], i1 = P.t.leaf_ptr[l + 1];
+    if (!in_range(P, i0, P.n + 1) || !in_range(P, i1, P.n + 1) || i1 <= i0) continue;
+    const int pb = 1 << (item.y >> 24), sw = kItemThreads / pb;
+    const int64_t e = i0 + (int64_t)(item.y & 0xffffff) * pb + (int)threadIdx.x / sw;
+    const int sl = (int)threadIdx.x % sw;
     const bool act = e < i1;
+    const float r = half_width(P.t, d);
+    const int32_t w0 = P.t.w_ptr[b], w1 = P.t.w_ptr[b + 1];
+    const int ndn = d >= kFirstDepth ? 1 : 0;
+    const int neqs = ndn + (w1 - w0);
     float x[3] = {0.f, 0.f, 0.f}, uf[3] = {0.f, 0.f, 0.f}, uq[3] = {0.f, 0.f, 0.f};
     if (act)
 #pragma unroll
@@ -1154,40 +1210,19 @@ __global__ void __launch_bounds__(kL2tThreads) k_fast_l2t(Pass P) {
       stage_eq_batch(P, E, src, nb);
       __syncthreads();
       if (act) {
-        if (P.nc == 4) eval_equiv_acc<true>(E, sl, nb * P.ns, S, x[0], x[1], x[2], uf, uq);
-        else eval_equiv_acc<false>(E, sl, nb * P.ns, S, x[0], x[1], x[2], uf, uq);
+        if (P.nc == 4) eval_equiv_acc<true>(E, sl, nb * P.ns, sw, x[0], x[1], x[2], uf, uq);
+        else eval_equiv_acc<false>(E, sl, nb * P.ns, sw, x[0], x[1], x[2], uf, uq);
       }
     }
     float u[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) u[q] = csl * uf[q] + csrc * uq[q];
-    for (int o = 1; o < S; o <<= 1)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) u[q] += __shfl_xor_sync(kFull, u[q], o);
+    lane_sum(u, sw);
     if (act && sl == 0) {
       double *out = P.out + 3 * e;
 #pragma unroll
       for (int a = 0; a < 3; ++a) out[a] = (P.accumulate ? out[a] : 0.0) + (double)u[a];
     }
-  }
-}
-
-// Cost keys of the leaves for the L2T order (the bucket order of the
-// near-field items: targets in the high word, sources in the low word).
-__global__ void k_fast_l2t_keys(Pass P) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < P.t.nleaf; l += stride) {
-    const int32_t b = P.t.leaf_box[l];
-    int64_t npts = 0, nw = 0;
-    if (b >= 0 && b < P.t.nbox) {
-      npts = (int64_t)P.t.leaf_ptr[l + 1] - P.t.leaf_ptr[l];
-      nw = (int64_t)P.t.w_ptr[b + 1] - P.t.w_ptr[b];
-    }
-    const int64_t work = npts * (1 + nw);
-    const uint64_t tn = work >= 4096 ? 129 : 1;  // long W-lists first
-    const uint64_t ns = (uint64_t)min(work, (int64_t)0xffffffff);
-    P.lkeys[l] = (tn << 32) | ns;
-    P.lvals[l] = (int32_t)l;
   }
 }
 
@@ -1260,6 +1295,18 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
   pre("plist");
   k_fast_plist<<<gs(P.t.nbox), 256, 0, st>>>(P);
   post();
+  {
+    // work items of the L2T (counts, their scan, the item list)
+    const int64_t ne = P.t.nleaf;
+    pre("items");
+    k_fast_item_counts<<<gs(ne), 256, 0, st>>>(P);
+    count_launches(1);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    launch_scan(P.icnt, ne, P.ioff, P.ioff + ne, st);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    k_fast_item_expand<<<gs(ne), 256, 0, st>>>(P);
+    post();
+  }
   if (fft) {
     pre("vpar");
     k_fast_vpar<<<gs((int64_t)P.t.nbox * 26), 256, 0, st>>>(P);
@@ -1353,16 +1400,12 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
     launch_c2e<false>(P, nb, ns, st);
     post();
   }
-  pre("l2t_order");
-  k_fast_l2t_keys<<<gs(P.t.nleaf), 256, 0, st>>>(P);
-  if (err == cudaSuccess) err = cudaGetLastError();
-  count_launches(1);
-  launch_bucket_order(P.t.nleaf, P.lkeys, P.lvals, P.lcnt, P.loff, P.lrank, P.lorder, st);
-  if (err == cudaSuccess) err = cudaGetLastError();
-  hk.after(seq, st);
-  ++seq;
   pre("l2t");
-  k_fast_l2t<<<P.t.nleaf, kL2tThreads, sizeof(EqStage) * eq_batch_boxes(ns) * ns, st>>>(P);
+  {
+    const int64_t bound = (int64_t)P.t.nleaf + (P.n + 7) / 8;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(bound, (int64_t)sms * 8));
+    k_fast_l2t<<<g, kItemThreads, sizeof(EqStage) * eq_batch_boxes(ns) * ns, st>>>(P);
+  }
   post();
   return err;
 }

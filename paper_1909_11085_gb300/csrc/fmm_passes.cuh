@@ -160,10 +160,10 @@ struct Pass {
                        // fmm_fast.cu)
   int32_t *vpar;       // [26][nbox] plist position of the neighbour in each direction of the
                        // parent at each plist position (-1 where it has no children)
-  // leaf order of the blocked L2T (most work first): cost keys, leaf numbers,
-  // bucket counts and offsets, ranks and the order
-  uint64_t *lkeys;
-  int32_t *lvals, *lcnt, *loff, *lrank, *lorder;
+  // work items of the blocked L2T (fmm_fast.cu): per leaf the item count,
+  // log2 of the points per item and the exclusive scan of the counts; the
+  // items as (leaf, block | log2 << 24) pairs
+  int32_t *icnt, *ipb, *ioff, *items;
 };
 
 // Boundary points of the p^3 grid on [-1, 1]^3, i slowest, k fastest.
@@ -958,7 +958,7 @@ struct Layout {
   size_t chk32, ops_hi, ops_lo;
   size_t child8, bflag, bpos, plist, ftab, fitab, vpar, uhh, uhl, btab;
   int64_t uslots;
-  size_t lkeys, lvals, lcnt, loff, lrank, lorder;
+  size_t icnt, ipb, ioff, items;
   size_t total;
 };
 
@@ -1003,7 +1003,7 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t 
   L.child8 = L.bflag = L.bpos = L.plist = L.ftab = L.fitab = L.vpar = L.uhh = L.uhl = L.btab =
       none;
   L.uslots = spectrum_slots(depth_ptr, max_depth);
-  L.lkeys = L.lvals = L.lcnt = L.loff = L.lrank = L.lorder = none;
+  L.icnt = L.ipb = L.ioff = L.items = none;
   if (!mixed) {
     L.chk = take(sizeof(double) * 3 * ns * B);
     L.up = take(sizeof(double) * nc * ns * B);
@@ -1045,13 +1045,11 @@ inline Layout layout(int64_t nbox, int p, int nc, bool fft, bool mixed, int64_t 
     L.bflag = take(sizeof(int32_t) * B);
     L.bpos = take(sizeof(int32_t) * (B + 1));
     L.plist = take(sizeof(int32_t) * B);
-    const size_t NL = (size_t)nbox;  // >= leaves
-    L.lkeys = take(sizeof(uint64_t) * NL);
-    L.lvals = take(sizeof(int32_t) * NL);
-    L.lcnt = take(sizeof(int32_t) * 256);
-    L.loff = take(sizeof(int32_t) * 256);
-    L.lrank = take(sizeof(int32_t) * NL);
-    L.lorder = take(sizeof(int32_t) * NL);
+    // L2T items: at most ceil(points / 8) per leaf
+    L.icnt = take(sizeof(int32_t) * B);  // B >= leaves
+    L.ipb = take(sizeof(int32_t) * B);
+    L.ioff = take(sizeof(int32_t) * (B + 1));
+    L.items = take(sizeof(int32_t) * 2 * (B + (N + 7) / 8 + 1));
   }
   L.total = o + 256;  // slack for aligning the caller's base
   return L;
@@ -1099,12 +1097,10 @@ inline void bind(Pass &P, char *ws, const Layout &L, bool fft, bool mixed) {
   P.uhh = (fft && mixed) ? f(L.uhh) : nullptr;
   P.uhl = (fft && mixed) ? f(L.uhl) : nullptr;
   P.btab = (fft && mixed) ? f(L.btab) : nullptr;
-  P.lkeys = mixed ? reinterpret_cast<uint64_t *>(ws + L.lkeys) : nullptr;
-  P.lvals = mixed ? i32(L.lvals) : nullptr;
-  P.lcnt = mixed ? i32(L.lcnt) : nullptr;
-  P.loff = mixed ? i32(L.loff) : nullptr;
-  P.lrank = mixed ? i32(L.lrank) : nullptr;
-  P.lorder = mixed ? i32(L.lorder) : nullptr;
+  P.icnt = mixed ? i32(L.icnt) : nullptr;
+  P.ipb = mixed ? i32(L.ipb) : nullptr;
+  P.ioff = mixed ? i32(L.ioff) : nullptr;
+  P.items = mixed ? i32(L.items) : nullptr;
 }
 
 // Surface points, lattice indices and twiddles (one thread; set-up of a call).

@@ -84,11 +84,11 @@ def test_far_field_matches_the_oracle(lib, case, flux, kinds, m2l, precision, to
     # set-up + the passes; Fourier space adds 3 per depth; mixed adds the
     # packing and operator-splitting passes and, with spectra, their rounding,
     # and (the CTA-blocked form) the octant table, the first-child scan, the
-    # parent list and the leaves' cost order (keys and a three-launch bucket order),
-    # and with spectra the table of each parent's source boxes and the table of
-    # the tensor-core operand B
+    # parent list and the work items of the L2T (counts, their scan, the
+    # list), and with spectra the table of each parent's neighbours and the
+    # table of the tensor-core operand B
     assert launches == (1 + 2 + 4 * (t["max_depth"] - 1) - 1 + 3 * fft * (t["max_depth"] - 1)
-                        + mixed * (2 + fft * 3 + 7))
+                        + mixed * (2 + fft * 3 + 6))
     # accumulate
     import torch
     base = torch.full((wl.pts.shape[0], 3), 0.5, dtype=torch.float64, device="cuda")
@@ -185,9 +185,9 @@ def test_far_field_six_deep_tree(lib, deep, m2l, precision, tol):
     A.check(L.stokes_device_status(A.ptr(plan.ws), plan.ws.numel()))
     assert _rel(far, ref) <= tol, _rel(far, ref)
     if precision == "mixed":
-        # the set-up kernel is not hooked; the leaves' cost order (keys and a
-        # three-launch bucket order) is timed as one entry
-        assert count.value == launches - 4
+        # the set-up kernel is not hooked; the work items (counts, scan, list)
+        # are timed as one entry
+        assert count.value == launches - 3
         got = {names[k].decode() for k in range(count.value)}
         assert {"s2m", "uc2e", "dchk", "dc2e", "l2t"} <= got
         assert ({"ufft", "kmulp", "ifft"} <= got) == (m2l == "fft")

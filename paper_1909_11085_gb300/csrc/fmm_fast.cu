@@ -67,98 +67,6 @@ __device__ __forceinline__ float half_width(const Tree &t, int d) {
   return (float)ldexp(t.root_size, -d - 1);
 }
 
-// Source points staged in shared memory: local position, q = w f csl,
-// psi = w phi cdl, normal (unused parts zero).
-struct SrcStage {
-  float4 y, q, p, n;
-};
-
-// Adds the single and double layer of the staged points j0, j0 + js, ... < n
-// at x.
-template <bool SL, bool DL>
-__device__ __forceinline__ void eval_sources(const SrcStage *S, int j0, int n, int js, float x0,
-                                             float x1, float x2, float u[3]) {
-  for (int i = j0; i < n; i += js) {
-    const float4 y = S[i].y;
-    const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
-    const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
-    if (!(r2 > 0.0f)) continue;
-    const float ri = rsqrtf(r2), ri2 = ri * ri;
-    if (SL) {
-      const float4 q = S[i].q;
-      const float dq = (d0 * q.x + d1 * q.y + d2 * q.z) * ri2 * ri;
-      u[0] += q.x * ri + d0 * dq;
-      u[1] += q.y * ri + d1 * dq;
-      u[2] += q.z * ri + d2 * dq;
-    }
-    if (DL) {
-      const float4 s = S[i].p, nn = S[i].n;
-      const float c = (d0 * s.x + d1 * s.y + d2 * s.z) * (d0 * nn.x + d1 * nn.y + d2 * nn.z) *
-                      ri2 * ri2 * ri;
-      u[0] += d0 * c;
-      u[1] += d1 * c;
-      u[2] += d2 * c;
-    }
-  }
-}
-
-__device__ __forceinline__ void eval_sources_any(const Pass &P, const SrcStage *S, int j0, int n,
-                                                 int js, float x0, float x1, float x2,
-                                                 float u[3]) {
-  if (P.qf && P.pf) eval_sources<true, true>(S, j0, n, js, x0, x1, x2, u);
-  else if (P.qf) eval_sources<true, false>(S, j0, n, js, x0, x1, x2, u);
-  else eval_sources<false, true>(S, j0, n, js, x0, x1, x2, u);
-}
-
-// Stages points [i0, i0 + n) (n <= blockDim.x) of the packed arrays.
-__device__ __forceinline__ void stage_points(const Pass &P, SrcStage *S, int64_t i0, int n) {
-  const int t = threadIdx.x;
-  if (t < n) {
-    const int64_t i = i0 + t;
-    SrcStage s;
-    s.y = make_float4(P.ploc[3 * i], P.ploc[3 * i + 1], P.ploc[3 * i + 2], 0.f);
-    s.q = P.qf ? make_float4(P.qf[3 * i], P.qf[3 * i + 1], P.qf[3 * i + 2], 0.f)
-               : make_float4(0.f, 0.f, 0.f, 0.f);
-    s.p = P.pf ? make_float4(P.pf[3 * i], P.pf[3 * i + 1], P.pf[3 * i + 2], 0.f)
-               : make_float4(0.f, 0.f, 0.f, 0.f);
-    s.n = P.nf ? make_float4(P.nf[3 * i], P.nf[3 * i + 1], P.nf[3 * i + 2], 0.f)
-               : make_float4(0.f, 0.f, 0.f, 0.f);
-    S[t] = s;
-  }
-}
-
-// Equivalent density staged in shared memory: surface point (already scaled
-// by the radius) and density (force x, y, z and source strength).
-struct EqStage {
-  float4 y, e;
-};
-
-// Adds the field of ns staged equivalent points at x (csl, csrc applied).
-template <bool FLUX>
-__device__ __forceinline__ void eval_equiv(const EqStage *E, int ns, float x0, float x1, float x2,
-                                           float csl, float csrc, float u[3]) {
-  float uf[3] = {0.f, 0.f, 0.f}, uq[3] = {0.f, 0.f, 0.f};
-  for (int j = 0; j < ns; ++j) {
-    const float4 y = E[j].y, e = E[j].e;
-    const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
-    const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
-    if (!(r2 > 0.0f)) continue;
-    const float ri = rsqrtf(r2), ri3 = ri * ri * ri;
-    const float df = (d0 * e.x + d1 * e.y + d2 * e.z) * ri3;
-    uf[0] += e.x * ri + d0 * df;
-    uf[1] += e.y * ri + d1 * df;
-    uf[2] += e.z * ri + d2 * df;
-    if (FLUX) {
-      const float s = e.w * ri3;
-      uq[0] += d0 * s;
-      uq[1] += d1 * s;
-      uq[2] += d2 * s;
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) u[a] += csl * uf[a] + csrc * uq[a];
-}
-
 // x rounded to TF32 (10 explicit mantissa bits, round to nearest, ties away),
 // kept in an FP32 register.
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -176,43 +84,148 @@ struct EqSrc {
   float off[3];  // centre(target box) - centre(source box), FP32
 };
 
-// Stages the boxes src[0, nb) into E (nb ns points), each surface point in
-// the target box's frame: rad s_j - off.
-__device__ __forceinline__ void stage_eq_batch(const Pass &P, EqStage *E, const EqSrc *src,
-                                               int nb) {
-  const int total = nb * P.ns;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int k = e / P.ns, j = e % P.ns;
-    const EqSrc &S = src[k];
-    const float *sp = P.surf32 + 3 * j;
-    const float *d = S.dens + (size_t)S.nc * j;
-    E[e].y = make_float4(S.rad * sp[0] - S.off[0], S.rad * sp[1] - S.off[1],
-                         S.rad * sp[2] - S.off[2], 0.f);
-    E[e].e = S.nc == 0 ? make_float4(0.f, 0.f, 0.f, 0.f)
-                       : make_float4(d[0], d[1], d[2], S.nc == 4 ? d[3] : 0.f);
+// ---------------------------------------------------------------- pair math
+// Packed FP32 pairs: two staged sources per instruction (FFMA2 and friends);
+// per half the operations are those of a scalar evaluation.
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_lo(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 p_hi(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 p_dup(float v) { return make_float2(v, v); }
+// 1/sqrt per half (rsqrt.approx, relative error below 2^-22), 0 where r2 is 0
+// (a coincident pair contributes nothing).
+__device__ __forceinline__ float2 p_rsqrt(float2 r2) {
+  float a, b;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(a) : "f"(r2.x));
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(b) : "f"(r2.y));
+  return make_float2(r2.x > 0.f ? a : 0.f, r2.y > 0.f ? b : 0.f);
+}
+constexpr float kFarAway = 1e18f;  // position of the missing half of a pair (zero strength)
+
+// Source points staged two by two, the pair's halves interleaved, positions
+// negated, in kSrcFields planes of cap float4 (lanes reading consecutive
+// pairs touch consecutive words): plane 0 (-y.x, -y.y), 1 (-y.z, q.x),
+// 2 (q.y, q.z), 3 (p.x, p.y), 4 (p.z, n.x), 5 (n.y, n.z), each entry a
+// (first, second) pair.
+constexpr int kSrcFields = 6;
+// Stages points [i0, i0 + n) (n <= 2 blockDim, (n + 1) / 2 <= cap) as pairs.
+__device__ __forceinline__ void stage_point_pairs(const Pass &P, float4 *S, int cap, int64_t i0,
+                                                  int n) {
+  const int t = threadIdx.x;
+  if (2 * t >= n) return;
+  float v[2][12];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t i = i0 + 2 * t + h;
+    const bool ok = 2 * t + h < n;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      v[h][q] = ok ? -P.ploc[3 * i + q] : -kFarAway;
+      v[h][3 + q] = ok && P.qf ? P.qf[3 * i + q] : 0.f;
+      v[h][6 + q] = ok && P.pf ? P.pf[3 * i + q] : 0.f;
+      v[h][9 + q] = ok && P.nf ? P.nf[3 * i + q] : 0.f;
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < kSrcFields; ++f)
+    S[(size_t)f * cap + t] = make_float4(v[0][2 * f], v[1][2 * f], v[0][2 * f + 1], v[1][2 * f + 1]);
+}
+// Adds the single and double layer of the staged pairs j0, j0 + js, ... < np
+// at two targets (x: each coordinate duplicated into both halves; u: per-half
+// sums).  SL: (q + d (d.q)/r^2)/r, DL: d (d.psi)(d.n)/r^5.
+template <bool SL, bool DL>
+__device__ __forceinline__ void eval_src_pairs(const float4 *S, int cap, int j0, int np, int js,
+                                               const float2 (&x)[2][3], float2 (&u)[2][3]) {
+  for (int j = j0; j < np; j += js) {
+    const float4 a = S[j], b = S[cap + j];
+    const float2 nyx = p_lo(a), nyy = p_hi(a), nyz = p_lo(b);
+    float2 qx, qy, qz, px, py, pz, nx, ny, nz;
+    if (SL) {
+      const float4 c = S[2 * cap + j];
+      qx = p_hi(b);
+      qy = p_lo(c);
+      qz = p_hi(c);
+    }
+    if (DL) {
+      const float4 d = S[3 * cap + j], e = S[4 * cap + j], f = S[5 * cap + j];
+      px = p_lo(d);
+      py = p_hi(d);
+      pz = p_lo(e);
+      nx = p_hi(e);
+      ny = p_lo(f);
+      nz = p_hi(f);
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const float2 dx = p_add(x[t][0], nyx), dy = p_add(x[t][1], nyy), dz = p_add(x[t][2], nyz);
+      const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
+      const float2 ri = p_rsqrt(r2), ri2 = p_mul(ri, ri);
+      if (SL && DL) {
+        const float2 dq = p_fma(dx, qx, p_fma(dy, qy, p_mul(dz, qz)));
+        const float2 dp = p_fma(dx, px, p_fma(dy, py, p_mul(dz, pz)));
+        const float2 dn = p_fma(dx, nx, p_fma(dy, ny, p_mul(dz, nz)));
+        const float2 c = p_mul(p_fma(p_mul(dp, dn), ri2, dq), ri2);
+        u[t][0] = p_fma(p_fma(dx, c, qx), ri, u[t][0]);
+        u[t][1] = p_fma(p_fma(dy, c, qy), ri, u[t][1]);
+        u[t][2] = p_fma(p_fma(dz, c, qz), ri, u[t][2]);
+      } else if (SL) {
+        const float2 dq = p_fma(dx, qx, p_fma(dy, qy, p_mul(dz, qz)));
+        const float2 c = p_mul(dq, ri2);
+        u[t][0] = p_fma(p_fma(dx, c, qx), ri, u[t][0]);
+        u[t][1] = p_fma(p_fma(dy, c, qy), ri, u[t][1]);
+        u[t][2] = p_fma(p_fma(dz, c, qz), ri, u[t][2]);
+      } else {
+        const float2 dp = p_fma(dx, px, p_fma(dy, py, p_mul(dz, pz)));
+        const float2 dn = p_fma(dx, nx, p_fma(dy, ny, p_mul(dz, nz)));
+        const float2 c = p_mul(p_mul(dp, dn), p_mul(p_mul(ri2, ri2), ri));
+        u[t][0] = p_fma(dx, c, u[t][0]);
+        u[t][1] = p_fma(dy, c, u[t][1]);
+        u[t][2] = p_fma(dz, c, u[t][2]);
+      }
+    }
   }
 }
+__device__ __forceinline__ void eval_src_pairs_any(const Pass &P, const float4 *S, int cap, int j0,
+                                                   int np, int js, const float2 (&x)[2][3],
+                                                   float2 (&u)[2][3]) {
+  if (P.qf && P.pf) eval_src_pairs<true, true>(S, cap, j0, np, js, x, u);
+  else if (P.qf) eval_src_pairs<true, false>(S, cap, j0, np, js, x, u);
+  else eval_src_pairs<false, true>(S, cap, j0, np, js, x, u);
+}
 
-// Adds the field of the staged points j0, j0 + js, ... < n at x (csl, csrc
-// applied by the caller through uf, uq).
-template <bool FLUX>
-__device__ __forceinline__ void eval_equiv_acc(const EqStage *E, int j0, int n, int js, float x0,
-                                               float x1, float x2, float uf[3], float uq[3]) {
-  for (int j = j0; j < n; j += js) {
-    const float4 y = E[j].y, e = E[j].e;
-    const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
-    const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
-    if (!(r2 > 0.0f)) continue;
-    const float ri = rsqrtf(r2), ri3 = ri * ri * ri;
-    const float df = (d0 * e.x + d1 * e.y + d2 * e.z) * ri3;
-    uf[0] += e.x * ri + d0 * df;
-    uf[1] += e.y * ri + d1 * df;
-    uf[2] += e.z * ri + d2 * df;
-    if (FLUX) {
-      const float sv = e.w * ri3;
-      uq[0] += d0 * sv;
-      uq[1] += d1 * sv;
-      uq[2] += d2 * sv;
+// Equivalent points staged two by two in kEqFields planes of cap float4:
+// plane 0 (-y.x, -y.y), 1 (-y.z, e.x), 2 (e.y, e.z), 3 (e.w, unused), each
+// entry a (first, second) pair; the positions already scaled by the radius
+// and in the target box's frame.
+constexpr int kEqFields = 4;
+// Adds the field of the staged pairs j0, j0 + js, ... < np at T targets:
+// Stokeslet (e + d (d.e)/r^2)/r into uf, point source d e.w/r^3 into uq.
+template <bool FLUX, int T = 2>
+__device__ __forceinline__ void eval_eq_pairs(const float4 *E, int cap, int j0, int np, int js,
+                                              const float2 (&x)[T][3], float2 (&uf)[T][3],
+                                              float2 (&uq)[T][3]) {
+  for (int j = j0; j < np; j += js) {
+    const float4 a = E[j], b = E[cap + j], c = E[2 * cap + j];
+    const float2 nyx = p_lo(a), nyy = p_hi(a), nyz = p_lo(b);
+    const float2 ex = p_hi(b), ey = p_lo(c), ez = p_hi(c);
+    float2 ew;
+    if (FLUX) ew = p_lo(E[3 * cap + j]);
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const float2 dx = p_add(x[t][0], nyx), dy = p_add(x[t][1], nyy), dz = p_add(x[t][2], nyz);
+      const float2 r2 = p_fma(dx, dx, p_fma(dy, dy, p_mul(dz, dz)));
+      const float2 ri = p_rsqrt(r2), ri3 = p_mul(p_mul(ri, ri), ri);
+      const float2 df = p_mul(p_fma(dx, ex, p_fma(dy, ey, p_mul(dz, ez))), ri3);
+      uf[t][0] = p_fma(ex, ri, p_fma(dx, df, uf[t][0]));
+      uf[t][1] = p_fma(ey, ri, p_fma(dy, df, uf[t][1]));
+      uf[t][2] = p_fma(ez, ri, p_fma(dz, df, uf[t][2]));
+      if (FLUX) {
+        const float2 sv = p_mul(ew, ri3);
+        uq[t][0] = p_fma(dx, sv, uq[t][0]);
+        uq[t][1] = p_fma(dy, sv, uq[t][1]);
+        uq[t][2] = p_fma(dz, sv, uq[t][2]);
+      }
     }
   }
 }
@@ -232,6 +245,64 @@ __device__ __forceinline__ EqSrc eq_none(const Pass &P) {
   q.rad = 0.f;
   q.off[0] = q.off[1] = q.off[2] = 0.f;
   return q;
+}
+
+// Stages the boxes src[0, nb) into E as (nb ns + 1) / 2 <= cap pairs, each
+// surface point in the target box's frame: rad s_j - off (negated).
+__device__ __forceinline__ void stage_eq_pairs(const Pass &P, float4 *E, int cap, const EqSrc *src,
+                                               int nb) {
+  const int total = nb * P.ns, npair = (total + 1) / 2;
+  for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+    float v[2][7];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * e + h;
+      if (i < total) {
+        const int k = i / P.ns, j = i % P.ns;
+        const EqSrc &S = src[k];
+        const float *sp = P.surf32 + 3 * j;
+        const float *d = S.dens + (size_t)S.nc * j;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[h][q] = S.off[q] - S.rad * sp[q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[h][3 + q] = q < S.nc ? d[q] : 0.f;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[h][q] = -kFarAway;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[h][3 + q] = 0.f;
+      }
+    }
+    E[e] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+    E[cap + e] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
+    E[2 * cap + e] = make_float4(v[0][4], v[1][4], v[0][5], v[1][5]);
+    E[3 * cap + e] = make_float4(v[0][6], v[1][6], 0.f, 0.f);
+  }
+}
+
+// Targets of the pair-packed evaluations: two per thread, the coordinates
+// duplicated into both halves of a pair.
+__device__ __forceinline__ void dup_targets(const float (&x)[2][3], float2 (&x2)[2][3]) {
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) x2[t][q] = p_dup(x[t][q]);
+}
+// Sums u over the S adjacent lanes of a target pair (S a power of two <= 32),
+// in a fixed order.
+__device__ __forceinline__ void lane_sum2(float (&u)[2][3], int S) {
+  for (int o = 1; o < S; o <<= 1)
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) u[t][q] += __shfl_xor_sync(kFull, u[t][q], o);
+}
+// Sum of the two halves of each of the 6 packed sums.
+__device__ __forceinline__ void fold_halves(const float2 (&u2)[2][3], float (&u)[2][3]) {
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) u[t][q] = u2[t][q].x + u2[t][q].y;
 }
 
 // ------------------------------------------------------------------ set-up
@@ -337,10 +408,12 @@ __global__ void k_fast_pack(Pass P) {
 }
 
 // ---------------------------------------------------------------- upward
-// S2M: one CTA per leaf, thread k = check point on the 2.95 r surface.
+// S2M: one CTA per leaf; threads 2c and 2c + 1 take check points 2c and
+// 2c + 1 on the 2.95 r surface, each every other staged source pair.
 __global__ void k_fast_s2m(Pass P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  SrcStage *S = reinterpret_cast<SrcStage *>(smem);
+  float4 *S = reinterpret_cast<float4 *>(smem);  // kSrcFields planes of blockDim pairs
+  const int cap = blockDim.x;
   const int32_t l = blockIdx.x;
   const int32_t b = P.t.leaf_box[l];
   if (!in_range(P, b, P.t.nbox)) return;
@@ -348,30 +421,46 @@ __global__ void k_fast_s2m(Pass P) {
   if (d < kFirstDepth) return;
   const int64_t i0 = P.t.leaf_ptr[l], i1 = P.t.leaf_ptr[l + 1];
   if (!in_range(P, i0, P.n + 1) || !in_range(P, i1, P.n + 1) || i1 < i0) return;
-  const int k = threadIdx.x;
+  const int k0 = threadIdx.x & ~1, sl = threadIdx.x & 1;
+  const bool act = k0 + 1 < P.ns;  // ns is even
   const float rad = (float)(kOuter * (double)half_width(P.t, d));
-  float x[3] = {0.f, 0.f, 0.f}, u[3] = {0.f, 0.f, 0.f};
-  if (k < P.ns)
+  float x[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  if (act)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) x[q] = rad * P.surf32[3 * k + q];
-  for (int64_t c0 = i0; c0 < i1; c0 += blockDim.x) {
-    const int n = (int)min((int64_t)blockDim.x, i1 - c0);
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) x[t][q] = rad * P.surf32[3 * (k0 + t) + q];
+  float2 x2[2][3], u2[2][3];
+  dup_targets(x, x2);
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) u2[t][q] = make_float2(0.f, 0.f);
+  const int chunk = 2 * (int)blockDim.x;
+  for (int64_t c0 = i0; c0 < i1; c0 += chunk) {
+    const int n = (int)min((int64_t)chunk, i1 - c0);
     __syncthreads();
-    stage_points(P, S, c0, n);
+    stage_point_pairs(P, S, cap, c0, n);
     __syncthreads();
-    if (k < P.ns) eval_sources_any(P, S, 0, n, 1, x[0], x[1], x[2], u);
+    if (act) eval_src_pairs_any(P, S, cap, sl, (n + 1) / 2, 2, x2, u2);
   }
-  if (k < P.ns)
+  float u[2][3];
+  fold_halves(u2, u);
+  lane_sum2(u, 2);
+  if (act && sl == 0)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) P.chk32[(size_t)b * 3 * P.ns + 3 * k + q] = u[q];
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) P.chk32[(size_t)b * 3 * P.ns + 3 * (k0 + t) + q] = u[t][q];
 }
 
-// M2M: one CTA per box of one depth with children; thread k = check point;
-// the children's upward densities staged in batches, in this box's frame.
+// M2M: one CTA per box of one depth with children; threads 2c, 2c + 1 take
+// check points 2c, 2c + 1 (every other staged pair each); the children's
+// upward densities staged in batches, in this box's frame.
 __global__ void k_fast_m2m(Pass P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ EqSrc src[8];
-  EqStage *E = reinterpret_cast<EqStage *>(smem);  // [min(8, neq) ns]
+  float4 *E = reinterpret_cast<float4 *>(smem);  // kEqFields planes of cap pairs
   const int32_t b = P.box0 + blockIdx.x;
   const int32_t c0 = P.t.child_ptr[b], c1 = P.t.child_ptr[b + 1];
   if (c0 >= c1) return;
@@ -380,11 +469,13 @@ __global__ void k_fast_m2m(Pass P) {
     return;
   }
   const int nch = c1 - c0, neq = min(8, eq_batch_boxes(P.ns));
-  const int k = threadIdx.x;
+  const int cap = (neq * P.ns + 1) / 2;
+  const int k0 = threadIdx.x & ~1, sl = threadIdx.x & 1;
+  const bool act = k0 + 1 < P.ns;
   const float r = half_width(P.t, P.depth);
   const float rad = (float)(kOuter * (double)r), rc = (float)(kInner * (double)r / 2);
-  if (k < nch) {
-    const int32_t ch = c0 + k;
+  if ((int)threadIdx.x < nch) {
+    const int32_t ch = c0 + threadIdx.x;
     EqSrc e;
     if (in_range(P, ch, P.t.nbox)) {
       e.dens = P.up32 + (size_t)ch * P.nc * P.ns;
@@ -394,28 +485,44 @@ __global__ void k_fast_m2m(Pass P) {
     } else {
       e = eq_none(P);
     }
-    src[k] = e;
+    src[threadIdx.x] = e;
   }
-  float x[3] = {0.f, 0.f, 0.f}, uf[3] = {0.f, 0.f, 0.f}, uq[3] = {0.f, 0.f, 0.f};
-  if (k < P.ns)
+  float x[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  if (act)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) x[q] = rad * P.surf32[3 * k + q];
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) x[t][q] = rad * P.surf32[3 * (k0 + t) + q];
+  float2 x2[2][3], uf[2][3], uq[2][3];
+  dup_targets(x, x2);
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) uf[t][q] = uq[t][q] = make_float2(0.f, 0.f);
   for (int e0 = 0; e0 < nch; e0 += neq) {
     const int nb = min(neq, nch - e0);
     __syncthreads();
-    stage_eq_batch(P, E, src + e0, nb);
+    stage_eq_pairs(P, E, cap, src + e0, nb);
     __syncthreads();
-    if (k < P.ns) {
-      if (P.nc == 4) eval_equiv_acc<true>(E, 0, nb * P.ns, 1, x[0], x[1], x[2], uf, uq);
-      else eval_equiv_acc<false>(E, 0, nb * P.ns, 1, x[0], x[1], x[2], uf, uq);
+    if (act) {
+      if (P.nc == 4) eval_eq_pairs<true>(E, cap, sl, (nb * P.ns + 1) / 2, 2, x2, uf, uq);
+      else eval_eq_pairs<false>(E, cap, sl, (nb * P.ns + 1) / 2, 2, x2, uf, uq);
     }
   }
-  if (k < P.ns) {
-    const float csl = (float)P.csl, csrc = (float)P.csrc;
+  float a1[2][3], a2[2][3], u[2][3];
+  fold_halves(uf, a1);
+  fold_halves(uq, a2);
+  const float csl = (float)P.csl, csrc = (float)P.csrc;
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
-      P.chk32[(size_t)b * 3 * P.ns + 3 * k + q] = csl * uf[q] + csrc * uq[q];
-  }
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) u[t][q] = csl * a1[t][q] + csrc * a2[t][q];
+  lane_sum2(u, 2);
+  if (act && sl == 0)
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) P.chk32[(size_t)b * 3 * P.ns + 3 * (k0 + t) + q] = u[t][q];
 }
 
 // Check-to-equivalent products of a tile of NB boxes of one depth:
@@ -739,11 +846,14 @@ static_assert(kTcChunks % 2 == 0, "two octant halves per direction");
 __global__ void k_fast_btab(Pass P, int64_t n) {
   const int m = 3 * P.nc * 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // e runs over the table in its own order (coalesced stores): float pos of
+  // row nn of tile wc holds k = ((pos / 4) ^ (nn mod 8)) 4 + pos mod 4
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
     const int64_t wc = e / (kTcCols * kTcK);
     const int r = (int)(e % (kTcCols * kTcK));
     const int w = (int)(wc / kTcChunks), ch = (int)(wc % kTcChunks);
-    const int nn = r / kTcK, k = r % kTcK;
+    const int nn = r / kTcK, pos = r % kTcK;
+    const int k = ((((pos >> 2) ^ (nn & 7)) & 7) << 2) | (pos & 3);
     const int t = nn / 6, q = (nn >> 1) % 3, rn = nn & 1;
     const int sl = 4 * (ch & 1) + (k >> 3), c = (k >> 1) & 3, rk = k & 1;
     const int dd = ch >> 1, dir = dd < 13 ? dd : dd + 1;
@@ -757,10 +867,9 @@ __global__ void k_fast_btab(Pass P, int64_t n) {
       val = (rk == rn) ? K[0] : (rk == 0 ? K[1] : -K[1]);
     }
     const float hi = tf32_rna(val), lo = tf32_rna(val - hi);
-    float *o = P.btab + (size_t)wc * 2 * kTcCols * kTcK;
-    const uint32_t off = sw128_off(nn, k) >> 2;
-    o[off] = hi;
-    o[kTcCols * kTcK + off] = lo;
+    float *o = P.btab + (size_t)wc * 2 * kTcCols * kTcK + (size_t)nn * kTcK + pos;
+    o[0] = hi;  // sw128_off(nn, k) / 4 == nn kTcK + pos
+    o[kTcCols * kTcK] = lo;
   }
 }
 
@@ -999,7 +1108,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_fast_kmulp_tc(
 // Work items of the L2T (leaf points against the leaf's downward density and
 // its W-list boxes' upward densities): a block of pb points (a power of two,
 // 8 <= pb <= 256) against all of the leaf's sources, S = 256 / pb threads per
-// point (adjacent lanes, each taking every S-th staged source, summed by
+// point (adjacent lanes, each taking every S-th staged source pair, summed by
 // shuffles in a fixed order).  pb is the largest with pb x sources <=
 // kItemWork (and no larger than the points need), so that a leaf with a long
 // W-list is spread over many CTAs; every point is evaluated by one item,
@@ -1046,38 +1155,36 @@ __global__ void k_fast_item_expand(Pass P) {
   }
 }
 
-// Sums u over the S adjacent lanes of a target (S a power of two <= 32).
-__device__ __forceinline__ void lane_sum(float u[3], int S) {
-  for (int o = 1; o < S; o <<= 1)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) u[q] += __shfl_xor_sync(kFull, u[q], o);
-}
-
-// DCHK: one CTA per box of one depth, thread k = downward check point:
-// M2L (spectral result, or dense over the V-list in batches of boxes), X-list
-// sources (one leaf at a time, in this box's frame), L2L.  Offsets of source
-// boxes are computed once per box, by one thread.
+// DCHK: one CTA per box of one depth; threads 2c, 2c + 1 take downward check
+// points 2c, 2c + 1 (every other staged pair each): M2L (spectral result, or
+// dense over the V-list in batches of boxes), X-list sources (one leaf at a
+// time, in this box's frame), L2L.  Offsets of source boxes are computed once
+// per box, by one thread.
 __global__ void k_fast_dchk(Pass P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ EqSrc src[kEqBatchMax];
   __shared__ float xoff[3];
   const int neq = eq_batch_boxes(P.ns);
-  EqStage *E = reinterpret_cast<EqStage *>(smem);                                  // [neq ns]
-  SrcStage *S = reinterpret_cast<SrcStage *>(smem + sizeof(EqStage) * neq * P.ns);  // [blockDim]
+  const int cap = (neq * P.ns + 1) / 2, scap = blockDim.x;
+  float4 *E = reinterpret_cast<float4 *>(smem);  // kEqFields planes of cap pairs
+  float4 *S = E + (size_t)kEqFields * cap;       // kSrcFields planes of scap pairs
   const int32_t b = P.box0 + blockIdx.x;
-  const int k = threadIdx.x;
-  const bool act = k < P.ns;
+  const int k0 = threadIdx.x & ~1, sl = threadIdx.x & 1;
+  const bool act = k0 + 1 < P.ns;  // ns is even
   const float r = half_width(P.t, P.depth);
   const float rad = (float)(kInner * (double)r);
-  float xs[3] = {0.f, 0.f, 0.f}, u[3] = {0.f, 0.f, 0.f};
-  float uf[3] = {0.f, 0.f, 0.f}, uq[3] = {0.f, 0.f, 0.f};
-  if (act) {
+  float xs[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  if (act)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) xs[q] = rad * P.surf32[3 * k + q];
-    if (P.spec)
+    for (int t = 0; t < 2; ++t)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) u[q] = P.m2l32[((size_t)b * 3 + q) * P.ns + k];
-  }
+      for (int q = 0; q < 3; ++q) xs[t][q] = rad * P.surf32[3 * (k0 + t) + q];
+  float2 x2[2][3], u2[2][3], uf[2][3], uq[2][3];
+  dup_targets(xs, x2);
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) u2[t][q] = uf[t][q] = uq[t][q] = make_float2(0.f, 0.f);
   // equivalent sources: the dense V-list (no spectra) and the parent (L2L)
   const int32_t v0 = P.spec ? 0 : P.t.v_ptr[b], v1 = P.spec ? 0 : P.t.v_ptr[b + 1];
   const int nl2l = P.depth > kFirstDepth ? 1 : 0;
@@ -1085,8 +1192,8 @@ __global__ void k_fast_dchk(Pass P) {
   for (int e0 = 0; e0 < neqs; e0 += neq) {
     const int nb = min(neq, neqs - e0);
     __syncthreads();
-    if (k < nb) {
-      const int e = e0 + k;
+    if ((int)threadIdx.x < nb) {
+      const int e = e0 + threadIdx.x;
       EqSrc q;
       if (e < v1 - v0) {
         const int32_t a = P.t.v_idx[v0 + e];
@@ -1109,16 +1216,17 @@ __global__ void k_fast_dchk(Pass P) {
           q = eq_none(P);
         }
       }
-      src[k] = q;
+      src[threadIdx.x] = q;
     }
     __syncthreads();
-    stage_eq_batch(P, E, src, nb);
+    stage_eq_pairs(P, E, cap, src, nb);
     __syncthreads();
     if (act) {
-      if (P.nc == 4) eval_equiv_acc<true>(E, 0, nb * P.ns, 1, xs[0], xs[1], xs[2], uf, uq);
-      else eval_equiv_acc<false>(E, 0, nb * P.ns, 1, xs[0], xs[1], xs[2], uf, uq);
+      if (P.nc == 4) eval_eq_pairs<true>(E, cap, sl, (nb * P.ns + 1) / 2, 2, x2, uf, uq);
+      else eval_eq_pairs<false>(E, cap, sl, (nb * P.ns + 1) / 2, 2, x2, uf, uq);
     }
   }
+  const int chunk = 2 * (int)blockDim.x;
   for (int32_t v = P.t.x_ptr[b]; v < P.t.x_ptr[b + 1]; ++v) {  // X-list sources
     const int32_t a = P.t.x_idx[v];
     if (!in_range(P, a, P.t.nbox)) continue;
@@ -1128,36 +1236,55 @@ __global__ void k_fast_dchk(Pass P) {
     const int64_t i0 = P.t.leaf_ptr[l], i1 = P.t.leaf_ptr[l + 1];
     if (!in_range(P, i0, P.n + 1) || !in_range(P, i1, P.n + 1)) continue;
     __syncthreads();
-    if (k == 0) offset_f(P.t, b, P.depth, a, P.t.depth[a], xoff);
+    if (threadIdx.x == 0) offset_f(P.t, b, P.depth, a, P.t.depth[a], xoff);
     __syncthreads();
-    const float o0 = xoff[0], o1 = xoff[1], o2 = xoff[2];
-    for (int64_t c0 = i0; c0 < i1; c0 += blockDim.x) {
-      const int n = (int)min((int64_t)blockDim.x, i1 - c0);
+    float2 xo[2][3];
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) xo[t][q] = p_dup(xoff[q] + xs[t][q]);
+    for (int64_t c0 = i0; c0 < i1; c0 += chunk) {
+      const int n = (int)min((int64_t)chunk, i1 - c0);
       __syncthreads();
-      stage_points(P, S, c0, n);
+      stage_point_pairs(P, S, scap, c0, n);
       __syncthreads();
-      if (act) eval_sources_any(P, S, 0, n, 1, o0 + xs[0], o1 + xs[1], o2 + xs[2], u);
+      if (act) eval_src_pairs_any(P, S, scap, sl, (n + 1) / 2, 2, xo, u2);
     }
   }
-  if (act) {
-    const float csl = (float)P.csl, csrc = (float)P.csrc;
+  float a0[2][3], a1[2][3], a2[2][3], u[2][3];
+  fold_halves(u2, a0);
+  fold_halves(uf, a1);
+  fold_halves(uq, a2);
+  const float csl = (float)P.csl, csrc = (float)P.csrc;
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
-      P.chk32[(size_t)b * 3 * P.ns + 3 * k + q] = u[q] + csl * uf[q] + csrc * uq[q];
-  }
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) u[t][q] = a0[t][q] + csl * a1[t][q] + csrc * a2[t][q];
+  lane_sum2(u, 2);
+  if (act && sl == 0)
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int k = k0 + t;
+        const float m2l = P.spec ? P.m2l32[((size_t)b * 3 + q) * P.ns + k] : 0.f;
+        P.chk32[(size_t)b * 3 * P.ns + 3 * k + q] = m2l + u[t][q];
+      }
 }
 
-// L2T + W-list: items of the leaves (k_fast_item_counts), thread = (point,
-// lane of S); the leaf's downward density and its W-list boxes' upward
-// densities are staged in batches in the leaf's frame.
+// L2T + W-list: items of the leaves (k_fast_item_counts); a thread takes one
+// point and every S-th staged source pair (S adjacent lanes per point); the
+// leaf's downward density and its W-list boxes' upward densities are staged
+// in batches in the leaf's frame.
 __global__ void __launch_bounds__(kItemThreads) k_fast_l2t(Pass P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ EqSrc src[kEqBatchMax];
   const int neq = eq_batch_boxes(P.ns);
-  EqStage *E = reinterpret_cast<EqStage *>(smem);  // [neq ns]
-  const int32_t it0 = 0, it1 = P.ioff[P.t.nleaf];
+  const int cap = (neq * P.ns + 1) / 2;
+  float4 *E = reinterpret_cast<float4 *>(smem);  // kEqFields planes of cap pairs
+  const int32_t it1 = P.ioff[P.t.nleaf];
   const float csl = (float)P.csl, csrc = (float)P.csrc;
-  for (int32_t it = it0 + blockIdx.x; it < it1; it += gridDim.x) {
+  for (int32_t it = blockIdx.x; it < it1; it += gridDim.x) {
     const int2 item = make_int2(P.items[2 * (size_t)it], P.items[2 * (size_t)it + 1]);
     const int32_t l = item.x;
     if (l < 0 || l >= P.t.nleaf) {  // uniform over the CTA
@@ -1177,10 +1304,12 @@ __global__ void __launch_bounds__(kItemThreads) k_fast_l2t(Pass P) {
     const int32_t w0 = P.t.w_ptr[b], w1 = P.t.w_ptr[b + 1];
     const int ndn = d >= kFirstDepth ? 1 : 0;
     const int neqs = ndn + (w1 - w0);
-    float x[3] = {0.f, 0.f, 0.f}, uf[3] = {0.f, 0.f, 0.f}, uq[3] = {0.f, 0.f, 0.f};
-    if (act)
+    float2 x2[1][3], uf[1][3], uq[1][3];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) x[q] = P.ploc[3 * e + q];
+    for (int q = 0; q < 3; ++q) {
+      x2[0][q] = p_dup(act ? P.ploc[3 * e + q] : 0.f);
+      uf[0][q] = uq[0][q] = make_float2(0.f, 0.f);
+    }
     for (int e0 = 0; e0 < neqs; e0 += neq) {
       const int nb = min(neq, neqs - e0);
       __syncthreads();
@@ -1207,17 +1336,19 @@ __global__ void __launch_bounds__(kItemThreads) k_fast_l2t(Pass P) {
         src[threadIdx.x] = q;
       }
       __syncthreads();
-      stage_eq_batch(P, E, src, nb);
+      stage_eq_pairs(P, E, cap, src, nb);
       __syncthreads();
       if (act) {
-        if (P.nc == 4) eval_equiv_acc<true>(E, sl, nb * P.ns, sw, x[0], x[1], x[2], uf, uq);
-        else eval_equiv_acc<false>(E, sl, nb * P.ns, sw, x[0], x[1], x[2], uf, uq);
+        if (P.nc == 4) eval_eq_pairs<true, 1>(E, cap, sl, (nb * P.ns + 1) / 2, sw, x2, uf, uq);
+        else eval_eq_pairs<false, 1>(E, cap, sl, (nb * P.ns + 1) / 2, sw, x2, uf, uq);
       }
     }
     float u[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) u[q] = csl * uf[q] + csrc * uq[q];
-    lane_sum(u, sw);
+    for (int q = 0; q < 3; ++q) {
+      u[q] = csl * (uf[0][q].x + uf[0][q].y) + csrc * (uq[0][q].x + uq[0][q].y);
+      for (int o = 1; o < sw; o <<= 1) u[q] += __shfl_xor_sync(kFull, u[q], o);
+    }
     if (act && sl == 0) {
       double *out = P.out + 3 * e;
 #pragma unroll
@@ -1332,7 +1463,7 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
     post();
   }
   pre("s2m");
-  k_fast_s2m<<<P.t.nleaf, bt, sizeof(SrcStage) * bt, st>>>(P);
+  k_fast_s2m<<<P.t.nleaf, bt, sizeof(float4) * kSrcFields * bt, st>>>(P);
   post();
   for (int32_t d = max_depth; d >= kFirstDepth; --d) {
     P.depth = d;
@@ -1342,7 +1473,9 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
     if (nb <= 0) continue;
     if (d < max_depth) {
       pre("m2m");
-      k_fast_m2m<<<nb, bt, sizeof(EqStage) * std::min(8, eq_batch_boxes(ns)) * ns, st>>>(P);
+      k_fast_m2m<<<nb, bt,
+                   sizeof(float4) * kEqFields * ((std::min(8, eq_batch_boxes(ns)) * ns + 1) / 2),
+                   st>>>(P);
       post();
     }
     pre("uc2e");
@@ -1394,7 +1527,10 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
       post();
     }
     pre("dchk");
-    k_fast_dchk<<<nb, bt, sizeof(EqStage) * eq_batch_boxes(ns) * ns + sizeof(SrcStage) * bt, st>>>(P);
+    k_fast_dchk<<<nb, bt,
+                  sizeof(float4) * (kEqFields * ((eq_batch_boxes(ns) * ns + 1) / 2) +
+                                    kSrcFields * bt),
+                  st>>>(P);
     post();
     pre("dc2e");
     launch_c2e<false>(P, nb, ns, st);
@@ -1404,7 +1540,8 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
   {
     const int64_t bound = (int64_t)P.t.nleaf + (P.n + 7) / 8;
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(bound, (int64_t)sms * 8));
-    k_fast_l2t<<<g, kItemThreads, sizeof(EqStage) * eq_batch_boxes(ns) * ns, st>>>(P);
+    k_fast_l2t<<<g, kItemThreads,
+                 sizeof(float4) * kEqFields * ((eq_batch_boxes(ns) * ns + 1) / 2), st>>>(P);
   }
   post();
   return err;

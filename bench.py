@@ -21,6 +21,7 @@ balanced by pair count, a one-off halo, one all_gather per step.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -149,6 +150,72 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(loaded) if loaded else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm), "samples_under_load": len([u for u in util if u >= 50])}
+
+
+class NvmlClocks:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    libnvidia-ml, read-only queries) inside the timed region, right after each
+    step is queued, while the GPU has work: the samples the 100 ms nvidia-smi
+    poll misses when the whole timed region lasts a few tens of milliseconds."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device):
+        self.ok, self.sm, self.reasons, self.max = False, [], set(), None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return
+        if lib.nvmlInit_v2() != 0:
+            return
+        h = ctypes.c_void_p()
+        found = False
+        try:  # the CUDA device by PCI bus id (NVML may number the GPUs differently)
+            import torch
+            pr = torch.cuda.get_device_properties(device)
+            bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+            found = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) == 0
+        except (AttributeError, RuntimeError):
+            found = False
+        if not found and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(0), ctypes.byref(h)) != 0:
+            return
+        self.lib, self.h = lib, h
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) == 0:
+            self.max = mx.value
+        self.reason_fn = (getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or
+                          getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None))
+        self.ok = True
+
+    def sample(self, busy: bool):
+        if not self.ok or not busy:
+            return
+        c = ctypes.c_uint()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, ctypes.c_int(1), ctypes.byref(c)) == 0:
+            self.sm.append(c.value)
+        if self.reason_fn is not None:
+            r = ctypes.c_ulonglong()
+            if self.reason_fn(self.h, ctypes.byref(r)) == 0:
+                for bit, name in self.REASONS.items():
+                    if r.value & bit:
+                        self.reasons.add(name)
+
+    def merge(self, clocks: dict) -> dict:
+        """The nvidia-smi record with the in-region NVML samples: the SM clock
+        becomes their median, the reasons the union."""
+        if not self.ok or not self.sm:
+            return clocks
+        out = dict(clocks)
+        out["sm_mhz"] = float(statistics.median(self.sm))
+        if self.max:
+            out["sm_max_mhz"] = float(self.max)
+        out["reasons"] = sorted(set(clocks.get("reasons") or []) | self.reasons)
+        out["nvml_samples_in_region"] = len(self.sm)
+        out["nvml_sm_mhz_min"] = float(min(self.sm))
+        out["source"] = ("NVML after each step was queued (GPU busy), reasons from NVML and "
+                         "nvidia-smi")
+        return out
 
 
 def oracle_sample(wl, targets):
@@ -709,6 +776,7 @@ def run_sharded(args, rank, world, local_rank):
           for _ in range(K)]
     dist.barrier()
     from paper_1909_11085_gb300 import _abi as A
+    nvml = NvmlClocks(dev)
     sampler = ClockSampler(local_rank)
     sampler.start()
     time.sleep(0.3)
@@ -719,9 +787,10 @@ def run_sharded(args, rank, world, local_rank):
         ev[i][0].record(stream)
         full = sp.step()
         ev[i][1].record(stream)
+        nvml.sample(not stream.query())
     torch.cuda.synchronize()
     launches = A.lib().stokes_launch_count() - launches0
-    clocks = sampler.stop()
+    clocks = nvml.merge(sampler.stop())
     dist.barrier()
     bufs["plan"].device_status()
     tot = torch.tensor([sum(a.elapsed_time(b) for a, b in ev) / 1e3], dtype=torch.float64,
@@ -839,6 +908,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     peaks = run_peaks(dev, stream) if not args.no_peaks else None
+    nvml = NvmlClocks(dev)
     sampler = ClockSampler(local_rank)
     sampler.start()
     time.sleep(0.3)
@@ -851,11 +921,12 @@ def run_ours(args, rank, world, local_rank):
         L.stokes_set_engine_events(eng[i][0].cuda_event, eng[i][1].cuda_event)
         step()
         ev[i][1].record(stream)
+        nvml.sample(not stream.query())
     L.stokes_set_engine_events(None, None)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = L.stokes_launch_count() - launches0
-    clocks = sampler.stop()
+    clocks = nvml.merge(sampler.stop())
     if world > 1:
         dist.barrier()
     plan.device_status()

@@ -77,6 +77,13 @@ void stokes_default_opts(stk_opts *opts);
  * src [ns][3], trg [nt][3]; f, phi, nrm [ns][3]; w [ns]; h [ns] local spacing
  * (may be NULL: then only exactly coincident pairs take the FP64 path).
  * Targets may alias the sources.  ns, nt in [0, 2^31 - 1].
+ * In the mixed form with the default options (source_splits = 0,
+ * tile_config = -1), a sum of at most 2^26 target-source pairs runs as one
+ * launch over blocks of 256 targets x source splits (no sort, no work items,
+ * near pairs queued per warp and evaluated in FP64 in the same launch, the
+ * last split of a target block adding the splits in order; it has no device
+ * waits, so its workspace's status word stays 0); larger sums and any other
+ * options take the work-item engine.  Both meet the same accuracy.
  */
 stk_status stokes_sl_eval(const double *src, const double *f, const double *w, const double *h,
                           int64_t ns, const double *trg, int64_t nt, double mu, double *out,

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstokesgpu.so")
 SOURCES = ["stokes_abi.cu", "engine_mixed.cu", "engine_fp64.cu", "prep.cu", "noalloc.cu",
-           "adjoint.cu", "near.cu", "checkpoint.cu",
+           "adjoint.cu", "near.cu", "checkpoint.cu", "direct_small.cu",
            "nearzone.cu", "fmm_ops.cu", "fmm.cu", "fmm_fast.cu", "tc_gemm.cu", "octree.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -138,7 +138,10 @@ extern "C" stk_status stokes_sl_eval_noalloc(const double *src, const double *f,
   stk_status s = scratch_address(&scratch, true);
   if (s != STK_OK) return s;
   // Use the requested source splits, or fewer until the workspace fits the buffer.
+  // The default work-item shape is named explicitly: this entry point keeps the
+  // engine form (bounded waits, device status) at every size.
   stk_opts o = *opts;
+  if (o.tile_config < 0) o.tile_config = 0;
   size_t need = 0;
   s = stokes_direct_workspace_size(ns < 0 ? 0 : ns, nt < 0 ? 0 : nt, 1, &o, &need);
   if (s != STK_OK) return s;

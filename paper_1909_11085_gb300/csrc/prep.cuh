@@ -39,6 +39,17 @@ void launch_bucket_order(int64_t n, const uint64_t *keys, const int32_t *vals, i
                          int32_t *off, int32_t *rank, int32_t *order, cudaStream_t st);
 // Near pairs of the mixed engine's items (near.cu); runs after the engine.
 void launch_near(const EngineParams &P, int sms, int64_t max_items, cudaStream_t st);
+// Small direct sums (direct_small.cu): one launch over blocks of targets x
+// source splits writing part[split][target][3]; the last split of each block
+// (counter blocks[block], zero before the launch and left zero) writes out.
+constexpr int64_t kSmallPairs = (int64_t)1 << 26;  // targets x sources taking this form
+int64_t direct_small_blocks(int64_t nt);
+int direct_small_splits(int64_t ns, int64_t nt, int sms);
+cudaError_t launch_direct_small(int kinds, const double *src, const double *f, const double *nrm,
+                                const double *phi, const double *w, const double *h, int64_t ns,
+                                const double *trg, int64_t nt, double alpha, double csl,
+                                double cdl, int32_t nsplit, int32_t accumulate, double *part,
+                                int32_t *blocks, double *out, cudaStream_t st);
 void launch_finish(int64_t nt, int32_t nparts, const double *part_out, const int32_t *tperm,
                    int32_t accumulate, double *out, cudaStream_t st);
 void launch_zero_ints(int32_t *p, int n, cudaStream_t st);

@@ -112,6 +112,7 @@ struct Plan {
   int32_t nseg_ranges = 0;  // entries of range_ptr minus one
   bool sort_targets = false;
   bool sort_items = false;
+  bool small = false;  // the one-launch small direct form (direct_small.cu)
   int32_t ngroup = 0;
   // offsets (the counters always sit at offset 0 of the aligned workspace)
   size_t counters, rec, keys_a, keys_b, vals_a, vals_b, ikeys_a, ikeys_b, ivals_a, ivals_b, hist,
@@ -138,6 +139,12 @@ int auto_splits(int64_t nt, int64_t ns, const DevInfo &di, int occ) {
 void layout(Plan &p) {
   Alloc a;
   p.counters = a.take(sizeof(int32_t) * 4);
+  if (p.small) {  // partial results per source split and a counter per target block
+    p.cnt = a.take(sizeof(int32_t) * (size_t)direct_small_blocks(p.nt));
+    p.part = a.take(sizeof(double) * 3 * (size_t)p.nt * (size_t)p.nsplit);
+    p.total = a.off + 256;
+    return;
+  }
   p.rec = a.take((size_t)p.ns * (p.mixed ? sizeof(SrcRec) : sizeof(SrcRec64)));
   const int64_t nsort = p.sort_targets ? p.nt : 0;
   const int64_t nitem = p.sort_items ? p.max_items : 0;
@@ -177,6 +184,14 @@ stk_status plan_direct(int64_t ns, int64_t nt, const stk_opts *o, Plan &p) {
   p.tile = tile_config(o->tile_config < 0 ? 0 : o->tile_config);
   p.ns = ns;
   p.nt = nt;
+  // small mixed sums with the default options: one launch and the finish
+  if (p.mixed && o->source_splits == 0 && o->tile_config < 0 && ns > 0 && nt > 0 &&
+      (double)ns * (double)nt <= (double)kSmallPairs) {
+    p.small = true;
+    p.nsplit = direct_small_splits(ns, nt, di.sms);
+    layout(p);
+    return STK_OK;
+  }
   const int occ = p.mixed ? di.occ_mixed : di.occ_fp64;
   p.nsplit = o->source_splits > 0 ? o->source_splits : auto_splits(nt, ns, di, occ);
   if (p.nsplit > ns && ns > 0) p.nsplit = (int32_t)ns;
@@ -362,6 +377,17 @@ stk_status direct_common(int32_t kinds, const double *src, const double *f, cons
   if (s != STK_OK) return s;
   if (!workspace || wbytes < p.total) return fail(STK_ENOMEM, "workspace too small");
   void *ws = align_ws(workspace);
+  if (p.small) {
+    CU(cudaMemsetAsync(at<int32_t>(ws, p.counters), 0, sizeof(int32_t) * 4, st));
+    CU(cudaMemsetAsync(at<int32_t>(ws, p.cnt), 0,
+                       sizeof(int32_t) * (size_t)direct_small_blocks(nt), st));
+    const double csl = (kinds & K_SL) ? 1.0 / (8.0 * kPi * mu) : 0.0, cdl = 6.0 / (8.0 * kPi);
+    CU(launch_direct_small(kinds, src, (kinds & K_SL) ? f : nullptr, nrm,
+                           (kinds & K_DL) ? phi : nullptr, w, h, ns, trg, nt, o->near_ratio, csl,
+                           cdl, p.nsplit, o->accumulate ? 1 : 0, at<double>(ws, p.part),
+                           at<int32_t>(ws, p.cnt), out, st));
+    return STK_OK;
+  }
   launch_zero_ints(at<int32_t>(ws, p.counters), 4, st);
   s = pack(p, ws, src, (kinds & K_SL) ? f : nullptr, nrm, (kinds & K_DL) ? phi : nullptr, w, h,
            (kinds & K_SL) ? mu : 1.0, o->near_ratio, st);

@@ -63,7 +63,8 @@ def test_forced_expiry_on_the_direct_sum(lib):
     d = W.sl_direct_workload(ncell=3, box=20.0)
     src, f, w, h = cuda(d.src, d.f, d.w, d.h)
     n = d.src.shape[0]
-    o = A.make_opts("mixed")
+    # the work-item engine (named tile shape): the small one-launch form has no waits
+    o = A.make_opts("mixed", tile_config=0)
     nb = ctypes.c_size_t(0)
     L = A.lib()
     A.check(L.stokes_direct_workspace_size(n, n, 1, ctypes.byref(o), ctypes.byref(nb)))
@@ -92,3 +93,32 @@ def test_wait_policy_arguments_checked(lib):
     assert L.stokes_set_wait_policy(-1, 0) == A.STK_EINVAL
     assert L.stokes_set_wait_policy(0, 2) == A.STK_EINVAL
     A.check(L.stokes_set_wait_policy(0, 0))
+
+
+def test_small_direct_form_has_no_waits(lib):
+    """With the default options a small mixed direct sum runs as one launch
+    without device waits: a forced expiry leaves its status word at 0 and the
+    result at the oracle's."""
+    import torch
+    P, A = lib
+    d = W.sl_direct_workload(ncell=3, box=20.0)
+    src, f, w, h = cuda(d.src, d.f, d.w, d.h)
+    n = d.src.shape[0]
+    o = A.make_opts("mixed")
+    nb = ctypes.c_size_t(0)
+    L = A.lib()
+    A.check(L.stokes_direct_workspace_size(n, n, 1, ctypes.byref(o), ctypes.byref(nb)))
+    ws = A.workspace(nb.value, src.device)
+    out = torch.empty((n, 3), dtype=torch.float64, device=src.device)
+    A.check(L.stokes_set_wait_policy(0, 1))
+    try:
+        A.check(L.stokes_sl_eval(A.ptr(src), A.ptr(f), A.ptr(w), A.ptr(h), n, A.ptr(src), n, 1.0,
+                                 A.ptr(out), ctypes.byref(o), A.ptr(ws), ws.numel(),
+                                 A.stream_ptr(src.device)))
+    finally:
+        A.check(L.stokes_set_wait_policy(0, 0))
+    torch.cuda.synchronize()
+    A.check(L.stokes_device_status(A.ptr(ws), ws.numel()))
+    ref = oracle.sl(d.src, d.f, d.w, d.src, 1.0)
+    got = out.cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-6

@@ -528,28 +528,34 @@ __global__ void k_fast_m2m(Pass P) {
 // Check-to-equivalent products of a tile of NB boxes of one depth:
 // out[b][i] = (hi + lo)[i] . chk32[b] in double-FP32 arithmetic (the exact
 // FMA product and two-sum accumulation of apply_row_df), operator stored
-// column by column, read four columns ahead of their use.
+// column by column, read four columns ahead of their use; the boxes in pairs
+// on packed FP32 instructions (per half the same operations and roundings).
 template <bool UP, int NB>
 __global__ void __launch_bounds__(256) k_fast_c2e(Pass P) {
+  static_assert(NB % 2 == 0, "boxes in pairs");
   extern __shared__ __align__(16) unsigned char smem[];
-  float *X = reinterpret_cast<float *>(smem);  // [NB][cols]
+  float *X = reinterpret_cast<float *>(smem);  // [cols][NB]: a column's boxes adjacent
   const int cols = 3 * P.ns;
   const int rows = UP ? P.nc * P.ns : 3 * P.ns;
   const int32_t bt = P.box0 + blockIdx.x * NB;
   const int nbt = min(NB, P.box1 - bt);
   for (int e = threadIdx.x; e < NB * cols; e += blockDim.x) {
     const int bb = e / cols, j = e % cols;
-    X[e] = bb < nbt ? P.chk32[(size_t)(bt + bb) * cols + j] : 0.f;
+    X[j * NB + bb] = bb < nbt ? P.chk32[(size_t)(bt + bb) * cols + j] : 0.f;
   }
   __syncthreads();
   const size_t off = UP ? (size_t)(P.depth - kFirstDepth) * rows * cols
                         : (size_t)P.n_uc2e + (size_t)(P.depth - kFirstDepth) * rows * cols;
   const float *hi = P.ops_hi + off, *lo = P.ops_lo + off;
   float *out = UP ? P.up32 : P.dn32;
+  const float2 m1 = make_float2(-1.f, -1.f);
+  // a - b as one packed FMA: b (-1) + a, exact product, one rounding
+  auto sub2 = [&](float2 a2, float2 b2) { return p_fma(b2, m1, a2); };
   for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-    float sh[NB], sl[NB];
+    // packed over box pairs: per half the operations of the scalar double-FP32 form
+    float2 sh[NB / 2], sl[NB / 2];
 #pragma unroll
-    for (int bb = 0; bb < NB; ++bb) sh[bb] = sl[bb] = 0.f;
+    for (int h = 0; h < NB / 2; ++h) sh[h] = sl[h] = make_float2(0.f, 0.f);
     for (int j0 = 0; j0 < cols; j0 += 4) {
       float ah[4], al[4];
 #pragma unroll
@@ -561,22 +567,24 @@ __global__ void __launch_bounds__(256) k_fast_c2e(Pass P) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (j0 + q >= cols) break;
+        const float2 ah2 = p_dup(ah[q]), al2 = p_dup(al[q]);
+        const float2 *x2p = reinterpret_cast<const float2 *>(X + (j0 + q) * NB);
 #pragma unroll
-        for (int bb = 0; bb < NB; ++bb) {
-          const float x = X[bb * cols + j0 + q];
-          const float p = __fmul_rn(ah[q], x);
-          const float err = __fmaf_rn(al[q], x, __fmaf_rn(ah[q], x, -p));
-          const float t = __fadd_rn(sh[bb], p), bv = __fsub_rn(t, sh[bb]);
-          sl[bb] = __fadd_rn(sl[bb], __fadd_rn(__fadd_rn(__fsub_rn(sh[bb], __fsub_rn(t, bv)),
-                                                         __fsub_rn(p, bv)),
-                                               err));
-          sh[bb] = t;
+        for (int h = 0; h < NB / 2; ++h) {
+          const float2 x = x2p[h];
+          const float2 p = p_mul(ah2, x);
+          const float2 err = p_fma(al2, x, p_fma(ah2, x, p_mul(p, m1)));
+          const float2 t = p_add(sh[h], p), bv = sub2(t, sh[h]);
+          sl[h] = p_add(sl[h], p_add(p_add(sub2(sh[h], sub2(t, bv)), sub2(p, bv)), err));
+          sh[h] = t;
         }
       }
     }
 #pragma unroll
-    for (int bb = 0; bb < NB; ++bb)
-      if (bb < nbt) out[(size_t)(bt + bb) * rows + i] = __fadd_rn(sh[bb], sl[bb]);
+    for (int h = 0; h < NB / 2; ++h) {
+      if (2 * h < nbt) out[(size_t)(bt + 2 * h) * rows + i] = __fadd_rn(sh[h].x, sl[h].x);
+      if (2 * h + 1 < nbt) out[(size_t)(bt + 2 * h + 1) * rows + i] = __fadd_rn(sh[h].y, sl[h].y);
+    }
   }
 }
 
@@ -1362,7 +1370,7 @@ __global__ void __launch_bounds__(kItemThreads) k_fast_l2t(Pass P) {
 int box_threads(int ns) { return ((ns + 31) / 32) * 32; }
 
 // Check-to-equivalent products of the nb boxes of one depth: kFastTile boxes
-// per CTA, one operator row per thread.
+// per CTA, one operator row per thread (16 boxes per CTA measured slower).
 template <bool UP>
 void launch_c2e(const Pass &P, int32_t nb, int ns, cudaStream_t st) {
   const int rows = UP ? P.nc * ns : 3 * ns;

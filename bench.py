@@ -1138,6 +1138,63 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_only_form(args, dev, flush, stream):
+    """One of the other forms alone, at a size small enough for a full ncu
+    capture: the 4,352-point direct single layer (one-launch small form) and the
+    same sum on the work-item engine; 128 batched suspensions; the check-point
+    double layer on the 320-patch wall; the adjoint of SL + DL (34,816 points);
+    the P2P step of the --ncell / --wall-patches workload in FP64."""
+    import torch
+    import paper_1909_11085_gb300 as P
+    from synth import workloads as W
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    res = {}
+    if args.only == "direct":
+        c1 = W.sl_direct_workload()
+        src, f, w, h = T(c1.src), T(c1.f), T(c1.w), T(c1.h)
+        n1 = c1.src.shape[0]
+        res["small_form_ms"] = _time_ms(lambda: P.sl(src, f, w, None, c1.mu, h=h), stream, flush, 10)
+        # an explicit split count keeps the work-item engine
+        res["engine_ms"] = _time_ms(lambda: P.sl(src, f, w, None, c1.mu, h=h, source_splits=16),
+                                    stream, flush, 10)
+        res["pairs"] = n1 * (n1 - 1)
+    elif args.only == "batched":
+        c3 = W.batched_workload(nsusp=128)
+        pts, f, phi, nrm, w, h = (T(a) for a in (c3.pts, c3.f, c3.phi, c3.nrm, c3.w, c3.h))
+        plan = P.BatchedPlan(c3.pts.shape[0], c3.susp_ptr, c3.n_cell)
+        out = torch.empty((c3.pts.shape[0], 3), dtype=torch.float64, device=dev)
+        res["ms"] = _time_ms(lambda: plan(pts, f, phi, nrm, w, h, c3.mu, out), stream, flush, 5)
+        res["pairs"], res["points"] = c3.pairs(), int(c3.pts.shape[0])
+    elif args.only == "checkpoint":
+        c6 = W.checkpoint_wall_workload()
+        p6, R6, r6 = 4, 3.0 * c6.hc, c6.hc
+        x6, n6, phi6 = T(c6.pts), T(c6.nrm), T(c6.phi)
+        fp6, fn6, fw6, fh6 = T(c6.fine_pts), T(c6.fine_nrm), T(c6.fine_w), T(c6.fine_h)
+        plan6 = P.CheckpointPlan(c6.npatch, fp6, fn6, fw6, fh6, x6, x6, n6, R6, r6, p6, c6.q,
+                                 c6.eta, kernels=2)
+        out6 = torch.empty((c6.pts.shape[0], 3), dtype=torch.float64, device=dev)
+        res["ms"] = _time_ms(lambda: plan6(None, phi6, out=out6), stream, flush, 3)
+        res["pairs"] = c6.pairs(p6)
+    elif args.only == "adjoint":
+        c5, g5 = W.adjoint_workload()
+        src, f, nrm, phi, w, h, g = (T(a) for a in (c5.src, c5.f, c5.nrm, c5.phi, c5.w, c5.h, g5))
+
+        def fwd_bwd():
+            s_, f_, n_, p_ = (t.detach().requires_grad_(True) for t in (src, f, nrm, phi))
+            P.StokesLayerFn.apply(s_, f_, n_, p_, w, s_, c5.mu, h).backward(g)
+        res["ms_forward_backward"] = _time_ms(fwd_bwd, stream, flush, 3)
+        res["pairs_per_pass"] = c5.src.shape[0] * (c5.src.shape[0] - 1)
+    else:  # p2p in FP64
+        wl = W.p2p_workload(ncell=args.ncell, n_wall_patch=args.wall_patches)
+        t = wl.tree
+        plan = P.P2PPlan(wl.pts.shape[0], t.leaf_ptr, t.ulist_ptr, t.ulist_idx, 3, "fp64",
+                         NEAR_RATIO, dev)
+        a_ = tuple(T(a) for a in (wl.pts, wl.f, wl.phi, wl.nrm, wl.w, wl.h))
+        out = torch.empty((wl.pts.shape[0], 3), dtype=torch.float64, device=dev)
+        res["fp64_ms"] = _time_ms(lambda: plan(*a_, wl.mu, out), stream, flush, 2)
+    return res
+
+
 def run_only(args):
     """One form alone (see --only)."""
     import torch
@@ -1151,6 +1208,8 @@ def run_only(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     if args.only == "nearzone":
         res = run_nearzone(dev, flush, stream)
+    elif args.only in ("direct", "batched", "checkpoint", "adjoint", "p2p"):
+        res = run_only_form(args, dev, flush, stream)
     else:
         import paper_1909_11085_gb300 as P
         from synth import workloads as W
@@ -1188,10 +1247,13 @@ def main():
                     help="skip the near-pair threshold sweep (alpha = 1, 2, 4)")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip the measured FP32 / FP64 / MUFU pipe rates")
-    ap.add_argument("--only", choices=["fmm", "nearzone"], default=None,
+    ap.add_argument("--only", choices=["fmm", "nearzone", "direct", "batched", "checkpoint",
+                                       "adjoint", "p2p"], default=None,
                     help="run one form alone and print its JSON (profiling helper: small device "
                          "footprint): the FMM far field beside the near field of the --ncell / "
-                         "--wall-patches workload, or the near-zone search")
+                         "--wall-patches workload, the near-zone search, the small direct sum, "
+                         "128 batched suspensions, the check-point wall, the adjoint, or the "
+                         "FP64 P2P step")
     ap.add_argument("--shard", action="store_true",
                     help="split the one near-field step over the ranks (strong scaling: target "
                          "leaves by pair count, a one-off halo, an all_gather per step) instead "

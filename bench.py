@@ -250,6 +250,38 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
+def cpu_model() -> str:
+    """The host CPU's model as the kernel reports it (x86 "model name", or the
+    Arm implementer / part codes), for the CPU baseline's record."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model name"):
+        for line in info:
+            if line.split(":")[0].strip() == key:
+                return line.split(":", 1)[1].strip()
+    imp = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")]
+    part = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU part")]
+    if imp and part:
+        return f"Arm CPU implementer {imp[0]}, part {part[0]}"
+    return "unknown"
+
+
+def one_core_rate(wl, rng, targets: int = 200) -> float:
+    """The oracle on one thread over a small target sample (Gpair/s)."""
+    import oracle
+    tg = np.sort(rng.choice(wl.pts.shape[0], targets, replace=False))
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle_sample(wl, tg)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cpu_cores())
+    return sample_pairs(wl, tg) / dt / 1e9
+
+
 def timed_oracle(wl, seconds: float, rng):
     """Runs the oracle on a random target sample sized for about `seconds` of CPU time."""
     import oracle
@@ -723,6 +755,7 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(wl, pairs),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "cpu_model": cpu_model(),
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -1126,7 +1159,8 @@ def run_ours(args, rank, world, local_rank):
         err = lambda u: float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
         mx = lambda u: float(np.abs(u - ref).max() / np.abs(ref).max())
         result["cpu_baseline"] = {"value": sp / dt / 1e9, "unit": UNIT, "cores": cpu_cores(),
-                                  "kind": "oracle",
+                                  "kind": "oracle", "cpu_model": cpu_model(),
+                                  "one_core_value": one_core_rate(wl, rng),
                                   "sample": (f"all {tg.size} targets" if tg.size == wl.pts.shape[0]
                                              else f"{tg.size} random targets of {wl.pts.shape[0]}")
                                             + f" with all their U-list sources ({sp} pairs), "

@@ -286,30 +286,34 @@ __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the block's partials of one split are 3 x 256 contiguous doubles: each
+  // thread sums 6 of those values over the splits (from L2, written by the
+  // other CTAs before their fence; loads of 5 splits in flight), in split order
+  constexpr int kPer = 3 * kSmallBlock / kSmallThreads;
+  const int64_t v0 = 3 * tb, vend = 3 * min(tb + (int64_t)kSmallBlock, a.nt);
+  double sum[kPer];
 #pragma unroll
-  for (int k = 0; k < kSmallT; ++k) {
-    const int64_t t = t0 + 32 * k + lane;
-    if (!act[k]) continue;
-    // the splits' partials from L2 (written by other CTAs before their fence),
-    // eight splits' loads in flight at a time, added in split order
-    double sum[3] = {0.0, 0.0, 0.0};
-    for (int y0 = 0; y0 < a.nsplit; y0 += 8) {
-      double v[8][3];
+  for (int m = 0; m < kPer; ++m) sum[m] = 0.0;
+  for (int y0 = 0; y0 < a.nsplit; y0 += 5) {
+    double v[5][kPer];
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 5; ++i)
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
-          v[i][q] = y0 + i < a.nsplit
-                        ? __ldcg(a.part + ((size_t)(y0 + i) * (size_t)a.nt + (size_t)t) * 3 + q)
-                        : 0.0;
+      for (int m = 0; m < kPer; ++m) {
+        const int64_t e = v0 + tid + kSmallThreads * m;
+        v[i][m] = (y0 + i < a.nsplit && e < vend)
+                      ? __ldcg(a.part + (size_t)(y0 + i) * (size_t)a.nt * 3 + (size_t)e)
+                      : 0.0;
+      }
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 5; ++i)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) sum[q] += v[i][q];
-    }
-    double *out = a.out + 3 * t;
+      for (int m = 0; m < kPer; ++m) sum[m] += v[i][m];
+  }
 #pragma unroll
-    for (int q = 0; q < 3; ++q) out[q] = (a.accumulate ? out[q] : 0.0) + sum[q];
+  for (int m = 0; m < kPer; ++m) {
+    const int64_t e = v0 + tid + kSmallThreads * m;
+    if (e < vend) a.out[e] = (a.accumulate ? a.out[e] : 0.0) + sum[m];
   }
   if (tid == 0) a.blocks[blockIdx.x] = 0;  // ready for the next call
 }

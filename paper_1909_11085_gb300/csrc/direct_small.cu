@@ -6,20 +6,20 @@
 // Grid: blocks of 256 targets (two per thread, sharing every staged source) x
 // source splits.  A CTA stages its split's sources 128 at a time in shared
 // memory, two by two (eight float4 per pair, read as broadcasts): positions
-// hi/lo relative
-// to the CTA's origin (its first target), so that d = (x_h - y_h) + (x_l - y_l)
-// is accurate relative to |x - y| wherever the targets lie; q = w f / (8 pi mu)
-// and psi = 6 w phi / (8 pi) in FP32; (alpha h_j)^2.  A pair with
-// |r|^2 <= (alpha h_j)^2 (exactly coincident pairs included) takes the FP64
-// difference and 1/|r| (near_contrib): each warp queues them in shared memory
-// and evaluates them 32 at a time, one per lane, since GB300's FP64 pipe is
-// only fed efficiently by full warps; the values are added per target in
-// queue order (deterministic).  The FP32 pairs run packed (two staged sources
-// per instruction).  Each thread sums a tile of 128 sources in FP32 and
-// two-sums the tile into (hi, lo); the split's partial goes to
-// part[split][target], and the last split of a target block to finish (a
-// counter per block) adds the splits in order and writes out (deterministic,
-// no second launch and no waiting).
+// hi/lo relative to the CTA's origin (its first target), so that
+// d = (x_h - y_h) + (x_l - y_l) is accurate relative to |x - y| wherever the
+// targets lie; q = w f / (8 pi mu) and psi = 6 w phi / (8 pi) in FP32;
+// (alpha h_j)^2.  A pair with |r|^2 <= (alpha h_j)^2 (exactly coincident
+// pairs included) takes the FP64 difference and 1/|r| (near_contrib): each
+// warp queues them in shared memory and evaluates them 32 at a time, one per
+// lane, since GB300's FP64 pipe is only fed efficiently by full warps; the
+// values of one target are added in queue order (deterministic).  The FP32
+// pairs run packed (two staged sources per instruction).  Each thread sums a
+// tile of 128 sources in FP32 and two-sums the tile into (hi, lo); the
+// split's (hi, lo) goes to part[split][target], and the last split of a
+// target block to finish (a counter per block) adds the splits in order
+// (FP32 two-sum, one conversion to FP64 at the end) and writes out
+// (deterministic, no second launch and no waiting).
 #include "common.cuh"
 #include "prep.cuh"
 
@@ -35,7 +35,7 @@ struct SmallArgs {
   double alpha, csl, cdl;
   int32_t nsplit;
   int32_t accumulate;
-  double *part;     // [nsplit][nt][3]
+  float2 *part;     // [nsplit][nt][3]: a split's compensated sum (hi, lo)
   int32_t *blocks;  // per target block: splits done (zero before the launch)
   double *out;      // [nt][3]
 };
@@ -102,60 +102,76 @@ __device__ __forceinline__ void small_pair(const float4 (&s)[kSmallFields], cons
 
 constexpr int kSmallQueue = 256;  // near pairs queued per warp (>= 128 free before a pair)
 
+// A warp's shared scratch for evaluating its queued near pairs.
+struct SmallNear {
+  int32_t queue[kSmallQueue];  // source within the staged tile | target slot << 8
+  float val[32][3];            // one round's values, by lane
+  float tot[32 * kSmallT][3];  // one round's sums, by target slot (zero between rounds)
+};
+
 // Evaluates a warp's queued near pairs, one per lane, with the FP64
-// difference and 1/|r| (near_contrib), and adds each value to its target's
-// near sum (un, held by the owner lane) in queue order: deterministic.
-// Entry: source within the staged tile | target slot (lane + 32 k) << 8.
+// difference and 1/|r| (near_contrib), and adds them to the near sums un of
+// the lanes owning their targets.  In each round the lanes of one target
+// (found with match_any) are summed in queue order by the group's first lane;
+// the owner then adds the round's sum: the order is fixed, so the result is
+// deterministic.  t0: the warp's first target (slot s is target t0 + s).
 template <int KIND>
-__device__ __forceinline__ void small_flush(const int32_t *queue, int qn,
+__device__ __forceinline__ void small_flush(SmallNear &sn, int qn,
                                             const float4 (*S)[kSmallFields], const double *src,
-                                            int64_t c0, int lane, const double (&x64)[kSmallT][3],
+                                            const double *trg, int64_t c0, int64_t t0, int lane,
                                             float (&un)[kSmallT][3]) {
   for (int e0 = 0; e0 < qn; e0 += 32) {
     const int e = e0 + lane;
-    const int32_t ent = e < qn ? queue[e] : 0;
-    const int j = ent & 0xff, slot = ent >> 8, owner = slot & 31, k = slot >> 5;
-    double x[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const double a0 = __shfl_sync(kFull, x64[0][q], owner);
-      const double a1 = __shfl_sync(kFull, x64[1][q], owner);
-      x[q] = k ? a1 : a0;
-    }
+    int slot = -1 - lane;  // idle lanes: keys of their own
     float c[3] = {0.f, 0.f, 0.f};
     if (e < qn) {
+      const int32_t ent = sn.queue[e];
+      const int j = ent & 0xff;
+      slot = ent >> 8;
       const float *F = reinterpret_cast<const float *>(S[j >> 1]);
       const int h = j & 1;
       const float4 qq = make_float4(F[14 + h], F[16 + h], F[18 + h], 0.f);
       const float4 nn = make_float4(F[20 + h], F[22 + h], F[24 + h], 0.f);
       const float4 pp = make_float4(F[26 + h], F[28 + h], F[30 + h], 0.f);
-      if (!near_contrib(x, src + 3 * (c0 + j), qq, nn, pp, KIND, c)) c[0] = c[1] = c[2] = 0.f;
+      if (!near_contrib(trg + 3 * (t0 + slot), src + 3 * (c0 + j), qq, nn, pp, KIND, c))
+        c[0] = c[1] = c[2] = 0.f;
     }
-    const int m = min(32, qn - e0);
-    for (int i = 0; i < m; ++i) {
-      const int32_t ei = __shfl_sync(kFull, ent, i);
-      float ci[3];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) ci[q] = __shfl_sync(kFull, c[q], i);
-      if (((ei >> 8) & 31) == lane) {
-        const int ki = ei >> 13;
+    for (int q = 0; q < 3; ++q) sn.val[lane][q] = c[q];
+    const unsigned grp = __match_any_sync(kFull, slot);
+    __syncwarp();
+    if (slot >= 0 && lane == __ffs(grp) - 1) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if (ki) un[1][q] += ci[q];
-          else un[0][q] += ci[q];
-        }
+      for (int q = 0; q < 3; ++q) {
+        float v = 0.f;
+        for (unsigned m = grp; m; m &= m - 1) v += sn.val[__ffs(m) - 1][q];
+        sn.tot[slot][q] = v;
       }
     }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < kSmallT; ++k)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        un[k][q] += sn.tot[lane + 32 * k][q];
+        sn.tot[lane + 32 * k][q] = 0.f;
+      }
+    __syncwarp();
   }
 }
 
 template <int KIND>
 __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
   __shared__ float4 S[kSmallPairsPerTile][kSmallFields];
-  __shared__ int32_t queue_all[kSmallThreads / 32][kSmallQueue];
+  __shared__ SmallNear near_all[kSmallThreads / 32];
   __shared__ int last;
   const int tid = threadIdx.x, lane = tid & 31;
-  int32_t *queue = queue_all[tid >> 5];
+  SmallNear &sn = near_all[tid >> 5];
+  int32_t *queue = sn.queue;
+#pragma unroll
+  for (int k = 0; k < kSmallT; ++k)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) sn.tot[lane + 32 * k][q] = 0.f;
   const unsigned lt = (1u << lane) - 1u;
   // a thread's targets: lane + 32 k of its warp's 64 (k < kSmallT)
   const int64_t tb = (int64_t)blockIdx.x * kSmallBlock;
@@ -164,7 +180,6 @@ __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
   const int64_t s0 = a.ns * y / a.nsplit, s1 = a.ns * (y + 1) / a.nsplit;
   // the CTA's origin: its first target
   const double oo[3] = {a.trg[3 * tb], a.trg[3 * tb + 1], a.trg[3 * tb + 2]};
-  double x64[kSmallT][3];
   float2 xh[kSmallT][3], xl[kSmallT][3];
   float hi[kSmallT][3], lo[kSmallT][3];
   bool act[kSmallT];
@@ -174,9 +189,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
     act[k] = t < a.nt;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      x64[k][q] = act[k] ? a.trg[3 * t + q] : oo[q];
+      const double xq = act[k] ? a.trg[3 * t + q] : oo[q];
       float vh, vl;
-      split_hl(x64[k][q] - oo[q], vh, vl);
+      split_hl(xq - oo[q], vh, vl);
       xh[k][q] = make_float2(vh, vh);
       xl[k][q] = make_float2(vl, vl);
       hi[k][q] = lo[k][q] = 0.f;
@@ -255,14 +270,14 @@ __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
           }
         if (qn > kSmallQueue - 32 * 2 * kSmallT) {
           __syncwarp();
-          small_flush<KIND>(queue, qn, S, a.src, c0, lane, x64, un);
+          small_flush<KIND>(sn, qn, S, a.src, a.trg, c0, t0, lane, un);
           qn = 0;
           __syncwarp();
         }
       }
     }
     __syncwarp();
-    if (qn) small_flush<KIND>(queue, qn, S, a.src, c0, lane, x64, un);
+    if (qn) small_flush<KIND>(sn, qn, S, a.src, a.trg, c0, t0, lane, un);
 #pragma unroll
     for (int k = 0; k < kSmallT; ++k)
 #pragma unroll
@@ -275,9 +290,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
   for (int k = 0; k < kSmallT; ++k) {
     const int64_t t = t0 + 32 * k + lane;
     if (!act[k]) continue;
-    double *o = a.part + ((size_t)y * (size_t)a.nt + (size_t)t) * 3;
+    float2 *o = a.part + ((size_t)y * (size_t)a.nt + (size_t)t) * 3;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) o[q] = (double)hi[k][q] + (double)lo[k][q];
+    for (int q = 0; q < 3; ++q) o[q] = make_float2(hi[k][q], lo[k][q]);
   }
   // the last split of this target block to finish adds the splits in order
   __threadfence();
@@ -286,16 +301,17 @@ __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // the block's partials of one split are 3 x 256 contiguous doubles: each
-  // thread sums 6 of those values over the splits (from L2, written by the
-  // other CTAs before their fence; loads of 5 splits in flight), in split order
+  // the block's partials of one split are 3 x 256 contiguous (hi, lo) pairs:
+  // each thread sums 6 of those values over the splits (from L2, written by
+  // the other CTAs before their fence; loads of 5 splits in flight), in split
+  // order, two-summing the hi parts and adding the lo parts
   constexpr int kPer = 3 * kSmallBlock / kSmallThreads;
   const int64_t v0 = 3 * tb, vend = 3 * min(tb + (int64_t)kSmallBlock, a.nt);
-  double sum[kPer];
+  float sh[kPer], sl[kPer];
 #pragma unroll
-  for (int m = 0; m < kPer; ++m) sum[m] = 0.0;
+  for (int m = 0; m < kPer; ++m) sh[m] = sl[m] = 0.f;
   for (int y0 = 0; y0 < a.nsplit; y0 += 5) {
-    double v[5][kPer];
+    float2 v[5][kPer];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
@@ -303,17 +319,20 @@ __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
         const int64_t e = v0 + tid + kSmallThreads * m;
         v[i][m] = (y0 + i < a.nsplit && e < vend)
                       ? __ldcg(a.part + (size_t)(y0 + i) * (size_t)a.nt * 3 + (size_t)e)
-                      : 0.0;
+                      : make_float2(0.f, 0.f);
       }
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
-      for (int m = 0; m < kPer; ++m) sum[m] += v[i][m];
+      for (int m = 0; m < kPer; ++m) {
+        two_sum_acc(sh[m], sl[m], v[i][m].x);
+        sl[m] += v[i][m].y;
+      }
   }
 #pragma unroll
   for (int m = 0; m < kPer; ++m) {
     const int64_t e = v0 + tid + kSmallThreads * m;
-    if (e < vend) a.out[e] = (a.accumulate ? a.out[e] : 0.0) + sum[m];
+    if (e < vend) a.out[e] = (a.accumulate ? a.out[e] : 0.0) + ((double)sh[m] + (double)sl[m]);
   }
   if (tid == 0) a.blocks[blockIdx.x] = 0;  // ready for the next call
 }
@@ -344,8 +363,8 @@ cudaError_t launch_direct_small(int kinds, const double *src, const double *f, c
                                 const double *trg, int64_t nt, double alpha, double csl,
                                 double cdl, int32_t nsplit, int32_t accumulate, double *part,
                                 int32_t *blocks, double *out, cudaStream_t st) {
-  SmallArgs a{src, f, nrm, phi, w, h, trg, ns, nt, alpha, csl, cdl, nsplit, accumulate, part,
-              blocks, out};
+  SmallArgs a{src, f, nrm, phi, w, h, trg, ns, nt, alpha, csl, cdl, nsplit, accumulate,
+              reinterpret_cast<float2 *>(part), blocks, out};
   const dim3 grid((unsigned)direct_small_blocks(nt), (unsigned)nsplit);
   if (kinds == K_SL)
     k_direct_small<K_SL><<<grid, kSmallThreads, 0, st>>>(a);

@@ -40,7 +40,8 @@ void launch_bucket_order(int64_t n, const uint64_t *keys, const int32_t *vals, i
 // Near pairs of the mixed engine's items (near.cu); runs after the engine.
 void launch_near(const EngineParams &P, int sms, int64_t max_items, cudaStream_t st);
 // Small direct sums (direct_small.cu): one launch over blocks of targets x
-// source splits writing part[split][target][3]; the last split of each block
+// source splits writing part[split][target][3] (an FP32 (hi, lo) pair in
+// each double's bytes); the last split of each block
 // (counter blocks[block], zero before the launch and left zero) writes out.
 constexpr int64_t kSmallPairs = (int64_t)1 << 26;  // targets x sources taking this form
 int64_t direct_small_blocks(int64_t nt);

@@ -38,7 +38,9 @@ constexpr int kNearQueue = 256;           // >= 128 free slots before each candi
 constexpr int kNearSegWin = 64;           // segments per window
 
 struct __align__(16) NearSmem {
-  float4 xt[kItemMax];               // targets: local coordinates, caller index bits in .w
+  float xs[3][kItemMax];             // targets: local coordinates (slots to a multiple of 8;
+                                     //   padding far away),
+  int32_t sid[kItemMax];             //   caller index (self pairs; -1: none)
   float sv[kWarp][3];                // values of one round of evaluations
   float acc[2][3][kItemMax];         // per-target compensated sums (hi, lo)
   int32_t qj[kNearQueue];            // queued pair: source index | kind << 30
@@ -130,10 +132,17 @@ __global__ void __launch_bounds__(kNearWarps *kWarp, kNearMinBlocks) k_near(Engi
     for (int li = lane; li < tn; li += kWarp)
 #pragma unroll
       for (int k = 0; k < 3; ++k) sm.acc[0][k][li] = sm.acc[1][k][li] = 0.f;
+    const int tn8 = (tn + 7) & ~7;
 #pragma unroll
-    for (int t = 0; t < kNearT; ++t)
-      if (lane + kWarp * t < tn)
-        sm.xt[lane + kWarp * t] = make_float4(x[t][0], x[t][1], x[t][2], __int_as_float(self_id[t]));
+    for (int t = 0; t < kNearT; ++t) {
+      const int li = lane + kWarp * t;
+      if (li < tn8) {  // x holds 1e30 and self_id -1 beyond tn
+        sm.xs[0][li] = x[t][0];
+        sm.xs[1][li] = x[t][1];
+        sm.xs[2][li] = x[t][2];
+        sm.sid[li] = self_id[t];
+      }
+    }
     __syncwarp();
 
     // 2./3. candidate sources: each is broadcast and every lane tests its
@@ -178,13 +187,16 @@ __global__ void __launch_bounds__(kNearWarps *kWarp, kNearMinBlocks) k_near(Engi
     const int32_t ncl = P.cand_cnt[id];
     if (ncl >= 0) {
       // The engine listed this item's candidates.  Each lane takes one
-      // candidate and the warp walks the targets (broadcast from shared
-      // memory); near pairs are queued by target, then by lane.
+      // candidate and tests it against every target of the item, two targets
+      // per packed FP32 instruction (per half the same IEEE operations as the
+      // engine's test), into a bit mask without a vote per target; the near
+      // pairs are then queued by candidate (lane), then by target.
       const int32_t *cl = P.cand_list + (size_t)id * (size_t)P.cand_cap;
       const int n_list = min(ncl, P.cand_cap);
       for (int p0 = 0; p0 < n_list; p0 += kWarp) {
         const int pp = p0 + lane;
-        float y0 = 0.f, y1 = 0.f, y2 = 0.f, hh = -1.f;  // hh < 0: idle lane, never near
+        float2 ny0 = make_float2(0.f, 0.f), ny1 = ny0, ny2 = ny0;
+        float hh = -1.f;  // hh < 0: idle lane, never near
         int32_t j = -1;
         uint32_t kb = 0;
         if (pp < n_list) {
@@ -194,36 +206,68 @@ __global__ void __launch_bounds__(kNearWarps *kWarp, kNearMinBlocks) k_near(Engi
           const float4 yh = __ldg(&P.rec[j].yh);
           const float ylx = __ldg(&P.rec[j].q.w), yly = __ldg(&P.rec[j].n.w),
                       ylz = __ldg(&P.rec[j].p.w);
-          y0 = to_local(yh.x, ylx, oh[0], ol[0]);
-          y1 = to_local(yh.y, yly, oh[1], ol[1]);
-          y2 = to_local(yh.z, ylz, oh[2], ol[2]);
+          const float y0 = to_local(yh.x, ylx, oh[0], ol[0]);
+          const float y1 = to_local(yh.y, yly, oh[1], ol[1]);
+          const float y2 = to_local(yh.z, ylz, oh[2], ol[2]);
+          ny0 = make_float2(-y0, -y0);  // x + (-y) is the IEEE x - y
+          ny1 = make_float2(-y1, -y1);
+          ny2 = make_float2(-y2, -y2);
           hh = yh.w;
         }
-        const int32_t jq = (int32_t)((uint32_t)j | kb);
-        for (int t0 = 0; t0 < tn; t0 += 4) {
-          if (qn > kNearQueue - 4 * kWarp) {
-            __syncwarp();
-            eval_queue(sm, P, it.t0, qn, lane);
-            qn = 0;
-          }
+        unsigned mask[kNearT];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int ti = t0 + u;
-            if (ti < tn) {
-              const float4 X = sm.xt[ti];
-              const float r2 = pair_r2(__fsub_rn(X.x, y0), __fsub_rn(X.y, y1), __fsub_rn(X.z, y2));
-              const bool nr = is_near(r2, hh) && __float_as_int(X.w) != j;
-              const unsigned m = __ballot_sync(kFull, nr);
-              if (m) {
-                if (nr) {
-                  const int pos = qn + __popc(m & lt);
-                  sm.qt[pos] = (uint8_t)ti;
-                  sm.qj[pos] = jq;
-                }
-                qn += __popc(m);
-              }
+        for (int w = 0; w < kNearT; ++w) {
+          mask[w] = 0u;
+          if (w * kWarp < tn) {
+#pragma unroll
+            for (int i = 0; i < kWarp; i += 2) {
+              const int ti = w * kWarp + i;
+              if (ti >= tn8) break;
+              const float2 X0 = *reinterpret_cast<const float2 *>(&sm.xs[0][ti]);
+              const float2 X1 = *reinterpret_cast<const float2 *>(&sm.xs[1][ti]);
+              const float2 X2 = *reinterpret_cast<const float2 *>(&sm.xs[2][ti]);
+              const int2 S2 = *reinterpret_cast<const int2 *>(&sm.sid[ti]);
+              const float2 d0 = __fadd2_rn(X0, ny0), d1 = __fadd2_rn(X1, ny1),
+                           d2 = __fadd2_rn(X2, ny2);
+              const float2 r2 = __ffma2_rn(d0, d0, __ffma2_rn(d1, d1, __fmul2_rn(d2, d2)));
+              if (is_near(r2.x, hh) && S2.x != j) mask[w] |= 1u << i;
+              if (is_near(r2.y, hh) && S2.y != j) mask[w] |= 2u << i;
             }
           }
+        }
+        int cnt = 0;
+#pragma unroll
+        for (int w = 0; w < kNearT; ++w) cnt += __popc(mask[w]);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {
+          const int v = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(kFull, incl, kWarp - 1);
+        if (total == 0) continue;
+        const int base = incl - cnt;  // this lane's first entry within the round
+        const int32_t jq = (int32_t)((uint32_t)j | kb);
+        // the round's entries [done, done + room) go to the queue; a full queue
+        // is evaluated before the rest
+        for (int done = 0;;) {
+          const int room = kNearQueue - qn;
+          int idx = base;
+#pragma unroll
+          for (int w = 0; w < kNearT; ++w)
+            for (unsigned m = mask[w]; m; m &= m - 1, ++idx)
+              if (idx >= done && idx < done + room) {
+                const int pos = qn + idx - done;
+                sm.qt[pos] = (uint8_t)(w * kWarp + __ffs(m) - 1);
+                sm.qj[pos] = jq;
+              }
+          const int n_emit = min(room, total - done);
+          qn += n_emit;
+          done += n_emit;
+          if (done == total) break;
+          __syncwarp();
+          eval_queue(sm, P, it.t0, qn, lane);
+          qn = 0;
         }
       }
     } else {

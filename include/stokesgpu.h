@@ -530,6 +530,20 @@ stk_status stokes_pipe_probe_size(size_t *sink_bytes);
 stk_status stokes_pipe_probe(int32_t op, int32_t iters, void *sink, size_t sink_bytes,
                              double *ops, void *stream);
 
+/* ------------------------------------------------ conversion self-check
+ * The library converts between FP64 and FP32 with integer operations (IEEE
+ * 754 round to nearest, ties to even, for results in the normal FP32 range;
+ * exact widening of normal floats), because GB300 runs the conversion
+ * instructions on its 1/64-rate FP64 pipe.  This call puts them beside
+ * CUDA's own conversions for a check: for each in[i] (device, n values),
+ * narrow_own[i] / narrow_cuda[i] receive the library's and CUDA's FP32
+ * rounding of in[i], and widen_own[i] / widen_cuda[i] the library's and
+ * CUDA's FP64 widening of narrow_cuda[i].  All pointers are device memory of
+ * n elements, written on the stream; n = 0 does nothing. */
+stk_status stokes_convert_check(const double *in, int64_t n, float *narrow_own,
+                                float *narrow_cuda, double *widen_own, double *widen_cuda,
+                                void *stream);
+
 /* ----------------------------------------------------------------- status */
 /* Reads the device error word kept in a workspace used by an earlier call.
  * The caller must have synchronised the stream.  Returns STK_OK or

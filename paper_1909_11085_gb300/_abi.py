@@ -37,7 +37,7 @@ EXPORTS = [
     "stokes_octree_build", "stokes_octree_info", "stokes_octree_export", "stokes_octree_destroy",
     "stokes_set_wait_policy", "stokes_pipe_probe_size", "stokes_pipe_probe",
     "stokes_fmm_set_pass_events", "stokes_fmm_operators", "stokes_fmm_tree_complete",
-    "stokes_direct_graph_create",
+    "stokes_direct_graph_create", "stokes_convert_check",
 ]
 
 
@@ -107,6 +107,7 @@ def lib():
             L.stokes_fmm_operators.argtypes = [i32, d, i32, d, i32, d, i32, p, p]
             L.stokes_fmm_tree_complete.argtypes = [i32, i32, p, p, p, p, p, p, p, p, p]
             L.stokes_pipe_probe.argtypes = [i32, i32, p, sz, ctypes.POINTER(ctypes.c_double), p]
+            L.stokes_convert_check.argtypes = [p, i64, p, p, p, p, p]
             L.stokes_sl_eval_noalloc.argtypes = [p, p, p, p, i64, p, i64, d, p, po, p]
             L.stokes_sldl_grad.argtypes = [p, p, p, p, p, p, i64, p, i64, p, d, p, p, p, p, p, po,
                                            p, sz, p]

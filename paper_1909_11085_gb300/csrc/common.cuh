@@ -99,12 +99,43 @@ __device__ __forceinline__ int seg_kind(const EngineParams &P, int32_t sid) {
   return P.kind_alternating ? ((sid & 1) ? K_DL : K_SL) : P.kind;
 }
 
+// FP64 <-> FP32 conversions on the integer pipe.  GB300 runs conversions
+// that involve FP64 on its FP64 pipe (1/64 of the FP32 rate), where they were
+// a third of the near pairs' FP64 operations and most of the packing's.
+// f64_to_f32_rn rounds to nearest, ties to even (IEEE 754 binary64 to
+// binary32), for values whose FP32 result is normal: the sign, the rebiased
+// exponent and the top 23 of the 52 fraction bits, plus one when the 29
+// dropped bits are above half an FP32 ulp or exactly half with an odd kept
+// fraction; a carry out of the fraction moves into the exponent, so a value
+// just below 2^k rounds up to 2^k and one at or above FLT_MAX + ulp/2 to
+// infinity.  Zeros, results below 2^-126, infinities and NaN take the
+// hardware conversion.  f32_to_f64 widens a normal float exactly (exponent
+// rebiased by 1023 - 127, fraction shifted into the top of the 52 bits).
+__device__ __forceinline__ float f64_to_f32_rn(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023;  // unbiased exponent
+  if (e < -126 || e > 127) return __double2float_rn(v);
+  const unsigned kept = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 fraction bits
+  const unsigned dropped = lo & 0x1fffffffu;                    // the other 29
+  const unsigned up =
+      (dropped > 0x10000000u || (dropped == 0x10000000u && (kept & 1u))) ? 1u : 0u;
+  return __uint_as_float(((hi & 0x80000000u) | ((unsigned)(e + 127) << 23) | kept) + up);
+}
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 // Exact-enough split of (x - c) into two floats; used identically for
 // sources and targets so that coincident points get bit-identical local
 // coordinates.
 __device__ __forceinline__ void split_hl(double v, float &hi, float &lo) {
-  hi = __double2float_rn(v);
-  lo = __double2float_rn(v - (double)hi);
+  hi = f64_to_f32_rn(v);
+  lo = f64_to_f32_rn(v - f32_to_f64(hi));
 }
 __device__ __forceinline__ float to_local(float vh, float vl, float oh, float ol) {
   return __fadd_rn(__fsub_rn(vh, oh), __fsub_rn(vl, ol));
@@ -178,22 +209,23 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p) {
 // zero distance (no contribution).
 __device__ __forceinline__ bool near_contrib(const double *x, const double *y, float4 q,
                                              float4 n, float4 p, int kind, float (&c)[3]) {
-  // The FP64 and conversion instructions below run on GB300's FP64 pipe (1/64
-  // of the FP32 rate), so there are as few as the FP64 difference and 1/|r|
-  // allow: 3 DADD, 3 + 2 conversions, 3 for r^2, 4 for the Newton step.
+  // The FP64 instructions below run on GB300's FP64 pipe (1/64 of the FP32
+  // rate), so there are as few as the FP64 difference and 1/|r| allow: 3
+  // DADD, 3 for r^2, 4 for the Newton step; the conversions run on the
+  // integer pipe.
   const double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
-  const float fx = __double2float_rn(dx), fy = __double2float_rn(dy), fz = __double2float_rn(dz);
+  const float fx = f64_to_f32_rn(dx), fy = f64_to_f32_rn(dy), fz = f64_to_f32_rn(dz);
   if (fx == 0.f && fy == 0.f && fz == 0.f) return false;  // coincident (to 1e-45)
   const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
   const double r2 = dx * dx + dy * dy + dz * dz;
   double rid;
   if (r2f > 1e-30f && r2f < 1e30f) {
-    const double y0 = (double)rsqrt_ftz(r2f);
+    const double y0 = f32_to_f64(rsqrt_ftz(r2f));
     rid = y0 * fma(-0.5 * r2, y0 * y0, 1.5);  // one FP64 Newton step
   } else {
     rid = 1.0 / sqrt(r2);
   }
-  const float ri = __double2float_rn(rid);
+  const float ri = f64_to_f32_rn(rid);
   // unit vector in FP32; below r2 ~ 1e-30 the FP64 product avoids underflow
   float ex = fx * ri, ey = fy * ri, ez = fz * ri;
   if (!(r2f > 1e-30f)) {

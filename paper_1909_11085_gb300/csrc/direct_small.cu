@@ -212,16 +212,16 @@ __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
           const double al = a.alpha * a.h[j];
           hh = al * al;
         }
-        const double wj = a.w ? a.w[j] : 1.0;
+        const double wj = a.w ? a.w[j] : 1.0, ws = wj * a.csl, wd = wj * a.cdl;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           v[q] = -vh[q];
           v[4 + q] = -vl[q];
-          v[7 + q] = (KIND & K_SL) ? (float)(wj * a.csl * a.f[3 * j + q]) : 0.f;
-          v[10 + q] = (KIND & K_DL) ? (float)a.nrm[3 * j + q] : 0.f;
-          v[13 + q] = (KIND & K_DL) ? (float)(wj * a.cdl * a.phi[3 * j + q]) : 0.f;
+          v[7 + q] = (KIND & K_SL) ? f64_to_f32_rn(ws * a.f[3 * j + q]) : 0.f;
+          v[10 + q] = (KIND & K_DL) ? f64_to_f32_rn(a.nrm[3 * j + q]) : 0.f;
+          v[13 + q] = (KIND & K_DL) ? f64_to_f32_rn(wd * a.phi[3 * j + q]) : 0.f;
         }
-        v[3] = (float)fmin(hh, 3.0e38);
+        v[3] = fminf(f64_to_f32_rn(hh), 3.0e38f);
       } else {
 #pragma unroll
         for (int q = 0; q < 16; ++q) v[q] = 0.f;

@@ -461,7 +461,7 @@ __device__ bool run_item(const EngineParams &P, const Item &it, int id, WarpSmem
         const double *xp = P.trg64 + 3 * (size_t)(P.tperm ? P.tperm[gi] : gi);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const float rk = __double2float_rn(xp[k] - x0[k]);
+          const float rk = f64_to_f32_rn(xp[k] - x0[k]);
           mn[k] = fminf(mn[k], rk);
           mx[k] = fmaxf(mx[k], rk);
         }

@@ -88,6 +88,19 @@ cudaError_t launch_probe(int blocks, int32_t iters, void *sink, cudaStream_t st)
   return cudaGetLastError();
 }
 
+// The library's integer-pipe conversions beside CUDA's (stokes_convert_check).
+__global__ void k_convert_check(const double *in, int64_t n, float *narrow_own,
+                                float *narrow_cuda, double *widen_own, double *widen_cuda) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = in[i];
+  const float c = __double2float_rn(v);
+  narrow_own[i] = stk::f64_to_f32_rn(v);
+  narrow_cuda[i] = c;
+  widen_own[i] = stk::f32_to_f64(c);
+  widen_cuda[i] = (double)c;
+}
+
 }  // namespace
 
 extern "C" {
@@ -126,6 +139,23 @@ stk_status stokes_pipe_probe(int32_t op, int32_t iters, void *sink, size_t sink_
     case 2: e = launch_probe<2>(blocks, iters, sink, st); break;
     default: e = launch_probe<3>(blocks, iters, sink, st); break;
   }
+  if (e != cudaSuccess) return stk::report_error(STK_ECUDA, cudaGetErrorString(e));
+  return STK_OK;
+}
+
+stk_status stokes_convert_check(const double *in, int64_t n, float *narrow_own,
+                                float *narrow_cuda, double *widen_own, double *widen_cuda,
+                                void *stream) {
+  if (n < 0) return stk::report_error(STK_EINVAL, "n must be >= 0");
+  if (n == 0) return STK_OK;
+  if (!in || !narrow_own || !narrow_cuda || !widen_own || !widen_cuda)
+    return stk::report_error(STK_EINVAL, "a pointer is NULL");
+  const int64_t blocks = (n + 255) / 256;
+  if (blocks > 0x7fffffff) return stk::report_error(STK_EINVAL, "n too large");
+  k_convert_check<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      in, n, narrow_own, narrow_cuda, widen_own, widen_cuda);
+  stk::count_launches(1);
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return stk::report_error(STK_ECUDA, cudaGetErrorString(e));
   return STK_OK;
 }

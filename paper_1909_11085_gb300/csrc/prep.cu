@@ -31,18 +31,22 @@ __global__ void k_pack_mixed(int64_t ns, const double *__restrict__ src,
       const double a = alpha * h[j];
       hh = a * a;
     }
-    float hhf = (float)fmin(hh, (double)FLT_MAX);
+    float hhf = fminf(f64_to_f32_rn(hh), FLT_MAX);
     hhf = fmaxf(hhf, FLT_MIN);  // exactly coincident points always take the FP64 path
     R.yh = make_float4(hx, hy, hz, hhf);
     const double wj = w ? w[j] : 1.0;
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f), nn = q, pp = q;
-    if (f)
-      q = make_float4((float)(wj * csl * f[3 * j]), (float)(wj * csl * f[3 * j + 1]),
-                      (float)(wj * csl * f[3 * j + 2]), 0.f);
+    if (f) {
+      const double s = wj * csl;
+      q = make_float4(f64_to_f32_rn(s * f[3 * j]), f64_to_f32_rn(s * f[3 * j + 1]),
+                      f64_to_f32_rn(s * f[3 * j + 2]), 0.f);
+    }
     if (phi) {
-      nn = make_float4((float)nrm[3 * j], (float)nrm[3 * j + 1], (float)nrm[3 * j + 2], 0.f);
-      pp = make_float4((float)(wj * cdl * phi[3 * j]), (float)(wj * cdl * phi[3 * j + 1]),
-                       (float)(wj * cdl * phi[3 * j + 2]), 0.f);
+      const double s = wj * cdl;
+      nn = make_float4(f64_to_f32_rn(nrm[3 * j]), f64_to_f32_rn(nrm[3 * j + 1]),
+                       f64_to_f32_rn(nrm[3 * j + 2]), 0.f);
+      pp = make_float4(f64_to_f32_rn(s * phi[3 * j]), f64_to_f32_rn(s * phi[3 * j + 1]),
+                       f64_to_f32_rn(s * phi[3 * j + 2]), 0.f);
     }
     q.w = lx;
     nn.w = ly;

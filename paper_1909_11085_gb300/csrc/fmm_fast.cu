@@ -395,16 +395,19 @@ __global__ void k_fast_pack(Pass P) {
   centre(P.t, b, d, c);
   const int64_t i0 = P.t.leaf_ptr[l], i1 = P.t.leaf_ptr[l + 1];
   if (!in_range(P, i0, P.n + 1) || !in_range(P, i1, P.n + 1)) return;
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+  // (the FP32 roundings on the integer pipe: f64_to_f32_rn)
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const double wi = P.w[i];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      P.ploc[3 * i + q] = (float)(P.pts[3 * i + q] - c[q]);
-      if (P.qf) P.qf[3 * i + q] = (float)(P.csl * (P.w[i] * P.f[3 * i + q]));
+      P.ploc[3 * i + q] = f64_to_f32_rn(P.pts[3 * i + q] - c[q]);
+      if (P.qf) P.qf[3 * i + q] = f64_to_f32_rn(P.csl * (wi * P.f[3 * i + q]));
       if (P.pf) {
-        P.pf[3 * i + q] = (float)(P.cdl * (P.w[i] * P.phi[3 * i + q]));
-        P.nf[3 * i + q] = (float)P.nrm[3 * i + q];
+        P.pf[3 * i + q] = f64_to_f32_rn(P.cdl * (wi * P.phi[3 * i + q]));
+        P.nf[3 * i + q] = f64_to_f32_rn(P.nrm[3 * i + q]);
       }
     }
+  }
 }
 
 // ---------------------------------------------------------------- upward
@@ -1360,7 +1363,7 @@ __global__ void __launch_bounds__(kItemThreads) k_fast_l2t(Pass P) {
     if (act && sl == 0) {
       double *out = P.out + 3 * e;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) out[a] = (P.accumulate ? out[a] : 0.0) + (double)u[a];
+      for (int a = 0; a < 3; ++a) out[a] = (P.accumulate ? out[a] : 0.0) + f32_to_f64(u[a]);
     }
   }
 }

@@ -4,7 +4,9 @@
 // Morton sort, no items, no separate near-pair pass.
 //
 // Grid: blocks of 256 targets (two per thread, sharing every staged source) x
-// source splits.  A CTA stages its split's sources 128 at a time in shared
+// source splits (split y holds sources y, y + nsplit, ...: near pairs, which
+// cluster where sources and targets share a region, spread evenly over the
+// CTAs).  A CTA stages its split's sources 128 at a time in shared
 // memory, two by two (eight float4 per pair, read as broadcasts): positions
 // hi/lo relative to the CTA's origin (its first target), so that
 // d = (x_h - y_h) + (x_l - y_l) is accurate relative to |x - y| wherever the
@@ -114,11 +116,13 @@ struct SmallNear {
 // the lanes owning their targets.  In each round the lanes of one target
 // (found with match_any) are summed in queue order by the group's first lane;
 // the owner then adds the round's sum: the order is fixed, so the result is
-// deterministic.  t0: the warp's first target (slot s is target t0 + s).
+// deterministic.  t0: the warp's first target (slot s is target t0 + s);
+// staged source j is source c0 + cs j.
 template <int KIND>
 __device__ __forceinline__ void small_flush(SmallNear &sn, int qn,
                                             const float4 (*S)[kSmallFields], const double *src,
-                                            const double *trg, int64_t c0, int64_t t0, int lane,
+                                            const double *trg, int64_t c0, int64_t cs, int64_t t0,
+                                            int lane,
                                             float (&un)[kSmallT][3]) {
   for (int e0 = 0; e0 < qn; e0 += 32) {
     const int e = e0 + lane;
@@ -133,7 +137,7 @@ __device__ __forceinline__ void small_flush(SmallNear &sn, int qn,
       const float4 qq = make_float4(F[14 + h], F[16 + h], F[18 + h], 0.f);
       const float4 nn = make_float4(F[20 + h], F[22 + h], F[24 + h], 0.f);
       const float4 pp = make_float4(F[26 + h], F[28 + h], F[30 + h], 0.f);
-      if (!near_contrib(trg + 3 * (t0 + slot), src + 3 * (c0 + j), qq, nn, pp, KIND, c))
+      if (!near_contrib(trg + 3 * (t0 + slot), src + 3 * (c0 + cs * j), qq, nn, pp, KIND, c))
         c[0] = c[1] = c[2] = 0.f;
     }
 #pragma unroll
@@ -177,7 +181,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
   const int64_t tb = (int64_t)blockIdx.x * kSmallBlock;
   const int64_t t0 = tb + (int64_t)(tid >> 5) * 32 * kSmallT;
   const int y = blockIdx.y;
-  const int64_t s0 = a.ns * y / a.nsplit, s1 = a.ns * (y + 1) / a.nsplit;
+  // the split's sources: y, y + nsplit, y + 2 nsplit, ... (strided, so that
+  // the near pairs, which cluster where sources and targets share a region,
+  // spread over all splits instead of loading a few CTAs of the one wave)
+  const int64_t cnt = (a.ns - y + a.nsplit - 1) / a.nsplit;
   // the CTA's origin: its first target
   const double oo[3] = {a.trg[3 * tb], a.trg[3 * tb + 1], a.trg[3 * tb + 2]};
   float2 xh[kSmallT][3], xl[kSmallT][3];
@@ -197,13 +204,15 @@ __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
       hi[k][q] = lo[k][q] = 0.f;
     }
   }
-  for (int64_t c0 = s0; c0 < s1; c0 += kSmallThreads) {
-    const int n = (int)min((int64_t)kSmallThreads, s1 - c0), np = (n + 1) / 2;
+  for (int64_t i0 = 0; i0 < cnt; i0 += kSmallThreads) {
+    const int n = (int)min((int64_t)kSmallThreads, cnt - i0), np = (n + 1) / 2;
+    const int64_t c0 = y + (int64_t)a.nsplit * i0;  // staged source k is c0 + nsplit k
     __syncthreads();
-    {  // source c0 + tid into half tid & 1 of pair tid / 2 (a missing one: far, zero strength)
+    {  // source c0 + nsplit tid into half tid & 1 of pair tid / 2 (a missing one: far,
+       // zero strength)
       float v[16];
       if (tid < n) {
-        const int64_t j = c0 + tid;
+        const int64_t j = c0 + (int64_t)a.nsplit * tid;
         float vh[3], vl[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) split_hl(a.src[3 * j + q] - oo[q], vh[q], vl[q]);
@@ -270,14 +279,14 @@ __global__ void __launch_bounds__(kSmallThreads) k_direct_small(SmallArgs a) {
           }
         if (qn > kSmallQueue - 32 * 2 * kSmallT) {
           __syncwarp();
-          small_flush<KIND>(sn, qn, S, a.src, a.trg, c0, t0, lane, un);
+          small_flush<KIND>(sn, qn, S, a.src, a.trg, c0, a.nsplit, t0, lane, un);
           qn = 0;
           __syncwarp();
         }
       }
     }
     __syncwarp();
-    if (qn) small_flush<KIND>(sn, qn, S, a.src, a.trg, c0, t0, lane, un);
+    if (qn) small_flush<KIND>(sn, qn, S, a.src, a.trg, c0, a.nsplit, t0, lane, un);
 #pragma unroll
     for (int k = 0; k < kSmallT; ++k)
 #pragma unroll

@@ -201,7 +201,8 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p) {
 }
 
 // Near pair (|x - y| < alpha h_y): the difference x - y in FP64 from the FP64
-// positions and 1/|r| in FP64 (one Newton step on the FP32 estimate); the
+// positions and 1/|r| to FP32 rounding from the FP64 r^2 (one Newton step on
+// the FP32 estimate, its residual in FP64); the
 // kernel products in FP32, written through the unit vector e = d/|r| so that
 // they stay in range however close the pair is:
 //   SL: (q + e (e.q)) / r      DL: e (e.psi)(e.n) / r^2
@@ -211,21 +212,27 @@ __device__ __forceinline__ bool near_contrib(const double *x, const double *y, f
                                              float4 n, float4 p, int kind, float (&c)[3]) {
   // The FP64 instructions below run on GB300's FP64 pipe (1/64 of the FP32
   // rate), so there are as few as the FP64 difference and 1/|r| allow: 3
-  // DADD, 3 for r^2, 4 for the Newton step; the conversions run on the
+  // DADD, 3 for r^2, 2 for the Newton residual; the conversions run on the
   // integer pipe.
   const double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
   const float fx = f64_to_f32_rn(dx), fy = f64_to_f32_rn(dy), fz = f64_to_f32_rn(dz);
   if (fx == 0.f && fy == 0.f && fz == 0.f) return false;  // coincident (to 1e-45)
   const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
   const double r2 = dx * dx + dy * dy + dz * dz;
-  double rid;
+  double rid = 0.0;
+  float ri;
   if (r2f > 1e-30f && r2f < 1e30f) {
-    const double y0 = f32_to_f64(rsqrt_ftz(r2f));
-    rid = y0 * fma(-0.5 * r2, y0 * y0, 1.5);  // one FP64 Newton step
+    // One Newton step on the FP32 estimate y0 = rsqrt(r^2 in FP32):
+    // 1/|r| = y0 (1 + e/2 + 3e^2/8 + ...) with the residual e = 1 - r^2 y0^2
+    // (|e| < 2^-21), which cancels and so is formed in FP64 from the FP64
+    // r^2; e/2 then needs only FP32, and the dropped 3e^2/8 < 2^-43.
+    const float y0f = rsqrt_ftz(r2f);
+    const double y0 = f32_to_f64(y0f);
+    ri = fmaf(0.5f * y0f, f64_to_f32_rn(fma(-r2, y0 * y0, 1.0)), y0f);
   } else {
     rid = 1.0 / sqrt(r2);
+    ri = f64_to_f32_rn(rid);
   }
-  const float ri = f64_to_f32_rn(rid);
   // unit vector in FP32; below r2 ~ 1e-30 the FP64 product avoids underflow
   float ex = fx * ri, ey = fy * ri, ez = fz * ri;
   if (!(r2f > 1e-30f)) {

@@ -34,8 +34,8 @@ namespace {
 constexpr int kNearWarps = 4;
 constexpr int kNearMinBlocks = 8;
 constexpr int kNearT = kItemMax / kWarp;  // targets per lane
-constexpr int kNearQueue = 256;           // >= 128 free slots before each candidate
-constexpr int kNearSegWin = 64;           // segments per window
+constexpr int kNearQueue = 192;           // >= 128 free slots before each candidate
+constexpr int kNearSegWin = 32;           // segments per window
 
 struct __align__(16) NearSmem {
   float xs[3][kItemMax];             // targets: local coordinates (slots to a multiple of 8;
@@ -45,7 +45,7 @@ struct __align__(16) NearSmem {
   float acc[2][3][kItemMax];         // per-target compensated sums (hi, lo)
   int32_t qj[kNearQueue];            // queued pair: source index | kind << 30
   uint8_t qt[kNearQueue];            //   target within the item
-  int64_t seg_start[kNearSegWin];    // window of segments: first source,
+  int32_t seg_start[kNearSegWin];    // window of segments: first source (< 2^30),
   int32_t seg_pre[kNearSegWin + 1];  //   sources before it in the window,
   int32_t seg_kind[kNearSegWin];     //   kind bits
 };
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kNearWarps *kWarp, kNearMinBlocks) k_near(Engi
             const int32_t sid = P.seg_list ? P.seg_list[w0 + e] : w0 + e;
             const int64_t a = P.range_ptr[sid];
             sz[h] = (int32_t)(P.range_ptr[sid + 1] - a);
-            sm.seg_start[e] = a;
+            sm.seg_start[e] = (int32_t)a;
             sm.seg_kind[e] = seg_kind(P, sid) << 30;
           }
         }

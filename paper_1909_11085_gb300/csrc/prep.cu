@@ -160,7 +160,11 @@ __global__ void k_morton(int64_t n, const double *__restrict__ pts, const double
 
 // ---------------------------------------------------------------- scan
 // Single-block exclusive scan of n int32 values; out has n + 1 entries.
+// Each thread takes kScanPer consecutive values of a tile (all its loads in
+// flight at once), sums them, and the block scans the thread sums; a tile is
+// kScanThreads * kScanPer values, so the per-tile barriers are few.
 constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 16;
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_excl(const int32_t *__restrict__ in,
                                                             int64_t n, int32_t *__restrict__ out,
@@ -170,10 +174,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_excl(const int32_t *__res
   if (threadIdx.x == 0) carry_s = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int64_t base = 0; base < n; base += kScanThreads) {
-    const int64_t i = base + threadIdx.x;
-    const int32_t v = i < n ? in[i] : 0;
-    int32_t x = v;
+  for (int64_t base = 0; base < n; base += (int64_t)kScanThreads * kScanPer) {
+    const int64_t i0 = base + (int64_t)threadIdx.x * kScanPer;
+    int32_t v[kScanPer];
+    int32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      v[k] = i0 + k < n ? in[i0 + k] : 0;
+      sum += v[k];
+    }
+    int32_t x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int32_t y = __shfl_up_sync(kFull, x, o);
@@ -192,10 +202,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_excl(const int32_t *__res
     }
     __syncthreads();
     const int32_t carry = carry_s;
-    const int32_t incl = x + (wid > 0 ? warp_sums[wid - 1] : 0);
-    if (i < n) out[i] = carry + incl - v;
+    int32_t run = carry + x - sum + (wid > 0 ? warp_sums[wid - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      if (i0 + k < n) out[i0 + k] = run;
+      run += v[k];
+    }
     __syncthreads();
-    if (threadIdx.x == kScanThreads - 1) carry_s = carry + incl;
+    if (threadIdx.x == 0) carry_s = carry + warp_sums[kScanThreads / kWarp - 1];
     __syncthreads();
   }
   if (threadIdx.x == 0) {

@@ -160,9 +160,10 @@ __global__ void k_morton(int64_t n, const double *__restrict__ pts, const double
 
 // ---------------------------------------------------------------- scan
 // Single-block exclusive scan of n int32 values; out has n + 1 entries.
-// Each thread takes kScanPer consecutive values of a tile (all its loads in
-// flight at once), sums them, and the block scans the thread sums; a tile is
-// kScanThreads * kScanPer values, so the per-tile barriers are few.
+// A tile is kScanThreads * kScanPer values; warp w takes kScanPer rows of 32
+// consecutive values (loads and stores coalesced, all loads in flight at
+// once), scans each row with shuffles and chains the rows, and the block
+// scans the warps' totals.
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 16;
 
@@ -175,21 +176,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_excl(const int32_t *__res
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int64_t base = 0; base < n; base += (int64_t)kScanThreads * kScanPer) {
-    const int64_t i0 = base + (int64_t)threadIdx.x * kScanPer;
-    int32_t v[kScanPer];
-    int32_t sum = 0;
+    const int64_t w0 = base + (int64_t)wid * kWarp * kScanPer + lane;  // row k: w0 + 32 k
+    int32_t v[kScanPer], x[kScanPer];
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) v[k] = w0 + kWarp * k < n ? in[w0 + kWarp * k] : 0;
+    int32_t run = 0;  // the warp's values before row k
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-      v[k] = i0 + k < n ? in[i0 + k] : 0;
-      sum += v[k];
-    }
-    int32_t x = sum;
+      int32_t t = v[k];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t y = __shfl_up_sync(kFull, x, o);
-      if (lane >= o) x += y;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(kFull, t, o);
+        if (lane >= o) t += y;
+      }
+      x[k] = run + t - v[k];  // exclusive within the warp's rows
+      run += __shfl_sync(kFull, t, 31);
     }
-    if (lane == 31) warp_sums[wid] = x;
+    if (lane == 0) warp_sums[wid] = run;
     __syncthreads();
     if (wid == 0) {
       int32_t s = warp_sums[lane];
@@ -201,13 +204,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_excl(const int32_t *__res
       warp_sums[lane] = s;  // inclusive over warps
     }
     __syncthreads();
-    const int32_t carry = carry_s;
-    int32_t run = carry + x - sum + (wid > 0 ? warp_sums[wid - 1] : 0);
+    const int32_t carry = carry_s, before = carry + (wid > 0 ? warp_sums[wid - 1] : 0);
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-      if (i0 + k < n) out[i0 + k] = run;
-      run += v[k];
-    }
+    for (int k = 0; k < kScanPer; ++k)
+      if (w0 + kWarp * k < n) out[w0 + kWarp * k] = before + x[k];
     __syncthreads();
     if (threadIdx.x == 0) carry_s = carry + warp_sums[kScanThreads / kWarp - 1];
     __syncthreads();

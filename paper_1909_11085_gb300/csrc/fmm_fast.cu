@@ -857,30 +857,51 @@ static_assert(kTcChunks % 2 == 0, "two octant halves per direction");
 __global__ void k_fast_btab(Pass P, int64_t n) {
   const int m = 3 * P.nc * 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // e runs over the table in its own order (coalesced stores): float pos of
-  // row nn of tile wc holds k = ((pos / 4) ^ (nn mod 8)) 4 + pos mod 4
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+  // e4 runs over the table four floats at a time in its own order (coalesced
+  // float4 stores): float pos of row nn of tile wc holds k = ((pos / 4) ^ (nn
+  // mod 8)) 4 + pos mod 4, so the four floats pos = 4 a .. 4 a + 3 hold
+  // k = 4 b + j, b = a ^ (nn mod 8): one source octant sl and offset, the
+  // components c = 2 b mod 4 (j = 0, 1) and c + 1 (j = 2, 3), re/im rk = j mod 2
+  for (int64_t e4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * e4 < n; e4 += stride) {
+    const int64_t e = 4 * e4;
     const int64_t wc = e / (kTcCols * kTcK);
     const int r = (int)(e % (kTcCols * kTcK));
     const int w = (int)(wc / kTcChunks), ch = (int)(wc % kTcChunks);
     const int nn = r / kTcK, pos = r % kTcK;
-    const int k = ((((pos >> 2) ^ (nn & 7)) & 7) << 2) | (pos & 3);
+    const int bq = ((pos >> 2) ^ (nn & 7)) & 7;
     const int t = nn / 6, q = (nn >> 1) % 3, rn = nn & 1;
-    const int sl = 4 * (ch & 1) + (k >> 3), c = (k >> 1) & 3, rk = k & 1;
+    const int sl = 4 * (ch & 1) + (bq >> 1);
     const int dd = ch >> 1, dir = dd < 13 ? dd : dd + 1;
     const int ox = 2 * (dir / 9 - 1) + (sl >> 2) - (t >> 2);
     const int oy = 2 * ((dir / 3) % 3 - 1) + ((sl >> 1) & 1) - ((t >> 1) & 1);
     const int oz = 2 * (dir % 3 - 1) + (sl & 1) - (t & 1);
-    float val = 0.f;
-    if (c < P.nc && !(ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1)) {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (!(ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1)) {
       const int oi = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
-      const float *K = P.spec32 + ((size_t)w * 343 + oi) * m + (q * P.nc + c) * 2;
-      val = (rk == rn) ? K[0] : (rk == 0 ? K[1] : -K[1]);
+      const float *K = P.spec32 + ((size_t)w * 343 + oi) * m + (size_t)q * P.nc * 2;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = (2 * bq + h) & 3;
+        if (c < P.nc) {
+          const float2 kc = *reinterpret_cast<const float2 *>(K + 2 * c);
+#pragma unroll
+          for (int rk = 0; rk < 2; ++rk)
+            v[2 * h + rk] = (rk == rn) ? kc.x : (rk == 0 ? kc.y : -kc.y);
+        }
+      }
     }
-    const float hi = tf32_rna(val), lo = tf32_rna(val - hi);
+    float4 hi, lo;
+    hi.x = tf32_rna(v[0]);
+    hi.y = tf32_rna(v[1]);
+    hi.z = tf32_rna(v[2]);
+    hi.w = tf32_rna(v[3]);
+    lo.x = tf32_rna(v[0] - hi.x);
+    lo.y = tf32_rna(v[1] - hi.y);
+    lo.z = tf32_rna(v[2] - hi.z);
+    lo.w = tf32_rna(v[3] - hi.w);
     float *o = P.btab + (size_t)wc * 2 * kTcCols * kTcK + (size_t)nn * kTcK + pos;
-    o[0] = hi;  // sw128_off(nn, k) / 4 == nn kTcK + pos
-    o[kTcCols * kTcK] = lo;
+    *reinterpret_cast<float4 *>(o) = hi;  // sw128_off(nn, k) / 4 == nn kTcK + pos
+    *reinterpret_cast<float4 *>(o + kTcCols * kTcK) = lo;
   }
 }
 
@@ -1470,7 +1491,7 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
     post();
     const int64_t nb = (int64_t)nf * kTcChunks * kTcCols * kTcK;
     pre("btab");
-    k_fast_btab<<<gs(nb), 256, 0, st>>>(P, nb);
+    k_fast_btab<<<gs(nb / 4), 256, 0, st>>>(P, nb);
     post();
   }
   pre("s2m");

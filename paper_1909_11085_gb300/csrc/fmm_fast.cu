@@ -36,7 +36,6 @@ namespace fmm {
 namespace {
 
 constexpr int kFastTile = 8;       // boxes per CTA of the products
-constexpr int kStageThreads = 128; // CTA of the leaf kernels
 constexpr int kErrIndex = 6;
 
 __device__ __forceinline__ void bad_index(const Pass &P) {
@@ -385,9 +384,12 @@ __global__ void k_fast_spec(Pass P, int64_t n) {
 }
 
 // Points relative to their leaf's centre and pre-scaled FP32 densities; one
-// CTA per leaf.
-__global__ void k_fast_pack(Pass P) {
-  const int32_t l = blockIdx.x;
+// warp per leaf (leaves hold about 64 points), kPackLeaves leaves per CTA.
+constexpr int kPackLeaves = 4;
+__global__ void __launch_bounds__(kPackLeaves * 32) k_fast_pack(Pass P) {
+  const int32_t l = blockIdx.x * kPackLeaves + (int)(threadIdx.x >> 5);
+  if (l >= P.t.nleaf) return;
+  const int lane = threadIdx.x & 31;
   const int32_t b = P.t.leaf_box[l];
   if (!in_range(P, b, P.t.nbox)) return;
   const int d = P.t.depth[b];
@@ -396,7 +398,7 @@ __global__ void k_fast_pack(Pass P) {
   const int64_t i0 = P.t.leaf_ptr[l], i1 = P.t.leaf_ptr[l + 1];
   if (!in_range(P, i0, P.n + 1) || !in_range(P, i1, P.n + 1)) return;
   // (the FP32 roundings on the integer pipe: f64_to_f32_rn)
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+  for (int64_t i = i0 + lane; i < i1; i += 32) {
     const double wi = P.w[i];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -1476,7 +1478,7 @@ cudaError_t far_field_fast(const Pass &P0, const int32_t *depth_ptr, int32_t max
     post();
   }
   pre("pack");
-  k_fast_pack<<<P.t.nleaf, kStageThreads, 0, st>>>(P);
+  k_fast_pack<<<(P.t.nleaf + kPackLeaves - 1) / kPackLeaves, kPackLeaves * 32, 0, st>>>(P);
   post();
   {
     const int64_t n = P.n_uc2e + P.n_dc2e;

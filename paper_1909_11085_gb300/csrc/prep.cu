@@ -10,9 +10,11 @@
 namespace stk {
 
 // ---------------------------------------------------------------- packing
-// Mixed records: positions split hi/lo about the frame centre c = src[0];
-// quadrature weight and kernel constant folded into the densities
-// (q = w f / (8 pi mu), psi = w phi * 6 / (8 pi)); hh = (alpha h)^2.
+// Mixed records: positions split hi/lo about the frame centre c = src[0]
+// (in FP64: the difference is where FP32 would cancel); quadrature weight and
+// kernel constant folded into the densities (q = w f / (8 pi mu), psi = w phi
+// * 6 / (8 pi)) and hh = (alpha h)^2, products of the FP32-rounded factors in
+// FP32 (a few FP32 ulps, against the FP64 pipe's 1/64 rate for the products).
 __global__ void k_pack_mixed(int64_t ns, const double *__restrict__ src,
                              const double *__restrict__ f, const double *__restrict__ nrm,
                              const double *__restrict__ phi, const double *__restrict__ w,
@@ -26,27 +28,26 @@ __global__ void k_pack_mixed(int64_t ns, const double *__restrict__ src,
     split_hl(src[3 * j] - cx, hx, lx);
     split_hl(src[3 * j + 1] - cy, hy, ly);
     split_hl(src[3 * j + 2] - cz, hz, lz);
-    double hh = 0.0;
+    float hhf = 0.f;
     if (h) {
-      const double a = alpha * h[j];
-      hh = a * a;
+      const float a = f64_to_f32_rn(alpha) * f64_to_f32_rn(h[j]);
+      hhf = a * a;
     }
-    float hhf = fminf(f64_to_f32_rn(hh), FLT_MAX);
-    hhf = fmaxf(hhf, FLT_MIN);  // exactly coincident points always take the FP64 path
+    hhf = fmaxf(fminf(hhf, FLT_MAX), FLT_MIN);
     R.yh = make_float4(hx, hy, hz, hhf);
-    const double wj = w ? w[j] : 1.0;
+    const float wj = w ? f64_to_f32_rn(w[j]) : 1.f;
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f), nn = q, pp = q;
     if (f) {
-      const double s = wj * csl;
-      q = make_float4(f64_to_f32_rn(s * f[3 * j]), f64_to_f32_rn(s * f[3 * j + 1]),
-                      f64_to_f32_rn(s * f[3 * j + 2]), 0.f);
+      const float s = wj * f64_to_f32_rn(csl);
+      q = make_float4(s * f64_to_f32_rn(f[3 * j]), s * f64_to_f32_rn(f[3 * j + 1]),
+                      s * f64_to_f32_rn(f[3 * j + 2]), 0.f);
     }
     if (phi) {
-      const double s = wj * cdl;
+      const float s = wj * f64_to_f32_rn(cdl);
       nn = make_float4(f64_to_f32_rn(nrm[3 * j]), f64_to_f32_rn(nrm[3 * j + 1]),
                        f64_to_f32_rn(nrm[3 * j + 2]), 0.f);
-      pp = make_float4(f64_to_f32_rn(s * phi[3 * j]), f64_to_f32_rn(s * phi[3 * j + 1]),
-                       f64_to_f32_rn(s * phi[3 * j + 2]), 0.f);
+      pp = make_float4(s * f64_to_f32_rn(phi[3 * j]), s * f64_to_f32_rn(phi[3 * j + 1]),
+                       s * f64_to_f32_rn(phi[3 * j + 2]), 0.f);
     }
     q.w = lx;
     nn.w = ly;

@@ -261,7 +261,10 @@ void *align_ws(void *ws) {
 }
 
 // Engine launch common to all forms.
-stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st) {
+// direct_out (optional): with one part and targets in caller order, the
+// engines write the caller's output instead of the partial buffer (no finish).
+stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st,
+                      double *direct_out = nullptr) {
   DevInfo di;
   CU(dev_info(di));
   int32_t *counters = at<int32_t>(ws, p.counters);
@@ -273,7 +276,7 @@ stk_status run_engine(const Plan &p, void *ws, EngineParams &P, cudaStream_t st)
   P.drain_limit = P.spin_limit > kSpinLimit ? P.spin_limit : kSpinLimit;
   P.force_expire = g_force_expire;
   P.policy = p.tile.policy;
-  P.part_out = at<double>(ws, p.part);
+  P.part_out = direct_out ? direct_out : at<double>(ws, p.part);
   P.nt = (int32_t)p.nt;
   const int occ = p.mixed ? di.occ_mixed : di.occ_fp64;
   int64_t grid = (int64_t)di.sms * occ;
@@ -629,9 +632,12 @@ stk_status stokes_p2p_leaflists(const double *pts, const double *f, const double
   P.range_ptr = range;
   P.kind = kernels;
   P.kind_alternating = 0;
-  s = run_engine(p, ws, P, st);
+  // points are targets in caller order and there is one part: without
+  // accumulation the engines write out directly
+  const bool direct = !opts->accumulate;
+  s = run_engine(p, ws, P, st, direct ? out : nullptr);
   if (s != STK_OK) return s;
-  launch_finish(n, 1, at<double>(ws, p.part), nullptr, opts->accumulate, out, st);
+  if (!direct) launch_finish(n, 1, at<double>(ws, p.part), nullptr, opts->accumulate, out, st);
   CU(cudaGetLastError());
   return STK_OK;
 }

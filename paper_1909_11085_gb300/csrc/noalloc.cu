@@ -113,6 +113,13 @@ stk_status scratch_address(void **addr, bool lookup) {
 }  // namespace
 
 namespace stk {
+// Identity of the calling thread's current CUDA context (0 if it cannot be
+// read), for caches of per-context handles elsewhere in the library.
+unsigned long long context_id() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  return current_context_id();
+}
+
 // The buffer's address in the current context if stokes_sl_eval_noalloc has
 // run there (its error word is read by stokes_device_status(NULL, 0)).
 stk_status noalloc_scratch(void **addr, size_t *bytes) {

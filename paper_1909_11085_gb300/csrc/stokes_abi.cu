@@ -27,6 +27,10 @@
 
 using namespace stk;
 
+namespace stk {
+unsigned long long context_id();  // noalloc.cu
+}
+
 namespace {
 
 thread_local std::string g_err;
@@ -258,6 +262,68 @@ T *at(void *ws, size_t off) {
 void *align_ws(void *ws) {
   const uintptr_t u = reinterpret_cast<uintptr_t>(ws);
   return reinterpret_cast<void *>((u + 255) & ~(uintptr_t)255);
+}
+
+// A second stream per host thread and device, for the part of a call that can
+// run beside the caller's stream: a fork event recorded on the caller's
+// stream, the work on this stream, a join event the caller's stream waits on
+// (graph capture follows the fork and the join).  The handles belong to one
+// context and are made again in another; none is made while the caller's
+// stream is being captured.
+struct SideStream {
+  unsigned long long ctx = 0;
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int kSideDevices = 64;
+thread_local SideStream t_side[kSideDevices];
+
+SideStream *side_stream(bool create) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kSideDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  SideStream &sd = t_side[dev];
+  const unsigned long long ctx = stk::context_id();
+  if (ctx == 0) return nullptr;
+  if (sd.s && sd.ctx == ctx) return &sd;
+  if (!create) return nullptr;
+  sd = SideStream{};  // handles of an earlier context went with it
+  cudaStream_t st = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+    if (b) cudaEventDestroy(b);
+    if (a) cudaEventDestroy(a);
+    if (st) cudaStreamDestroy(st);
+    cudaGetLastError();
+    return nullptr;
+  }
+  sd.ctx = ctx;
+  sd.s = st;
+  sd.fork = a;
+  sd.join = b;
+  return &sd;
+}
+
+// Forks the side stream off st: returns it with its work ordered after st's
+// work so far, or nullptr (the call then runs on st alone).
+SideStream *fork_side(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  SideStream *sd = side_stream(cs == cudaStreamCaptureStatusNone);
+  if (!sd) return nullptr;
+  if (cudaEventRecord(sd->fork, st) != cudaSuccess ||
+      cudaStreamWaitEvent(sd->s, sd->fork, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return sd;
 }
 
 // Engine launch common to all forms.
@@ -609,9 +675,12 @@ stk_status stokes_p2p_leaflists(const double *pts, const double *f, const double
   if (!workspace || workspace_bytes < p.total) return fail(STK_ENOMEM, "workspace too small");
   void *ws = align_ws(workspace);
   launch_zero_ints(at<int32_t>(ws, p.counters), 4, st);
+  // the packing runs beside the item build (they meet at the engine)
+  SideStream *sd = fork_side(st);
   s = pack(p, ws, pts, (kernels & K_SL) ? f : nullptr, nrm, (kernels & K_DL) ? phi : nullptr, w,
-           h, (kernels & K_SL) ? mu : 1.0, opts->near_ratio, st);
+           h, (kernels & K_SL) ? mu : 1.0, opts->near_ratio, sd ? sd->s : st);
   if (s != STK_OK) return s;
+  if (sd) CU(cudaEventRecord(sd->join, sd->s));
   int64_t *range = at<int64_t>(ws, p.range);
   launch_widen((int64_t)nleaf + 1, leaf_ptr, range, st);
   int32_t *counters = at<int32_t>(ws, p.counters);
@@ -620,6 +689,7 @@ stk_status stokes_p2p_leaflists(const double *pts, const double *f, const double
                      at<int32_t>(ws, p.offs), counters, at<Item>(ws, p.items), keys, vals, st);
   });
   CU(cudaGetLastError());
+  if (sd) CU(cudaStreamWaitEvent(st, sd->join, 0));
   EngineParams P;
   std::memset(&P, 0, sizeof(P));
   P.src64 = pts;
@@ -895,6 +965,7 @@ stk_status capture_graph(cudaStream_t st, Call call, void **graph_exec) {
   if (!st) return fail(STK_EINVAL, "capture needs a stream other than the legacy default stream");
   DevInfo di;
   CU(dev_info(di));  // one-time per-device set-up stays outside the capture
+  side_stream(true);
   const cudaEvent_t save0 = g_ev_start, save1 = g_ev_stop;
   g_ev_start = g_ev_stop = nullptr;
   CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));

@@ -55,6 +55,46 @@ def test_p2p_repeat_is_deterministic(lib, small):
     plan.device_status()
 
 
+def test_p2p_caller_streams_graph_and_accumulate(lib, small):
+    """The packing runs on a second stream of the library's, forked from the
+    caller's stream and joined back before the engine.  Calls on two caller
+    streams issued back to back without synchronising, and a captured graph of
+    the call, give the same bits as a plain call; the accumulating form (which
+    keeps the finish kernel, the plain one writes out directly) adds onto out."""
+    import torch
+    c, t = small, small.tree
+    n = c.pts.shape[0]
+    pts, f, phi, nrm, w, h = cuda(c.pts, c.f, c.phi, c.nrm, c.w, c.h)
+    plan_a = lib.P2PPlan(n, t.leaf_ptr, t.ulist_ptr, t.ulist_idx, 3)
+    plan_b = lib.P2PPlan(n, t.leaf_ptr, t.ulist_ptr, t.ulist_idx, 3)
+    ref = plan_a(pts, f, phi, nrm, w, h).clone()
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for k in range(6):
+        st, plan = (s1, plan_a) if k % 2 == 0 else (s2, plan_b)
+        with torch.cuda.stream(st):
+            o = torch.empty_like(ref)
+            plan(pts, f, phi, nrm, w, h, out=o)
+            outs.append(o)
+    torch.cuda.synchronize()
+    for o in outs:
+        assert torch.equal(o, ref)
+    g = plan_a.capture(pts, f, phi, nrm, w, h)
+    g.out.zero_()
+    g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(g.out, ref)
+    base = torch.full_like(ref, 0.25)
+    acc = plan_b(pts, f, phi, nrm, w, h, out=base.clone(), accumulate=True)
+    torch.cuda.synchronize()
+    assert torch.allclose(acc - base, ref, rtol=0, atol=1e-12 * float(ref.abs().max()))
+    plan_a.device_status()
+    plan_b.device_status()
+    exact = oracle.p2p(c.pts, c.f, c.phi, c.nrm, c.w, t.leaf_ptr, t.ulist_ptr, t.ulist_idx, 3, 1.0)
+    assert rel_l2(ref.cpu().numpy(), exact) <= 1e-6
+
+
 @pytest.fixture(scope="module")
 def full():
     return W.p2p_workload()

@@ -72,7 +72,10 @@ def test_constant_density_identity_on_gpu(lib):
         assert np.abs(u + c).max() <= tol
 
 
-@pytest.mark.parametrize("ns,nt", [(1, 1), (1, 130), (7, 3), (129, 257), (300, 1000), (2, 0)])
+# (5000, 300) and (1000, 4000): the one-launch small form with many strided
+# source splits whose counts differ by one, and targets that end mid-block
+@pytest.mark.parametrize("ns,nt", [(1, 1), (1, 130), (7, 3), (129, 257), (300, 1000), (2, 0),
+                                   (5000, 300), (1000, 4000)])
 def test_ragged_sizes(lib, ns, nt):
     rng = W.rng_for(100 + ns + nt)
     y = rng.uniform(-3, 3, (ns, 3))

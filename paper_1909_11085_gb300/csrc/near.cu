@@ -12,10 +12,14 @@
 // One warp per item, persistent, items in the engine's cost order:
 //  1. the item's frame and its targets' local coordinates, as the engine
 //     stored them (so the decisions below match the engine's bit for bit);
-//  2. its sources, 32 per round across segment boundaries: a conservative box
-//     test on the 16-byte position record alone, then for the few sources it
-//     keeps, the exact local coordinates and the engine's box test; each
-//     candidate is broadcast and every lane tests its targets;
+//  2. the candidate sources the engine listed for the item: each lane takes
+//     one, computes its local coordinates and tests it against every target
+//     (two per packed FP32 instruction) into a bit mask.  An item whose list
+//     overflowed has all its sources scanned again, 32 per round across
+//     segment boundaries: a conservative box test on the 16-byte position
+//     record, then for the few sources it keeps the exact local coordinates
+//     and the engine's box test; each candidate is broadcast and every lane
+//     tests its targets;
 //  3. near pairs go to a queue in shared memory in a fixed order; a full
 //     queue is evaluated one pair per lane (the FP64 pipe of GB300 runs at
 //     1/64 of the FP32 rate, so it is only ever fed full warps), and the

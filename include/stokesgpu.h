@@ -111,6 +111,11 @@ stk_status stokes_direct_workspace_size(int64_t ns, int64_t nt, int32_t kernels,
  * target: out_i = sum over sources in the leaves of U(leaf(i)).
  * kernels: 1 = SL (uses f), 2 = DL (uses nrm, phi), 3 = both.  Unused density
  * pointers may be NULL.  Leaves may hold at most 65535 points.
+ * The call stays ordered on `stream` as every other: part of its work (the
+ * packing of the sources) runs on a second stream the library keeps per host
+ * thread and device (created on the first call outside a stream capture,
+ * made again in a new context), forked from and joined back into `stream` by
+ * events, which a stream capture follows.
  */
 stk_status stokes_p2p_leaflists(const double *pts, const double *f, const double *phi,
                                 const double *nrm, const double *w, const double *h, int64_t n,

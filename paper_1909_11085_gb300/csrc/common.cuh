@@ -101,33 +101,66 @@ __device__ __forceinline__ int seg_kind(const EngineParams &P, int32_t sid) {
 
 // FP64 <-> FP32 conversions on the integer pipe.  GB300 runs conversions
 // that involve FP64 on its FP64 pipe (1/64 of the FP32 rate), where they were
-// a third of the near pairs' FP64 operations and most of the packing's.
+// a third of the near pairs' FP64 operations and most of the packing's.  An
+// FP64 instruction on a rarely taken path costs the same pipe time as a taken
+// one when the compiler predicates it, so every finite input is handled here
+// with integer operations, and only infinities and NaN (never met by the sums)
+// reach the hardware conversion, through a call that runs only when made.
 // f64_to_f32_rn rounds to nearest, ties to even (IEEE 754 binary64 to
-// binary32), for values whose FP32 result is normal: the sign, the rebiased
-// exponent and the top 23 of the 52 fraction bits, plus one when the 29
-// dropped bits are above half an FP32 ulp or exactly half with an odd kept
-// fraction; a carry out of the fraction moves into the exponent, so a value
-// just below 2^k rounds up to 2^k and one at or above FLT_MAX + ulp/2 to
-// infinity.  Zeros, results below 2^-126, infinities and NaN take the
-// hardware conversion.  f32_to_f64 widens a normal float exactly (exponent
-// rebiased by 1023 - 127, fraction shifted into the top of the 52 bits).
+// binary32): for a normal result the sign, the rebiased exponent and the top
+// 23 of the 52 fraction bits, plus one when the 29 dropped bits are above half
+// an FP32 ulp or exactly half with an odd kept fraction (a carry out of the
+// fraction moves into the exponent, so a value just below 2^k rounds up to
+// 2^k and one at or above FLT_MAX + ulp/2 to infinity); values of 2^128 and
+// above give infinity; below 2^-126 the 53-bit significand is shifted to a
+// multiple of 2^-149 with the same rounding (subnormal results, zero below
+// 2^-150, the smallest normal when the rounding carries).  f32_to_f64 widens
+// exactly: rebiased exponent and the fraction in the top of the 52 bits, a
+// subnormal float normalised by its leading bit.
+static __device__ __noinline__ float f64_to_f32_special(double v) { return __double2float_rn(v); }
+static __device__ __noinline__ double f32_to_f64_special(float f) { return (double)f; }
+// |v| < 2^-126 (out of line too: rare, and several 64-bit operations): k =
+// 1.f x 2^(e + 149) rounded to nearest even, the result k x 2^-149.
+static __device__ __noinline__ float f64_to_f32_small(unsigned long long u) {
+  const int ef = (int)((u >> 52) & 0x7ffu), sh = -97 - (ef - 1023);  // shift >= 30
+  unsigned k = 0u;
+  if (ef != 0 && sh <= 53) {
+    const unsigned long long m = (u & 0xfffffffffffffull) | (1ull << 52);
+    const unsigned long long q = m >> sh, rest = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    k = (unsigned)q + ((rest > half || (rest == half && (q & 1ull))) ? 1u : 0u);
+  }
+  return __uint_as_float(((unsigned)(u >> 32) & 0x80000000u) | k);
+}
+// A subnormal float m x 2^-149 = 1.f x 2^(p - 149), p the index of m's leading bit.
+static __device__ __noinline__ double f32_to_f64_small(unsigned b) {
+  const unsigned m = b & 0x7fffffu, sign = b & 0x80000000u;
+  const int p = 31 - __clz(m);
+  const unsigned long long frac = ((unsigned long long)m << (52 - p)) & 0xfffffffffffffull;
+  return __hiloint2double((int)(sign | ((unsigned)(p + 874) << 20) | (unsigned)(frac >> 32)),
+                          (int)(unsigned)frac);
+}
 __device__ __forceinline__ float f64_to_f32_rn(double v) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
   const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023;  // unbiased exponent
-  if (e < -126 || e > 127) return __double2float_rn(v);
+  const unsigned sign = hi & 0x80000000u;
+  const int ef = (int)((hi >> 20) & 0x7ffu), e = ef - 1023;  // e: unbiased exponent
+  if (ef == 0x7ff) return f64_to_f32_special(v);            // infinity or NaN
+  if (e < -126)  // zero (common: the low part of an FP32-exact value) inline, the rest out of line
+    return (u << 1) == 0ull ? __uint_as_float(sign) : f64_to_f32_small(u);
+  if (e > 127) return __uint_as_float(sign | 0x7f800000u);
   const unsigned kept = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 fraction bits
   const unsigned dropped = lo & 0x1fffffffu;                    // the other 29
   const unsigned up =
       (dropped > 0x10000000u || (dropped == 0x10000000u && (kept & 1u))) ? 1u : 0u;
-  return __uint_as_float(((hi & 0x80000000u) | ((unsigned)(e + 127) << 23) | kept) + up);
+  return __uint_as_float((sign | ((unsigned)(e + 127) << 23) | kept) + up);
 }
 __device__ __forceinline__ double f32_to_f64(float f) {
   const unsigned b = __float_as_uint(f);
-  const unsigned e = (b >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-  return __hiloint2double((int)hi, (int)(b << 29));
+  const unsigned e = (b >> 23) & 0xffu, m = b & 0x7fffffu, sign = b & 0x80000000u;
+  if (e == 0xffu) return f32_to_f64_special(f);  // infinity or NaN
+  if (e != 0u) return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+  if (m == 0u) return __hiloint2double((int)sign, 0);
+  return f32_to_f64_small(b);
 }
 
 // Exact-enough split of (x - c) into two floats; used identically for
@@ -200,14 +233,48 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p) {
   lo = __fadd_rn(lo, err);
 }
 
+// The kernel products of a near pair in FP32 from its unit vector e = d/|r|
+// and 1/|r| (q and psi carry the weight and kernel constant):
+//   SL: (q + e (e.q)) / r      DL: e (e.psi)(e.n) / r^2
+__device__ __forceinline__ float3 near_products(float ex, float ey, float ez, float ri, float4 q,
+                                                float4 n, float4 p, int kind) {
+  float3 c = make_float3(0.f, 0.f, 0.f);
+  if (kind & K_SL) {
+    const float eq = fmaf(ex, q.x, fmaf(ey, q.y, ez * q.z));
+    c.x = fmaf(ex, eq, q.x) * ri;
+    c.y = fmaf(ey, eq, q.y) * ri;
+    c.z = fmaf(ez, eq, q.z) * ri;
+  }
+  if (kind & K_DL) {
+    const float ep = fmaf(ex, p.x, fmaf(ey, p.y, ez * p.z));
+    const float en = fmaf(ex, n.x, fmaf(ey, n.y, ez * n.z));
+    const float cc = (ep * en) * (ri * ri);
+    c.x = fmaf(ex, cc, c.x);
+    c.y = fmaf(ey, cc, c.y);
+    c.z = fmaf(ez, cc, c.z);
+  }
+  return c;
+}
+
+// A near pair whose r^2 in FP32 falls outside (1e-30, 1e30), where the FP32
+// unit vector could underflow or the estimate overflow: 1/|r| and the unit
+// vector from the FP64 values.  Out of line, so that its FP64 work runs only
+// for such a pair (predicated into the common path it would hold the FP64
+// pipe for every pair).
+static __device__ __noinline__ float3 near_contrib_extreme(const double *x, const double *y, float4 q,
+                                                    float4 n, float4 p, int kind) {
+  const double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+  const double rid = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+  return near_products(f64_to_f32_rn(dx * rid), f64_to_f32_rn(dy * rid), f64_to_f32_rn(dz * rid),
+                       f64_to_f32_rn(rid), q, n, p, kind);
+}
+
 // Near pair (|x - y| < alpha h_y): the difference x - y in FP64 from the FP64
 // positions and 1/|r| to FP32 rounding from the FP64 r^2 (one Newton step on
-// the FP32 estimate, its residual in FP64); the
-// kernel products in FP32, written through the unit vector e = d/|r| so that
-// they stay in range however close the pair is:
-//   SL: (q + e (e.q)) / r      DL: e (e.psi)(e.n) / r^2
-// q and psi carry the weight and kernel constant.  Returns false for a pair at
-// zero distance (no contribution).
+// the FP32 estimate, its residual in FP64); the kernel products in FP32,
+// written through the unit vector so that they stay in range however close
+// the pair is (near_products).  Returns false for a pair at zero distance (no
+// contribution).
 __device__ __forceinline__ bool near_contrib(const double *x, const double *y, float4 q,
                                              float4 n, float4 p, int kind, float (&c)[3]) {
   // The FP64 instructions below run on GB300's FP64 pipe (1/64 of the FP32
@@ -218,43 +285,23 @@ __device__ __forceinline__ bool near_contrib(const double *x, const double *y, f
   const float fx = f64_to_f32_rn(dx), fy = f64_to_f32_rn(dy), fz = f64_to_f32_rn(dz);
   if (fx == 0.f && fy == 0.f && fz == 0.f) return false;  // coincident (to 1e-45)
   const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
-  const double r2 = dx * dx + dy * dy + dz * dz;
-  double rid = 0.0;
-  float ri;
+  float3 v;
   if (r2f > 1e-30f && r2f < 1e30f) {
     // One Newton step on the FP32 estimate y0 = rsqrt(r^2 in FP32):
     // 1/|r| = y0 (1 + e/2 + 3e^2/8 + ...) with the residual e = 1 - r^2 y0^2
     // (|e| < 2^-21), which cancels and so is formed in FP64 from the FP64
     // r^2; e/2 then needs only FP32, and the dropped 3e^2/8 < 2^-43.
+    const double r2 = dx * dx + dy * dy + dz * dz;
     const float y0f = rsqrt_ftz(r2f);
     const double y0 = f32_to_f64(y0f);
-    ri = fmaf(0.5f * y0f, f64_to_f32_rn(fma(-r2, y0 * y0, 1.0)), y0f);
+    const float ri = fmaf(0.5f * y0f, f64_to_f32_rn(fma(-r2, y0 * y0, 1.0)), y0f);
+    v = near_products(fx * ri, fy * ri, fz * ri, ri, q, n, p, kind);
   } else {
-    rid = 1.0 / sqrt(r2);
-    ri = f64_to_f32_rn(rid);
+    v = near_contrib_extreme(x, y, q, n, p, kind);
   }
-  // unit vector in FP32; below r2 ~ 1e-30 the FP64 product avoids underflow
-  float ex = fx * ri, ey = fy * ri, ez = fz * ri;
-  if (!(r2f > 1e-30f)) {
-    ex = __double2float_rn(dx * rid);
-    ey = __double2float_rn(dy * rid);
-    ez = __double2float_rn(dz * rid);
-  }
-  c[0] = c[1] = c[2] = 0.f;
-  if (kind & K_SL) {
-    const float eq = fmaf(ex, q.x, fmaf(ey, q.y, ez * q.z));
-    c[0] = fmaf(ex, eq, q.x) * ri;
-    c[1] = fmaf(ey, eq, q.y) * ri;
-    c[2] = fmaf(ez, eq, q.z) * ri;
-  }
-  if (kind & K_DL) {
-    const float ep = fmaf(ex, p.x, fmaf(ey, p.y, ez * p.z));
-    const float en = fmaf(ex, n.x, fmaf(ey, n.y, ez * n.z));
-    const float cc = (ep * en) * (ri * ri);
-    c[0] = fmaf(ex, cc, c[0]);
-    c[1] = fmaf(ey, cc, c[1]);
-    c[2] = fmaf(ez, cc, c[2]);
-  }
+  c[0] = v.x;
+  c[1] = v.y;
+  c[2] = v.z;
   return true;
 }
 
